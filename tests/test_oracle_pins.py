@@ -1,0 +1,331 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+* closed-form input derivatives of one-hidden-layer tanh networks;
+* complex-step input derivatives of deep networks (first order, exact to rounding)
+  and Richardson central differences of those for the second order;
+* complex-step directional derivatives of the loss for the reverse sweep, and the
+  same per coordinate on a tiny network;
+* analytic PDE solutions: the viscous Burgers travelling wave (exactly a
+  one-neuron tanh network), Kovasznay flow (Navier-Stokes), a TE standing mode
+  with PEC walls (Maxwell);
+* closed-form losses of constant networks on symmetric point sets;
+* torch float64 double-backward autograd (the paper's own method);
+* torch.optim.Adam in float64.
+Mutation tests plant a mistake in the oracle and check that a pin catches it.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import pinn_oracle as po
+from synth import Batch, NetSpec, Problem, init_params, ff_matrix, make_batch, make_workload
+from synth.workloads import PDE_BURGERS, PDE_NS, PDE_MAXWELL
+
+
+def _model(spec):
+    return oracle.Model.from_spec(spec)
+
+
+# ------------------------------------------------------------------ tanh derivatives
+
+def test_tanh_identities_against_differences():
+    z = np.linspace(-4, 4, 41)
+    t, t1, t2, t3 = oracle.tanh_derivs(z)
+    # tanh'' = -2 tanh tanh' (the identity used by the GPU jet rule)
+    np.testing.assert_allclose(t2, -2 * t * t1, rtol=1e-13, atol=1e-15)
+    # each derivative is the derivative of the previous one (Richardson central differences)
+    def rich(f, h=1e-3):
+        d = lambda hh: (f(z + hh) - f(z - hh)) / (2 * hh)
+        return (4 * d(h / 2) - d(h)) / 3
+    np.testing.assert_allclose(rich(np.tanh), t1, atol=1e-11)
+    np.testing.assert_allclose(rich(lambda x: oracle.tanh_derivs(x)[1]), t2, atol=1e-10)
+    np.testing.assert_allclose(rich(lambda x: oracle.tanh_derivs(x)[2]), t3, atol=1e-9)
+    # t''' = t' (6 t^2 - 2)
+    np.testing.assert_allclose(t3, t1 * (6 * t * t - 2), atol=1e-13)
+
+
+# ------------------------------------------------------------------ input jets
+
+@pytest.mark.parametrize("rwf", [False, True])
+def test_one_hidden_layer_closed_form(rwf):
+    spec = NetSpec(PDE_BURGERS, 2, 1, [5], rwf=rwf)
+    theta = init_params(spec, 11, random_bias=0.3).astype(np.float64)
+    m = _model(spec)
+    layers = po.unpack(theta, m.dims, rwf)
+    W1 = po.effective_weight(layers[0][0], layers[0][1]); b1 = layers[0][2]
+    c = po.effective_weight(layers[1][0], layers[1][1])[0]; d = layers[1][2][0]
+    X = np.random.default_rng(1).uniform(-1, 1, (7, 2))
+    u, u1, u2 = oracle.output_jets(m, theta, None, X, 2)
+    z = X @ W1.T + b1
+    sech2 = 1 / np.cosh(z) ** 2
+    np.testing.assert_allclose(u[:, 0], np.tanh(z) @ c + d, rtol=1e-14)
+    for k in range(2):
+        np.testing.assert_allclose(u1[k, :, 0], (sech2 * W1[:, k]) @ c, rtol=1e-13, atol=1e-15)
+        for l in range(2):
+            closed = (-2 * np.tanh(z) * sech2 * W1[:, k] * W1[:, l]) @ c
+            np.testing.assert_allclose(u2[k, l, :, 0], closed, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("ff", [0, 3])
+@pytest.mark.parametrize("d_in", [2, 3])
+def test_deep_jets_complex_step_and_differences(ff, d_in):
+    spec = NetSpec(PDE_NS, d_in, 3, [4, 5, 4], ff_m=ff, ff_sigma=1.3, rwf=True)
+    theta = init_params(spec, 21, random_bias=0.2).astype(np.float64)
+    B = ff_matrix(spec, 22)
+    m = _model(spec)
+    X = np.random.default_rng(2).uniform(0, 1, (6, d_in))
+    u, u1, u2 = oracle.output_jets(m, theta, B, X, 2)
+    h = 1e-30
+    for k in range(d_in):
+        Xc = X.astype(complex); Xc[:, k] += 1j * h
+        uc, _, _ = oracle.output_jets(m, theta, B, Xc, 0)
+        np.testing.assert_allclose(u1[k], uc.imag / h, rtol=1e-12, atol=1e-14)
+    # second order: Richardson central differences of the (complex-step-pinned) first order
+    for l in range(d_in):
+        def g(hh):
+            Xp, Xm = X.copy(), X.copy(); Xp[:, l] += hh; Xm[:, l] -= hh
+            return (oracle.output_jets(m, theta, B, Xp, 1)[1] - oracle.output_jets(m, theta, B, Xm, 1)[1]) / (2 * hh)
+        hh = 2e-4
+        fd = (4 * g(hh / 2) - g(hh)) / 3
+        for k in range(d_in):
+            np.testing.assert_allclose(u2[k, l], fd[k], rtol=1e-7, atol=1e-8)
+    np.testing.assert_allclose(u2, np.swapaxes(u2, 0, 1), rtol=1e-13, atol=1e-14)
+
+
+def test_fourier_feature_jets_complex_step():
+    rng = np.random.default_rng(3)
+    B = rng.normal(0, 2.0, (2, 5))
+    X = rng.uniform(0, 1, (4, 2))
+    a, a1, a2 = oracle.input_jets(X, B, 2)
+    # cosine block first (Eq. 14)
+    np.testing.assert_allclose(a[:, :5], np.cos(X @ B), rtol=1e-15)
+    np.testing.assert_allclose(a[:, 5:], np.sin(X @ B), rtol=1e-15)
+    h = 1e-30
+    for k in range(2):
+        Xc = X.astype(complex); Xc[:, k] += 1j * h
+        ac, _, _ = oracle.input_jets(Xc, B, 0)
+        np.testing.assert_allclose(a1[k], ac.imag / h, rtol=1e-13, atol=1e-15)
+        for l in range(2):
+            Xc2 = X.astype(complex); Xc2[:, l] += 1j * h
+            def first(Xr):
+                return oracle.input_jets(Xr, B, 1)[1][k]
+            dd = 1e-4
+            Xp, Xm = X.copy(), X.copy(); Xp[:, l] += dd; Xm[:, l] -= dd
+            np.testing.assert_allclose(a2[k, l], (first(Xp) - first(Xm)) / (2 * dd), atol=2e-7)
+
+
+# ------------------------------------------------------------------ analytic solutions
+
+@pytest.mark.parametrize("rwf", [False, True])
+def test_burgers_travelling_wave_is_a_one_neuron_network(rwf):
+    # u = c - a tanh(a (x - c t) / (2 nu)) solves u_t + u u_x = nu u_xx exactly.
+    a, c, nu = 0.5, 0.3, 0.05
+    k = a / (2 * nu)
+    spec = NetSpec(PDE_BURGERS, 2, 1, [1], rwf=rwf)
+    if rwf:
+        theta = np.array([1.0, -c, math.log(k), 0.0, -a, 0.0, c])
+    else:
+        theta = np.array([k, -k * c, 0.0, -a, c])
+    X = np.random.default_rng(4).uniform([-1, 0], [1, 1], (50, 2))
+    u, u1, u2 = oracle.output_jets(_model(spec), theta, None, X, 2)
+    np.testing.assert_allclose(u[:, 0], c - a * np.tanh(k * (X[:, 0] - c * X[:, 1])), rtol=1e-14)
+    r = oracle.residuals(PDE_BURGERS, u, u1, u2, nu)
+    assert np.max(np.abs(r)) < 1e-13
+    # the residual has teeth: a wrong viscosity leaves a clearly nonzero residual
+    assert np.max(np.abs(oracle.residuals(PDE_BURGERS, u, u1, u2, 1.1 * nu))) > 1e-3
+
+
+def _kovasznay(X, Re):
+    lam = Re / 2 - math.sqrt(Re ** 2 / 4 + 4 * math.pi ** 2)
+    kk = 2 * math.pi
+    x, y = X[:, 0], X[:, 1]
+    e, C, S = np.exp(lam * x), np.cos(kk * y), np.sin(kk * y)
+    N = X.shape[0]
+    u = np.stack([1 - e * C, lam / kk * e * S, 0.5 * (1 - e * e)], axis=1)
+    u1 = np.zeros((2, N, 3)); u2 = np.zeros((2, 2, N, 3))
+    u1[0, :, 0], u1[1, :, 0] = -lam * e * C, kk * e * S
+    u1[0, :, 1], u1[1, :, 1] = lam ** 2 / kk * e * S, lam * e * C
+    u1[0, :, 2], u1[1, :, 2] = -lam * e * e, 0.0
+    u2[0, 0, :, 0], u2[1, 1, :, 0] = -lam ** 2 * e * C, kk ** 2 * e * C
+    u2[0, 0, :, 1], u2[1, 1, :, 1] = lam ** 3 / kk * e * S, -lam * kk * e * S
+    return u, u1, u2
+
+
+def test_kovasznay_flow_zero_navier_stokes_residual():
+    Re = 100.0
+    X = np.random.default_rng(5).uniform(0, 1, (64, 2))
+    u, u1, u2 = _kovasznay(X, Re)
+    r = oracle.residuals(PDE_NS, u, u1, u2, 1 / Re)
+    assert np.max(np.abs(r)) < 1e-12
+    assert np.max(np.abs(oracle.residuals(PDE_NS, u, u1, u2, 1 / 50.0))) > 1e-3
+
+
+def test_te_standing_mode_zero_maxwell_residual():
+    mx, ny = 2, 3
+    w = math.pi * math.sqrt(mx * mx + ny * ny)
+    X = np.random.default_rng(6).uniform(0, 1, (64, 3))
+    x, y, t = X[:, 0], X[:, 1], X[:, 2]
+    sx, cx = np.sin(mx * math.pi * x), np.cos(mx * math.pi * x)
+    sy, cy = np.sin(ny * math.pi * y), np.cos(ny * math.pi * y)
+    st, ct = np.sin(w * t), np.cos(w * t)
+    N = X.shape[0]
+    u = np.stack([sx * sy * ct, -(ny * math.pi / w) * sx * cy * st, (mx * math.pi / w) * cx * sy * st], axis=1)
+    u1 = np.zeros((3, N, 3))
+    u1[:, :, 0] = [mx * math.pi * cx * sy * ct, ny * math.pi * sx * cy * ct, -w * sx * sy * st]
+    u1[:, :, 1] = [-(ny * math.pi / w) * mx * math.pi * cx * cy * st,
+                   (ny * math.pi / w) * ny * math.pi * sx * sy * st,
+                   -(ny * math.pi) * sx * cy * ct]
+    u1[:, :, 2] = [-(mx * math.pi / w) * mx * math.pi * sx * sy * st,
+                   (mx * math.pi / w) * ny * math.pi * cx * cy * st,
+                   (mx * math.pi) * cx * sy * ct]
+    r = oracle.residuals(PDE_MAXWELL, u, u1, None, 0.0)
+    assert np.max(np.abs(r)) < 1e-12
+    # PEC: Ez vanishes on the walls
+    assert abs(math.sin(mx * math.pi * 1.0)) < 1e-12 and abs(math.sin(ny * math.pi * 0.0)) < 1e-15
+    # a sign slip (Hy_x + Hx_y) would be caught
+    bad = u1.copy(); bad[1, :, 1] *= -1
+    assert np.max(np.abs(oracle.residuals(PDE_MAXWELL, u, bad, None, 0.0))) > 1e-2
+
+
+# ------------------------------------------------------------------ loss definitions
+
+def _constant_net_theta(spec, const):
+    m = _model(spec)
+    theta = np.zeros(sum(fo * fi + fo + (fo if spec.rwf else 0) for fi, fo in m.dims))
+    theta[-spec.d_out:] = const      # output bias is the last block
+    return m, theta
+
+
+def test_constant_network_burgers_loss_closed_form():
+    spec = NetSpec(PDE_BURGERS, 2, 1, [3, 3])
+    c = 0.7
+    m, theta = _constant_net_theta(spec, [c])
+    n = 64
+    xi = -1 + (2 * np.arange(n) + 1) / n           # midpoint grid over one full period of sin(pi x)
+    batch = Batch(np.random.default_rng(7).uniform(0, 1, (2, 16)),
+                  np.stack([xi, np.zeros(n)]), -np.sin(np.pi * xi)[None], 1,
+                  np.stack([np.r_[-np.ones(4), np.ones(4)], np.linspace(0, 1, 8)]), np.zeros((1, 8)), 1)
+    terms = oracle.loss_terms(m, theta, None, batch, 0.01, (1.0, 2.0, 3.0))
+    assert abs(terms["pde"]) < 1e-30
+    assert terms["ic"] == pytest.approx(c * c + 0.5, rel=1e-13)
+    assert terms["bc"] == pytest.approx(c * c, rel=1e-13)
+    assert terms["total"] == pytest.approx(2.0 * (c * c + 0.5) + 3.0 * c * c, rel=1e-13)
+
+
+def test_constant_network_cavity_wall_loss_closed_form():
+    spec = NetSpec(PDE_NS, 2, 3, [4], ff_m=2, ff_sigma=1.0, rwf=True)
+    u0, v0, p0 = 0.4, -0.2, 5.0
+    m, theta = _constant_net_theta(spec, [u0, v0, p0])
+    B = ff_matrix(spec, 8)
+    batch = make_batch(PDE_NS, 32, 0, 400, 9, 10)
+    terms = oracle.loss_terms(m, theta, B, batch, 0.01)
+    assert abs(terms["pde"]) < 1e-30      # constant outputs have zero derivatives
+    # 1/4 of the wall points are on the lid (u = 1); v = 0 everywhere; p unconstrained
+    assert terms["bc"] == pytest.approx(0.75 * u0 ** 2 + 0.25 * (u0 - 1) ** 2 + v0 ** 2, rel=1e-6)
+
+
+# ------------------------------------------------------------------ gradient
+
+@pytest.mark.parametrize("name", ["burgers1d_4x64", "ns_cavity_6x256", "maxwell_te_5x512"])
+def test_gradient_complex_step_directions(name):
+    w, p, B, b = make_workload(name, n_res=48, n_ic=16, n_bc=16, random_bias=0.1)
+    if w.spec.widths[0] > 64:
+        w.spec.widths = [16] * 3
+        from synth import init_params as ip
+        p = ip(w.spec, 99, 0.1)
+    m = _model(w.spec)
+    terms, g = oracle.loss_and_grad(m, p, B, b, w.problem.nu, (1.0, 0.5, 2.0))
+    rng = np.random.default_rng(8)
+    h = 1e-30
+    for _ in range(3):
+        v = rng.standard_normal(p.shape)
+        tc = oracle.loss_terms(m, p.astype(np.float64) + 1j * h * v, B, b, w.problem.nu, (1.0, 0.5, 2.0))
+        assert tc["total"].real == pytest.approx(terms["total"], rel=1e-13)
+        assert tc["total"].imag / h == pytest.approx(g @ v, rel=1e-11)
+
+
+@pytest.mark.parametrize("pde,d_in,ff", [(PDE_BURGERS, 2, 0), (PDE_NS, 2, 2), (PDE_MAXWELL, 3, 0)])
+def test_gradient_every_coordinate_complex_step(pde, d_in, ff):
+    spec = NetSpec(pde, d_in, 1 if pde == PDE_BURGERS else 3, [3, 4], ff_m=ff, ff_sigma=1.0, rwf=True)
+    p = init_params(spec, 31, 0.2).astype(np.float64)
+    B = ff_matrix(spec, 32)
+    b = make_batch(pde, 8, 4, 8, 33, 34)
+    if pde == PDE_NS:
+        b = Batch(b.x_res, b.x_ic, b.g_ic, 0, b.x_bc, b.g_bc, 0b111)
+    m = _model(spec)
+    _, g = oracle.loss_and_grad(m, p, B, b, 0.02)
+    h = 1e-30
+    cs = np.empty_like(p)
+    for i in range(p.size):
+        pc = p.astype(complex); pc[i] += 1j * h
+        cs[i] = oracle.loss_terms(m, pc, B, b, 0.02)["total"].imag / h
+    np.testing.assert_allclose(g, cs, rtol=1e-10, atol=1e-14 * np.max(np.abs(cs)))
+
+
+@pytest.mark.parametrize("name", ["burgers1d_4x64", "ns_cavity_6x256", "maxwell_te_5x512"])
+def test_agrees_with_torch_float64_double_backward(name):
+    from baseline import torch_autograd
+    w, p, B, b = make_workload(name, n_res=64, n_ic=32, n_bc=32, random_bias=0.1)
+    if w.spec.widths[0] > 64:
+        w.spec.widths = [32] * len(w.spec.widths)
+        p = init_params(w.spec, 77, 0.1)
+    m = _model(w.spec)
+    terms, g = oracle.loss_and_grad(m, p, B, b, w.problem.nu, (1.0, 0.7, 1.3))
+    tl, tg, _ = torch_autograd.loss_and_grad(w.spec, p, B, b, w.problem.nu, lambdas=(1.0, 0.7, 1.3))
+    assert float(tl) == pytest.approx(terms["total"], rel=1e-12)
+    np.testing.assert_allclose(tg.numpy(), g, rtol=1e-9, atol=1e-12 * np.max(np.abs(g)))
+
+
+# ------------------------------------------------------------------ Adam
+
+def test_adam_matches_torch_float64():
+    rng = np.random.default_rng(9)
+    theta = rng.standard_normal(50)
+    t = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([t], lr=1e-3)
+    m = np.zeros(50); v = np.zeros(50); th = theta.copy()
+    for step in range(1, 6):
+        g = rng.standard_normal(50)
+        t.grad = torch.tensor(g)
+        opt.step()
+        th, m, v = oracle.adam_step(th, g, m, v, step, 1e-3)
+    np.testing.assert_allclose(th, t.detach().numpy(), rtol=1e-14, atol=1e-16)
+
+
+# ------------------------------------------------------------------ mutations
+
+def test_mutation_dropped_second_order_term_is_caught(monkeypatch):
+    """Plant a mistake (drop t'' from the jet rule's second-order term); the
+    closed-form pin must see it."""
+    orig = po.tanh_derivs
+
+    def broken(z):
+        t, t1, t2, t3 = orig(z)
+        return t, t1, 0 * t2, t3
+    spec = NetSpec(PDE_BURGERS, 2, 1, [5])
+    theta = init_params(spec, 11, random_bias=0.3).astype(np.float64)
+    m = _model(spec)
+    X = np.random.default_rng(1).uniform(-1, 1, (7, 2))
+    good = oracle.output_jets(m, theta, None, X, 2)[2]
+    monkeypatch.setattr(po, "tanh_derivs", broken)
+    bad = oracle.output_jets(m, theta, None, X, 2)[2]
+    assert np.max(np.abs(good - bad)) > 1e-3
+
+
+def test_mutation_wrong_adjoint_sign_is_caught(monkeypatch):
+    """Plant a sign error in a residual seed; the complex-step pin must see it."""
+    w, p, B, b = make_workload("burgers1d_4x64", n_res=16, n_ic=4, n_bc=4, random_bias=0.1)
+    m = _model(w.spec)
+    orig = po.residual_seeds
+
+    def broken(*a, **k):
+        ub, u1b, u2b = orig(*a, **k)
+        return ub, u1b, -u2b
+    monkeypatch.setattr(po, "residual_seeds", broken)
+    _, g = oracle.loss_and_grad(m, p, B, b, w.problem.nu)
+    v = np.random.default_rng(3).standard_normal(p.shape)
+    cs = oracle.loss_terms(m, p.astype(np.float64) + 1e-30j * v, B, b, w.problem.nu)["total"].imag / 1e-30
+    assert abs(cs - g @ v) > 1e-6 * abs(cs)
