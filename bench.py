@@ -1,0 +1,429 @@
+#!/usr/bin/env python
+"""Throughput of one PINN loss + gradient step (collocation points per second).
+
+Default workload: the steady lid-driven cavity at Re = 100 with Gaussian Fourier
+features (128 frequencies, sigma 1), random weight factorisation and a 6 x 256
+tanh MLP -> (u, v, p), 65,536 interior + 4 x 1,024 wall points, BF16 jet GEMMs
+with FP32 accumulation.  A step is one pinn_loss_grad call (embedding -> jet
+forward -> residual/loss -> adjoint -> ordered FP64 reductions).
+
+Prints one JSON line.  Besides the device-resident throughput it reports the
+end-to-end figure through the public API with host buffers, the phase timings and
+roofline of the dominant kernel, plain torch double-backward autograd on the same
+GPU, and the FP64 oracle on the host cores (a baseline only).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision fp32|tf32|bf16]
+Under torchrun every rank runs an independent replica (no collectives on the data
+path); the value is all points processed over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "collocation pts/sec per loss+grad step"
+UNIT = "points/s"
+CSRC = os.path.join(ROOT, "paper_2604_15645_gb300", "csrc")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ns_cavity_6x256")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--no-torch", action="store_true", help="skip the torch autograd baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ helpers
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def blas_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        n = [i["num_threads"] for i in info if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def src_sha():
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        smax = 0.0
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+            except ValueError:
+                continue
+            for i, n in enumerate(names):
+                if r[5 + i].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ workload
+
+def workload_inputs(name):
+    from synth import make_workload
+    w, params, B, batch = make_workload(name)
+    return w, params, B, batch
+
+
+def gemm_flops(w, ncols):
+    """Algorithmic jet-GEMM FLOPs of one step, per phase (2 per multiply-add)."""
+    spec = w.spec
+    first_in = 2 * spec.ff_m if spec.ff_m else spec.d_in
+    dims, prev = [], first_in
+    for width in spec.widths:
+        dims.append((prev, width))
+        prev = width
+    fwd = dw = adj = 0.0
+    for li, (fi, fo) in enumerate(dims):
+        raw = (li == 0 and not spec.ff_m)
+        if raw:
+            continue
+        fwd += 2.0 * fi * fo * ncols
+        dw += 2.0 * fi * fo * ncols
+        if li >= 1:
+            adj += 2.0 * fi * fo * ncols
+    dw += 2.0 * spec.d_out * spec.widths[-1] * ncols    # output-layer dW shares the phase
+    return {"fwd_gemm": fwd, "dw_gemm": dw, "adj_gemm": adj}
+
+
+# ------------------------------------------------------------------------------ arms
+
+def oracle_sample_rate(w, params, B, batch, target_s=10.0, n_res=8192):
+    """FP64 oracle throughput on a bounded sample of the workload (host cores)."""
+    import oracle
+    frac = min(1.0, n_res / max(batch.n_res, 1))
+    sub = batch.subset(min(n_res, batch.n_res), int(round(batch.n_ic * frac)), int(round(batch.n_bc * frac)))
+    m = oracle.Model.from_spec(w.spec)
+    lam = (w.problem.lambda_pde, w.problem.lambda_ic, w.problem.lambda_bc)
+    pts = sub.n_res + sub.n_ic + sub.n_bc
+    t0 = time.perf_counter()
+    calls = 0
+    while True:
+        oracle.loss_and_grad(m, params, B, sub, w.problem.nu, lam)
+        calls += 1
+        if time.perf_counter() - t0 >= target_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": pts * calls / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": f"{sub.n_res} interior + {sub.n_ic} initial + {sub.n_bc} boundary points of {w.name}, "
+                      f"{calls} loss+grad call(s), FP64 numpy"}
+
+
+def torch_autograd_rate(w, params, B, batch, steps=5, warmup=2):
+    """The paper's recipe (torch.autograd.grad create_graph + loss.backward), FP32,
+    TF32 off, same parameters and points, CUDA events."""
+    import torch
+    from baseline import torch_autograd as ta
+    torch.backends.cuda.matmul.allow_tf32 = False
+    torch.backends.cudnn.allow_tf32 = False
+    model = ta.TorchPINN(w.spec, params, B, "cuda", torch.float32)
+    bt = ta.batch_to_torch(batch, "cuda", torch.float32)
+    lam = (w.problem.lambda_pde, w.problem.lambda_ic, w.problem.lambda_bc)
+
+    def step():
+        model.zero_grad()
+        total, _ = ta.loss(model, bt, w.problem.nu, lam)
+        total.backward()
+        return total
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pts = batch.n_res + batch.n_ic + batch.n_bc
+    return {"value": pts / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "dtype": "f32 (tf32 off)",
+            "how": "torch.autograd.grad(create_graph=True) input derivatives + loss.backward(), eager"}
+
+
+def run_ours(args, ws_n, rank, local):
+    import torch
+    from paper_2604_15645_gb300 import _lib, api
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, params, B, batch = workload_inputs(args.workload)
+    precision = args.precision or w.precision
+    net = api.PinnNet.from_spec(w.spec, precision, device=dev)
+    if B is not None:
+        net.set_ff_matrix(B)
+    db = api.DeviceBatch.from_host(batch, device=dev)
+    p = torch.tensor(params, device=dev)
+    grad = torch.empty_like(p)
+    prob = api.make_problem(w.problem.nu, w.problem.lambda_pde, w.problem.lambda_ic, w.problem.lambda_bc)
+    n_pts = batch.n_res + batch.n_ic + batch.n_bc
+    ncols = 4 * batch.n_res + batch.n_ic + batch.n_bc
+    ws_bytes = net.workspace_bytes(*db.sizes)
+
+    def barrier():
+        if ws_n > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        net.loss_grad(p, db, prob, grad=grad)
+    torch.cuda.synchronize()
+    assert net.status_poll() == 0, "device status after warm-up"
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    _lib.pinn_set_profiling(net.h, True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        net.loss_grad(p, db, prob, grad=grad)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = _lib.pinn_profile_read(net.h)
+    _lib.pinn_set_profiling(net.h, False)
+    clk = clocks.stop()
+    status = net.status_poll()
+
+    # end to end through the public API with host buffers: per step, H2D of the
+    # collocation sets from pinned memory, the step, D2H of the loss terms.
+    host = {k: torch.tensor(getattr(batch, k)).pin_memory() for k in ("x_res", "x_ic", "g_ic", "x_bc", "g_bc")}
+    loss_host = torch.empty(8, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = loss_host.numel() * loss_host.element_size()
+
+    def e2e_step():
+        for k, t in host.items():
+            getattr(db, k).copy_(t, non_blocking=True)
+        terms, _ = net.loss_grad(p, db, prob, grad=grad)
+        loss_host.copy_(terms, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    barrier()
+
+    # max over ranks
+    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device=dev)
+    if ws_n > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max, e2e_ms_max = float(t[0]), float(t[1])
+    if rank != 0:
+        return None
+
+    peaks, peak_src = load_peaks()
+    flops = gemm_flops(w, ncols)
+    gemm_phases = {k: prof[k] for k in ("fwd_gemm", "dw_gemm", "adj_gemm", "out_loss", "embed", "reduce", "rwf")}
+    dom = max(gemm_phases, key=lambda k: gemm_phases[k][0])
+    dom_ms, dom_launches = prof[dom]
+    roof = None
+    if dom in flops and dom_launches > 0:
+        per_launch_ms = dom_ms / dom_launches
+        per_launch_flop = flops[dom] * args.steps / dom_launches
+        achieved = per_launch_flop / (per_launch_ms / 1e3) / 1e12
+        if net.tensor_core_layers(*db.sizes) > 0:
+            peak = peaks["bf16_tflops_sustained"] * (0.5 if precision == "tf32" else 1.0)
+            roof = {"bound": "tensor", "unit": "TFLOP/s"}
+        else:
+            # CUDA-core FP32 FMA peak: 152 SMs x 128 FMA/clk x 2 FLOP x max SM clock
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof = {"bound": "alu", "unit": "TFLOP/s"}
+        roof.update({"kernel": dom, "achieved": round(achieved, 2), "peak": round(peak, 1),
+                     "frac": round(achieved / peak, 4), "traffic": _traffic(dom, args.workload),
+                     "peak_source": peak_src, "flop_per_launch": per_launch_flop,
+                     "launch_ms": round(per_launch_ms, 4)})
+
+    out = {
+        "metric": METRIC, "value": round(n_pts * ws_n / (ms_max / 1e3), 1), "unit": UNIT, "n_gpus": ws_n,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
+        "config": {"workload": w.name, "pde": "ns_steady_2d" if w.spec.pde == 1 else w.spec.pde,
+                   "network": f"{'FF' + str(2 * w.spec.ff_m) + ' -> ' if w.spec.ff_m else ''}"
+                              f"{len(w.spec.widths)}x{w.spec.widths[0]} tanh -> {w.spec.d_out}"
+                              f"{' RWF' if w.spec.rwf else ''}",
+                   "n_res": batch.n_res, "n_ic": batch.n_ic, "n_bc": batch.n_bc, "points_per_step": n_pts,
+                   "jet_columns": ncols, "parallelism": f"replicas x{ws_n}",
+                   "l2": f"working set {ws_bytes / 1e9:.2f} GB per step > 129 MB L2 (no flush needed)"},
+        "e2e": {"value": round(n_pts * ws_n / (e2e_ms_max / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms_max, 4)},
+        "gpu_launches": int(sum(v[1] for v in prof.values() if v[1] > 0)),
+        "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+        "roofline": roof,
+        "clocks": clk,
+        "device_status": status,
+    }
+    if not args.no_torch and ws_n == 1:
+        try:
+            tr = torch_autograd_rate(w, params, B, batch)
+            tr["speedup"] = round(out["value"] / tr["value"], 2)
+            out["torch_autograd"] = tr
+        except Exception as e:   # reported, not hidden
+            out["torch_autograd"] = {"error": repr(e)[:300]}
+    if not args.no_cpu and ws_n == 1:
+        out["cpu_baseline"] = oracle_sample_rate(w, params, B, batch)
+    return out
+
+
+def _traffic(kernel, workload):
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(f"{workload}:{kernel}")
+    if not e or e.get("src_sha") != src_sha():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def run_reference(args, ws_n, rank):
+    """The oracle, as it stands, on the host cores: each step is one FP64 loss+grad
+    call on a bounded sample of the workload (rank 0 only)."""
+    if rank != 0:
+        return None
+    import oracle
+    w, params, B, batch = workload_inputs(args.workload)
+    n_res = 1024
+    frac = n_res / max(batch.n_res, 1)
+    sub = batch.subset(min(n_res, batch.n_res), int(round(batch.n_ic * frac)), int(round(batch.n_bc * frac)))
+    m = oracle.Model.from_spec(w.spec)
+    lam = (w.problem.lambda_pde, w.problem.lambda_ic, w.problem.lambda_bc)
+    for _ in range(args.warmup):
+        oracle.loss_and_grad(m, params, B, sub, w.problem.nu, lam)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.loss_and_grad(m, params, B, sub, w.problem.nu, lam)
+    dt = (time.perf_counter() - t0) / args.steps
+    pts = sub.n_res + sub.n_ic + sub.n_bc
+    v = pts / dt
+    sample = f"{sub.n_res} interior + {sub.n_ic} initial + {sub.n_bc} boundary points of {w.name} per step"
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": UNIT, "n_gpus": ws_n,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sample": sample, "parallelism": "host cores"},
+            "cpu_baseline": {"value": round(v, 2), "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws_n, rank, local = dist_setup()
+    if args.impl == "reference":
+        out = run_reference(args, ws_n, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    import torch
+    if ws_n > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2604_15645_gb300 import _lib
+    _lib.load()
+    out = run_ours(args, ws_n, rank, local)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if ws_n > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * pinn.h - C ABI of the GB300 PINN loss + gradient library (libpinn.so).
+ *
+ * The library computes, on one GPU, the physics-informed loss of a tanh MLP
+ * over a batch of collocation points and its gradient with respect to the
+ * network parameters, plus a fused Adam update.  What is computed follows the
+ * paper (arXiv 2604.15645):
+ *   - MLP layers f = W g + b, g = tanh(f), final layer linear (Sec. 2.2, Eqs. 4-6);
+ *   - random Fourier features gamma(x) = [cos(xB), sin(xB)], B frozen (Sec. 2.7.1, Eq. 14);
+ *   - random weight factorisation W = diag(exp(s)) V on every layer (Sec. 2.7.2, Eq. 15);
+ *   - composite MSE loss, each term the mean over its own point set (Sec. 2.3,
+ *     Eqs. 10-13) weighted by lambda_pde, lambda_ic, lambda_bc (Sec. 2.7.4, Eq. 17);
+ *   - residuals of viscous Burgers (Sec. 4.3 with a viscosity term), steady
+ *     incompressible Navier-Stokes (Sec. 4.4) and TE Maxwell, eps = mu = 1 (Sec. 4.7);
+ *   - Adam (Sec. 2.7.5).
+ * Input derivatives, which the paper takes with autograd, are carried as
+ * per-point jets (value plus derivative rows) through every layer, and the
+ * parameter gradient comes from a hand-written adjoint of those jets.
+ *
+ * Conventions for every entry point:
+ *   - All pointers named d_* are DEVICE pointers owned by the caller; the library
+ *     never frees them.  Host pointers are read during the call only.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  A call returns once the work is
+ *     queued.
+ *   - Argument errors are detected on the host and returned synchronously
+ *     without queuing work.  Numerical faults found on the device (a non-finite
+ *     loss, or a kernel wait that ran past its bound) are latched in a device
+ *     status word and reported by pinn_status_poll().
+ *   - After pinn_create() no entry point allocates device memory: the caller
+ *     provides the workspace (size from pinn_workspace_bytes()).
+ *   - A handle is not thread-safe; one handle per host thread.
+ */
+#ifndef PINN_H
+#define PINN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PINN_API __attribute__((visibility("default")))
+#else
+#define PINN_API
+#endif
+
+#define PINN_MAX_HIDDEN 16
+#define PINN_LOSS_TERMS 8
+
+typedef enum {
+  PINN_OK = 0,
+  PINN_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or spec field        */
+  PINN_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement        */
+  PINN_ERR_CUDA = 3,          /* a CUDA runtime/driver call failed                  */
+  PINN_ERR_WORKSPACE = 4,     /* workspace smaller than pinn_workspace_bytes()      */
+  PINN_ERR_NONFINITE = 5,     /* device saw a NaN/Inf loss (latched)                */
+  PINN_ERR_TIMEOUT = 6        /* a bounded device-side wait expired (latched)       */
+} pinn_status;
+
+typedef enum {
+  PINN_FP32 = 0,   /* jet GEMMs in FP32 on CUDA cores                            */
+  PINN_TF32 = 1,   /* jet GEMMs on tensor cores, TF32 inputs, FP32 accumulation  */
+  PINN_BF16 = 2    /* jet GEMMs on tensor cores, BF16 inputs, FP32 accumulation  */
+} pinn_precision;
+
+typedef enum {
+  PINN_BURGERS_1D = 0,     /* inputs (x,t),   output u;          r = u_t + u u_x - nu u_xx  */
+  PINN_NS_STEADY_2D = 1,   /* inputs (x,y),   outputs (u,v,p);   momentum x, y + continuity */
+  PINN_MAXWELL_TE_2D = 2   /* inputs (x,y,t), outputs (Ez,Hx,Hy); TE curl equations       */
+} pinn_pde;
+
+/* Network description (pinn_create).  d_in and d_out follow from `pde`
+ * (Burgers 2->1, Navier-Stokes 2->3, Maxwell 3->3). */
+typedef struct {
+  int32_t pde;                       /* pinn_pde                                          */
+  int32_t n_hidden;                  /* L, number of tanh layers, 1..PINN_MAX_HIDDEN      */
+  int32_t widths[PINN_MAX_HIDDEN];   /* widths[0..L-1], each 1..4096                      */
+  int32_t ff_m;                      /* Fourier frequencies m (embedding width 2m), 0=none */
+  int32_t rwf;                       /* 1: every layer is W = diag(exp(s)) V (Eq. 15)     */
+  int32_t precision;                 /* pinn_precision of the hidden-layer jet GEMMs      */
+  int32_t flags;                     /* reserved, must be 0                               */
+} pinn_spec;
+
+/* Loss weights and the PDE coefficient (nu for Burgers; 1/Re for Navier-Stokes;
+ * ignored for Maxwell). */
+typedef struct {
+  double nu;
+  double lambda_pde, lambda_ic, lambda_bc;
+} pinn_problem;
+
+/* One batch of collocation points.  Coordinates are SoA FP32 device arrays
+ * [d_in][n] (coordinate-major, n contiguous); targets are [d_out][n].  Bit c of a
+ * mask constrains output c on that set.  A set with n = 0 or mask = 0 adds no
+ * term.  Pointers of empty sets may be NULL. */
+typedef struct {
+  const float* x_res; int64_t n_res;
+  const float* x_ic;  const float* g_ic; int64_t n_ic; uint32_t ic_mask;
+  const float* x_bc;  const float* g_bc; int64_t n_bc; uint32_t bc_mask;
+} pinn_batch;
+
+typedef struct pinn_handle pinn_handle;
+
+/* Validate `spec`, compute the packed parameter layout and allocate the handle
+ * (host metadata plus a 256-byte device status word).  The parameter vector is
+ * packed per layer l = 1..L+1 as  V_l [fan_out x fan_in, row-major] | s_l [fan_out]
+ * (only if rwf) | b_l [fan_out];  the first fan_in is 2m with Fourier features,
+ * else d_in.  Returns PINN_ERR_INVALID_ARG for a bad spec. */
+PINN_API pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out);
+
+/* Free the handle and its status word.  NULL is accepted. */
+PINN_API pinn_status pinn_destroy(pinn_handle* h);
+
+/* Number of FP32 entries P in the packed parameter (and gradient) vector. */
+PINN_API pinn_status pinn_param_count(const pinn_handle* h, int64_t* P);
+
+/* Bytes of device workspace one call on a batch of these sizes needs (jets of
+ * every layer, adjoints, split reduction partials). */
+PINN_API pinn_status pinn_workspace_bytes(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc,
+                                 size_t* bytes);
+
+/* Register the frozen Fourier-feature matrix B, FP32 device [d_in][m] (Eq. 14).
+ * Required before any loss call when ff_m > 0.  The pointer is kept, not copied. */
+PINN_API pinn_status pinn_set_ff_matrix(pinn_handle* h, const float* d_B);
+
+/* Loss only.  d_loss_terms receives PINN_LOSS_TERMS doubles:
+ *   [0] total = lambda_pde*L_pde + lambda_ic*L_ic + lambda_bc*L_bc
+ *   [1] L_pde (sum over equations)  [2..4] L_pde per equation (unused = 0)
+ *   [5] L_ic   [6] L_bc   [7] 0
+ * d_params: FP32 [P].  d_ws: at least pinn_workspace_bytes(), 256-byte aligned. */
+PINN_API pinn_status pinn_loss(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch,
+                      const float* d_params, void* d_ws, size_t ws_bytes,
+                      double* d_loss_terms, void* stream);
+
+/* Loss and its gradient dL/dtheta, FP32 [P] in the packed layout (overwritten).
+ * Reductions over points are ordered and done in FP64, so repeated calls on the
+ * same inputs give bitwise identical results. */
+PINN_API pinn_status pinn_loss_grad(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch,
+                           const float* d_params, void* d_ws, size_t ws_bytes,
+                           double* d_loss_terms, float* d_grad, void* stream);
+
+/* One Adam step in place over n entries (Sec. 2.7.5): m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, theta -= lr * (m/(1-b1^step)) / (sqrt(v/(1-b2^step)) + eps).
+ * step is 1-based.  All four arrays FP32 device [n]. */
+PINN_API pinn_status pinn_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t n,
+                           int64_t step, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* Synchronise `stream`, then read and clear the device status word: PINN_OK,
+ * PINN_ERR_NONFINITE or PINN_ERR_TIMEOUT. */
+PINN_API pinn_status pinn_status_poll(pinn_handle* h, void* stream);
+
+/* Last error message recorded on the handle (never NULL). */
+PINN_API const char* pinn_last_error(const pinn_handle* h);
+
+/* Static name of a status code. */
+PINN_API const char* pinn_status_string(pinn_status s);
+
+/* Phase profiler.  While enabled, every loss call brackets each launch group
+ * with CUDA events on the caller's stream (no synchronisation inside the call).
+ * Phases: 0 RWF weights, 1 input embedding / first layer, 2 forward jet GEMMs,
+ * 3 output layer + residual + loss, 4 weight-gradient GEMMs, 5 adjoint GEMMs,
+ * 6 reductions and finalisation, 7 other.  At most 16384 event pairs are kept
+ * between reads; later ones are dropped (and counted in launches as -1). */
+#define PINN_PROF_PHASES 8
+PINN_API pinn_status pinn_set_profiling(pinn_handle* h, int enable);
+
+/* Synchronise on the recorded events, then return per phase the summed GPU time
+ * in milliseconds and the number of kernel launches since the last read, and
+ * reset the record.  Both arrays have PINN_PROF_PHASES entries. */
+PINN_API pinn_status pinn_profile_read(pinn_handle* h, double* ms, int64_t* launches);
+
+/* Number of hidden layers whose jet GEMMs run on tcgen05 tensor cores for a batch
+ * of these sizes (the rest run on CUDA cores), written to *n. */
+PINN_API pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc,
+                                             int32_t* n);
+
+/* Library version string. */
+PINN_API const char* pinn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PINN_H */

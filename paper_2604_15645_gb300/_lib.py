@@ -1,0 +1,172 @@
+"""ctypes binding of libpinn.so (include/pinn.h).  Argument marshalling only:
+every step of the computation runs in the library's CUDA kernels.  The library
+must have been built (``python -m paper_2604_15645_gb300._build`` or
+``__graft_entry__.build()``); there is no fallback when it is missing."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpinn.so")
+
+PINN_MAX_HIDDEN = 16
+PINN_LOSS_TERMS = 8
+PINN_FP32, PINN_TF32, PINN_BF16 = 0, 1, 2
+PRECISIONS = {"fp32": PINN_FP32, "tf32": PINN_TF32, "bf16": PINN_BF16}
+STATUS = {0: "PINN_OK", 1: "PINN_ERR_INVALID_ARG", 2: "PINN_ERR_UNSUPPORTED", 3: "PINN_ERR_CUDA",
+          4: "PINN_ERR_WORKSPACE", 5: "PINN_ERR_NONFINITE", 6: "PINN_ERR_TIMEOUT"}
+
+# Every symbol declared in include/pinn.h (checked by the CPU tests).
+EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_bytes", "pinn_set_ff_matrix",
+           "pinn_loss", "pinn_loss_grad", "pinn_adam_step", "pinn_status_poll", "pinn_last_error",
+           "pinn_status_string", "pinn_version", "pinn_set_profiling", "pinn_profile_read", "pinn_tensor_core_layers"]
+PINN_PROF_PHASES = 8
+PHASE_NAMES = ["rwf", "embed", "fwd_gemm", "out_loss", "dw_gemm", "adj_gemm", "reduce", "other"]
+
+
+class pinn_spec(C.Structure):
+    _fields_ = [("pde", C.c_int32), ("n_hidden", C.c_int32), ("widths", C.c_int32 * PINN_MAX_HIDDEN),
+                ("ff_m", C.c_int32), ("rwf", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32)]
+
+
+class pinn_problem(C.Structure):
+    _fields_ = [("nu", C.c_double), ("lambda_pde", C.c_double), ("lambda_ic", C.c_double),
+                ("lambda_bc", C.c_double)]
+
+
+class pinn_batch(C.Structure):
+    _fields_ = [("x_res", C.c_void_p), ("n_res", C.c_int64),
+                ("x_ic", C.c_void_p), ("g_ic", C.c_void_p), ("n_ic", C.c_int64), ("ic_mask", C.c_uint32),
+                ("x_bc", C.c_void_p), ("g_bc", C.c_void_p), ("n_bc", C.c_int64), ("bc_mask", C.c_uint32)]
+
+
+class PinnError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpinn.so and declare the C signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpinn.so not built at {path}; run __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    lib.pinn_create.argtypes = [C.POINTER(pinn_spec), C.POINTER(H)]
+    lib.pinn_destroy.argtypes = [H]
+    lib.pinn_param_count.argtypes = [H, C.POINTER(C.c_int64)]
+    lib.pinn_workspace_bytes.argtypes = [H, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_size_t)]
+    lib.pinn_set_ff_matrix.argtypes = [H, C.c_void_p]
+    lib.pinn_loss.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
+                              C.c_size_t, C.c_void_p, C.c_void_p]
+    lib.pinn_loss_grad.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
+                                   C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.pinn_adam_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
+                                   C.c_float, C.c_float, C.c_float, C.c_float, C.c_void_p]
+    lib.pinn_status_poll.argtypes = [H, C.c_void_p]
+    lib.pinn_last_error.argtypes = [H]
+    lib.pinn_last_error.restype = C.c_char_p
+    lib.pinn_status_string.argtypes = [C.c_int]
+    lib.pinn_status_string.restype = C.c_char_p
+    lib.pinn_version.restype = C.c_char_p
+    lib.pinn_set_profiling.argtypes = [H, C.c_int]
+    lib.pinn_tensor_core_layers.argtypes = [H, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int32)]
+    lib.pinn_profile_read.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    for name in EXPORTS:
+        if name not in ("pinn_last_error", "pinn_status_string", "pinn_version"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def check(status: int, handle=None):
+    if status != 0:
+        msg = load().pinn_last_error(handle).decode() if handle else ""
+        raise PinnError(status, msg)
+
+
+def make_spec(pde: int, widths, ff_m: int = 0, rwf: bool = False, precision: int = PINN_FP32) -> pinn_spec:
+    s = pinn_spec()
+    s.pde = pde
+    s.n_hidden = len(widths)
+    for i, w in enumerate(widths):
+        s.widths[i] = int(w)
+    s.ff_m = ff_m
+    s.rwf = int(bool(rwf))
+    s.precision = precision
+    s.flags = 0
+    return s
+
+
+# ---- thin wrappers with the C names ---------------------------------------------------
+
+def pinn_create(spec: pinn_spec) -> int:
+    h = C.c_void_p()
+    check(load().pinn_create(C.byref(spec), C.byref(h)))
+    return h.value
+
+
+def pinn_destroy(h: int):
+    check(load().pinn_destroy(h))
+
+
+def pinn_param_count(h: int) -> int:
+    P = C.c_int64()
+    check(load().pinn_param_count(h, C.byref(P)), h)
+    return P.value
+
+
+def pinn_workspace_bytes(h: int, n_res: int, n_ic: int, n_bc: int) -> int:
+    b = C.c_size_t()
+    check(load().pinn_workspace_bytes(h, n_res, n_ic, n_bc, C.byref(b)), h)
+    return b.value
+
+
+def pinn_set_ff_matrix(h: int, d_B: int):
+    check(load().pinn_set_ff_matrix(h, d_B), h)
+
+
+def pinn_loss(h, prob, batch, d_params, d_ws, ws_bytes, d_loss, stream):
+    check(load().pinn_loss(h, C.byref(prob), C.byref(batch), d_params, d_ws, ws_bytes, d_loss, stream), h)
+
+
+def pinn_loss_grad(h, prob, batch, d_params, d_ws, ws_bytes, d_loss, d_grad, stream):
+    check(load().pinn_loss_grad(h, C.byref(prob), C.byref(batch), d_params, d_ws, ws_bytes, d_loss, d_grad,
+                                stream), h)
+
+
+def pinn_adam_step(d_params, d_grad, d_m, d_v, n, step, lr, beta1, beta2, eps, stream):
+    check(load().pinn_adam_step(d_params, d_grad, d_m, d_v, n, step, lr, beta1, beta2, eps, stream))
+
+
+def pinn_status_poll(h, stream) -> int:
+    return load().pinn_status_poll(h, stream)
+
+
+def pinn_version() -> str:
+    return load().pinn_version().decode()
+
+
+def pinn_set_profiling(h, enable: bool):
+    check(load().pinn_set_profiling(h, int(enable)), h)
+
+
+def pinn_profile_read(h):
+    """{phase name: (ms, launches)} since the last read."""
+    ms = (C.c_double * PINN_PROF_PHASES)()
+    n = (C.c_int64 * PINN_PROF_PHASES)()
+    check(load().pinn_profile_read(h, ms, n), h)
+    return {PHASE_NAMES[i]: (ms[i], n[i]) for i in range(PINN_PROF_PHASES)}
+
+
+def pinn_tensor_core_layers(h, n_res, n_ic, n_bc) -> int:
+    n = C.c_int32()
+    check(load().pinn_tensor_core_layers(h, n_res, n_ic, n_bc, C.byref(n)), h)
+    return n.value

@@ -1,0 +1,133 @@
+"""PyTorch-facing wrapper of libpinn: device buffers and streams come from torch,
+all computation from the library's kernels."""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+
+def _ptr(t):
+    return 0 if t is None else t.data_ptr()
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+class DeviceBatch:
+    """Collocation sets resident on the GPU (FP32, SoA [d][n])."""
+
+    def __init__(self, x_res, x_ic, g_ic, ic_mask, x_bc, g_bc, bc_mask, device="cuda"):
+        f = lambda a: torch.as_tensor(a, dtype=torch.float32, device=device).contiguous()
+        self.x_res, self.x_ic, self.g_ic = f(x_res), f(x_ic), f(g_ic)
+        self.x_bc, self.g_bc = f(x_bc), f(g_bc)
+        self.ic_mask, self.bc_mask = int(ic_mask), int(bc_mask)
+
+    @classmethod
+    def from_host(cls, b, device="cuda"):
+        return cls(b.x_res, b.x_ic, b.g_ic, b.ic_mask, b.x_bc, b.g_bc, b.bc_mask, device)
+
+    @property
+    def sizes(self):
+        return self.x_res.shape[1], self.x_ic.shape[1], self.x_bc.shape[1]
+
+    def c_struct(self) -> _lib.pinn_batch:
+        s = _lib.pinn_batch()
+        s.x_res, s.n_res = _ptr(self.x_res), self.x_res.shape[1]
+        s.x_ic, s.g_ic, s.n_ic, s.ic_mask = _ptr(self.x_ic), _ptr(self.g_ic), self.x_ic.shape[1], self.ic_mask
+        s.x_bc, s.g_bc, s.n_bc, s.bc_mask = _ptr(self.x_bc), _ptr(self.g_bc), self.x_bc.shape[1], self.bc_mask
+        return s
+
+
+def make_problem(nu, lambda_pde=1.0, lambda_ic=1.0, lambda_bc=1.0) -> _lib.pinn_problem:
+    p = _lib.pinn_problem()
+    p.nu, p.lambda_pde, p.lambda_ic, p.lambda_bc = float(nu), float(lambda_pde), float(lambda_ic), float(lambda_bc)
+    return p
+
+
+class PinnNet:
+    """One network handle (pinn_create) plus a cached workspace."""
+
+    def __init__(self, pde, widths, ff_m=0, rwf=False, precision="fp32", device="cuda"):
+        self.device = torch.device(device)
+        self.precision = precision
+        with torch.cuda.device(self.device):
+            self.spec = _lib.make_spec(pde, widths, ff_m, rwf, _lib.PRECISIONS[precision])
+            self.h = _lib.pinn_create(self.spec)
+        self.P = _lib.pinn_param_count(self.h)
+        self._B = None
+        self._ws = None
+        self._ws_key = None
+        self.loss_buf = torch.zeros(_lib.PINN_LOSS_TERMS, dtype=torch.float64, device=self.device)
+
+    @classmethod
+    def from_spec(cls, spec, precision="fp32", device="cuda"):
+        return cls(spec.pde, spec.widths, spec.ff_m, spec.rwf, precision, device)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            try:
+                _lib.pinn_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def set_ff_matrix(self, B):
+        self._B = torch.as_tensor(B, dtype=torch.float32, device=self.device).contiguous()
+        _lib.pinn_set_ff_matrix(self.h, self._B.data_ptr())
+
+    def workspace_bytes(self, n_res, n_ic, n_bc):
+        return _lib.pinn_workspace_bytes(self.h, n_res, n_ic, n_bc)
+
+    def workspace(self, batch: DeviceBatch):
+        key = batch.sizes
+        if self._ws_key != key:
+            nbytes = self.workspace_bytes(*key)
+            self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+            self._ws_key = key
+        return self._ws
+
+    def loss(self, params, batch: DeviceBatch, problem, out=None):
+        ws = self.workspace(batch)
+        out = self.loss_buf if out is None else out
+        _lib.pinn_loss(self.h, problem, batch.c_struct(), params.data_ptr(), ws.data_ptr(), ws.numel(),
+                       out.data_ptr(), _stream())
+        return out
+
+    def loss_grad(self, params, batch: DeviceBatch, problem, grad=None, out=None):
+        assert params.dtype == torch.float32 and params.is_contiguous() and params.numel() == self.P
+        ws = self.workspace(batch)
+        out = self.loss_buf if out is None else out
+        grad = torch.empty_like(params) if grad is None else grad
+        _lib.pinn_loss_grad(self.h, problem, batch.c_struct(), params.data_ptr(), ws.data_ptr(), ws.numel(),
+                            out.data_ptr(), grad.data_ptr(), _stream())
+        return out, grad
+
+    def tensor_core_layers(self, n_res, n_ic, n_bc):
+        return _lib.pinn_tensor_core_layers(self.h, n_res, n_ic, n_bc)
+
+    def status_poll(self):
+        return _lib.pinn_status_poll(self.h, _stream())
+
+
+def adam_step(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    _lib.pinn_adam_step(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), params.numel(), step,
+                        lr, beta1, beta2, eps, _stream())
+
+
+class PinnLoss(torch.autograd.Function):
+    """torch.autograd.Function whose backward is the library's hand-written adjoint
+    (computed together with the loss), replacing double-backward autograd."""
+
+    @staticmethod
+    def forward(ctx, params, net, batch, problem):
+        terms, grad = net.loss_grad(params, batch, problem, out=torch.empty_like(net.loss_buf))
+        ctx.save_for_backward(grad)
+        return terms[0].clone()
+
+    @staticmethod
+    def backward(ctx, gout):
+        (grad,) = ctx.saved_tensors
+        return grad * gout.to(grad.dtype), None, None, None

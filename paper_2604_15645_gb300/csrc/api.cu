@@ -1,0 +1,468 @@
+// C ABI entry points of libpinn: validation, workspace planning and the launch
+// sequence of one loss / loss+gradient evaluation.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "tc.h"
+
+using namespace pinn;
+
+namespace {
+
+void set_err(pinn_handle* h, const char* fmt, ...) {
+  if (!h) return;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(h->err, sizeof(h->err), fmt, ap);
+  va_end(ap);
+}
+
+pinn_status cuda_check(pinn_handle* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PINN_OK;
+  set_err(h, "%s: %s", what, cudaGetErrorString(e));
+  return PINN_ERR_CUDA;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+constexpr int PROF_MAX = 16384;
+enum Phase { PH_RWF = 0, PH_EMBED = 1, PH_FWD = 2, PH_OUT = 3, PH_DW = 4, PH_ADJ = 5, PH_RED = 6, PH_OTHER = 7 };
+
+// Brackets one launch group with a pair of CUDA events when profiling is on.
+struct PhaseScope {
+  pinn_handle* h;
+  cudaStream_t st;
+  int idx = -1;
+  PhaseScope(pinn_handle* hh, cudaStream_t s, int phase, int launches) : h(hh), st(s) {
+    if (!h->prof) return;
+    if (h->prof_n >= PROF_MAX) { ++h->prof_dropped; return; }
+    idx = h->prof_n++;
+    h->prof_phase[idx] = phase;
+    h->prof_launches[idx] = launches;
+    cudaEventRecord(h->prof_ev[2 * idx], st);
+  }
+  ~PhaseScope() {
+    if (idx >= 0) cudaEventRecord(h->prof_ev[2 * idx + 1], st);
+  }
+};
+
+int pde_din(int pde) { return pde == PINN_MAXWELL_TE_2D ? 3 : 2; }
+int pde_dout(int pde) { return pde == PINN_BURGERS_1D ? 1 : 3; }
+
+}  // namespace
+
+namespace pinn {
+
+pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc, Plan* p) {
+  Plan q;
+  q.n_res = n_res; q.n_ic = n_ic; q.n_bc = n_bc;
+  q.ncols = 4 * n_res + n_ic + n_bc;
+  q.NC = (int64_t)align_up((size_t)std::max<int64_t>(q.ncols, 1), COL_ALIGN);
+  q.es = (h->spec.precision == PINN_BF16) ? 2 : 4;
+  const int L = h->L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  q.nbpart = (int)std::min<int64_t>(256, std::max<int64_t>(1, q.NC / 8192));
+  if (h->spec.ff_m) q.A[0] = take((size_t)2 * h->spec.ff_m * q.NC * q.es);
+  for (int l = 1; l <= L; ++l) {
+    q.A[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
+    q.Z[l] = take((size_t)h->spec.widths[l - 1] * q.NC * 4);
+  }
+  q.Zbar[0] = take((size_t)h->w_max * q.NC * q.es);
+  q.Zbar[1] = take((size_t)h->w_max * q.NC * q.es);
+  q.Ubar = take((size_t)h->d_out * q.NC * 4);
+  q.nloss_blocks = out_loss_blocks(q.NC / 4);
+  q.losspart = take((size_t)q.nloss_blocks * 8 * sizeof(double));
+  *p = q;
+  p->total = off;
+  return PINN_OK;
+}
+
+}  // namespace pinn
+
+// Per-call layer plan (weights and split partials live in the workspace too).
+namespace {
+
+struct CallPlan {
+  Plan p;
+  LayerPlan lay[PINN_MAX_HIDDEN + 1];
+  bool tc[PINN_MAX_HIDDEN + 1];      // layer li runs its jet GEMMs on tensor cores
+};
+
+pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc, CallPlan* c) {
+  make_plan(h, n_res, n_ic, n_bc, &c->p);
+  size_t off = c->p.total;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const int L1 = h->L + 1;
+  for (int li = 0; li < L1; ++li) {
+    LayerPlan lp = h->layers[li];
+    const bool raw = (li == 0 && !h->spec.ff_m);
+    const bool hidden = li < h->L;
+    c->tc[li] = hidden && !raw && tc_layer_supported(h, li, c->p.NC);
+    lp.w32 = take((size_t)lp.fin * lp.fout * 4);
+    lp.wc = take((size_t)lp.fin * lp.fout * c->p.es);
+    lp.wtc = take((size_t)lp.fin * lp.fout * c->p.es);
+    if (raw) {
+      lp.nsplit = 0;
+    } else if (c->tc[li]) {
+      lp.nsplit = tc_dw_splits(h, lp.fout, lp.fin, c->p.NC);
+    } else {
+      const int tiles = ((lp.fout + 63) / 64) * ((lp.fin + 63) / 64);
+      int ns = (4 * std::max(h->sm_count, 1) + tiles - 1) / tiles;
+      ns = (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->p.NC / 512));
+      lp.nsplit = ns;
+    }
+    lp.dwpart = take((size_t)std::max(lp.nsplit, 0) * lp.fout * lp.fin * 4);
+    const int dbs = raw ? 1 + h->d_in : 1;
+    lp.dbpart = take((size_t)c->p.nbpart * lp.fout * dbs * 4);
+    c->lay[li] = lp;
+  }
+  c->p.total = off;
+  return PINN_OK;
+}
+
+pinn_status validate_batch(pinn_handle* h, const pinn_batch* b) {
+  if (!b) { set_err(h, "batch is NULL"); return PINN_ERR_INVALID_ARG; }
+  if (b->n_res < 0 || b->n_ic < 0 || b->n_bc < 0) { set_err(h, "negative point count"); return PINN_ERR_INVALID_ARG; }
+  if (b->n_res + b->n_ic + b->n_bc == 0) { set_err(h, "empty batch"); return PINN_ERR_INVALID_ARG; }
+  if (b->n_res > ((int64_t)1 << 34) || b->n_ic > ((int64_t)1 << 34) || b->n_bc > ((int64_t)1 << 34)) {
+    set_err(h, "point count too large"); return PINN_ERR_INVALID_ARG;
+  }
+  if (b->n_res && !b->x_res) { set_err(h, "x_res is NULL"); return PINN_ERR_INVALID_ARG; }
+  if (b->n_ic && (!b->x_ic || (b->ic_mask && !b->g_ic))) { set_err(h, "initial-set pointer is NULL"); return PINN_ERR_INVALID_ARG; }
+  if (b->n_bc && (!b->x_bc || (b->bc_mask && !b->g_bc))) { set_err(h, "boundary-set pointer is NULL"); return PINN_ERR_INVALID_ARG; }
+  if ((b->ic_mask | b->bc_mask) >> h->d_out) { set_err(h, "mask names an output the network does not have"); return PINN_ERR_INVALID_ARG; }
+  return PINN_OK;
+}
+
+pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params, void* d_ws,
+                size_t ws_bytes, double* d_loss, float* d_grad, void* stream, bool want_grad) {
+  if (!h) return PINN_ERR_INVALID_ARG;
+  if (!prob || !d_params || !d_ws || !d_loss || (want_grad && !d_grad)) {
+    set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG;
+  }
+  if (reinterpret_cast<uintptr_t>(d_ws) % 256) { set_err(h, "workspace must be 256-byte aligned"); return PINN_ERR_INVALID_ARG; }
+  pinn_status s = validate_batch(h, b);
+  if (s) return s;
+  if (h->spec.ff_m && !h->ff_B) { set_err(h, "Fourier-feature matrix not set (pinn_set_ff_matrix)"); return PINN_ERR_INVALID_ARG; }
+  CallPlan cp;
+  plan_call(h, b->n_res, b->n_ic, b->n_bc, &cp);
+  if (ws_bytes < cp.p.total) {
+    set_err(h, "workspace too small: %zu < %zu bytes", ws_bytes, cp.p.total); return PINN_ERR_WORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  const Plan& p = cp.p;
+  const int L = h->L, L1 = L + 1, prec = h->spec.precision;
+  const int mode = h->jet_mode;
+
+  // 1. RWF weights (Eq. 15) for every layer.
+  RwfArgs ra{};
+  ra.params = d_params; ra.ws = ws; ra.L1 = L1; ra.rwf = h->spec.rwf; ra.prec = prec;
+  for (int li = 0; li < L1; ++li) {
+    ra.fin[li] = cp.lay[li].fin; ra.fout[li] = cp.lay[li].fout;
+    ra.offV[li] = cp.lay[li].off_V; ra.offs[li] = cp.lay[li].off_s;
+    ra.w32[li] = cp.lay[li].w32; ra.wc[li] = cp.lay[li].wc; ra.wtc[li] = cp.lay[li].wtc;
+  }
+  { PhaseScope ps(h, st, PH_RWF, 1); launch_rwf_prep(ra, st); }
+
+  auto W32 = [&](int li) { return reinterpret_cast<const float*>(ws + cp.lay[li].w32); };
+  auto bias = [&](int li) { return d_params + cp.lay[li].off_b; };
+
+  // 2. Input embedding jets (Eq. 14) or the first layer on raw coordinates.
+  {
+  PhaseScope ps(h, st, PH_EMBED, 1);
+  if (h->spec.ff_m) {
+    launch_embed_ff(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, h->ff_B, h->spec.ff_m, mode,
+                    ws + p.A[0], p.NC, prec, st);
+  } else {
+    launch_first_layer(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, W32(0), bias(0),
+                       cp.lay[0].fout, mode, ws + p.A[1], reinterpret_cast<float*>(ws + p.Z[1]), p.NC, prec, st);
+  }
+  }
+
+  // 3. Hidden jet GEMMs with the tanh-jet epilogue.
+  for (int li = h->first_gemm; li < L; ++li) {
+    EpiArgs e{};
+    e.bias = bias(li); e.out = ws + p.A[li + 1]; e.zout = reinterpret_cast<float*>(ws + p.Z[li + 1]);
+    e.n_res4 = 4 * p.n_res; e.ncols = p.ncols; e.jet_mode = mode;
+    PhaseScope ps(h, st, PH_FWD, 1);
+    if (cp.tc[li]) {
+      s = tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NC, e, st);
+      if (s) return s;
+    } else {
+      launch_simt_gemm_fwd(ws + cp.lay[li].wc, ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NC, e, prec, st);
+    }
+  }
+
+  // 4. Output layer, residual, loss partials, adjoint seed and Zbar_L.
+  OutArgs oa{};
+  oa.AL = ws + p.A[L]; oa.ZL = reinterpret_cast<const float*>(ws + p.Z[L]);
+  oa.W = W32(L); oa.b = bias(L);
+  oa.g_ic = b->g_ic; oa.g_bc = b->g_bc; oa.ic_mask = b->ic_mask; oa.bc_mask = b->bc_mask;
+  oa.n_res = p.n_res; oa.n_ic = p.n_ic; oa.n_bc = p.n_bc; oa.NC = p.NC;
+  oa.w = cp.lay[L].fin; oa.d_out = h->d_out; oa.pde = h->spec.pde; oa.jet_mode = mode;
+  oa.nu = (float)prob->nu;
+  oa.k_pde = p.n_res ? (float)(prob->lambda_pde / (double)p.n_res) : 0.f;
+  oa.k_ic = p.n_ic ? (float)(prob->lambda_ic / (double)p.n_ic) : 0.f;
+  oa.k_bc = p.n_bc ? (float)(prob->lambda_bc / (double)p.n_bc) : 0.f;
+  oa.want_grad = want_grad;
+  oa.Ubar = reinterpret_cast<float*>(ws + p.Ubar);
+  oa.Zbar = ws + p.Zbar[L % 2];
+  oa.losspart = reinterpret_cast<double*>(ws + p.losspart);
+  oa.status = h->d_status;
+  { PhaseScope ps(h, st, PH_OUT, 1); launch_out_loss(oa, prec, p.nloss_blocks, st); }
+  {
+  PhaseScope ps_fl(h, st, PH_RED, 1);
+  launch_finalize_loss(oa.losspart, p.nloss_blocks, p.n_res, (b->ic_mask ? p.n_ic : 0), (b->bc_mask ? p.n_bc : 0),
+                       prob->lambda_pde, prob->lambda_ic, prob->lambda_bc, d_loss, h->d_status, st);
+  }
+  if (!want_grad) return cuda_check(h, cudaGetLastError(), "loss launch");
+
+  // 5. Output layer gradient: dW = Ubar^T A_L, db = sum of value-column seeds.
+  {
+  {
+  PhaseScope ps(h, st, PH_DW, 1);
+  launch_simt_gemm_dw(ws + p.Ubar, true, ws + p.A[L], false, h->d_out, cp.lay[L].fin, p.NC, cp.lay[L].nsplit,
+                      reinterpret_cast<float*>(ws + cp.lay[L].dwpart), prec, st);
+  }
+  PhaseScope ps_r(h, st, PH_RED, 1);
+  launch_row_reduce(ws + p.Ubar, h->d_out, p.NC, p.n_res, p.ncols, p.nbpart, b->x_res, b->x_ic, b->x_bc, p.n_ic,
+                    p.n_bc, 0, mode, reinterpret_cast<float*>(ws + cp.lay[L].dbpart), PINN_FP32, st);
+  }
+
+  // 6. Hidden layers in reverse: dW, db, then the adjoint GEMM into the layer below.
+  for (int li = L - 1; li >= 0; --li) {
+    const LayerPlan& lp = cp.lay[li];
+    void* zb = ws + p.Zbar[(li + 1) % 2];
+    const bool raw = (li == 0 && !h->spec.ff_m);
+    if (!raw) {
+      PhaseScope ps(h, st, PH_DW, 1);
+      if (cp.tc[li]) {
+        s = tc_gemm_dw(h, zb, ws + p.A[li], lp.fout, lp.fin, p.NC, lp.nsplit, reinterpret_cast<float*>(ws + lp.dwpart), st);
+        if (s) return s;
+      } else {
+        launch_simt_gemm_dw(zb, false, ws + p.A[li], false, lp.fout, lp.fin, p.NC, lp.nsplit,
+                            reinterpret_cast<float*>(ws + lp.dwpart), prec, st);
+      }
+    }
+    { PhaseScope ps(h, st, PH_RED, 1);
+    launch_row_reduce(zb, lp.fout, p.NC, p.n_res, p.ncols, p.nbpart, b->x_res, b->x_ic, b->x_bc, p.n_ic, p.n_bc,
+                      raw ? h->d_in : 0, mode, reinterpret_cast<float*>(ws + lp.dbpart), prec, st); }
+    if (li >= 1) {
+      EpiArgs e{};
+      e.out = ws + p.Zbar[li % 2]; e.zin = reinterpret_cast<const float*>(ws + p.Z[li]);
+      e.n_res4 = 4 * p.n_res; e.ncols = p.ncols; e.jet_mode = mode;
+      PhaseScope ps(h, st, PH_ADJ, 1);
+      if (cp.tc[li]) {
+        s = tc_gemm_adj(h, ws + lp.wtc, zb, lp.fin, lp.fout, p.NC, e, st);
+        if (s) return s;
+      } else {
+        launch_simt_gemm_adj(ws + lp.wtc, zb, lp.fin, lp.fout, p.NC, e, prec, st);
+      }
+    }
+  }
+
+  // 7. Ordered FP64 reduction + RWF chain rule into the packed gradient.
+  FinalizeArgs fa{};
+  fa.params = d_params; fa.grad = d_grad; fa.ws = ws; fa.L1 = L1; fa.rwf = h->spec.rwf;
+  fa.first_raw = !h->spec.ff_m; fa.nbpart = p.nbpart;
+  for (int li = 0; li < L1; ++li) {
+    fa.fin[li] = cp.lay[li].fin; fa.fout[li] = cp.lay[li].fout;
+    fa.offV[li] = cp.lay[li].off_V; fa.offs[li] = cp.lay[li].off_s; fa.offb[li] = cp.lay[li].off_b;
+    fa.w32[li] = cp.lay[li].w32; fa.dwpart[li] = cp.lay[li].dwpart; fa.dbpart[li] = cp.lay[li].dbpart;
+    fa.nsplit[li] = cp.lay[li].nsplit;
+    fa.dbstride[li] = (li == 0 && fa.first_raw) ? 1 + h->d_in : 1;
+  }
+  { PhaseScope ps(h, st, PH_RED, 1); launch_finalize_grad(fa, st); }
+  return cuda_check(h, cudaGetLastError(), "loss_grad launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
+  if (!spec || !out) return PINN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (spec->pde < 0 || spec->pde > 2) return PINN_ERR_INVALID_ARG;
+  if (spec->n_hidden < 1 || spec->n_hidden > PINN_MAX_HIDDEN) return PINN_ERR_INVALID_ARG;
+  for (int i = 0; i < spec->n_hidden; ++i)
+    if (spec->widths[i] < 1 || spec->widths[i] > 4096) return PINN_ERR_INVALID_ARG;
+  if (spec->ff_m < 0 || spec->ff_m > 2048) return PINN_ERR_INVALID_ARG;
+  if (spec->rwf != 0 && spec->rwf != 1) return PINN_ERR_INVALID_ARG;
+  if (spec->precision < PINN_FP32 || spec->precision > PINN_BF16) return PINN_ERR_INVALID_ARG;
+  if (spec->flags != 0) return PINN_ERR_INVALID_ARG;
+  pinn_handle* h = new (std::nothrow) pinn_handle();
+  if (!h) return PINN_ERR_INVALID_ARG;
+  h->spec = *spec;
+  h->L = spec->n_hidden;
+  h->d_in = pde_din(spec->pde);
+  h->d_out = pde_dout(spec->pde);
+  h->jet_mode = spec->pde == PINN_BURGERS_1D ? JET_BURGERS : spec->pde == PINN_NS_STEADY_2D ? JET_NS : JET_MAXWELL;
+  h->first_gemm = spec->ff_m ? 0 : 1;
+  int64_t off = 0;
+  int prev = spec->ff_m ? 2 * spec->ff_m : h->d_in;
+  h->w_max = 0;
+  for (int li = 0; li <= h->L; ++li) {
+    const int fout = li < h->L ? spec->widths[li] : h->d_out;
+    LayerPlan& lp = h->layers[li];
+    lp.fin = prev; lp.fout = fout;
+    lp.off_V = off; off += (int64_t)prev * fout;
+    if (spec->rwf) { lp.off_s = off; off += fout; } else lp.off_s = -1;
+    lp.off_b = off; off += fout;
+    if (li < h->L) h->w_max = std::max(h->w_max, fout);
+    prev = fout;
+  }
+  h->P = off;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+      cudaMalloc(&h->d_status, 256) != cudaSuccess || cudaMemset(h->d_status, 0, 256) != cudaSuccess) {
+    if (h->d_status) cudaFree(h->d_status);
+    delete h;
+    return PINN_ERR_CUDA;
+  }
+  tc_init(h);
+  *out = h;
+  return PINN_OK;
+}
+
+pinn_status pinn_destroy(pinn_handle* h) {
+  if (!h) return PINN_OK;
+  if (h->prof_ev) {
+    for (int i = 0; i < 2 * PROF_MAX; ++i) cudaEventDestroy(h->prof_ev[i]);
+    delete[] h->prof_ev;
+    delete[] h->prof_phase;
+    delete[] h->prof_launches;
+  }
+  if (h->d_status) cudaFree(h->d_status);
+  delete h;
+  return PINN_OK;
+}
+
+pinn_status pinn_param_count(const pinn_handle* h, int64_t* P) {
+  if (!h || !P) return PINN_ERR_INVALID_ARG;
+  *P = h->P;
+  return PINN_OK;
+}
+
+pinn_status pinn_workspace_bytes(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc, size_t* bytes) {
+  if (!h || !bytes || n_res < 0 || n_ic < 0 || n_bc < 0) return PINN_ERR_INVALID_ARG;
+  CallPlan cp;
+  plan_call(h, n_res, n_ic, n_bc, &cp);
+  *bytes = cp.p.total;
+  return PINN_OK;
+}
+
+pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc, int32_t* n) {
+  if (!h || !n || n_res < 0 || n_ic < 0 || n_bc < 0) return PINN_ERR_INVALID_ARG;
+  CallPlan cp;
+  plan_call(h, n_res, n_ic, n_bc, &cp);
+  int32_t c = 0;
+  for (int li = 0; li < h->L; ++li) c += cp.tc[li] ? 1 : 0;
+  *n = c;
+  return PINN_OK;
+}
+
+pinn_status pinn_set_ff_matrix(pinn_handle* h, const float* d_B) {
+  if (!h || !d_B) return PINN_ERR_INVALID_ARG;
+  if (!h->spec.ff_m) { set_err(h, "network has no Fourier features"); return PINN_ERR_INVALID_ARG; }
+  h->ff_B = d_B;
+  return PINN_OK;
+}
+
+pinn_status pinn_loss(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch, const float* d_params,
+                      void* d_ws, size_t ws_bytes, double* d_loss_terms, void* stream) {
+  return run(h, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, nullptr, stream, false);
+}
+
+pinn_status pinn_loss_grad(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch, const float* d_params,
+                           void* d_ws, size_t ws_bytes, double* d_loss_terms, float* d_grad, void* stream) {
+  return run(h, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, d_grad, stream, true);
+}
+
+pinn_status pinn_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t n, int64_t step,
+                           float lr, float beta1, float beta2, float eps, void* stream) {
+  if (!d_params || !d_grad || !d_m || !d_v || n < 0 || step < 1) return PINN_ERR_INVALID_ARG;
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f)) return PINN_ERR_INVALID_ARG;
+  if (n == 0) return PINN_OK;
+  const double bc1 = 1.0 - std::pow((double)beta1, (double)step);
+  const double bc2 = 1.0 - std::pow((double)beta2, (double)step);
+  launch_adam(d_params, d_grad, d_m, d_v, n, lr, beta1, beta2, eps, (float)bc1, (float)bc2, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? PINN_OK : PINN_ERR_CUDA;
+}
+
+pinn_status pinn_status_poll(pinn_handle* h, void* stream) {
+  if (!h) return PINN_ERR_INVALID_ARG;
+  pinn_status s = cuda_check(h, cudaStreamSynchronize((cudaStream_t)stream), "stream sync");
+  if (s) return s;
+  int v = 0;
+  s = cuda_check(h, cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  if (s) return s;
+  if (v) cudaMemset(h->d_status, 0, sizeof(int));
+  if (v & 2) { set_err(h, "a device-side wait exceeded its bound"); return PINN_ERR_TIMEOUT; }
+  if (v & 1) { set_err(h, "non-finite loss"); return PINN_ERR_NONFINITE; }
+  return PINN_OK;
+}
+
+pinn_status pinn_set_profiling(pinn_handle* h, int enable) {
+  if (!h) return PINN_ERR_INVALID_ARG;
+  if (enable && !h->prof_ev) {
+    h->prof_ev = new (std::nothrow) cudaEvent_t[2 * PROF_MAX];
+    h->prof_phase = new (std::nothrow) int[PROF_MAX];
+    h->prof_launches = new (std::nothrow) int[PROF_MAX];
+    if (!h->prof_ev || !h->prof_phase || !h->prof_launches) return PINN_ERR_INVALID_ARG;
+    for (int i = 0; i < 2 * PROF_MAX; ++i) {
+      pinn_status s = cuda_check(h, cudaEventCreate(&h->prof_ev[i]), "profiler event");
+      if (s) return s;
+    }
+  }
+  h->prof = enable != 0;
+  h->prof_n = 0;
+  h->prof_dropped = 0;
+  return PINN_OK;
+}
+
+pinn_status pinn_profile_read(pinn_handle* h, double* ms, int64_t* launches) {
+  if (!h || !ms || !launches) return PINN_ERR_INVALID_ARG;
+  for (int i = 0; i < PINN_PROF_PHASES; ++i) { ms[i] = 0.0; launches[i] = 0; }
+  if (h->prof_n > 0) {
+    pinn_status s = cuda_check(h, cudaEventSynchronize(h->prof_ev[2 * h->prof_n - 1]), "profiler sync");
+    if (s) return s;
+    for (int i = 0; i < h->prof_n; ++i) {
+      float t = 0.f;
+      s = cuda_check(h, cudaEventElapsedTime(&t, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]), "profiler elapsed");
+      if (s) return s;
+      ms[h->prof_phase[i]] += t;
+      launches[h->prof_phase[i]] += h->prof_launches[i];
+    }
+  }
+  if (h->prof_dropped) launches[PINN_PROF_PHASES - 1] = -1;
+  h->prof_n = 0;
+  h->prof_dropped = 0;
+  return PINN_OK;
+}
+
+const char* pinn_last_error(const pinn_handle* h) { return h ? h->err : "NULL handle"; }
+
+const char* pinn_status_string(pinn_status s) {
+  switch (s) {
+    case PINN_OK: return "PINN_OK";
+    case PINN_ERR_INVALID_ARG: return "PINN_ERR_INVALID_ARG";
+    case PINN_ERR_UNSUPPORTED: return "PINN_ERR_UNSUPPORTED";
+    case PINN_ERR_CUDA: return "PINN_ERR_CUDA";
+    case PINN_ERR_WORKSPACE: return "PINN_ERR_WORKSPACE";
+    case PINN_ERR_NONFINITE: return "PINN_ERR_NONFINITE";
+    case PINN_ERR_TIMEOUT: return "PINN_ERR_TIMEOUT";
+  }
+  return "PINN_ERR_UNKNOWN";
+}
+
+const char* pinn_version(void) { return "pinn-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,217 @@
+// CUDA-core jet GEMMs: the FP32 path, and the fallback for shapes the tensor-core
+// kernels do not take.  Same data layout as the tensor-core path: activations are
+// feature-major [features][NC] with the four jet rows of a point in adjacent
+// columns, so every epilogue owns whole points and applies the jet rule locally.
+#include "internal.h"
+#include "jet.cuh"
+
+namespace pinn {
+
+namespace {
+
+constexpr int BM = 64, BN = 128, BK = 16, THREADS = 256;
+
+template <typename T>
+__device__ __forceinline__ void load_vec8(const T* p, float v[8]);
+template <>
+__device__ __forceinline__ void load_vec8<float>(const float* p, float v[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void load_vec8<__nv_bfloat16>(const __nv_bfloat16* p, float v[8]) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+    v[2 * i] = f.x; v[2 * i + 1] = f.y;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const float v[4]) {
+  for (int i = 0; i < 4; ++i) p[i] = from_f<T>(v[i]);
+}
+template <>
+__device__ __forceinline__ void st4<float>(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// EPI 0: forward (bias on value columns, tanh jet, writes A and Z)
+// EPI 1: adjoint (reads Z_{l-1}, tanh-jet adjoint, writes Zbar_{l-1})
+template <typename T, int EPI>
+__global__ void __launch_bounds__(THREADS) k_simt_gemm(const T* __restrict__ Aop, const T* __restrict__ Bop, int M,
+                                                       int K, int64_t NC, EpiArgs e) {
+  __shared__ float As[BK][BM + 4];
+  __shared__ float Bs[BK][BN + 4];
+  const int t = threadIdx.x;
+  const int ty = t >> 4, tx = t & 15;
+  const int m0 = blockIdx.y * BM;
+  const int64_t n0 = (int64_t)blockIdx.x * BN;
+  float acc[4][8];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    {  // A tile: 64 rows x 16 k, 4 per thread
+      const int i = t >> 2, kk = (t & 3) * 4;
+      for (int q = 0; q < 4; ++q) {
+        const int m = m0 + i, k = k0 + kk + q;
+        As[kk + q][i] = (m < M && k < K) ? to_f<T>(Aop[(int64_t)m * K + k]) : 0.f;
+      }
+    }
+    {  // B tile: 16 k x 128 columns, 8 per thread
+      const int kk = t >> 4, j = (t & 15) * 8;
+      float v[8];
+      if (k0 + kk < K) load_vec8<T>(Bop + (int64_t)(k0 + kk) * NC + n0 + j, v);
+      else
+        for (int q = 0; q < 8; ++q) v[q] = 0.f;
+      for (int q = 0; q < 8; ++q) Bs[kk][j + q] = v[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+  T* out = reinterpret_cast<T*>(e.out);
+  for (int i = 0; i < 4; ++i) {
+    const int f = m0 + ty * 4 + i;
+    if (f >= M) continue;
+    const float bias = (EPI == 0) ? e.bias[f] : 0.f;
+    for (int q = 0; q < 2; ++q) {
+      const int64_t c = n0 + tx * 8 + 4 * q;
+      const float* ac = &acc[i][4 * q];
+      float o[4];
+      if (EPI == 0) {
+        float z[4] = {ac[0], ac[1], ac[2], ac[3]};
+        if (c < e.n_res4) {
+          z[0] += bias;
+          jet_fwd(z, o, e.jet_mode);
+        } else {
+          for (int r = 0; r < 4; ++r) {
+            if (c + r < e.ncols) { z[r] += bias; o[r] = val_fwd(z[r]); }
+            else { z[r] = 0.f; o[r] = 0.f; }
+          }
+        }
+        st4<float>(e.zout + (int64_t)f * NC + c, z);
+        st4<T>(out + (int64_t)f * NC + c, o);
+      } else {
+        const float4 z4 = *reinterpret_cast<const float4*>(e.zin + (int64_t)f * NC + c);
+        const float z[4] = {z4.x, z4.y, z4.z, z4.w};
+        if (c < e.n_res4) {
+          jet_adj(z, ac, o, e.jet_mode);
+        } else {
+          for (int r = 0; r < 4; ++r) o[r] = (c + r < e.ncols) ? val_adj(z[r], ac[r]) : 0.f;
+        }
+        st4<T>(out + (int64_t)f * NC + c, o);
+      }
+    }
+  }
+}
+
+// Split-K weight gradient: part[s][m][n] = sum_{k in split s} Aop[m][k] Bop[n][k].
+constexpr int DBM = 64, DBN = 64, DBK = 32;
+
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(THREADS) k_simt_dw(const TA* __restrict__ Aop, const TB* __restrict__ Bop, int M,
+                                                     int N, int64_t NC, int64_t kchunk, float* __restrict__ part) {
+  __shared__ float As[DBK][DBM + 4];
+  __shared__ float Bs[DBK][DBN + 4];
+  const int t = threadIdx.x;
+  const int ty = t >> 4, tx = t & 15;
+  const int m0 = blockIdx.y * DBM, nn0 = blockIdx.x * DBN;
+  const int s = blockIdx.z;
+  const int64_t kb = (int64_t)s * kchunk, ke = min(NC, kb + kchunk);
+  float acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int64_t k0 = kb; k0 < ke; k0 += DBK) {
+    const int i = t >> 2, kk = (t & 3) * 8;   // 64 rows x 32 k, 8 per thread
+    {
+      float v[8];
+      if (m0 + i < M) load_vec8<TA>(Aop + (int64_t)(m0 + i) * NC + k0 + kk, v);
+      else
+        for (int q = 0; q < 8; ++q) v[q] = 0.f;
+      for (int q = 0; q < 8; ++q) As[kk + q][i] = v[q];
+    }
+    {
+      float v[8];
+      if (nn0 + i < N) load_vec8<TB>(Bop + (int64_t)(nn0 + i) * NC + k0 + kk, v);
+      else
+        for (int q = 0; q < 8; ++q) v[q] = 0.f;
+      for (int q = 0; q < 8; ++q) Bs[kk + q][i] = v[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < DBK; ++k) {
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+  for (int p = 0; p < 4; ++p) {
+    const int m = m0 + ty * 4 + p;
+    if (m >= M) continue;
+    for (int q = 0; q < 4; ++q) {
+      const int n = nn0 + tx * 4 + q;
+      if (n < N) part[((int64_t)s * M + m) * N + n] = acc[p][q];
+    }
+  }
+}
+
+}  // namespace
+
+void launch_simt_gemm_fwd(const void* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
+                          cudaStream_t st) {
+  dim3 grid((unsigned)(NC / BN), (M + BM - 1) / BM);
+  if (prec == PINN_BF16)
+    k_simt_gemm<__nv_bfloat16, 0><<<grid, THREADS, 0, st>>>((const __nv_bfloat16*)Aop, (const __nv_bfloat16*)Bop, M,
+                                                            K, NC, e);
+  else
+    k_simt_gemm<float, 0><<<grid, THREADS, 0, st>>>((const float*)Aop, (const float*)Bop, M, K, NC, e);
+}
+
+void launch_simt_gemm_adj(const void* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
+                          cudaStream_t st) {
+  dim3 grid((unsigned)(NC / BN), (M + BM - 1) / BM);
+  if (prec == PINN_BF16)
+    k_simt_gemm<__nv_bfloat16, 1><<<grid, THREADS, 0, st>>>((const __nv_bfloat16*)Aop, (const __nv_bfloat16*)Bop, M,
+                                                            K, NC, e);
+  else
+    k_simt_gemm<float, 1><<<grid, THREADS, 0, st>>>((const float*)Aop, (const float*)Bop, M, K, NC, e);
+}
+
+void launch_simt_gemm_dw(const void* Aop, bool a_fp32, const void* Bop, bool b_fp32, int M, int N, int64_t NC,
+                         int nsplit, float* part, int prec, cudaStream_t st) {
+  int64_t kchunk = (NC + nsplit - 1) / nsplit;
+  kchunk = (kchunk + DBK - 1) / DBK * DBK;
+  dim3 grid((N + DBN - 1) / DBN, (M + DBM - 1) / DBM, nsplit);
+  const bool bf = (prec == PINN_BF16);
+  if (!bf || (a_fp32 && b_fp32)) {
+    k_simt_dw<float, float><<<grid, THREADS, 0, st>>>((const float*)Aop, (const float*)Bop, M, N, NC, kchunk, part);
+  } else if (a_fp32) {
+    k_simt_dw<float, __nv_bfloat16><<<grid, THREADS, 0, st>>>((const float*)Aop, (const __nv_bfloat16*)Bop, M, N, NC,
+                                                             kchunk, part);
+  } else {
+    k_simt_dw<__nv_bfloat16, __nv_bfloat16><<<grid, THREADS, 0, st>>>(
+        (const __nv_bfloat16*)Aop, (const __nv_bfloat16*)Bop, M, N, NC, kchunk, part);
+  }
+}
+
+}  // namespace pinn

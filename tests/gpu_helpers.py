@@ -1,0 +1,89 @@
+"""Shared helpers of the GPU tests: run the CUDA path and the oracle on the same
+seeded inputs and compare them."""
+import numpy as np
+import torch
+
+import oracle
+from paper_2604_15645_gb300 import api
+
+TOL = {"fp32": 1e-5, "tf32": 1e-3, "bf16": 2e-2}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def run_gpu(spec, params, B, batch, problem, precision, want_grad=True):
+    net = api.PinnNet.from_spec(spec, precision)
+    if B is not None:
+        net.set_ff_matrix(B)
+    db = api.DeviceBatch.from_host(batch)
+    p = torch.as_tensor(params, dtype=torch.float32, device="cuda")
+    prob = api.make_problem(problem.nu, problem.lambda_pde, problem.lambda_ic, problem.lambda_bc)
+    if want_grad:
+        terms, grad = net.loss_grad(p, db, prob)
+        torch.cuda.synchronize()
+        assert net.status_poll() == 0
+        return terms.cpu().numpy().copy(), grad.cpu().numpy().astype(np.float64)
+    terms = net.loss(p, db, prob)
+    torch.cuda.synchronize()
+    return terms.cpu().numpy().copy(), None
+
+
+def run_oracle(spec, params, B, batch, problem, chunk=None):
+    """Oracle loss terms (as the 8-vector layout of the library) and gradient.
+    With `chunk`, interior points are split into chunks whose sums are combined
+    (every loss term is a sum over points divided by its count)."""
+    m = oracle.Model.from_spec(spec)
+    lam = (problem.lambda_pde, problem.lambda_ic, problem.lambda_bc)
+    n = batch.n_res
+    if chunk is None or n <= chunk:
+        t, g = oracle.loss_and_grad(m, params, B, batch, problem.nu, lam)
+        return _pack(t), g
+    from synth import Batch
+    g_tot = 0.0
+    pde_eq = np.zeros(3)
+    first = True
+    bd = None
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        sub = Batch(batch.x_res[:, s:e], batch.x_ic if first else batch.x_ic[:, :0],
+                    batch.g_ic if first else batch.g_ic[:, :0], batch.ic_mask,
+                    batch.x_bc if first else batch.x_bc[:, :0], batch.g_bc if first else batch.g_bc[:, :0],
+                    batch.bc_mask)
+        frac = (e - s) / n
+        t, g = oracle.loss_and_grad(m, params, B, sub, problem.nu, (lam[0] * frac, lam[1], lam[2]))
+        g_tot = g_tot + g
+        pde_eq[:len(t["pde_eq"])] += frac * np.array(t["pde_eq"])
+        if first:
+            bd = (t["ic"], t["bc"])
+        first = False
+    out = np.zeros(8)
+    out[2:5] = pde_eq
+    out[1] = pde_eq.sum()
+    out[5], out[6] = bd
+    out[0] = lam[0] * out[1] + lam[1] * out[5] + lam[2] * out[6]
+    return out, g_tot
+
+
+def _pack(t):
+    out = np.zeros(8)
+    out[0], out[1] = t["total"], t["pde"]
+    out[2:2 + len(t["pde_eq"])] = t["pde_eq"]
+    out[5], out[6] = t["ic"], t["bc"]
+    return out
+
+
+def assert_parity(gpu_terms, gpu_grad, ref_terms, ref_grad, tol, what=""):
+    for i in (0, 1, 2, 3, 4, 5, 6):
+        if abs(ref_terms[i]) > 0:
+            e = abs(gpu_terms[i] - ref_terms[i]) / abs(ref_terms[i])
+            assert e <= tol, f"{what} loss term {i}: rel err {e:.3e} > {tol} ({gpu_terms[i]} vs {ref_terms[i]})"
+        else:
+            assert abs(gpu_terms[i]) <= 1e-30, f"{what} term {i} should be 0, got {gpu_terms[i]}"
+    if gpu_grad is not None:
+        e = rel(gpu_grad, ref_grad)
+        assert e <= tol, f"{what} gradient rel L2 err {e:.3e} > {tol}"
