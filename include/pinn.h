@@ -176,6 +176,16 @@ PINN_API pinn_status pinn_profile_read(pinn_handle* h, double* ms, int64_t* laun
 PINN_API pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc,
                                              int32_t* n);
 
+/* Self-test of the tensor-core GEMM core (no PINN arithmetic): BF16 inputs,
+ * FP32 output D [M][N] row-major, all device pointers.
+ *   kind 0: D = A B (+ A2 B when d_A2 != NULL), A, A2 [M][K], B [K][N] (N
+ *           contiguous, the layout of the forward / adjoint jet GEMMs); N % 256 == 0.
+ *   kind 1: D = A B^T, A [M][K], B [N][K] (K contiguous, the weight-gradient layout).
+ * M, N, K multiples of 8.  Synchronises `stream`; returns PINN_ERR_TIMEOUT if a
+ * bounded device wait expired.  No counterpart in the paper: a test hook. */
+PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, const void* d_A, const void* d_A2,
+                                      const void* d_B, float* d_D, void* stream);
+
 /* Library version string. */
 PINN_API const char* pinn_version(void);
 

@@ -107,6 +107,8 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
     lp.w32 = take((size_t)lp.fin * lp.fout * 4);
     lp.wc = take((size_t)lp.fin * lp.fout * c->p.es);
     lp.wtc = take((size_t)lp.fin * lp.fout * c->p.es);
+    lp.wt32 = take((size_t)lp.fin * lp.fout * 4);
+    lp.wlo = take((size_t)lp.fin * lp.fout * c->p.es);
     if (raw) {
       lp.nsplit = 0;
     } else if (c->tc[li]) {
@@ -168,6 +170,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
     ra.fin[li] = cp.lay[li].fin; ra.fout[li] = cp.lay[li].fout;
     ra.offV[li] = cp.lay[li].off_V; ra.offs[li] = cp.lay[li].off_s;
     ra.w32[li] = cp.lay[li].w32; ra.wc[li] = cp.lay[li].wc; ra.wtc[li] = cp.lay[li].wtc;
+    ra.wt32[li] = cp.lay[li].wt32; ra.wlo[li] = cp.lay[li].wlo;
   }
   { PhaseScope ps(h, st, PH_RWF, 1); launch_rwf_prep(ra, st); }
 
@@ -193,10 +196,10 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
     e.n_res4 = 4 * p.n_res; e.ncols = p.ncols; e.jet_mode = mode;
     PhaseScope ps(h, st, PH_FWD, 1);
     if (cp.tc[li]) {
-      s = tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NC, e, st);
+      s = tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + cp.lay[li].wlo, ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NC, e, st);
       if (s) return s;
     } else {
-      launch_simt_gemm_fwd(ws + cp.lay[li].wc, ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NC, e, prec, st);
+      launch_simt_gemm_fwd(W32(li), ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NC, e, prec, st);
     }
   }
 
@@ -263,7 +266,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
         s = tc_gemm_adj(h, ws + lp.wtc, zb, lp.fin, lp.fout, p.NC, e, st);
         if (s) return s;
       } else {
-        launch_simt_gemm_adj(ws + lp.wtc, zb, lp.fin, lp.fout, p.NC, e, prec, st);
+        launch_simt_gemm_adj(reinterpret_cast<const float*>(ws + lp.wt32), zb, lp.fin, lp.fout, p.NC, e, prec, st);
       }
     }
   }

@@ -32,6 +32,8 @@ struct LayerPlan {
   size_t w32 = 0;      // W fp32 [fout][fin]
   size_t wc = 0;       // W in compute type [fout][fin]
   size_t wtc = 0;      // W^T in compute type [fin][fout]
+  size_t wt32 = 0;     // W^T fp32 [fin][fout]
+  size_t wlo = 0;      // BF16 only: W - bf16(W) rounded to bf16 [fout][fin] (second half of the split weight)
   size_t dwpart = 0;   // dW split partials fp32 [nsplit][fout][fin]
   size_t dbpart = 0;   // db partials fp32 [nbpart][fout]
   int nsplit = 1;
@@ -86,6 +88,7 @@ struct RwfArgs {
   int fin[PINN_MAX_HIDDEN + 1], fout[PINN_MAX_HIDDEN + 1];
   int64_t offV[PINN_MAX_HIDDEN + 1], offs[PINN_MAX_HIDDEN + 1];
   size_t w32[PINN_MAX_HIDDEN + 1], wc[PINN_MAX_HIDDEN + 1], wtc[PINN_MAX_HIDDEN + 1];
+  size_t wt32[PINN_MAX_HIDDEN + 1], wlo[PINN_MAX_HIDDEN + 1];
 };
 void launch_rwf_prep(const RwfArgs& a, cudaStream_t st);
 
@@ -107,10 +110,11 @@ struct EpiArgs {
   int jet_mode;
 };
 
-// D[M][N] = Aop[M][K] Bop[K][N] (+ epilogue), Aop row-major ld=K, Bop row-major ld=NC.
-void launch_simt_gemm_fwd(const void* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
+// D[M][N] = Aop[M][K] Bop[K][N] (+ epilogue), Aop row-major ld=K (FP32 weights),
+// Bop row-major ld=NC (activations in the compute type).
+void launch_simt_gemm_fwd(const float* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
                           cudaStream_t st);
-void launch_simt_gemm_adj(const void* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
+void launch_simt_gemm_adj(const float* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
                           cudaStream_t st);
 // part[s][M][N] = sum_{k in split s} Aop[m][k] Bop[n][k]; Aop/Bop row-major with ld = NC.
 // a_fp32 / b_fp32 select float storage, else the compute type.

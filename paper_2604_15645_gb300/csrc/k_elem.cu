@@ -10,7 +10,9 @@ namespace pinn {
 
 // ------------------------------------------------------------------------------------
 // RWF (Sec. 2.7.2, Eq. 15): W_l = diag(exp(s_l)) V_l for l = 1..L+1, written as an FP32
-// master copy, a copy in the compute type, and its transpose (operand of the adjoint
+// master copy and its transpose, a copy in the compute type with its transpose
+// (operands of the tensor-core GEMMs), and the rounding remainder W - round(W) in
+// the compute type (the low half of the two-term BF16 weight used by the forward
 // GEMM).  blockIdx.y selects the layer.
 // ------------------------------------------------------------------------------------
 template <typename T>
@@ -23,13 +25,18 @@ __global__ void k_rwf_prep(RwfArgs a) {
   float* W32 = reinterpret_cast<float*>(a.ws + a.w32[l]);
   T* Wc = reinterpret_cast<T*>(a.ws + a.wc[l]);
   T* WTc = reinterpret_cast<T*>(a.ws + a.wtc[l]);
+  float* WT32 = reinterpret_cast<float*>(a.ws + a.wt32[l]);
+  T* Wlo = reinterpret_cast<T*>(a.ws + a.wlo[l]);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx / fin), j = (int)(idx % fin);
     float w = V[idx];
     if (s) w *= expf(s[i]);
     W32[idx] = w;
-    Wc[idx] = from_f<T>(w);
-    WTc[(int64_t)j * fout + i] = from_f<T>(w);
+    const T wh = from_f<T>(w);
+    Wc[idx] = wh;
+    Wlo[idx] = from_f<T>(w - to_f<T>(wh));
+    WTc[(int64_t)j * fout + i] = wh;
+    WT32[(int64_t)j * fout + i] = w;
   }
 }
 

@@ -40,7 +40,7 @@ __device__ __forceinline__ void st4<float>(float* p, const float v[4]) {
 // EPI 0: forward (bias on value columns, tanh jet, writes A and Z)
 // EPI 1: adjoint (reads Z_{l-1}, tanh-jet adjoint, writes Zbar_{l-1})
 template <typename T, int EPI>
-__global__ void __launch_bounds__(THREADS) k_simt_gemm(const T* __restrict__ Aop, const T* __restrict__ Bop, int M,
+__global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__ Aop, const T* __restrict__ Bop, int M,
                                                        int K, int64_t NC, EpiArgs e) {
   __shared__ float As[BK][BM + 4];
   __shared__ float Bs[BK][BN + 4];
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const T* __restrict__ Aop
       const int i = t >> 2, kk = (t & 3) * 4;
       for (int q = 0; q < 4; ++q) {
         const int m = m0 + i, k = k0 + kk + q;
-        As[kk + q][i] = (m < M && k < K) ? to_f<T>(Aop[(int64_t)m * K + k]) : 0.f;
+        As[kk + q][i] = (m < M && k < K) ? Aop[(int64_t)m * K + k] : 0.f;
       }
     }
     {  // B tile: 16 k x 128 columns, 8 per thread
@@ -177,24 +177,22 @@ __global__ void __launch_bounds__(THREADS) k_simt_dw(const TA* __restrict__ Aop,
 
 }  // namespace
 
-void launch_simt_gemm_fwd(const void* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
+void launch_simt_gemm_fwd(const float* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
                           cudaStream_t st) {
   dim3 grid((unsigned)(NC / BN), (M + BM - 1) / BM);
   if (prec == PINN_BF16)
-    k_simt_gemm<__nv_bfloat16, 0><<<grid, THREADS, 0, st>>>((const __nv_bfloat16*)Aop, (const __nv_bfloat16*)Bop, M,
-                                                            K, NC, e);
+    k_simt_gemm<__nv_bfloat16, 0><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, M, K, NC, e);
   else
-    k_simt_gemm<float, 0><<<grid, THREADS, 0, st>>>((const float*)Aop, (const float*)Bop, M, K, NC, e);
+    k_simt_gemm<float, 0><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, M, K, NC, e);
 }
 
-void launch_simt_gemm_adj(const void* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
+void launch_simt_gemm_adj(const float* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
                           cudaStream_t st) {
   dim3 grid((unsigned)(NC / BN), (M + BM - 1) / BM);
   if (prec == PINN_BF16)
-    k_simt_gemm<__nv_bfloat16, 1><<<grid, THREADS, 0, st>>>((const __nv_bfloat16*)Aop, (const __nv_bfloat16*)Bop, M,
-                                                            K, NC, e);
+    k_simt_gemm<__nv_bfloat16, 1><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, M, K, NC, e);
   else
-    k_simt_gemm<float, 1><<<grid, THREADS, 0, st>>>((const float*)Aop, (const float*)Bop, M, K, NC, e);
+    k_simt_gemm<float, 1><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, M, K, NC, e);
 }
 
 void launch_simt_gemm_dw(const void* Aop, bool a_fp32, const void* Bop, bool b_fp32, int M, int N, int64_t NC,

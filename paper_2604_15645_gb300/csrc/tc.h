@@ -13,8 +13,8 @@ bool tc_layer_supported(const pinn_handle* h, int li, int64_t NC);
 // Number of K (column) splits of the tensor-core weight-gradient GEMM.
 int tc_dw_splits(const pinn_handle* h, int fout, int fin, int64_t NC);
 
-// Z = W A (+ bias, tanh jet): W [fout][fin] compute type (K-major), A^T [fin][NC].
-pinn_status tc_gemm_fwd(pinn_handle* h, const void* W, const void* A, int fout, int fin, int64_t NC,
+// Z = (W_hi + W_lo) A (+ bias, tanh jet): W_hi, W_lo [fout][fin] BF16 (K-major), A^T [fin][NC].
+pinn_status tc_gemm_fwd(pinn_handle* h, const void* W, const void* Wlo, const void* A, int fout, int fin, int64_t NC,
                         const EpiArgs& e, cudaStream_t st);
 // Abar = W^T Zbar (tanh-jet adjoint epilogue): WT [fin][fout], Zbar^T [fout][NC].
 pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fin, int fout, int64_t NC,

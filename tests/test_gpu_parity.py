@@ -103,10 +103,12 @@ def test_adam_matches_oracle(cuda_lib):
     m = np.zeros(n, np.float32); v = np.zeros(n, np.float32)
     tp, tm, tv = (torch.tensor(a, device="cuda") for a in (theta, m, v))
     th64, m64, v64 = theta.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    # the kernel receives float32 hyper-parameters; give the oracle the same values
+    b1, b2, lr, eps = (float(np.float32(x)) for x in (0.9, 0.999, 1e-3, 1e-8))
     for step in range(1, 4):
         g = rng.standard_normal(n).astype(np.float32)
         api.adam_step(tp, torch.tensor(g, device="cuda"), tm, tv, step, lr=1e-3)
-        th64, m64, v64 = oracle.adam_step(th64, g.astype(np.float64), m64, v64, step, 1e-3)
+        th64, m64, v64 = oracle.adam_step(th64, g.astype(np.float64), m64, v64, step, lr, b1, b2, eps)
     torch.cuda.synchronize()
     assert rel(tp.cpu().numpy(), th64) < 1e-6
     assert rel(tm.cpu().numpy(), m64) < 1e-6 and rel(tv.cpu().numpy(), v64) < 1e-6
