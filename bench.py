@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ns_cavity_6x256")
     ap.add_argument("--precision", default=None)
+    ap.add_argument("--n-res", type=int, default=None, help="interior points (default: the workload's own)")
     ap.add_argument("--no-torch", action="store_true", help="skip the torch autograd baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     return ap.parse_args()
@@ -151,9 +152,13 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------ workload
 
-def workload_inputs(name):
+def workload_inputs(name, n_res=None):
     from synth import make_workload
     w, params, B, batch = make_workload(name)
+    if n_res is not None and n_res != batch.n_res:
+        frac = n_res / batch.n_res
+        batch = make_workload(name, n_res=n_res, n_ic=int(round(batch.n_ic * frac)),
+                              n_bc=int(round(batch.n_bc * frac)))[3]
     return w, params, B, batch
 
 
@@ -237,7 +242,7 @@ def run_ours(args, ws_n, rank, local):
     from paper_2604_15645_gb300 import _lib, api
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w, params, B, batch = workload_inputs(args.workload)
+    w, params, B, batch = workload_inputs(args.workload, args.n_res)
     precision = args.precision or w.precision
     net = api.PinnNet.from_spec(w.spec, precision, device=dev)
     if B is not None:

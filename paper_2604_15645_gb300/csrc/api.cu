@@ -71,7 +71,7 @@ pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   if (h->spec.ff_m) q.A[0] = take((size_t)2 * h->spec.ff_m * q.NC * q.es);
   for (int l = 1; l <= L; ++l) {
     q.A[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
-    q.Z[l] = take((size_t)h->spec.widths[l - 1] * q.NC * 4);
+    q.Z[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
   }
   q.Zbar[0] = take((size_t)h->w_max * q.NC * q.es);
   q.Zbar[1] = take((size_t)h->w_max * q.NC * q.es);
@@ -185,14 +185,14 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
                     ws + p.A[0], p.NC, prec, st);
   } else {
     launch_first_layer(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, W32(0), bias(0),
-                       cp.lay[0].fout, mode, ws + p.A[1], reinterpret_cast<float*>(ws + p.Z[1]), p.NC, prec, st);
+                       cp.lay[0].fout, mode, ws + p.A[1], ws + p.Z[1], p.NC, prec, st);
   }
   }
 
   // 3. Hidden jet GEMMs with the tanh-jet epilogue.
   for (int li = h->first_gemm; li < L; ++li) {
     EpiArgs e{};
-    e.bias = bias(li); e.out = ws + p.A[li + 1]; e.zout = reinterpret_cast<float*>(ws + p.Z[li + 1]);
+    e.bias = bias(li); e.out = ws + p.A[li + 1]; e.zout = ws + p.Z[li + 1];
     e.n_res4 = 4 * p.n_res; e.ncols = p.ncols; e.jet_mode = mode;
     PhaseScope ps(h, st, PH_FWD, 1);
     if (cp.tc[li]) {
@@ -205,7 +205,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
 
   // 4. Output layer, residual, loss partials, adjoint seed and Zbar_L.
   OutArgs oa{};
-  oa.AL = ws + p.A[L]; oa.ZL = reinterpret_cast<const float*>(ws + p.Z[L]);
+  oa.AL = ws + p.A[L]; oa.ZL = ws + p.Z[L];
   oa.W = W32(L); oa.b = bias(L);
   oa.g_ic = b->g_ic; oa.g_bc = b->g_bc; oa.ic_mask = b->ic_mask; oa.bc_mask = b->bc_mask;
   oa.n_res = p.n_res; oa.n_ic = p.n_ic; oa.n_bc = p.n_bc; oa.NC = p.NC;
@@ -259,7 +259,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
                       raw ? h->d_in : 0, mode, reinterpret_cast<float*>(ws + lp.dbpart), prec, st); }
     if (li >= 1) {
       EpiArgs e{};
-      e.out = ws + p.Zbar[li % 2]; e.zin = reinterpret_cast<const float*>(ws + p.Z[li]);
+      e.out = ws + p.Zbar[li % 2]; e.zin = ws + p.Z[li];
       e.n_res4 = 4 * p.n_res; e.ncols = p.ncols; e.jet_mode = mode;
       PhaseScope ps(h, st, PH_ADJ, 1);
       if (cp.tc[li]) {

@@ -45,7 +45,7 @@ struct Plan {
   int64_t NC = 0;      // ncols padded to COL_ALIGN
   int es = 4;          // bytes per element of the compute type (2 bf16, 4 fp32/tf32)
   size_t A[PINN_MAX_HIDDEN + 1] = {};   // A_l^T [w_l][NC] compute type, l = 0..L (A_0 only with FF)
-  size_t Z[PINN_MAX_HIDDEN + 1] = {};   // Z_l^T [w_l][NC] fp32, l = 1..L
+  size_t Z[PINN_MAX_HIDDEN + 1] = {};   // Z_l^T [w_l][NC] compute type, l = 1..L
   size_t Zbar[2] = {};                  // ping-pong adjoints [w_max][NC] compute type
   size_t Ubar = 0;                      // output seeds [d_out][NC] fp32
   size_t losspart = 0;                  // per-block loss partials, double [nloss_blocks][8]
@@ -98,13 +98,13 @@ void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, i
 
 void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                         int64_t n_bc, int d_in, const float* W, const float* b, int fout, int jet_mode, void* A1,
-                        float* Z1, int64_t NC, int prec, cudaStream_t st);
+                        void* Z1, int64_t NC, int prec, cudaStream_t st);
 
 struct EpiArgs {
   const float* bias;      // fwd: bias of this layer [M]
   void* out;              // fwd: A_l^T, adj: Zbar_{l-1}^T (compute type)
-  float* zout;            // fwd: Z_l^T (fp32)
-  const float* zin;       // adj: Z_{l-1}^T (fp32)
+  void* zout;             // fwd: Z_l^T (compute type)
+  const void* zin;        // adj: Z_{l-1}^T (compute type)
   int64_t n_res4;         // 4 n_res: columns below it are jet columns
   int64_t ncols;          // valid columns
   int jet_mode;
@@ -123,7 +123,7 @@ void launch_simt_gemm_dw(const void* Aop, bool a_fp32, const void* Bop, bool b_f
 
 struct OutArgs {
   const void* AL;        // A_L^T [w][NC] compute type
-  const float* ZL;       // Z_L^T [w][NC]
+  const void* ZL;        // Z_L^T [w][NC] compute type
   const float* W;        // output weights fp32 [d_out][w]
   const float* b;        // output bias [d_out]
   const float* g_ic; const float* g_bc;   // targets [d_out][n]

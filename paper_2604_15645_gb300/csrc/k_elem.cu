@@ -165,7 +165,7 @@ void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, i
 template <typename T>
 __global__ void k_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                               int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, T* A1,
-                              float* Z1, int64_t NC) {
+                              T* Z1, int64_t NC) {
   const int f = blockIdx.y;
   const int64_t ngroups = NC / 4;
   float Wf[3] = {0.f, 0.f, 0.f};
@@ -194,21 +194,21 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
       }
     }
     store4<T>(A1 + (int64_t)f * NC + c0, a);
-    store4<float>(Z1 + (int64_t)f * NC + c0, z);
+    store4<T>(Z1 + (int64_t)f * NC + c0, z);
   }
 }
 
 void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                         int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, void* A1,
-                        float* Z1, int64_t NC, int prec, cudaStream_t st) {
+                        void* Z1, int64_t NC, int prec, cudaStream_t st) {
   const int64_t ngroups = NC / 4;
   dim3 grid((unsigned)std::min<int64_t>((ngroups + 255) / 256, 4096), fout);
   if (prec == PINN_BF16)
     k_first_layer<__nv_bfloat16><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
-                                                       (__nv_bfloat16*)A1, Z1, NC);
+                                                       (__nv_bfloat16*)A1, (__nv_bfloat16*)Z1, NC);
   else
     k_first_layer<float><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
-                                               (float*)A1, Z1, NC);
+                                               (float*)A1, (float*)Z1, NC);
 }
 
 // ------------------------------------------------------------------------------------
@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
     float U[3][4];
     for (int c = 0; c < 3; ++c)
       for (int r = 0; r < 4; ++r) U[c][r] = 0.f;
+#pragma unroll 4
     for (int f = 0; f < w; ++f) {
       float v[4];
       load4<T>(AL + (int64_t)f * a.NC + c0, v);
@@ -313,6 +314,8 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
     if (!a.want_grad) continue;
     for (int c = 0; c < D; ++c) store4<float>(a.Ubar + (int64_t)c * a.NC + c0, Ub[c]);
     // abar_L = Ubar W_out (rank <= 3), then the tanh-jet adjoint with Z_L.
+    const T* ZL = reinterpret_cast<const T*>(a.ZL);
+#pragma unroll 4
     for (int f = 0; f < w; ++f) {
       float ab[4] = {0.f, 0.f, 0.f, 0.f};
       for (int c = 0; c < D; ++c) {
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
         for (int r = 0; r < 4; ++r) ab[r] = fmaf(wc, Ub[c][r], ab[r]);
       }
       float z[4], zb[4];
-      load4<float>(a.ZL + (int64_t)f * a.NC + c0, z);
+      load4<T>(ZL + (int64_t)f * a.NC + c0, z);
       if (interior) {
         jet_adj(z, ab, zb, a.jet_mode);
       } else {
@@ -353,6 +356,31 @@ void launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st) {
 // One warp per (row, column chunk); partials [chunk][M][1 + d_in_terms].
 // ------------------------------------------------------------------------------------
 template <typename T>
+__device__ __forceinline__ void row_group(const float v[4], int64_t c0, int64_t n_res, int64_t n_ic, int64_t n_bc,
+                                          const float* x_res, const float* x_ic, const float* x_bc, int dterms,
+                                          int mode, float acc[4]) {
+  if (c0 < 4 * n_res) {
+    const int64_t g = c0 >> 2;
+    acc[0] += v[0];
+    for (int j = 0; j < dterms; ++j) acc[1 + j] = fmaf(v[0], x_res[(int64_t)j * n_res + g], acc[1 + j]);
+    if (dterms) {
+      for (int r = 1; r < 4; ++r) {
+        const int d = row_dir(mode, r);
+        if (d >= 0) acc[1 + d] += v[r];
+      }
+    }
+  } else {
+    for (int r = 0; r < 4; ++r) {
+      const ColPoint cp = classify_col(c0 + r, n_res, n_ic, n_bc);
+      if (cp.set == 3) continue;
+      acc[0] += v[r];
+      for (int j = 0; j < dterms; ++j)
+        acc[1 + j] = fmaf(v[r], coord(x_res, x_ic, x_bc, n_res, n_ic, n_bc, cp, j), acc[1 + j]);
+    }
+  }
+}
+
+template <typename T>
 __global__ void k_row_reduce(const T* Zb, int M, int64_t NC, int64_t n_res, int64_t ncols, int nbpart,
                              const float* x_res, const float* x_ic, const float* x_bc, int64_t n_ic, int64_t n_bc,
                              int dterms, int mode, float* part) {
@@ -360,33 +388,18 @@ __global__ void k_row_reduce(const T* Zb, int M, int64_t NC, int64_t n_res, int6
   const int row = blockIdx.x * (blockDim.x >> 5) + warp;
   if (row >= M) return;
   const int chunk = blockIdx.y;
-  const int64_t ngroups = NC / 4;
-  const int64_t per = (ngroups + nbpart - 1) / nbpart;
-  const int64_t g0 = chunk * per, g1 = min(ngroups, g0 + per);
+  const int64_t noct = NC / 8;                          // 8-column units
+  const int64_t per = (noct + nbpart - 1) / nbpart;
+  const int64_t o0 = chunk * per, o1 = min(noct, o0 + per);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   const T* rowp = Zb + (int64_t)row * NC;
-  for (int64_t g = g0 + lane; g < g1; g += 32) {
-    float v[4];
-    load4<T>(rowp + 4 * g, v);
-    const int64_t c0 = 4 * g;
-    if (c0 < 4 * n_res) {
-      acc[0] += v[0];
-      for (int j = 0; j < dterms; ++j) acc[1 + j] = fmaf(v[0], x_res[(int64_t)j * n_res + g], acc[1 + j]);
-      if (dterms) {
-        for (int r = 1; r < 4; ++r) {
-          const int d = row_dir(mode, r);
-          if (d >= 0) acc[1 + d] += v[r];
-        }
-      }
-    } else {
-      for (int r = 0; r < 4; ++r) {
-        const ColPoint cp = classify_col(c0 + r, n_res, n_ic, n_bc);
-        if (cp.set == 3) continue;
-        acc[0] += v[r];
-        for (int j = 0; j < dterms; ++j)
-          acc[1 + j] = fmaf(v[r], coord(x_res, x_ic, x_bc, n_res, n_ic, n_bc, cp, j), acc[1 + j]);
-      }
-    }
+#pragma unroll 4
+  for (int64_t o = o0 + lane; o < o1; o += 32) {
+    float v[4], u[4];
+    load4<T>(rowp + 8 * o, v);
+    load4<T>(rowp + 8 * o + 4, u);
+    row_group<T>(v, 8 * o, n_res, n_ic, n_bc, x_res, x_ic, x_bc, dterms, mode, acc);
+    row_group<T>(u, 8 * o + 4, n_res, n_ic, n_bc, x_res, x_ic, x_bc, dterms, mode, acc);
   }
   for (int j = 0; j <= dterms; ++j) {
     float s = acc[j];

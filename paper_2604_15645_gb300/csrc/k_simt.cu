@@ -104,11 +104,12 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
             else { z[r] = 0.f; o[r] = 0.f; }
           }
         }
-        st4<float>(e.zout + (int64_t)f * NC + c, z);
+        st4<T>(reinterpret_cast<T*>(e.zout) + (int64_t)f * NC + c, z);
         st4<T>(out + (int64_t)f * NC + c, o);
       } else {
-        const float4 z4 = *reinterpret_cast<const float4*>(e.zin + (int64_t)f * NC + c);
-        const float z[4] = {z4.x, z4.y, z4.z, z4.w};
+        float z[4];
+        const T* zp = reinterpret_cast<const T*>(e.zin) + (int64_t)f * NC + c;
+        for (int r = 0; r < 4; ++r) z[r] = to_f<T>(zp[r]);
         if (c < e.n_res4) {
           jet_adj(z, ac, o, e.jet_mode);
         } else {

@@ -13,10 +13,11 @@
 // 64 whole points and applies the tanh jet rule (or its adjoint) without any
 // cross-thread exchange.
 //
-// Warp roles per CTA (192 threads, one CTA per SM, persistent over tiles):
+// Warp roles per CTA (320 threads, one CTA per SM, persistent over tiles):
 //   warp 0     TMA producer (one lane)
 //   warp 1     TMEM allocator + MMA issuer (one lane)
-//   warps 2-5  epilogue; warp w reads TMEM lanes 32*(w%4) .. +31
+//   warps 2-9  epilogue; warp w reads TMEM lanes 32*(w%4) .. +31, columns
+//              128*((w-2)/4) .. +127 of the 256-column accumulator
 // Two accumulator buffers of 256 columns let the epilogue of one tile overlap the
 // MMAs of the next.  Every mbarrier wait is bounded (global timer); on expiry the
 // CTA latches PINN_ERR_TIMEOUT in the status word, stops issuing work, waits for
@@ -36,7 +37,8 @@ namespace {
 
 constexpr int BM = 128;          // accumulator rows (TMEM lanes)
 constexpr int BN = 256;          // accumulator columns per buffer
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 8;     // two warps per TMEM lane quadrant, each on half the columns
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
 
 enum TcMode { TC_FWD = 0, TC_ADJ = 1, TC_DW = 2, TC_STORE = 3 };
@@ -186,11 +188,28 @@ __device__ __forceinline__ void store16<__nv_bfloat16>(__nv_bfloat16* p, const f
   reinterpret_cast<uint4*>(p)[0] = make_uint4(u[0], u[1], u[2], u[3]);
   reinterpret_cast<uint4*>(p)[1] = make_uint4(u[4], u[5], u[6], u[7]);
 }
-__device__ __forceinline__ void load16f(const float* p, float v[16]) {
+template <typename T>
+__device__ __forceinline__ void load16(const T* p, float v[16]);
+template <>
+__device__ __forceinline__ void load16<float>(const float* p, float v[16]) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const float4 q = reinterpret_cast<const float4*>(p)[i];
     v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+  }
+}
+template <>
+__device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, float v[16]) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const uint4 q = reinterpret_cast<const uint4*>(p)[i];
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[j]));
+      v[8 * i + 2 * j] = f.x;
+      v[8 * i + 2 * j + 1] = f.y;
+    }
   }
 }
 
@@ -220,7 +239,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 128);
+      mbar_init(&acc_empty[b], 32 * EPI_WARPS);
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -319,6 +338,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     // ---------------------------------------------------------------- epilogue
     const int quad = warp & 3;                 // TMEM lane quadrant this warp may read
+    const int half = (warp - 2) >> 2;          // which 128 columns of the tile
     const int row = quad * 32 + lane;
     int local = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
@@ -332,11 +352,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN;
       const float bias = (MODE == TC_FWD && mvalid) ? p.e.bias[m] : 0.f;
 #pragma unroll 1
-      for (int c = 0; c < BN / 16; ++c) {
-        float v[16];
+      for (int c = half * (BN / 32); c < (half + 1) * (BN / 32); ++c) {
+        const int64_t col0 = (int64_t)nb * BN + c * 16;
+        float v[16], z[16];
+        if (MODE == TC_ADJ && mvalid) load16<T>(reinterpret_cast<const T*>(p.e.zin) + (int64_t)m * p.NC + col0, z);
         tmem_ld16(taddr + c * 16, v);
         if (!mvalid) continue;
-        const int64_t col0 = (int64_t)nb * BN + c * 16;
         if (MODE == TC_FWD) {
           float a[16];
 #pragma unroll
@@ -355,10 +376,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
           }
           store16<T>(reinterpret_cast<T*>(p.e.out) + (int64_t)m * p.NC + col0, a);
-          store16<float>(p.e.zout + (int64_t)m * p.NC + col0, v);
+          store16<T>(reinterpret_cast<T*>(p.e.zout) + (int64_t)m * p.NC + col0, v);
         } else if (MODE == TC_ADJ) {
-          float z[16], o[16];
-          load16f(p.e.zin + (int64_t)m * p.NC + col0, z);
+          float o[16];
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             const int64_t col = col0 + 4 * g;
