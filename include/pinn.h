@@ -186,6 +186,28 @@ PINN_API pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res
 PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, const void* d_A, const void* d_A2,
                                       const void* d_B, float* d_D, void* stream);
 
+/* Size of the scratch array compiled into the library for pinn_loss_grad_static. */
+#define PINN_STATIC_WS_BYTES ((size_t)64 << 20)
+
+/* Loss and gradient exactly as pinn_loss_grad, for callers that cannot allocate
+ * device memory (code in host callbacks or real-time loops where an allocation may
+ * block or fail, plug-ins whose host runtime owns the memory pool, processes with a
+ * memory budget fixed at start-up) and so cannot provide a workspace.  The paper
+ * has no counterpart: this is a library-interface convenience.
+ *   - Scratch is a 64 MiB (PINN_STATIC_WS_BYTES) file-scope __device__ array inside
+ *     libpinn.so; every GPU that loads the library holds it until process exit.
+ *   - A batch whose pinn_workspace_bytes() exceeds that size is rejected with
+ *     PINN_ERR_WORKSPACE (message in pinn_last_error) and nothing is queued.
+ *   - The call allocates nothing (no cudaMalloc/cudaFree or allocating library call).
+ *     Its first call on a device, with that device current, looks up the array's
+ *     address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; every value
+ *     a call reads is written earlier in the same call.  Calls whose GPU work
+ *     overlaps (e.g. on two streams) race on the array. */
+PINN_API pinn_status pinn_loss_grad_static(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch,
+                                           const float* d_params, double* d_loss_terms, float* d_grad,
+                                           void* stream);
+
 /* Library version string. */
 PINN_API const char* pinn_version(void);
 
