@@ -186,6 +186,11 @@ PINN_API pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res
 PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, const void* d_A, const void* d_A2,
                                       const void* d_B, float* d_D, void* stream);
 
+/* Test hook: the tanh used by the BF16 epilogues, t = tanh(z) and tp = 1 - tanh(z)^2,
+ * computed from e = exp(-2|z|) as t = sign(z)(1-e)/(1+e), tp = 4e/(1+e)^2, for n
+ * FP32 device values.  Asynchronous on `stream`.  No counterpart in the paper. */
+PINN_API pinn_status pinn_tanh_selftest(int64_t n, const float* d_z, float* d_t, float* d_tp, void* stream);
+
 /* Size of the scratch array compiled into the library for pinn_loss_grad_static. */
 #define PINN_STATIC_WS_BYTES ((size_t)64 << 20)
 

@@ -21,7 +21,7 @@ STATUS = {0: "PINN_OK", 1: "PINN_ERR_INVALID_ARG", 2: "PINN_ERR_UNSUPPORTED", 3:
 EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_bytes", "pinn_set_ff_matrix",
            "pinn_loss", "pinn_loss_grad", "pinn_adam_step", "pinn_status_poll", "pinn_last_error",
            "pinn_status_string", "pinn_version", "pinn_set_profiling", "pinn_profile_read", "pinn_tensor_core_layers", "pinn_tc_selftest",
-           "pinn_loss_grad_static"]
+           "pinn_loss_grad_static", "pinn_tanh_selftest"]
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 8
 PHASE_NAMES = ["rwf", "embed", "fwd_gemm", "out_loss", "dw_gemm", "adj_gemm", "reduce", "other"]
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
     lib.pinn_status_string.restype = C.c_char_p
     lib.pinn_version.restype = C.c_char_p
     lib.pinn_set_profiling.argtypes = [H, C.c_int]
+    lib.pinn_tanh_selftest.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.pinn_loss_grad_static.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]
     lib.pinn_tc_selftest.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -184,3 +185,7 @@ def pinn_tc_selftest(kind, M, N, K, d_A, d_A2, d_B, d_D, stream):
 
 def pinn_loss_grad_static(h, prob, batch, d_params, d_loss, d_grad, stream):
     check(load().pinn_loss_grad_static(h, C.byref(prob), C.byref(batch), d_params, d_loss, d_grad, stream), h)
+
+
+def pinn_tanh_selftest(n, d_z, d_t, d_tp, stream):
+    check(load().pinn_tanh_selftest(n, d_z, d_t, d_tp, stream))

@@ -92,6 +92,8 @@ struct CallPlan {
   Plan p;
   LayerPlan lay[PINN_MAX_HIDDEN + 1];
   bool tc[PINN_MAX_HIDDEN + 1];      // layer li runs its jet GEMMs on tensor cores
+  bool fused_db[PINN_MAX_HIDDEN + 1];  // layer li's bias partials come from a fused adjoint epilogue
+  int nbpart[PINN_MAX_HIDDEN + 1];     // bias partial count of layer li
 };
 
 pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc, CallPlan* c) {
@@ -100,10 +102,12 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   const int L1 = h->L + 1;
   for (int li = 0; li < L1; ++li) {
+    const bool raw = (li == 0 && !h->spec.ff_m);
+    c->tc[li] = li < h->L && !raw && tc_layer_supported(h, li, c->p.NC);
+  }
+  for (int li = 0; li < L1; ++li) {
     LayerPlan lp = h->layers[li];
     const bool raw = (li == 0 && !h->spec.ff_m);
-    const bool hidden = li < h->L;
-    c->tc[li] = hidden && !raw && tc_layer_supported(h, li, c->p.NC);
     lp.w32 = take((size_t)lp.fin * lp.fout * 4);
     lp.wc = take((size_t)lp.fin * lp.fout * c->p.es);
     lp.wtc = take((size_t)lp.fin * lp.fout * c->p.es);
@@ -111,6 +115,8 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
     lp.wlo = take((size_t)lp.fin * lp.fout * c->p.es);
     if (raw) {
       lp.nsplit = 0;
+    } else if (li == h->L) {
+      lp.nsplit = c->p.nbpart;                     // output layer: column chunks of k_dw_out
     } else if (c->tc[li]) {
       lp.nsplit = tc_dw_splits(h, lp.fout, lp.fin, c->p.NC);
     } else {
@@ -120,8 +126,12 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
       lp.nsplit = ns;
     }
     lp.dwpart = take((size_t)std::max(lp.nsplit, 0) * lp.fout * lp.fin * 4);
+    // Bias partials of hidden layer li come from the tensor-core adjoint epilogue of
+    // layer li+1 when that one runs on tensor cores, else from a row reduction.
+    c->fused_db[li] = (li + 1 < h->L) && c->tc[li + 1];
+    c->nbpart[li] = c->fused_db[li] ? (int)(c->p.NC / TC_BN) * TC_DB_PARTS : c->p.nbpart;
     const int dbs = raw ? 1 + h->d_in : 1;
-    lp.dbpart = take((size_t)c->p.nbpart * lp.fout * dbs * 4);
+    lp.dbpart = take((size_t)c->nbpart[li] * lp.fout * dbs * 4);
     c->lay[li] = lp;
   }
   c->p.total = off;
@@ -231,8 +241,8 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   {
   {
   PhaseScope ps(h, st, PH_DW, 1);
-  launch_simt_gemm_dw(ws + p.Ubar, true, ws + p.A[L], false, h->d_out, cp.lay[L].fin, p.NC, cp.lay[L].nsplit,
-                      reinterpret_cast<float*>(ws + cp.lay[L].dwpart), prec, st);
+  launch_dw_out(ws + p.A[L], reinterpret_cast<const float*>(ws + p.Ubar), cp.lay[L].fin, h->d_out, p.NC,
+                cp.lay[L].nsplit, reinterpret_cast<float*>(ws + cp.lay[L].dwpart), prec, st);
   }
   PhaseScope ps_r(h, st, PH_RED, 1);
   launch_row_reduce(ws + p.Ubar, h->d_out, p.NC, p.n_res, p.ncols, p.nbpart, b->x_res, b->x_ic, b->x_bc, p.n_ic,
@@ -254,13 +264,21 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
                             reinterpret_cast<float*>(ws + lp.dwpart), prec, st);
       }
     }
-    { PhaseScope ps(h, st, PH_RED, 1);
-    launch_row_reduce(zb, lp.fout, p.NC, p.n_res, p.ncols, p.nbpart, b->x_res, b->x_ic, b->x_bc, p.n_ic, p.n_bc,
-                      raw ? h->d_in : 0, mode, reinterpret_cast<float*>(ws + lp.dbpart), prec, st); }
+    if (!cp.fused_db[li]) {
+      PhaseScope ps(h, st, PH_RED, 1);
+      launch_row_reduce(zb, lp.fout, p.NC, p.n_res, p.ncols, p.nbpart, b->x_res, b->x_ic, b->x_bc, p.n_ic, p.n_bc,
+                        raw ? h->d_in : 0, mode, reinterpret_cast<float*>(ws + lp.dbpart), prec, st);
+    }
     if (li >= 1) {
       EpiArgs e{};
       e.out = ws + p.Zbar[li % 2]; e.zin = ws + p.Z[li];
       e.n_res4 = 4 * p.n_res; e.ncols = p.ncols; e.jet_mode = mode;
+      if (cp.fused_db[li - 1]) {
+        e.dbpart = reinterpret_cast<float*>(ws + cp.lay[li - 1].dbpart);
+        e.dterms = (li - 1 == 0 && !h->spec.ff_m) ? h->d_in : 0;
+        e.x_res = b->x_res; e.x_ic = b->x_ic; e.x_bc = b->x_bc;
+        e.n_res = p.n_res; e.n_ic = p.n_ic; e.n_bc = p.n_bc;
+      }
       PhaseScope ps(h, st, PH_ADJ, 1);
       if (cp.tc[li]) {
         s = tc_gemm_adj(h, ws + lp.wtc, zb, lp.fin, lp.fout, p.NC, e, st);
@@ -280,6 +298,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
     fa.offV[li] = cp.lay[li].off_V; fa.offs[li] = cp.lay[li].off_s; fa.offb[li] = cp.lay[li].off_b;
     fa.w32[li] = cp.lay[li].w32; fa.dwpart[li] = cp.lay[li].dwpart; fa.dbpart[li] = cp.lay[li].dbpart;
     fa.nsplit[li] = cp.lay[li].nsplit;
+    fa.nbpart_l[li] = li < L ? cp.nbpart[li] : p.nbpart;
     fa.dbstride[li] = (li == 0 && fa.first_raw) ? 1 + h->d_in : 1;
   }
   { PhaseScope ps(h, st, PH_RED, 1); launch_finalize_grad(fa, st); }

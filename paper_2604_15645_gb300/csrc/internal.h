@@ -108,6 +108,13 @@ struct EpiArgs {
   int64_t n_res4;         // 4 n_res: columns below it are jet columns
   int64_t ncols;          // valid columns
   int jet_mode;
+  // adjoint only: bias-gradient partials of the layer whose pre-activation adjoint
+  // this epilogue writes ([part][M][1 + dterms]; nullptr = not fused), and for a
+  // first layer on raw coordinates the coordinate terms of its dW (dterms = d_in).
+  float* dbpart;
+  int dterms;
+  const float* x_res; const float* x_ic; const float* x_bc;
+  int64_t n_res, n_ic, n_bc;
 };
 
 // D[M][N] = Aop[M][K] Bop[K][N] (+ epilogue), Aop row-major ld=K (FP32 weights),
@@ -139,6 +146,10 @@ struct OutArgs {
   int* status;
 };
 void launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st);
+// Output-layer weight gradient dW_out[c][f] = sum_col Ubar[c][col] A_L[f][col],
+// partials [nchunks][d_out][w].
+void launch_dw_out(const void* AL, const float* Ubar, int w, int d_out, int64_t NC, int nchunks, float* part,
+                   int prec, cudaStream_t st);
 int out_loss_blocks(int64_t n_points);
 
 // Bias gradient partials of a layer from its pre-activation adjoint (value
@@ -154,6 +165,7 @@ struct FinalizeArgs {
   int64_t offV[PINN_MAX_HIDDEN + 1], offs[PINN_MAX_HIDDEN + 1], offb[PINN_MAX_HIDDEN + 1];
   size_t w32[PINN_MAX_HIDDEN + 1], dwpart[PINN_MAX_HIDDEN + 1], dbpart[PINN_MAX_HIDDEN + 1];
   int nsplit[PINN_MAX_HIDDEN + 1];
+  int nbpart_l[PINN_MAX_HIDDEN + 1];   // bias partial count per layer
   int dbstride[PINN_MAX_HIDDEN + 1];   // floats per (part, row) in dbpart: 1, or 1 + d_in for a raw-coordinate first layer
   int first_raw;                        // 1: layer 0 takes raw coordinates (its dW comes from dbpart too)
   int nbpart;

@@ -18,9 +18,32 @@ namespace pinn {
 
 __device__ __forceinline__ float tanh_exact(float x) { return tanhf(x); }
 
+// tanh and its derivative from the exponential form: with e = exp(-2|z|),
+//   tanh z = sign(z) (1 - e) / (1 + e),   tanh' z = sech^2 z = 4 e / (1 + e)^2.
+// One fast exponential and one fast reciprocal; both t and t' keep a relative
+// error of a few 1e-7 for every z, including saturated units where 1 - t^2 would
+// cancel.  Used by the BF16 path, whose storage rounding is ~4e-3.
+__device__ __forceinline__ void tanh_fast(float z, float& t, float& tp) {
+  const float e = __expf(-2.f * fabsf(z));
+  const float r = __fdividef(1.f, 1.f + e);
+  t = copysignf((1.f - e) * r, z);
+  tp = 4.f * e * r * r;
+}
+
+template <bool FAST>
+__device__ __forceinline__ void tanh_pair(float z, float& t, float& tp) {
+  if (FAST) {
+    tanh_fast(z, t, tp);
+  } else {
+    t = tanh_exact(z);
+    tp = (1.f - t) * (1.f + t);
+  }
+}
+
+template <bool FAST = false>
 __device__ __forceinline__ void jet_fwd(const float z[4], float a[4], int mode) {
-  const float t = tanh_exact(z[0]);
-  const float tp = (1.f - t) * (1.f + t);
+  float t, tp;
+  tanh_pair<FAST>(z[0], t, tp);
   a[0] = t;
   a[1] = tp * z[1];
   a[2] = tp * z[2];
@@ -33,9 +56,10 @@ __device__ __forceinline__ void jet_fwd(const float z[4], float a[4], int mode) 
   }
 }
 
+template <bool FAST = false>
 __device__ __forceinline__ void jet_adj(const float z[4], const float ab[4], float zb[4], int mode) {
-  const float t = tanh_exact(z[0]);
-  const float tp = (1.f - t) * (1.f + t);
+  float t, tp;
+  tanh_pair<FAST>(z[0], t, tp);
   const float tpp = -2.f * t * tp;
   if (mode == JET_MAXWELL) {
     zb[1] = ab[1] * tp;
@@ -54,11 +78,43 @@ __device__ __forceinline__ void jet_adj(const float z[4], const float ab[4], flo
 }
 
 // Value-only column (initial/boundary point).
-__device__ __forceinline__ float val_fwd(float z) { return tanh_exact(z); }
-__device__ __forceinline__ float val_adj(float z, float ab) {
-  const float t = tanh_exact(z);
-  return ab * (1.f - t) * (1.f + t);
+template <bool FAST = false>
+__device__ __forceinline__ float val_fwd(float z) {
+  float t, tp;
+  tanh_pair<FAST>(z, t, tp);
+  return t;
 }
+template <bool FAST = false>
+__device__ __forceinline__ float val_adj(float z, float ab) {
+  float t, tp;
+  tanh_pair<FAST>(z, t, tp);
+  return ab * tp;
+}
+
+// Column classification of the jet matrices: group g covers columns 4g..4g+3.
+// Groups below n_res are interior points (4 jet rows); later columns are
+// initial-condition points, then boundary points (one value column each), then padding.
+struct ColPoint {
+  int set;      // 0 interior, 1 initial, 2 boundary, 3 padding
+  int64_t idx;  // point index within its set
+};
+__device__ __forceinline__ ColPoint classify_col(int64_t c, int64_t n_res, int64_t n_ic, int64_t n_bc) {
+  const int64_t b = c - 4 * n_res;
+  if (b < 0) return {0, c >> 2};
+  if (b < n_ic) return {1, b};
+  if (b < n_ic + n_bc) return {2, b - n_ic};
+  return {3, 0};
+}
+
+__device__ __forceinline__ float coord(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res,
+                                       int64_t n_ic, int64_t n_bc, ColPoint cp, int i) {
+  if (cp.set == 0) return x_res[(int64_t)i * n_res + cp.idx];
+  if (cp.set == 1) return x_ic[(int64_t)i * n_ic + cp.idx];
+  return x_bc[(int64_t)i * n_bc + cp.idx];
+}
+
+// Derivative direction of jet row r (1..3) and whether row 3 is second order.
+__device__ __forceinline__ int row_dir(int mode, int r) { return (mode == JET_MAXWELL || r < 3) ? r - 1 : -1; }
 
 // ---- element type helpers ---------------------------------------------------------
 template <typename T> __device__ __forceinline__ float to_f(T v);

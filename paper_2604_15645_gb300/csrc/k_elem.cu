@@ -46,31 +46,6 @@ void launch_rwf_prep(const RwfArgs& a, cudaStream_t st) {
   else k_rwf_prep<float><<<grid, 256, 0, st>>>(a);
 }
 
-// Column classification of the jet matrices: group g covers columns 4g..4g+3.
-// Groups below n_res are interior points (4 jet rows); later columns are
-// initial-condition points, then boundary points (one value column each), then padding.
-struct ColPoint {
-  int set;      // 0 interior, 1 initial, 2 boundary, 3 padding
-  int64_t idx;  // point index within its set
-};
-__device__ __forceinline__ ColPoint classify_col(int64_t c, int64_t n_res, int64_t n_ic, int64_t n_bc) {
-  const int64_t b = c - 4 * n_res;
-  if (b < 0) return {0, c >> 2};
-  if (b < n_ic) return {1, b};
-  if (b < n_ic + n_bc) return {2, b - n_ic};
-  return {3, 0};
-}
-
-__device__ __forceinline__ float coord(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res,
-                                       int64_t n_ic, int64_t n_bc, ColPoint cp, int i) {
-  if (cp.set == 0) return x_res[(int64_t)i * n_res + cp.idx];
-  if (cp.set == 1) return x_ic[(int64_t)i * n_ic + cp.idx];
-  return x_bc[(int64_t)i * n_bc + cp.idx];
-}
-
-// Derivative direction of jet row r (1..3) and whether row 3 is second order.
-__device__ __forceinline__ int row_dir(int mode, int r) { return (mode == JET_MAXWELL || r < 3) ? r - 1 : -1; }
-
 template <typename T>
 __device__ __forceinline__ void store4(T* p, const float v[4]);
 template <>
@@ -231,10 +206,10 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
   return s;
 }
 
-template <typename T>
+template <typename T, int D, bool FAST>
 __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
-  extern __shared__ float sW[];   // [d_out][w] then bias
-  const int w = a.w, D = a.d_out;
+  extern __shared__ float sW[];   // [d_out][w]
+  const int w = a.w;
   for (int i = threadIdx.x; i < D * w; i += blockDim.x) sW[i] = a.W[i];
   __syncthreads();
   const T* AL = reinterpret_cast<const T*>(a.AL);
@@ -244,22 +219,29 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c0 = 4 * g;
     float U[3][4];
+#pragma unroll
     for (int c = 0; c < 3; ++c)
+#pragma unroll
       for (int r = 0; r < 4; ++r) U[c][r] = 0.f;
 #pragma unroll 4
     for (int f = 0; f < w; ++f) {
       float v[4];
       load4<T>(AL + (int64_t)f * a.NC + c0, v);
+#pragma unroll
       for (int c = 0; c < D; ++c) {
         const float wc = sW[c * w + f];
+#pragma unroll
         for (int r = 0; r < 4; ++r) U[c][r] = fmaf(wc, v[r], U[c][r]);
       }
     }
     float Ub[3][4];
+#pragma unroll
     for (int c = 0; c < 3; ++c)
+#pragma unroll
       for (int r = 0; r < 4; ++r) Ub[c][r] = 0.f;
     const bool interior = c0 < 4 * a.n_res;
     if (interior) {
+#pragma unroll
       for (int c = 0; c < D; ++c) U[c][0] += a.b[c];
       const float k = a.k_pde, nu = a.nu;
       if (a.pde == PINN_BURGERS_1D) {
@@ -301,6 +283,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
         const float* g = ic ? a.g_ic : a.g_bc;
         const int64_t n = ic ? a.n_ic : a.n_bc;
         const float k = ic ? a.k_ic : a.k_bc;
+#pragma unroll
         for (int c = 0; c < D; ++c) {
           U[c][r] += a.b[c];
           if (mask >> c & 1u) {
@@ -312,22 +295,27 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
       }
     }
     if (!a.want_grad) continue;
+#pragma unroll
     for (int c = 0; c < D; ++c) store4<float>(a.Ubar + (int64_t)c * a.NC + c0, Ub[c]);
     // abar_L = Ubar W_out (rank <= 3), then the tanh-jet adjoint with Z_L.
     const T* ZL = reinterpret_cast<const T*>(a.ZL);
 #pragma unroll 4
     for (int f = 0; f < w; ++f) {
       float ab[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
       for (int c = 0; c < D; ++c) {
         const float wc = sW[c * w + f];
+#pragma unroll
         for (int r = 0; r < 4; ++r) ab[r] = fmaf(wc, Ub[c][r], ab[r]);
       }
       float z[4], zb[4];
       load4<T>(ZL + (int64_t)f * a.NC + c0, z);
       if (interior) {
-        jet_adj(z, ab, zb, a.jet_mode);
+        jet_adj<FAST>(z, ab, zb, a.jet_mode);
       } else {
-        for (int r = 0; r < 4; ++r) zb[r] = (c0 + r < a.n_res * 4 + a.n_ic + a.n_bc) ? val_adj(z[r], ab[r]) : 0.f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          zb[r] = (c0 + r < a.n_res * 4 + a.n_ic + a.n_bc) ? val_adj<FAST>(z[r], ab[r]) : 0.f;
       }
       store4<T>(Zb + (int64_t)f * a.NC + c0, zb);
     }
@@ -345,8 +333,65 @@ int out_loss_blocks(int64_t ngroups) {
 
 void launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st) {
   const size_t smem = sizeof(float) * a.d_out * a.w;
-  if (prec == PINN_BF16) k_out_loss<__nv_bfloat16><<<nblocks, OUT_THREADS, smem, st>>>(a);
-  else k_out_loss<float><<<nblocks, OUT_THREADS, smem, st>>>(a);
+  if (prec == PINN_BF16) {
+    if (a.d_out == 1) k_out_loss<__nv_bfloat16, 1, true><<<nblocks, OUT_THREADS, smem, st>>>(a);
+    else k_out_loss<__nv_bfloat16, 3, true><<<nblocks, OUT_THREADS, smem, st>>>(a);
+  } else {
+    if (a.d_out == 1) k_out_loss<float, 1, false><<<nblocks, OUT_THREADS, smem, st>>>(a);
+    else k_out_loss<float, 3, false><<<nblocks, OUT_THREADS, smem, st>>>(a);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Output-layer weight gradient: dW_out[c][f] = sum over columns of Ubar[c][col] A_L[f][col].
+// One warp per (feature row f, column chunk), coalesced along columns; partials
+// [chunk][d_out][w] reduced in FP64 by the finalisation.
+// ------------------------------------------------------------------------------------
+template <typename T, int D>
+__global__ void k_dw_out(const T* AL, const float* Ubar, int w, int64_t NC, int nchunks, float* part) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (f >= w) return;
+  const int chunk = blockIdx.y;
+  const int64_t noct = NC / 8;
+  const int64_t per = (noct + nchunks - 1) / nchunks;
+  const int64_t o0 = chunk * per, o1 = min(noct, o0 + per);
+  float acc[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) acc[c] = 0.f;
+  const T* rowp = AL + (int64_t)f * NC;
+#pragma unroll 2
+  for (int64_t o = o0 + lane; o < o1; o += 32) {
+    float v[4], u[4];
+    load4<T>(rowp + 8 * o, v);
+    load4<T>(rowp + 8 * o + 4, u);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      float g[4], h[4];
+      load4<float>(Ubar + (int64_t)c * NC + 8 * o, g);
+      load4<float>(Ubar + (int64_t)c * NC + 8 * o + 4, h);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[c] = fmaf(g[r], v[r], fmaf(h[r], u[r], acc[c]));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    float s = acc[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) part[((int64_t)chunk * D + c) * w + f] = s;
+  }
+}
+
+void launch_dw_out(const void* AL, const float* Ubar, int w, int d_out, int64_t NC, int nchunks, float* part,
+                   int prec, cudaStream_t st) {
+  dim3 grid((w + 7) / 8, nchunks);
+  if (prec == PINN_BF16) {
+    if (d_out == 1) k_dw_out<__nv_bfloat16, 1><<<grid, 256, 0, st>>>((const __nv_bfloat16*)AL, Ubar, w, NC, nchunks, part);
+    else k_dw_out<__nv_bfloat16, 3><<<grid, 256, 0, st>>>((const __nv_bfloat16*)AL, Ubar, w, NC, nchunks, part);
+  } else {
+    if (d_out == 1) k_dw_out<float, 1><<<grid, 256, 0, st>>>((const float*)AL, Ubar, w, NC, nchunks, part);
+    else k_dw_out<float, 3><<<grid, 256, 0, st>>>((const float*)AL, Ubar, w, NC, nchunks, part);
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -425,6 +470,20 @@ void launch_row_reduce(const void* Zbar, int M, int64_t NC, int64_t n_res, int64
 // (Eq. 15): dV = exp(s) dW, ds_i = sum_j dW_ij W_ij, plus db.  One block per
 // (output row, layer).
 // ------------------------------------------------------------------------------------
+// Deterministic block sum of N doubles per thread (fixed assignment and order).
+template <int N>
+__device__ __forceinline__ void block_sum_n(double v[N], double (*sh)[N]) {
+  for (int k = 0; k < N; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < N; ++k) sh[threadIdx.x >> 5][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      for (int k = 0; k < N; ++k) v[k] += sh[w][k];
+}
+
 __global__ void k_finalize_grad(FinalizeArgs a) {
   const int l = blockIdx.y, i = blockIdx.x;
   const int fin = a.fin[l], fout = a.fout[l];
@@ -433,30 +492,55 @@ __global__ void k_finalize_grad(FinalizeArgs a) {
   const float* W = reinterpret_cast<const float*>(a.ws + a.w32[l]) + (int64_t)i * fin;
   const float* dbp = reinterpret_cast<const float*>(a.ws + a.dbpart[l]);
   const int dbs = a.dbstride[l];
+  const int nbp = a.nbpart_l[l];
   const float es = a.rwf ? expf(a.params[a.offs[l] + i]) : 1.f;
-  double dsum = 0.0;
-  for (int j = threadIdx.x; j < fin; j += blockDim.x) {
-    double dW = 0.0;
-    if (raw) {
-      for (int p = 0; p < a.nbpart; ++p) dW += (double)dbp[((int64_t)p * fout + i) * dbs + 1 + j];
-    } else {
-      const float* part = reinterpret_cast<const float*>(a.ws + a.dwpart[l]);
-      for (int s = 0; s < a.nsplit[l]; ++s) dW += (double)part[((int64_t)s * fout + i) * fin + j];
-    }
-    a.grad[a.offV[l] + (int64_t)i * fin + j] = (float)(dW * es);
-    dsum += dW * (double)W[j];
+  __shared__ double sh[32][5];
+  // v[0]: sum_j dW_ij W_ij (RWF scale gradient), v[1]: bias, v[2..4]: raw-coordinate dW
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int p = threadIdx.x; p < nbp; p += blockDim.x) {
+    const float* q = dbp + ((int64_t)p * fout + i) * dbs;
+    v[1] += (double)q[0];
+    if (raw)
+      for (int j = 0; j < fin && j < 3; ++j) v[2 + j] += (double)q[1 + j];
   }
-  __shared__ double sh[32];
-  for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dsum;
-  __syncthreads();
+  if (!raw) {
+    const float* part = reinterpret_cast<const float*>(a.ws + a.dwpart[l]);
+    const int ns = a.nsplit[l];
+    const int64_t sstride = (int64_t)fout * fin;
+    if ((fin & 3) == 0) {
+      for (int j4 = threadIdx.x * 4; j4 < fin; j4 += blockDim.x * 4) {
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+        const float* q = part + (int64_t)i * fin + j4;
+#pragma unroll 4
+        for (int s = 0; s < ns; ++s) {
+          const float4 x = *reinterpret_cast<const float4*>(q + s * sstride);
+          d0 += (double)x.x; d1 += (double)x.y; d2 += (double)x.z; d3 += (double)x.w;
+        }
+        const double dd[4] = {d0, d1, d2, d3};
+        for (int k = 0; k < 4; ++k) {
+          a.grad[a.offV[l] + (int64_t)i * fin + j4 + k] = (float)(dd[k] * es);
+          v[0] += dd[k] * (double)W[j4 + k];
+        }
+      }
+    } else {
+      for (int j = threadIdx.x; j < fin; j += blockDim.x) {
+        double dW = 0.0;
+        for (int s = 0; s < ns; ++s) dW += (double)part[s * sstride + (int64_t)i * fin + j];
+        a.grad[a.offV[l] + (int64_t)i * fin + j] = (float)(dW * es);
+        v[0] += dW * (double)W[j];
+      }
+    }
+  }
+  block_sum_n<5>(v, sh);
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    if (a.rwf) a.grad[a.offs[l] + i] = (float)s;
-    double db = 0.0;
-    for (int p = 0; p < a.nbpart; ++p) db += (double)dbp[((int64_t)p * fout + i) * dbs];
-    a.grad[a.offb[l] + i] = (float)db;
+    if (raw) {
+      for (int j = 0; j < fin && j < 3; ++j) {
+        a.grad[a.offV[l] + (int64_t)i * fin + j] = (float)(v[2 + j] * es);
+        v[0] += v[2 + j] * (double)W[j];
+      }
+    }
+    if (a.rwf) a.grad[a.offs[l] + i] = (float)v[0];
+    a.grad[a.offb[l] + i] = (float)v[1];
   }
 }
 
@@ -518,3 +602,24 @@ void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float 
 }
 
 }  // namespace pinn
+
+// Test hook: the fast tanh pair used by the BF16 epilogues, elementwise.
+namespace {
+__global__ void k_tanh_selftest(int64_t n, const float* z, float* t, float* tp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float a, b;
+    pinn::tanh_fast(z[i], a, b);
+    t[i] = a;
+    tp[i] = b;
+  }
+}
+}  // namespace
+
+extern "C" PINN_API pinn_status pinn_tanh_selftest(int64_t n, const float* d_z, float* d_t, float* d_tp,
+                                                   void* stream) {
+  if (n < 0 || (n && (!d_z || !d_t || !d_tp))) return PINN_ERR_INVALID_ARG;
+  if (n == 0) return PINN_OK;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  k_tanh_selftest<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, d_z, d_t, d_tp);
+  return cudaGetLastError() == cudaSuccess ? PINN_OK : PINN_ERR_CUDA;
+}

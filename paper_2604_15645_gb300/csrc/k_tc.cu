@@ -13,11 +13,11 @@
 // 64 whole points and applies the tanh jet rule (or its adjoint) without any
 // cross-thread exchange.
 //
-// Warp roles per CTA (320 threads, one CTA per SM, persistent over tiles):
-//   warp 0     TMA producer (one lane)
-//   warp 1     TMEM allocator + MMA issuer (one lane)
-//   warps 2-9  epilogue; warp w reads TMEM lanes 32*(w%4) .. +31, columns
-//              128*((w-2)/4) .. +127 of the 256-column accumulator
+// Warp roles per CTA (576 threads, one CTA per SM, persistent over tiles):
+//   warp 0      TMA producer (one lane)
+//   warp 1      TMEM allocator + MMA issuer (one lane)
+//   warps 2-17  epilogue; warp w reads TMEM lanes 32*(w%4) .. +31, columns
+//               64*((w-2)/4) .. +63 of the 256-column accumulator
 // Two accumulator buffers of 256 columns let the epilogue of one tile overlap the
 // MMAs of the next.  Every mbarrier wait is bounded (global timer); on expiry the
 // CTA latches PINN_ERR_TIMEOUT in the status word, stops issuing work, waits for
@@ -37,7 +37,7 @@ namespace {
 
 constexpr int BM = 128;          // accumulator rows (TMEM lanes)
 constexpr int BN = 256;          // accumulator columns per buffer
-constexpr int EPI_WARPS = 8;     // two warps per TMEM lane quadrant, each on half the columns
+constexpr int EPI_WARPS = 16;    // four warps per TMEM lane quadrant, each on a quarter of the columns
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
 
@@ -125,6 +125,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, float v[16]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Bulk tensor store shared -> global (asynchronous proxy) and its group bookkeeping.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Shared-memory matrix descriptor (tcgen05), 128-byte swizzle, version 1.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -161,12 +181,17 @@ struct Cfg {
   static constexpr int A_BYTES = BM * 128;        // 16 KB
   static constexpr int B_BYTES = BN * 128;        // 32 KB
   static constexpr int STAGE = A_BYTES * (SPLIT ? 2 : 1) + B_BYTES;
-  static constexpr int STAGES = SPLIT ? 3 : 4;
+  // Epilogues that write jet matrices stage each 32-row x 16-column chunk in shared
+  // memory and store it with a bulk tensor copy (double-buffered per warp).
+  static constexpr bool STAGED = (MODE == TC_FWD || MODE == TC_ADJ);
+  static constexpr int STG_BYTES = 32 * 16 * ES;                        // one chunk of one array
+  static constexpr int STAGING = STAGED ? EPI_WARPS * 2 * 2 * STG_BYTES : 0;
+  static constexpr int STAGES = STAGED ? (SPLIT ? 2 : 3) : (SPLIT ? 3 : 4);
   static constexpr bool B_MN = (MODE != TC_DW);
   static constexpr int BOXN = 128 / ES;           // MN-major box width (columns)
   static constexpr int NBOX = BN / BOXN;
   static constexpr int BOX_BYTES = BOXN * 0 + BKE * 128;   // one MN-major box: BKE rows of 128 bytes
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE + STAGING + 1024 /*align*/ + 256 /*barriers*/;
 };
 
 template <typename T>
@@ -188,6 +213,36 @@ __device__ __forceinline__ void store16<__nv_bfloat16>(__nv_bfloat16* p, const f
   reinterpret_cast<uint4*>(p)[0] = make_uint4(u[0], u[1], u[2], u[3]);
   reinterpret_cast<uint4*>(p)[1] = make_uint4(u[4], u[5], u[6], u[7]);
 }
+// 16 elements as raw 128-bit words (8 registers for BF16), converted on use.
+template <typename T>
+struct Raw16 {
+  uint4 w[sizeof(T) * 16 / 16];
+};
+template <typename T>
+__device__ __forceinline__ void load_raw16(const T* p, Raw16<T>& r) {
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(r.w) / sizeof(uint4)); ++i) r.w[i] = reinterpret_cast<const uint4*>(p)[i];
+}
+__device__ __forceinline__ void unpack16(const Raw16<__nv_bfloat16>& r, float v[16]) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const uint32_t w[4] = {r.w[i].x, r.w[i].y, r.w[i].z, r.w[i].w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[j]));
+      v[8 * i + 2 * j] = f.x;
+      v[8 * i + 2 * j + 1] = f.y;
+    }
+  }
+}
+__device__ __forceinline__ void unpack16(const Raw16<float>& r, float v[16]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[4 * i] = __uint_as_float(r.w[i].x); v[4 * i + 1] = __uint_as_float(r.w[i].y);
+    v[4 * i + 2] = __uint_as_float(r.w[i].z); v[4 * i + 3] = __uint_as_float(r.w[i].w);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void load16(const T* p, float v[16]);
 template <>
@@ -217,12 +272,14 @@ __device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, fl
 template <bool TF32, int MODE, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
-              const __grid_constant__ CUtensorMap mapB, const TcParams p) {
+              const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapO1,
+              const __grid_constant__ CUtensorMap mapO2, const TcParams p) {
   using C = Cfg<TF32, MODE, SPLIT>;
   using T = typename std::conditional<TF32, float, __nv_bfloat16>::type;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint8_t* staging = smem + C::STAGES * C::STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(staging + C::STAGING);
   uint64_t* empty = full + C::STAGES;
   uint64_t* acc_full = empty + C::STAGES;
   uint64_t* acc_empty = acc_full + 2;
@@ -337,9 +394,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ---------------------------------------------------------------- epilogue
+    constexpr bool FAST = !TF32;
+    constexpr int PARTS = EPI_WARPS / 4;       // column parts per tile
+    constexpr int CPP = BN / 16 / PARTS;       // 16-column chunks per part
     const int quad = warp & 3;                 // TMEM lane quadrant this warp may read
-    const int half = (warp - 2) >> 2;          // which 128 columns of the tile
+    const int part = (warp - 2) >> 2;          // which quarter of the tile's columns
     const int row = quad * 32 + lane;
+    T* stg = reinterpret_cast<T*>(staging + (warp - 2) * (2 * 2 * C::STG_BYTES));   // [buf][array][32][16]
+    uint32_t nstore = 0;
     int local = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
       int mb, nb, k0, k1;
@@ -348,65 +410,133 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!mbar_wait(&acc_full[buf], (local >> 1) & 1, abort_flag, p.status)) break;
       tc_fence_after();
       const int m = mb * BM + row;
+      const int row0 = mb * BM + quad * 32;    // first row of this warp's 32-row slab
       const bool mvalid = m < p.M;
       const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN;
       const float bias = (MODE == TC_FWD && mvalid) ? p.e.bias[m] : 0.f;
-#pragma unroll 1
-      for (int c = half * (BN / 32); c < (half + 1) * (BN / 32); ++c) {
+      float dbacc[4] = {0.f, 0.f, 0.f, 0.f};
+      float v[2][16];
+      Raw16<T> zr[2];
+      const T* zrow = (MODE == TC_ADJ) ? reinterpret_cast<const T*>(p.e.zin) + (int64_t)m * p.NC : nullptr;
+      if (MODE == TC_ADJ && mvalid) load_raw16<T>(zrow + (int64_t)nb * BN + part * CPP * 16, zr[0]);
+      tmem_ld16_issue(taddr + part * CPP * 16, v[0]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int cc = 0; cc < CPP; ++cc) {
+        const int c = part * CPP + cc;
         const int64_t col0 = (int64_t)nb * BN + c * 16;
-        float v[16], z[16];
-        if (MODE == TC_ADJ && mvalid) load16<T>(reinterpret_cast<const T*>(p.e.zin) + (int64_t)m * p.NC + col0, z);
-        tmem_ld16(taddr + c * 16, v);
-        if (!mvalid) continue;
-        if (MODE == TC_FWD) {
-          float a[16];
+        float* cur = v[cc & 1];
+        float z[16];
+        if (MODE == TC_ADJ) unpack16(zr[cc & 1], z);
+        if (cc + 1 < CPP) {                    // prefetch the next chunk
+          if (MODE == TC_ADJ && mvalid) load_raw16<T>(zrow + col0 + 16, zr[(cc + 1) & 1]);
+          tmem_ld16_issue(taddr + (c + 1) * 16, v[(cc + 1) & 1]);
+        }
+        if (C::STAGED) {
+          float o[16];
+          if (MODE == TC_FWD) {
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int64_t col = col0 + 4 * g;
-            float* z = &v[4 * g];
-            if (col < p.e.n_res4) {
-              z[0] += bias;
-              jet_fwd(z, &a[4 * g], p.e.jet_mode);
-            } else {
+            for (int g = 0; g < 4; ++g) {
+              const int64_t col = col0 + 4 * g;
+              float* zz = &cur[4 * g];
+              if (col < p.e.n_res4) {
+                zz[0] += bias;
+                jet_fwd<FAST>(zz, &o[4 * g], p.e.jet_mode);
+              } else {
 #pragma unroll
-              for (int r = 0; r < 4; ++r) {
-                if (col + r < p.e.ncols) { z[r] += bias; a[4 * g + r] = val_fwd(z[r]); }
-                else { z[r] = 0.f; a[4 * g + r] = 0.f; }
+                for (int r = 0; r < 4; ++r) {
+                  if (col + r < p.e.ncols) { zz[r] += bias; o[4 * g + r] = val_fwd<FAST>(zz[r]); }
+                  else { zz[r] = 0.f; o[4 * g + r] = 0.f; }
+                }
+              }
+            }
+          } else {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const int64_t col = col0 + 4 * g;
+              if (col < p.e.n_res4) {
+                jet_adj<FAST>(&z[4 * g], &cur[4 * g], &o[4 * g], p.e.jet_mode);
+              } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                  o[4 * g + r] = (col + r < p.e.ncols) ? val_adj<FAST>(z[4 * g + r], cur[4 * g + r]) : 0.f;
+              }
+            }
+            if (p.e.dbpart && mvalid) {
+              // bias gradient (value columns) and, for a first layer on raw
+              // coordinates, the coordinate terms of its weight gradient
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                const int64_t col = col0 + 4 * g;
+                if (col < p.e.n_res4) {
+                  dbacc[0] += o[4 * g];
+                  if (p.e.dterms) {
+                    const int64_t pt = col >> 2;
+                    for (int jj = 0; jj < p.e.dterms; ++jj)
+                      dbacc[1 + jj] = fmaf(o[4 * g], p.e.x_res[(int64_t)jj * p.e.n_res + pt], dbacc[1 + jj]);
+                    for (int r = 1; r < 4; ++r) {
+                      const int d = row_dir(p.e.jet_mode, r);
+                      if (d >= 0) dbacc[1 + d] += o[4 * g + r];
+                    }
+                  }
+                } else {
+                  for (int r = 0; r < 4; ++r) {
+                    const ColPoint cp = classify_col(col + r, p.e.n_res, p.e.n_ic, p.e.n_bc);
+                    if (cp.set == 3) continue;
+                    dbacc[0] += o[4 * g + r];
+                    for (int jj = 0; jj < p.e.dterms; ++jj)
+                      dbacc[1 + jj] = fmaf(o[4 * g + r],
+                                           coord(p.e.x_res, p.e.x_ic, p.e.x_bc, p.e.n_res, p.e.n_ic, p.e.n_bc, cp, jj),
+                                           dbacc[1 + jj]);
+                  }
+                }
               }
             }
           }
-          store16<T>(reinterpret_cast<T*>(p.e.out) + (int64_t)m * p.NC + col0, a);
-          store16<T>(reinterpret_cast<T*>(p.e.zout) + (int64_t)m * p.NC + col0, v);
-        } else if (MODE == TC_ADJ) {
-          float o[16];
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int64_t col = col0 + 4 * g;
-            if (col < p.e.n_res4) {
-              jet_adj(&z[4 * g], &v[4 * g], &o[4 * g], p.e.jet_mode);
-            } else {
-#pragma unroll
-              for (int r = 0; r < 4; ++r)
-                o[4 * g + r] = (col + r < p.e.ncols) ? val_adj(z[4 * g + r], v[4 * g + r]) : 0.f;
+          // stage this warp's 32 x 16 chunk(s) and store them with one bulk copy each
+          const int sb = nstore & 1;
+          if (nstore >= 2) {
+            if (lane == 0) bulk_wait_read1();   // the copy that used this buffer has read it
+            __syncwarp();
+          }
+          T* s0 = stg + (sb * 2 + 0) * (32 * 16);
+          T* s1 = stg + (sb * 2 + 1) * (32 * 16);
+          store16<T>(s0 + lane * 16, o);
+          if (MODE == TC_FWD) store16<T>(s1 + lane * 16, cur);
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) {
+            if (row0 < p.M) {
+              tma_store_2d(&mapO1, s0, (int)col0, row0);
+              if (MODE == TC_FWD) tma_store_2d(&mapO2, s1, (int)col0, row0);
             }
+            bulk_commit();   // one group per chunk (possibly empty) keeps the buffer parity exact
           }
-          store16<T>(reinterpret_cast<T*>(p.e.out) + (int64_t)m * p.NC + col0, o);
-        } else if (MODE == TC_DW) {
-          const int split = t / (p.m_tiles * p.n_tiles);
-          float* dst = p.out32 + ((int64_t)split * p.M + m) * p.N;
-          if (col0 + 16 <= p.N && (p.N & 3) == 0) {
-            store16<float>(dst + col0, v);
-          } else {
-            for (int j = 0; j < 16; ++j)
-              if (col0 + j < p.N) dst[col0 + j] = v[j];
+          ++nstore;
+        } else if (mvalid) {
+          if (MODE == TC_DW) {
+            const int split = t / (p.m_tiles * p.n_tiles);
+            float* dst = p.out32 + ((int64_t)split * p.M + m) * p.N;
+            if (col0 + 16 <= p.N && (p.N & 3) == 0) {
+              store16<float>(dst + col0, cur);
+            } else {
+              for (int j = 0; j < 16; ++j)
+                if (col0 + j < p.N) dst[col0 + j] = cur[j];
+            }
+          } else {   // TC_STORE
+            store16<float>(p.out32 + (int64_t)m * p.NC + col0, cur);
           }
-        } else {   // TC_STORE
-          store16<float>(p.out32 + (int64_t)m * p.NC + col0, v);
         }
+        if (cc + 1 < CPP) tmem_wait_ld();
+      }
+      if (MODE == TC_ADJ && p.e.dbpart && mvalid) {
+        float* dst = p.e.dbpart + ((int64_t)(nb * PARTS + part) * p.M + m) * (1 + p.e.dterms);
+        for (int jj = 0; jj <= p.e.dterms; ++jj) dst[jj] = dbacc[jj];
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[buf]);
     }
+    if (C::STAGED && lane == 0) bulk_wait_all();   // bulk stores done before the CTA exits
   }
 
   // ---- teardown: wait (bounded) for copies still in flight, free TMEM ----------------
@@ -448,9 +578,25 @@ bool make_map(CUtensorMap* m, const void* base, bool tf32, uint64_t cols, uint64
   return r == CUDA_SUCCESS;
 }
 
+// Output map for the staged bulk stores: [rows][cols], box 32 rows x 16 columns,
+// no swizzle (the staging buffer is plain row-major).
+bool make_store_map(CUtensorMap* m, const void* base, bool tf32, uint64_t cols, uint64_t rows) {
+  if (!g_encode) return false;
+  const uint32_t es = tf32 ? 4 : 2;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * es};
+  cuuint32_t box[2] = {16, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 template <bool TF32, int MODE, bool SPLIT>
 pinn_status launch(pinn_handle* h, const CUtensorMap& a, const CUtensorMap& a2, const CUtensorMap& b,
-                   const TcParams& p, int grid, cudaStream_t st) {
+                   const CUtensorMap& o1, const CUtensorMap& o2, const TcParams& p, int grid, cudaStream_t st) {
   using C = Cfg<TF32, MODE, SPLIT>;
   auto kern = k_tc_gemm<TF32, MODE, SPLIT>;
   static bool attr_set = false;   // per instantiation
@@ -461,7 +607,7 @@ pinn_status launch(pinn_handle* h, const CUtensorMap& a, const CUtensorMap& a2, 
     }
     attr_set = true;
   }
-  kern<<<grid, THREADS, C::SMEM, st>>>(a, a2, b, p);
+  kern<<<grid, THREADS, C::SMEM, st>>>(a, a2, b, o1, o2, p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(h->err, sizeof(h->err), "tcgen05 kernel launch: %s", cudaGetErrorString(e));
@@ -529,9 +675,12 @@ pinn_status tc_gemm_fwd(pinn_handle* h, const void* W, const void* Wlo, const vo
   if (!make_map(&ma, W, false, fin, fout, 64, BM) || !make_map(&ma2, Wlo, false, fin, fout, 64, BM))
     return map_err(h, "forward weights");
   if (!make_map(&mb, A, false, NC, fin, 64, 64)) return map_err(h, "forward activations");
+  CUtensorMap o1, o2;
+  if (!make_store_map(&o1, e.out, false, NC, fout) || !make_store_map(&o2, e.zout, false, NC, fout))
+    return map_err(h, "forward outputs");
   TcParams p = base_params(fout, (int)NC, fin, NC, 64, h->d_status);
   p.e = e;
-  return launch<false, TC_FWD, true>(h, ma, ma2, mb, p, grid_for(h, p.m_tiles * p.n_tiles), st);
+  return launch<false, TC_FWD, true>(h, ma, ma2, mb, o1, o2, p, grid_for(h, p.m_tiles * p.n_tiles), st);
 }
 
 pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fin, int fout, int64_t NC,
@@ -539,9 +688,11 @@ pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fi
   CUtensorMap ma, mb;
   if (!make_map(&ma, WT, false, fout, fin, 64, BM)) return map_err(h, "adjoint weights");
   if (!make_map(&mb, Zbar, false, NC, fout, 64, 64)) return map_err(h, "adjoint input");
+  CUtensorMap o1;
+  if (!make_store_map(&o1, e.out, false, NC, fin)) return map_err(h, "adjoint output");
   TcParams p = base_params(fin, (int)NC, fout, NC, 64, h->d_status);
   p.e = e;
-  return launch<false, TC_ADJ, false>(h, ma, ma, mb, p, grid_for(h, p.m_tiles * p.n_tiles), st);
+  return launch<false, TC_ADJ, false>(h, ma, ma, mb, o1, o1, p, grid_for(h, p.m_tiles * p.n_tiles), st);
 }
 
 pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout, int fin, int64_t NC, int nsplit,
@@ -557,7 +708,7 @@ pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout
     return PINN_ERR_INVALID_ARG;
   }
   p.out32 = part;
-  return launch<false, TC_DW, false>(h, ma, ma, mb, p, grid_for(h, p.m_tiles * p.n_tiles * nsplit), st);
+  return launch<false, TC_DW, false>(h, ma, ma, mb, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles * nsplit), st);
 }
 
 }  // namespace pinn
@@ -589,8 +740,12 @@ extern "C" PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, 
     } else {
       TcParams p = base_params(M, N, K, N, 64, status);
       p.out32 = d_D;
-      if (d_A2) r = launch<false, TC_STORE, true>(&h, ma, ma2, mb, p, grid_for(&h, p.m_tiles * p.n_tiles), (cudaStream_t)stream);
-      else r = launch<false, TC_STORE, false>(&h, ma, ma, mb, p, grid_for(&h, p.m_tiles * p.n_tiles), (cudaStream_t)stream);
+      if (d_A2)
+        r = launch<false, TC_STORE, true>(&h, ma, ma2, mb, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
+                                          (cudaStream_t)stream);
+      else
+        r = launch<false, TC_STORE, false>(&h, ma, ma, mb, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
+                                           (cudaStream_t)stream);
     }
   } else {
     // D[M][N] = A[M][K] . B[N][K]^T   (both K contiguous: K-major)
@@ -599,7 +754,8 @@ extern "C" PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, 
     } else {
       TcParams p = base_params(M, N, K, N, 64, status);
       p.out32 = d_D;
-      r = launch<false, TC_DW, false>(&h, ma, ma, mb, p, grid_for(&h, p.m_tiles * p.n_tiles), (cudaStream_t)stream);
+      r = launch<false, TC_DW, false>(&h, ma, ma, mb, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
+                                      (cudaStream_t)stream);
     }
   }
   int st = 0;

@@ -10,6 +10,9 @@ namespace pinn {
 void tc_init(pinn_handle* h);
 // True when hidden layer li (0-based weight layer) runs on tensor cores.
 bool tc_layer_supported(const pinn_handle* h, int li, int64_t NC);
+// Bias partials per column tile written by the fused adjoint epilogue.
+constexpr int TC_DB_PARTS = 4;
+constexpr int TC_BN = 256;
 // Number of K (column) splits of the tensor-core weight-gradient GEMM.
 int tc_dw_splits(const pinn_handle* h, int fout, int fin, int64_t NC);
 

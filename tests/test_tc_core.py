@@ -40,3 +40,24 @@ def test_k_major_both_operands(cuda_lib, M, N, K):
     ref = A.float() @ B.float().T
     assert torch.isfinite(D).all()
     assert _rel(D, ref) < 1e-5
+
+
+def test_fast_tanh_against_cuda_tanh(cuda_lib):
+    """The BF16 epilogues' tanh (exponential form) against CUDA's tanh and a float64
+    sech^2, including saturated arguments where 1 - tanh^2 would cancel."""
+    from paper_2604_15645_gb300 import _lib
+    z = torch.cat([torch.linspace(-12, 12, 200001, device="cuda"),
+                   torch.tensor([0.0, -0.0, 1e-30, -1e-30, 1e-8, 20.0, -20.0, 50.0], device="cuda")])
+    t = torch.empty_like(z)
+    tp = torch.empty_like(z)
+    _lib.pinn_tanh_selftest(z.numel(), z.data_ptr(), t.data_ptr(), tp.data_ptr(),
+                            torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    ref_t = torch.tanh(z)                                   # CUDA's tanh
+    assert float((t - ref_t).abs().max()) < 4e-7
+    zd = z.double()
+    ref_tp = 1.0 / torch.cosh(zd) ** 2
+    ok = ref_tp > 1e-30
+    relerr = ((tp.double() - ref_tp).abs() / ref_tp)[ok]
+    assert float(relerr.max()) < 2e-5
+    assert torch.all(t.abs() <= 1) and torch.all(tp >= 0)
