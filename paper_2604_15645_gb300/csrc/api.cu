@@ -61,22 +61,28 @@ namespace pinn {
 pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc, Plan* p) {
   Plan q;
   q.n_res = n_res; q.n_ic = n_ic; q.n_bc = n_bc;
-  q.ncols = 4 * n_res + n_ic + n_bc;
-  q.NC = (int64_t)align_up((size_t)std::max<int64_t>(q.ncols, 1), COL_ALIGN);
+  q.ncols = 4 * (n_res + n_ic + n_bc);
+  q.NP = (int64_t)align_up((size_t)std::max<int64_t>(n_res + n_ic + n_bc, 1), PT_ALIGN);
+  q.NC = 4 * q.NP;
   q.es = (h->spec.precision == PINN_BF16) ? 2 : 4;
+  q.lo = (h->spec.precision == PINN_BF16);
   const int L = h->L;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   q.nbpart = (int)std::min<int64_t>(256, std::max<int64_t>(1, q.NC / 8192));
-  if (h->spec.ff_m) q.A[0] = take((size_t)2 * h->spec.ff_m * q.NC * q.es);
+  if (h->spec.ff_m) {
+    q.A[0] = take((size_t)2 * h->spec.ff_m * q.NC * q.es);
+    if (q.lo) q.Alo[0] = take((size_t)2 * h->spec.ff_m * q.NP * 2);
+  }
   for (int l = 1; l <= L; ++l) {
     q.A[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
+    if (q.lo) q.Alo[l] = take((size_t)h->spec.widths[l - 1] * q.NP * 2);
     q.Z[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
   }
   q.Zbar[0] = take((size_t)h->w_max * q.NC * q.es);
   q.Zbar[1] = take((size_t)h->w_max * q.NC * q.es);
   q.Ubar = take((size_t)h->d_out * q.NC * 4);
-  q.nloss_blocks = out_loss_blocks(q.NC / 4);
+  q.nloss_blocks = out_loss_blocks(q.NP);
   q.losspart = take((size_t)q.nloss_blocks * 8 * sizeof(double));
   *p = q;
   p->total = off;
@@ -116,7 +122,7 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
     if (raw) {
       lp.nsplit = 0;
     } else if (li == h->L) {
-      lp.nsplit = c->p.nbpart;                     // output layer: column chunks of k_dw_out
+      lp.nsplit = std::min(4 * c->p.nbpart, 1024);   // output layer: column chunks of k_dw_out
     } else if (c->tc[li]) {
       lp.nsplit = tc_dw_splits(h, lp.fout, lp.fin, c->p.NC);
     } else {
@@ -192,10 +198,11 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   PhaseScope ps(h, st, PH_EMBED, 1);
   if (h->spec.ff_m) {
     launch_embed_ff(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, h->ff_B, h->spec.ff_m, mode,
-                    ws + p.A[0], p.NC, prec, st);
+                    ws + p.A[0], p.lo ? ws + p.Alo[0] : nullptr, p.NP, prec, st);
   } else {
     launch_first_layer(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, W32(0), bias(0),
-                       cp.lay[0].fout, mode, ws + p.A[1], ws + p.Z[1], p.NC, prec, st);
+                       cp.lay[0].fout, mode, ws + p.A[1], p.lo ? ws + p.Alo[1] : nullptr, ws + p.Z[1], p.NP, prec,
+                       st);
   }
   }
 
@@ -203,22 +210,25 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   for (int li = h->first_gemm; li < L; ++li) {
     EpiArgs e{};
     e.bias = bias(li); e.out = ws + p.A[li + 1]; e.zout = ws + p.Z[li + 1];
-    e.n_res4 = 4 * p.n_res; e.ncols = p.ncols; e.jet_mode = mode;
+    e.alo_out = p.lo ? ws + p.Alo[li + 1] : nullptr;
+    e.alo_in = p.lo ? ws + p.Alo[li] : nullptr;
+    e.jet_mode = mode;
     PhaseScope ps(h, st, PH_FWD, 1);
     if (cp.tc[li]) {
-      s = tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + cp.lay[li].wlo, ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NC, e, st);
+      s = tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + cp.lay[li].wlo, ws + p.A[li], ws + p.Alo[li], cp.lay[li].fout,
+                      cp.lay[li].fin, p.NC, e, st);
       if (s) return s;
     } else {
-      launch_simt_gemm_fwd(W32(li), ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NC, e, prec, st);
+      launch_simt_gemm_fwd(W32(li), ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NP, e, prec, st);
     }
   }
 
   // 4. Output layer, residual, loss partials, adjoint seed and Zbar_L.
   OutArgs oa{};
-  oa.AL = ws + p.A[L]; oa.ZL = ws + p.Z[L];
+  oa.AL = ws + p.A[L]; oa.ALlo = p.lo ? ws + p.Alo[L] : nullptr; oa.ZL = ws + p.Z[L];
   oa.W = W32(L); oa.b = bias(L);
   oa.g_ic = b->g_ic; oa.g_bc = b->g_bc; oa.ic_mask = b->ic_mask; oa.bc_mask = b->bc_mask;
-  oa.n_res = p.n_res; oa.n_ic = p.n_ic; oa.n_bc = p.n_bc; oa.NC = p.NC;
+  oa.n_res = p.n_res; oa.n_ic = p.n_ic; oa.n_bc = p.n_bc; oa.NP = p.NP; oa.NC = p.NC;
   oa.w = cp.lay[L].fin; oa.d_out = h->d_out; oa.pde = h->spec.pde; oa.jet_mode = mode;
   oa.nu = (float)prob->nu;
   oa.k_pde = p.n_res ? (float)(prob->lambda_pde / (double)p.n_res) : 0.f;
@@ -245,8 +255,8 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
                 cp.lay[L].nsplit, reinterpret_cast<float*>(ws + cp.lay[L].dwpart), prec, st);
   }
   PhaseScope ps_r(h, st, PH_RED, 1);
-  launch_row_reduce(ws + p.Ubar, h->d_out, p.NC, p.n_res, p.ncols, p.nbpart, b->x_res, b->x_ic, b->x_bc, p.n_ic,
-                    p.n_bc, 0, mode, reinterpret_cast<float*>(ws + cp.lay[L].dbpart), PINN_FP32, st);
+  launch_row_reduce(ws + p.Ubar, true, h->d_out, p.NP, p.n_res, p.n_ic, p.n_bc, p.nbpart, b->x_res, b->x_ic,
+                    b->x_bc, 0, mode, reinterpret_cast<float*>(ws + cp.lay[L].dbpart), prec, st);
   }
 
   // 6. Hidden layers in reverse: dW, db, then the adjoint GEMM into the layer below.
@@ -266,13 +276,13 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
     }
     if (!cp.fused_db[li]) {
       PhaseScope ps(h, st, PH_RED, 1);
-      launch_row_reduce(zb, lp.fout, p.NC, p.n_res, p.ncols, p.nbpart, b->x_res, b->x_ic, b->x_bc, p.n_ic, p.n_bc,
+      launch_row_reduce(zb, false, lp.fout, p.NP, p.n_res, p.n_ic, p.n_bc, p.nbpart, b->x_res, b->x_ic, b->x_bc,
                         raw ? h->d_in : 0, mode, reinterpret_cast<float*>(ws + lp.dbpart), prec, st);
     }
     if (li >= 1) {
       EpiArgs e{};
       e.out = ws + p.Zbar[li % 2]; e.zin = ws + p.Z[li];
-      e.n_res4 = 4 * p.n_res; e.ncols = p.ncols; e.jet_mode = mode;
+      e.jet_mode = mode;
       if (cp.fused_db[li - 1]) {
         e.dbpart = reinterpret_cast<float*>(ws + cp.lay[li - 1].dbpart);
         e.dterms = (li - 1 == 0 && !h->spec.ff_m) ? h->d_in : 0;
@@ -284,7 +294,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
         s = tc_gemm_adj(h, ws + lp.wtc, zb, lp.fin, lp.fout, p.NC, e, st);
         if (s) return s;
       } else {
-        launch_simt_gemm_adj(reinterpret_cast<const float*>(ws + lp.wt32), zb, lp.fin, lp.fout, p.NC, e, prec, st);
+        launch_simt_gemm_adj(reinterpret_cast<const float*>(ws + lp.wt32), zb, lp.fin, lp.fout, p.NP, e, prec, st);
       }
     }
   }

@@ -10,14 +10,13 @@
 
 namespace pinn {
 
-// Jet rows per interior point.  Column 4p+r of every activation matrix holds
-// row r of point p: r=0 value, r=1,2 first derivatives, r=3 either a second-order
-// row (Burgers d2/dx2, Navier-Stokes Laplacian) or a third first derivative
-// (Maxwell d/dt).  Initial/boundary points take one (value) column each, after
-// all interior columns.
+// Jet rows per point: r=0 value, r=1,2 first derivatives, r=3 either a
+// second-order row (Burgers d2/dx2, Navier-Stokes Laplacian) or a third first
+// derivative (Maxwell d/dt).  The column layout (tiles of 64 points, blocked by
+// row) is described in jet.cuh.
 constexpr int R = 4;
-// Column tiles are multiples of this; the jet matrices are padded to it.
-constexpr int COL_ALIGN = 256;
+// Points are padded to a multiple of this (one 256-column tile).
+constexpr int PT_ALIGN = 64;
 
 enum JetMode : int {
   JET_BURGERS = 0,  // rows [u, d/dx, d/dt, d2/dx2]; second-order set S = {x}
@@ -41,10 +40,13 @@ struct LayerPlan {
 
 struct Plan {
   int64_t n_res = 0, n_ic = 0, n_bc = 0;
-  int64_t ncols = 0;   // 4 n_res + n_ic + n_bc
-  int64_t NC = 0;      // ncols padded to COL_ALIGN
+  int64_t ncols = 0;   // 4 (n_res + n_ic + n_bc): columns of real points
+  int64_t NP = 0;      // points padded to PT_ALIGN
+  int64_t NC = 0;      // 4 NP
   int es = 4;          // bytes per element of the compute type (2 bf16, 4 fp32/tf32)
+  bool lo = false;     // BF16: value rows also keep a low half (x - bf16(x)) in Alo
   size_t A[PINN_MAX_HIDDEN + 1] = {};   // A_l^T [w_l][NC] compute type, l = 0..L (A_0 only with FF)
+  size_t Alo[PINN_MAX_HIDDEN + 1] = {}; // BF16: low half of the value rows [w_l][NP]
   size_t Z[PINN_MAX_HIDDEN + 1] = {};   // Z_l^T [w_l][NC] compute type, l = 1..L
   size_t Zbar[2] = {};                  // ping-pong adjoints [w_max][NC] compute type
   size_t Ubar = 0;                      // output seeds [d_out][NC] fp32
@@ -93,20 +95,20 @@ struct RwfArgs {
 void launch_rwf_prep(const RwfArgs& a, cudaStream_t st);
 
 void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
-                     int64_t n_bc, int d_in, const float* B, int m, int jet_mode, void* A0, int64_t NC, int prec,
-                     cudaStream_t st);
+                     int64_t n_bc, int d_in, const float* B, int m, int jet_mode, void* A0, void* A0lo, int64_t NP,
+                     int prec, cudaStream_t st);
 
 void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                         int64_t n_bc, int d_in, const float* W, const float* b, int fout, int jet_mode, void* A1,
-                        void* Z1, int64_t NC, int prec, cudaStream_t st);
+                        void* A1lo, void* Z1, int64_t NP, int prec, cudaStream_t st);
 
 struct EpiArgs {
   const float* bias;      // fwd: bias of this layer [M]
   void* out;              // fwd: A_l^T, adj: Zbar_{l-1}^T (compute type)
   void* zout;             // fwd: Z_l^T (compute type)
+  void* alo_out;          // fwd, BF16: low half of A_l's value rows [M][NP] (else nullptr)
+  const void* alo_in;     // fwd, CUDA-core BF16 path: low half of the input's value rows [K][NP]
   const void* zin;        // adj: Z_{l-1}^T (compute type)
-  int64_t n_res4;         // 4 n_res: columns below it are jet columns
-  int64_t ncols;          // valid columns
   int jet_mode;
   // adjoint only: bias-gradient partials of the layer whose pre-activation adjoint
   // this epilogue writes ([part][M][1 + dterms]; nullptr = not fused), and for a
@@ -117,11 +119,11 @@ struct EpiArgs {
   int64_t n_res, n_ic, n_bc;
 };
 
-// D[M][N] = Aop[M][K] Bop[K][N] (+ epilogue), Aop row-major ld=K (FP32 weights),
-// Bop row-major ld=NC (activations in the compute type).
-void launch_simt_gemm_fwd(const float* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
+// D[M][4 NP] = Aop[M][K] Bop[K][4 NP] (+ epilogue), Aop row-major ld=K (FP32 weights),
+// Bop row-major (activations in the compute type).
+void launch_simt_gemm_fwd(const float* Aop, const void* Bop, int M, int K, int64_t NP, const EpiArgs& e, int prec,
                           cudaStream_t st);
-void launch_simt_gemm_adj(const float* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
+void launch_simt_gemm_adj(const float* Aop, const void* Bop, int M, int K, int64_t NP, const EpiArgs& e, int prec,
                           cudaStream_t st);
 // part[s][M][N] = sum_{k in split s} Aop[m][k] Bop[n][k]; Aop/Bop row-major with ld = NC.
 // a_fp32 / b_fp32 select float storage, else the compute type.
@@ -130,12 +132,13 @@ void launch_simt_gemm_dw(const void* Aop, bool a_fp32, const void* Bop, bool b_f
 
 struct OutArgs {
   const void* AL;        // A_L^T [w][NC] compute type
+  const void* ALlo;      // BF16: low half of A_L's value rows [w][NP] (else nullptr)
   const void* ZL;        // Z_L^T [w][NC] compute type
   const float* W;        // output weights fp32 [d_out][w]
   const float* b;        // output bias [d_out]
   const float* g_ic; const float* g_bc;   // targets [d_out][n]
   uint32_t ic_mask, bc_mask;
-  int64_t n_res, n_ic, n_bc, NC;
+  int64_t n_res, n_ic, n_bc, NP, NC;
   int w, d_out, pde, jet_mode;
   float nu;
   float k_pde, k_ic, k_bc;  // 2 lambda / N per set (adjoint seed scale)
@@ -152,12 +155,12 @@ void launch_dw_out(const void* AL, const float* Ubar, int w, int d_out, int64_t 
                    int prec, cudaStream_t st);
 int out_loss_blocks(int64_t n_points);
 
-// Bias gradient partials of a layer from its pre-activation adjoint (value
-// columns only), plus, for a first layer applied to raw coordinates, the
-// coordinate terms of dW.  part [nbpart][M][1 + d_in_terms].
-void launch_row_reduce(const void* Zbar, int M, int64_t NC, int64_t n_res, int64_t ncols, int nbpart,
-                       const float* x_res, const float* x_ic, const float* x_bc, int64_t n_ic, int64_t n_bc,
-                       int d_in_terms, int jet_mode, float* part, int prec, cudaStream_t st);
+// Bias gradient partials of a layer from its pre-activation adjoint (value rows
+// only), plus, for a first layer applied to raw coordinates, the coordinate terms
+// of dW.  part [M][nbpart][1 + d_in_terms].  `fp32_in` reads the adjoint as FP32.
+void launch_row_reduce(const void* Zbar, bool fp32_in, int M, int64_t NP, int64_t n_res, int64_t n_ic, int64_t n_bc,
+                       int nbpart, const float* x_res, const float* x_ic, const float* x_bc, int d_in_terms,
+                       int jet_mode, float* part, int prec, cudaStream_t st);
 
 struct FinalizeArgs {
   const float* params; float* grad; char* ws; int L1; int rwf;

@@ -91,29 +91,43 @@ __device__ __forceinline__ float val_adj(float z, float ab) {
   return ab * tp;
 }
 
-// Column classification of the jet matrices: group g covers columns 4g..4g+3.
-// Groups below n_res are interior points (4 jet rows); later columns are
-// initial-condition points, then boundary points (one value column each), then padding.
-struct ColPoint {
-  int set;      // 0 interior, 1 initial, 2 boundary, 3 padding
-  int64_t idx;  // point index within its set
-};
-__device__ __forceinline__ ColPoint classify_col(int64_t c, int64_t n_res, int64_t n_ic, int64_t n_bc) {
-  const int64_t b = c - 4 * n_res;
-  if (b < 0) return {0, c >> 2};
-  if (b < n_ic) return {1, b};
-  if (b < n_ic + n_bc) return {2, b - n_ic};
-  return {3, 0};
+// ---- geometry of the jet matrices ------------------------------------------------------
+// Every point (interior, initial, boundary, padding) owns four columns.  Points are
+// grouped in tiles of 64; inside a 256-column tile the columns are blocked by jet
+// row: [64 values | 64 first rows | 64 second rows | 64 fourth rows].  Column of
+// row r of point p:  256 * (p / 64) + 64 * r + p % 64.  Interior points come
+// first, then initial, then boundary points, then padding up to a multiple of 64.
+// Initial/boundary points only have a value row: their three derivative rows are
+// zero and stay exactly zero through every layer (and so do their adjoints).
+constexpr int TILE_PTS = 64;
+constexpr int TILE_COLS = 256;
+
+__host__ __device__ __forceinline__ int64_t jcol(int64_t p, int r) {
+  return ((p >> 6) << 8) + ((int64_t)r << 6) + (p & 63);
 }
 
-__device__ __forceinline__ float coord(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res,
-                                       int64_t n_ic, int64_t n_bc, ColPoint cp, int i) {
-  if (cp.set == 0) return x_res[(int64_t)i * n_res + cp.idx];
-  if (cp.set == 1) return x_ic[(int64_t)i * n_ic + cp.idx];
-  return x_bc[(int64_t)i * n_bc + cp.idx];
+enum PointSet : int { SET_RES = 0, SET_IC = 1, SET_BC = 2, SET_PAD = 3 };
+
+__device__ __forceinline__ int point_set(int64_t p, int64_t n_res, int64_t n_ic, int64_t n_bc, int64_t& idx) {
+  if (p < n_res) { idx = p; return SET_RES; }
+  if (p < n_res + n_ic) { idx = p - n_res; return SET_IC; }
+  if (p < n_res + n_ic + n_bc) { idx = p - n_res - n_ic; return SET_BC; }
+  idx = 0;
+  return SET_PAD;
 }
 
-// Derivative direction of jet row r (1..3) and whether row 3 is second order.
+// Coordinate j of point p (0 for padding).
+__device__ __forceinline__ float point_coord(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res,
+                                             int64_t n_ic, int64_t n_bc, int64_t p, int j) {
+  int64_t idx;
+  const int s = point_set(p, n_res, n_ic, n_bc, idx);
+  if (s == SET_RES) return x_res[(int64_t)j * n_res + idx];
+  if (s == SET_IC) return x_ic[(int64_t)j * n_ic + idx];
+  if (s == SET_BC) return x_bc[(int64_t)j * n_bc + idx];
+  return 0.f;
+}
+
+// Input direction of jet row r (1..3), or -1 for a second-order row.
 __device__ __forceinline__ int row_dir(int mode, int r) { return (mode == JET_MAXWELL || r < 3) ? r - 1 : -1; }
 
 // ---- element type helpers ---------------------------------------------------------
@@ -123,5 +137,36 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v
 template <typename T> __device__ __forceinline__ T from_f(float v);
 template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename T>
+__device__ __forceinline__ void store4(T* p, const float v[4]);
+template <>
+__device__ __forceinline__ void store4<float>(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16* p, const float v[4]) {
+  __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+  __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 u;
+  u.x = *reinterpret_cast<uint32_t*>(&lo);
+  u.y = *reinterpret_cast<uint32_t*>(&hi);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, float v[4]);
+template <>
+__device__ __forceinline__ void load4<float>(const float* p, float v[4]) {
+  float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void load4<__nv_bfloat16>(const __nv_bfloat16* p, float v[4]) {
+  uint2 u = *reinterpret_cast<const uint2*>(p);
+  __nv_bfloat162 lo = *reinterpret_cast<__nv_bfloat162*>(&u.x);
+  __nv_bfloat162 hi = *reinterpret_cast<__nv_bfloat162*>(&u.y);
+  float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
 
 }  // namespace pinn

@@ -46,144 +46,150 @@ void launch_rwf_prep(const RwfArgs& a, cudaStream_t st) {
   else k_rwf_prep<float><<<grid, 256, 0, st>>>(a);
 }
 
-template <typename T>
-__device__ __forceinline__ void store4(T* p, const float v[4]);
-template <>
-__device__ __forceinline__ void store4<float>(float* p, const float v[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-template <>
-__device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16* p, const float v[4]) {
-  __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
-  __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
-  uint2 u;
-  u.x = *reinterpret_cast<uint32_t*>(&lo);
-  u.y = *reinterpret_cast<uint32_t*>(&hi);
-  *reinterpret_cast<uint2*>(p) = u;
-}
-template <typename T>
-__device__ __forceinline__ void load4(const T* p, float v[4]);
-template <>
-__device__ __forceinline__ void load4<float>(const float* p, float v[4]) {
-  float4 q = *reinterpret_cast<const float4*>(p);
-  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-}
-template <>
-__device__ __forceinline__ void load4<__nv_bfloat16>(const __nv_bfloat16* p, float v[4]) {
-  uint2 u = *reinterpret_cast<const uint2*>(p);
-  __nv_bfloat162 lo = *reinterpret_cast<__nv_bfloat162*>(&u.x);
-  __nv_bfloat162 hi = *reinterpret_cast<__nv_bfloat162*>(&u.y);
-  float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+// Low half of a value stored in BF16: v - bf16(v), itself rounded to BF16.
+__device__ __forceinline__ __nv_bfloat16 bf16_lo(float v) {
+  return __float2bfloat16_rn(v - __bfloat162float(__float2bfloat16_rn(v)));
 }
 
 // ------------------------------------------------------------------------------------
 // Fourier-feature input jets (Sec. 2.7.1, Eq. 14): phi_j = sum_i x_i B_ij,
 // gamma = [cos phi, sin phi].  Row k (direction d): d cos = -sin phi B_dj,
 // d sin = cos phi B_dj; second-order row: -cos phi sum_{k in S} B_kj^2 (and -sin
-// for the sine block).  One thread per (feature j < m, column group).
+// for the sine block).  Initial/boundary points get their value row only.  One
+// thread per (feature j < m, point).
 // ------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool LO>
 __global__ void k_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
-                           int64_t n_bc, int d_in, const float* B, int m, int mode, T* A0, int64_t NC) {
+                           int64_t n_bc, int d_in, const float* B, int m, int mode, T* A0, T* A0lo, int64_t NP) {
   const int j = blockIdx.y;
-  const int64_t ngroups = NC / 4;
+  const int64_t NC = 4 * NP;
   float Bj[3] = {0.f, 0.f, 0.f};
   for (int i = 0; i < d_in; ++i) Bj[i] = B[(int64_t)i * m + j];
   const float q = (mode == JET_MAXWELL) ? 0.f : (Bj[0] * Bj[0] + (mode == JET_NS ? Bj[1] * Bj[1] : 0.f));
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c0 = 4 * g;
-    float vc[4], vs[4];
-    if (c0 < 4 * n_res) {
-      const int64_t p = g;
-      float phi = 0.f;
-      for (int i = 0; i < d_in; ++i) phi = fmaf(x_res[(int64_t)i * n_res + p], Bj[i], phi);
-      float sn, cs;
-      sincosf(phi, &sn, &cs);
-      vc[0] = cs; vs[0] = sn;
-      for (int r = 1; r < 4; ++r) {
-        const int d = row_dir(mode, r);
-        if (d >= 0) { vc[r] = -sn * Bj[d]; vs[r] = cs * Bj[d]; }
-        else { vc[r] = -cs * q; vs[r] = -sn * q; }
-      }
-    } else {
-      for (int r = 0; r < 4; ++r) {
-        const ColPoint cp = classify_col(c0 + r, n_res, n_ic, n_bc);
-        if (cp.set == 3) { vc[r] = 0.f; vs[r] = 0.f; continue; }
+  T* rc = A0 + (int64_t)j * NC;
+  T* rs = A0 + (int64_t)(m + j) * NC;
+  // four consecutive points per thread (same tile): vector stores per jet row
+  for (int64_t p0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); p0 < NP;
+       p0 += 4 * (int64_t)gridDim.x * blockDim.x) {
+    float vc[4][4], vs[4][4];   // [row][point]
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t p = p0 + k;
+      int64_t idx;
+      const int set = point_set(p, n_res, n_ic, n_bc, idx);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) { vc[r][k] = 0.f; vs[r][k] = 0.f; }
+      if (set != SET_PAD) {
         float phi = 0.f;
-        for (int i = 0; i < d_in; ++i) phi = fmaf(coord(x_res, x_ic, x_bc, n_res, n_ic, n_bc, cp, i), Bj[i], phi);
-        sincosf(phi, &vs[r], &vc[r]);
+        for (int i = 0; i < d_in; ++i) phi = fmaf(point_coord(x_res, x_ic, x_bc, n_res, n_ic, n_bc, p, i), Bj[i], phi);
+        float sn, cs;
+        sincosf(phi, &sn, &cs);
+        vc[0][k] = cs; vs[0][k] = sn;
+        if (set == SET_RES) {
+#pragma unroll
+          for (int r = 1; r < 4; ++r) {
+            const int d = row_dir(mode, r);
+            if (d >= 0) { vc[r][k] = -sn * Bj[d]; vs[r][k] = cs * Bj[d]; }
+            else { vc[r][k] = -cs * q; vs[r][k] = -sn * q; }
+          }
+        }
       }
     }
-    store4<T>(A0 + (int64_t)j * NC + c0, vc);
-    store4<T>(A0 + (int64_t)(m + j) * NC + c0, vs);
+    const int64_t c0 = jcol(p0, 0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      store4<T>(rc + c0 + 64 * r, vc[r]);
+      store4<T>(rs + c0 + 64 * r, vs[r]);
+    }
+    if (LO) {
+      float lc[4], ls[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        lc[k] = vc[0][k] - __bfloat162float(__float2bfloat16_rn(vc[0][k]));
+        ls[k] = vs[0][k] - __bfloat162float(__float2bfloat16_rn(vs[0][k]));
+      }
+      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A0lo) + (int64_t)j * NP + p0, lc);
+      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A0lo) + (int64_t)(m + j) * NP + p0, ls);
+    }
   }
 }
 
 void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
-                     int64_t n_bc, int d_in, const float* B, int m, int mode, void* A0, int64_t NC, int prec,
-                     cudaStream_t st) {
-  const int64_t ngroups = NC / 4;
-  dim3 grid((unsigned)std::min<int64_t>((ngroups + 255) / 256, 4096), m);
+                     int64_t n_bc, int d_in, const float* B, int m, int mode, void* A0, void* A0lo, int64_t NP,
+                     int prec, cudaStream_t st) {
+  dim3 grid((unsigned)std::min<int64_t>((NP / 4 + 255) / 256, 4096), m);
   if (prec == PINN_BF16)
-    k_embed_ff<__nv_bfloat16><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode,
-                                                    (__nv_bfloat16*)A0, NC);
+    k_embed_ff<__nv_bfloat16, true><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode,
+                                                          (__nv_bfloat16*)A0, (__nv_bfloat16*)A0lo, NP);
   else
-    k_embed_ff<float><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode, (float*)A0, NC);
+    k_embed_ff<float, false><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode,
+                                                   (float*)A0, nullptr, NP);
 }
 
 // ------------------------------------------------------------------------------------
 // First hidden layer on raw coordinates (no Fourier features): z = W x + b on the
-// value row, z_k = W[:, d_k] on first-derivative rows, 0 on the second-order row
-// (the input has no curvature); then the tanh jet rule.  Writes A_1 and Z_1.
+// value row, z_k = W[:, d_k] on the first-derivative rows of interior points, 0 on
+// the second-order row (the input has no curvature); then the tanh jet rule.
+// Writes A_1 (and its value-row low half) and Z_1.
 // ------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool LO>
 __global__ void k_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                               int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, T* A1,
-                              T* Z1, int64_t NC) {
+                              T* A1lo, T* Z1, int64_t NP) {
   const int f = blockIdx.y;
-  const int64_t ngroups = NC / 4;
+  const int64_t NC = 4 * NP;
   float Wf[3] = {0.f, 0.f, 0.f};
   for (int i = 0; i < d_in; ++i) Wf[i] = W[(int64_t)f * d_in + i];
   const float bf = b[f];
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c0 = 4 * g;
-    float z[4], a[4];
-    if (c0 < 4 * n_res) {
-      float v = bf;
-      for (int i = 0; i < d_in; ++i) v = fmaf(Wf[i], x_res[(int64_t)i * n_res + g], v);
-      z[0] = v;
-      for (int r = 1; r < 4; ++r) {
-        const int d = row_dir(mode, r);
-        z[r] = d >= 0 ? Wf[d] : 0.f;
+  T* ra = A1 + (int64_t)f * NC;
+  T* rz = Z1 + (int64_t)f * NC;
+  for (int64_t p0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); p0 < NP;
+       p0 += 4 * (int64_t)gridDim.x * blockDim.x) {
+    float za[4][4], aa[4][4];   // [row][point]
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t p = p0 + k;
+      int64_t idx;
+      const int set = point_set(p, n_res, n_ic, n_bc, idx);
+      float z[4] = {bf, 0.f, 0.f, 0.f}, a[4];
+      for (int i = 0; i < d_in; ++i) z[0] = fmaf(Wf[i], point_coord(x_res, x_ic, x_bc, n_res, n_ic, n_bc, p, i), z[0]);
+      if (set == SET_RES) {
+#pragma unroll
+        for (int r = 1; r < 4; ++r) {
+          const int d = row_dir(mode, r);
+          z[r] = d >= 0 ? Wf[d] : 0.f;
+        }
       }
-      jet_fwd(z, a, mode);
-    } else {
-      for (int r = 0; r < 4; ++r) {
-        const ColPoint cp = classify_col(c0 + r, n_res, n_ic, n_bc);
-        if (cp.set == 3) { z[r] = 0.f; a[r] = 0.f; continue; }
-        float v = bf;
-        for (int i = 0; i < d_in; ++i) v = fmaf(Wf[i], coord(x_res, x_ic, x_bc, n_res, n_ic, n_bc, cp, i), v);
-        z[r] = v;
-        a[r] = val_fwd(v);
-      }
+      jet_fwd<LO>(z, a, mode);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) { za[r][k] = z[r]; aa[r][k] = a[r]; }
     }
-    store4<T>(A1 + (int64_t)f * NC + c0, a);
-    store4<T>(Z1 + (int64_t)f * NC + c0, z);
+    const int64_t c0 = jcol(p0, 0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      store4<T>(ra + c0 + 64 * r, aa[r]);
+      store4<T>(rz + c0 + 64 * r, za[r]);
+    }
+    if (LO) {
+      float lo[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) lo[k] = aa[0][k] - __bfloat162float(__float2bfloat16_rn(aa[0][k]));
+      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A1lo) + (int64_t)f * NP + p0, lo);
+    }
   }
 }
 
 void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                         int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, void* A1,
-                        void* Z1, int64_t NC, int prec, cudaStream_t st) {
-  const int64_t ngroups = NC / 4;
-  dim3 grid((unsigned)std::min<int64_t>((ngroups + 255) / 256, 4096), fout);
+                        void* A1lo, void* Z1, int64_t NP, int prec, cudaStream_t st) {
+  dim3 grid((unsigned)std::min<int64_t>((NP / 4 + 255) / 256, 4096), fout);
   if (prec == PINN_BF16)
-    k_first_layer<__nv_bfloat16><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
-                                                       (__nv_bfloat16*)A1, (__nv_bfloat16*)Z1, NC);
+    k_first_layer<__nv_bfloat16, true><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout,
+                                                             mode, (__nv_bfloat16*)A1, (__nv_bfloat16*)A1lo,
+                                                             (__nv_bfloat16*)Z1, NP);
   else
-    k_first_layer<float><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
-                                               (float*)A1, (float*)Z1, NC);
+    k_first_layer<float, false><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
+                                                      (float*)A1, nullptr, (float*)Z1, NP);
 }
 
 // ------------------------------------------------------------------------------------
@@ -206,6 +212,67 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
   return s;
 }
 
+// Residual and seed for one point from its output jets U[c][r] (bias included).
+template <int D>
+__device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_t idx, float U[3][4], float Ub[3][4],
+                                               double lacc[5]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) Ub[c][r] = 0.f;
+  if (set == SET_RES) {
+    const float k = a.k_pde, nu = a.nu;
+    if (a.pde == PINN_BURGERS_1D) {
+      // rows [u, u_x, u_t, u_xx]
+      const float r = U[0][2] + U[0][0] * U[0][1] - nu * U[0][3];
+      lacc[0] += (double)r * r;
+      const float g2 = 2.f * k * r;
+      Ub[0][0] = g2 * U[0][1]; Ub[0][1] = g2 * U[0][0]; Ub[0][2] = g2; Ub[0][3] = -nu * g2;
+    } else if (a.pde == PINN_NS_STEADY_2D) {
+      // outputs u, v, p; rows [value, d/dx, d/dy, Laplacian]
+      const float u = U[0][0], v = U[1 % D][0];
+      const float r1 = u * U[0][1] + v * U[0][2] + U[2 % D][1] - nu * U[0][3];
+      const float r2 = u * U[1 % D][1] + v * U[1 % D][2] + U[2 % D][2] - nu * U[1 % D][3];
+      const float r3 = U[0][1] + U[1 % D][2];
+      lacc[0] += (double)r1 * r1; lacc[1] += (double)r2 * r2; lacc[2] += (double)r3 * r3;
+      const float g1 = 2.f * k * r1, g2 = 2.f * k * r2, g3 = 2.f * k * r3;
+      Ub[0][0] = g1 * U[0][1] + g2 * U[1 % D][1];
+      Ub[1 % D][0] = g1 * U[0][2] + g2 * U[1 % D][2];
+      Ub[0][1] = g1 * u + g3; Ub[0][2] = g1 * v; Ub[0][3] = -nu * g1;
+      Ub[1 % D][1] = g2 * u; Ub[1 % D][2] = g2 * v + g3; Ub[1 % D][3] = -nu * g2;
+      Ub[2 % D][1] = g1; Ub[2 % D][2] = g2;
+    } else {
+      // outputs Ez, Hx, Hy; rows [value, d/dx, d/dy, d/dt]
+      const float r1 = U[0][3] - (U[2 % D][1] - U[1 % D][2]);
+      const float r2 = U[1 % D][3] + U[0][2];
+      const float r3 = U[2 % D][3] - U[0][1];
+      lacc[0] += (double)r1 * r1; lacc[1] += (double)r2 * r2; lacc[2] += (double)r3 * r3;
+      const float g1 = 2.f * k * r1, g2 = 2.f * k * r2, g3 = 2.f * k * r3;
+      Ub[0][3] = g1; Ub[2 % D][1] = -g1; Ub[1 % D][2] = g1;
+      Ub[1 % D][3] = g2; Ub[0][2] = g2;
+      Ub[2 % D][3] = g3; Ub[0][1] = -g3;
+    }
+  } else if (set != SET_PAD) {
+    const bool ic = set == SET_IC;
+    const uint32_t mask = ic ? a.ic_mask : a.bc_mask;
+    const float* gt = ic ? a.g_ic : a.g_bc;
+    const int64_t n = ic ? a.n_ic : a.n_bc;
+    const float k = ic ? a.k_ic : a.k_bc;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      if (mask >> c & 1u) {
+        const float err = U[c][0] - gt[(int64_t)c * n + idx];
+        lacc[ic ? 3 : 4] += (double)err * err;
+        Ub[c][0] = 2.f * k * err;
+      }
+    }
+  }
+}
+
+// One block per 64-point tile (grid-stride).  Warp w takes points 16w..16w+15;
+// lane = 8 * pg + sl: point group pg (4 consecutive points) and feature slice sl
+// (features sl, sl+8, ...).  The 8 slices of a point group combine their partial
+// outputs with three xor-shuffles; every slice then holds the group's outputs.
 template <typename T, int D, bool FAST>
 __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   extern __shared__ float sW[];   // [d_out][w]
@@ -213,111 +280,105 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   for (int i = threadIdx.x; i < D * w; i += blockDim.x) sW[i] = a.W[i];
   __syncthreads();
   const T* AL = reinterpret_cast<const T*>(a.AL);
+  const __nv_bfloat16* ALlo = reinterpret_cast<const __nv_bfloat16*>(a.ALlo);
+  const T* ZL = reinterpret_cast<const T*>(a.ZL);
   T* Zb = reinterpret_cast<T*>(a.Zbar);
-  const int64_t ngroups = a.NC / 4;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pg = lane >> 3, sl = lane & 7;
+  const int q0 = 16 * warp + 4 * pg;               // first of this thread's 4 points in the tile
+  const int64_t NC = a.NC, ntiles = a.NP / TILE_PTS;
   double acc[5] = {0, 0, 0, 0, 0};
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c0 = 4 * g;
-    float U[3][4];
+  for (int64_t T0 = blockIdx.x; T0 < ntiles; T0 += gridDim.x) {
+    const int64_t cb = T0 * TILE_COLS + q0;        // column of row 0 of the first point
+    const int64_t p0 = T0 * TILE_PTS + q0;
+    float U[4][3][4];                              // [point][output][row]
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) U[c][r] = 0.f;
-#pragma unroll 4
-    for (int f = 0; f < w; ++f) {
-      float v[4];
-      load4<T>(AL + (int64_t)f * a.NC + c0, v);
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) U[j][c][r] = 0.f;
+#pragma unroll 2
+    for (int f = sl; f < w; f += 8) {
+      const T* row = AL + (int64_t)f * NC + cb;
+      float v[4][4];                               // [row][point]
+#pragma unroll
+      for (int r = 0; r < 4; ++r) load4<T>(row + 64 * r, v[r]);
+      if (ALlo) {
+        float lo[4];
+        load4<__nv_bfloat16>(ALlo + (int64_t)f * a.NP + p0, lo);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[0][j] += lo[j];
+      }
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         const float wc = sW[c * w + f];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) U[c][r] = fmaf(wc, v[r], U[c][r]);
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) U[j][c][r] = fmaf(wc, v[r][j], U[j][c][r]);
       }
     }
-    float Ub[3][4];
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) Ub[c][r] = 0.f;
-    const bool interior = c0 < 4 * a.n_res;
-    if (interior) {
+      for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int c = 0; c < D; ++c) U[c][0] += a.b[c];
-      const float k = a.k_pde, nu = a.nu;
-      if (a.pde == PINN_BURGERS_1D) {
-        // rows [u, u_x, u_t, u_xx]
-        const float r = U[0][2] + U[0][0] * U[0][1] - nu * U[0][3];
-        acc[0] += (double)r * r;
-        const float g2 = 2.f * k * r;
-        Ub[0][0] = g2 * U[0][1]; Ub[0][1] = g2 * U[0][0]; Ub[0][2] = g2; Ub[0][3] = -nu * g2;
-      } else if (a.pde == PINN_NS_STEADY_2D) {
-        // outputs u, v, p; rows [value, d/dx, d/dy, Laplacian]
-        const float u = U[0][0], v = U[1][0];
-        const float r1 = u * U[0][1] + v * U[0][2] + U[2][1] - nu * U[0][3];
-        const float r2 = u * U[1][1] + v * U[1][2] + U[2][2] - nu * U[1][3];
-        const float r3 = U[0][1] + U[1][2];
-        acc[0] += (double)r1 * r1; acc[1] += (double)r2 * r2; acc[2] += (double)r3 * r3;
-        const float g1 = 2.f * k * r1, g2 = 2.f * k * r2, g3 = 2.f * k * r3;
-        Ub[0][0] = g1 * U[0][1] + g2 * U[1][1];
-        Ub[1][0] = g1 * U[0][2] + g2 * U[1][2];
-        Ub[0][1] = g1 * u + g3; Ub[0][2] = g1 * v; Ub[0][3] = -nu * g1;
-        Ub[1][1] = g2 * u; Ub[1][2] = g2 * v + g3; Ub[1][3] = -nu * g2;
-        Ub[2][1] = g1; Ub[2][2] = g2;
-      } else {
-        // outputs Ez, Hx, Hy; rows [value, d/dx, d/dy, d/dt]
-        const float r1 = U[0][3] - (U[2][1] - U[1][2]);
-        const float r2 = U[1][3] + U[0][2];
-        const float r3 = U[2][3] - U[0][1];
-        acc[0] += (double)r1 * r1; acc[1] += (double)r2 * r2; acc[2] += (double)r3 * r3;
-        const float g1 = 2.f * k * r1, g2 = 2.f * k * r2, g3 = 2.f * k * r3;
-        Ub[0][3] = g1; Ub[2][1] = -g1; Ub[1][2] = g1;
-        Ub[1][3] = g2; Ub[0][2] = g2;
-        Ub[2][3] = g3; Ub[0][1] = -g3;
-      }
-    } else {
-      for (int r = 0; r < 4; ++r) {
-        const ColPoint cp = classify_col(c0 + r, a.n_res, a.n_ic, a.n_bc);
-        if (cp.set == 3) continue;
-        const bool ic = cp.set == 1;
-        const uint32_t mask = ic ? a.ic_mask : a.bc_mask;
-        const float* g = ic ? a.g_ic : a.g_bc;
-        const int64_t n = ic ? a.n_ic : a.n_bc;
-        const float k = ic ? a.k_ic : a.k_bc;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          U[c][r] += a.b[c];
-          if (mask >> c & 1u) {
-            const float e = U[c][r] - g[(int64_t)c * n + cp.idx];
-            acc[ic ? 3 : 4] += (double)e * e;
-            Ub[c][r] = 2.f * k * e;
-          }
+        for (int r = 0; r < 4; ++r) {
+          float x = U[j][c][r];
+          x += __shfl_xor_sync(0xffffffffu, x, 1);
+          x += __shfl_xor_sync(0xffffffffu, x, 2);
+          x += __shfl_xor_sync(0xffffffffu, x, 4);
+          U[j][c][r] = x;
         }
+    float Ub[4][3][4];
+    double lacc[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t idx;
+      const int set = point_set(p0 + j, a.n_res, a.n_ic, a.n_bc, idx);
+      if (set != SET_PAD) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) U[j][c][0] += a.b[c];
       }
+      point_residual<D>(a, set, idx, U[j], Ub[j], lacc);
     }
+    if (sl == 0)
+      for (int i = 0; i < 5; ++i) acc[i] += lacc[i];
     if (!a.want_grad) continue;
 #pragma unroll
-    for (int c = 0; c < D; ++c) store4<float>(a.Ubar + (int64_t)c * a.NC + c0, Ub[c]);
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (((c * 4 + r) & 7) == sl) {
+          const float o[4] = {Ub[0][c][r], Ub[1][c][r], Ub[2][c][r], Ub[3][c][r]};
+          store4<float>(a.Ubar + (int64_t)c * NC + cb + 64 * r, o);
+        }
     // abar_L = Ubar W_out (rank <= 3), then the tanh-jet adjoint with Z_L.
-    const T* ZL = reinterpret_cast<const T*>(a.ZL);
-#pragma unroll 4
-    for (int f = 0; f < w; ++f) {
-      float ab[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+    for (int f = sl; f < w; f += 8) {
+      float z[4][4], zb[4][4];                     // [row][point]
+      const T* zrow = ZL + (int64_t)f * NC + cb;
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const float wc = sW[c * w + f];
+      for (int r = 0; r < 4; ++r) load4<T>(zrow + 64 * r, z[r]);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) ab[r] = fmaf(wc, Ub[c][r], ab[r]);
+      for (int j = 0; j < 4; ++j) {
+        float ab[4] = {0.f, 0.f, 0.f, 0.f}, zz[4], o[4];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const float wc = sW[c * w + f];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) ab[r] = fmaf(wc, Ub[j][c][r], ab[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) zz[r] = z[r][j];
+        jet_adj<FAST>(zz, ab, o, a.jet_mode);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) zb[r][j] = o[r];
       }
-      float z[4], zb[4];
-      load4<T>(ZL + (int64_t)f * a.NC + c0, z);
-      if (interior) {
-        jet_adj<FAST>(z, ab, zb, a.jet_mode);
-      } else {
+      T* zbrow = Zb + (int64_t)f * NC + cb;
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-          zb[r] = (c0 + r < a.n_res * 4 + a.n_ic + a.n_bc) ? val_adj<FAST>(z[r], ab[r]) : 0.f;
-      }
-      store4<T>(Zb + (int64_t)f * a.NC + c0, zb);
+      for (int r = 0; r < 4; ++r) store4<T>(zbrow + 64 * r, zb[r]);
     }
   }
   __shared__ double sh[OUT_THREADS / 32];
@@ -327,8 +388,8 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   }
 }
 
-int out_loss_blocks(int64_t ngroups) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((ngroups + OUT_THREADS - 1) / OUT_THREADS, 1184));
+int out_loss_blocks(int64_t NP) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(NP / TILE_PTS, 4096));
 }
 
 void launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st) {
@@ -347,44 +408,56 @@ void launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st) {
 // One warp per (feature row f, column chunk), coalesced along columns; partials
 // [chunk][d_out][w] reduced in FP64 by the finalisation.
 // ------------------------------------------------------------------------------------
+constexpr int DWO_ROWS = 8;   // feature rows per warp (each Ubar load serves all of them)
+
 template <typename T, int D>
 __global__ void k_dw_out(const T* AL, const float* Ubar, int w, int64_t NC, int nchunks, float* part) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int f = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (f >= w) return;
+  const int f0 = (blockIdx.x * (blockDim.x >> 5) + warp) * DWO_ROWS;
+  if (f0 >= w) return;
   const int chunk = blockIdx.y;
   const int64_t noct = NC / 8;
   const int64_t per = (noct + nchunks - 1) / nchunks;
   const int64_t o0 = chunk * per, o1 = min(noct, o0 + per);
-  float acc[D];
+  float acc[DWO_ROWS][D];
 #pragma unroll
-  for (int c = 0; c < D; ++c) acc[c] = 0.f;
-  const T* rowp = AL + (int64_t)f * NC;
-#pragma unroll 2
+  for (int i = 0; i < DWO_ROWS; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[i][c] = 0.f;
   for (int64_t o = o0 + lane; o < o1; o += 32) {
-    float v[4], u[4];
-    load4<T>(rowp + 8 * o, v);
-    load4<T>(rowp + 8 * o + 4, u);
+    float g[D][8];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      float g[4], h[4];
-      load4<float>(Ubar + (int64_t)c * NC + 8 * o, g);
-      load4<float>(Ubar + (int64_t)c * NC + 8 * o + 4, h);
+      load4<float>(Ubar + (int64_t)c * NC + 8 * o, &g[c][0]);
+      load4<float>(Ubar + (int64_t)c * NC + 8 * o + 4, &g[c][4]);
+    }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[c] = fmaf(g[r], v[r], fmaf(h[r], u[r], acc[c]));
+    for (int i = 0; i < DWO_ROWS; ++i) {
+      if (f0 + i >= w) break;
+      float v[8];
+      load4<T>(AL + (int64_t)(f0 + i) * NC + 8 * o, v);
+      load4<T>(AL + (int64_t)(f0 + i) * NC + 8 * o + 4, v + 4);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[i][c] = fmaf(g[c][r], v[r], acc[i][c]);
     }
   }
 #pragma unroll
-  for (int c = 0; c < D; ++c) {
-    float s = acc[c];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) part[((int64_t)chunk * D + c) * w + f] = s;
+  for (int i = 0; i < DWO_ROWS; ++i) {
+    if (f0 + i >= w) break;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      float s = acc[i][c];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) part[((int64_t)chunk * D + c) * w + f0 + i] = s;
+    }
   }
 }
 
 void launch_dw_out(const void* AL, const float* Ubar, int w, int d_out, int64_t NC, int nchunks, float* part,
                    int prec, cudaStream_t st) {
-  dim3 grid((w + 7) / 8, nchunks);
+  dim3 grid((w + 8 * DWO_ROWS - 1) / (8 * DWO_ROWS), nchunks);
   if (prec == PINN_BF16) {
     if (d_out == 1) k_dw_out<__nv_bfloat16, 1><<<grid, 256, 0, st>>>((const __nv_bfloat16*)AL, Ubar, w, NC, nchunks, part);
     else k_dw_out<__nv_bfloat16, 3><<<grid, 256, 0, st>>>((const __nv_bfloat16*)AL, Ubar, w, NC, nchunks, part);
@@ -400,69 +473,57 @@ void launch_dw_out(const void* AL, const float* Ubar, int w, int d_out, int64_t 
 // coordinate part of dW: dW_ij = sum_value zbar x_j + sum_{rows k with direction j} zbar_k.
 // One warp per (row, column chunk); partials [chunk][M][1 + d_in_terms].
 // ------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------
+// Row reductions over a pre-activation adjoint Zbar^T [M][NC]: the bias gradient
+// (value rows; padding and derivative rows of initial/boundary points are zero) and,
+// for a first layer applied to raw coordinates, the coordinate part of dW:
+// dW_ij = sum_points zbar x_j + sum_{rows k with direction j} zbar_k.
+// One warp per (row, chunk of points), one lane per point; partials
+// [M][nbpart][1 + dterms] in a fixed order (deterministic).
+// ------------------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void row_group(const float v[4], int64_t c0, int64_t n_res, int64_t n_ic, int64_t n_bc,
-                                          const float* x_res, const float* x_ic, const float* x_bc, int dterms,
-                                          int mode, float acc[4]) {
-  if (c0 < 4 * n_res) {
-    const int64_t g = c0 >> 2;
-    acc[0] += v[0];
-    for (int j = 0; j < dterms; ++j) acc[1 + j] = fmaf(v[0], x_res[(int64_t)j * n_res + g], acc[1 + j]);
-    if (dterms) {
-      for (int r = 1; r < 4; ++r) {
-        const int d = row_dir(mode, r);
-        if (d >= 0) acc[1 + d] += v[r];
-      }
-    }
-  } else {
-    for (int r = 0; r < 4; ++r) {
-      const ColPoint cp = classify_col(c0 + r, n_res, n_ic, n_bc);
-      if (cp.set == 3) continue;
-      acc[0] += v[r];
-      for (int j = 0; j < dterms; ++j)
-        acc[1 + j] = fmaf(v[r], coord(x_res, x_ic, x_bc, n_res, n_ic, n_bc, cp, j), acc[1 + j]);
-    }
-  }
-}
-
-template <typename T>
-__global__ void k_row_reduce(const T* Zb, int M, int64_t NC, int64_t n_res, int64_t ncols, int nbpart,
-                             const float* x_res, const float* x_ic, const float* x_bc, int64_t n_ic, int64_t n_bc,
-                             int dterms, int mode, float* part) {
+__global__ void k_row_reduce(const T* Zb, int M, int64_t NP, int64_t n_res, int64_t n_ic, int64_t n_bc, int nbpart,
+                             const float* x_res, const float* x_ic, const float* x_bc, int dterms, int mode,
+                             float* part) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * (blockDim.x >> 5) + warp;
   if (row >= M) return;
   const int chunk = blockIdx.y;
-  const int64_t noct = NC / 8;                          // 8-column units
-  const int64_t per = (noct + nbpart - 1) / nbpart;
-  const int64_t o0 = chunk * per, o1 = min(noct, o0 + per);
+  const int64_t NC = 4 * NP;
+  const int64_t per = (NP + nbpart - 1) / nbpart;
+  const int64_t p0 = chunk * per, p1 = min(NP, p0 + per);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   const T* rowp = Zb + (int64_t)row * NC;
 #pragma unroll 4
-  for (int64_t o = o0 + lane; o < o1; o += 32) {
-    float v[4], u[4];
-    load4<T>(rowp + 8 * o, v);
-    load4<T>(rowp + 8 * o + 4, u);
-    row_group<T>(v, 8 * o, n_res, n_ic, n_bc, x_res, x_ic, x_bc, dterms, mode, acc);
-    row_group<T>(u, 8 * o + 4, n_res, n_ic, n_bc, x_res, x_ic, x_bc, dterms, mode, acc);
+  for (int64_t p = p0 + lane; p < p1; p += 32) {
+    const float v0 = to_f<T>(rowp[jcol(p, 0)]);
+    acc[0] += v0;
+    if (dterms) {
+      for (int j = 0; j < dterms; ++j)
+        acc[1 + j] = fmaf(v0, point_coord(x_res, x_ic, x_bc, n_res, n_ic, n_bc, p, j), acc[1 + j]);
+      for (int r = 1; r < 4; ++r) {
+        const int d = row_dir(mode, r);
+        if (d >= 0) acc[1 + d] += to_f<T>(rowp[jcol(p, r)]);
+      }
+    }
   }
   for (int j = 0; j <= dterms; ++j) {
     float s = acc[j];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) part[((int64_t)chunk * M + row) * (1 + dterms) + j] = s;
+    if (lane == 0) part[((int64_t)row * nbpart + chunk) * (1 + dterms) + j] = s;
   }
 }
 
-void launch_row_reduce(const void* Zbar, int M, int64_t NC, int64_t n_res, int64_t ncols, int nbpart,
-                       const float* x_res, const float* x_ic, const float* x_bc, int64_t n_ic, int64_t n_bc,
-                       int dterms, int mode, float* part, int prec, cudaStream_t st) {
+void launch_row_reduce(const void* Zbar, bool fp32_in, int M, int64_t NP, int64_t n_res, int64_t n_ic, int64_t n_bc,
+                       int nbpart, const float* x_res, const float* x_ic, const float* x_bc, int dterms, int mode,
+                       float* part, int prec, cudaStream_t st) {
   dim3 grid((M + 7) / 8, nbpart);
-  if (prec == PINN_BF16)
-    k_row_reduce<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16*)Zbar, M, NC, n_res, ncols, nbpart, x_res,
-                                                      x_ic, x_bc, n_ic, n_bc, dterms, mode, part);
+  if (prec == PINN_BF16 && !fp32_in)
+    k_row_reduce<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16*)Zbar, M, NP, n_res, n_ic, n_bc, nbpart,
+                                                      x_res, x_ic, x_bc, dterms, mode, part);
   else
-    k_row_reduce<float><<<grid, 256, 0, st>>>((const float*)Zbar, M, NC, n_res, ncols, nbpart, x_res, x_ic, x_bc,
-                                              n_ic, n_bc, dterms, mode, part);
+    k_row_reduce<float><<<grid, 256, 0, st>>>((const float*)Zbar, M, NP, n_res, n_ic, n_bc, nbpart, x_res, x_ic,
+                                              x_bc, dterms, mode, part);
 }
 
 // ------------------------------------------------------------------------------------
@@ -470,6 +531,20 @@ void launch_row_reduce(const void* Zbar, int M, int64_t NC, int64_t n_res, int64
 // (Eq. 15): dV = exp(s) dW, ds_i = sum_j dW_ij W_ij, plus db.  One block per
 // (output row, layer).
 // ------------------------------------------------------------------------------------
+// Compensated FP32 accumulation (Knuth's TwoSum): s + c tracks the exact sum of
+// the added values to about 2^-48 relative, using the FP32 pipe; it is turned into
+// FP64 once per thread, so the FP64 work of the final reductions stays small.
+struct Acc2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // Deterministic block sum of N doubles per thread (fixed assignment and order).
 template <int N>
 __device__ __forceinline__ void block_sum_n(double v[N], double (*sh)[N]) {
@@ -497,26 +572,59 @@ __global__ void k_finalize_grad(FinalizeArgs a) {
   __shared__ double sh[32][5];
   // v[0]: sum_j dW_ij W_ij (RWF scale gradient), v[1]: bias, v[2..4]: raw-coordinate dW
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int p = threadIdx.x; p < nbp; p += blockDim.x) {
-    const float* q = dbp + ((int64_t)p * fout + i) * dbs;
-    v[1] += (double)q[0];
-    if (raw)
-      for (int j = 0; j < fin && j < 3; ++j) v[2 + j] += (double)q[1 + j];
+  {
+    Acc2 ab[4];
+    for (int p = threadIdx.x; p < nbp; p += blockDim.x) {
+      const float* q = dbp + ((int64_t)i * nbp + p) * dbs;
+      ab[0].add(q[0]);
+      if (raw)
+        for (int j = 0; j < fin && j < 3; ++j) ab[1 + j].add(q[1 + j]);
+    }
+    v[1] = ab[0].value();
+    for (int j = 0; j < 3; ++j) v[2 + j] = ab[1 + j].value();
   }
   if (!raw) {
     const float* part = reinterpret_cast<const float*>(a.ws + a.dwpart[l]);
     const int ns = a.nsplit[l];
     const int64_t sstride = (int64_t)fout * fin;
-    if ((fin & 3) == 0) {
+    if ((fin & 3) == 0 && fin / 4 <= (int)blockDim.x) {
+      // G thread groups each sum every G-th split of the same float4 column; the
+      // groups are then combined in a fixed order (deterministic).
+      __shared__ double shd[128][4];
+      const int ncol4 = fin / 4;
+      const int G = blockDim.x / ncol4;
+      const int q = threadIdx.x % ncol4, g = threadIdx.x / ncol4;
+      double d[4] = {0.0, 0.0, 0.0, 0.0};
+      if (g < G) {
+        const float* base = part + (int64_t)i * fin + 4 * q;
+        Acc2 a0, a1, a2, a3;
+#pragma unroll 4
+        for (int s = g; s < ns; s += G) {
+          const float4 x = *reinterpret_cast<const float4*>(base + s * sstride);
+          a0.add(x.x); a1.add(x.y); a2.add(x.z); a3.add(x.w);
+        }
+        d[0] = a0.value(); d[1] = a1.value(); d[2] = a2.value(); d[3] = a3.value();
+      }
+      for (int k = 0; k < 4; ++k) shd[threadIdx.x][k] = d[k];
+      __syncthreads();
+      if (g == 0) {
+        for (int gg = 1; gg < G; ++gg)
+          for (int k = 0; k < 4; ++k) d[k] += shd[gg * ncol4 + q][k];
+        for (int k = 0; k < 4; ++k) {
+          a.grad[a.offV[l] + (int64_t)i * fin + 4 * q + k] = (float)(d[k] * es);
+          v[0] += d[k] * (double)W[4 * q + k];
+        }
+      }
+    } else if ((fin & 3) == 0) {
       for (int j4 = threadIdx.x * 4; j4 < fin; j4 += blockDim.x * 4) {
-        double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+        Acc2 a0, a1, a2, a3;
         const float* q = part + (int64_t)i * fin + j4;
 #pragma unroll 4
         for (int s = 0; s < ns; ++s) {
           const float4 x = *reinterpret_cast<const float4*>(q + s * sstride);
-          d0 += (double)x.x; d1 += (double)x.y; d2 += (double)x.z; d3 += (double)x.w;
+          a0.add(x.x); a1.add(x.y); a2.add(x.z); a3.add(x.w);
         }
-        const double dd[4] = {d0, d1, d2, d3};
+        const double dd[4] = {a0.value(), a1.value(), a2.value(), a3.value()};
         for (int k = 0; k < 4; ++k) {
           a.grad[a.offV[l] + (int64_t)i * fin + j4 + k] = (float)(dd[k] * es);
           v[0] += dd[k] * (double)W[j4 + k];
@@ -524,8 +632,9 @@ __global__ void k_finalize_grad(FinalizeArgs a) {
       }
     } else {
       for (int j = threadIdx.x; j < fin; j += blockDim.x) {
-        double dW = 0.0;
-        for (int s = 0; s < ns; ++s) dW += (double)part[s * sstride + (int64_t)i * fin + j];
+        Acc2 acc;
+        for (int s = 0; s < ns; ++s) acc.add(part[s * sstride + (int64_t)i * fin + j]);
+        const double dW = acc.value();
         a.grad[a.offV[l] + (int64_t)i * fin + j] = (float)(dW * es);
         v[0] += dW * (double)W[j];
       }

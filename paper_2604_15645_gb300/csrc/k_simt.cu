@@ -9,7 +9,7 @@ namespace pinn {
 
 namespace {
 
-constexpr int BM = 64, BN = 128, BK = 16, THREADS = 256;
+constexpr int BM = 64, BN = TILE_COLS, BK = 16, THREADS = 256;
 
 template <typename T>
 __device__ __forceinline__ void load_vec8(const T* p, float v[8]);
@@ -28,29 +28,30 @@ __device__ __forceinline__ void load_vec8<__nv_bfloat16>(const __nv_bfloat16* p,
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void st4(T* p, const float v[4]) {
-  for (int i = 0; i < 4; ++i) p[i] = from_f<T>(v[i]);
-}
-template <>
-__device__ __forceinline__ void st4<float>(float* p, const float v[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
 
-// EPI 0: forward (bias on value columns, tanh jet, writes A and Z)
+// One block per (64 features, one 256-column tile = 64 points).  Thread (ty, tx)
+// owns features 4ty..4ty+3 and points 4tx..4tx+3 of the tile, i.e. the columns
+// 64 r + 4 tx + j of all four jet rows r, so the jet rule is thread-local.
+// EPI 0: forward (bias on value rows, tanh jet, writes A, Z and the BF16 low half)
 // EPI 1: adjoint (reads Z_{l-1}, tanh-jet adjoint, writes Zbar_{l-1})
 template <typename T, int EPI>
-__global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__ Aop, const T* __restrict__ Bop, int M,
-                                                       int K, int64_t NC, EpiArgs e) {
+__global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__ Aop, const T* __restrict__ Bop,
+                                                       const __nv_bfloat16* __restrict__ Blo, int M, int K,
+                                                       int64_t NP, EpiArgs e) {
+  constexpr bool FAST = sizeof(T) == 2;
   __shared__ float As[BK][BM + 4];
   __shared__ float Bs[BK][BN + 4];
   const int t = threadIdx.x;
   const int ty = t >> 4, tx = t & 15;
   const int m0 = blockIdx.y * BM;
-  const int64_t n0 = (int64_t)blockIdx.x * BN;
-  float acc[4][8];
+  const int64_t tile = blockIdx.x;
+  const int64_t NC = 4 * NP;
+  const int64_t n0 = tile * BN;
+  float acc[4][16];
+#pragma unroll
   for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[i][j] = 0.f;
 
   for (int k0 = 0; k0 < K; k0 += BK) {
     {  // A tile: 64 rows x 16 k, 4 per thread
@@ -60,26 +61,38 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
         As[kk + q][i] = (m < M && k < K) ? Aop[(int64_t)m * K + k] : 0.f;
       }
     }
-    {  // B tile: 16 k x 128 columns, 8 per thread
-      const int kk = t >> 4, j = (t & 15) * 8;
-      float v[8];
-      if (k0 + kk < K) load_vec8<T>(Bop + (int64_t)(k0 + kk) * NC + n0 + j, v);
-      else
-        for (int q = 0; q < 8; ++q) v[q] = 0.f;
-      for (int q = 0; q < 8; ++q) Bs[kk][j + q] = v[q];
+    {  // B tile: 16 k x 256 columns, 16 per thread (value columns add the low half)
+      const int kk = t >> 4, c = (t & 15) * 16;
+      float v[16];
+      if (k0 + kk < K) {
+        load_vec8<T>(Bop + (int64_t)(k0 + kk) * NC + n0 + c, v);
+        load_vec8<T>(Bop + (int64_t)(k0 + kk) * NC + n0 + c + 8, v + 8);
+        if (Blo && c < TILE_PTS) {
+          float lo[16];
+          load_vec8<__nv_bfloat16>(Blo + (int64_t)(k0 + kk) * NP + tile * TILE_PTS + c, lo);
+          load_vec8<__nv_bfloat16>(Blo + (int64_t)(k0 + kk) * NP + tile * TILE_PTS + c + 8, lo + 8);
+          for (int q = 0; q < 16; ++q) v[q] += lo[q];
+        }
+      } else {
+        for (int q = 0; q < 16; ++q) v[q] = 0.f;
+      }
+      for (int q = 0; q < 16; ++q) Bs[kk][c + q] = v[q];
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
       const float a[4] = {a4.x, a4.y, a4.z, a4.w};
-      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      float b[16];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][64 * r + 4 * tx]);
+        b[4 * r] = b4.x; b[4 * r + 1] = b4.y; b[4 * r + 2] = b4.z; b[4 * r + 3] = b4.w;
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 16; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
@@ -88,34 +101,35 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
   for (int i = 0; i < 4; ++i) {
     const int f = m0 + ty * 4 + i;
     if (f >= M) continue;
+    float o[4][4], zz[4][4];   // [row][point]
+    if (EPI == 1) {
+      const T* zr = reinterpret_cast<const T*>(e.zin) + (int64_t)f * NC + n0 + 4 * tx;
+      for (int r = 0; r < 4; ++r) load4<T>(zr + 64 * r, zz[r]);
+    }
     const float bias = (EPI == 0) ? e.bias[f] : 0.f;
-    for (int q = 0; q < 2; ++q) {
-      const int64_t c = n0 + tx * 8 + 4 * q;
-      const float* ac = &acc[i][4 * q];
-      float o[4];
+    for (int j = 0; j < 4; ++j) {
+      float z[4], a[4], ab[4];
+      for (int r = 0; r < 4; ++r) {
+        if (EPI == 0) z[r] = acc[i][4 * r + j] + (r == 0 ? bias : 0.f);
+        else { z[r] = zz[r][j]; ab[r] = acc[i][4 * r + j]; }
+      }
       if (EPI == 0) {
-        float z[4] = {ac[0], ac[1], ac[2], ac[3]};
-        if (c < e.n_res4) {
-          z[0] += bias;
-          jet_fwd(z, o, e.jet_mode);
-        } else {
-          for (int r = 0; r < 4; ++r) {
-            if (c + r < e.ncols) { z[r] += bias; o[r] = val_fwd(z[r]); }
-            else { z[r] = 0.f; o[r] = 0.f; }
-          }
-        }
-        st4<T>(reinterpret_cast<T*>(e.zout) + (int64_t)f * NC + c, z);
-        st4<T>(out + (int64_t)f * NC + c, o);
+        jet_fwd<FAST>(z, a, e.jet_mode);
+        for (int r = 0; r < 4; ++r) { o[r][j] = a[r]; zz[r][j] = z[r]; }
       } else {
-        float z[4];
-        const T* zp = reinterpret_cast<const T*>(e.zin) + (int64_t)f * NC + c;
-        for (int r = 0; r < 4; ++r) z[r] = to_f<T>(zp[r]);
-        if (c < e.n_res4) {
-          jet_adj(z, ac, o, e.jet_mode);
-        } else {
-          for (int r = 0; r < 4; ++r) o[r] = (c + r < e.ncols) ? val_adj(z[r], ac[r]) : 0.f;
-        }
-        st4<T>(out + (int64_t)f * NC + c, o);
+        jet_adj<FAST>(z, ab, a, e.jet_mode);
+        for (int r = 0; r < 4; ++r) o[r][j] = a[r];
+      }
+    }
+    T* orow = out + (int64_t)f * NC + n0 + 4 * tx;
+    for (int r = 0; r < 4; ++r) store4<T>(orow + 64 * r, o[r]);
+    if (EPI == 0) {
+      T* zrow = reinterpret_cast<T*>(e.zout) + (int64_t)f * NC + n0 + 4 * tx;
+      for (int r = 0; r < 4; ++r) store4<T>(zrow + 64 * r, zz[r]);
+      if (e.alo_out) {
+        __nv_bfloat16* lo = reinterpret_cast<__nv_bfloat16*>(e.alo_out) + (int64_t)f * NP + tile * TILE_PTS + 4 * tx;
+        for (int j = 0; j < 4; ++j)
+          lo[j] = __float2bfloat16_rn(o[0][j] - __bfloat162float(__float2bfloat16_rn(o[0][j])));
       }
     }
   }
@@ -178,22 +192,23 @@ __global__ void __launch_bounds__(THREADS) k_simt_dw(const TA* __restrict__ Aop,
 
 }  // namespace
 
-void launch_simt_gemm_fwd(const float* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
+void launch_simt_gemm_fwd(const float* Aop, const void* Bop, int M, int K, int64_t NP, const EpiArgs& e, int prec,
                           cudaStream_t st) {
-  dim3 grid((unsigned)(NC / BN), (M + BM - 1) / BM);
+  dim3 grid((unsigned)(NP / TILE_PTS), (M + BM - 1) / BM);
   if (prec == PINN_BF16)
-    k_simt_gemm<__nv_bfloat16, 0><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, M, K, NC, e);
+    k_simt_gemm<__nv_bfloat16, 0><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop,
+                                                            (const __nv_bfloat16*)e.alo_in, M, K, NP, e);
   else
-    k_simt_gemm<float, 0><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, M, K, NC, e);
+    k_simt_gemm<float, 0><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
 }
 
-void launch_simt_gemm_adj(const float* Aop, const void* Bop, int M, int K, int64_t NC, const EpiArgs& e, int prec,
+void launch_simt_gemm_adj(const float* Aop, const void* Bop, int M, int K, int64_t NP, const EpiArgs& e, int prec,
                           cudaStream_t st) {
-  dim3 grid((unsigned)(NC / BN), (M + BM - 1) / BM);
+  dim3 grid((unsigned)(NP / TILE_PTS), (M + BM - 1) / BM);
   if (prec == PINN_BF16)
-    k_simt_gemm<__nv_bfloat16, 1><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, M, K, NC, e);
+    k_simt_gemm<__nv_bfloat16, 1><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, nullptr, M, K, NP, e);
   else
-    k_simt_gemm<float, 1><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, M, K, NC, e);
+    k_simt_gemm<float, 1><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
 }
 
 void launch_simt_gemm_dw(const void* Aop, bool a_fp32, const void* Bop, bool b_fp32, int M, int N, int64_t NC,

@@ -13,11 +13,11 @@
 // 64 whole points and applies the tanh jet rule (or its adjoint) without any
 // cross-thread exchange.
 //
-// Warp roles per CTA (576 threads, one CTA per SM, persistent over tiles):
-//   warp 0      TMA producer (one lane)
-//   warp 1      TMEM allocator + MMA issuer (one lane)
-//   warps 2-17  epilogue; warp w reads TMEM lanes 32*(w%4) .. +31, columns
-//               64*((w-2)/4) .. +63 of the 256-column accumulator
+// Warp roles per CTA (320 threads, one CTA per SM, persistent over tiles):
+//   warp 0     TMA producer (one lane)
+//   warp 1     TMEM allocator + MMA issuer (one lane)
+//   warps 2-9  epilogue; warp w reads TMEM lanes 32*(w%4) .. +31 and handles the
+//              points 32*((w-2)/4) .. +31 of the tile, 16 at a time
 // Two accumulator buffers of 256 columns let the epilogue of one tile overlap the
 // MMAs of the next.  Every mbarrier wait is bounded (global timer); on expiry the
 // CTA latches PINN_ERR_TIMEOUT in the status word, stops issuing work, waits for
@@ -37,7 +37,7 @@ namespace {
 
 constexpr int BM = 128;          // accumulator rows (TMEM lanes)
 constexpr int BN = 256;          // accumulator columns per buffer
-constexpr int EPI_WARPS = 16;    // four warps per TMEM lane quadrant, each on a quarter of the columns
+constexpr int EPI_WARPS = 8;     // two warps per TMEM lane quadrant, each on 32 of a tile's 64 points
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
 
@@ -134,16 +134,45 @@ __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, float v[16]) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-// Bulk tensor store shared -> global (asynchronous proxy) and its group bookkeeping.
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
-               "r"(smem_u32(src)), "r"(x), "r"(y)
+// 32-byte (256-bit) global accesses: one full L2 sector per thread.
+__device__ __forceinline__ void st_global_256(void* p, const uint32_t w[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+               "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
                : "memory");
 }
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void ld_global_256(const void* p, uint32_t w[8]) {
+  asm volatile("ld.global.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+               : "l"(p));
+}
+// 16 consecutive elements of a row: BF16 as one 32-byte access, FP32 as two.
+__device__ __forceinline__ void st16(__nv_bfloat16* p, const float v[16]) {
+  uint32_t w[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    w[i] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  st_global_256(p, w);
+}
+__device__ __forceinline__ void st16(float* p, const float v[16]) {
+  st_global_256(p, reinterpret_cast<const uint32_t*>(v));
+  st_global_256(p + 8, reinterpret_cast<const uint32_t*>(v + 8));
+}
+__device__ __forceinline__ void ld16(const __nv_bfloat16* p, float v[16]) {
+  uint32_t w[8];
+  ld_global_256(p, w);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+__device__ __forceinline__ void ld16(const float* p, float v[16]) {
+  ld_global_256(p, reinterpret_cast<uint32_t*>(v));
+  ld_global_256(p + 8, reinterpret_cast<uint32_t*>(v + 8));
+}
 
 // Shared-memory matrix descriptor (tcgen05), 128-byte swizzle, version 1.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -156,9 +185,9 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 // Instruction descriptor: FP32 accumulate, A/B format (1 = BF16, 2 = TF32),
-// A K-major, B K-major (b_mn = 0) or MN-major (b_mn = 1), N = BN, M = BM.
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t b_mn) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | (b_mn << 16) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// A K-major, B K-major (b_mn = 0) or MN-major (b_mn = 1), N columns, M = BM.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t b_mn, uint32_t n = BN) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (b_mn << 16) | ((n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 struct TcParams {
@@ -180,18 +209,17 @@ struct Cfg {
   static constexpr int UK = TF32 ? 8 : 16;        // K per MMA instruction
   static constexpr int A_BYTES = BM * 128;        // 16 KB
   static constexpr int B_BYTES = BN * 128;        // 32 KB
-  static constexpr int STAGE = A_BYTES * (SPLIT ? 2 : 1) + B_BYTES;
-  // Epilogues that write jet matrices stage each 32-row x 16-column chunk in shared
-  // memory and store it with a bulk tensor copy (double-buffered per warp).
-  static constexpr bool STAGED = (MODE == TC_FWD || MODE == TC_ADJ);
-  static constexpr int STG_BYTES = 32 * 16 * ES;                        // one chunk of one array
-  static constexpr int STAGING = STAGED ? EPI_WARPS * 2 * 2 * STG_BYTES : 0;
-  static constexpr int STAGES = STAGED ? (SPLIT ? 2 : 3) : (SPLIT ? 3 : 4);
+  // Forward only: low half of the input's value rows, one 64-column MN-major box.
+  static constexpr bool VLO = (MODE == TC_FWD);
+  static constexpr int BLO_BYTES = VLO ? TILE_PTS * 128 : 0;   // 8 KB
+  static constexpr int STAGE = A_BYTES * (SPLIT ? 2 : 1) + B_BYTES + BLO_BYTES;
+  static constexpr int STAGES = (MODE == TC_FWD || SPLIT) ? 3 : 4;
+  static_assert(STAGES * STAGE + 1024 + 256 <= 227 * 1024, "shared memory budget");
   static constexpr bool B_MN = (MODE != TC_DW);
   static constexpr int BOXN = 128 / ES;           // MN-major box width (columns)
   static constexpr int NBOX = BN / BOXN;
-  static constexpr int BOX_BYTES = BOXN * 0 + BKE * 128;   // one MN-major box: BKE rows of 128 bytes
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE + STAGING + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int BOX_BYTES = BKE * 128;     // one MN-major box: BKE rows of 128 bytes
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
 };
 
 template <typename T>
@@ -272,14 +300,13 @@ __device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, fl
 template <bool TF32, int MODE, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
-              const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapO1,
-              const __grid_constant__ CUtensorMap mapO2, const TcParams p) {
+              const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
+              const TcParams p) {
   using C = Cfg<TF32, MODE, SPLIT>;
   using T = typename std::conditional<TF32, float, __nv_bfloat16>::type;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* staging = smem + C::STAGES * C::STAGE;
-  uint64_t* full = reinterpret_cast<uint64_t*>(staging + C::STAGING);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
   uint64_t* empty = full + C::STAGES;
   uint64_t* acc_full = empty + C::STAGES;
   uint64_t* acc_empty = acc_full + 2;
@@ -348,6 +375,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int j = 0; j < C::NBOX; ++j)
               tma_load_2d(sb + j * C::BOX_BYTES, &mapB, &full[stage], nb * BN + j * C::BOXN, kx);
+            if (C::VLO) tma_load_2d(sb + C::B_BYTES, &mapBlo, &full[stage], nb * TILE_PTS, kx);
           } else {
             tma_load_2d(sb, &mapB, &full[stage], kx, nb * BN);
           }
@@ -384,6 +412,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                                         : make_desc(sb + kk * 32, 16, 1024);
             tc_mma<TF32>(d, ad, bd, idesc, (kb > k0 || kk > 0) ? 1u : 0u);
             if (SPLIT) tc_mma<TF32>(d, make_desc(sa2 + kk * 32, 16, 1024), bd, idesc, 1u);
+            if (C::VLO) {
+              // value rows' low half: D[:, 0:64] += W_hi . Alo (64 columns)
+              constexpr uint32_t idesc64 = make_idesc(TF32 ? 2u : 1u, 1u, TILE_PTS);
+              tc_mma<TF32>(d, ad, make_desc(sb + C::B_BYTES + kk * C::UK * 128, C::BOX_BYTES, 1024), idesc64, 1u);
+            }
           }
           tc_commit(&empty[stage]);
           if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
@@ -394,14 +427,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ---------------------------------------------------------------- epilogue
+    // Warp part pt handles points 16 pt .. 16 pt + 15 of the tile: the four 16-column
+    // chunks at columns 16 pt + 64 r (jet row r), so every thread holds whole points.
     constexpr bool FAST = !TF32;
-    constexpr int PARTS = EPI_WARPS / 4;       // column parts per tile
-    constexpr int CPP = BN / 16 / PARTS;       // 16-column chunks per part
-    const int quad = warp & 3;                 // TMEM lane quadrant this warp may read
-    const int part = (warp - 2) >> 2;          // which quarter of the tile's columns
+    constexpr int PARTS = EPI_WARPS / 4;                 // warps per lane quadrant
+    constexpr int GROUPS = TILE_PTS / (16 * PARTS);      // 16-point groups per warp and tile
+    static_assert(PARTS * GROUPS * 16 == TILE_PTS, "epilogue warps cover a 64-point tile");
+    const int quad = warp & 3;
+    const int part = (warp - 2) >> 2;
     const int row = quad * 32 + lane;
-    T* stg = reinterpret_cast<T*>(staging + (warp - 2) * (2 * 2 * C::STG_BYTES));   // [buf][array][32][16]
-    uint32_t nstore = 0;
     int local = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
       int mb, nb, k0, k1;
@@ -410,133 +444,124 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!mbar_wait(&acc_full[buf], (local >> 1) & 1, abort_flag, p.status)) break;
       tc_fence_after();
       const int m = mb * BM + row;
-      const int row0 = mb * BM + quad * 32;    // first row of this warp's 32-row slab
       const bool mvalid = m < p.M;
-      const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN;
-      const float bias = (MODE == TC_FWD && mvalid) ? p.e.bias[m] : 0.f;
-      float dbacc[4] = {0.f, 0.f, 0.f, 0.f};
-      float v[2][16];
-      Raw16<T> zr[2];
-      const T* zrow = (MODE == TC_ADJ) ? reinterpret_cast<const T*>(p.e.zin) + (int64_t)m * p.NC : nullptr;
-      if (MODE == TC_ADJ && mvalid) load_raw16<T>(zrow + (int64_t)nb * BN + part * CPP * 16, zr[0]);
-      tmem_ld16_issue(taddr + part * CPP * 16, v[0]);
-      tmem_wait_ld();
+      float db[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+      for (int grp = 0; grp < GROUPS; ++grp) {
+      const int pt = part * GROUPS + grp;                // 16-point group index within the tile
+      const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN + 16 * pt;
+      float v[4][16];
+      // adjoint: Z of the layer below, kept as raw 32-byte rows (BF16: 8 registers a row)
+      uint32_t zw[4][8 * (sizeof(T) / 2)];
+      if (MODE == TC_ADJ && mvalid) {
+        const T* zr = reinterpret_cast<const T*>(p.e.zin) + (int64_t)m * p.NC + (int64_t)nb * BN + 16 * pt;
 #pragma unroll
-      for (int cc = 0; cc < CPP; ++cc) {
-        const int c = part * CPP + cc;
-        const int64_t col0 = (int64_t)nb * BN + c * 16;
-        float* cur = v[cc & 1];
-        float z[16];
-        if (MODE == TC_ADJ) unpack16(zr[cc & 1], z);
-        if (cc + 1 < CPP) {                    // prefetch the next chunk
-          if (MODE == TC_ADJ && mvalid) load_raw16<T>(zrow + col0 + 16, zr[(cc + 1) & 1]);
-          tmem_ld16_issue(taddr + (c + 1) * 16, v[(cc + 1) & 1]);
+        for (int r = 0; r < 4; ++r) {
+          ld_global_256(zr + 64 * r, zw[r]);
+          if (sizeof(T) == 4) ld_global_256(zr + 64 * r + 8, zw[r] + 8 * (sizeof(T) / 4));
         }
-        if (C::STAGED) {
-          float o[16];
-          if (MODE == TC_FWD) {
+      }
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-              const int64_t col = col0 + 4 * g;
-              float* zz = &cur[4 * g];
-              if (col < p.e.n_res4) {
-                zz[0] += bias;
-                jet_fwd<FAST>(zz, &o[4 * g], p.e.jet_mode);
+      for (int r = 0; r < 4; ++r) tmem_ld16_issue(taddr + 64 * r, v[r]);
+      tmem_wait_ld();
+      if (mvalid) {
+        const int64_t cbase = (int64_t)m * p.NC + (int64_t)nb * BN + 16 * pt;
+        if (MODE == TC_FWD) {
+          const float bias = p.e.bias[m];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[0][i] += bias;
+          T* zo = reinterpret_cast<T*>(p.e.zout) + cbase;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) st16(zo + 64 * r, v[r]);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            float z[4] = {v[0][i], v[1][i], v[2][i], v[3][i]}, a[4];
+            jet_fwd<FAST>(z, a, p.e.jet_mode);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) v[r][i] = a[r];
+          }
+          T* ao = reinterpret_cast<T*>(p.e.out) + cbase;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) st16(ao + 64 * r, v[r]);
+          if (!TF32 && p.e.alo_out) {
+            float lo[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) lo[i] = v[0][i] - __bfloat162float(__float2bfloat16_rn(v[0][i]));
+            st16(reinterpret_cast<__nv_bfloat16*>(p.e.alo_out) + (int64_t)m * (p.NC / 4) + (int64_t)nb * TILE_PTS +
+                     16 * pt,
+                 lo);
+          }
+        } else if (MODE == TC_ADJ) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            float z[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              if (sizeof(T) == 2) {
+                const uint32_t w = zw[r][i >> 1];
+                z[r] = __uint_as_float((i & 1) ? (w & 0xFFFF0000u) : (w << 16));
               } else {
+                z[r] = __uint_as_float(zw[r][i]);
+              }
+            }
+            float ab[4] = {v[0][i], v[1][i], v[2][i], v[3][i]}, zb[4];
+            jet_adj<FAST>(z, ab, zb, p.e.jet_mode);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                  if (col + r < p.e.ncols) { zz[r] += bias; o[4 * g + r] = val_fwd<FAST>(zz[r]); }
-                  else { zz[r] = 0.f; o[4 * g + r] = 0.f; }
+            for (int r = 0; r < 4; ++r) v[r][i] = zb[r];
+          }
+          T* zbo = reinterpret_cast<T*>(p.e.out) + cbase;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) st16(zbo + 64 * r, v[r]);
+          if (p.e.dbpart) {
+            // bias gradient of the layer below (value rows) and, for a first layer on
+            // raw coordinates, the coordinate terms of its weight gradient
+#pragma unroll
+            for (int i = 0; i < 16; ++i) db[0] += v[0][i];
+            if (p.e.dterms) {
+              const int64_t p0 = (int64_t)nb * TILE_PTS + 16 * pt;
+              const int nd = (p.e.jet_mode == JET_MAXWELL) ? 3 : 2;   // rows 1..nd are first derivatives
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int64_t pp = p0 + i;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                  if (j >= p.e.dterms) break;
+                  float x = point_coord(p.e.x_res, p.e.x_ic, p.e.x_bc, p.e.n_res, p.e.n_ic, p.e.n_bc, pp, j);
+                  db[1 + j] = fmaf(v[0][i], x, db[1 + j]);
+                  if (j < nd) db[1 + j] += v[1 + j][i];
                 }
               }
             }
-          } else {
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-              const int64_t col = col0 + 4 * g;
-              if (col < p.e.n_res4) {
-                jet_adj<FAST>(&z[4 * g], &cur[4 * g], &o[4 * g], p.e.jet_mode);
-              } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-                  o[4 * g + r] = (col + r < p.e.ncols) ? val_adj<FAST>(z[4 * g + r], cur[4 * g + r]) : 0.f;
-              }
-            }
-            if (p.e.dbpart && mvalid) {
-              // bias gradient (value columns) and, for a first layer on raw
-              // coordinates, the coordinate terms of its weight gradient
-#pragma unroll
-              for (int g = 0; g < 4; ++g) {
-                const int64_t col = col0 + 4 * g;
-                if (col < p.e.n_res4) {
-                  dbacc[0] += o[4 * g];
-                  if (p.e.dterms) {
-                    const int64_t pt = col >> 2;
-                    for (int jj = 0; jj < p.e.dterms; ++jj)
-                      dbacc[1 + jj] = fmaf(o[4 * g], p.e.x_res[(int64_t)jj * p.e.n_res + pt], dbacc[1 + jj]);
-                    for (int r = 1; r < 4; ++r) {
-                      const int d = row_dir(p.e.jet_mode, r);
-                      if (d >= 0) dbacc[1 + d] += o[4 * g + r];
-                    }
-                  }
-                } else {
-                  for (int r = 0; r < 4; ++r) {
-                    const ColPoint cp = classify_col(col + r, p.e.n_res, p.e.n_ic, p.e.n_bc);
-                    if (cp.set == 3) continue;
-                    dbacc[0] += o[4 * g + r];
-                    for (int jj = 0; jj < p.e.dterms; ++jj)
-                      dbacc[1 + jj] = fmaf(o[4 * g + r],
-                                           coord(p.e.x_res, p.e.x_ic, p.e.x_bc, p.e.n_res, p.e.n_ic, p.e.n_bc, cp, jj),
-                                           dbacc[1 + jj]);
-                  }
-                }
-              }
-            }
           }
-          // stage this warp's 32 x 16 chunk(s) and store them with one bulk copy each
-          const int sb = nstore & 1;
-          if (nstore >= 2) {
-            if (lane == 0) bulk_wait_read1();   // the copy that used this buffer has read it
-            __syncwarp();
-          }
-          T* s0 = stg + (sb * 2 + 0) * (32 * 16);
-          T* s1 = stg + (sb * 2 + 1) * (32 * 16);
-          store16<T>(s0 + lane * 16, o);
-          if (MODE == TC_FWD) store16<T>(s1 + lane * 16, cur);
-          fence_proxy_async();
-          __syncwarp();
-          if (lane == 0) {
-            if (row0 < p.M) {
-              tma_store_2d(&mapO1, s0, (int)col0, row0);
-              if (MODE == TC_FWD) tma_store_2d(&mapO2, s1, (int)col0, row0);
-            }
-            bulk_commit();   // one group per chunk (possibly empty) keeps the buffer parity exact
-          }
-          ++nstore;
-        } else if (mvalid) {
-          if (MODE == TC_DW) {
-            const int split = t / (p.m_tiles * p.n_tiles);
-            float* dst = p.out32 + ((int64_t)split * p.M + m) * p.N;
-            if (col0 + 16 <= p.N && (p.N & 3) == 0) {
-              store16<float>(dst + col0, cur);
+        } else if (MODE == TC_DW) {
+          const int split = t / (p.m_tiles * p.n_tiles);
+          float* dst = p.out32 + ((int64_t)split * p.M + m) * p.N;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int64_t col0 = (int64_t)nb * BN + 16 * pt + 64 * r;
+            if (col0 + 16 <= p.N && (p.N & 7) == 0) {
+              st16(dst + col0, v[r]);
             } else {
               for (int j = 0; j < 16; ++j)
-                if (col0 + j < p.N) dst[col0 + j] = cur[j];
+                if (col0 + j < p.N) dst[col0 + j] = v[r][j];
             }
-          } else {   // TC_STORE
-            store16<float>(p.out32 + (int64_t)m * p.NC + col0, cur);
           }
+        } else {   // TC_STORE
+#pragma unroll
+          for (int r = 0; r < 4; ++r) st16(p.out32 + (int64_t)m * p.NC + (int64_t)nb * BN + 16 * pt + 64 * r, v[r]);
         }
-        if (cc + 1 < CPP) tmem_wait_ld();
       }
-      if (MODE == TC_ADJ && p.e.dbpart && mvalid) {
-        float* dst = p.e.dbpart + ((int64_t)(nb * PARTS + part) * p.M + m) * (1 + p.e.dterms);
-        for (int jj = 0; jj <= p.e.dterms; ++jj) dst[jj] = dbacc[jj];
+      }   // groups
+      if (MODE == TC_ADJ && mvalid && p.e.dbpart) {
+        float* dst = p.e.dbpart + ((int64_t)m * (p.n_tiles * PARTS) + nb * PARTS + part) * (1 + p.e.dterms);
+        dst[0] = db[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          if (j < p.e.dterms) dst[1 + j] = db[1 + j];
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[buf]);
     }
-    if (C::STAGED && lane == 0) bulk_wait_all();   // bulk stores done before the CTA exits
   }
 
   // ---- teardown: wait (bounded) for copies still in flight, free TMEM ----------------
@@ -578,36 +603,21 @@ bool make_map(CUtensorMap* m, const void* base, bool tf32, uint64_t cols, uint64
   return r == CUDA_SUCCESS;
 }
 
-// Output map for the staged bulk stores: [rows][cols], box 32 rows x 16 columns,
-// no swizzle (the staging buffer is plain row-major).
-bool make_store_map(CUtensorMap* m, const void* base, bool tf32, uint64_t cols, uint64_t rows) {
-  if (!g_encode) return false;
-  const uint32_t es = tf32 ? 4 : 2;
-  cuuint64_t dims[2] = {cols, rows};
-  cuuint64_t strides[1] = {cols * es};
-  cuuint32_t box[2] = {16, 32};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                        const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 template <bool TF32, int MODE, bool SPLIT>
 pinn_status launch(pinn_handle* h, const CUtensorMap& a, const CUtensorMap& a2, const CUtensorMap& b,
-                   const CUtensorMap& o1, const CUtensorMap& o2, const TcParams& p, int grid, cudaStream_t st) {
+                   const CUtensorMap& blo, const TcParams& p, int grid, cudaStream_t st) {
   using C = Cfg<TF32, MODE, SPLIT>;
   auto kern = k_tc_gemm<TF32, MODE, SPLIT>;
   static bool attr_set = false;   // per instantiation
   if (!attr_set) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) != cudaSuccess) {
+      cudaGetLastError();   // do not leave the failure for the next launch to report
       snprintf(h->err, sizeof(h->err), "tcgen05 kernel: cannot reserve %zu bytes of shared memory", C::SMEM);
       return PINN_ERR_CUDA;
     }
     attr_set = true;
   }
-  kern<<<grid, THREADS, C::SMEM, st>>>(a, a2, b, o1, o2, p);
+  kern<<<grid, THREADS, C::SMEM, st>>>(a, a2, b, blo, p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(h->err, sizeof(h->err), "tcgen05 kernel launch: %s", cudaGetErrorString(e));
@@ -669,18 +679,16 @@ pinn_status map_err(pinn_handle* h, const char* what) {
 
 }  // namespace
 
-pinn_status tc_gemm_fwd(pinn_handle* h, const void* W, const void* Wlo, const void* A, int fout, int fin, int64_t NC,
-                        const EpiArgs& e, cudaStream_t st) {
-  CUtensorMap ma, ma2, mb;
+pinn_status tc_gemm_fwd(pinn_handle* h, const void* W, const void* Wlo, const void* A, const void* Alo, int fout,
+                        int fin, int64_t NC, const EpiArgs& e, cudaStream_t st) {
+  CUtensorMap ma, ma2, mb, mlo;
   if (!make_map(&ma, W, false, fin, fout, 64, BM) || !make_map(&ma2, Wlo, false, fin, fout, 64, BM))
     return map_err(h, "forward weights");
   if (!make_map(&mb, A, false, NC, fin, 64, 64)) return map_err(h, "forward activations");
-  CUtensorMap o1, o2;
-  if (!make_store_map(&o1, e.out, false, NC, fout) || !make_store_map(&o2, e.zout, false, NC, fout))
-    return map_err(h, "forward outputs");
+  if (!make_map(&mlo, Alo, false, NC / 4, fin, 64, 64)) return map_err(h, "forward value-row low half");
   TcParams p = base_params(fout, (int)NC, fin, NC, 64, h->d_status);
   p.e = e;
-  return launch<false, TC_FWD, true>(h, ma, ma2, mb, o1, o2, p, grid_for(h, p.m_tiles * p.n_tiles), st);
+  return launch<false, TC_FWD, true>(h, ma, ma2, mb, mlo, p, grid_for(h, p.m_tiles * p.n_tiles), st);
 }
 
 pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fin, int fout, int64_t NC,
@@ -688,11 +696,9 @@ pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fi
   CUtensorMap ma, mb;
   if (!make_map(&ma, WT, false, fout, fin, 64, BM)) return map_err(h, "adjoint weights");
   if (!make_map(&mb, Zbar, false, NC, fout, 64, 64)) return map_err(h, "adjoint input");
-  CUtensorMap o1;
-  if (!make_store_map(&o1, e.out, false, NC, fin)) return map_err(h, "adjoint output");
   TcParams p = base_params(fin, (int)NC, fout, NC, 64, h->d_status);
   p.e = e;
-  return launch<false, TC_ADJ, false>(h, ma, ma, mb, o1, o1, p, grid_for(h, p.m_tiles * p.n_tiles), st);
+  return launch<false, TC_ADJ, false>(h, ma, ma, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles), st);
 }
 
 pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout, int fin, int64_t NC, int nsplit,
@@ -708,7 +714,7 @@ pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout
     return PINN_ERR_INVALID_ARG;
   }
   p.out32 = part;
-  return launch<false, TC_DW, false>(h, ma, ma, mb, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles * nsplit), st);
+  return launch<false, TC_DW, false>(h, ma, ma, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles * nsplit), st);
 }
 
 }  // namespace pinn
@@ -741,10 +747,10 @@ extern "C" PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, 
       TcParams p = base_params(M, N, K, N, 64, status);
       p.out32 = d_D;
       if (d_A2)
-        r = launch<false, TC_STORE, true>(&h, ma, ma2, mb, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
+        r = launch<false, TC_STORE, true>(&h, ma, ma2, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
                                           (cudaStream_t)stream);
       else
-        r = launch<false, TC_STORE, false>(&h, ma, ma, mb, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
+        r = launch<false, TC_STORE, false>(&h, ma, ma, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
                                            (cudaStream_t)stream);
     }
   } else {
@@ -754,7 +760,7 @@ extern "C" PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, 
     } else {
       TcParams p = base_params(M, N, K, N, 64, status);
       p.out32 = d_D;
-      r = launch<false, TC_DW, false>(&h, ma, ma, mb, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
+      r = launch<false, TC_DW, false>(&h, ma, ma, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
                                       (cudaStream_t)stream);
     }
   }
