@@ -177,10 +177,12 @@ PINN_API pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res
                                              int32_t* n);
 
 /* Self-test of the tensor-core GEMM core (no PINN arithmetic): BF16 inputs,
- * FP32 output D [M][N] row-major, all device pointers.
- *   kind 0: D = A B (+ A2 B when d_A2 != NULL), A, A2 [M][K], B [K][N] (N
- *           contiguous, the layout of the forward / adjoint jet GEMMs); N % 256 == 0.
- *   kind 1: D = A B^T, A [M][K], B [N][K] (K contiguous, the weight-gradient layout).
+ * FP32 output, all device pointers.  "Tile-major" is the library's jet-matrix
+ * layout: a logical [R][C] matrix stored as [C/256][R][256].
+ *   kind 0: D = A B (+ A2 B when d_A2 != NULL), A, A2 [M][K] row-major, B [K][N]
+ *           and D [M][N] tile-major (the forward / adjoint layout); N % 256 == 0.
+ *   kind 1: D = A B^T, A [M][K] and B [N][K] tile-major (the weight-gradient
+ *           layout), D [M][N] row-major; K % 256 == 0.
  * M, N, K multiples of 8.  Synchronises `stream`; returns PINN_ERR_TIMEOUT if a
  * bounded device wait expired.  No counterpart in the paper: a test hook. */
 PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, const void* d_A, const void* d_A2,

@@ -106,6 +106,17 @@ __host__ __device__ __forceinline__ int64_t jcol(int64_t p, int r) {
   return ((p >> 6) << 8) + ((int64_t)r << 6) + (p & 63);
 }
 
+// Storage is tile-major: a jet matrix with w feature rows is [NP/64][w][256], so
+// the 256 columns of one tile and one feature are contiguous and a whole tile
+// (w x 256) is one contiguous block.  Element offset of (feature f, column c):
+__host__ __device__ __forceinline__ int64_t toff(int64_t f, int64_t c, int64_t w) {
+  return (((c >> 8) * w + f) << 8) + (c & 255);
+}
+// The BF16 low half of the value rows is [NP/64][w][64]; offset of (f, point p):
+__host__ __device__ __forceinline__ int64_t loff(int64_t f, int64_t p, int64_t w) {
+  return (((p >> 6) * w + f) << 6) + (p & 63);
+}
+
 enum PointSet : int { SET_RES = 0, SET_IC = 1, SET_BC = 2, SET_PAD = 3 };
 
 __device__ __forceinline__ int point_set(int64_t p, int64_t n_res, int64_t n_ic, int64_t n_bc, int64_t& idx) {

@@ -66,8 +66,7 @@ __global__ void k_embed_ff(const float* x_res, const float* x_ic, const float* x
   float Bj[3] = {0.f, 0.f, 0.f};
   for (int i = 0; i < d_in; ++i) Bj[i] = B[(int64_t)i * m + j];
   const float q = (mode == JET_MAXWELL) ? 0.f : (Bj[0] * Bj[0] + (mode == JET_NS ? Bj[1] * Bj[1] : 0.f));
-  T* rc = A0 + (int64_t)j * NC;
-  T* rs = A0 + (int64_t)(m + j) * NC;
+  const int64_t wA = 2 * (int64_t)m;   // rows of A_0
   // four consecutive points per thread (same tile): vector stores per jet row
   for (int64_t p0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); p0 < NP;
        p0 += 4 * (int64_t)gridDim.x * blockDim.x) {
@@ -98,8 +97,8 @@ __global__ void k_embed_ff(const float* x_res, const float* x_ic, const float* x
     const int64_t c0 = jcol(p0, 0);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      store4<T>(rc + c0 + 64 * r, vc[r]);
-      store4<T>(rs + c0 + 64 * r, vs[r]);
+      store4<T>(A0 + toff(j, c0 + 64 * r, wA), vc[r]);
+      store4<T>(A0 + toff(m + j, c0 + 64 * r, wA), vs[r]);
     }
     if (LO) {
       float lc[4], ls[4];
@@ -108,8 +107,8 @@ __global__ void k_embed_ff(const float* x_res, const float* x_ic, const float* x
         lc[k] = vc[0][k] - __bfloat162float(__float2bfloat16_rn(vc[0][k]));
         ls[k] = vs[0][k] - __bfloat162float(__float2bfloat16_rn(vs[0][k]));
       }
-      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A0lo) + (int64_t)j * NP + p0, lc);
-      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A0lo) + (int64_t)(m + j) * NP + p0, ls);
+      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A0lo) + loff(j, p0, wA), lc);
+      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A0lo) + loff(m + j, p0, wA), ls);
     }
   }
 }
@@ -141,8 +140,7 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
   float Wf[3] = {0.f, 0.f, 0.f};
   for (int i = 0; i < d_in; ++i) Wf[i] = W[(int64_t)f * d_in + i];
   const float bf = b[f];
-  T* ra = A1 + (int64_t)f * NC;
-  T* rz = Z1 + (int64_t)f * NC;
+
   for (int64_t p0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); p0 < NP;
        p0 += 4 * (int64_t)gridDim.x * blockDim.x) {
     float za[4][4], aa[4][4];   // [row][point]
@@ -167,14 +165,14 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
     const int64_t c0 = jcol(p0, 0);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      store4<T>(ra + c0 + 64 * r, aa[r]);
-      store4<T>(rz + c0 + 64 * r, za[r]);
+      store4<T>(A1 + toff(f, c0 + 64 * r, fout), aa[r]);
+      store4<T>(Z1 + toff(f, c0 + 64 * r, fout), za[r]);
     }
     if (LO) {
       float lo[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) lo[k] = aa[0][k] - __bfloat162float(__float2bfloat16_rn(aa[0][k]));
-      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A1lo) + (int64_t)f * NP + p0, lo);
+      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A1lo) + loff(f, p0, fout), lo);
     }
   }
 }
@@ -300,13 +298,13 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
         for (int r = 0; r < 4; ++r) U[j][c][r] = 0.f;
 #pragma unroll 2
     for (int f = sl; f < w; f += 8) {
-      const T* row = AL + (int64_t)f * NC + cb;
+      const T* row = AL + toff(f, cb, w);
       float v[4][4];                               // [row][point]
 #pragma unroll
       for (int r = 0; r < 4; ++r) load4<T>(row + 64 * r, v[r]);
       if (ALlo) {
         float lo[4];
-        load4<__nv_bfloat16>(ALlo + (int64_t)f * a.NP + p0, lo);
+        load4<__nv_bfloat16>(ALlo + loff(f, p0, w), lo);
 #pragma unroll
         for (int j = 0; j < 4; ++j) v[0][j] += lo[j];
       }
@@ -352,13 +350,13 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
       for (int r = 0; r < 4; ++r)
         if (((c * 4 + r) & 7) == sl) {
           const float o[4] = {Ub[0][c][r], Ub[1][c][r], Ub[2][c][r], Ub[3][c][r]};
-          store4<float>(a.Ubar + (int64_t)c * NC + cb + 64 * r, o);
+          store4<float>(a.Ubar + toff(c, cb + 64 * r, D), o);
         }
     // abar_L = Ubar W_out (rank <= 3), then the tanh-jet adjoint with Z_L.
 #pragma unroll 2
     for (int f = sl; f < w; f += 8) {
       float z[4][4], zb[4][4];                     // [row][point]
-      const T* zrow = ZL + (int64_t)f * NC + cb;
+      const T* zrow = ZL + toff(f, cb, w);
 #pragma unroll
       for (int r = 0; r < 4; ++r) load4<T>(zrow + 64 * r, z[r]);
 #pragma unroll
@@ -376,7 +374,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) zb[r][j] = o[r];
       }
-      T* zbrow = Zb + (int64_t)f * NC + cb;
+      T* zbrow = Zb + toff(f, cb, w);
 #pragma unroll
       for (int r = 0; r < 4; ++r) store4<T>(zbrow + 64 * r, zb[r]);
     }
@@ -428,15 +426,15 @@ __global__ void k_dw_out(const T* AL, const float* Ubar, int w, int64_t NC, int 
     float g[D][8];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      load4<float>(Ubar + (int64_t)c * NC + 8 * o, &g[c][0]);
-      load4<float>(Ubar + (int64_t)c * NC + 8 * o + 4, &g[c][4]);
+      load4<float>(Ubar + toff(c, 8 * o, D), &g[c][0]);
+      load4<float>(Ubar + toff(c, 8 * o, D) + 4, &g[c][4]);
     }
 #pragma unroll
     for (int i = 0; i < DWO_ROWS; ++i) {
       if (f0 + i >= w) break;
       float v[8];
-      load4<T>(AL + (int64_t)(f0 + i) * NC + 8 * o, v);
-      load4<T>(AL + (int64_t)(f0 + i) * NC + 8 * o + 4, v + 4);
+      load4<T>(AL + toff(f0 + i, 8 * o, w), v);
+      load4<T>(AL + toff(f0 + i, 8 * o, w) + 4, v + 4);
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
@@ -493,17 +491,16 @@ __global__ void k_row_reduce(const T* Zb, int M, int64_t NP, int64_t n_res, int6
   const int64_t per = (NP + nbpart - 1) / nbpart;
   const int64_t p0 = chunk * per, p1 = min(NP, p0 + per);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  const T* rowp = Zb + (int64_t)row * NC;
 #pragma unroll 4
   for (int64_t p = p0 + lane; p < p1; p += 32) {
-    const float v0 = to_f<T>(rowp[jcol(p, 0)]);
+    const float v0 = to_f<T>(Zb[toff(row, jcol(p, 0), M)]);
     acc[0] += v0;
     if (dterms) {
       for (int j = 0; j < dterms; ++j)
         acc[1 + j] = fmaf(v0, point_coord(x_res, x_ic, x_bc, n_res, n_ic, n_bc, p, j), acc[1 + j]);
       for (int r = 1; r < 4; ++r) {
         const int d = row_dir(mode, r);
-        if (d >= 0) acc[1 + d] += to_f<T>(rowp[jcol(p, r)]);
+        if (d >= 0) acc[1 + d] += to_f<T>(Zb[toff(row, jcol(p, r), M)]);
       }
     }
   }

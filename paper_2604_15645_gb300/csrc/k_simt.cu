@@ -1,7 +1,7 @@
 // CUDA-core jet GEMMs: the FP32 path, and the fallback for shapes the tensor-core
-// kernels do not take.  Same data layout as the tensor-core path: activations are
-// feature-major [features][NC] with the four jet rows of a point in adjacent
-// columns, so every epilogue owns whole points and applies the jet rule locally.
+// kernels do not take.  Same data layout as the tensor-core path (tile-major jet
+// matrices, see jet.cuh); every thread owns whole points, so the jet rule and its
+// adjoint are applied locally.
 #include "internal.h"
 #include "jet.cuh"
 
@@ -65,12 +65,12 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
       const int kk = t >> 4, c = (t & 15) * 16;
       float v[16];
       if (k0 + kk < K) {
-        load_vec8<T>(Bop + (int64_t)(k0 + kk) * NC + n0 + c, v);
-        load_vec8<T>(Bop + (int64_t)(k0 + kk) * NC + n0 + c + 8, v + 8);
+        load_vec8<T>(Bop + toff(k0 + kk, n0 + c, K), v);
+        load_vec8<T>(Bop + toff(k0 + kk, n0 + c, K) + 8, v + 8);
         if (Blo && c < TILE_PTS) {
           float lo[16];
-          load_vec8<__nv_bfloat16>(Blo + (int64_t)(k0 + kk) * NP + tile * TILE_PTS + c, lo);
-          load_vec8<__nv_bfloat16>(Blo + (int64_t)(k0 + kk) * NP + tile * TILE_PTS + c + 8, lo + 8);
+          load_vec8<__nv_bfloat16>(Blo + loff(k0 + kk, tile * TILE_PTS + c, K), lo);
+          load_vec8<__nv_bfloat16>(Blo + loff(k0 + kk, tile * TILE_PTS + c, K) + 8, lo + 8);
           for (int q = 0; q < 16; ++q) v[q] += lo[q];
         }
       } else {
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
     if (f >= M) continue;
     float o[4][4], zz[4][4];   // [row][point]
     if (EPI == 1) {
-      const T* zr = reinterpret_cast<const T*>(e.zin) + (int64_t)f * NC + n0 + 4 * tx;
+      const T* zr = reinterpret_cast<const T*>(e.zin) + toff(f, n0 + 4 * tx, M);
       for (int r = 0; r < 4; ++r) load4<T>(zr + 64 * r, zz[r]);
     }
     const float bias = (EPI == 0) ? e.bias[f] : 0.f;
@@ -121,13 +121,13 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
         for (int r = 0; r < 4; ++r) o[r][j] = a[r];
       }
     }
-    T* orow = out + (int64_t)f * NC + n0 + 4 * tx;
+    T* orow = out + toff(f, n0 + 4 * tx, M);
     for (int r = 0; r < 4; ++r) store4<T>(orow + 64 * r, o[r]);
     if (EPI == 0) {
-      T* zrow = reinterpret_cast<T*>(e.zout) + (int64_t)f * NC + n0 + 4 * tx;
+      T* zrow = reinterpret_cast<T*>(e.zout) + toff(f, n0 + 4 * tx, M);
       for (int r = 0; r < 4; ++r) store4<T>(zrow + 64 * r, zz[r]);
       if (e.alo_out) {
-        __nv_bfloat16* lo = reinterpret_cast<__nv_bfloat16*>(e.alo_out) + (int64_t)f * NP + tile * TILE_PTS + 4 * tx;
+        __nv_bfloat16* lo = reinterpret_cast<__nv_bfloat16*>(e.alo_out) + loff(f, tile * TILE_PTS + 4 * tx, M);
         for (int j = 0; j < 4; ++j)
           lo[j] = __float2bfloat16_rn(o[0][j] - __bfloat162float(__float2bfloat16_rn(o[0][j])));
       }
@@ -155,14 +155,14 @@ __global__ void __launch_bounds__(THREADS) k_simt_dw(const TA* __restrict__ Aop,
     const int i = t >> 2, kk = (t & 3) * 8;   // 64 rows x 32 k, 8 per thread
     {
       float v[8];
-      if (m0 + i < M) load_vec8<TA>(Aop + (int64_t)(m0 + i) * NC + k0 + kk, v);
+      if (m0 + i < M) load_vec8<TA>(Aop + toff(m0 + i, k0 + kk, M), v);
       else
         for (int q = 0; q < 8; ++q) v[q] = 0.f;
       for (int q = 0; q < 8; ++q) As[kk + q][i] = v[q];
     }
     {
       float v[8];
-      if (nn0 + i < N) load_vec8<TB>(Bop + (int64_t)(nn0 + i) * NC + k0 + kk, v);
+      if (nn0 + i < N) load_vec8<TB>(Bop + toff(nn0 + i, k0 + kk, N), v);
       else
         for (int q = 0; q < 8; ++q) v[q] = 0.f;
       for (int q = 0; q < 8; ++q) Bs[kk + q][i] = v[q];

@@ -2,16 +2,17 @@
 // memory by TMA (cp.async.bulk.tensor, 128-byte swizzle) and FP32 accumulators in
 // tensor memory, read back with tcgen05.ld for the fused epilogues.
 //
-// Data layout (shared with the CUDA-core path): every activation-like matrix is
-// feature-major, [features][NC] with NC jet columns, and the four jet rows of an
-// interior point are adjacent columns.  The three GEMMs of a hidden layer are
+// Data layout (shared with the CUDA-core path): every jet matrix is tile-major,
+// [NC/256][features][256]: a tile holds 64 points, its 256 columns blocked by jet
+// row ([values | d1 | d2 | d2nd], see jet.cuh).  The three GEMMs of a hidden layer are
 //   forward  Z^T[fout][NC]    = W[fout][fin]   . A^T[fin][NC]       (B operand MN-major)
 //   adjoint  Abar^T[fin][NC]  = W^T[fin][fout] . Zbar^T[fout][NC]   (B operand MN-major)
 //   weights  dW[fout][fin]    = Zbar^T[fout][NC] . (A^T[fin][NC])^T (both K-major, split over NC)
-// so a 128-row accumulator tile puts one feature in each TMEM lane and 256
-// consecutive jet columns in its columns: each epilogue thread owns one feature of
-// 64 whole points and applies the tanh jet rule (or its adjoint) without any
-// cross-thread exchange.
+// so a 128-row accumulator tile puts one feature in each TMEM lane and the 256
+// columns of one point tile in its columns: each epilogue thread owns one feature
+// of whole points and applies the tanh jet rule (or its adjoint) without any
+// cross-thread exchange.  On the BF16 path the forward also adds the low halves of
+// the weights and of the input's value rows on the 64 value columns.
 //
 // Warp roles per CTA (320 threads, one CTA per SM, persistent over tiles):
 //   warp 0     TMA producer (one lane)
@@ -93,6 +94,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
           smem_u32(dst)),
       "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -369,15 +377,20 @@ __global__ void __launch_bounds__(THREADS, 1)
           mbar_expect_tx(&full[stage], C::STAGE);
           inflight[stage] = (int)phase + 1;
           const int kx = kb * C::BKE;
-          tma_load_2d(sa, &mapA, &full[stage], kx, mb * BM);
-          if (SPLIT) tma_load_2d(sa2, &mapA2, &full[stage], kx, mb * BM);
           if (C::B_MN) {
+            // A: weights [M][K] (2-D); B: jet tile nb, rows kx..kx+BKE (3-D, tile-major)
+            tma_load_2d(sa, &mapA, &full[stage], kx, mb * BM);
+            if (SPLIT) tma_load_2d(sa2, &mapA2, &full[stage], kx, mb * BM);
 #pragma unroll
             for (int j = 0; j < C::NBOX; ++j)
-              tma_load_2d(sb + j * C::BOX_BYTES, &mapB, &full[stage], nb * BN + j * C::BOXN, kx);
-            if (C::VLO) tma_load_2d(sb + C::B_BYTES, &mapBlo, &full[stage], nb * TILE_PTS, kx);
+              tma_load_3d(sb + j * C::BOX_BYTES, &mapB, &full[stage], j * C::BOXN, kx, nb);
+            if (C::VLO) tma_load_3d(sb + C::B_BYTES, &mapBlo, &full[stage], 0, kx, nb);
           } else {
-            tma_load_2d(sb, &mapB, &full[stage], kx, nb * BN);
+            // weight gradient: K runs over jet columns, 256 / BKE K-blocks per tile
+            constexpr int KPT = TILE_COLS / C::BKE;
+            const int tz = kb / KPT, tx = (kb % KPT) * C::BKE;
+            tma_load_3d(sa, &mapA, &full[stage], tx, mb * BM, tz);
+            tma_load_3d(sb, &mapB, &full[stage], tx, nb * BN, tz);
           }
           if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
         }
@@ -411,11 +424,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint64_t bd = C::B_MN ? make_desc(sb + kk * C::UK * 128, C::BOX_BYTES, 1024)
                                         : make_desc(sb + kk * 32, 16, 1024);
             tc_mma<TF32>(d, ad, bd, idesc, (kb > k0 || kk > 0) ? 1u : 0u);
-            if (SPLIT) tc_mma<TF32>(d, make_desc(sa2 + kk * 32, 16, 1024), bd, idesc, 1u);
             if (C::VLO) {
-              // value rows' low half: D[:, 0:64] += W_hi . Alo (64 columns)
+              // low halves on the 64 value columns only:
+              // D[:, 0:64] += W_lo . A[:, 0:64] + W_hi . A_lo
               constexpr uint32_t idesc64 = make_idesc(TF32 ? 2u : 1u, 1u, TILE_PTS);
+              const uint64_t bv = make_desc(sb + kk * C::UK * 128, C::BOX_BYTES, 1024);
+              tc_mma<TF32>(d, make_desc(sa2 + kk * 32, 16, 1024), bv, idesc64, 1u);
               tc_mma<TF32>(d, ad, make_desc(sb + C::B_BYTES + kk * C::UK * 128, C::BOX_BYTES, 1024), idesc64, 1u);
+            } else if (SPLIT) {
+              tc_mma<TF32>(d, make_desc(sa2 + kk * 32, 16, 1024), bd, idesc, 1u);
             }
           }
           tc_commit(&empty[stage]);
@@ -454,7 +471,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       // adjoint: Z of the layer below, kept as raw 32-byte rows (BF16: 8 registers a row)
       uint32_t zw[4][8 * (sizeof(T) / 2)];
       if (MODE == TC_ADJ && mvalid) {
-        const T* zr = reinterpret_cast<const T*>(p.e.zin) + (int64_t)m * p.NC + (int64_t)nb * BN + 16 * pt;
+        const T* zr = reinterpret_cast<const T*>(p.e.zin) + toff(m, (int64_t)nb * BN, p.M) + 16 * pt;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           ld_global_256(zr + 64 * r, zw[r]);
@@ -465,7 +482,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int r = 0; r < 4; ++r) tmem_ld16_issue(taddr + 64 * r, v[r]);
       tmem_wait_ld();
       if (mvalid) {
-        const int64_t cbase = (int64_t)m * p.NC + (int64_t)nb * BN + 16 * pt;
+        const int64_t cbase = toff(m, (int64_t)nb * BN, p.M) + 16 * pt;   // tile nb, row m, point group pt
         if (MODE == TC_FWD) {
           const float bias = p.e.bias[m];
 #pragma unroll
@@ -487,9 +504,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             float lo[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) lo[i] = v[0][i] - __bfloat162float(__float2bfloat16_rn(v[0][i]));
-            st16(reinterpret_cast<__nv_bfloat16*>(p.e.alo_out) + (int64_t)m * (p.NC / 4) + (int64_t)nb * TILE_PTS +
-                     16 * pt,
-                 lo);
+            st16(reinterpret_cast<__nv_bfloat16*>(p.e.alo_out) + loff(m, (int64_t)nb * TILE_PTS, p.M) + 16 * pt, lo);
           }
         } else if (MODE == TC_ADJ) {
 #pragma unroll
@@ -548,7 +563,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         } else {   // TC_STORE
 #pragma unroll
-          for (int r = 0; r < 4; ++r) st16(p.out32 + (int64_t)m * p.NC + (int64_t)nb * BN + 16 * pt + 64 * r, v[r]);
+          for (int r = 0; r < 4; ++r) st16(p.out32 + toff(m, (int64_t)nb * BN, p.M) + 16 * pt + 64 * r, v[r]);
         }
       }
       }   // groups
@@ -597,6 +612,24 @@ bool make_map(CUtensorMap* m, const void* base, bool tf32, uint64_t cols, uint64
   cuuint32_t box[2] = {box_cols, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// 3-D tensor map over a tile-major jet matrix [ntiles][rows][tcols] (tcols = 256 for
+// jet matrices, 64 for value-row low halves), box [1][box_rows][box_cols], 128-byte
+// swizzle, zero fill out of bounds.
+bool make_map3(CUtensorMap* m, const void* base, bool tf32, uint64_t tcols, uint64_t rows, uint64_t ntiles,
+               uint32_t box_cols, uint32_t box_rows) {
+  if (!g_encode) return false;
+  const uint32_t es = tf32 ? 4 : 2;
+  cuuint64_t dims[3] = {tcols, rows, ntiles};
+  cuuint64_t strides[2] = {tcols * es, tcols * rows * es};
+  cuuint32_t box[3] = {box_cols, box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                         const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -682,10 +715,11 @@ pinn_status map_err(pinn_handle* h, const char* what) {
 pinn_status tc_gemm_fwd(pinn_handle* h, const void* W, const void* Wlo, const void* A, const void* Alo, int fout,
                         int fin, int64_t NC, const EpiArgs& e, cudaStream_t st) {
   CUtensorMap ma, ma2, mb, mlo;
+  const uint64_t nt = (uint64_t)(NC / TILE_COLS);
   if (!make_map(&ma, W, false, fin, fout, 64, BM) || !make_map(&ma2, Wlo, false, fin, fout, 64, BM))
     return map_err(h, "forward weights");
-  if (!make_map(&mb, A, false, NC, fin, 64, 64)) return map_err(h, "forward activations");
-  if (!make_map(&mlo, Alo, false, NC / 4, fin, 64, 64)) return map_err(h, "forward value-row low half");
+  if (!make_map3(&mb, A, false, TILE_COLS, fin, nt, 64, 64)) return map_err(h, "forward activations");
+  if (!make_map3(&mlo, Alo, false, TILE_PTS, fin, nt, 64, 64)) return map_err(h, "forward value-row low half");
   TcParams p = base_params(fout, (int)NC, fin, NC, 64, h->d_status);
   p.e = e;
   return launch<false, TC_FWD, true>(h, ma, ma2, mb, mlo, p, grid_for(h, p.m_tiles * p.n_tiles), st);
@@ -695,7 +729,8 @@ pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fi
                         const EpiArgs& e, cudaStream_t st) {
   CUtensorMap ma, mb;
   if (!make_map(&ma, WT, false, fout, fin, 64, BM)) return map_err(h, "adjoint weights");
-  if (!make_map(&mb, Zbar, false, NC, fout, 64, 64)) return map_err(h, "adjoint input");
+  if (!make_map3(&mb, Zbar, false, TILE_COLS, fout, (uint64_t)(NC / TILE_COLS), 64, 64))
+    return map_err(h, "adjoint input");
   TcParams p = base_params(fin, (int)NC, fout, NC, 64, h->d_status);
   p.e = e;
   return launch<false, TC_ADJ, false>(h, ma, ma, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles), st);
@@ -704,8 +739,9 @@ pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fi
 pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout, int fin, int64_t NC, int nsplit,
                        float* part, cudaStream_t st) {
   CUtensorMap ma, mb;
-  if (!make_map(&ma, Zbar, false, NC, fout, 64, BM)) return map_err(h, "weight-gradient adjoint");
-  if (!make_map(&mb, A, false, NC, fin, 64, BN)) return map_err(h, "weight-gradient activations");
+  const uint64_t nt = (uint64_t)(NC / TILE_COLS);
+  if (!make_map3(&ma, Zbar, false, TILE_COLS, fout, nt, 64, BM)) return map_err(h, "weight-gradient adjoint");
+  if (!make_map3(&mb, A, false, TILE_COLS, fin, nt, 64, BN)) return map_err(h, "weight-gradient activations");
   TcParams p = base_params(fout, fin, (int)NC, NC, 64, h->d_status);
   p.nsplit = nsplit;
   p.kps = (p.k_iters + nsplit - 1) / nsplit;
@@ -726,7 +762,8 @@ extern "C" PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, 
   using namespace pinn;
   if (!d_A || !d_B || !d_D || M < 1 || N < 1 || K < 1 || (kind != 0 && kind != 1)) return PINN_ERR_INVALID_ARG;
   if (K % 8 || M % 8 || N % 8) return PINN_ERR_INVALID_ARG;
-  if (kind == 0 && N % BN) return PINN_ERR_INVALID_ARG;
+  if (kind == 0 && N % TILE_COLS) return PINN_ERR_INVALID_ARG;
+  if (kind == 1 && K % TILE_COLS) return PINN_ERR_INVALID_ARG;
   pinn_handle h;
   tc_init(&h);
   if (!g_encode) return PINN_ERR_UNSUPPORTED;
@@ -739,9 +776,9 @@ extern "C" PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, 
   CUtensorMap ma, ma2, mb;
   pinn_status r = PINN_OK;
   if (kind == 0) {
-    // D[M][N] = A[M][K] . B[K][N]   (B stored K x N, N contiguous: MN-major)
+    // D = A B: A [M][K] row-major, B [K][N] and D [M][N] in the tile-major jet layout
     if (!make_map(&ma, d_A, false, K, M, 64, BM) || !make_map(&ma2, d_A2 ? d_A2 : d_A, false, K, M, 64, BM) ||
-        !make_map(&mb, d_B, false, N, K, 64, 64)) {
+        !make_map3(&mb, d_B, false, TILE_COLS, K, N / TILE_COLS, 64, 64)) {
       r = PINN_ERR_CUDA;
     } else {
       TcParams p = base_params(M, N, K, N, 64, status);
@@ -754,8 +791,9 @@ extern "C" PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, 
                                            (cudaStream_t)stream);
     }
   } else {
-    // D[M][N] = A[M][K] . B[N][K]^T   (both K contiguous: K-major)
-    if (!make_map(&ma, d_A, false, K, M, 64, BM) || !make_map(&mb, d_B, false, K, N, 64, BN)) {
+    // D = A B^T: A [M][K] and B [N][K] in the tile-major layout (K over jet columns), D [M][N]
+    if (!make_map3(&ma, d_A, false, TILE_COLS, M, K / TILE_COLS, 64, BM) ||
+        !make_map3(&mb, d_B, false, TILE_COLS, N, K / TILE_COLS, 64, BN)) {
       r = PINN_ERR_CUDA;
     } else {
       TcParams p = base_params(M, N, K, N, 64, status);

@@ -1,5 +1,6 @@
 """The tcgen05 GEMM core in isolation (no PINN arithmetic): both operand layouts the
-jet GEMMs use, against an FP32 matmul of the same BF16 values."""
+jet GEMMs use, against an FP32 matmul of the same BF16 values.  Jet matrices are
+tile-major: a logical [R][C] matrix is stored as [C/256][R][256]."""
 import pytest
 import torch
 
@@ -10,6 +11,16 @@ def _rel(a, b):
     return float((a - b).norm() / b.norm())
 
 
+def _to_tiles(X):
+    R, C = X.shape
+    return X.reshape(R, C // 256, 256).permute(1, 0, 2).contiguous()
+
+
+def _from_tiles(Xt):
+    T, R, _ = Xt.shape
+    return Xt.permute(1, 0, 2).reshape(R, T * 256)
+
+
 @pytest.mark.parametrize("M,N,K,split", [(128, 256, 64, False), (256, 512, 320, False), (200, 768, 256, True),
                                          (24, 256, 16, False), (384, 1024, 512, True)])
 def test_mn_major_b_operand(cuda_lib, M, N, K, split):
@@ -18,9 +29,11 @@ def test_mn_major_b_operand(cuda_lib, M, N, K, split):
     A = torch.randn(M, K, device="cuda", generator=g).bfloat16()
     A2 = (torch.randn(M, K, device="cuda", generator=g) * 1e-3).bfloat16() if split else None
     B = torch.randn(K, N, device="cuda", generator=g).bfloat16()
-    D = torch.full((M, N), float("nan"), device="cuda")
-    _lib.pinn_tc_selftest(0, M, N, K, A.data_ptr(), A2.data_ptr() if split else None, B.data_ptr(), D.data_ptr(),
+    Bt = _to_tiles(B)
+    Dt = torch.full((N // 256, M, 256), float("nan"), device="cuda")
+    _lib.pinn_tc_selftest(0, M, N, K, A.data_ptr(), A2.data_ptr() if split else None, Bt.data_ptr(), Dt.data_ptr(),
                           torch.cuda.current_stream().cuda_stream)
+    D = _from_tiles(Dt)
     ref = A.float() @ B.float()
     if split:
         ref = ref + A2.float() @ B.float()
@@ -28,14 +41,15 @@ def test_mn_major_b_operand(cuda_lib, M, N, K, split):
     assert _rel(D, ref) < 1e-5
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (256, 512, 4096), (200, 296, 1000), (8, 16, 8)])
+@pytest.mark.parametrize("M,N,K", [(128, 256, 256), (256, 512, 4096), (200, 296, 1024), (8, 16, 256)])
 def test_k_major_both_operands(cuda_lib, M, N, K):
     from paper_2604_15645_gb300 import _lib
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K)
     A = torch.randn(M, K, device="cuda", generator=g).bfloat16()
     B = torch.randn(N, K, device="cuda", generator=g).bfloat16()
+    At, Bt = _to_tiles(A), _to_tiles(B)
     D = torch.full((M, N), float("nan"), device="cuda")
-    _lib.pinn_tc_selftest(1, M, N, K, A.data_ptr(), None, B.data_ptr(), D.data_ptr(),
+    _lib.pinn_tc_selftest(1, M, N, K, At.data_ptr(), None, Bt.data_ptr(), D.data_ptr(),
                           torch.cuda.current_stream().cuda_stream)
     ref = A.float() @ B.float().T
     assert torch.isfinite(D).all()
