@@ -237,6 +237,63 @@ def torch_autograd_rate(w, params, B, batch, steps=5, warmup=2):
             "how": "torch.autograd.grad(create_graph=True) input derivatives + loss.backward(), eager"}
 
 
+def run_family(args, ws_n, rank, local):
+    """The many-network workload: 64 independent Burgers nets, one graph-captured
+    training step (loss, adjoint, fused Adam) per timed step."""
+    import torch
+    from paper_2604_15645_gb300 import _lib, api
+    from synth import make_family
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fam = make_family(64)
+    precision = args.precision or "bf16"
+    multi = api.PinnMulti([s for s, _, _, _ in fam], precision, device=dev)
+    multi.set_inputs([api.DeviceBatch.from_host(b, device=dev) for _, _, b, _ in fam],
+                     [api.make_problem(pr.nu) for _, _, _, pr in fam])
+    p0 = np.concatenate([p for _, p, _, _ in fam]).astype(np.float32)
+    params = torch.tensor(p0, device=dev)
+    grad, m, v = (torch.zeros_like(params) for _ in range(3))
+    multi.autotune(params, grad, os.path.join(ROOT, "paper_2604_15645_gb300", "autotune_cache.json"))
+    n_pts = sum(b.n_res + b.n_ic + b.n_bc for _, _, b, _ in fam)
+    step = 0
+    for _ in range(args.warmup):
+        step += 1
+        multi.train_step(params, grad, m, v, step)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws_n > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step += 1
+        multi.train_step(params, grad, m, v, step)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    status = multi.status_poll()
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws_n > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    if rank != 0:
+        return None
+    engines = multi.engines()
+    return {
+        "metric": METRIC, "value": round(n_pts * ws_n / (float(t[0]) / 1e3), 1), "unit": UNIT, "n_gpus": ws_n,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(float(t[0]), 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
+        "config": {"workload": "burgers_family_64", "networks": 64, "points_per_step": n_pts,
+                   "params": int(params.numel()), "step": "loss + adjoint + fused Adam, one CUDA graph",
+                   "engines": {"tc": engines.count("tc"), "cuda_cores": engines.count("cuda_cores")},
+                   "parallelism": f"replicas x{ws_n}"},
+        "clocks": clk, "device_status": status,
+    }
+
+
 def run_ours(args, ws_n, rank, local):
     import torch
     from paper_2604_15645_gb300 import _lib, api
@@ -423,7 +480,10 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2604_15645_gb300 import _lib
     _lib.load()
-    out = run_ours(args, ws_n, rank, local)
+    if args.workload == "burgers_family_64":
+        out = run_family(args, ws_n, rank, local)
+    else:
+        out = run_ours(args, ws_n, rank, local)
     if out is not None:
         print(json.dumps(out), flush=True)
     if ws_n > 1:

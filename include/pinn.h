@@ -81,8 +81,12 @@ typedef struct {
   int32_t ff_m;                      /* Fourier frequencies m (embedding width 2m), 0=none */
   int32_t rwf;                       /* 1: every layer is W = diag(exp(s)) V (Eq. 15)     */
   int32_t precision;                 /* pinn_precision of the hidden-layer jet GEMMs      */
-  int32_t flags;                     /* reserved, must be 0                               */
+  int32_t flags;                     /* PINN_FLAG_* bits, 0 = defaults                    */
 } pinn_spec;
+
+/* pinn_spec.flags: run every jet GEMM on CUDA cores even where tcgen05 kernels
+ * apply (the many-network autotuner picks per network between the two). */
+#define PINN_FLAG_CUDA_CORES 1
 
 /* Loss weights and the PDE coefficient (nu for Burgers; 1/Re for Navier-Stokes;
  * ignored for Maxwell). */
@@ -187,6 +191,45 @@ PINN_API pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res
  * bounded device wait expired.  No counterpart in the paper: a test hook. */
 PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, const void* d_A, const void* d_A2,
                                       const void* d_B, float* d_D, void* stream);
+
+/* ---- many independent networks in one training step --------------------------------
+ * A pinn_multi holds one network handle per spec (uneven widths, depths and point
+ * counts allowed).  pinn_multi_train_step runs, for every network, the loss and
+ * gradient of its own batch and problem (as pinn_loss_grad), then one Adam step
+ * (Sec. 2.7.5) over the concatenation of all parameter vectors.  The first call with
+ * a given set of buffers captures the whole step in a CUDA graph (networks on
+ * parallel worker streams, then the Adam launch); later calls replay it, updating
+ * only the Adam scalars.  Parameters, gradients and Adam moments are single FP32
+ * device vectors laid out by pinn_multi_param_offsets (network i owns
+ * [offsets[i], offsets[i+1])).  d_loss receives PINN_LOSS_TERMS doubles per network.
+ * The workspace (pinn_multi_workspace_bytes) serves both GEMM engines, so
+ * pinn_multi_set_engine / pinn_multi_autotune never require a new one.  Not
+ * thread-safe; the graph keeps the buffers it was captured with alive by address. */
+typedef struct pinn_multi pinn_multi;
+
+PINN_API pinn_status pinn_multi_create(const pinn_spec* specs, int32_t n_nets, pinn_multi** out);
+PINN_API pinn_status pinn_multi_destroy(pinn_multi* m);
+/* n_nets + 1 offsets into the concatenated parameter vector. */
+PINN_API pinn_status pinn_multi_param_offsets(const pinn_multi* m, int64_t* offsets);
+PINN_API pinn_status pinn_multi_workspace_bytes(pinn_multi* m, const pinn_batch* batches, size_t* bytes);
+PINN_API pinn_status pinn_multi_set_ff_matrix(pinn_multi* m, int32_t net, const float* d_B);
+/* cuda_cores = 1 forces the CUDA-core GEMMs for network `net`, 0 allows tcgen05. */
+PINN_API pinn_status pinn_multi_set_engine(pinn_multi* m, int32_t net, int32_t cuda_cores);
+PINN_API pinn_status pinn_multi_get_engine(const pinn_multi* m, int32_t net, int32_t* cuda_cores);
+/* One training step (1-based `step`); asynchronous on `stream` except for graph
+ * (re)capture on the first call with new buffers. */
+PINN_API pinn_status pinn_multi_train_step(pinn_multi* m, const pinn_problem* probs, const pinn_batch* batches,
+                                           float* d_params, float* d_grad, float* d_m, float* d_v, int64_t step,
+                                           float lr, float beta1, float beta2, float eps, void* d_ws,
+                                           size_t ws_bytes, double* d_loss, void* stream);
+/* Times both GEMM engines per network (keyed by width, depth, power-of-two point
+ * bucket and precision), selects the faster, and reads / writes the choices as a
+ * JSON object in `cache_path` (NULL: no file).  Runs eagerly and synchronises. */
+PINN_API pinn_status pinn_multi_autotune(pinn_multi* m, const pinn_problem* probs, const pinn_batch* batches,
+                                         const float* d_params, void* d_ws, size_t ws_bytes, double* d_loss,
+                                         float* d_grad, const char* cache_path, void* stream);
+PINN_API pinn_status pinn_multi_status_poll(pinn_multi* m, void* stream);
+PINN_API const char* pinn_multi_last_error(const pinn_multi* m);
 
 /* Test hook: the tanh used by the BF16 epilogues, t = tanh(z) and tp = 1 - tanh(z)^2,
  * computed from e = exp(-2|z|) as t = sign(z)(1-e)/(1+e), tp = 4e/(1+e)^2, for n

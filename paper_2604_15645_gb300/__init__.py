@@ -6,7 +6,7 @@ from ._lib import load, PinnError, PRECISIONS  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("PinnNet", "DeviceBatch", "make_problem", "adam_step", "PinnLoss"):
+    if name in ("PinnNet", "DeviceBatch", "make_problem", "adam_step", "PinnLoss", "PinnMulti"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

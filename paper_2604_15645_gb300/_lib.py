@@ -21,7 +21,10 @@ STATUS = {0: "PINN_OK", 1: "PINN_ERR_INVALID_ARG", 2: "PINN_ERR_UNSUPPORTED", 3:
 EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_bytes", "pinn_set_ff_matrix",
            "pinn_loss", "pinn_loss_grad", "pinn_adam_step", "pinn_status_poll", "pinn_last_error",
            "pinn_status_string", "pinn_version", "pinn_set_profiling", "pinn_profile_read", "pinn_tensor_core_layers", "pinn_tc_selftest",
-           "pinn_loss_grad_static", "pinn_tanh_selftest"]
+           "pinn_loss_grad_static", "pinn_tanh_selftest", "pinn_multi_create", "pinn_multi_destroy",
+           "pinn_multi_param_offsets", "pinn_multi_workspace_bytes", "pinn_multi_set_ff_matrix",
+           "pinn_multi_set_engine", "pinn_multi_get_engine", "pinn_multi_train_step", "pinn_multi_autotune",
+           "pinn_multi_status_poll", "pinn_multi_last_error"]
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 8
 PHASE_NAMES = ["rwf", "embed", "fwd_gemm", "out_loss", "dw_gemm", "adj_gemm", "reduce", "other"]
@@ -79,6 +82,21 @@ def load(path: str = LIB_PATH):
     lib.pinn_status_string.restype = C.c_char_p
     lib.pinn_version.restype = C.c_char_p
     lib.pinn_set_profiling.argtypes = [H, C.c_int]
+    lib.pinn_multi_create.argtypes = [C.POINTER(pinn_spec), C.c_int32, C.POINTER(H)]
+    lib.pinn_multi_destroy.argtypes = [H]
+    lib.pinn_multi_param_offsets.argtypes = [H, C.POINTER(C.c_int64)]
+    lib.pinn_multi_workspace_bytes.argtypes = [H, C.POINTER(pinn_batch), C.POINTER(C.c_size_t)]
+    lib.pinn_multi_set_ff_matrix.argtypes = [H, C.c_int32, C.c_void_p]
+    lib.pinn_multi_set_engine.argtypes = [H, C.c_int32, C.c_int32]
+    lib.pinn_multi_get_engine.argtypes = [H, C.c_int32, C.POINTER(C.c_int32)]
+    lib.pinn_multi_train_step.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_float,
+                                          C.c_float, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
+    lib.pinn_multi_autotune.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
+                                        C.c_size_t, C.c_void_p, C.c_void_p, C.c_char_p, C.c_void_p]
+    lib.pinn_multi_status_poll.argtypes = [H, C.c_void_p]
+    lib.pinn_multi_last_error.argtypes = [H]
+    lib.pinn_multi_last_error.restype = C.c_char_p
     lib.pinn_tanh_selftest.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.pinn_loss_grad_static.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]
@@ -87,7 +105,7 @@ def load(path: str = LIB_PATH):
     lib.pinn_tensor_core_layers.argtypes = [H, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int32)]
     lib.pinn_profile_read.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     for name in EXPORTS:
-        if name not in ("pinn_last_error", "pinn_status_string", "pinn_version"):
+        if name not in ("pinn_last_error", "pinn_status_string", "pinn_version", "pinn_multi_last_error"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -189,3 +207,8 @@ def pinn_loss_grad_static(h, prob, batch, d_params, d_loss, d_grad, stream):
 
 def pinn_tanh_selftest(n, d_z, d_t, d_tp, stream):
     check(load().pinn_tanh_selftest(n, d_z, d_t, d_tp, stream))
+
+
+def check_multi(status: int, m):
+    if status != 0:
+        raise PinnError(status, load().pinn_multi_last_error(m).decode() if m else "")

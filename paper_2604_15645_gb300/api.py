@@ -131,3 +131,69 @@ class PinnLoss(torch.autograd.Function):
     def backward(ctx, gout):
         (grad,) = ctx.saved_tensors
         return grad * gout.to(grad.dtype), None, None, None
+
+
+class PinnMulti:
+    """Many independent networks, one graph-captured training step (pinn_multi_*)."""
+
+    def __init__(self, specs, precision="bf16", device="cuda"):
+        self.device = torch.device(device)
+        self.n = len(specs)
+        arr = (_lib.pinn_spec * self.n)(*[_lib.make_spec(s.pde, s.widths, s.ff_m, s.rwf, _lib.PRECISIONS[precision])
+                                          for s in specs])
+        h = _lib.C.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.load().pinn_multi_create(arr, self.n, _lib.C.byref(h)))
+        self.h = h.value
+        off = (_lib.C.c_int64 * (self.n + 1))()
+        _lib.check_multi(_lib.load().pinn_multi_param_offsets(self.h, off), self.h)
+        self.offsets = list(off)
+        self.P = self.offsets[-1]
+        self._ws = None
+        self._keep = None
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            try:
+                _lib.load().pinn_multi_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def set_inputs(self, batches, problems):
+        """batches: DeviceBatch per network; problems: pinn_problem per network."""
+        self._batches = list(batches)
+        self._cb = (_lib.pinn_batch * self.n)(*[b.c_struct() for b in batches])
+        self._cp = (_lib.pinn_problem * self.n)(*problems)
+        nbytes = _lib.C.c_size_t()
+        _lib.check_multi(_lib.load().pinn_multi_workspace_bytes(self.h, self._cb, _lib.C.byref(nbytes)), self.h)
+        if self._ws is None or self._ws.numel() < nbytes.value:
+            self._ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=self.device)
+        self.loss = torch.zeros(self.n, _lib.PINN_LOSS_TERMS, dtype=torch.float64, device=self.device)
+
+    def engines(self):
+        out = []
+        for i in range(self.n):
+            v = _lib.C.c_int32()
+            _lib.check_multi(_lib.load().pinn_multi_get_engine(self.h, i, _lib.C.byref(v)), self.h)
+            out.append("cuda_cores" if v.value else "tc")
+        return out
+
+    def set_engine(self, i, cuda_cores):
+        _lib.check_multi(_lib.load().pinn_multi_set_engine(self.h, i, int(bool(cuda_cores))), self.h)
+
+    def autotune(self, params, grad, cache_path=None):
+        path = cache_path.encode() if cache_path else None
+        _lib.check_multi(_lib.load().pinn_multi_autotune(
+            self.h, self._cp, self._cb, params.data_ptr(), self._ws.data_ptr(), self._ws.numel(),
+            self.loss.data_ptr(), grad.data_ptr(), path, _stream()), self.h)
+
+    def train_step(self, params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _lib.check_multi(_lib.load().pinn_multi_train_step(
+            self.h, self._cp, self._cb, params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), step,
+            lr, beta1, beta2, eps, self._ws.data_ptr(), self._ws.numel(), self.loss.data_ptr(), _stream()), self.h)
+        return self.loss
+
+    def status_poll(self):
+        return _lib.load().pinn_multi_status_poll(self.h, _stream())

@@ -701,6 +701,8 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, 
   }
 }
 
+const void* adam_kernel() { return reinterpret_cast<const void*>(&k_adam); }
+
 void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
                  float bc1, float bc2, cudaStream_t st) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048));

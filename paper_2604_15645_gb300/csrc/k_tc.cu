@@ -11,8 +11,8 @@
 // so a 128-row accumulator tile puts one feature in each TMEM lane and the 256
 // columns of one point tile in its columns: each epilogue thread owns one feature
 // of whole points and applies the tanh jet rule (or its adjoint) without any
-// cross-thread exchange.  On the BF16 path the forward also adds the low halves of
-// the weights and of the input's value rows on the 64 value columns.
+// cross-thread exchange.  On the BF16 path the forward also adds the low half of
+// the weights (all columns) and of the input's value rows (the 64 value columns).
 //
 // Warp roles per CTA (320 threads, one CTA per SM, persistent over tiles):
 //   warp 0     TMA producer (one lane)
@@ -424,15 +424,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint64_t bd = C::B_MN ? make_desc(sb + kk * C::UK * 128, C::BOX_BYTES, 1024)
                                         : make_desc(sb + kk * 32, 16, 1024);
             tc_mma<TF32>(d, ad, bd, idesc, (kb > k0 || kk > 0) ? 1u : 0u);
+            // low half of the weights on every column: D += W_lo . A
+            if (SPLIT) tc_mma<TF32>(d, make_desc(sa2 + kk * 32, 16, 1024), bd, idesc, 1u);
             if (C::VLO) {
-              // low halves on the 64 value columns only:
-              // D[:, 0:64] += W_lo . A[:, 0:64] + W_hi . A_lo
+              // low half of the input's value rows: D[:, 0:64] += W_hi . A_lo
               constexpr uint32_t idesc64 = make_idesc(TF32 ? 2u : 1u, 1u, TILE_PTS);
-              const uint64_t bv = make_desc(sb + kk * C::UK * 128, C::BOX_BYTES, 1024);
-              tc_mma<TF32>(d, make_desc(sa2 + kk * 32, 16, 1024), bv, idesc64, 1u);
               tc_mma<TF32>(d, ad, make_desc(sb + C::B_BYTES + kk * C::UK * 128, C::BOX_BYTES, 1024), idesc64, 1u);
-            } else if (SPLIT) {
-              tc_mma<TF32>(d, make_desc(sa2 + kk * 32, 16, 1024), bd, idesc, 1u);
             }
           }
           tc_commit(&empty[stage]);
@@ -676,7 +673,7 @@ void tc_init(pinn_handle* h) {
 
 bool tc_layer_supported(const pinn_handle* h, int li, int64_t NC) {
   (void)li;
-  if (!g_encode || h->spec.precision != PINN_BF16) return false;
+  if (!g_encode || h->spec.precision != PINN_BF16 || (h->spec.flags & PINN_FLAG_CUDA_CORES)) return false;
   if (NC % BN) return false;
   const int fin = h->layers[li].fin, fout = h->layers[li].fout;
   // TMA row strides must be multiples of 16 bytes: fin and fout multiples of 8 (bf16).

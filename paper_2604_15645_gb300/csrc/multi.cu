@@ -1,0 +1,409 @@
+// Many independent PINNs in one training step (pinn_multi_*).
+//
+// Every network keeps its own handle (its own widths, depth, point counts and
+// problem).  One call of pinn_multi_train_step runs, for all of them, the whole
+// step: input jets -> jet forward -> residual/loss -> adjoint -> ordered FP64
+// reductions, then one fused Adam update over the concatenated parameter vector.
+// The first call captures that step into a CUDA graph: the networks' launch
+// sequences are forked onto worker streams (so small networks run side by side on
+// the GPU), joined, and followed by the Adam launch; later calls with the same
+// buffers replay the graph.  The Adam scalars that change per step (learning rate,
+// step-dependent bias corrections) are written into the captured Adam node's
+// arguments before each replay, so a replay needs no re-capture.
+//
+// pinn_multi_autotune picks, per network, the faster of the two GEMM engines
+// (tcgen05 tiles of 128 features x 256 columns, or CUDA-core tiles of 64 x 256) by
+// timing both, and caches the choice per (width, depth, point-count bucket,
+// precision) in a JSON file.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace pinn {
+const void* adam_kernel();
+}
+
+struct pinn_multi {
+  int n = 0;
+  std::vector<pinn_handle*> nets;
+  std::vector<int64_t> poff;            // parameter offsets [n + 1]
+  std::vector<cudaStream_t> streams;
+  cudaStream_t cap = nullptr;           // capture stream (the caller's may be the legacy default stream)
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t adam_node = nullptr;
+  std::string key;                      // buffers / sizes / engines the graph was captured with
+  char err[512] = {0};
+};
+
+namespace {
+
+constexpr int kMaxStreams = 16;
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+pinn_status set_err(pinn_multi* m, const char* msg) {
+  if (m) snprintf(m->err, sizeof(m->err), "%s", msg);
+  return PINN_ERR_INVALID_ARG;
+}
+
+// Workspace of network i: the larger of its two engines' needs, so switching
+// engines never invalidates the caller's buffer.
+pinn_status net_ws(pinn_handle* h, const pinn_batch& b, size_t* bytes) {
+  const int32_t saved = h->spec.flags;
+  size_t a = 0, c = 0;
+  h->spec.flags = saved & ~PINN_FLAG_CUDA_CORES;
+  pinn_status s = pinn_workspace_bytes(h, b.n_res, b.n_ic, b.n_bc, &a);
+  h->spec.flags = saved | PINN_FLAG_CUDA_CORES;
+  if (!s) s = pinn_workspace_bytes(h, b.n_res, b.n_ic, b.n_bc, &c);
+  h->spec.flags = saved;
+  *bytes = align256(std::max(a, c));
+  return s;
+}
+
+std::string make_key(pinn_multi* m, const pinn_batch* batches, const float* p, const float* g, const float* mm,
+                     const float* v, void* ws, const double* loss, void* stream) {
+  std::string k;
+  char buf[160];
+  snprintf(buf, sizeof(buf), "%p %p %p %p %p %p %p|", (const void*)p, (const void*)g, (const void*)mm, (const void*)v,
+           ws, (const void*)loss, stream);
+  k += buf;
+  for (int i = 0; i < m->n; ++i) {
+    const pinn_batch& b = batches[i];
+    snprintf(buf, sizeof(buf), "%d:%p,%lld,%p,%p,%lld,%u,%p,%p,%lld,%u,%d;", i, (const void*)b.x_res,
+             (long long)b.n_res, (const void*)b.x_ic, (const void*)b.g_ic, (long long)b.n_ic, b.ic_mask,
+             (const void*)b.x_bc, (const void*)b.g_bc, (long long)b.n_bc, b.bc_mask, m->nets[i]->spec.flags);
+    k += buf;
+  }
+  return k;
+}
+
+void drop_graph(pinn_multi* m) {
+  if (m->exec) cudaGraphExecDestroy(m->exec);
+  if (m->graph) cudaGraphDestroy(m->graph);
+  m->exec = nullptr;
+  m->graph = nullptr;
+  m->adam_node = nullptr;
+  m->key.clear();
+}
+
+struct AdamArgs {
+  float lr, b1, b2, eps, bc1, bc2;
+};
+
+// Enqueue one whole training step on `st` (under stream capture).
+pinn_status enqueue_step(pinn_multi* m, const pinn_problem* probs, const pinn_batch* batches, float* d_p, float* d_g,
+                         float* d_m, float* d_v, char* ws, const std::vector<size_t>& ws_off,
+                         const std::vector<size_t>& ws_sz, const AdamArgs& ad, double* d_loss, cudaStream_t st) {
+  if (cudaEventRecord(m->fork, st) != cudaSuccess) return PINN_ERR_CUDA;
+  const int ns = (int)m->streams.size();
+  for (int k = 0; k < ns; ++k)
+    if (cudaStreamWaitEvent(m->streams[k], m->fork, 0) != cudaSuccess) return PINN_ERR_CUDA;
+  for (int i = 0; i < m->n; ++i) {
+    pinn_status s = pinn_loss_grad(m->nets[i], &probs[i], &batches[i], d_p + m->poff[i], ws + ws_off[i], ws_sz[i],
+                                   d_loss + (int64_t)i * PINN_LOSS_TERMS, d_g + m->poff[i], m->streams[i % ns]);
+    if (s) {
+      snprintf(m->err, sizeof(m->err), "network %d: %s", i, pinn_last_error(m->nets[i]));
+      return s;
+    }
+  }
+  for (int k = 0; k < ns; ++k) {
+    if (cudaEventRecord(m->joins[k], m->streams[k]) != cudaSuccess || cudaStreamWaitEvent(st, m->joins[k], 0) != cudaSuccess)
+      return PINN_ERR_CUDA;
+  }
+  pinn::launch_adam(d_p, d_g, d_m, d_v, m->poff[m->n], ad.lr, ad.b1, ad.b2, ad.eps, ad.bc1, ad.bc2, st);
+  return cudaGetLastError() == cudaSuccess ? PINN_OK : PINN_ERR_CUDA;
+}
+
+pinn_status plan_ws(pinn_multi* m, const pinn_batch* batches, std::vector<size_t>& off, std::vector<size_t>& sz,
+                    size_t* total) {
+  off.resize(m->n);
+  sz.resize(m->n);
+  size_t t = 0;
+  for (int i = 0; i < m->n; ++i) {
+    pinn_status s = net_ws(m->nets[i], batches[i], &sz[i]);
+    if (s) return s;
+    off[i] = t;
+    t += sz[i];
+  }
+  *total = t;
+  return PINN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+PINN_API pinn_status pinn_multi_create(const pinn_spec* specs, int32_t n_nets, pinn_multi** out) {
+  if (!specs || !out || n_nets < 1 || n_nets > 4096) return PINN_ERR_INVALID_ARG;
+  *out = nullptr;
+  pinn_multi* m = new (std::nothrow) pinn_multi();
+  if (!m) return PINN_ERR_INVALID_ARG;
+  m->n = n_nets;
+  m->poff.assign(n_nets + 1, 0);
+  for (int i = 0; i < n_nets; ++i) {
+    pinn_handle* h = nullptr;
+    pinn_status s = pinn_create(&specs[i], &h);
+    if (s) {
+      for (pinn_handle* x : m->nets) pinn_destroy(x);
+      delete m;
+      return s;
+    }
+    m->nets.push_back(h);
+    int64_t P = 0;
+    pinn_param_count(h, &P);
+    m->poff[i + 1] = m->poff[i] + P;
+  }
+  const int ns = std::min(n_nets, kMaxStreams);
+  bool ok = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; ok && k < ns; ++k) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+      m->streams.push_back(s);
+      m->joins.push_back(e);
+    }
+  }
+  if (!ok) {
+    pinn_multi_destroy(m);
+    return PINN_ERR_CUDA;
+  }
+  *out = m;
+  return PINN_OK;
+}
+
+PINN_API pinn_status pinn_multi_destroy(pinn_multi* m) {
+  if (!m) return PINN_OK;
+  drop_graph(m);
+  for (cudaStream_t s : m->streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : m->joins) cudaEventDestroy(e);
+  if (m->fork) cudaEventDestroy(m->fork);
+  if (m->cap) cudaStreamDestroy(m->cap);
+  for (pinn_handle* h : m->nets) pinn_destroy(h);
+  delete m;
+  return PINN_OK;
+}
+
+PINN_API pinn_status pinn_multi_param_offsets(const pinn_multi* m, int64_t* offsets) {
+  if (!m || !offsets) return PINN_ERR_INVALID_ARG;
+  for (int i = 0; i <= m->n; ++i) offsets[i] = m->poff[i];
+  return PINN_OK;
+}
+
+PINN_API pinn_status pinn_multi_workspace_bytes(pinn_multi* m, const pinn_batch* batches, size_t* bytes) {
+  if (!m || !batches || !bytes) return PINN_ERR_INVALID_ARG;
+  std::vector<size_t> off, sz;
+  return plan_ws(m, batches, off, sz, bytes);
+}
+
+PINN_API pinn_status pinn_multi_set_ff_matrix(pinn_multi* m, int32_t net, const float* d_B) {
+  if (!m || net < 0 || net >= m->n) return PINN_ERR_INVALID_ARG;
+  drop_graph(m);
+  return pinn_set_ff_matrix(m->nets[net], d_B);
+}
+
+PINN_API pinn_status pinn_multi_set_engine(pinn_multi* m, int32_t net, int32_t cuda_cores) {
+  if (!m || net < 0 || net >= m->n) return PINN_ERR_INVALID_ARG;
+  int32_t& f = m->nets[net]->spec.flags;
+  f = cuda_cores ? (f | PINN_FLAG_CUDA_CORES) : (f & ~PINN_FLAG_CUDA_CORES);
+  return PINN_OK;
+}
+
+PINN_API pinn_status pinn_multi_get_engine(const pinn_multi* m, int32_t net, int32_t* cuda_cores) {
+  if (!m || !cuda_cores || net < 0 || net >= m->n) return PINN_ERR_INVALID_ARG;
+  *cuda_cores = (m->nets[net]->spec.flags & PINN_FLAG_CUDA_CORES) ? 1 : 0;
+  return PINN_OK;
+}
+
+PINN_API pinn_status pinn_multi_train_step(pinn_multi* m, const pinn_problem* probs, const pinn_batch* batches,
+                                           float* d_params, float* d_grad, float* d_m, float* d_v, int64_t step,
+                                           float lr, float beta1, float beta2, float eps, void* d_ws,
+                                           size_t ws_bytes, double* d_loss, void* stream) {
+  if (!m || !probs || !batches || !d_params || !d_grad || !d_m || !d_v || !d_ws || !d_loss || step < 1)
+    return set_err(m, "NULL argument or step < 1");
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f))
+    return set_err(m, "bad Adam hyper-parameters");
+  if (reinterpret_cast<uintptr_t>(d_ws) % 256) return set_err(m, "workspace must be 256-byte aligned");
+  std::vector<size_t> off, sz;
+  size_t total = 0;
+  pinn_status s = plan_ws(m, batches, off, sz, &total);
+  if (s) return s;
+  if (ws_bytes < total) {
+    snprintf(m->err, sizeof(m->err), "workspace too small: %zu < %zu bytes", ws_bytes, total);
+    return PINN_ERR_WORKSPACE;
+  }
+  char* ws = static_cast<char*>(d_ws);
+  cudaStream_t st = (cudaStream_t)stream;
+  AdamArgs ad;
+  ad.lr = lr; ad.b1 = beta1; ad.b2 = beta2; ad.eps = eps;
+  ad.bc1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+  ad.bc2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+  const std::string key = make_key(m, batches, d_params, d_grad, d_m, d_v, d_ws, d_loss, stream);
+  if (key != m->key) {
+    drop_graph(m);
+    // capture on the handle's own stream; the graph is launched on the caller's
+    if (cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      snprintf(m->err, sizeof(m->err), "cannot begin stream capture");
+      return PINN_ERR_CUDA;
+    }
+    s = enqueue_step(m, probs, batches, d_params, d_grad, d_m, d_v, ws, off, sz, ad, d_loss, m->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(m->cap, &g);
+    if (s || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (!s) snprintf(m->err, sizeof(m->err), "graph capture failed: %s", cudaGetErrorString(e));
+      return s ? s : PINN_ERR_CUDA;
+    }
+    // find the Adam node, whose scalar arguments change from step to step
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+      cudaKernelNodeParams kp;
+      if (cudaGraphKernelNodeGetParams(nd, &kp) == cudaSuccess && kp.func == pinn::adam_kernel()) m->adam_node = nd;
+    }
+    if (!m->adam_node || cudaGraphInstantiate(&m->exec, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      m->exec = nullptr;
+      snprintf(m->err, sizeof(m->err), "graph instantiation failed");
+      return PINN_ERR_CUDA;
+    }
+    m->graph = g;
+    m->key = key;
+  } else {
+    cudaKernelNodeParams kp;
+    if (cudaGraphKernelNodeGetParams(m->adam_node, &kp) != cudaSuccess) return PINN_ERR_CUDA;
+    int64_t n = m->poff[m->n];
+    float* p0 = d_params;
+    const float* g0 = d_grad;
+    float* m0 = d_m;
+    float* v0 = d_v;
+    void* args[] = {&p0, &g0, &m0, &v0, &n, &ad.lr, &ad.b1, &ad.b2, &ad.eps, &ad.bc1, &ad.bc2};
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    if (cudaGraphExecKernelNodeSetParams(m->exec, m->adam_node, &kp) != cudaSuccess) {
+      snprintf(m->err, sizeof(m->err), "cannot update the Adam node");
+      return PINN_ERR_CUDA;
+    }
+  }
+  const cudaError_t le = cudaGraphLaunch(m->exec, st);
+  if (le != cudaSuccess) {
+    snprintf(m->err, sizeof(m->err), "graph launch: %s", cudaGetErrorString(le));
+    return PINN_ERR_CUDA;
+  }
+  return PINN_OK;
+}
+
+PINN_API pinn_status pinn_multi_status_poll(pinn_multi* m, void* stream) {
+  if (!m) return PINN_ERR_INVALID_ARG;
+  pinn_status worst = PINN_OK;
+  for (pinn_handle* h : m->nets) {
+    pinn_status s = pinn_status_poll(h, stream);
+    if (s && !worst) worst = s;
+  }
+  return worst;
+}
+
+PINN_API const char* pinn_multi_last_error(const pinn_multi* m) { return m ? m->err : "NULL handle"; }
+
+// Autotuner: time both engines per (width, depth, point bucket, precision) and keep
+// the faster.  The cache file holds one JSON object of "key": "tc" | "cuda_cores".
+PINN_API pinn_status pinn_multi_autotune(pinn_multi* m, const pinn_problem* probs, const pinn_batch* batches,
+                                         const float* d_params, void* d_ws, size_t ws_bytes, double* d_loss,
+                                         float* d_grad, const char* cache_path, void* stream) {
+  if (!m || !probs || !batches || !d_params || !d_ws || !d_loss || !d_grad) return set_err(m, "NULL argument");
+  std::vector<size_t> off, sz;
+  size_t total = 0;
+  pinn_status s = plan_ws(m, batches, off, sz, &total);
+  if (s) return s;
+  if (ws_bytes < total) return PINN_ERR_WORKSPACE;
+  std::map<std::string, int> cache;   // key -> 1 = CUDA cores, 0 = tensor cores
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[256], k[128], v[32];
+      while (fgets(line, sizeof(line), f))
+        if (sscanf(line, " \"%127[^\"]\" : \"%31[^\"]\"", k, v) == 2) cache[k] = strcmp(v, "cuda_cores") == 0 ? 1 : 0;
+      fclose(f);
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    snprintf(m->err, sizeof(m->err), "autotune: cannot create timing events");
+    return PINN_ERR_CUDA;
+  }
+  drop_graph(m);
+  for (int i = 0; i < m->n && !s; ++i) {
+    pinn_handle* h = m->nets[i];
+    const pinn_batch& b = batches[i];
+    int width = 0;
+    for (int l = 0; l < h->L; ++l) width = std::max(width, h->spec.widths[l]);
+    const int64_t npts = b.n_res + b.n_ic + b.n_bc;
+    const int bucket = (int)std::floor(std::log2((double)std::max<int64_t>(npts, 1)));
+    char key[128];
+    snprintf(key, sizeof(key), "w%d_L%d_n2^%d_%s", width, h->L, bucket,
+             h->spec.precision == PINN_BF16 ? "bf16" : h->spec.precision == PINN_TF32 ? "tf32" : "fp32");
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      pinn_multi_set_engine(m, i, it->second);
+      continue;
+    }
+    float best_ms[2] = {1e30f, 1e30f};
+    for (int eng = 0; eng < 2 && !s; ++eng) {
+      pinn_multi_set_engine(m, i, eng);
+      int32_t tc_layers = 0;
+      pinn_tensor_core_layers(h, b.n_res, b.n_ic, b.n_bc, &tc_layers);
+      if (eng == 0 && tc_layers == 0) continue;   // tensor cores do not apply to this network
+      for (int rep = 0; rep < 4 && !s; ++rep) {
+        cudaEventRecord(e0, st);
+        s = pinn_loss_grad(h, &probs[i], &b, d_params + m->poff[i], static_cast<char*>(d_ws) + off[i], sz[i],
+                           d_loss + (int64_t)i * PINN_LOSS_TERMS, d_grad + m->poff[i], st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best_ms[eng] = std::min(best_ms[eng], ms);
+      }
+    }
+    const int choice = best_ms[1] < best_ms[0] ? 1 : 0;
+    pinn_multi_set_engine(m, i, choice);
+    cache[key] = choice;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) {
+    snprintf(m->err, sizeof(m->err), "autotune: %s", pinn_status_string(s));
+    return s;
+  }
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "w")) {
+      fputs("{\n", f);
+      size_t k = 0;
+      for (const auto& kv : cache)
+        fprintf(f, "  \"%s\": \"%s\"%s\n", kv.first.c_str(), kv.second ? "cuda_cores" : "tc",
+                ++k < cache.size() ? "," : "");
+      fputs("}\n", f);
+      fclose(f);
+    }
+  }
+  return PINN_OK;
+}
+
+}  // extern "C"

@@ -324,3 +324,15 @@ def make_workload(name: str, n_res: Optional[int] = None, n_ic: Optional[int] = 
     batch = make_batch(w.spec.pde, n_res, n_ic, n_bc, 2000 + k, 3000 + k,
                        low_discrepancy=(w.spec.pde == PDE_MAXWELL))
     return w, params, B, batch
+
+
+def make_family(n_nets: int = 64, max_res: Optional[int] = None, random_bias: float = 0.0):
+    """The many-network Burgers family as a list of (spec, params, batch, problem);
+    `max_res` caps the interior points per network (for small test cases)."""
+    out = []
+    for m in family_specs(n_nets):
+        n_res = m["n_res"] if max_res is None else min(m["n_res"], max_res)
+        params = init_params(m["spec"], m["seed_params"], random_bias)
+        batch = make_batch(PDE_BURGERS, n_res, m["n_ic"], m["n_bc"], m["seed_res"], m["seed_bd"])
+        out.append((m["spec"], params, batch, Problem(nu=m["nu"])))
+    return out

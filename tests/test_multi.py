@@ -1,0 +1,94 @@
+"""Many independent networks in one graph-captured training step (pinn_multi_*):
+per-network loss and gradient against the FP64 oracle, the fused Adam update,
+bitwise equality of graph replays with eager single-network steps, and the engine
+autotuner's JSON cache."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import make_family
+
+from gpu_helpers import TOL, assert_parity, rel, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(n, max_res, precision):
+    from paper_2604_15645_gb300 import api
+    fam = make_family(n, max_res=max_res, random_bias=0.1)
+    multi = api.PinnMulti([s for s, _, _, _ in fam], precision)
+    multi.set_inputs([api.DeviceBatch.from_host(b) for _, _, b, _ in fam],
+                     [api.make_problem(pr.nu) for _, _, _, pr in fam])
+    p0 = np.concatenate([p for _, p, _, _ in fam]).astype(np.float32)
+    assert p0.size == multi.P
+    return api, fam, multi, p0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_multi_step_matches_oracle_per_network(cuda_lib, precision):
+    api, fam, multi, p0 = _setup(8, 1536, precision)
+    params = torch.tensor(p0, device="cuda")
+    grad = torch.zeros_like(params)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    loss = multi.train_step(params, grad, m, v, step=1, lr=1e-3)
+    torch.cuda.synchronize()
+    assert multi.status_poll() == 0
+    g = grad.cpu().numpy().astype(np.float64)
+    L = loss.cpu().numpy()
+    off = multi.offsets
+    for i, (spec, p, b, pr) in enumerate(fam):
+        rt, rg = run_oracle(spec, p, None, b, pr)
+        assert_parity(L[i], g[off[i]:off[i + 1]], rt, rg, TOL[precision], f"net {i} {spec.widths}")
+    b1, b2, lr, eps = (float(np.float32(x)) for x in (0.9, 0.999, 1e-3, 1e-8))
+    th, _, _ = oracle.adam_step(p0.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, lr, b1, b2, eps)
+    assert rel(params.cpu().numpy(), th) < 1e-6
+
+
+def test_multi_graph_replays_equal_eager_steps(cuda_lib):
+    api, fam, multi, p0 = _setup(5, 1024, "bf16")
+    params = torch.tensor(p0, device="cuda")
+    grad, m, v = (torch.zeros_like(params) for _ in range(3))
+    for step in range(1, 4):
+        multi.train_step(params, grad, m, v, step=step, lr=1e-3)
+    torch.cuda.synchronize()
+    # the same three steps, one network at a time, without a graph
+    nets = []
+    for spec, _, b, pr in fam:
+        net = api.PinnNet.from_spec(spec, "bf16")
+        nets.append((net, api.DeviceBatch.from_host(b), api.make_problem(pr.nu)))
+    p2 = torch.tensor(p0, device="cuda")
+    g2, m2, v2 = (torch.zeros_like(p2) for _ in range(3))
+    off = multi.offsets
+    for step in range(1, 4):
+        for i, (net, db, prob) in enumerate(nets):
+            net.loss_grad(p2[off[i]:off[i + 1]], db, prob, grad=g2[off[i]:off[i + 1]])
+        api.adam_step(p2, g2, m2, v2, step, lr=1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(params, p2) and torch.equal(m, m2) and torch.equal(v, v2)
+
+
+def test_multi_autotune_cache(cuda_lib, tmp_path):
+    api, fam, multi, p0 = _setup(6, 2048, "bf16")
+    params = torch.tensor(p0, device="cuda")
+    grad = torch.zeros_like(params)
+    path = str(tmp_path / "tune.json")
+    multi.autotune(params, grad, path)
+    with open(path) as f:
+        cache = json.load(f)
+    assert cache and all(v in ("tc", "cuda_cores") for v in cache.values())
+    first = multi.engines()
+    for i in range(multi.n):
+        multi.set_engine(i, i % 2)
+    multi.autotune(params, grad, path)          # reads the cache, no re-timing
+    assert multi.engines() == first
+    # a step after tuning still matches the oracle
+    m, v = torch.zeros_like(params), torch.zeros_like(params)
+    loss = multi.train_step(params, grad, m, v, step=1)
+    torch.cuda.synchronize()
+    spec, p, b, pr = fam[0]
+    rt, rg = run_oracle(spec, p, None, b, pr)
+    assert_parity(loss[0].cpu().numpy(), grad[:multi.offsets[1]].cpu().numpy(), rt, rg, TOL["bf16"], "tuned net 0")
