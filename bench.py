@@ -162,25 +162,48 @@ def workload_inputs(name, n_res=None):
     return w, params, B, batch
 
 
-def gemm_flops(w, ncols):
-    """Algorithmic jet-GEMM FLOPs of one step, per phase (2 per multiply-add)."""
-    spec = w.spec
+def layer_dims_of(spec):
     first_in = 2 * spec.ff_m if spec.ff_m else spec.d_in
     dims, prev = [], first_in
     for width in spec.widths:
         dims.append((prev, width))
         prev = width
-    fwd = dw = adj = 0.0
-    for li, (fi, fo) in enumerate(dims):
-        raw = (li == 0 and not spec.ff_m)
-        if raw:
+    return dims
+
+
+def algorithmic_work(w, n_pts, precision):
+    """Algorithmic FLOPs and HBM bytes of one step, per GEMM phase.
+
+    Units: a jet column (4 per point; initial/boundary points carry zero derivative
+    rows, so 4 * points columns).  Per column and hidden GEMM layer (fan_in fi,
+    fan_out fo), FLOPs are 2 fi fo for each of forward, adjoint and weight
+    gradient (no adjoint into the first GEMM after a frozen Fourier embedding; the
+    tiny raw-coordinate first layer and the output layer's dW are counted in the dW
+    phase only where they are GEMMs).  Bytes per column and layer, e = element size:
+      forward   read A (fi e) + write A, Z (2 fo e)   [+ BF16 value-row low halves,
+                                                       fi/2 + fo/2 bytes per column]
+      adjoint   read Zbar (fo e) + Z (fi e) + write Zbar (fi e)
+      weights   read Zbar (fo e) + A (fi e)
+    """
+    spec = w.spec
+    e = 2 if precision == "bf16" else 4
+    lo = 1.0 if precision == "bf16" else 0.0   # (fi + fo) * 2 bytes per point = (fi + fo) / 2 per column
+    cols = 4.0 * n_pts
+    fl = {"fwd_gemm": 0.0, "dw_gemm": 0.0, "adj_gemm": 0.0}
+    by = {"fwd_gemm": 0.0, "dw_gemm": 0.0, "adj_gemm": 0.0}
+    for li, (fi, fo) in enumerate(layer_dims_of(spec)):
+        if li == 0 and not spec.ff_m:
             continue
-        fwd += 2.0 * fi * fo * ncols
-        dw += 2.0 * fi * fo * ncols
+        fl["fwd_gemm"] += 2.0 * fi * fo * cols
+        by["fwd_gemm"] += cols * ((fi + 2 * fo) * e + lo * (fi + fo) / 2.0)
+        fl["dw_gemm"] += 2.0 * fi * fo * cols
+        by["dw_gemm"] += cols * (fo + fi) * e
         if li >= 1:
-            adj += 2.0 * fi * fo * ncols
-    dw += 2.0 * spec.d_out * spec.widths[-1] * ncols    # output-layer dW shares the phase
-    return {"fwd_gemm": fwd, "dw_gemm": dw, "adj_gemm": adj}
+            fl["adj_gemm"] += 2.0 * fi * fo * cols
+            by["adj_gemm"] += cols * (fo + 2 * fi) * e
+    fl["dw_gemm"] += 2.0 * spec.d_out * spec.widths[-1] * cols
+    by["dw_gemm"] += cols * (spec.widths[-1] * e + spec.d_out * 4)
+    return fl, by
 
 
 # ------------------------------------------------------------------------------ arms
@@ -372,26 +395,34 @@ def run_ours(args, ws_n, rank, local):
         return None
 
     peaks, peak_src = load_peaks()
-    flops = gemm_flops(w, ncols)
-    gemm_phases = {k: prof[k] for k in ("fwd_gemm", "dw_gemm", "adj_gemm", "out_loss", "embed", "reduce", "rwf")}
-    dom = max(gemm_phases, key=lambda k: gemm_phases[k][0])
+    flops, nbytes = algorithmic_work(w, n_pts, precision)
+    phases = {k: prof[k] for k in ("fwd_gemm", "dw_gemm", "adj_gemm", "out_loss", "embed", "reduce", "rwf")}
+    dom = max(phases, key=lambda k: phases[k][0])
     dom_ms, dom_launches = prof[dom]
-    roof = None
+    roof, roof_alt = None, None
     if dom in flops and dom_launches > 0:
         per_launch_ms = dom_ms / dom_launches
-        per_launch_flop = flops[dom] * args.steps / dom_launches
-        achieved = per_launch_flop / (per_launch_ms / 1e3) / 1e12
+        f_l = flops[dom] * args.steps / dom_launches
+        b_l = nbytes[dom] * args.steps / dom_launches
+        tflops = f_l / (per_launch_ms / 1e3) / 1e12
+        gbs = b_l / (per_launch_ms / 1e3) / 1e9
         if net.tensor_core_layers(*db.sizes) > 0:
-            peak = peaks["bf16_tflops_sustained"] * (0.5 if precision == "tf32" else 1.0)
-            roof = {"bound": "tensor", "unit": "TFLOP/s"}
+            # a kernel inside a long step: the sustained tensor peak (TF32 at half the BF16 rate)
+            tpeak = peaks["bf16_tflops_sustained"] * (0.5 if precision == "tf32" else 1.0)
+            tbound = "tensor"
         else:
             # CUDA-core FP32 FMA peak: 152 SMs x 128 FMA/clk x 2 FLOP x max SM clock
-            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            roof = {"bound": "alu", "unit": "TFLOP/s"}
-        roof.update({"kernel": dom, "achieved": round(achieved, 2), "peak": round(peak, 1),
-                     "frac": round(achieved / peak, 4), "traffic": _traffic(dom, args.workload),
-                     "peak_source": peak_src, "flop_per_launch": per_launch_flop,
-                     "launch_ms": round(per_launch_ms, 4)})
+            tpeak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            tbound = "alu"
+        compute = {"bound": tbound, "achieved": round(tflops, 2), "peak": round(tpeak, 1), "unit": "TFLOP/s",
+                   "frac": round(tflops / tpeak, 4), "traffic": _traffic(dom, args.workload),
+                   "kernel": dom, "flop_per_launch": f_l, "launch_ms": round(per_launch_ms, 4),
+                   "peak_source": peak_src}
+        memory = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                  "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": _traffic(dom, args.workload),
+                  "kernel": dom, "bytes_per_launch": b_l, "launch_ms": round(per_launch_ms, 4),
+                  "peak_source": peak_src}
+        roof, roof_alt = (memory, compute) if memory["frac"] >= compute["frac"] else (compute, memory)
 
     out = {
         "metric": METRIC, "value": round(n_pts * ws_n / (ms_max / 1e3), 1), "unit": UNIT, "n_gpus": ws_n,
@@ -409,6 +440,7 @@ def run_ours(args, ws_n, rank, local):
         "gpu_launches": int(sum(v[1] for v in prof.values() if v[1] > 0)),
         "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
         "roofline": roof,
+        "roofline_other": roof_alt,
         "clocks": clk,
         "device_status": status,
     }
