@@ -180,13 +180,16 @@ PINN_API pinn_status pinn_profile_read(pinn_handle* h, double* ms, int64_t* laun
 PINN_API pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc,
                                              int32_t* n);
 
-/* Self-test of the tensor-core GEMM core (no PINN arithmetic): BF16 inputs,
- * FP32 output, all device pointers.  "Tile-major" is the library's jet-matrix
- * layout: a logical [R][C] matrix stored as [C/256][R][256].
+/* Self-test of the tensor-core GEMM core (no PINN arithmetic): FP32 output, all
+ * device pointers.  "Tile-major" is the library's jet-matrix layout: a logical
+ * [R][C] matrix stored as [C/256][R][256].
  *   kind 0: D = A B (+ A2 B when d_A2 != NULL), A, A2 [M][K] row-major, B [K][N]
  *           and D [M][N] tile-major (the forward / adjoint layout); N % 256 == 0.
  *   kind 1: D = A B^T, A [M][K] and B [N][K] tile-major (the weight-gradient
  *           layout), D [M][N] row-major; K % 256 == 0.
+ *   kinds 0, 1: BF16 inputs (kind::f16 MMA); kind 3: the kind-1 layout with FP32
+ *           inputs that the tensor cores read as TF32 (kind::tf32 MMA).  Kind 2
+ *           (TF32 with an MN-major operand) returns PINN_ERR_UNSUPPORTED.
  * M, N, K multiples of 8.  Synchronises `stream`; returns PINN_ERR_TIMEOUT if a
  * bounded device wait expired.  No counterpart in the paper: a test hook. */
 PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, const void* d_A, const void* d_A2,

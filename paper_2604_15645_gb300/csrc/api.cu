@@ -65,18 +65,19 @@ pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   q.NP = (int64_t)align_up((size_t)std::max<int64_t>(n_res + n_ic + n_bc, 1), PT_ALIGN);
   q.NC = 4 * q.NP;
   q.es = (h->spec.precision == PINN_BF16) ? 2 : 4;
-  q.lo = (h->spec.precision == PINN_BF16);
+  q.lo = (h->spec.precision == PINN_BF16 || h->spec.precision == PINN_TF32);
+  q.lo_es = (h->spec.precision == PINN_BF16) ? 2 : 4;
   const int L = h->L;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   q.nbpart = (int)std::min<int64_t>(256, std::max<int64_t>(1, q.NC / 8192));
   if (h->spec.ff_m) {
     q.A[0] = take((size_t)2 * h->spec.ff_m * q.NC * q.es);
-    if (q.lo) q.Alo[0] = take((size_t)2 * h->spec.ff_m * q.NP * 2);
+    if (q.lo) q.Alo[0] = take((size_t)2 * h->spec.ff_m * q.NP * q.lo_es);
   }
   for (int l = 1; l <= L; ++l) {
     q.A[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
-    if (q.lo) q.Alo[l] = take((size_t)h->spec.widths[l - 1] * q.NP * 2);
+    if (q.lo) q.Alo[l] = take((size_t)h->spec.widths[l - 1] * q.NP * q.lo_es);
     q.Z[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
   }
   q.Zbar[0] = take((size_t)h->w_max * q.NC * q.es);
@@ -211,7 +212,9 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
     EpiArgs e{};
     e.bias = bias(li); e.out = ws + p.A[li + 1]; e.zout = ws + p.Z[li + 1];
     e.alo_out = p.lo ? ws + p.Alo[li + 1] : nullptr;
-    e.alo_in = p.lo ? ws + p.Alo[li] : nullptr;
+    // BF16 storage is rounded, so consumers add the low half back; TF32 storage is
+    // exact FP32 and only the tensor-core forward (which truncates) uses the low half.
+    e.alo_in = (p.lo && prec == PINN_BF16) ? ws + p.Alo[li] : nullptr;
     e.jet_mode = mode;
     PhaseScope ps(h, st, PH_FWD, 1);
     if (cp.tc[li]) {
@@ -225,7 +228,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
 
   // 4. Output layer, residual, loss partials, adjoint seed and Zbar_L.
   OutArgs oa{};
-  oa.AL = ws + p.A[L]; oa.ALlo = p.lo ? ws + p.Alo[L] : nullptr; oa.ZL = ws + p.Z[L];
+  oa.AL = ws + p.A[L]; oa.ALlo = (p.lo && prec == PINN_BF16) ? ws + p.Alo[L] : nullptr; oa.ZL = ws + p.Z[L];
   oa.W = W32(L); oa.b = bias(L);
   oa.g_ic = b->g_ic; oa.g_bc = b->g_bc; oa.ic_mask = b->ic_mask; oa.bc_mask = b->bc_mask;
   oa.n_res = p.n_res; oa.n_ic = p.n_ic; oa.n_bc = p.n_bc; oa.NP = p.NP; oa.NC = p.NC;

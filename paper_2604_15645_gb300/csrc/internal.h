@@ -44,9 +44,10 @@ struct Plan {
   int64_t NP = 0;      // points padded to PT_ALIGN
   int64_t NC = 0;      // 4 NP
   int es = 4;          // bytes per element of the compute type (2 bf16, 4 fp32/tf32)
-  bool lo = false;     // BF16: value rows also keep a low half (x - bf16(x)) in Alo
+  bool lo = false;     // BF16 / TF32: value rows also keep a low half in Alo
+  int lo_es = 2;       // bytes per low-half element (BF16 2, TF32 4)
   size_t A[PINN_MAX_HIDDEN + 1] = {};   // A_l^T [w_l][NC] compute type, l = 0..L (A_0 only with FF)
-  size_t Alo[PINN_MAX_HIDDEN + 1] = {}; // BF16: low half of the value rows [w_l][NP]
+  size_t Alo[PINN_MAX_HIDDEN + 1] = {}; // low half of the value rows, tile-major [NP/64][w_l][64]
   size_t Z[PINN_MAX_HIDDEN + 1] = {};   // Z_l^T [w_l][NC] compute type, l = 1..L
   size_t Zbar[2] = {};                  // ping-pong adjoints [w_max][NC] compute type
   size_t Ubar = 0;                      // output seeds [d_out][NC] fp32

@@ -12,6 +12,8 @@
 //   zbar   = abar t' + sum_k abar_k t'' z_k + abar_L (t''' sum_{k in S} z_k^2 + t'' z_L).
 #pragma once
 
+#include <cstring>
+
 #include "internal.h"
 
 namespace pinn {
@@ -140,6 +142,22 @@ __device__ __forceinline__ float point_coord(const float* x_res, const float* x_
 
 // Input direction of jet row r (1..3), or -1 for a second-order row.
 __device__ __forceinline__ int row_dir(int mode, int r) { return (mode == JET_MAXWELL || r < 3) ? r - 1 : -1; }
+
+// TF32 keeps the top 19 bits of an FP32 value (1 sign, 8 exponent, 10 mantissa);
+// the tensor cores read FP32 operands that way.  The remainder x - trunc(x) is exact
+// in FP32 and is the low half the TF32 path adds back where precision matters.
+__host__ __device__ __forceinline__ float tf32_trunc(float x) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+#else
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  u &= 0xFFFFE000u;
+  float y;
+  memcpy(&y, &u, 4);
+  return y;
+#endif
+}
 
 // ---- element type helpers ---------------------------------------------------------
 template <typename T> __device__ __forceinline__ float to_f(T v);

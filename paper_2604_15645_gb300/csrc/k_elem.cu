@@ -32,9 +32,11 @@ __global__ void k_rwf_prep(RwfArgs a) {
     float w = V[idx];
     if (s) w *= expf(s[i]);
     W32[idx] = w;
-    const T wh = from_f<T>(w);
+    // high / low halves of the weight in the compute type (BF16 rounding; TF32 truncation)
+    const float whf = (a.prec == PINN_TF32) ? tf32_trunc(w) : to_f<T>(from_f<T>(w));
+    const T wh = from_f<T>(whf);
     Wc[idx] = wh;
-    Wlo[idx] = from_f<T>(w - to_f<T>(wh));
+    Wlo[idx] = from_f<T>(w - whf);
     WTc[(int64_t)j * fout + i] = wh;
     WT32[(int64_t)j * fout + i] = w;
   }
@@ -46,9 +48,21 @@ void launch_rwf_prep(const RwfArgs& a, cudaStream_t st) {
   else k_rwf_prep<float><<<grid, 256, 0, st>>>(a);
 }
 
-// Low half of a value stored in BF16: v - bf16(v), itself rounded to BF16.
-__device__ __forceinline__ __nv_bfloat16 bf16_lo(float v) {
-  return __float2bfloat16_rn(v - __bfloat162float(__float2bfloat16_rn(v)));
+// Low half of a value-row entry: BF16 storage keeps v - bf16(v) (rounded to BF16);
+// TF32 keeps v - trunc_tf32(v) in FP32 (read only by the tensor-core forward).
+// LO: 0 none, 1 BF16, 2 TF32.
+template <int LO>
+__device__ __forceinline__ void store_lo4(void* base, int64_t off, const float v[4]) {
+  float lo[4];
+  if (LO == 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) lo[k] = v[k] - __bfloat162float(__float2bfloat16_rn(v[k]));
+    store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(base) + off, lo);
+  } else if (LO == 2) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) lo[k] = v[k] - tf32_trunc(v[k]);
+    store4<float>(reinterpret_cast<float*>(base) + off, lo);
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -58,9 +72,9 @@ __device__ __forceinline__ __nv_bfloat16 bf16_lo(float v) {
 // for the sine block).  Initial/boundary points get their value row only.  One
 // thread per (feature j < m, point).
 // ------------------------------------------------------------------------------------
-template <typename T, bool LO>
+template <typename T, int LO>
 __global__ void k_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
-                           int64_t n_bc, int d_in, const float* B, int m, int mode, T* A0, T* A0lo, int64_t NP) {
+                           int64_t n_bc, int d_in, const float* B, int m, int mode, T* A0, void* A0lo, int64_t NP) {
   const int j = blockIdx.y;
   const int64_t NC = 4 * NP;
   float Bj[3] = {0.f, 0.f, 0.f};
@@ -101,14 +115,8 @@ __global__ void k_embed_ff(const float* x_res, const float* x_ic, const float* x
       store4<T>(A0 + toff(m + j, c0 + 64 * r, wA), vs[r]);
     }
     if (LO) {
-      float lc[4], ls[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        lc[k] = vc[0][k] - __bfloat162float(__float2bfloat16_rn(vc[0][k]));
-        ls[k] = vs[0][k] - __bfloat162float(__float2bfloat16_rn(vs[0][k]));
-      }
-      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A0lo) + loff(j, p0, wA), lc);
-      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A0lo) + loff(m + j, p0, wA), ls);
+      store_lo4<LO>(A0lo, loff(j, p0, wA), vc[0]);
+      store_lo4<LO>(A0lo, loff(m + j, p0, wA), vs[0]);
     }
   }
 }
@@ -118,11 +126,14 @@ void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, i
                      int prec, cudaStream_t st) {
   dim3 grid((unsigned)std::min<int64_t>((NP / 4 + 255) / 256, 4096), m);
   if (prec == PINN_BF16)
-    k_embed_ff<__nv_bfloat16, true><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode,
-                                                          (__nv_bfloat16*)A0, (__nv_bfloat16*)A0lo, NP);
+    k_embed_ff<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode,
+                                                       (__nv_bfloat16*)A0, A0lo, NP);
+  else if (prec == PINN_TF32 && A0lo)
+    k_embed_ff<float, 2><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode, (float*)A0,
+                                               A0lo, NP);
   else
-    k_embed_ff<float, false><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode,
-                                                   (float*)A0, nullptr, NP);
+    k_embed_ff<float, 0><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode,
+                                               (float*)A0, nullptr, NP);
 }
 
 // ------------------------------------------------------------------------------------
@@ -131,10 +142,10 @@ void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, i
 // the second-order row (the input has no curvature); then the tanh jet rule.
 // Writes A_1 (and its value-row low half) and Z_1.
 // ------------------------------------------------------------------------------------
-template <typename T, bool LO>
+template <typename T, int LO>
 __global__ void k_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                               int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, T* A1,
-                              T* A1lo, T* Z1, int64_t NP) {
+                              void* A1lo, T* Z1, int64_t NP) {
   const int f = blockIdx.y;
   const int64_t NC = 4 * NP;
   float Wf[3] = {0.f, 0.f, 0.f};
@@ -158,7 +169,7 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
           z[r] = d >= 0 ? Wf[d] : 0.f;
         }
       }
-      jet_fwd<LO>(z, a, mode);
+      jet_fwd<(LO == 1)>(z, a, mode);
 #pragma unroll
       for (int r = 0; r < 4; ++r) { za[r][k] = z[r]; aa[r][k] = a[r]; }
     }
@@ -168,12 +179,7 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
       store4<T>(A1 + toff(f, c0 + 64 * r, fout), aa[r]);
       store4<T>(Z1 + toff(f, c0 + 64 * r, fout), za[r]);
     }
-    if (LO) {
-      float lo[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) lo[k] = aa[0][k] - __bfloat162float(__float2bfloat16_rn(aa[0][k]));
-      store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(A1lo) + loff(f, p0, fout), lo);
-    }
+    if (LO) store_lo4<LO>(A1lo, loff(f, p0, fout), aa[0]);
   }
 }
 
@@ -182,12 +188,14 @@ void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc
                         void* A1lo, void* Z1, int64_t NP, int prec, cudaStream_t st) {
   dim3 grid((unsigned)std::min<int64_t>((NP / 4 + 255) / 256, 4096), fout);
   if (prec == PINN_BF16)
-    k_first_layer<__nv_bfloat16, true><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout,
-                                                             mode, (__nv_bfloat16*)A1, (__nv_bfloat16*)A1lo,
-                                                             (__nv_bfloat16*)Z1, NP);
+    k_first_layer<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout,
+                                                          mode, (__nv_bfloat16*)A1, A1lo, (__nv_bfloat16*)Z1, NP);
+  else if (prec == PINN_TF32 && A1lo)
+    k_first_layer<float, 2><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
+                                                  (float*)A1, A1lo, (float*)Z1, NP);
   else
-    k_first_layer<float, false><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
-                                                      (float*)A1, nullptr, (float*)Z1, NP);
+    k_first_layer<float, 0><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
+                                                  (float*)A1, nullptr, (float*)Z1, NP);
 }
 
 // ------------------------------------------------------------------------------------

@@ -384,7 +384,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int j = 0; j < C::NBOX; ++j)
               tma_load_3d(sb + j * C::BOX_BYTES, &mapB, &full[stage], j * C::BOXN, kx, nb);
-            if (C::VLO) tma_load_3d(sb + C::B_BYTES, &mapBlo, &full[stage], 0, kx, nb);
+            if (C::VLO) {
+#pragma unroll
+              for (int j = 0; j < TILE_PTS / C::BOXN; ++j)
+                tma_load_3d(sb + C::B_BYTES + j * C::BOX_BYTES, &mapBlo, &full[stage], j * C::BOXN, kx, nb);
+            }
           } else {
             // weight gradient: K runs over jet columns, 256 / BKE K-blocks per tile
             constexpr int KPT = TILE_COLS / C::BKE;
@@ -497,11 +501,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           T* ao = reinterpret_cast<T*>(p.e.out) + cbase;
 #pragma unroll
           for (int r = 0; r < 4; ++r) st16(ao + 64 * r, v[r]);
-          if (!TF32 && p.e.alo_out) {
+          if (p.e.alo_out) {
+            // low half of the value rows for the next forward: BF16 rounding / TF32 truncation remainder
             float lo[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) lo[i] = v[0][i] - __bfloat162float(__float2bfloat16_rn(v[0][i]));
-            st16(reinterpret_cast<__nv_bfloat16*>(p.e.alo_out) + loff(m, (int64_t)nb * TILE_PTS, p.M) + 16 * pt, lo);
+            for (int i = 0; i < 16; ++i)
+              lo[i] = TF32 ? v[0][i] - tf32_trunc(v[0][i]) : v[0][i] - __bfloat162float(__float2bfloat16_rn(v[0][i]));
+            st16(reinterpret_cast<T*>(p.e.alo_out) + loff(m, (int64_t)nb * TILE_PTS, p.M) + 16 * pt, lo);
           }
         } else if (MODE == TC_ADJ) {
 #pragma unroll
@@ -672,17 +678,19 @@ void tc_init(pinn_handle* h) {
 }
 
 bool tc_layer_supported(const pinn_handle* h, int li, int64_t NC) {
-  (void)li;
+  // kind::tf32 reads both operands K-major only, and the forward / adjoint B operand
+  // (the jets) is MN-major in this layout: only BF16 runs these GEMMs on tensor cores.
   if (!g_encode || h->spec.precision != PINN_BF16 || (h->spec.flags & PINN_FLAG_CUDA_CORES)) return false;
   if (NC % BN) return false;
   const int fin = h->layers[li].fin, fout = h->layers[li].fout;
-  // TMA row strides must be multiples of 16 bytes: fin and fout multiples of 8 (bf16).
+  // TMA row strides must be multiples of 16 bytes: fin and fout multiples of 8 elements.
   return (fin % 8 == 0) && (fout % 8 == 0) && fin >= 16 && fout >= 16;
 }
 
 int tc_dw_splits(const pinn_handle* h, int fout, int fin, int64_t NC) {
   const int tiles = ((fout + BM - 1) / BM) * ((fin + BN - 1) / BN);
-  const int k_iters = (int)((NC + 63) / 64);
+  const int kblock = (h->spec.precision == PINN_TF32) ? 32 : 64;
+  const int k_iters = (int)((NC + kblock - 1) / kblock);
   int ns = std::max(1, (std::max(h->sm_count, 1) + tiles - 1) / tiles);
   ns = std::min(ns, k_iters);
   const int kps = (k_iters + ns - 1) / ns;
@@ -709,37 +717,46 @@ pinn_status map_err(pinn_handle* h, const char* what) {
 
 }  // namespace
 
-pinn_status tc_gemm_fwd(pinn_handle* h, const void* W, const void* Wlo, const void* A, const void* Alo, int fout,
-                        int fin, int64_t NC, const EpiArgs& e, cudaStream_t st) {
+namespace {
+
+template <bool TF32>
+pinn_status fwd_impl(pinn_handle* h, const void* W, const void* Wlo, const void* A, const void* Alo, int fout, int fin,
+                     int64_t NC, const EpiArgs& e, cudaStream_t st) {
+  using C = Cfg<TF32, TC_FWD, true>;
   CUtensorMap ma, ma2, mb, mlo;
   const uint64_t nt = (uint64_t)(NC / TILE_COLS);
-  if (!make_map(&ma, W, false, fin, fout, 64, BM) || !make_map(&ma2, Wlo, false, fin, fout, 64, BM))
+  if (!make_map(&ma, W, TF32, fin, fout, C::BKE, BM) || !make_map(&ma2, Wlo, TF32, fin, fout, C::BKE, BM))
     return map_err(h, "forward weights");
-  if (!make_map3(&mb, A, false, TILE_COLS, fin, nt, 64, 64)) return map_err(h, "forward activations");
-  if (!make_map3(&mlo, Alo, false, TILE_PTS, fin, nt, 64, 64)) return map_err(h, "forward value-row low half");
-  TcParams p = base_params(fout, (int)NC, fin, NC, 64, h->d_status);
+  if (!make_map3(&mb, A, TF32, TILE_COLS, fin, nt, C::BOXN, C::BKE)) return map_err(h, "forward activations");
+  if (!make_map3(&mlo, Alo, TF32, TILE_PTS, fin, nt, C::BOXN, C::BKE))
+    return map_err(h, "forward value-row low half");
+  TcParams p = base_params(fout, (int)NC, fin, NC, C::BKE, h->d_status);
   p.e = e;
-  return launch<false, TC_FWD, true>(h, ma, ma2, mb, mlo, p, grid_for(h, p.m_tiles * p.n_tiles), st);
+  return launch<TF32, TC_FWD, true>(h, ma, ma2, mb, mlo, p, grid_for(h, p.m_tiles * p.n_tiles), st);
 }
 
-pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fin, int fout, int64_t NC,
-                        const EpiArgs& e, cudaStream_t st) {
+template <bool TF32>
+pinn_status adj_impl(pinn_handle* h, const void* WT, const void* Zbar, int fin, int fout, int64_t NC, const EpiArgs& e,
+                     cudaStream_t st) {
+  using C = Cfg<TF32, TC_ADJ, false>;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, WT, false, fout, fin, 64, BM)) return map_err(h, "adjoint weights");
-  if (!make_map3(&mb, Zbar, false, TILE_COLS, fout, (uint64_t)(NC / TILE_COLS), 64, 64))
+  if (!make_map(&ma, WT, TF32, fout, fin, C::BKE, BM)) return map_err(h, "adjoint weights");
+  if (!make_map3(&mb, Zbar, TF32, TILE_COLS, fout, (uint64_t)(NC / TILE_COLS), C::BOXN, C::BKE))
     return map_err(h, "adjoint input");
-  TcParams p = base_params(fin, (int)NC, fout, NC, 64, h->d_status);
+  TcParams p = base_params(fin, (int)NC, fout, NC, C::BKE, h->d_status);
   p.e = e;
-  return launch<false, TC_ADJ, false>(h, ma, ma, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles), st);
+  return launch<TF32, TC_ADJ, false>(h, ma, ma, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles), st);
 }
 
-pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout, int fin, int64_t NC, int nsplit,
-                       float* part, cudaStream_t st) {
+template <bool TF32>
+pinn_status dw_impl(pinn_handle* h, const void* Zbar, const void* A, int fout, int fin, int64_t NC, int nsplit,
+                    float* part, cudaStream_t st) {
+  using C = Cfg<TF32, TC_DW, false>;
   CUtensorMap ma, mb;
   const uint64_t nt = (uint64_t)(NC / TILE_COLS);
-  if (!make_map3(&ma, Zbar, false, TILE_COLS, fout, nt, 64, BM)) return map_err(h, "weight-gradient adjoint");
-  if (!make_map3(&mb, A, false, TILE_COLS, fin, nt, 64, BN)) return map_err(h, "weight-gradient activations");
-  TcParams p = base_params(fout, fin, (int)NC, NC, 64, h->d_status);
+  if (!make_map3(&ma, Zbar, TF32, TILE_COLS, fout, nt, C::BKE, BM)) return map_err(h, "weight-gradient adjoint");
+  if (!make_map3(&mb, A, TF32, TILE_COLS, fin, nt, C::BKE, BN)) return map_err(h, "weight-gradient activations");
+  TcParams p = base_params(fout, fin, (int)NC, NC, C::BKE, h->d_status);
   p.nsplit = nsplit;
   p.kps = (p.k_iters + nsplit - 1) / nsplit;
   if ((p.k_iters + p.kps - 1) / p.kps != nsplit) {
@@ -747,20 +764,72 @@ pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout
     return PINN_ERR_INVALID_ARG;
   }
   p.out32 = part;
-  return launch<false, TC_DW, false>(h, ma, ma, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles * nsplit), st);
+  return launch<TF32, TC_DW, false>(h, ma, ma, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles * nsplit), st);
+}
+
+}  // namespace
+
+pinn_status tc_gemm_fwd(pinn_handle* h, const void* W, const void* Wlo, const void* A, const void* Alo, int fout,
+                        int fin, int64_t NC, const EpiArgs& e, cudaStream_t st) {
+  if (h->spec.precision == PINN_TF32) return fwd_impl<true>(h, W, Wlo, A, Alo, fout, fin, NC, e, st);
+  return fwd_impl<false>(h, W, Wlo, A, Alo, fout, fin, NC, e, st);
+}
+
+pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fin, int fout, int64_t NC,
+                        const EpiArgs& e, cudaStream_t st) {
+  if (h->spec.precision == PINN_TF32) return adj_impl<true>(h, WT, Zbar, fin, fout, NC, e, st);
+  return adj_impl<false>(h, WT, Zbar, fin, fout, NC, e, st);
+}
+
+pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout, int fin, int64_t NC, int nsplit,
+                       float* part, cudaStream_t st) {
+  if (h->spec.precision == PINN_TF32) return dw_impl<true>(h, Zbar, A, fout, fin, NC, nsplit, part, st);
+  return dw_impl<false>(h, Zbar, A, fout, fin, NC, nsplit, part, st);
 }
 
 }  // namespace pinn
 
 // Raw tensor-core GEMM of the library's two operand layouts, FP32 output, for
 // testing the MMA core in isolation (no epilogue).
+namespace {
+template <bool TF32>
+pinn_status selftest_impl(pinn_handle* h, int layout, int M, int N, int K, const void* d_A, const void* d_A2,
+                          const void* d_B, float* d_D, int* status, cudaStream_t st) {
+  using namespace pinn;
+  CUtensorMap ma, ma2, mb;
+  if (layout == 0) {
+    // D = A B: A [M][K] row-major, B [K][N] and D [M][N] in the tile-major jet layout
+    using C = Cfg<TF32, TC_STORE, false>;
+    if (!make_map(&ma, d_A, TF32, K, M, C::BKE, BM) || !make_map(&ma2, d_A2 ? d_A2 : d_A, TF32, K, M, C::BKE, BM) ||
+        !make_map3(&mb, d_B, TF32, TILE_COLS, K, N / TILE_COLS, C::BOXN, C::BKE))
+      return PINN_ERR_CUDA;
+    TcParams p = base_params(M, N, K, N, C::BKE, status);
+    p.out32 = d_D;
+    const int grid = grid_for(h, p.m_tiles * p.n_tiles);
+    if (d_A2) return launch<TF32, TC_STORE, true>(h, ma, ma2, mb, mb, p, grid, st);
+    return launch<TF32, TC_STORE, false>(h, ma, ma, mb, mb, p, grid, st);
+  }
+  // D = A B^T: A [M][K] and B [N][K] in the tile-major layout (K over jet columns), D [M][N]
+  using C = Cfg<TF32, TC_DW, false>;
+  if (!make_map3(&ma, d_A, TF32, TILE_COLS, M, K / TILE_COLS, C::BKE, BM) ||
+      !make_map3(&mb, d_B, TF32, TILE_COLS, N, K / TILE_COLS, C::BKE, BN))
+    return PINN_ERR_CUDA;
+  TcParams p = base_params(M, N, K, N, C::BKE, status);
+  p.out32 = d_D;
+  return launch<TF32, TC_DW, false>(h, ma, ma, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles), st);
+}
+}  // namespace
+
 extern "C" PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, const void* d_A, const void* d_A2,
                                                  const void* d_B, float* d_D, void* stream) {
   using namespace pinn;
-  if (!d_A || !d_B || !d_D || M < 1 || N < 1 || K < 1 || (kind != 0 && kind != 1)) return PINN_ERR_INVALID_ARG;
+  if (!d_A || !d_B || !d_D || M < 1 || N < 1 || K < 1 || kind < 0 || kind > 3) return PINN_ERR_INVALID_ARG;
+  const int layout = kind & 1;
+  const bool tf32 = (kind & 2) != 0;
+  if (tf32 && layout == 0) return PINN_ERR_UNSUPPORTED;   // kind::tf32 takes K-major operands only
   if (K % 8 || M % 8 || N % 8) return PINN_ERR_INVALID_ARG;
-  if (kind == 0 && N % TILE_COLS) return PINN_ERR_INVALID_ARG;
-  if (kind == 1 && K % TILE_COLS) return PINN_ERR_INVALID_ARG;
+  if (layout == 0 && N % TILE_COLS) return PINN_ERR_INVALID_ARG;
+  if (layout == 1 && K % TILE_COLS) return PINN_ERR_INVALID_ARG;
   pinn_handle h;
   tc_init(&h);
   if (!g_encode) return PINN_ERR_UNSUPPORTED;
@@ -770,35 +839,8 @@ extern "C" PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, 
   int* status = nullptr;
   if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return PINN_ERR_CUDA;
   cudaMemsetAsync(status, 0, sizeof(int), (cudaStream_t)stream);
-  CUtensorMap ma, ma2, mb;
-  pinn_status r = PINN_OK;
-  if (kind == 0) {
-    // D = A B: A [M][K] row-major, B [K][N] and D [M][N] in the tile-major jet layout
-    if (!make_map(&ma, d_A, false, K, M, 64, BM) || !make_map(&ma2, d_A2 ? d_A2 : d_A, false, K, M, 64, BM) ||
-        !make_map3(&mb, d_B, false, TILE_COLS, K, N / TILE_COLS, 64, 64)) {
-      r = PINN_ERR_CUDA;
-    } else {
-      TcParams p = base_params(M, N, K, N, 64, status);
-      p.out32 = d_D;
-      if (d_A2)
-        r = launch<false, TC_STORE, true>(&h, ma, ma2, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
-                                          (cudaStream_t)stream);
-      else
-        r = launch<false, TC_STORE, false>(&h, ma, ma, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
-                                           (cudaStream_t)stream);
-    }
-  } else {
-    // D = A B^T: A [M][K] and B [N][K] in the tile-major layout (K over jet columns), D [M][N]
-    if (!make_map3(&ma, d_A, false, TILE_COLS, M, K / TILE_COLS, 64, BM) ||
-        !make_map3(&mb, d_B, false, TILE_COLS, N, K / TILE_COLS, 64, BN)) {
-      r = PINN_ERR_CUDA;
-    } else {
-      TcParams p = base_params(M, N, K, N, 64, status);
-      p.out32 = d_D;
-      r = launch<false, TC_DW, false>(&h, ma, ma, mb, mb, p, grid_for(&h, p.m_tiles * p.n_tiles),
-                                      (cudaStream_t)stream);
-    }
-  }
+  pinn_status r = tf32 ? selftest_impl<true>(&h, layout, M, N, K, d_A, d_A2, d_B, d_D, status, (cudaStream_t)stream)
+                       : selftest_impl<false>(&h, layout, M, N, K, d_A, d_A2, d_B, d_D, status, (cudaStream_t)stream);
   int st = 0;
   if (r == PINN_OK) {
     if (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||

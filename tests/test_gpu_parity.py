@@ -36,19 +36,31 @@ def test_cavity_architecture_ragged_subset(cuda_lib, precision):
     _check(w.spec, p, B, b, w.problem, precision, f"cavity {precision}")
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
 def test_maxwell_architecture_subset(cuda_lib, precision):
     w, p, B, b = make_workload("maxwell_te_5x512", n_res=600, n_ic=100, n_bc=150, random_bias=0.1)
     _check(w.spec, p, B, b, w.problem, precision, f"maxwell {precision}")
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
 def test_ragged_widths_and_weights(cuda_lib, precision):
     spec = NetSpec(PDE_NS, 2, 3, [48, 80, 48], ff_m=20, ff_sigma=1.5, rwf=True)
     p = init_params(spec, 51, 0.2)
     B = ff_matrix(spec, 52)
     b = make_batch(PDE_NS, 333, 0, 77, 53, 54)
     _check(spec, p, B, b, Problem(0.02, 0.3, 2.0, 5.0), precision, "ragged")
+
+
+@pytest.mark.parametrize("precision,expect_tc", [("fp32", False), ("tf32", False), ("bf16", True)])
+def test_tensor_core_engine_selection(cuda_lib, precision, expect_tc):
+    # FP32 and TF32 run the exact CUDA-core GEMMs; BF16 runs every hidden layer on tcgen05
+    from paper_2604_15645_gb300 import api
+    w, p, B, b = make_workload("ns_cavity_6x256", n_res=4096, n_bc=512)
+    net = api.PinnNet.from_spec(w.spec, precision)
+    n_tc = net.tensor_core_layers(b.n_res, 0, b.n_bc)
+    n_layers = len(w.spec.widths)           # every layer into a hidden width (the Fourier one included)
+    assert n_tc == (n_layers if expect_tc else 0)
+    _check(w.spec, p, B, b, w.problem, precision, f"engine {precision}")
 
 
 def test_only_boundary_points(cuda_lib):

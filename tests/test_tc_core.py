@@ -1,5 +1,5 @@
 """The tcgen05 GEMM core in isolation (no PINN arithmetic): both operand layouts the
-jet GEMMs use, against an FP32 matmul of the same BF16 values.  Jet matrices are
+jet GEMMs use, against an FP32 matmul of the same BF16 (or TF32-truncated FP32) values.  Jet matrices are
 tile-major: a logical [R][C] matrix is stored as [C/256][R][256]."""
 import pytest
 import torch
@@ -54,6 +54,35 @@ def test_k_major_both_operands(cuda_lib, M, N, K):
     ref = A.float() @ B.float().T
     assert torch.isfinite(D).all()
     assert _rel(D, ref) < 1e-5
+
+
+def _tf32(X):
+    # the tensor cores read FP32 operands truncated to TF32 (10 explicit mantissa bits)
+    return (X.view(torch.int32) & -8192).view(torch.float32)
+
+
+def test_tf32_mn_major_is_refused(cuda_lib):
+    from paper_2604_15645_gb300 import _lib
+    A = torch.zeros(128, 64, device="cuda")
+    B = torch.zeros(1, 64, 256, device="cuda")
+    D = torch.zeros(1, 128, 256, device="cuda")
+    with pytest.raises(_lib.PinnError):
+        _lib.pinn_tc_selftest(2, 128, 256, 64, A.data_ptr(), None, B.data_ptr(), D.data_ptr(),
+                              torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 256), (200, 296, 1024)])
+def test_tf32_k_major_both_operands(cuda_lib, M, N, K):
+    from paper_2604_15645_gb300 import _lib
+    g = torch.Generator(device="cuda").manual_seed(M * 3 + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g)
+    B = torch.randn(N, K, device="cuda", generator=g)
+    D = torch.full((M, N), float("nan"), device="cuda")
+    _lib.pinn_tc_selftest(3, M, N, K, _to_tiles(A).data_ptr(), None, _to_tiles(B).data_ptr(), D.data_ptr(),
+                          torch.cuda.current_stream().cuda_stream)
+    ref = _tf32(A).double() @ _tf32(B).double().T
+    assert torch.isfinite(D).all()
+    assert _rel(D.double(), ref) < 1e-5
 
 
 def test_fast_tanh_against_cuda_tanh(cuda_lib):
