@@ -6,13 +6,13 @@
  * network parameters, plus a fused Adam update.  What is computed follows the
  * paper (arXiv 2604.15645):
  *   - MLP layers f = W g + b, g = tanh(f), final layer linear (Sec. 2.2, Eqs. 4-6);
- *   - random Fourier features gamma(x) = [cos(xB), sin(xB)], B frozen (Sec. 2.7.1, Eq. 14);
- *   - random weight factorisation W = diag(exp(s)) V on every layer (Sec. 2.7.2, Eq. 15);
+ *   - random Fourier features gamma(x) = [cos(xB), sin(xB)], B frozen (Sec. 2.6.1, Eq. 14);
+ *   - random weight factorisation W = diag(exp(s)) V on every layer (Sec. 2.6.2, Eq. 15);
  *   - composite MSE loss, each term the mean over its own point set (Sec. 2.3,
- *     Eqs. 10-13) weighted by lambda_pde, lambda_ic, lambda_bc (Sec. 2.7.4, Eq. 17);
+ *     Eqs. 10-13) weighted by lambda_pde, lambda_ic, lambda_bc (Sec. 2.6.4, Eq. 17);
  *   - residuals of viscous Burgers (Sec. 4.3 with a viscosity term), steady
- *     incompressible Navier-Stokes (Sec. 4.4) and TE Maxwell, eps = mu = 1 (Sec. 4.7);
- *   - Adam (Sec. 2.7.5).
+ *     incompressible Navier-Stokes (Sec. 4.4) and TE Maxwell, eps = mu = 1 (Sec. 4.8);
+ *   - Adam (Sec. 2.6.5).
  * Input derivatives, which the paper takes with autograd, are carried as
  * per-point jets (value plus derivative rows) through every layer, and the
  * parameter gradient comes from a hand-written adjoint of those jets.
@@ -145,7 +145,7 @@ PINN_API pinn_status pinn_loss_grad(pinn_handle* h, const pinn_problem* prob, co
                            const float* d_params, void* d_ws, size_t ws_bytes,
                            double* d_loss_terms, float* d_grad, void* stream);
 
-/* One Adam step in place over n entries (Sec. 2.7.5): m = b1 m + (1-b1) g,
+/* One Adam step in place over n entries (Sec. 2.6.5): m = b1 m + (1-b1) g,
  * v = b2 v + (1-b2) g^2, theta -= lr * (m/(1-b1^step)) / (sqrt(v/(1-b2^step)) + eps).
  * step is 1-based.  All four arrays FP32 device [n]. */
 PINN_API pinn_status pinn_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t n,
@@ -199,7 +199,7 @@ PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, const void*
  * A pinn_multi holds one network handle per spec (uneven widths, depths and point
  * counts allowed).  pinn_multi_train_step runs, for every network, the loss and
  * gradient of its own batch and problem (as pinn_loss_grad), then one Adam step
- * (Sec. 2.7.5) over the concatenation of all parameter vectors.  The first call with
+ * (Sec. 2.6.5) over the concatenation of all parameter vectors.  The first call with
  * a given set of buffers captures the whole step in a CUDA graph (networks on
  * parallel worker streams, then the Adam launch); later calls replay it, updating
  * only the Adam scalars.  Parameters, gradients and Adam moments are single FP32

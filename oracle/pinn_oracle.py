@@ -5,9 +5,9 @@ baseline may import this module; the library's compute path never does.  It
 shares no code with the CUDA path (it imports only numpy).
 
 What it computes, in the paper's order and notation:
-  * Random Fourier features (Sec. 2.7.1, Eq. 14): gamma(x) = [cos(xB), sin(xB)],
+  * Random Fourier features (Sec. 2.6.1, Eq. 14): gamma(x) = [cos(xB), sin(xB)],
     B of shape [d, m] drawn N(0, sigma^2) and frozen (not trained).
-  * Random weight factorisation (Sec. 2.7.2, Eq. 15): W^(l) = diag(exp(s^(l))) V^(l)
+  * Random weight factorisation (Sec. 2.6.2, Eq. 15): W^(l) = diag(exp(s^(l))) V^(l)
     for every layer l = 1..L+1.
   * The MLP (Sec. 2.2, Eqs. 4-6): f^(l) = W^(l) g^(l-1) + b^(l), g^(l) = tanh(f^(l))
     for l = 1..L, and a final linear layer without activation.
@@ -17,15 +17,15 @@ What it computes, in the paper's order and notation:
     what the paper obtains with autograd (Sec. 2.3, "autoGrad" terms).
   * Residuals: viscous Burgers u_t + u u_x - nu u_xx (Sec. 4.3 with viscosity),
     steady incompressible Navier-Stokes (Sec. 4.4, continuity and two momentum
-    equations, nu = 1/Re), TE Maxwell with eps = mu = 1 (Sec. 4.7, Eqs. for
+    equations, nu = 1/Re), TE Maxwell with eps = mu = 1 (Sec. 4.8, Eqs. for
     dEz/dt, dHx/dt, dHy/dt).
-  * Loss (Sec. 2.3, Eqs. 10-13 and Sec. 2.7.4 Eq. 17): each term is a mean of
+  * Loss (Sec. 2.3, Eqs. 10-13 and Sec. 2.6.4 Eq. 17): each term is a mean of
     squares over its own point set; several equations or output components are
     summed; L = lambda_pde L_pde + lambda_ic L_ic + lambda_bc L_bc.
   * Gradient: an explicit reverse sweep through the jets (adjoint of each step
     above), then the RWF chain rule dL/dV = exp(s) * dL/dW, dL/ds_i =
     sum_j dL/dW_ij W_ij.  B gets no gradient.
-  * Adam (Sec. 2.7.5): biased moments, bias correction, theta -= alpha m_hat /
+  * Adam (Sec. 2.6.5): biased moments, bias correction, theta -= alpha m_hat /
     (sqrt(v_hat) + eps).
 
 All arithmetic is float64 (or complex128 when a caller passes complex parameters
@@ -428,7 +428,7 @@ def output_jets(model, theta, B, X, order):
 
 
 # --------------------------------------------------------------------------------------
-# Adam (Sec. 2.7.5)
+# Adam (Sec. 2.6.5)
 # --------------------------------------------------------------------------------------
 
 def adam_step(theta, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -9,7 +9,7 @@
 namespace pinn {
 
 // ------------------------------------------------------------------------------------
-// RWF (Sec. 2.7.2, Eq. 15): W_l = diag(exp(s_l)) V_l for l = 1..L+1, written as an FP32
+// RWF (Sec. 2.6.2, Eq. 15): W_l = diag(exp(s_l)) V_l for l = 1..L+1, written as an FP32
 // master copy and its transpose, a copy in the compute type with its transpose
 // (operands of the tensor-core GEMMs), and the rounding remainder W - round(W) in
 // the compute type (the low half of the two-term BF16 weight used by the forward
@@ -66,7 +66,7 @@ __device__ __forceinline__ void store_lo4(void* base, int64_t off, const float v
 }
 
 // ------------------------------------------------------------------------------------
-// Fourier-feature input jets (Sec. 2.7.1, Eq. 14): phi_j = sum_i x_i B_ij,
+// Fourier-feature input jets (Sec. 2.6.1, Eq. 14): phi_j = sum_i x_i B_ij,
 // gamma = [cos phi, sin phi].  Row k (direction d): d cos = -sin phi B_dj,
 // d sin = cos phi B_dj; second-order row: -cos phi sum_{k in S} B_kj^2 (and -sin
 // for the sine block).  Initial/boundary points get their value row only.  One
@@ -695,7 +695,7 @@ void launch_finalize_loss(const double* part, int nblocks, int64_t n_res, int64_
 }
 
 // ------------------------------------------------------------------------------------
-// Adam (Sec. 2.7.5), bias-corrected, in place.
+// Adam (Sec. 2.6.5), bias-corrected, in place.
 // ------------------------------------------------------------------------------------
 __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
                        float eps, float bc1, float bc2) {

@@ -16,7 +16,7 @@ Fourier matrix=4000+k for workload index k):
                           viscosity), 2 -> 4x64 tanh -> 1, plain weights
   k=1 ns_cavity_6x256     steady lid-driven cavity (Sec. 4.4, Re=100), Fourier
                           features m=128 sigma=1 (Eq. 14), RWF (Eq. 15), 6x256 -> 3
-  k=2 maxwell_te_5x512    2-D TE Maxwell (Sec. 4.7 equations), Gaussian pulse,
+  k=2 maxwell_te_5x512    2-D TE Maxwell (Sec. 4.8 equations), Gaussian pulse,
                           PEC walls, 5x512 tanh with RWF -> 3
   k=3 burgers_family_64   64 independent Burgers nets of uneven width/depth
   k=4 ns_cavity_8x512     cavity at scale: m=256 sigma=2, 8x512, 1M points
