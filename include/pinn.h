@@ -88,6 +88,14 @@ typedef struct {
  * apply (the many-network autotuner picks per network between the two). */
 #define PINN_FLAG_CUDA_CORES 1
 
+/* pinn_spec.flags: recompute the layer jets instead of storing them.  The forward
+ * keeps each layer's pre-activation jets Z_l but only two activation buffers; the
+ * reverse sweep rebuilds A_{l-1} = tanh-jet(Z_{l-1}) just before the weight
+ * gradient of layer l needs it.  Activation memory drops from L buffers to two, for
+ * one extra read of Z and write of A per layer.  The adjoint epilogues always
+ * recompute tanh', tanh'' and tanh''' from the stored Z. */
+#define PINN_FLAG_RECOMPUTE 2
+
 /* Loss weights and the PDE coefficient (nu for Burgers; 1/Re for Navier-Stokes;
  * ignored for Maxwell). */
 typedef struct {
@@ -121,9 +129,21 @@ PINN_API pinn_status pinn_destroy(pinn_handle* h);
 PINN_API pinn_status pinn_param_count(const pinn_handle* h, int64_t* P);
 
 /* Bytes of device workspace one call on a batch of these sizes needs (jets of
- * every layer, adjoints, split reduction partials). */
+ * every layer, adjoints, split reduction partials).  With point chunking
+ * (pinn_set_chunk_points) it is the size of one chunk's pass plus a small staging
+ * area, independent of the batch size beyond one chunk. */
 PINN_API pinn_status pinn_workspace_bytes(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc,
                                  size_t* bytes);
+
+/* Point chunking: process a batch in consecutive chunks of at most `points`
+ * collocation points (rounded up to a multiple of 64; 0 = one pass over the whole
+ * batch, the default).  Points are taken in the order interior, initial, boundary.
+ * Each chunk runs the whole forward and reverse sweep; loss sums and the gradient
+ * accumulate over chunks in a fixed order, with every mean normalised by the
+ * batch's full point counts, so the result equals the one-pass result up to
+ * rounding and is deterministic.  Peak workspace then stays at one chunk's size for
+ * any batch.  Negative `points` is PINN_ERR_INVALID_ARG. */
+PINN_API pinn_status pinn_set_chunk_points(pinn_handle* h, int64_t points);
 
 /* Register the frozen Fourier-feature matrix B, FP32 device [d_in][m] (Eq. 14).
  * Required before any loss call when ff_m > 0.  The pointer is kept, not copied. */

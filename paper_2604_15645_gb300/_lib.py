@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(PKG, "libpinn.so")
 PINN_MAX_HIDDEN = 16
 PINN_LOSS_TERMS = 8
 PINN_FP32, PINN_TF32, PINN_BF16 = 0, 1, 2
+PINN_FLAG_CUDA_CORES, PINN_FLAG_RECOMPUTE = 1, 2
 PRECISIONS = {"fp32": PINN_FP32, "tf32": PINN_TF32, "bf16": PINN_BF16}
 STATUS = {0: "PINN_OK", 1: "PINN_ERR_INVALID_ARG", 2: "PINN_ERR_UNSUPPORTED", 3: "PINN_ERR_CUDA",
           4: "PINN_ERR_WORKSPACE", 5: "PINN_ERR_NONFINITE", 6: "PINN_ERR_TIMEOUT"}
@@ -24,7 +25,7 @@ EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_by
            "pinn_loss_grad_static", "pinn_tanh_selftest", "pinn_multi_create", "pinn_multi_destroy",
            "pinn_multi_param_offsets", "pinn_multi_workspace_bytes", "pinn_multi_set_ff_matrix",
            "pinn_multi_set_engine", "pinn_multi_get_engine", "pinn_multi_train_step", "pinn_multi_autotune",
-           "pinn_multi_status_poll", "pinn_multi_last_error"]
+           "pinn_multi_status_poll", "pinn_multi_last_error", "pinn_set_chunk_points"]
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 8
 PHASE_NAMES = ["rwf", "embed", "fwd_gemm", "out_loss", "dw_gemm", "adj_gemm", "reduce", "other"]
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH):
                                      C.c_void_p, C.c_void_p]
     lib.pinn_tensor_core_layers.argtypes = [H, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int32)]
     lib.pinn_profile_read.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    lib.pinn_set_chunk_points.argtypes = [H, C.c_int64]
     for name in EXPORTS:
         if name not in ("pinn_last_error", "pinn_status_string", "pinn_version", "pinn_multi_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -117,7 +119,8 @@ def check(status: int, handle=None):
         raise PinnError(status, msg)
 
 
-def make_spec(pde: int, widths, ff_m: int = 0, rwf: bool = False, precision: int = PINN_FP32) -> pinn_spec:
+def make_spec(pde: int, widths, ff_m: int = 0, rwf: bool = False, precision: int = PINN_FP32,
+              flags: int = 0) -> pinn_spec:
     s = pinn_spec()
     s.pde = pde
     s.n_hidden = len(widths)
@@ -126,7 +129,7 @@ def make_spec(pde: int, widths, ff_m: int = 0, rwf: bool = False, precision: int
     s.ff_m = ff_m
     s.rwf = int(bool(rwf))
     s.precision = precision
-    s.flags = 0
+    s.flags = flags
     return s
 
 
@@ -152,6 +155,10 @@ def pinn_workspace_bytes(h: int, n_res: int, n_ic: int, n_bc: int) -> int:
     b = C.c_size_t()
     check(load().pinn_workspace_bytes(h, n_res, n_ic, n_bc, C.byref(b)), h)
     return b.value
+
+
+def pinn_set_chunk_points(h: int, points: int):
+    check(load().pinn_set_chunk_points(h, points), h)
 
 
 def pinn_set_ff_matrix(h: int, d_B: int):

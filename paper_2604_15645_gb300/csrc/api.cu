@@ -71,13 +71,27 @@ pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   q.nbpart = (int)std::min<int64_t>(256, std::max<int64_t>(1, q.NC / 8192));
+  q.recompute = (h->spec.flags & PINN_FLAG_RECOMPUTE) != 0;
   if (h->spec.ff_m) {
     q.A[0] = take((size_t)2 * h->spec.ff_m * q.NC * q.es);
     if (q.lo) q.Alo[0] = take((size_t)2 * h->spec.ff_m * q.NP * q.lo_es);
   }
+  size_t abuf[2] = {0, 0}, alobuf[2] = {0, 0};
+  if (q.recompute) {
+    // two activation buffers shared by all hidden layers; A_l lives in buffer l % 2
+    for (int k = 0; k < 2; ++k) {
+      abuf[k] = take((size_t)h->w_max * q.NC * q.es);
+      if (q.lo) alobuf[k] = take((size_t)h->w_max * q.NP * q.lo_es);
+    }
+  }
   for (int l = 1; l <= L; ++l) {
-    q.A[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
-    if (q.lo) q.Alo[l] = take((size_t)h->spec.widths[l - 1] * q.NP * q.lo_es);
+    if (q.recompute) {
+      q.A[l] = abuf[l % 2];
+      q.Alo[l] = alobuf[l % 2];
+    } else {
+      q.A[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
+      if (q.lo) q.Alo[l] = take((size_t)h->spec.widths[l - 1] * q.NP * q.lo_es);
+    }
     q.Z[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
   }
   q.Zbar[0] = take((size_t)h->w_max * q.NC * q.es);
@@ -159,23 +173,23 @@ pinn_status validate_batch(pinn_handle* h, const pinn_batch* b) {
   return PINN_OK;
 }
 
-pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params, void* d_ws,
-                size_t ws_bytes, double* d_loss, float* d_grad, void* stream, bool want_grad) {
-  if (!h) return PINN_ERR_INVALID_ARG;
-  if (!prob || !d_params || !d_ws || !d_loss || (want_grad && !d_grad)) {
-    set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG;
-  }
-  if (reinterpret_cast<uintptr_t>(d_ws) % 256) { set_err(h, "workspace must be 256-byte aligned"); return PINN_ERR_INVALID_ARG; }
-  pinn_status s = validate_batch(h, b);
-  if (s) return s;
-  if (h->spec.ff_m && !h->ff_B) { set_err(h, "Fourier-feature matrix not set (pinn_set_ff_matrix)"); return PINN_ERR_INVALID_ARG; }
+// How one call is split into passes over point chunks, and what each pass adds to.
+struct PassCtx {
+  int64_t N_res, N_ic, N_bc;   // the batch's full counts: every mean is normalised by these
+  bool first, last;            // first pass starts the loss/gradient sums; last one writes the loss
+  double* loss_acc;            // 5 FP64 running loss sums (chunked calls only)
+};
+
+// One forward + reverse sweep over the points of `b` (the whole batch, or one chunk).
+pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
+                     char* ws, size_t ws_bytes, double* d_loss, float* d_grad, cudaStream_t st, bool want_grad,
+                     const PassCtx& pc) {
+  pinn_status s = PINN_OK;
   CallPlan cp;
   plan_call(h, b->n_res, b->n_ic, b->n_bc, &cp);
   if (ws_bytes < cp.p.total) {
     set_err(h, "workspace too small: %zu < %zu bytes", ws_bytes, cp.p.total); return PINN_ERR_WORKSPACE;
   }
-  cudaStream_t st = (cudaStream_t)stream;
-  char* ws = (char*)d_ws;
   const Plan& p = cp.p;
   const int L = h->L, L1 = L + 1, prec = h->spec.precision;
   const int mode = h->jet_mode;
@@ -234,9 +248,9 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   oa.n_res = p.n_res; oa.n_ic = p.n_ic; oa.n_bc = p.n_bc; oa.NP = p.NP; oa.NC = p.NC;
   oa.w = cp.lay[L].fin; oa.d_out = h->d_out; oa.pde = h->spec.pde; oa.jet_mode = mode;
   oa.nu = (float)prob->nu;
-  oa.k_pde = p.n_res ? (float)(prob->lambda_pde / (double)p.n_res) : 0.f;
-  oa.k_ic = p.n_ic ? (float)(prob->lambda_ic / (double)p.n_ic) : 0.f;
-  oa.k_bc = p.n_bc ? (float)(prob->lambda_bc / (double)p.n_bc) : 0.f;
+  oa.k_pde = pc.N_res ? (float)(prob->lambda_pde / (double)pc.N_res) : 0.f;
+  oa.k_ic = pc.N_ic ? (float)(prob->lambda_ic / (double)pc.N_ic) : 0.f;
+  oa.k_bc = pc.N_bc ? (float)(prob->lambda_bc / (double)pc.N_bc) : 0.f;
   oa.want_grad = want_grad;
   oa.Ubar = reinterpret_cast<float*>(ws + p.Ubar);
   oa.Zbar = ws + p.Zbar[L % 2];
@@ -245,8 +259,9 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   { PhaseScope ps(h, st, PH_OUT, 1); launch_out_loss(oa, prec, p.nloss_blocks, st); }
   {
   PhaseScope ps_fl(h, st, PH_RED, 1);
-  launch_finalize_loss(oa.losspart, p.nloss_blocks, p.n_res, (b->ic_mask ? p.n_ic : 0), (b->bc_mask ? p.n_bc : 0),
-                       prob->lambda_pde, prob->lambda_ic, prob->lambda_bc, d_loss, h->d_status, st);
+  launch_finalize_loss(oa.losspart, p.nloss_blocks, pc.N_res, (b->ic_mask ? pc.N_ic : 0), (b->bc_mask ? pc.N_bc : 0),
+                       prob->lambda_pde, prob->lambda_ic, prob->lambda_bc, d_loss, pc.loss_acc, pc.first, pc.last,
+                       h->d_status, st);
   }
   if (!want_grad) return cuda_check(h, cudaGetLastError(), "loss launch");
 
@@ -267,6 +282,11 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
     const LayerPlan& lp = cp.lay[li];
     void* zb = ws + p.Zbar[(li + 1) % 2];
     const bool raw = (li == 0 && !h->spec.ff_m);
+    if (p.recompute && li >= 1 && li <= L - 2) {
+      // A_li's buffer has since held A_{li+2}: rebuild it from the stored Z_li
+      PhaseScope ps(h, st, PH_OTHER, 1);
+      launch_jet_recompute(ws + p.Z[li], ws + p.A[li], lp.fin, p.NP, mode, prec, st);
+    }
     if (!raw) {
       PhaseScope ps(h, st, PH_DW, 1);
       if (cp.tc[li]) {
@@ -305,7 +325,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   // 7. Ordered FP64 reduction + RWF chain rule into the packed gradient.
   FinalizeArgs fa{};
   fa.params = d_params; fa.grad = d_grad; fa.ws = ws; fa.L1 = L1; fa.rwf = h->spec.rwf;
-  fa.first_raw = !h->spec.ff_m; fa.nbpart = p.nbpart;
+  fa.first_raw = !h->spec.ff_m; fa.nbpart = p.nbpart; fa.accumulate = pc.first ? 0 : 1;
   for (int li = 0; li < L1; ++li) {
     fa.fin[li] = cp.lay[li].fin; fa.fout[li] = cp.lay[li].fout;
     fa.offV[li] = cp.lay[li].off_V; fa.offs[li] = cp.lay[li].off_s; fa.offb[li] = cp.lay[li].off_b;
@@ -318,9 +338,121 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   return cuda_check(h, cudaGetLastError(), "loss_grad launch");
 }
 
+// Staging area of a chunked call: the loss accumulator, then compact copies of one
+// chunk's coordinates and targets, then the chunk's own pass workspace.
+struct ChunkLayout {
+  int64_t C = 0;                       // points per chunk
+  size_t acc = 0, x_res = 0, x_ic = 0, g_ic = 0, x_bc = 0, g_bc = 0;
+  size_t pass = 0;                     // offset of the pass workspace
+};
+
+ChunkLayout chunk_layout(const pinn_handle* h, int64_t C) {
+  ChunkLayout c;
+  c.C = C;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  c.acc = take(8 * sizeof(double));
+  c.x_res = take((size_t)h->d_in * C * 4);
+  c.x_ic = take((size_t)h->d_in * C * 4);
+  c.g_ic = take((size_t)h->d_out * C * 4);
+  c.x_bc = take((size_t)h->d_in * C * 4);
+  c.g_bc = take((size_t)h->d_out * C * 4);
+  c.pass = off;
+  return c;
+}
+
+// Point range [s, e) of the concatenated order (interior, initial, boundary) split per set.
+struct ChunkRange { int64_t r0, nr, i0, ni, b0, nb; };
+ChunkRange chunk_range(int64_t s, int64_t e, int64_t n_res, int64_t n_ic, int64_t n_bc) {
+  auto clip = [](int64_t s, int64_t e, int64_t lo, int64_t n, int64_t& start, int64_t& cnt) {
+    const int64_t a = std::max(s, lo), b = std::min(e, lo + n);
+    start = a - lo;
+    cnt = std::max<int64_t>(0, b - a);
+  };
+  ChunkRange r;
+  clip(s, e, 0, n_res, r.r0, r.nr);
+  clip(s, e, n_res, n_ic, r.i0, r.ni);
+  clip(s, e, n_res + n_ic, n_bc, r.b0, r.nb);
+  return r;
+}
+
+size_t chunked_bytes(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc) {
+  const int64_t C = h->chunk_points, N = n_res + n_ic + n_bc;
+  const ChunkLayout cl = chunk_layout(h, C);
+  size_t need = 0;
+  for (int64_t s = 0; s < N; s += C) {
+    const ChunkRange r = chunk_range(s, std::min(N, s + C), n_res, n_ic, n_bc);
+    CallPlan cp;
+    plan_call(h, r.nr, r.ni, r.nb, &cp);
+    need = std::max(need, cp.p.total);
+  }
+  return cl.pass + need;
+}
+
+// Copy rows [start, start + cnt) of a [rows][ld] FP32 array into a compact [rows][cnt] one.
+cudaError_t copy_rows(float* dst, const float* src, int rows, int64_t ld, int64_t start, int64_t cnt, cudaStream_t st) {
+  if (cnt == 0 || rows == 0 || !src) return cudaSuccess;
+  return cudaMemcpy2DAsync(dst, (size_t)cnt * 4, src + start, (size_t)ld * 4, (size_t)cnt * 4, (size_t)rows,
+                           cudaMemcpyDeviceToDevice, st);
+}
+
+pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params, void* d_ws,
+                size_t ws_bytes, double* d_loss, float* d_grad, void* stream, bool want_grad) {
+  if (!h) return PINN_ERR_INVALID_ARG;
+  if (!prob || !d_params || !d_ws || !d_loss || (want_grad && !d_grad)) {
+    set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG;
+  }
+  if (reinterpret_cast<uintptr_t>(d_ws) % 256) { set_err(h, "workspace must be 256-byte aligned"); return PINN_ERR_INVALID_ARG; }
+  pinn_status s = validate_batch(h, b);
+  if (s) return s;
+  if (h->spec.ff_m && !h->ff_B) { set_err(h, "Fourier-feature matrix not set (pinn_set_ff_matrix)"); return PINN_ERR_INVALID_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  const int64_t N = b->n_res + b->n_ic + b->n_bc;
+  PassCtx pc{b->n_res, b->n_ic, b->n_bc, true, true, nullptr};
+  if (h->chunk_points <= 0 || N <= h->chunk_points)
+    return run_pass(h, prob, b, d_params, ws, ws_bytes, d_loss, d_grad, st, want_grad, pc);
+
+  const int64_t C = h->chunk_points;
+  const size_t need = chunked_bytes(h, b->n_res, b->n_ic, b->n_bc);
+  if (ws_bytes < need) { set_err(h, "workspace too small: %zu < %zu bytes", ws_bytes, need); return PINN_ERR_WORKSPACE; }
+  const ChunkLayout cl = chunk_layout(h, C);
+  pc.loss_acc = reinterpret_cast<double*>(ws + cl.acc);
+  for (int64_t s0 = 0; s0 < N; s0 += C) {
+    const int64_t s1 = std::min(N, s0 + C);
+    const ChunkRange r = chunk_range(s0, s1, b->n_res, b->n_ic, b->n_bc);
+    pinn_batch cb = *b;
+    cb.n_res = r.nr; cb.n_ic = r.ni; cb.n_bc = r.nb;
+    cb.x_res = reinterpret_cast<float*>(ws + cl.x_res);
+    cb.x_ic = reinterpret_cast<float*>(ws + cl.x_ic);
+    cb.g_ic = reinterpret_cast<float*>(ws + cl.g_ic);
+    cb.x_bc = reinterpret_cast<float*>(ws + cl.x_bc);
+    cb.g_bc = reinterpret_cast<float*>(ws + cl.g_bc);
+    cudaError_t e = copy_rows(const_cast<float*>(cb.x_res), b->x_res, h->d_in, b->n_res, r.r0, r.nr, st);
+    if (e == cudaSuccess) e = copy_rows(const_cast<float*>(cb.x_ic), b->x_ic, h->d_in, b->n_ic, r.i0, r.ni, st);
+    if (e == cudaSuccess && b->ic_mask)
+      e = copy_rows(const_cast<float*>(cb.g_ic), b->g_ic, h->d_out, b->n_ic, r.i0, r.ni, st);
+    if (e == cudaSuccess) e = copy_rows(const_cast<float*>(cb.x_bc), b->x_bc, h->d_in, b->n_bc, r.b0, r.nb, st);
+    if (e == cudaSuccess && b->bc_mask)
+      e = copy_rows(const_cast<float*>(cb.g_bc), b->g_bc, h->d_out, b->n_bc, r.b0, r.nb, st);
+    if (e != cudaSuccess) return cuda_check(h, e, "chunk staging copy");
+    pc.first = (s0 == 0);
+    pc.last = (s1 == N);
+    s = run_pass(h, prob, &cb, d_params, ws + cl.pass, ws_bytes - cl.pass, d_loss, d_grad, st, want_grad, pc);
+    if (s) return s;
+  }
+  return PINN_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+pinn_status pinn_set_chunk_points(pinn_handle* h, int64_t points) {
+  if (!h || points < 0) return PINN_ERR_INVALID_ARG;
+  h->chunk_points = (int64_t)align_up((size_t)points, PT_ALIGN);
+  return PINN_OK;
+}
 
 pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
   if (!spec || !out) return PINN_ERR_INVALID_ARG;
@@ -332,7 +464,7 @@ pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
   if (spec->ff_m < 0 || spec->ff_m > 2048) return PINN_ERR_INVALID_ARG;
   if (spec->rwf != 0 && spec->rwf != 1) return PINN_ERR_INVALID_ARG;
   if (spec->precision < PINN_FP32 || spec->precision > PINN_BF16) return PINN_ERR_INVALID_ARG;
-  if (spec->flags & ~PINN_FLAG_CUDA_CORES) return PINN_ERR_INVALID_ARG;
+  if (spec->flags & ~(PINN_FLAG_CUDA_CORES | PINN_FLAG_RECOMPUTE)) return PINN_ERR_INVALID_ARG;
   pinn_handle* h = new (std::nothrow) pinn_handle();
   if (!h) return PINN_ERR_INVALID_ARG;
   h->spec = *spec;
@@ -388,6 +520,11 @@ pinn_status pinn_param_count(const pinn_handle* h, int64_t* P) {
 
 pinn_status pinn_workspace_bytes(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc, size_t* bytes) {
   if (!h || !bytes || n_res < 0 || n_ic < 0 || n_bc < 0) return PINN_ERR_INVALID_ARG;
+  const int64_t N = n_res + n_ic + n_bc;
+  if (h->chunk_points > 0 && N > h->chunk_points) {
+    *bytes = chunked_bytes(h, n_res, n_ic, n_bc);
+    return PINN_OK;
+  }
   CallPlan cp;
   plan_call(h, n_res, n_ic, n_bc, &cp);
   *bytes = cp.p.total;

@@ -46,6 +46,7 @@ struct Plan {
   int es = 4;          // bytes per element of the compute type (2 bf16, 4 fp32/tf32)
   bool lo = false;     // BF16 / TF32: value rows also keep a low half in Alo
   int lo_es = 2;       // bytes per low-half element (BF16 2, TF32 4)
+  bool recompute = false;   // A_l for l >= 1 live in two ping-pong buffers (PINN_FLAG_RECOMPUTE)
   size_t A[PINN_MAX_HIDDEN + 1] = {};   // A_l^T [w_l][NC] compute type, l = 0..L (A_0 only with FF)
   size_t Alo[PINN_MAX_HIDDEN + 1] = {}; // low half of the value rows, tile-major [NP/64][w_l][64]
   size_t Z[PINN_MAX_HIDDEN + 1] = {};   // Z_l^T [w_l][NC] compute type, l = 1..L
@@ -71,6 +72,7 @@ struct pinn_handle {
   int* d_status = nullptr;   // device status word (bit 0 nonfinite, bit 1 timeout)
   int device = 0;
   int sm_count = 0;
+  int64_t chunk_points = 0;  // 0: one pass; else points per chunk (multiple of 64)
   char err[512] = {0};
   // phase profiler (pinn_set_profiling)
   bool prof = false;
@@ -173,10 +175,16 @@ struct FinalizeArgs {
   int dbstride[PINN_MAX_HIDDEN + 1];   // floats per (part, row) in dbpart: 1, or 1 + d_in for a raw-coordinate first layer
   int first_raw;                        // 1: layer 0 takes raw coordinates (its dW comes from dbpart too)
   int nbpart;
+  int accumulate;                       // 1: add into grad (later point chunks) instead of overwriting
 };
 void launch_finalize_grad(const FinalizeArgs& a, cudaStream_t st);
+// acc: 5 running FP64 sums carried across point chunks (first: start from zero;
+// last: normalise by the full counts and write `out`, else store the sums in acc).
 void launch_finalize_loss(const double* losspart, int nblocks, int64_t n_res, int64_t n_ic, int64_t n_bc,
-                          double lam_pde, double lam_ic, double lam_bc, double* out, int* status, cudaStream_t st);
+                          double lam_pde, double lam_ic, double lam_bc, double* out, double* acc, int first, int last,
+                          int* status, cudaStream_t st);
+// A = tanh-jet(Z), tile-major [w][NC], for the recompute policy.
+void launch_jet_recompute(const void* Z, void* A, int w, int64_t NP, int mode, int prec, cudaStream_t st);
 void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
                  float bc1, float bc2, cudaStream_t st);
 

@@ -564,6 +564,10 @@ __device__ __forceinline__ void block_sum_n(double v[N], double (*sh)[N]) {
       for (int k = 0; k < N; ++k) v[k] += sh[w][k];
 }
 
+__device__ __forceinline__ void put_grad(const FinalizeArgs& a, int64_t idx, float v) {
+  a.grad[idx] = a.accumulate ? a.grad[idx] + v : v;
+}
+
 __global__ void k_finalize_grad(FinalizeArgs a) {
   const int l = blockIdx.y, i = blockIdx.x;
   const int fin = a.fin[l], fout = a.fout[l];
@@ -616,7 +620,7 @@ __global__ void k_finalize_grad(FinalizeArgs a) {
         for (int gg = 1; gg < G; ++gg)
           for (int k = 0; k < 4; ++k) d[k] += shd[gg * ncol4 + q][k];
         for (int k = 0; k < 4; ++k) {
-          a.grad[a.offV[l] + (int64_t)i * fin + 4 * q + k] = (float)(d[k] * es);
+          put_grad(a, a.offV[l] + (int64_t)i * fin + 4 * q + k, (float)(d[k] * es));
           v[0] += d[k] * (double)W[4 * q + k];
         }
       }
@@ -631,7 +635,7 @@ __global__ void k_finalize_grad(FinalizeArgs a) {
         }
         const double dd[4] = {a0.value(), a1.value(), a2.value(), a3.value()};
         for (int k = 0; k < 4; ++k) {
-          a.grad[a.offV[l] + (int64_t)i * fin + j4 + k] = (float)(dd[k] * es);
+          put_grad(a, a.offV[l] + (int64_t)i * fin + j4 + k, (float)(dd[k] * es));
           v[0] += dd[k] * (double)W[j4 + k];
         }
       }
@@ -640,7 +644,7 @@ __global__ void k_finalize_grad(FinalizeArgs a) {
         Acc2 acc;
         for (int s = 0; s < ns; ++s) acc.add(part[s * sstride + (int64_t)i * fin + j]);
         const double dW = acc.value();
-        a.grad[a.offV[l] + (int64_t)i * fin + j] = (float)(dW * es);
+        put_grad(a, a.offV[l] + (int64_t)i * fin + j, (float)(dW * es));
         v[0] += dW * (double)W[j];
       }
     }
@@ -649,12 +653,12 @@ __global__ void k_finalize_grad(FinalizeArgs a) {
   if (threadIdx.x == 0) {
     if (raw) {
       for (int j = 0; j < fin && j < 3; ++j) {
-        a.grad[a.offV[l] + (int64_t)i * fin + j] = (float)(v[2 + j] * es);
+        put_grad(a, a.offV[l] + (int64_t)i * fin + j, (float)(v[2 + j] * es));
         v[0] += v[2 + j] * (double)W[j];
       }
     }
-    if (a.rwf) a.grad[a.offs[l] + i] = (float)v[0];
-    a.grad[a.offb[l] + i] = (float)v[1];
+    if (a.rwf) put_grad(a, a.offs[l] + i, (float)v[0]);
+    put_grad(a, a.offb[l] + i, (float)v[1]);
   }
 }
 
@@ -666,7 +670,8 @@ void launch_finalize_grad(const FinalizeArgs& a, cudaStream_t st) {
 }
 
 __global__ void k_finalize_loss(const double* part, int nblocks, int64_t n_res, int64_t n_ic, int64_t n_bc,
-                                double lam_pde, double lam_ic, double lam_bc, double* out, int* status) {
+                                double lam_pde, double lam_ic, double lam_bc, double* out, double* acc, int first,
+                                int last, int* status) {
   __shared__ double sh[5][256];
   double s[5] = {0, 0, 0, 0, 0};
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
@@ -679,9 +684,15 @@ __global__ void k_finalize_loss(const double* part, int nblocks, int64_t n_res, 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double e0 = n_res ? sh[0][0] / n_res : 0.0, e1 = n_res ? sh[1][0] / n_res : 0.0,
-                 e2 = n_res ? sh[2][0] / n_res : 0.0;
-    const double lic = n_ic ? sh[3][0] / n_ic : 0.0, lbc = n_bc ? sh[4][0] / n_bc : 0.0;
+    double t[5];
+    for (int i = 0; i < 5; ++i) t[i] = (first ? 0.0 : acc[i]) + sh[i][0];
+    if (!last) {
+      for (int i = 0; i < 5; ++i) acc[i] = t[i];
+      return;
+    }
+    // each term is a mean over its own set (Eqs. 10-12), summed over equations
+    const double e0 = n_res ? t[0] / n_res : 0.0, e1 = n_res ? t[1] / n_res : 0.0, e2 = n_res ? t[2] / n_res : 0.0;
+    const double lic = n_ic ? t[3] / n_ic : 0.0, lbc = n_bc ? t[4] / n_bc : 0.0;
     const double lpde = e0 + e1 + e2;
     const double tot = lam_pde * lpde + lam_ic * lic + lam_bc * lbc;
     out[0] = tot; out[1] = lpde; out[2] = e0; out[3] = e1; out[4] = e2; out[5] = lic; out[6] = lbc; out[7] = 0.0;
@@ -690,8 +701,43 @@ __global__ void k_finalize_loss(const double* part, int nblocks, int64_t n_res, 
 }
 
 void launch_finalize_loss(const double* part, int nblocks, int64_t n_res, int64_t n_ic, int64_t n_bc, double lam_pde,
-                          double lam_ic, double lam_bc, double* out, int* status, cudaStream_t st) {
-  k_finalize_loss<<<1, 256, 0, st>>>(part, nblocks, n_res, n_ic, n_bc, lam_pde, lam_ic, lam_bc, out, status);
+                          double lam_ic, double lam_bc, double* out, double* acc, int first, int last, int* status,
+                          cudaStream_t st) {
+  k_finalize_loss<<<1, 256, 0, st>>>(part, nblocks, n_res, n_ic, n_bc, lam_pde, lam_ic, lam_bc, out, acc, first, last,
+                                     status);
+}
+
+// ------------------------------------------------------------------------------------
+// Recompute policy: A = tanh-jet(Z) for one layer, 4 points per thread, tile-major.
+// ------------------------------------------------------------------------------------
+template <typename T, bool FAST>
+__global__ void k_jet_recompute(const T* Z, T* A, int w, int64_t NP, int mode) {
+  const int f = blockIdx.y;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < NP / 4; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p0 = 4 * q;                                   // 4 points inside one 64-point tile
+    const int64_t c0 = (int64_t)TILE_COLS * (p0 / TILE_PTS) + (p0 % TILE_PTS);
+    float z[4][4], a[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) load4<T>(Z + toff(f, c0 + 64 * r, w), z[r]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float zz[4] = {z[0][k], z[1][k], z[2][k], z[3][k]}, aa[4];
+      jet_fwd<FAST>(zz, aa, mode);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r][k] = aa[r];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) store4<T>(A + toff(f, c0 + 64 * r, w), a[r]);
+  }
+}
+
+void launch_jet_recompute(const void* Z, void* A, int w, int64_t NP, int mode, int prec, cudaStream_t st) {
+  dim3 grid((unsigned)std::min<int64_t>((NP / 4 + 255) / 256, 4096), w);
+  if (prec == PINN_BF16)
+    k_jet_recompute<__nv_bfloat16, true><<<grid, 256, 0, st>>>((const __nv_bfloat16*)Z, (__nv_bfloat16*)A, w, NP,
+                                                               mode);
+  else
+    k_jet_recompute<float, false><<<grid, 256, 0, st>>>((const float*)Z, (float*)A, w, NP, mode);
 }
 
 // ------------------------------------------------------------------------------------

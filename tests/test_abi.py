@@ -52,7 +52,7 @@ def test_struct_layout_matches_header():
 
 
 @pytest.mark.parametrize("field,value", [("pde", 7), ("n_hidden", 0), ("n_hidden", 17), ("ff_m", -1),
-                                         ("rwf", 2), ("precision", 5), ("flags", 2)])
+                                         ("rwf", 2), ("precision", 5), ("flags", 4)])
 def test_invalid_spec_rejected_on_host(lib, field, value):
     spec = _lib.make_spec(1, [64, 64], 8, True, _lib.PINN_BF16)
     setattr(spec, field, value)
@@ -68,5 +68,6 @@ def test_invalid_width_and_null_args(lib):
     assert lib.pinn_create(None, C.byref(h)) == 1
     assert lib.pinn_param_count(None, None) == 1
     assert lib.pinn_destroy(None) == 0
+    assert lib.pinn_set_chunk_points(None, 64) == 1
     # Adam argument checks happen before any device work
     assert lib.pinn_adam_step(None, None, None, None, 10, 1, 1e-3, 0.9, 0.999, 1e-8, None) == 1
