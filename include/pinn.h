@@ -62,7 +62,8 @@ typedef enum {
 
 typedef enum {
   PINN_FP32 = 0,   /* jet GEMMs in FP32 on CUDA cores                            */
-  PINN_TF32 = 1,   /* jet GEMMs on tensor cores, TF32 inputs, FP32 accumulation  */
+  PINN_TF32 = 1,   /* jet GEMMs on tensor cores, TF32 inputs, FP32 accumulation;
+                      forward / adjoint add both truncation remainders (3 MMAs)  */
   PINN_BF16 = 2    /* jet GEMMs on tensor cores, BF16 inputs, FP32 accumulation  */
 } pinn_precision;
 

@@ -65,8 +65,8 @@ pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   q.NP = (int64_t)align_up((size_t)std::max<int64_t>(n_res + n_ic + n_bc, 1), PT_ALIGN);
   q.NC = 4 * q.NP;
   q.es = (h->spec.precision == PINN_BF16) ? 2 : 4;
-  q.lo = (h->spec.precision == PINN_BF16 || h->spec.precision == PINN_TF32);
-  q.lo_es = (h->spec.precision == PINN_BF16) ? 2 : 4;
+  q.lo = (h->spec.precision == PINN_BF16);
+  q.lo_es = 2;
   const int L = h->L;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -115,6 +115,9 @@ struct CallPlan {
   bool tc[PINN_MAX_HIDDEN + 1];      // layer li runs its jet GEMMs on tensor cores
   bool fused_db[PINN_MAX_HIDDEN + 1];  // layer li's bias partials come from a fused adjoint epilogue
   int nbpart[PINN_MAX_HIDDEN + 1];     // bias partial count of layer li
+  bool pm = false;                     // TF32 on tensor cores: point-major operand copies
+  size_t apm[2] = {0, 0};              // point-major A_l, buffer l % 2 ([NC][fin] FP32)
+  size_t zbpm[2] = {0, 0};             // point-major adjoints, ping-pong like Zbar
 };
 
 pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc, CallPlan* c) {
@@ -125,6 +128,13 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   for (int li = 0; li < L1; ++li) {
     const bool raw = (li == 0 && !h->spec.ff_m);
     c->tc[li] = li < h->L && !raw && tc_layer_supported(h, li, c->p.NC);
+  }
+  if (h->spec.precision == PINN_TF32) {
+    // TF32 tensor-core layers hand point-major operands to each other: all or none
+    bool all = true;
+    for (int li = h->first_gemm; li < h->L; ++li) all = all && c->tc[li];
+    for (int li = 0; li < L1; ++li) c->tc[li] = c->tc[li] && all;
+    c->pm = all && h->first_gemm < h->L;
   }
   for (int li = 0; li < L1; ++li) {
     LayerPlan lp = h->layers[li];
@@ -153,7 +163,14 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
     c->nbpart[li] = c->fused_db[li] ? (int)(c->p.NC / TC_BN) * TC_DB_PARTS : c->p.nbpart;
     const int dbs = raw ? 1 + h->d_in : 1;
     lp.dbpart = take((size_t)c->nbpart[li] * lp.fout * dbs * 4);
+    lp.wtlo = take((size_t)lp.fin * lp.fout * c->p.es);
     c->lay[li] = lp;
+  }
+  if (c->pm) {
+    int fin_max = 0;
+    for (int li = h->first_gemm; li < h->L; ++li) fin_max = std::max(fin_max, h->layers[li].fin);
+    for (int k = 0; k < 2; ++k) c->apm[k] = take((size_t)fin_max * c->p.NC * 4);
+    for (int k = 0; k < 2; ++k) c->zbpm[k] = take((size_t)h->w_max * c->p.NC * 4);
   }
   c->p.total = off;
   return PINN_OK;
@@ -201,7 +218,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     ra.fin[li] = cp.lay[li].fin; ra.fout[li] = cp.lay[li].fout;
     ra.offV[li] = cp.lay[li].off_V; ra.offs[li] = cp.lay[li].off_s;
     ra.w32[li] = cp.lay[li].w32; ra.wc[li] = cp.lay[li].wc; ra.wtc[li] = cp.lay[li].wtc;
-    ra.wt32[li] = cp.lay[li].wt32; ra.wlo[li] = cp.lay[li].wlo;
+    ra.wt32[li] = cp.lay[li].wt32; ra.wlo[li] = cp.lay[li].wlo; ra.wtlo[li] = cp.lay[li].wtlo;
   }
   { PhaseScope ps(h, st, PH_RWF, 1); launch_rwf_prep(ra, st); }
 
@@ -219,6 +236,10 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
                        cp.lay[0].fout, mode, ws + p.A[1], p.lo ? ws + p.Alo[1] : nullptr, ws + p.Z[1], p.NP, prec,
                        st);
   }
+  if (cp.pm) {
+    const int f0 = h->first_gemm;
+    launch_to_point_major(ws + p.A[f0], ws + cp.apm[f0 % 2], cp.lay[f0].fin, p.NC, st);
+  }
   }
 
   // 3. Hidden jet GEMMs with the tanh-jet epilogue.
@@ -231,7 +252,13 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     e.alo_in = (p.lo && prec == PINN_BF16) ? ws + p.Alo[li] : nullptr;
     e.jet_mode = mode;
     PhaseScope ps(h, st, PH_FWD, 1);
-    if (cp.tc[li]) {
+    if (cp.tc[li] && cp.pm) {
+      // TF32: point-major input; the epilogue also writes the next layer's point-major input
+      e.out_pm = (li + 1 < L) ? ws + cp.apm[(li + 1) % 2] : nullptr;
+      s = tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + cp.lay[li].wlo, ws + cp.apm[li % 2], nullptr, cp.lay[li].fout,
+                      cp.lay[li].fin, p.NC, e, st);
+      if (s) return s;
+    } else if (cp.tc[li]) {
       s = tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + cp.lay[li].wlo, ws + p.A[li], ws + p.Alo[li], cp.lay[li].fout,
                       cp.lay[li].fin, p.NC, e, st);
       if (s) return s;
@@ -264,6 +291,10 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
                        h->d_status, st);
   }
   if (!want_grad) return cuda_check(h, cudaGetLastError(), "loss launch");
+  if (cp.pm) {
+    PhaseScope ps(h, st, PH_OTHER, 1);
+    launch_to_point_major(ws + p.Zbar[L % 2], ws + cp.zbpm[L % 2], cp.lay[L].fin, p.NC, st);
+  }
 
   // 5. Output layer gradient: dW = Ubar^T A_L, db = sum of value-column seeds.
   {
@@ -313,8 +344,12 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
         e.n_res = p.n_res; e.n_ic = p.n_ic; e.n_bc = p.n_bc;
       }
       PhaseScope ps(h, st, PH_ADJ, 1);
-      if (cp.tc[li]) {
-        s = tc_gemm_adj(h, ws + lp.wtc, zb, lp.fin, lp.fout, p.NC, e, st);
+      if (cp.tc[li] && cp.pm) {
+        e.out_pm = (li - 1 >= 1) ? ws + cp.zbpm[li % 2] : nullptr;
+        s = tc_gemm_adj(h, ws + lp.wtc, ws + lp.wtlo, ws + cp.zbpm[(li + 1) % 2], lp.fin, lp.fout, p.NC, e, st);
+        if (s) return s;
+      } else if (cp.tc[li]) {
+        s = tc_gemm_adj(h, ws + lp.wtc, nullptr, zb, lp.fin, lp.fout, p.NC, e, st);
         if (s) return s;
       } else {
         launch_simt_gemm_adj(reinterpret_cast<const float*>(ws + lp.wt32), zb, lp.fin, lp.fout, p.NP, e, prec, st);

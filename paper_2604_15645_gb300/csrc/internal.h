@@ -32,7 +32,8 @@ struct LayerPlan {
   size_t wc = 0;       // W in compute type [fout][fin]
   size_t wtc = 0;      // W^T in compute type [fin][fout]
   size_t wt32 = 0;     // W^T fp32 [fin][fout]
-  size_t wlo = 0;      // BF16 only: W - bf16(W) rounded to bf16 [fout][fin] (second half of the split weight)
+  size_t wlo = 0;      // W - hi(W) in the compute type [fout][fin] (second half of the split weight)
+  size_t wtlo = 0;     // its transpose [fin][fout] (TF32 adjoint)
   size_t dwpart = 0;   // dW split partials fp32 [nsplit][fout][fin]
   size_t dbpart = 0;   // db partials fp32 [nbpart][fout]
   int nsplit = 1;
@@ -93,7 +94,7 @@ struct RwfArgs {
   int fin[PINN_MAX_HIDDEN + 1], fout[PINN_MAX_HIDDEN + 1];
   int64_t offV[PINN_MAX_HIDDEN + 1], offs[PINN_MAX_HIDDEN + 1];
   size_t w32[PINN_MAX_HIDDEN + 1], wc[PINN_MAX_HIDDEN + 1], wtc[PINN_MAX_HIDDEN + 1];
-  size_t wt32[PINN_MAX_HIDDEN + 1], wlo[PINN_MAX_HIDDEN + 1];
+  size_t wt32[PINN_MAX_HIDDEN + 1], wlo[PINN_MAX_HIDDEN + 1], wtlo[PINN_MAX_HIDDEN + 1];
 };
 void launch_rwf_prep(const RwfArgs& a, cudaStream_t st);
 
@@ -112,6 +113,7 @@ struct EpiArgs {
   void* alo_out;          // fwd, BF16: low half of A_l's value rows [M][NP] (else nullptr)
   const void* alo_in;     // fwd, CUDA-core BF16 path: low half of the input's value rows [K][NP]
   const void* zin;        // adj: Z_{l-1}^T (compute type)
+  void* out_pm;           // TF32 tensor-core path: point-major copy of `out`, [NC][M] FP32 (nullptr = none)
   int jet_mode;
   // adjoint only: bias-gradient partials of the layer whose pre-activation adjoint
   // this epilogue writes ([part][M][1 + dterms]; nullptr = not fused), and for a
@@ -183,6 +185,8 @@ void launch_finalize_grad(const FinalizeArgs& a, cudaStream_t st);
 void launch_finalize_loss(const double* losspart, int nblocks, int64_t n_res, int64_t n_ic, int64_t n_bc,
                           double lam_pde, double lam_ic, double lam_bc, double* out, double* acc, int first, int last,
                           int* status, cudaStream_t st);
+// Tile-major [w][NC] FP32 -> point-major [NC][w] (TF32 tensor-core operand layout).
+void launch_to_point_major(const void* src, void* dst, int w, int64_t NC, cudaStream_t st);
 // A = tanh-jet(Z), tile-major [w][NC], for the recompute policy.
 void launch_jet_recompute(const void* Z, void* A, int w, int64_t NP, int mode, int prec, cudaStream_t st);
 void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,

@@ -27,6 +27,7 @@ __global__ void k_rwf_prep(RwfArgs a) {
   T* WTc = reinterpret_cast<T*>(a.ws + a.wtc[l]);
   float* WT32 = reinterpret_cast<float*>(a.ws + a.wt32[l]);
   T* Wlo = reinterpret_cast<T*>(a.ws + a.wlo[l]);
+  T* WTlo = reinterpret_cast<T*>(a.ws + a.wtlo[l]);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx / fin), j = (int)(idx % fin);
     float w = V[idx];
@@ -36,7 +37,9 @@ __global__ void k_rwf_prep(RwfArgs a) {
     const float whf = (a.prec == PINN_TF32) ? tf32_trunc(w) : to_f<T>(from_f<T>(w));
     const T wh = from_f<T>(whf);
     Wc[idx] = wh;
-    Wlo[idx] = from_f<T>(w - whf);
+    const T wl = from_f<T>(w - whf);
+    Wlo[idx] = wl;
+    WTlo[(int64_t)j * fout + i] = wl;
     WTc[(int64_t)j * fout + i] = wh;
     WT32[(int64_t)j * fout + i] = w;
   }
@@ -48,20 +51,14 @@ void launch_rwf_prep(const RwfArgs& a, cudaStream_t st) {
   else k_rwf_prep<float><<<grid, 256, 0, st>>>(a);
 }
 
-// Low half of a value-row entry: BF16 storage keeps v - bf16(v) (rounded to BF16);
-// TF32 keeps v - trunc_tf32(v) in FP32 (read only by the tensor-core forward).
-// LO: 0 none, 1 BF16, 2 TF32.
+// Low half of a value-row entry stored in BF16: v - bf16(v), itself rounded to BF16.
 template <int LO>
 __device__ __forceinline__ void store_lo4(void* base, int64_t off, const float v[4]) {
-  float lo[4];
-  if (LO == 1) {
+  if (LO) {
+    float lo[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) lo[k] = v[k] - __bfloat162float(__float2bfloat16_rn(v[k]));
     store4<__nv_bfloat16>(reinterpret_cast<__nv_bfloat16*>(base) + off, lo);
-  } else if (LO == 2) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) lo[k] = v[k] - tf32_trunc(v[k]);
-    store4<float>(reinterpret_cast<float*>(base) + off, lo);
   }
 }
 
@@ -128,9 +125,6 @@ void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, i
   if (prec == PINN_BF16)
     k_embed_ff<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode,
                                                        (__nv_bfloat16*)A0, A0lo, NP);
-  else if (prec == PINN_TF32 && A0lo)
-    k_embed_ff<float, 2><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode, (float*)A0,
-                                               A0lo, NP);
   else
     k_embed_ff<float, 0><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m, mode,
                                                (float*)A0, nullptr, NP);
@@ -190,9 +184,6 @@ void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc
   if (prec == PINN_BF16)
     k_first_layer<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout,
                                                           mode, (__nv_bfloat16*)A1, A1lo, (__nv_bfloat16*)Z1, NP);
-  else if (prec == PINN_TF32 && A1lo)
-    k_first_layer<float, 2><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
-                                                  (float*)A1, A1lo, (float*)Z1, NP);
   else
     k_first_layer<float, 0><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
                                                   (float*)A1, nullptr, (float*)Z1, NP);
@@ -705,6 +696,30 @@ void launch_finalize_loss(const double* part, int nblocks, int64_t n_res, int64_
                           cudaStream_t st) {
   k_finalize_loss<<<1, 256, 0, st>>>(part, nblocks, n_res, n_ic, n_bc, lam_pde, lam_ic, lam_bc, out, acc, first, last,
                                      status);
+}
+
+// ------------------------------------------------------------------------------------
+// Tile-major [w][NC] FP32 -> point-major [NC][w] (the TF32 tensor-core operand layout),
+// through a padded shared-memory tile of 32 features x 64 columns; both sides coalesced.
+// ------------------------------------------------------------------------------------
+__global__ void k_to_point_major(const float* __restrict__ src, float* __restrict__ dst, int w, int64_t NC) {
+  __shared__ float t[32][65];
+  const int64_t c0 = (int64_t)blockIdx.x * 64;   // 64 columns inside one 256-column tile
+  const int f0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // 256 threads: 64 x 4
+  for (int fy = ty; fy < 32; fy += 4) {
+    const int f = f0 + fy;
+    t[fy][tx] = f < w ? src[toff(f, c0 + tx, w)] : 0.f;
+  }
+  __syncthreads();
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;   // 32 x 8
+  for (int cy = ly; cy < 64; cy += 8)
+    if (f0 + lx < w) dst[(c0 + cy) * w + f0 + lx] = t[lx][cy];
+}
+
+void launch_to_point_major(const void* src, void* dst, int w, int64_t NC, cudaStream_t st) {
+  dim3 grid((unsigned)(NC / 64), (unsigned)((w + 31) / 32));
+  k_to_point_major<<<grid, 256, 0, st>>>((const float*)src, (float*)dst, w, NC);
 }
 
 // ------------------------------------------------------------------------------------

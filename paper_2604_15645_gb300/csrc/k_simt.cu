@@ -126,15 +126,10 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
     if (EPI == 0) {
       T* zrow = reinterpret_cast<T*>(e.zout) + toff(f, n0 + 4 * tx, M);
       for (int r = 0; r < 4; ++r) store4<T>(zrow + 64 * r, zz[r]);
-      if (e.alo_out) {
-        if (sizeof(T) == 2) {
-          __nv_bfloat16* lo = reinterpret_cast<__nv_bfloat16*>(e.alo_out) + loff(f, tile * TILE_PTS + 4 * tx, M);
-          for (int j = 0; j < 4; ++j)
-            lo[j] = __float2bfloat16_rn(o[0][j] - __bfloat162float(__float2bfloat16_rn(o[0][j])));
-        } else {   // TF32: remainder after truncation, read only by the tensor-core forward
-          float* lo = reinterpret_cast<float*>(e.alo_out) + loff(f, tile * TILE_PTS + 4 * tx, M);
-          for (int j = 0; j < 4; ++j) lo[j] = o[0][j] - tf32_trunc(o[0][j]);
-        }
+      if (sizeof(T) == 2 && e.alo_out) {
+        __nv_bfloat16* lo = reinterpret_cast<__nv_bfloat16*>(e.alo_out) + loff(f, tile * TILE_PTS + 4 * tx, M);
+        for (int j = 0; j < 4; ++j)
+          lo[j] = __float2bfloat16_rn(o[0][j] - __bfloat162float(__float2bfloat16_rn(o[0][j])));
       }
     }
   }

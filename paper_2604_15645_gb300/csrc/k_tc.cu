@@ -14,11 +14,17 @@
 // cross-thread exchange.  On the BF16 path the forward also adds the low half of
 // the weights (all columns) and of the input's value rows (the 64 value columns).
 //
-// Warp roles per CTA (320 threads, one CTA per SM, persistent over tiles):
+// TF32 (kind::tf32) reads both operands K-major only, so its forward and adjoint take
+// the jets from a point-major copy [NC][features] (written by the epilogue of the
+// layer before) and add both truncation remainders: W_hi B + W_lo B + W_hi B_lo, with
+// B_lo = B - tf32(B) computed in shared memory by two converter warps.
+//
+// Warp roles per CTA (320 threads, 384 with converters, one CTA per SM, persistent):
 //   warp 0     TMA producer (one lane)
 //   warp 1     TMEM allocator + MMA issuer (one lane)
 //   warps 2-9  epilogue; warp w reads TMEM lanes 32*(w%4) .. +31 and handles the
 //              points 32*((w-2)/4) .. +31 of the tile, 16 at a time
+//   warps 10-11 (TF32 forward / adjoint only) B_lo converters
 // Two accumulator buffers of 256 columns let the epilogue of one tile overlap the
 // MMAs of the next.  Every mbarrier wait is bounded (global timer); on expiry the
 // CTA latches PINN_ERR_TIMEOUT in the status word, stops issuing work, waits for
@@ -39,7 +45,6 @@ namespace {
 constexpr int BM = 128;          // accumulator rows (TMEM lanes)
 constexpr int BN = 256;          // accumulator columns per buffer
 constexpr int EPI_WARPS = 8;     // two warps per TMEM lane quadrant, each on 32 of a tile's 64 points
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
 
 enum TcMode { TC_FWD = 0, TC_ADJ = 1, TC_DW = 2, TC_STORE = 3 };
@@ -217,17 +222,23 @@ struct Cfg {
   static constexpr int UK = TF32 ? 8 : 16;        // K per MMA instruction
   static constexpr int A_BYTES = BM * 128;        // 16 KB
   static constexpr int B_BYTES = BN * 128;        // 32 KB
-  // Forward only: low half of the input's value rows, one 64-column MN-major box.
-  static constexpr bool VLO = (MODE == TC_FWD);
+  // TF32 forward / adjoint: B from the point-major copy (K-major, 2-D map), its low
+  // half computed in shared memory (one B-sized buffer).
+  static constexpr bool KPM = TF32 && (MODE == TC_FWD || MODE == TC_ADJ);
+  static constexpr int BLOC_BYTES = KPM ? B_BYTES : 0;
+  static constexpr int CVT_WARPS = KPM ? 2 : 0;
+  static constexpr int NTHREADS = 64 + 32 * (EPI_WARPS + CVT_WARPS);
+  // BF16 forward: low half of the input's value rows, 64 MN-major columns per stage.
+  static constexpr bool VLO = (MODE == TC_FWD) && !TF32;
   static constexpr int BLO_BYTES = VLO ? TILE_PTS * 128 : 0;   // 8 KB
   static constexpr int STAGE = A_BYTES * (SPLIT ? 2 : 1) + B_BYTES + BLO_BYTES;
   static constexpr int STAGES = (MODE == TC_FWD || SPLIT) ? 3 : 4;
-  static_assert(STAGES * STAGE + 1024 + 256 <= 227 * 1024, "shared memory budget");
-  static constexpr bool B_MN = (MODE != TC_DW);
+  static_assert(STAGES * STAGE + BLOC_BYTES + 1024 + 256 <= 227 * 1024, "shared memory budget");
+  static constexpr bool B_MN = (MODE != TC_DW) && !KPM;
   static constexpr int BOXN = 128 / ES;           // MN-major box width (columns)
   static constexpr int NBOX = BN / BOXN;
   static constexpr int BOX_BYTES = BKE * 128;     // one MN-major box: BKE rows of 128 bytes
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE + BLOC_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 };
 
 template <typename T>
@@ -304,9 +315,19 @@ __device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, fl
   }
 }
 
+// Point-major copy [NC][M] of one thread's 16 points x 4 rows of feature m: column
+// c0 + 64 r + i.  Lanes hold consecutive features, so each store instruction writes
+// 128 contiguous bytes.
+__device__ __forceinline__ void store_pm(float* pm, int64_t c0, int M, int m, const float v[4][16]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) pm[(c0 + 64 * r + i) * M + m] = v[r][i];
+}
+
 // ---- the kernel -----------------------------------------------------------------------
 template <bool TF32, int MODE, bool SPLIT>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
               const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
               const TcParams p) {
@@ -314,11 +335,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   using T = typename std::conditional<TF32, float, __nv_bfloat16>::type;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint8_t* blo = smem + C::STAGES * C::STAGE;          // TF32 B_lo buffer (BLOC_BYTES)
+  uint64_t* full = reinterpret_cast<uint64_t*>(blo + C::BLOC_BYTES);
   uint64_t* empty = full + C::STAGES;
   uint64_t* acc_full = empty + C::STAGES;
   uint64_t* acc_empty = acc_full + 2;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(acc_empty + 2);
+  uint64_t* lo_full = acc_empty + 2;                  // converter -> MMA: B_lo ready
+  uint64_t* lo_empty = lo_full + 1;                   // MMA -> converter: B_lo consumed
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(lo_empty + 1);
   volatile int* inflight = abort_flag + 1;             // [STAGES]: parity+1 of an armed, unconsumed stage
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int*>(inflight + C::STAGES));
 
@@ -333,6 +357,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 32 * EPI_WARPS);
     }
+    mbar_init(lo_full, 1);
+    mbar_init(lo_empty, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -377,7 +403,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           mbar_expect_tx(&full[stage], C::STAGE);
           inflight[stage] = (int)phase + 1;
           const int kx = kb * C::BKE;
-          if (C::B_MN) {
+          if (C::KPM) {
+            // A: weights [M][K]; B: point-major jets [NC][K], columns nb*BN.. (both 2-D, K-major)
+            tma_load_2d(sa, &mapA, &full[stage], kx, mb * BM);
+            if (SPLIT) tma_load_2d(sa2, &mapA2, &full[stage], kx, mb * BM);
+            tma_load_2d(sb, &mapB, &full[stage], kx, nb * BN);
+          } else if (C::B_MN) {
             // A: weights [M][K] (2-D); B: jet tile nb, rows kx..kx+BKE (3-D, tile-major)
             tma_load_2d(sa, &mapA, &full[stage], kx, mb * BM);
             if (SPLIT) tma_load_2d(sa2, &mapA2, &full[stage], kx, mb * BM);
@@ -405,7 +436,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = make_idesc(TF32 ? 2u : 1u, C::B_MN ? 1u : 0u);
       int stage = 0;
-      uint32_t phase = 0;
+      uint32_t phase = 0, lo_phase = 0;
       int local = 0;
       for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++local) {
         int mb, nb, k0, k1;
@@ -436,6 +467,17 @@ __global__ void __launch_bounds__(THREADS, 1)
               tc_mma<TF32>(d, ad, make_desc(sb + C::B_BYTES + kk * C::UK * 128, C::BOX_BYTES, 1024), idesc64, 1u);
             }
           }
+          if (C::KPM) {
+            // TF32: D += W_hi . B_lo once the converters have written B_lo
+            if (!mbar_wait(lo_full, lo_phase, abort_flag, p.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sbl = smem_u32(blo);
+#pragma unroll
+            for (int kk = 0; kk < C::BKE / C::UK; ++kk)
+              tc_mma<TF32>(d, make_desc(sa + kk * 32, 16, 1024), make_desc(sbl + kk * 32, 16, 1024), idesc, 1u);
+            tc_commit(lo_empty);
+            lo_phase ^= 1;
+          }
           tc_commit(&empty[stage]);
           if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
         }
@@ -443,7 +485,37 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc_commit(&acc_full[buf]);
       }
     }
-  } else {
+  } else if (C::KPM && warp >= 2 + EPI_WARPS) {
+    // ---------------------------------------------------------------- TF32 B_lo converters
+    // B_lo = B - tf32(B), elementwise over the stage's B tile (layout-agnostic), into
+    // the single B_lo buffer once the MMAs of the previous stage have released it.
+    const int ct = threadIdx.x - 32 * (2 + EPI_WARPS);
+    int stage = 0;
+    uint32_t phase = 0, lo_phase = 0;
+    for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+      int mb, nb, k0, k1;
+      coords(t, mb, nb, k0, k1);
+      bool ok = true;
+      for (int kb = k0; kb < k1; ++kb) {
+        if (!mbar_wait(&full[stage], phase, abort_flag, p.status) ||
+            !mbar_wait(lo_empty, lo_phase ^ 1, abort_flag, p.status)) { ok = false; break; }
+        const float4* src = reinterpret_cast<const float4*>(smem + stage * C::STAGE + C::A_BYTES * (SPLIT ? 2 : 1));
+        float4* dst = reinterpret_cast<float4*>(blo);
+#pragma unroll 4
+        for (int i = ct; i < C::B_BYTES / 16; i += 32 * C::CVT_WARPS) {
+          float4 x = src[i];
+          x.x -= tf32_trunc(x.x); x.y -= tf32_trunc(x.y); x.z -= tf32_trunc(x.z); x.w -= tf32_trunc(x.w);
+          dst[i] = x;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * C::CVT_WARPS) : "memory");
+        if (ct == 0) mbar_arrive(lo_full);
+        lo_phase ^= 1;
+        if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+      }
+      if (!ok) break;
+    }
+  } else if (warp < 2 + EPI_WARPS) {
     // ---------------------------------------------------------------- epilogue
     // Warp part pt handles points 16 pt .. 16 pt + 15 of the tile: the four 16-column
     // chunks at columns 16 pt + 64 r (jet row r), so every thread holds whole points.
@@ -501,6 +573,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           T* ao = reinterpret_cast<T*>(p.e.out) + cbase;
 #pragma unroll
           for (int r = 0; r < 4; ++r) st16(ao + 64 * r, v[r]);
+          if (TF32 && p.e.out_pm) store_pm(reinterpret_cast<float*>(p.e.out_pm), (int64_t)nb * BN + 16 * pt, p.M, m, v);
           if (p.e.alo_out) {
             // low half of the value rows for the next forward: BF16 rounding / TF32 truncation remainder
             float lo[16];
@@ -530,6 +603,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           T* zbo = reinterpret_cast<T*>(p.e.out) + cbase;
 #pragma unroll
           for (int r = 0; r < 4; ++r) st16(zbo + 64 * r, v[r]);
+          if (TF32 && p.e.out_pm) store_pm(reinterpret_cast<float*>(p.e.out_pm), (int64_t)nb * BN + 16 * pt, p.M, m, v);
           if (p.e.dbpart) {
             // bias gradient of the layer below (value rows) and, for a first layer on
             // raw coordinates, the coordinate terms of its weight gradient
@@ -653,7 +727,7 @@ pinn_status launch(pinn_handle* h, const CUtensorMap& a, const CUtensorMap& a2, 
     }
     attr_set = true;
   }
-  kern<<<grid, THREADS, C::SMEM, st>>>(a, a2, b, blo, p);
+  kern<<<grid, C::NTHREADS, C::SMEM, st>>>(a, a2, b, blo, p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(h->err, sizeof(h->err), "tcgen05 kernel launch: %s", cudaGetErrorString(e));
@@ -678,9 +752,7 @@ void tc_init(pinn_handle* h) {
 }
 
 bool tc_layer_supported(const pinn_handle* h, int li, int64_t NC) {
-  // kind::tf32 reads both operands K-major only, and the forward / adjoint B operand
-  // (the jets) is MN-major in this layout: only BF16 runs these GEMMs on tensor cores.
-  if (!g_encode || h->spec.precision != PINN_BF16 || (h->spec.flags & PINN_FLAG_CUDA_CORES)) return false;
+  if (!g_encode || h->spec.precision == PINN_FP32 || (h->spec.flags & PINN_FLAG_CUDA_CORES)) return false;
   if (NC % BN) return false;
   const int fin = h->layers[li].fin, fout = h->layers[li].fout;
   // TMA row strides must be multiples of 16 bytes: fin and fout multiples of 8 elements.
@@ -727,25 +799,40 @@ pinn_status fwd_impl(pinn_handle* h, const void* W, const void* Wlo, const void*
   const uint64_t nt = (uint64_t)(NC / TILE_COLS);
   if (!make_map(&ma, W, TF32, fin, fout, C::BKE, BM) || !make_map(&ma2, Wlo, TF32, fin, fout, C::BKE, BM))
     return map_err(h, "forward weights");
-  if (!make_map3(&mb, A, TF32, TILE_COLS, fin, nt, C::BOXN, C::BKE)) return map_err(h, "forward activations");
-  if (!make_map3(&mlo, Alo, TF32, TILE_PTS, fin, nt, C::BOXN, C::BKE))
-    return map_err(h, "forward value-row low half");
+  if (TF32) {
+    // point-major jets [NC][fin], K-major boxes of BKE features x BN columns
+    if (!make_map(&mb, A, true, fin, (uint64_t)NC, C::BKE, BN)) return map_err(h, "forward activations");
+    mlo = mb;
+  } else {
+    if (!make_map3(&mb, A, false, TILE_COLS, fin, nt, C::BOXN, C::BKE)) return map_err(h, "forward activations");
+    if (!make_map3(&mlo, Alo, false, TILE_PTS, fin, nt, C::BOXN, C::BKE))
+      return map_err(h, "forward value-row low half");
+  }
   TcParams p = base_params(fout, (int)NC, fin, NC, C::BKE, h->d_status);
   p.e = e;
   return launch<TF32, TC_FWD, true>(h, ma, ma2, mb, mlo, p, grid_for(h, p.m_tiles * p.n_tiles), st);
 }
 
 template <bool TF32>
-pinn_status adj_impl(pinn_handle* h, const void* WT, const void* Zbar, int fin, int fout, int64_t NC, const EpiArgs& e,
-                     cudaStream_t st) {
-  using C = Cfg<TF32, TC_ADJ, false>;
-  CUtensorMap ma, mb;
+pinn_status adj_impl(pinn_handle* h, const void* WT, const void* WTlo, const void* Zbar, int fin, int fout,
+                     int64_t NC, const EpiArgs& e, cudaStream_t st) {
+  // TF32: split weights and the point-major adjoint with its low half (three MMAs);
+  // BF16: high halves only.
+  constexpr bool SPLIT = TF32;
+  using C = Cfg<TF32, TC_ADJ, SPLIT>;
+  CUtensorMap ma, ma2, mb;
   if (!make_map(&ma, WT, TF32, fout, fin, C::BKE, BM)) return map_err(h, "adjoint weights");
-  if (!make_map3(&mb, Zbar, TF32, TILE_COLS, fout, (uint64_t)(NC / TILE_COLS), C::BOXN, C::BKE))
-    return map_err(h, "adjoint input");
+  ma2 = ma;
+  if (TF32) {
+    if (!make_map(&ma2, WTlo, true, fout, fin, C::BKE, BM)) return map_err(h, "adjoint weights (low half)");
+    if (!make_map(&mb, Zbar, true, fout, (uint64_t)NC, C::BKE, BN)) return map_err(h, "adjoint input");
+  } else {
+    if (!make_map3(&mb, Zbar, false, TILE_COLS, fout, (uint64_t)(NC / TILE_COLS), C::BOXN, C::BKE))
+      return map_err(h, "adjoint input");
+  }
   TcParams p = base_params(fin, (int)NC, fout, NC, C::BKE, h->d_status);
   p.e = e;
-  return launch<TF32, TC_ADJ, false>(h, ma, ma, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles), st);
+  return launch<TF32, TC_ADJ, SPLIT>(h, ma, ma2, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles), st);
 }
 
 template <bool TF32>
@@ -775,10 +862,10 @@ pinn_status tc_gemm_fwd(pinn_handle* h, const void* W, const void* Wlo, const vo
   return fwd_impl<false>(h, W, Wlo, A, Alo, fout, fin, NC, e, st);
 }
 
-pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fin, int fout, int64_t NC,
-                        const EpiArgs& e, cudaStream_t st) {
-  if (h->spec.precision == PINN_TF32) return adj_impl<true>(h, WT, Zbar, fin, fout, NC, e, st);
-  return adj_impl<false>(h, WT, Zbar, fin, fout, NC, e, st);
+pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* WTlo, const void* Zbar, int fin, int fout,
+                        int64_t NC, const EpiArgs& e, cudaStream_t st) {
+  if (h->spec.precision == PINN_TF32) return adj_impl<true>(h, WT, WTlo, Zbar, fin, fout, NC, e, st);
+  return adj_impl<false>(h, WT, WTlo, Zbar, fin, fout, NC, e, st);
 }
 
 pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout, int fin, int64_t NC, int nsplit,

@@ -16,13 +16,19 @@ constexpr int TC_BN = 256;
 // Number of K (column) splits of the tensor-core weight-gradient GEMM.
 int tc_dw_splits(const pinn_handle* h, int fout, int fin, int64_t NC);
 
-// Z = (W_hi + W_lo) A + W_hi A_lo (+ bias, tanh jet): W_hi, W_lo [fout][fin] BF16 (K-major),
-// A^T [fin][NC], A_lo [fin][NC/4] the low half of A's value rows.
+// Forward (+ bias, tanh jet), W_hi, W_lo [fout][fin] (K-major).
+//   BF16: Z = (W_hi + W_lo) A + W_hi A_lo, A^T [fin][NC] tile-major, A_lo [fin][NC/4]
+//         the low half of A's value rows.
+//   TF32: Z = (W_hi + W_lo) A + W_hi (A - tf32(A)), A point-major [NC][fin]; Alo unused;
+//         the epilogue also writes e.out_pm (point-major A_l) when set.
 pinn_status tc_gemm_fwd(pinn_handle* h, const void* W, const void* Wlo, const void* A, const void* Alo, int fout,
                         int fin, int64_t NC, const EpiArgs& e, cudaStream_t st);
-// Abar = W^T Zbar (tanh-jet adjoint epilogue): WT [fin][fout], Zbar^T [fout][NC].
-pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* Zbar, int fin, int fout, int64_t NC,
-                        const EpiArgs& e, cudaStream_t st);
+// Abar = W^T Zbar (tanh-jet adjoint epilogue), WT [fin][fout].
+//   BF16: Zbar^T [fout][NC] tile-major, high halves only (WTlo unused).
+//   TF32: (WT_hi + WT_lo) Zbar + WT_hi (Zbar - tf32(Zbar)), Zbar point-major [NC][fout];
+//         the epilogue also writes e.out_pm when set.
+pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* WTlo, const void* Zbar, int fin, int fout,
+                        int64_t NC, const EpiArgs& e, cudaStream_t st);
 // part[s] = Zbar^T A over column split s: Zbar^T [fout][NC], A^T [fin][NC] (both K-major).
 pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout, int fin, int64_t NC, int nsplit,
                        float* part, cudaStream_t st);

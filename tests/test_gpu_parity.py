@@ -51,9 +51,9 @@ def test_ragged_widths_and_weights(cuda_lib, precision):
     _check(spec, p, B, b, Problem(0.02, 0.3, 2.0, 5.0), precision, "ragged")
 
 
-@pytest.mark.parametrize("precision,expect_tc", [("fp32", False), ("tf32", False), ("bf16", True)])
+@pytest.mark.parametrize("precision,expect_tc", [("fp32", False), ("tf32", True), ("bf16", True)])
 def test_tensor_core_engine_selection(cuda_lib, precision, expect_tc):
-    # FP32 and TF32 run the exact CUDA-core GEMMs; BF16 runs every hidden layer on tcgen05
+    # FP32 runs the exact CUDA-core GEMMs; TF32 and BF16 run every hidden layer on tcgen05
     from paper_2604_15645_gb300 import api
     w, p, B, b = make_workload("ns_cavity_6x256", n_res=4096, n_bc=512)
     net = api.PinnNet.from_spec(w.spec, precision)
