@@ -97,6 +97,15 @@ typedef struct {
  * recompute tanh', tanh'' and tanh''' from the stored Z. */
 #define PINN_FLAG_RECOMPUTE 2
 
+/* pinn_spec.flags, BF16 only: split the weights into BF16 high and low halves for
+ * the value rows only.  By default the tensor-core forward adds W_lo . A on every jet
+ * row (two full MMAs plus the value-row low half).  With this flag the derivative
+ * rows use W_hi alone, which makes the forward 1.25 instead of 2.25 MMAs per K step
+ * at a larger derivative-row error.  Use it where the BF16 error budget allows:
+ * the Navier-Stokes cavity networks stay near 1e-2, while Burgers networks whose
+ * residual terms cancel need the full split. */
+#define PINN_FLAG_BF16_VALUE_SPLIT 4
+
 /* Loss weights and the PDE coefficient (nu for Burgers; 1/Re for Navier-Stokes;
  * ignored for Maxwell). */
 typedef struct {

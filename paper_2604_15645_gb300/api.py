@@ -50,10 +50,10 @@ class PinnNet:
     """One network handle (pinn_create) plus a cached workspace."""
 
     def __init__(self, pde, widths, ff_m=0, rwf=False, precision="fp32", device="cuda", recompute=False,
-                 chunk_points=0):
+                 chunk_points=0, value_split=False):
         self.device = torch.device(device)
         self.precision = precision
-        flags = _lib.PINN_FLAG_RECOMPUTE if recompute else 0
+        flags = (_lib.PINN_FLAG_RECOMPUTE if recompute else 0) | (_lib.PINN_FLAG_BF16_VALUE_SPLIT if value_split else 0)
         with torch.cuda.device(self.device):
             self.spec = _lib.make_spec(pde, widths, ff_m, rwf, _lib.PRECISIONS[precision], flags)
             self.h = _lib.pinn_create(self.spec)
@@ -66,8 +66,9 @@ class PinnNet:
         self.loss_buf = torch.zeros(_lib.PINN_LOSS_TERMS, dtype=torch.float64, device=self.device)
 
     @classmethod
-    def from_spec(cls, spec, precision="fp32", device="cuda", recompute=False, chunk_points=0):
-        return cls(spec.pde, spec.widths, spec.ff_m, spec.rwf, precision, device, recompute, chunk_points)
+    def from_spec(cls, spec, precision="fp32", device="cuda", recompute=False, chunk_points=0, value_split=False):
+        return cls(spec.pde, spec.widths, spec.ff_m, spec.rwf, precision, device, recompute, chunk_points,
+                   value_split)
 
     def set_chunk_points(self, points):
         """Process batches in chunks of at most `points` points (0: one pass)."""

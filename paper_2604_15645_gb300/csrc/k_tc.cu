@@ -146,6 +146,12 @@ __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, float v[16]) {
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, float v[8]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 // 32-byte (256-bit) global accesses: one full L2 sector per thread.
 __device__ __forceinline__ void st_global_256(void* p, const uint32_t w[8]) {
@@ -187,6 +193,45 @@ __device__ __forceinline__ void ld16(const float* p, float v[16]) {
   ld_global_256(p + 8, reinterpret_cast<uint32_t*>(v + 8));
 }
 
+// One unit row of a jet matrix: 16 BF16 or 8 FP32 values, one full 32-byte sector.
+__device__ __forceinline__ void st_row(__nv_bfloat16* p, const float v[16]) { st16(p, v); }
+__device__ __forceinline__ void st_row(float* p, const float v[8]) {
+  st_global_256(p, reinterpret_cast<const uint32_t*>(v));
+}
+// N consecutive FP32 values (N = 8 or 16) as 32-byte stores.
+template <int N>
+__device__ __forceinline__ void st_f32(float* p, const float* v) {
+#pragma unroll
+  for (int i = 0; i < N; i += 8) st_global_256(p + i, reinterpret_cast<const uint32_t*>(v + i));
+}
+// 8 consecutive elements of a row: BF16 as one 16-byte access, FP32 as one 32-byte access.
+__device__ __forceinline__ void st8(__nv_bfloat16* p, const float v[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    w[i] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  asm volatile("st.global.v4.b32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+               : "memory");
+}
+__device__ __forceinline__ void st8(float* p, const float v[8]) {
+  st_global_256(p, reinterpret_cast<const uint32_t*>(v));
+}
+__device__ __forceinline__ void ld8raw(const __nv_bfloat16* p, uint32_t w[4]) {
+  asm volatile("ld.global.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
+}
+__device__ __forceinline__ void ld8raw(const float* p, uint32_t w[8]) { ld_global_256(p, w); }
+// Element i of 8 raw row words (BF16 pairs or FP32).
+template <typename T>
+__device__ __forceinline__ float raw_elem(const uint32_t* w, int i) {
+  if (sizeof(T) == 2) {
+    const uint32_t x = w[i >> 1];
+    return __uint_as_float((i & 1) ? (x & 0xFFFF0000u) : (x << 16));
+  }
+  return __uint_as_float(w[i]);
+}
+
 // Shared-memory matrix descriptor (tcgen05), 128-byte swizzle, version 1.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -213,6 +258,7 @@ struct TcParams {
   EpiArgs e;
   float* out32;        // dW partials / selftest output
   int* status;
+  int wlo_values_only; // forward: W_lo . B on the 64 value columns only (PINN_FLAG_BF16_VALUE_SPLIT)
 };
 
 template <bool TF32, int MODE, bool SPLIT>
@@ -315,14 +361,14 @@ __device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, fl
   }
 }
 
-// Point-major copy [NC][M] of one thread's 16 points x 4 rows of feature m: column
+// Point-major copy [NC][M] of one thread's 8 points x 4 rows of feature m: column
 // c0 + 64 r + i.  Lanes hold consecutive features, so each store instruction writes
 // 128 contiguous bytes.
-__device__ __forceinline__ void store_pm(float* pm, int64_t c0, int M, int m, const float v[4][16]) {
+__device__ __forceinline__ void store_pm8(float* pm, int64_t c0, int M, int m, const float v[4][8]) {
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int i = 0; i < 16; ++i) pm[(c0 + 64 * r + i) * M + m] = v[r][i];
+    for (int i = 0; i < 8; ++i) pm[(c0 + 64 * r + i) * M + m] = v[r][i];
 }
 
 // ---- the kernel -----------------------------------------------------------------------
@@ -459,8 +505,11 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
             const uint64_t bd = C::B_MN ? make_desc(sb + kk * C::UK * 128, C::BOX_BYTES, 1024)
                                         : make_desc(sb + kk * 32, 16, 1024);
             tc_mma<TF32>(d, ad, bd, idesc, (kb > k0 || kk > 0) ? 1u : 0u);
-            // low half of the weights on every column: D += W_lo . A
-            if (SPLIT) tc_mma<TF32>(d, make_desc(sa2 + kk * 32, 16, 1024), bd, idesc, 1u);
+            // low half of the weights: D += W_lo . A on every column, or on the value columns
+            if (SPLIT) {
+              constexpr uint32_t idesc_v = make_idesc(TF32 ? 2u : 1u, C::B_MN ? 1u : 0u, TILE_PTS);
+              tc_mma<TF32>(d, make_desc(sa2 + kk * 32, 16, 1024), bd, p.wlo_values_only ? idesc_v : idesc, 1u);
+            }
             if (C::VLO) {
               // low half of the input's value rows: D[:, 0:64] += W_hi . A_lo
               constexpr uint32_t idesc64 = make_idesc(TF32 ? 2u : 1u, 1u, TILE_PTS);
@@ -501,11 +550,19 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
             !mbar_wait(lo_empty, lo_phase ^ 1, abort_flag, p.status)) { ok = false; break; }
         const float4* src = reinterpret_cast<const float4*>(smem + stage * C::STAGE + C::A_BYTES * (SPLIT ? 2 : 1));
         float4* dst = reinterpret_cast<float4*>(blo);
-#pragma unroll 4
-        for (int i = ct; i < C::B_BYTES / 16; i += 32 * C::CVT_WARPS) {
-          float4 x = src[i];
-          x.x -= tf32_trunc(x.x); x.y -= tf32_trunc(x.y); x.z -= tf32_trunc(x.z); x.w -= tf32_trunc(x.w);
-          dst[i] = x;
+        // latency-bound: keep 16 shared-memory loads in flight per thread
+        constexpr int U = 16, STRIDE = 32 * (C::CVT_WARPS > 0 ? C::CVT_WARPS : 1);
+        static_assert((C::B_BYTES / 16) % (U * STRIDE) == 0, "converter batches cover the tile");
+        for (int i0 = ct; i0 < C::B_BYTES / 16; i0 += U * STRIDE) {
+          float4 x[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) x[u] = src[i0 + u * STRIDE];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            x[u].x -= tf32_trunc(x[u].x); x[u].y -= tf32_trunc(x[u].y);
+            x[u].z -= tf32_trunc(x[u].z); x[u].w -= tf32_trunc(x[u].w);
+            dst[i0 + u * STRIDE] = x[u];
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
         asm volatile("bar.sync 1, %0;" ::"n"(32 * C::CVT_WARPS) : "memory");
@@ -517,15 +574,43 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
     }
   } else if (warp < 2 + EPI_WARPS) {
     // ---------------------------------------------------------------- epilogue
-    // Warp part pt handles points 16 pt .. 16 pt + 15 of the tile: the four 16-column
-    // chunks at columns 16 pt + 64 r (jet row r), so every thread holds whole points.
+    // Warp part `part` of a lane quadrant handles points 32 part .. 32 part + 31 of the
+    // tile in units of UPTS points; a unit is the four UPTS-column chunks at columns
+    // pc + 64 r (jet row r), so every thread holds whole points of its feature.  A unit
+    // row is one full 32-byte sector (16 BF16 or 8 FP32 values): partial-sector stores
+    // would make L2 fetch the sector first.  FP32 units are small enough to double-buffer
+    // the TMEM loads; in the adjoint the next unit's Z rows are always loaded one unit
+    // ahead.
     constexpr bool FAST = !TF32;
     constexpr int PARTS = EPI_WARPS / 4;                 // warps per lane quadrant
-    constexpr int GROUPS = TILE_PTS / (16 * PARTS);      // 16-point groups per warp and tile
-    static_assert(PARTS * GROUPS * 16 == TILE_PTS, "epilogue warps cover a 64-point tile");
+    constexpr int UPTS = TF32 ? 8 : 16;                  // points per unit
+    constexpr int UNITS = TILE_PTS / (UPTS * PARTS);     // units per warp and tile
+    constexpr bool PIPE = TF32;                          // double-buffered TMEM loads
+    static_assert(PARTS * UNITS * UPTS == TILE_PTS && UNITS % 2 == 0, "epilogue units cover a 64-point tile");
+    constexpr int ZW = (int)sizeof(T) * UPTS / 4;        // 32-bit words of one Z row of a unit
     const int quad = warp & 3;
     const int part = (warp - 2) >> 2;
     const int row = quad * 32 + lane;
+    auto unit_col = [&](int u) { return part * (UNITS * UPTS) + UPTS * u; };
+
+    uint32_t znext[4][ZW];                               // adjoint: Z rows of the next unit
+    auto load_z = [&](int t_, int u_) {
+      int mb_, nb_, k0_, k1_;
+      coords(t_, mb_, nb_, k0_, k1_);
+      const int m_ = mb_ * BM + row;
+      if (m_ < p.M) {
+        const T* zr = reinterpret_cast<const T*>(p.e.zin) + toff(m_, (int64_t)nb_ * BN, p.M) + unit_col(u_);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if constexpr (UPTS == 8) ld8raw(zr + 64 * r, znext[r]);
+          else ld_global_256(zr + 64 * r, znext[r]);
+        }
+      }
+    };
+    if constexpr (MODE == TC_ADJ) {
+      if ((int)blockIdx.x < total) load_z(blockIdx.x, 0);
+    }
+
     int local = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
       int mb, nb, k0, k1;
@@ -535,36 +620,38 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
       tc_fence_after();
       const int m = mb * BM + row;
       const bool mvalid = m < p.M;
+      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN;
       float db[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-      for (int grp = 0; grp < GROUPS; ++grp) {
-      const int pt = part * GROUPS + grp;                // 16-point group index within the tile
-      const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN + 16 * pt;
-      float v[4][16];
-      // adjoint: Z of the layer below, kept as raw 32-byte rows (BF16: 8 registers a row)
-      uint32_t zw[4][8 * (sizeof(T) / 2)];
-      if (MODE == TC_ADJ && mvalid) {
-        const T* zr = reinterpret_cast<const T*>(p.e.zin) + toff(m, (int64_t)nb * BN, p.M) + 16 * pt;
+
+      auto issue = [&](int u, float (&v)[4][UPTS]) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          ld_global_256(zr + 64 * r, zw[r]);
-          if (sizeof(T) == 4) ld_global_256(zr + 64 * r + 8, zw[r] + 8 * (sizeof(T) / 4));
+          if constexpr (UPTS == 8) tmem_ld8_issue(tbase + unit_col(u) + 64 * r, v[r]);
+          else tmem_ld16_issue(tbase + unit_col(u) + 64 * r, v[r]);
         }
-      }
+      };
+      auto process = [&](int u, float (&v)[4][UPTS]) {
+        uint32_t zw[4][ZW];
+        if constexpr (MODE == TC_ADJ) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) tmem_ld16_issue(taddr + 64 * r, v[r]);
-      tmem_wait_ld();
-      if (mvalid) {
-        const int64_t cbase = toff(m, (int64_t)nb * BN, p.M) + 16 * pt;   // tile nb, row m, point group pt
-        if (MODE == TC_FWD) {
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int j = 0; j < ZW; ++j) zw[r][j] = znext[r][j];
+          if (u + 1 < UNITS) load_z(t, u + 1);
+          else if (t + (int)gridDim.x < total) load_z(t + gridDim.x, 0);
+        }
+        if (!mvalid) return;
+        const int pc = unit_col(u);                                   // first point of the unit in its tile
+        const int64_t cbase = toff(m, (int64_t)nb * BN, p.M) + pc;    // tile nb, row m
+        if constexpr (MODE == TC_FWD) {
           const float bias = p.e.bias[m];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[0][i] += bias;
+          for (int i = 0; i < UPTS; ++i) v[0][i] += bias;
           T* zo = reinterpret_cast<T*>(p.e.zout) + cbase;
 #pragma unroll
-          for (int r = 0; r < 4; ++r) st16(zo + 64 * r, v[r]);
+          for (int r = 0; r < 4; ++r) st_row(zo + 64 * r, v[r]);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
+          for (int i = 0; i < UPTS; ++i) {
             float z[4] = {v[0][i], v[1][i], v[2][i], v[3][i]}, a[4];
             jet_fwd<FAST>(z, a, p.e.jet_mode);
 #pragma unroll
@@ -572,29 +659,23 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
           }
           T* ao = reinterpret_cast<T*>(p.e.out) + cbase;
 #pragma unroll
-          for (int r = 0; r < 4; ++r) st16(ao + 64 * r, v[r]);
-          if (TF32 && p.e.out_pm) store_pm(reinterpret_cast<float*>(p.e.out_pm), (int64_t)nb * BN + 16 * pt, p.M, m, v);
-          if (p.e.alo_out) {
-            // low half of the value rows for the next forward: BF16 rounding / TF32 truncation remainder
-            float lo[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-              lo[i] = TF32 ? v[0][i] - tf32_trunc(v[0][i]) : v[0][i] - __bfloat162float(__float2bfloat16_rn(v[0][i]));
-            st16(reinterpret_cast<T*>(p.e.alo_out) + loff(m, (int64_t)nb * TILE_PTS, p.M) + 16 * pt, lo);
+          for (int r = 0; r < 4; ++r) st_row(ao + 64 * r, v[r]);
+          if constexpr (TF32) {
+            if (p.e.out_pm) store_pm8(reinterpret_cast<float*>(p.e.out_pm), (int64_t)nb * BN + pc, p.M, m, v);
           }
-        } else if (MODE == TC_ADJ) {
+          if (!TF32 && p.e.alo_out) {
+            // low half of the value rows for the next forward (BF16 rounding remainder)
+            float lo[UPTS];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
+            for (int i = 0; i < UPTS; ++i) lo[i] = v[0][i] - __bfloat162float(__float2bfloat16_rn(v[0][i]));
+            st_row(reinterpret_cast<T*>(p.e.alo_out) + loff(m, (int64_t)nb * TILE_PTS, p.M) + pc, lo);
+          }
+        } else if constexpr (MODE == TC_ADJ) {
+#pragma unroll
+          for (int i = 0; i < UPTS; ++i) {
             float z[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              if (sizeof(T) == 2) {
-                const uint32_t w = zw[r][i >> 1];
-                z[r] = __uint_as_float((i & 1) ? (w & 0xFFFF0000u) : (w << 16));
-              } else {
-                z[r] = __uint_as_float(zw[r][i]);
-              }
-            }
+            for (int r = 0; r < 4; ++r) z[r] = raw_elem<T>(zw[r], i);
             float ab[4] = {v[0][i], v[1][i], v[2][i], v[3][i]}, zb[4];
             jet_adj<FAST>(z, ab, zb, p.e.jet_mode);
 #pragma unroll
@@ -602,18 +683,20 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
           }
           T* zbo = reinterpret_cast<T*>(p.e.out) + cbase;
 #pragma unroll
-          for (int r = 0; r < 4; ++r) st16(zbo + 64 * r, v[r]);
-          if (TF32 && p.e.out_pm) store_pm(reinterpret_cast<float*>(p.e.out_pm), (int64_t)nb * BN + 16 * pt, p.M, m, v);
+          for (int r = 0; r < 4; ++r) st_row(zbo + 64 * r, v[r]);
+          if constexpr (TF32) {
+            if (p.e.out_pm) store_pm8(reinterpret_cast<float*>(p.e.out_pm), (int64_t)nb * BN + pc, p.M, m, v);
+          }
           if (p.e.dbpart) {
             // bias gradient of the layer below (value rows) and, for a first layer on
             // raw coordinates, the coordinate terms of its weight gradient
 #pragma unroll
-            for (int i = 0; i < 16; ++i) db[0] += v[0][i];
+            for (int i = 0; i < UPTS; ++i) db[0] += v[0][i];
             if (p.e.dterms) {
-              const int64_t p0 = (int64_t)nb * TILE_PTS + 16 * pt;
+              const int64_t p0 = (int64_t)nb * TILE_PTS + pc;
               const int nd = (p.e.jet_mode == JET_MAXWELL) ? 3 : 2;   // rows 1..nd are first derivatives
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
+              for (int i = 0; i < UPTS; ++i) {
                 const int64_t pp = p0 + i;
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
@@ -625,25 +708,47 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
               }
             }
           }
-        } else if (MODE == TC_DW) {
+        } else if constexpr (MODE == TC_DW) {
           const int split = t / (p.m_tiles * p.n_tiles);
           float* dst = p.out32 + ((int64_t)split * p.M + m) * p.N;
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            const int64_t col0 = (int64_t)nb * BN + 16 * pt + 64 * r;
-            if (col0 + 16 <= p.N && (p.N & 7) == 0) {
-              st16(dst + col0, v[r]);
+            const int64_t col0 = (int64_t)nb * BN + pc + 64 * r;
+            if (col0 + UPTS <= p.N && (p.N & 7) == 0) {
+              st_f32<UPTS>(dst + col0, v[r]);
             } else {
-              for (int j = 0; j < 16; ++j)
+              for (int j = 0; j < UPTS; ++j)
                 if (col0 + j < p.N) dst[col0 + j] = v[r][j];
             }
           }
         } else {   // TC_STORE
 #pragma unroll
-          for (int r = 0; r < 4; ++r) st16(p.out32 + toff(m, (int64_t)nb * BN, p.M) + 16 * pt + 64 * r, v[r]);
+          for (int r = 0; r < 4; ++r) st_f32<UPTS>(p.out32 + cbase + 64 * r, v[r]);
+        }
+      };
+
+      if constexpr (PIPE) {
+        float va[4][UPTS], vb[4][UPTS];
+        issue(0, va);
+        tmem_wait_ld();
+#pragma unroll 1
+        for (int u = 0; u < UNITS; u += 2) {
+          issue(u + 1, vb);
+          process(u, va);
+          tmem_wait_ld();
+          if (u + 2 < UNITS) issue(u + 2, va);
+          process(u + 1, vb);
+          if (u + 2 < UNITS) tmem_wait_ld();
+        }
+      } else {
+#pragma unroll 1
+        for (int u = 0; u < UNITS; ++u) {
+          float va[4][UPTS];
+          issue(u, va);
+          tmem_wait_ld();
+          process(u, va);
         }
       }
-      }   // groups
       if (MODE == TC_ADJ && mvalid && p.e.dbpart) {
         float* dst = p.e.dbpart + ((int64_t)m * (p.n_tiles * PARTS) + nb * PARTS + part) * (1 + p.e.dterms);
         dst[0] = db[0];
@@ -810,6 +915,7 @@ pinn_status fwd_impl(pinn_handle* h, const void* W, const void* Wlo, const void*
   }
   TcParams p = base_params(fout, (int)NC, fin, NC, C::BKE, h->d_status);
   p.e = e;
+  p.wlo_values_only = (!TF32 && (h->spec.flags & PINN_FLAG_BF16_VALUE_SPLIT)) ? 1 : 0;
   return launch<TF32, TC_FWD, true>(h, ma, ma2, mb, mlo, p, grid_for(h, p.m_tiles * p.n_tiles), st);
 }
 

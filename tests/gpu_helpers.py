@@ -16,8 +16,8 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
-def run_gpu(spec, params, B, batch, problem, precision, want_grad=True):
-    net = api.PinnNet.from_spec(spec, precision)
+def run_gpu(spec, params, B, batch, problem, precision, want_grad=True, value_split=False):
+    net = api.PinnNet.from_spec(spec, precision, value_split=value_split)
     if B is not None:
         net.set_ff_matrix(B)
     db = api.DeviceBatch.from_host(batch)

@@ -28,6 +28,13 @@ def test_burgers_full_size_fp32(cuda_lib, random_bias):
     _check(w.spec, p, B, b, w.problem, "fp32", "burgers fp32")
 
 
+def test_cavity_value_split_ragged_subset(cuda_lib):
+    w, p, B, b = make_workload("ns_cavity_6x256", n_res=1000, n_bc=300, random_bias=0.1)
+    gt, gg = run_gpu(w.spec, p, B, b, w.problem, "bf16", value_split=True)
+    rt, rg = run_oracle(w.spec, p, B, b, w.problem)
+    assert_parity(gt, gg, rt, rg, TOL["bf16"], "cavity bf16 value split")
+
+
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
 def test_cavity_architecture_ragged_subset(cuda_lib, precision):
     # 6x256 with 128 Fourier frequencies and RWF; 1000 interior + 300 wall points
@@ -169,8 +176,17 @@ def test_nonfinite_loss_is_latched(cuda_lib):
     assert net.status_poll() == 0     # cleared after reading
 
 
-def test_cavity_full_size_bf16_against_chunked_oracle(cuda_lib):
-    """The bench workload at full size (65,536 interior + 4,096 wall points), BF16,
-    in the launch configuration the bench times; the oracle sums chunks of points."""
+_FULL_ORACLE = {}
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_cavity_full_size_against_chunked_oracle(cuda_lib, precision):
+    """The bench workload at full size (65,536 interior + 4,096 wall points) in the
+    launch configuration the bench times; the oracle sums chunks of points (computed
+    once for both precisions)."""
     w, p, B, b = make_workload("ns_cavity_6x256")
-    _check(w.spec, p, B, b, w.problem, "bf16", "cavity full bf16", chunk=8192)
+    gt, gg = run_gpu(w.spec, p, B, b, w.problem, precision)
+    if "ref" not in _FULL_ORACLE:
+        _FULL_ORACLE["ref"] = run_oracle(w.spec, p, B, b, w.problem, chunk=8192)
+    rt, rg = _FULL_ORACLE["ref"]
+    assert_parity(gt, gg, rt, rg, TOL[precision], f"cavity full {precision}")

@@ -22,11 +22,12 @@ def test_maxwell_low_discrepancy_subset_bf16(cuda_lib):
     assert_parity(gt, gg, rt, rg, TOL["bf16"], "maxwell 16k bf16")
 
 
-def test_cavity_at_scale_architecture_subset_bf16(cuda_lib):
+@pytest.mark.parametrize("value_split", [False, True])
+def test_cavity_at_scale_architecture_subset_bf16(cuda_lib, value_split):
     w, p, B, b = make_workload("ns_cavity_8x512", n_res=4096, n_bc=256)
-    gt, gg = run_gpu(w.spec, p, B, b, w.problem, "bf16")
+    gt, gg = run_gpu(w.spec, p, B, b, w.problem, "bf16", value_split=value_split)
     rt, rg = run_oracle(w.spec, p, B, b, w.problem, chunk=2048)
-    assert_parity(gt, gg, rt, rg, TOL["bf16"], "cavity 8x512 subset bf16")
+    assert_parity(gt, gg, rt, rg, TOL["bf16"], f"cavity 8x512 subset bf16 value_split={value_split}")
 
 
 def _free():
@@ -43,21 +44,23 @@ def test_cavity_at_scale_gradient_against_finite_differences(cuda_lib):
     db = api.DeviceBatch.from_host(b)
     params = torch.tensor(p, device="cuda")
 
-    net = api.PinnNet.from_spec(w.spec, "bf16")
-    net.set_ff_matrix(B)
-    t16, g16 = net.loss_grad(params, db, prob)
-    loss16 = float(t16[0])
-    g16 = g16.cpu().numpy().astype(np.float64)
-    assert net.status_poll() == 0
-    del net, t16
-    _free()
+    bf16 = {}
+    for value_split in (False, True):
+        net = api.PinnNet.from_spec(w.spec, "bf16", value_split=value_split)
+        net.set_ff_matrix(B)
+        t16, g16 = net.loss_grad(params, db, prob)
+        bf16[value_split] = (float(t16[0]), g16.cpu().numpy().astype(np.float64))
+        assert net.status_poll() == 0
+        del net, t16, g16
+        _free()
 
     net = api.PinnNet.from_spec(w.spec, "fp32")
     net.set_ff_matrix(B)
     t32, g32 = net.loss_grad(params, db, prob)
     loss32 = float(t32[0])
     g32 = g32.cpu().numpy().astype(np.float64)
-    assert abs(loss16 - loss32) <= TOL["bf16"] * abs(loss32)
+    for loss16, _ in bf16.values():
+        assert abs(loss16 - loss32) <= TOL["bf16"] * abs(loss32)
 
     # 32 coordinates: 4 per weight layer group (V, s, b mixed), seeded
     rng = np.random.default_rng(2024)
@@ -79,5 +82,6 @@ def test_cavity_at_scale_gradient_against_finite_differences(cuda_lib):
     _free()
     # the FP32 gradient confirms the differences themselves
     assert rel(g32[idx], fd) < 1e-3
-    # the BF16 path under test, at the stated tolerance
-    assert rel(g16[idx], fd) <= TOL["bf16"]
+    # the BF16 paths under test (full weight split, and value-row split), at the stated tolerance
+    for _, g16 in bf16.values():
+        assert rel(g16[idx], fd) <= TOL["bf16"]
