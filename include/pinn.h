@@ -78,7 +78,7 @@ typedef enum {
 typedef struct {
   int32_t pde;                       /* pinn_pde                                          */
   int32_t n_hidden;                  /* L, number of tanh layers, 1..PINN_MAX_HIDDEN      */
-  int32_t widths[PINN_MAX_HIDDEN];   /* widths[0..L-1], each 1..4096                      */
+  int32_t widths[PINN_MAX_HIDDEN];   /* widths[0..L-1], each 1..2048                      */
   int32_t ff_m;                      /* Fourier frequencies m (embedding width 2m), 0=none */
   int32_t rwf;                       /* 1: every layer is W = diag(exp(s)) V (Eq. 15)     */
   int32_t precision;                 /* pinn_precision of the hidden-layer jet GEMMs      */

@@ -96,7 +96,6 @@ pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   }
   q.Zbar[0] = take((size_t)h->w_max * q.NC * q.es);
   q.Zbar[1] = take((size_t)h->w_max * q.NC * q.es);
-  q.Ubar = take((size_t)h->d_out * q.NC * 4);
   q.nloss_blocks = out_loss_blocks(q.NP);
   q.losspart = take((size_t)q.nloss_blocks * 8 * sizeof(double));
   *p = q;
@@ -147,7 +146,7 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
     if (raw) {
       lp.nsplit = 0;
     } else if (li == h->L) {
-      lp.nsplit = std::min(4 * c->p.nbpart, 1024);   // output layer: column chunks of k_dw_out
+      lp.nsplit = c->p.nloss_blocks;   // output layer: one dW partial per output/loss block
     } else if (c->tc[li]) {
       lp.nsplit = tc_dw_splits(h, lp.fout, lp.fin, c->p.NC);
     } else {
@@ -156,11 +155,14 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
       ns = (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->p.NC / 512));
       lp.nsplit = ns;
     }
-    lp.dwpart = take((size_t)std::max(lp.nsplit, 0) * lp.fout * lp.fin * 4);
+    // the output layer keeps room for its compacted partials after the per-block ones
+    const int slots = std::max(lp.nsplit, 0) + (li == h->L ? OUT_SUM_SLOTS : 0);
+    lp.dwpart = take((size_t)slots * lp.fout * lp.fin * 4);
     // Bias partials of hidden layer li come from the tensor-core adjoint epilogue of
     // layer li+1 when that one runs on tensor cores, else from a row reduction.
     c->fused_db[li] = (li + 1 < h->L) && c->tc[li + 1];
-    c->nbpart[li] = c->fused_db[li] ? (int)(c->p.NC / TC_BN) * TC_DB_PARTS : c->p.nbpart;
+    c->nbpart[li] = li == h->L ? c->p.nloss_blocks
+                    : c->fused_db[li] ? (int)(c->p.NC / TC_BN) * TC_DB_PARTS : c->p.nbpart;
     const int dbs = raw ? 1 + h->d_in : 1;
     lp.dbpart = take((size_t)c->nbpart[li] * lp.fout * dbs * 4);
     lp.wtlo = take((size_t)lp.fin * lp.fout * c->p.es);
@@ -279,11 +281,16 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
   oa.k_ic = pc.N_ic ? (float)(prob->lambda_ic / (double)pc.N_ic) : 0.f;
   oa.k_bc = pc.N_bc ? (float)(prob->lambda_bc / (double)pc.N_bc) : 0.f;
   oa.want_grad = want_grad;
-  oa.Ubar = reinterpret_cast<float*>(ws + p.Ubar);
+  oa.dwpart = reinterpret_cast<float*>(ws + cp.lay[L].dwpart);
+  oa.dbpart = reinterpret_cast<float*>(ws + cp.lay[L].dbpart);
   oa.Zbar = ws + p.Zbar[L % 2];
   oa.losspart = reinterpret_cast<double*>(ws + p.losspart);
   oa.status = h->d_status;
-  { PhaseScope ps(h, st, PH_OUT, 1); launch_out_loss(oa, prec, p.nloss_blocks, st); }
+  {
+    PhaseScope ps(h, st, PH_OUT, 1);
+    const cudaError_t e = launch_out_loss(oa, prec, p.nloss_blocks, st);
+    if (e != cudaSuccess) return cuda_check(h, e, "output/loss launch");
+  }
   {
   PhaseScope ps_fl(h, st, PH_RED, 1);
   launch_finalize_loss(oa.losspart, p.nloss_blocks, pc.N_res, (b->ic_mask ? pc.N_ic : 0), (b->bc_mask ? pc.N_bc : 0),
@@ -296,16 +303,14 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     launch_to_point_major(ws + p.Zbar[L % 2], ws + cp.zbpm[L % 2], cp.lay[L].fin, p.NC, st);
   }
 
-  // 5. Output layer gradient: dW = Ubar^T A_L, db = sum of value-column seeds.
+  // 5. The output layer's dW and bias partials came from the output/loss kernel; its
+  //    per-block dW partials are compacted (in order) so the finalisation reads a few.
   {
-  {
-  PhaseScope ps(h, st, PH_DW, 1);
-  launch_dw_out(ws + p.A[L], reinterpret_cast<const float*>(ws + p.Ubar), cp.lay[L].fin, h->d_out, p.NC,
-                cp.lay[L].nsplit, reinterpret_cast<float*>(ws + cp.lay[L].dwpart), prec, st);
-  }
-  PhaseScope ps_r(h, st, PH_RED, 1);
-  launch_row_reduce(ws + p.Ubar, true, h->d_out, p.NP, p.n_res, p.n_ic, p.n_bc, p.nbpart, b->x_res, b->x_ic,
-                    b->x_bc, 0, mode, reinterpret_cast<float*>(ws + cp.lay[L].dbpart), prec, st);
+    PhaseScope ps(h, st, PH_RED, 1);
+    const LayerPlan& lo = cp.lay[L];
+    float* part = reinterpret_cast<float*>(ws + lo.dwpart);
+    launch_sum_splits(part, part + (size_t)lo.nsplit * lo.fout * lo.fin, lo.nsplit, OUT_SUM_SLOTS,
+                      (int64_t)lo.fout * lo.fin, st);
   }
 
   // 6. Hidden layers in reverse: dW, db, then the adjoint GEMM into the layer below.
@@ -366,7 +371,11 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     fa.offV[li] = cp.lay[li].off_V; fa.offs[li] = cp.lay[li].off_s; fa.offb[li] = cp.lay[li].off_b;
     fa.w32[li] = cp.lay[li].w32; fa.dwpart[li] = cp.lay[li].dwpart; fa.dbpart[li] = cp.lay[li].dbpart;
     fa.nsplit[li] = cp.lay[li].nsplit;
-    fa.nbpart_l[li] = li < L ? cp.nbpart[li] : p.nbpart;
+    if (li == L) {   // the compacted output-layer partials
+      fa.dwpart[li] += (size_t)cp.lay[li].nsplit * cp.lay[li].fout * cp.lay[li].fin * 4;
+      fa.nsplit[li] = OUT_SUM_SLOTS;
+    }
+    fa.nbpart_l[li] = cp.nbpart[li];
     fa.dbstride[li] = (li == 0 && fa.first_raw) ? 1 + h->d_in : 1;
   }
   { PhaseScope ps(h, st, PH_RED, 1); launch_finalize_grad(fa, st); }
@@ -495,7 +504,7 @@ pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
   if (spec->pde < 0 || spec->pde > 2) return PINN_ERR_INVALID_ARG;
   if (spec->n_hidden < 1 || spec->n_hidden > PINN_MAX_HIDDEN) return PINN_ERR_INVALID_ARG;
   for (int i = 0; i < spec->n_hidden; ++i)
-    if (spec->widths[i] < 1 || spec->widths[i] > 4096) return PINN_ERR_INVALID_ARG;
+    if (spec->widths[i] < 1 || spec->widths[i] > 2048) return PINN_ERR_INVALID_ARG;
   if (spec->ff_m < 0 || spec->ff_m > 2048) return PINN_ERR_INVALID_ARG;
   if (spec->rwf != 0 && spec->rwf != 1) return PINN_ERR_INVALID_ARG;
   if (spec->precision < PINN_FP32 || spec->precision > PINN_BF16) return PINN_ERR_INVALID_ARG;

@@ -52,7 +52,6 @@ struct Plan {
   size_t Alo[PINN_MAX_HIDDEN + 1] = {}; // low half of the value rows, tile-major [NP/64][w_l][64]
   size_t Z[PINN_MAX_HIDDEN + 1] = {};   // Z_l^T [w_l][NC] compute type, l = 1..L
   size_t Zbar[2] = {};                  // ping-pong adjoints [w_max][NC] compute type
-  size_t Ubar = 0;                      // output seeds [d_out][NC] fp32
   size_t losspart = 0;                  // per-block loss partials, double [nloss_blocks][8]
   int nloss_blocks = 0;
   int nbpart = 0;                       // column chunks of the bias/first-layer reductions
@@ -148,16 +147,15 @@ struct OutArgs {
   float nu;
   float k_pde, k_ic, k_bc;  // 2 lambda / N per set (adjoint seed scale)
   int want_grad;
-  float* Ubar;           // [d_out][NC]
+  float* dwpart;         // output-layer dW partials [nblocks][d_out][w] (per block, fixed order)
+  float* dbpart;         // output-layer bias partials [d_out][nblocks]
   void* Zbar;            // Zbar_L^T [w][NC] compute type
   double* losspart;      // [nblocks][8]
   int* status;
 };
-void launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st);
-// Output-layer weight gradient dW_out[c][f] = sum_col Ubar[c][col] A_L[f][col],
-// partials [nchunks][d_out][w].
-void launch_dw_out(const void* AL, const float* Ubar, int w, int d_out, int64_t NC, int nchunks, float* part,
-                   int prec, cudaStream_t st);
+// Output layer, residuals, loss partials and (want_grad) the adjoint seeds, Zbar_L
+// and the output layer's dW and bias partials, one block per 64-point tile stride.
+cudaError_t launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st);
 int out_loss_blocks(int64_t n_points);
 
 // Bias gradient partials of a layer from its pre-activation adjoint (value rows
@@ -185,6 +183,9 @@ void launch_finalize_grad(const FinalizeArgs& a, cudaStream_t st);
 void launch_finalize_loss(const double* losspart, int nblocks, int64_t n_res, int64_t n_ic, int64_t n_bc,
                           double lam_pde, double lam_ic, double lam_bc, double* out, double* acc, int first, int last,
                           int* status, cudaStream_t st);
+// Ordered compaction of S split partials [S][n] into S2 [S2][n] (out may not alias in).
+void launch_sum_splits(const float* in, float* out, int S, int S2, int64_t n, cudaStream_t st);
+constexpr int OUT_SUM_SLOTS = 16;   // output-layer dW partials after compaction
 // Tile-major [w][NC] FP32 -> point-major [NC][w] (TF32 tensor-core operand layout).
 void launch_to_point_major(const void* src, void* dst, int w, int64_t NC, cudaStream_t st);
 // A = tanh-jet(Z), tile-major [w][NC], for the recompute policy.

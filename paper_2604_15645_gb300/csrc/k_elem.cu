@@ -272,9 +272,11 @@ __device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_
 // outputs with three xor-shuffles; every slice then holds the group's outputs.
 template <typename T, int D, bool FAST>
 __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
-  extern __shared__ float sW[];   // [d_out][w]
+  extern __shared__ float sW[];   // [d_out][w] weights, then [warps][d_out][w] dW accumulators
   const int w = a.w;
+  float* sdw = sW + D * w;
   for (int i = threadIdx.x; i < D * w; i += blockDim.x) sW[i] = a.W[i];
+  for (int i = threadIdx.x; i < (OUT_THREADS / 32) * D * w; i += blockDim.x) sdw[i] = 0.f;
   __syncthreads();
   const T* AL = reinterpret_cast<const T*>(a.AL);
   const __nv_bfloat16* ALlo = reinterpret_cast<const __nv_bfloat16*>(a.ALlo);
@@ -285,6 +287,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   const int q0 = 16 * warp + 4 * pg;               // first of this thread's 4 points in the tile
   const int64_t NC = a.NC, ntiles = a.NP / TILE_PTS;
   double acc[5] = {0, 0, 0, 0, 0};
+  float dbo[3] = {0.f, 0.f, 0.f};                 // output bias gradient (value-row seeds)
   for (int64_t T0 = blockIdx.x; T0 < ntiles; T0 += gridDim.x) {
     const int64_t cb = T0 * TILE_COLS + q0;        // column of row 0 of the first point
     const int64_t p0 = T0 * TILE_PTS + q0;
@@ -343,21 +346,38 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
     if (sl == 0)
       for (int i = 0; i < 5; ++i) acc[i] += lacc[i];
     if (!a.want_grad) continue;
+    if (sl == 0) {
 #pragma unroll
-    for (int c = 0; c < D; ++c)
+      for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
-        if (((c * 4 + r) & 7) == sl) {
-          const float o[4] = {Ub[0][c][r], Ub[1][c][r], Ub[2][c][r], Ub[3][c][r]};
-          store4<float>(a.Ubar + toff(c, cb + 64 * r, D), o);
-        }
-    // abar_L = Ubar W_out (rank <= 3), then the tanh-jet adjoint with Z_L.
+        for (int j = 0; j < 4; ++j) dbo[c] += Ub[j][c][0];
+    }
+    // abar_L = Ubar W_out (rank <= 3), then the tanh-jet adjoint with Z_L; and the
+    // output layer's dW[c][f] = sum over the tile's columns of Ubar[c] A_L[f] (A_L
+    // read again, from L2).
 #pragma unroll 2
     for (int f = sl; f < w; f += 8) {
       float z[4][4], zb[4][4];                     // [row][point]
       const T* zrow = ZL + toff(f, cb, w);
 #pragma unroll
       for (int r = 0; r < 4; ++r) load4<T>(zrow + 64 * r, z[r]);
+      {
+        float av[4][4];
+        const T* arow = AL + toff(f, cb, w);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) load4<T>(arow + 64 * r, av[r]);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          float g = 0.f;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) g = fmaf(Ub[j][c][r], av[r][j], g);
+          g += __shfl_xor_sync(0xffffffffu, g, 8);    // the warp's four point groups
+          g += __shfl_xor_sync(0xffffffffu, g, 16);
+          if (pg == 0) sdw[(warp * D + c) * w + f] += g;
+        }
+      }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         float ab[4] = {0.f, 0.f, 0.f, 0.f}, zz[4], o[4];
@@ -383,86 +403,58 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
     const double s = block_sum_d(acc[i], sh);
     if (threadIdx.x == 0) a.losspart[(int64_t)blockIdx.x * 8 + i] = s;
   }
+  if (!a.want_grad) return;
+  // block partials of the output layer's dW (warps summed in a fixed order) and bias
+  __syncthreads();
+  for (int i = threadIdx.x; i < D * w; i += blockDim.x) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < OUT_THREADS / 32; ++k) s += sdw[k * D * w + i];
+    a.dwpart[(int64_t)blockIdx.x * D * w + i] = s;
+  }
+  for (int c = 0; c < D; ++c) {
+    float v = dbo[c];
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    __shared__ float shb[OUT_THREADS / 32];
+    __syncthreads();
+    if (lane == 0) shb[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int k = 0; k < OUT_THREADS / 32; ++k) t += shb[k];
+      a.dbpart[(int64_t)c * gridDim.x + blockIdx.x] = t;
+    }
+  }
 }
 
 int out_loss_blocks(int64_t NP) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(NP / TILE_PTS, 4096));
 }
 
-void launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st) {
-  const size_t smem = sizeof(float) * a.d_out * a.w;
-  if (prec == PINN_BF16) {
-    if (a.d_out == 1) k_out_loss<__nv_bfloat16, 1, true><<<nblocks, OUT_THREADS, smem, st>>>(a);
-    else k_out_loss<__nv_bfloat16, 3, true><<<nblocks, OUT_THREADS, smem, st>>>(a);
-  } else {
-    if (a.d_out == 1) k_out_loss<float, 1, false><<<nblocks, OUT_THREADS, smem, st>>>(a);
-    else k_out_loss<float, 3, false><<<nblocks, OUT_THREADS, smem, st>>>(a);
+template <typename T, int D, bool FAST>
+cudaError_t out_loss_launch(const OutArgs& a, int nblocks, size_t smem, cudaStream_t st) {
+  auto kern = k_out_loss<T, D, FAST>;
+  // weights + per-warp dW accumulators: up to 120 KB for 2048-wide, 3-output networks
+  static size_t reserved = 48 * 1024;
+  if (smem > reserved) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    reserved = smem;
   }
+  kern<<<nblocks, OUT_THREADS, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------------
-// Output-layer weight gradient: dW_out[c][f] = sum over columns of Ubar[c][col] A_L[f][col].
-// One warp per (feature row f, column chunk), coalesced along columns; partials
-// [chunk][d_out][w] reduced in FP64 by the finalisation.
-// ------------------------------------------------------------------------------------
-constexpr int DWO_ROWS = 8;   // feature rows per warp (each Ubar load serves all of them)
-
-template <typename T, int D>
-__global__ void k_dw_out(const T* AL, const float* Ubar, int w, int64_t NC, int nchunks, float* part) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int f0 = (blockIdx.x * (blockDim.x >> 5) + warp) * DWO_ROWS;
-  if (f0 >= w) return;
-  const int chunk = blockIdx.y;
-  const int64_t noct = NC / 8;
-  const int64_t per = (noct + nchunks - 1) / nchunks;
-  const int64_t o0 = chunk * per, o1 = min(noct, o0 + per);
-  float acc[DWO_ROWS][D];
-#pragma unroll
-  for (int i = 0; i < DWO_ROWS; ++i)
-#pragma unroll
-    for (int c = 0; c < D; ++c) acc[i][c] = 0.f;
-  for (int64_t o = o0 + lane; o < o1; o += 32) {
-    float g[D][8];
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      load4<float>(Ubar + toff(c, 8 * o, D), &g[c][0]);
-      load4<float>(Ubar + toff(c, 8 * o, D) + 4, &g[c][4]);
-    }
-#pragma unroll
-    for (int i = 0; i < DWO_ROWS; ++i) {
-      if (f0 + i >= w) break;
-      float v[8];
-      load4<T>(AL + toff(f0 + i, 8 * o, w), v);
-      load4<T>(AL + toff(f0 + i, 8 * o, w) + 4, v + 4);
-#pragma unroll
-      for (int c = 0; c < D; ++c)
-#pragma unroll
-        for (int r = 0; r < 8; ++r) acc[i][c] = fmaf(g[c][r], v[r], acc[i][c]);
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < DWO_ROWS; ++i) {
-    if (f0 + i >= w) break;
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      float s = acc[i][c];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) part[((int64_t)chunk * D + c) * w + f0 + i] = s;
-    }
-  }
+cudaError_t launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st) {
+  const size_t smem = sizeof(float) * a.d_out * a.w * (1 + OUT_THREADS / 32);
+  if (prec == PINN_BF16)
+    return a.d_out == 1 ? out_loss_launch<__nv_bfloat16, 1, true>(a, nblocks, smem, st)
+                        : out_loss_launch<__nv_bfloat16, 3, true>(a, nblocks, smem, st);
+  return a.d_out == 1 ? out_loss_launch<float, 1, false>(a, nblocks, smem, st)
+                      : out_loss_launch<float, 3, false>(a, nblocks, smem, st);
 }
 
-void launch_dw_out(const void* AL, const float* Ubar, int w, int d_out, int64_t NC, int nchunks, float* part,
-                   int prec, cudaStream_t st) {
-  dim3 grid((w + 8 * DWO_ROWS - 1) / (8 * DWO_ROWS), nchunks);
-  if (prec == PINN_BF16) {
-    if (d_out == 1) k_dw_out<__nv_bfloat16, 1><<<grid, 256, 0, st>>>((const __nv_bfloat16*)AL, Ubar, w, NC, nchunks, part);
-    else k_dw_out<__nv_bfloat16, 3><<<grid, 256, 0, st>>>((const __nv_bfloat16*)AL, Ubar, w, NC, nchunks, part);
-  } else {
-    if (d_out == 1) k_dw_out<float, 1><<<grid, 256, 0, st>>>((const float*)AL, Ubar, w, NC, nchunks, part);
-    else k_dw_out<float, 3><<<grid, 256, 0, st>>>((const float*)AL, Ubar, w, NC, nchunks, part);
-  }
-}
 
 // ------------------------------------------------------------------------------------
 // Row reductions over a pre-activation adjoint Zbar^T [M][NC]: the bias gradient
@@ -696,6 +688,26 @@ void launch_finalize_loss(const double* part, int nblocks, int64_t n_res, int64_
                           cudaStream_t st) {
   k_finalize_loss<<<1, 256, 0, st>>>(part, nblocks, n_res, n_ic, n_bc, lam_pde, lam_ic, lam_bc, out, acc, first, last,
                                      status);
+}
+
+// ------------------------------------------------------------------------------------
+// Ordered partial-sum compaction: in [S][n] -> out [S2][n], slot k summing splits
+// k*ceil(S/S2) .. in order (compensated), so the finalisation reads S2 splits.
+// ------------------------------------------------------------------------------------
+__global__ void k_sum_splits(const float* __restrict__ in, float* __restrict__ out, int S, int S2, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (i >= n) return;
+  const int per = (S + S2 - 1) / S2;
+  const int s0 = k * per, s1 = min(S, s0 + per);
+  Acc2 acc;
+  for (int s = s0; s < s1; ++s) acc.add(in[(int64_t)s * n + i]);
+  out[(int64_t)k * n + i] = (float)acc.value();
+}
+
+void launch_sum_splits(const float* in, float* out, int S, int S2, int64_t n, cudaStream_t st) {
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)S2);
+  k_sum_splits<<<grid, 256, 0, st>>>(in, out, S, S2, n);
 }
 
 // ------------------------------------------------------------------------------------

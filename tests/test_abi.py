@@ -65,6 +65,8 @@ def test_invalid_width_and_null_args(lib):
     spec = _lib.make_spec(0, [64, 0], 0, False)
     h = C.c_void_p()
     assert lib.pinn_create(C.byref(spec), C.byref(h)) == 1
+    spec = _lib.make_spec(0, [64, 2049], 0, False)
+    assert lib.pinn_create(C.byref(spec), C.byref(h)) == 1
     assert lib.pinn_create(None, C.byref(h)) == 1
     assert lib.pinn_param_count(None, None) == 1
     assert lib.pinn_destroy(None) == 0
