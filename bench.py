@@ -49,7 +49,6 @@ def parse():
     ap.add_argument("--n-res", type=int, default=None, help="interior points (default: the workload's own)")
     ap.add_argument("--no-torch", action="store_true", help="skip the torch autograd baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--recompute", action="store_true", help="recompute layer jets instead of storing them")
     ap.add_argument("--chunk-points", type=int, default=0, help="process the batch in chunks of this many points")
     ap.add_argument("--value-split", action="store_true",
                     help="BF16: split the weights into high/low halves on the value rows only")
@@ -340,8 +339,8 @@ def run_ours(args, ws_n, rank, local):
     dev = torch.device("cuda", local)
     w, params, B, batch = workload_inputs(args.workload, args.n_res)
     precision = args.precision or w.precision
-    net = api.PinnNet.from_spec(w.spec, precision, device=dev, recompute=args.recompute,
-                                chunk_points=args.chunk_points, value_split=args.value_split)
+    net = api.PinnNet.from_spec(w.spec, precision, device=dev, chunk_points=args.chunk_points,
+                                value_split=args.value_split)
     if B is not None:
         net.set_ff_matrix(B)
     db = api.DeviceBatch.from_host(batch, device=dev)
@@ -448,8 +447,7 @@ def run_ours(args, ws_n, rank, local):
                               f"{' RWF' if w.spec.rwf else ''}",
                    "n_res": batch.n_res, "n_ic": batch.n_ic, "n_bc": batch.n_bc, "points_per_step": n_pts,
                    "jet_columns": ncols, "parallelism": f"replicas x{ws_n}",
-                   "workspace_gb": round(ws_bytes / 1e9, 2), "recompute": bool(args.recompute),
-                   "chunk_points": args.chunk_points,
+                   "workspace_gb": round(ws_bytes / 1e9, 2), "chunk_points": args.chunk_points,
                    "bf16_weight_split": ("value rows" if args.value_split else "all rows") if precision == "bf16" else None,
                    "l2": f"working set {ws_bytes / 1e9:.2f} GB per step > 129 MB L2 (no flush needed)"},
         "e2e": {"value": round(whole_job_rate(n_pts, ws_n, e2e_ms_max), 1), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -89,14 +89,6 @@ typedef struct {
  * apply (the many-network autotuner picks per network between the two). */
 #define PINN_FLAG_CUDA_CORES 1
 
-/* pinn_spec.flags: recompute the layer jets instead of storing them.  The forward
- * keeps each layer's pre-activation jets Z_l but only two activation buffers; the
- * reverse sweep rebuilds A_{l-1} = tanh-jet(Z_{l-1}) just before the weight
- * gradient of layer l needs it.  Activation memory drops from L buffers to two, for
- * one extra read of Z and write of A per layer.  The adjoint epilogues always
- * recompute tanh', tanh'' and tanh''' from the stored Z. */
-#define PINN_FLAG_RECOMPUTE 2
-
 /* pinn_spec.flags, BF16 only: split the weights into BF16 high and low halves for
  * the value rows only.  By default the tensor-core forward adds W_lo . A on every jet
  * row (two full MMAs plus the value-row low half).  With this flag the derivative
@@ -105,6 +97,7 @@ typedef struct {
  * the Navier-Stokes cavity networks stay near 1e-2, while Burgers networks whose
  * residual terms cancel need the full split. */
 #define PINN_FLAG_BF16_VALUE_SPLIT 4
+/* (flag value 2 is reserved) */
 
 /* Loss weights and the PDE coefficient (nu for Burgers; 1/Re for Navier-Stokes;
  * ignored for Maxwell). */

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(PKG, "libpinn.so")
 PINN_MAX_HIDDEN = 16
 PINN_LOSS_TERMS = 8
 PINN_FP32, PINN_TF32, PINN_BF16 = 0, 1, 2
-PINN_FLAG_CUDA_CORES, PINN_FLAG_RECOMPUTE, PINN_FLAG_BF16_VALUE_SPLIT = 1, 2, 4
+PINN_FLAG_CUDA_CORES, PINN_FLAG_BF16_VALUE_SPLIT = 1, 4
 PRECISIONS = {"fp32": PINN_FP32, "tf32": PINN_TF32, "bf16": PINN_BF16}
 STATUS = {0: "PINN_OK", 1: "PINN_ERR_INVALID_ARG", 2: "PINN_ERR_UNSUPPORTED", 3: "PINN_ERR_CUDA",
           4: "PINN_ERR_WORKSPACE", 5: "PINN_ERR_NONFINITE", 6: "PINN_ERR_TIMEOUT"}

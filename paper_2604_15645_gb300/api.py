@@ -49,11 +49,11 @@ def make_problem(nu, lambda_pde=1.0, lambda_ic=1.0, lambda_bc=1.0) -> _lib.pinn_
 class PinnNet:
     """One network handle (pinn_create) plus a cached workspace."""
 
-    def __init__(self, pde, widths, ff_m=0, rwf=False, precision="fp32", device="cuda", recompute=False,
-                 chunk_points=0, value_split=False):
+    def __init__(self, pde, widths, ff_m=0, rwf=False, precision="fp32", device="cuda", chunk_points=0,
+                 value_split=False):
         self.device = torch.device(device)
         self.precision = precision
-        flags = (_lib.PINN_FLAG_RECOMPUTE if recompute else 0) | (_lib.PINN_FLAG_BF16_VALUE_SPLIT if value_split else 0)
+        flags = _lib.PINN_FLAG_BF16_VALUE_SPLIT if value_split else 0
         with torch.cuda.device(self.device):
             self.spec = _lib.make_spec(pde, widths, ff_m, rwf, _lib.PRECISIONS[precision], flags)
             self.h = _lib.pinn_create(self.spec)
@@ -66,9 +66,8 @@ class PinnNet:
         self.loss_buf = torch.zeros(_lib.PINN_LOSS_TERMS, dtype=torch.float64, device=self.device)
 
     @classmethod
-    def from_spec(cls, spec, precision="fp32", device="cuda", recompute=False, chunk_points=0, value_split=False):
-        return cls(spec.pde, spec.widths, spec.ff_m, spec.rwf, precision, device, recompute, chunk_points,
-                   value_split)
+    def from_spec(cls, spec, precision="fp32", device="cuda", chunk_points=0, value_split=False):
+        return cls(spec.pde, spec.widths, spec.ff_m, spec.rwf, precision, device, chunk_points, value_split)
 
     def set_chunk_points(self, points):
         """Process batches in chunks of at most `points` points (0: one pass)."""

@@ -71,28 +71,15 @@ pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   q.nbpart = (int)std::min<int64_t>(256, std::max<int64_t>(1, q.NC / 8192));
-  q.recompute = (h->spec.flags & PINN_FLAG_RECOMPUTE) != 0;
   if (h->spec.ff_m) {
     q.A[0] = take((size_t)2 * h->spec.ff_m * q.NC * q.es);
     if (q.lo) q.Alo[0] = take((size_t)2 * h->spec.ff_m * q.NP * q.lo_es);
   }
-  size_t abuf[2] = {0, 0}, alobuf[2] = {0, 0};
-  if (q.recompute) {
-    // two activation buffers shared by all hidden layers; A_l lives in buffer l % 2
-    for (int k = 0; k < 2; ++k) {
-      abuf[k] = take((size_t)h->w_max * q.NC * q.es);
-      if (q.lo) alobuf[k] = take((size_t)h->w_max * q.NP * q.lo_es);
-    }
-  }
+  // One jet array per layer: the activations A_l.  The pre-activations Z_l are not
+  // kept: the adjoint epilogues recompute t', t'', t''' from A_l.
   for (int l = 1; l <= L; ++l) {
-    if (q.recompute) {
-      q.A[l] = abuf[l % 2];
-      q.Alo[l] = alobuf[l % 2];
-    } else {
-      q.A[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
-      if (q.lo) q.Alo[l] = take((size_t)h->spec.widths[l - 1] * q.NP * q.lo_es);
-    }
-    q.Z[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
+    q.A[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
+    if (q.lo) q.Alo[l] = take((size_t)h->spec.widths[l - 1] * q.NP * q.lo_es);
   }
   q.Zbar[0] = take((size_t)h->w_max * q.NC * q.es);
   q.Zbar[1] = take((size_t)h->w_max * q.NC * q.es);
@@ -235,8 +222,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
                     ws + p.A[0], p.lo ? ws + p.Alo[0] : nullptr, p.NP, prec, st);
   } else {
     launch_first_layer(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, W32(0), bias(0),
-                       cp.lay[0].fout, mode, ws + p.A[1], p.lo ? ws + p.Alo[1] : nullptr, ws + p.Z[1], p.NP, prec,
-                       st);
+                       cp.lay[0].fout, mode, ws + p.A[1], p.lo ? ws + p.Alo[1] : nullptr, p.NP, prec, st);
   }
   if (cp.pm) {
     const int f0 = h->first_gemm;
@@ -247,7 +233,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
   // 3. Hidden jet GEMMs with the tanh-jet epilogue.
   for (int li = h->first_gemm; li < L; ++li) {
     EpiArgs e{};
-    e.bias = bias(li); e.out = ws + p.A[li + 1]; e.zout = ws + p.Z[li + 1];
+    e.bias = bias(li); e.out = ws + p.A[li + 1];
     e.alo_out = p.lo ? ws + p.Alo[li + 1] : nullptr;
     // BF16 storage is rounded, so consumers add the low half back; TF32 storage is
     // exact FP32 and only the tensor-core forward (which truncates) uses the low half.
@@ -271,7 +257,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
 
   // 4. Output layer, residual, loss partials, adjoint seed and Zbar_L.
   OutArgs oa{};
-  oa.AL = ws + p.A[L]; oa.ALlo = (p.lo && prec == PINN_BF16) ? ws + p.Alo[L] : nullptr; oa.ZL = ws + p.Z[L];
+  oa.AL = ws + p.A[L]; oa.ALlo = (p.lo && prec == PINN_BF16) ? ws + p.Alo[L] : nullptr;
   oa.W = W32(L); oa.b = bias(L);
   oa.g_ic = b->g_ic; oa.g_bc = b->g_bc; oa.ic_mask = b->ic_mask; oa.bc_mask = b->bc_mask;
   oa.n_res = p.n_res; oa.n_ic = p.n_ic; oa.n_bc = p.n_bc; oa.NP = p.NP; oa.NC = p.NC;
@@ -318,11 +304,6 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     const LayerPlan& lp = cp.lay[li];
     void* zb = ws + p.Zbar[(li + 1) % 2];
     const bool raw = (li == 0 && !h->spec.ff_m);
-    if (p.recompute && li >= 1 && li <= L - 2) {
-      // A_li's buffer has since held A_{li+2}: rebuild it from the stored Z_li
-      PhaseScope ps(h, st, PH_OTHER, 1);
-      launch_jet_recompute(ws + p.Z[li], ws + p.A[li], lp.fin, p.NP, mode, prec, st);
-    }
     if (!raw) {
       PhaseScope ps(h, st, PH_DW, 1);
       if (cp.tc[li]) {
@@ -340,7 +321,8 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     }
     if (li >= 1) {
       EpiArgs e{};
-      e.out = ws + p.Zbar[li % 2]; e.zin = ws + p.Z[li];
+      e.out = ws + p.Zbar[li % 2]; e.ain = ws + p.A[li];
+      e.ain_lo = p.lo ? ws + p.Alo[li] : nullptr;
       e.jet_mode = mode;
       if (cp.fused_db[li - 1]) {
         e.dbpart = reinterpret_cast<float*>(ws + cp.lay[li - 1].dbpart);
@@ -508,7 +490,7 @@ pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
   if (spec->ff_m < 0 || spec->ff_m > 2048) return PINN_ERR_INVALID_ARG;
   if (spec->rwf != 0 && spec->rwf != 1) return PINN_ERR_INVALID_ARG;
   if (spec->precision < PINN_FP32 || spec->precision > PINN_BF16) return PINN_ERR_INVALID_ARG;
-  if (spec->flags & ~(PINN_FLAG_CUDA_CORES | PINN_FLAG_RECOMPUTE | PINN_FLAG_BF16_VALUE_SPLIT))
+  if (spec->flags & ~(PINN_FLAG_CUDA_CORES | PINN_FLAG_BF16_VALUE_SPLIT))
     return PINN_ERR_INVALID_ARG;
   pinn_handle* h = new (std::nothrow) pinn_handle();
   if (!h) return PINN_ERR_INVALID_ARG;

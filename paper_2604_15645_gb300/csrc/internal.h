@@ -47,10 +47,8 @@ struct Plan {
   int es = 4;          // bytes per element of the compute type (2 bf16, 4 fp32/tf32)
   bool lo = false;     // BF16 / TF32: value rows also keep a low half in Alo
   int lo_es = 2;       // bytes per low-half element (BF16 2, TF32 4)
-  bool recompute = false;   // A_l for l >= 1 live in two ping-pong buffers (PINN_FLAG_RECOMPUTE)
   size_t A[PINN_MAX_HIDDEN + 1] = {};   // A_l^T [w_l][NC] compute type, l = 0..L (A_0 only with FF)
   size_t Alo[PINN_MAX_HIDDEN + 1] = {}; // low half of the value rows, tile-major [NP/64][w_l][64]
-  size_t Z[PINN_MAX_HIDDEN + 1] = {};   // Z_l^T [w_l][NC] compute type, l = 1..L
   size_t Zbar[2] = {};                  // ping-pong adjoints [w_max][NC] compute type
   size_t losspart = 0;                  // per-block loss partials, double [nloss_blocks][8]
   int nloss_blocks = 0;
@@ -103,15 +101,15 @@ void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, i
 
 void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                         int64_t n_bc, int d_in, const float* W, const float* b, int fout, int jet_mode, void* A1,
-                        void* A1lo, void* Z1, int64_t NP, int prec, cudaStream_t st);
+                        void* A1lo, int64_t NP, int prec, cudaStream_t st);
 
 struct EpiArgs {
   const float* bias;      // fwd: bias of this layer [M]
   void* out;              // fwd: A_l^T, adj: Zbar_{l-1}^T (compute type)
-  void* zout;             // fwd: Z_l^T (compute type)
   void* alo_out;          // fwd, BF16: low half of A_l's value rows [M][NP] (else nullptr)
   const void* alo_in;     // fwd, CUDA-core BF16 path: low half of the input's value rows [K][NP]
-  const void* zin;        // adj: Z_{l-1}^T (compute type)
+  const void* ain;        // adj: A_{l-1}^T (compute type), the output jet of the layer below
+  const void* ain_lo;     // adj, BF16: low half of its value rows [NP/64][M][64] (t = hi + lo)
   void* out_pm;           // TF32 tensor-core path: point-major copy of `out`, [NC][M] FP32 (nullptr = none)
   int jet_mode;
   // adjoint only: bias-gradient partials of the layer whose pre-activation adjoint
@@ -137,7 +135,6 @@ void launch_simt_gemm_dw(const void* Aop, bool a_fp32, const void* Bop, bool b_f
 struct OutArgs {
   const void* AL;        // A_L^T [w][NC] compute type
   const void* ALlo;      // BF16: low half of A_L's value rows [w][NP] (else nullptr)
-  const void* ZL;        // Z_L^T [w][NC] compute type
   const float* W;        // output weights fp32 [d_out][w]
   const float* b;        // output bias [d_out]
   const float* g_ic; const float* g_bc;   // targets [d_out][n]
@@ -188,8 +185,7 @@ void launch_sum_splits(const float* in, float* out, int S, int S2, int64_t n, cu
 constexpr int OUT_SUM_SLOTS = 16;   // output-layer dW partials after compaction
 // Tile-major [w][NC] FP32 -> point-major [NC][w] (TF32 tensor-core operand layout).
 void launch_to_point_major(const void* src, void* dst, int w, int64_t NC, cudaStream_t st);
-// A = tanh-jet(Z), tile-major [w][NC], for the recompute policy.
-void launch_jet_recompute(const void* Z, void* A, int w, int64_t NP, int mode, int prec, cudaStream_t st);
+
 void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
                  float bc1, float bc2, cudaStream_t st);
 

@@ -10,6 +10,14 @@
 //   zbar_L = abar_L t'
 //   zbar_k = abar_k t' + [k in S] 2 abar_L t'' z_k
 //   zbar   = abar t' + sum_k abar_k t'' z_k + abar_L (t''' sum_{k in S} z_k^2 + t'' z_L).
+// The epilogues evaluate it from the layer's output jet a instead of z: substituting
+// z_k = a_k / t' and z_L = (a_L - t'' sum z_k^2) / t', every 1/t' cancels
+// (t'''/t' - t''^2/t'^2 = -2), leaving, with t = a and t' = (1 - t)(1 + t),
+//   zbar_L = abar_L t'
+//   zbar_k = abar_k t' - [k in S] 4 abar_L t a_k
+//   zbar   = abar t' - 2 t sum_k abar_k a_k - 2 abar_L (sum_{k in S} a_k^2 + t a_L).
+// So the forward stores A only (it feeds the next layer and the weight gradient
+// anyway), not Z.
 #pragma once
 
 #include <cstring>
@@ -58,39 +66,24 @@ __device__ __forceinline__ void jet_fwd(const float z[4], float a[4], int mode) 
   }
 }
 
-template <bool FAST = false>
-__device__ __forceinline__ void jet_adj(const float z[4], const float ab[4], float zb[4], int mode) {
-  float t, tp;
-  tanh_pair<FAST>(z[0], t, tp);
-  const float tpp = -2.f * t * tp;
+// The same adjoint from the output jet a (see the header comment); no tanh evaluation.
+__device__ __forceinline__ void jet_adj_a(const float a[4], const float ab[4], float zb[4], int mode) {
+  const float t = a[0];
+  const float tp = (1.f - t) * (1.f + t);
   if (mode == JET_MAXWELL) {
     zb[1] = ab[1] * tp;
     zb[2] = ab[2] * tp;
     zb[3] = ab[3] * tp;
-    zb[0] = fmaf(ab[0], tp, tpp * (ab[1] * z[1] + ab[2] * z[2] + ab[3] * z[3]));
+    zb[0] = fmaf(ab[0], tp, -2.f * t * (ab[1] * a[1] + ab[2] * a[2] + ab[3] * a[3]));
   } else {
     const bool ns = (mode == JET_NS);
-    const float tppp = tp * (6.f * t * t - 2.f);
-    const float q = z[1] * z[1] + (ns ? z[2] * z[2] : 0.f);
+    const float q = a[1] * a[1] + (ns ? a[2] * a[2] : 0.f);
+    const float t4 = 4.f * ab[3] * t;
     zb[3] = ab[3] * tp;
-    zb[1] = fmaf(ab[1], tp, 2.f * ab[3] * tpp * z[1]);
-    zb[2] = ns ? fmaf(ab[2], tp, 2.f * ab[3] * tpp * z[2]) : ab[2] * tp;
-    zb[0] = fmaf(ab[0], tp, tpp * (ab[1] * z[1] + ab[2] * z[2])) + ab[3] * fmaf(tppp, q, tpp * z[3]);
+    zb[1] = fmaf(ab[1], tp, -t4 * a[1]);
+    zb[2] = ns ? fmaf(ab[2], tp, -t4 * a[2]) : ab[2] * tp;
+    zb[0] = fmaf(ab[0], tp, -2.f * (t * (ab[1] * a[1] + ab[2] * a[2]) + ab[3] * fmaf(t, a[3], q)));
   }
-}
-
-// Value-only column (initial/boundary point).
-template <bool FAST = false>
-__device__ __forceinline__ float val_fwd(float z) {
-  float t, tp;
-  tanh_pair<FAST>(z, t, tp);
-  return t;
-}
-template <bool FAST = false>
-__device__ __forceinline__ float val_adj(float z, float ab) {
-  float t, tp;
-  tanh_pair<FAST>(z, t, tp);
-  return ab * tp;
 }
 
 // ---- geometry of the jet matrices ------------------------------------------------------

@@ -134,12 +134,12 @@ void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, i
 // First hidden layer on raw coordinates (no Fourier features): z = W x + b on the
 // value row, z_k = W[:, d_k] on the first-derivative rows of interior points, 0 on
 // the second-order row (the input has no curvature); then the tanh jet rule.
-// Writes A_1 (and its value-row low half) and Z_1.
+// Writes A_1 (and its value-row low half).
 // ------------------------------------------------------------------------------------
 template <typename T, int LO>
 __global__ void k_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                               int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, T* A1,
-                              void* A1lo, T* Z1, int64_t NP) {
+                              void* A1lo, int64_t NP) {
   const int f = blockIdx.y;
   const int64_t NC = 4 * NP;
   float Wf[3] = {0.f, 0.f, 0.f};
@@ -148,7 +148,7 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
 
   for (int64_t p0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); p0 < NP;
        p0 += 4 * (int64_t)gridDim.x * blockDim.x) {
-    float za[4][4], aa[4][4];   // [row][point]
+    float aa[4][4];   // [row][point]
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int64_t p = p0 + k;
@@ -165,13 +165,12 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
       }
       jet_fwd<(LO == 1)>(z, a, mode);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) { za[r][k] = z[r]; aa[r][k] = a[r]; }
+      for (int r = 0; r < 4; ++r) aa[r][k] = a[r];
     }
     const int64_t c0 = jcol(p0, 0);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       store4<T>(A1 + toff(f, c0 + 64 * r, fout), aa[r]);
-      store4<T>(Z1 + toff(f, c0 + 64 * r, fout), za[r]);
     }
     if (LO) store_lo4<LO>(A1lo, loff(f, p0, fout), aa[0]);
   }
@@ -179,14 +178,14 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
 
 void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                         int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, void* A1,
-                        void* A1lo, void* Z1, int64_t NP, int prec, cudaStream_t st) {
+                        void* A1lo, int64_t NP, int prec, cudaStream_t st) {
   dim3 grid((unsigned)std::min<int64_t>((NP / 4 + 255) / 256, 4096), fout);
   if (prec == PINN_BF16)
     k_first_layer<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout,
-                                                          mode, (__nv_bfloat16*)A1, A1lo, (__nv_bfloat16*)Z1, NP);
+                                                          mode, (__nv_bfloat16*)A1, A1lo, NP);
   else
     k_first_layer<float, 0><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
-                                                  (float*)A1, nullptr, (float*)Z1, NP);
+                                                  (float*)A1, nullptr, NP);
 }
 
 // ------------------------------------------------------------------------------------
@@ -280,7 +279,6 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   __syncthreads();
   const T* AL = reinterpret_cast<const T*>(a.AL);
   const __nv_bfloat16* ALlo = reinterpret_cast<const __nv_bfloat16*>(a.ALlo);
-  const T* ZL = reinterpret_cast<const T*>(a.ZL);
   T* Zb = reinterpret_cast<T*>(a.Zbar);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pg = lane >> 3, sl = lane & 7;
@@ -352,20 +350,22 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) dbo[c] += Ub[j][c][0];
     }
-    // abar_L = Ubar W_out (rank <= 3), then the tanh-jet adjoint with Z_L; and the
-    // output layer's dW[c][f] = sum over the tile's columns of Ubar[c] A_L[f] (A_L
-    // read again, from L2).
+    // A_L read again (from L2) for the output layer's dW[c][f] = sum over the tile's
+    // columns of Ubar[c] A_L[f], and for abar_L = Ubar W_out (rank <= 3) followed by
+    // the tanh-jet adjoint written in A_L.
 #pragma unroll 2
     for (int f = sl; f < w; f += 8) {
-      float z[4][4], zb[4][4];                     // [row][point]
-      const T* zrow = ZL + toff(f, cb, w);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) load4<T>(zrow + 64 * r, z[r]);
+      float av[4][4], zb[4][4];                    // [row][point]
       {
-        float av[4][4];
         const T* arow = AL + toff(f, cb, w);
 #pragma unroll
         for (int r = 0; r < 4; ++r) load4<T>(arow + 64 * r, av[r]);
+        if (ALlo) {
+          float lo[4];
+          load4<__nv_bfloat16>(ALlo + loff(f, p0, w), lo);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) av[0][j] += lo[j];
+        }
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           float g = 0.f;
@@ -388,8 +388,8 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
           for (int r = 0; r < 4; ++r) ab[r] = fmaf(wc, Ub[j][c][r], ab[r]);
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) zz[r] = z[r][j];
-        jet_adj<FAST>(zz, ab, o, a.jet_mode);
+        for (int r = 0; r < 4; ++r) zz[r] = av[r][j];
+        jet_adj_a(zz, ab, o, a.jet_mode);
 #pragma unroll
         for (int r = 0; r < 4; ++r) zb[r][j] = o[r];
       }
@@ -734,38 +734,6 @@ void launch_to_point_major(const void* src, void* dst, int w, int64_t NC, cudaSt
   k_to_point_major<<<grid, 256, 0, st>>>((const float*)src, (float*)dst, w, NC);
 }
 
-// ------------------------------------------------------------------------------------
-// Recompute policy: A = tanh-jet(Z) for one layer, 4 points per thread, tile-major.
-// ------------------------------------------------------------------------------------
-template <typename T, bool FAST>
-__global__ void k_jet_recompute(const T* Z, T* A, int w, int64_t NP, int mode) {
-  const int f = blockIdx.y;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < NP / 4; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p0 = 4 * q;                                   // 4 points inside one 64-point tile
-    const int64_t c0 = (int64_t)TILE_COLS * (p0 / TILE_PTS) + (p0 % TILE_PTS);
-    float z[4][4], a[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) load4<T>(Z + toff(f, c0 + 64 * r, w), z[r]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      float zz[4] = {z[0][k], z[1][k], z[2][k], z[3][k]}, aa[4];
-      jet_fwd<FAST>(zz, aa, mode);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) a[r][k] = aa[r];
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) store4<T>(A + toff(f, c0 + 64 * r, w), a[r]);
-  }
-}
-
-void launch_jet_recompute(const void* Z, void* A, int w, int64_t NP, int mode, int prec, cudaStream_t st) {
-  dim3 grid((unsigned)std::min<int64_t>((NP / 4 + 255) / 256, 4096), w);
-  if (prec == PINN_BF16)
-    k_jet_recompute<__nv_bfloat16, true><<<grid, 256, 0, st>>>((const __nv_bfloat16*)Z, (__nv_bfloat16*)A, w, NP,
-                                                               mode);
-  else
-    k_jet_recompute<float, false><<<grid, 256, 0, st>>>((const float*)Z, (float*)A, w, NP, mode);
-}
 
 // ------------------------------------------------------------------------------------
 // Adam (Sec. 2.6.5), bias-corrected, in place.

@@ -102,9 +102,14 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
     const int f = m0 + ty * 4 + i;
     if (f >= M) continue;
     float o[4][4], zz[4][4];   // [row][point]
-    if (EPI == 1) {
-      const T* zr = reinterpret_cast<const T*>(e.zin) + toff(f, n0 + 4 * tx, M);
-      for (int r = 0; r < 4; ++r) load4<T>(zr + 64 * r, zz[r]);
+    if (EPI == 1) {   // the output jet of the layer below (value row: hi + lo for BF16)
+      const T* ar = reinterpret_cast<const T*>(e.ain) + toff(f, n0 + 4 * tx, M);
+      for (int r = 0; r < 4; ++r) load4<T>(ar + 64 * r, zz[r]);
+      if (sizeof(T) == 2 && e.ain_lo) {
+        float lo[4];
+        load4<__nv_bfloat16>(reinterpret_cast<const __nv_bfloat16*>(e.ain_lo) + loff(f, tile * TILE_PTS + 4 * tx, M), lo);
+        for (int j = 0; j < 4; ++j) zz[0][j] += lo[j];
+      }
     }
     const float bias = (EPI == 0) ? e.bias[f] : 0.f;
     for (int j = 0; j < 4; ++j) {
@@ -115,17 +120,15 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
       }
       if (EPI == 0) {
         jet_fwd<FAST>(z, a, e.jet_mode);
-        for (int r = 0; r < 4; ++r) { o[r][j] = a[r]; zz[r][j] = z[r]; }
+        for (int r = 0; r < 4; ++r) o[r][j] = a[r];
       } else {
-        jet_adj<FAST>(z, ab, a, e.jet_mode);
+        jet_adj_a(z, ab, a, e.jet_mode);
         for (int r = 0; r < 4; ++r) o[r][j] = a[r];
       }
     }
     T* orow = out + toff(f, n0 + 4 * tx, M);
     for (int r = 0; r < 4; ++r) store4<T>(orow + 64 * r, o[r]);
     if (EPI == 0) {
-      T* zrow = reinterpret_cast<T*>(e.zout) + toff(f, n0 + 4 * tx, M);
-      for (int r = 0; r < 4; ++r) store4<T>(zrow + 64 * r, zz[r]);
       if (sizeof(T) == 2 && e.alo_out) {
         __nv_bfloat16* lo = reinterpret_cast<__nv_bfloat16*>(e.alo_out) + loff(f, tile * TILE_PTS + 4 * tx, M);
         for (int j = 0; j < 4; ++j)

@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
     // row is one full 32-byte sector (16 BF16 or 8 FP32 values): partial-sector stores
     // would make L2 fetch the sector first.  FP32 units are small enough to double-buffer
     // the TMEM loads; in the adjoint the next unit's Z rows are always loaded one unit
-    // ahead.
+    // ahead (the layer-below activations the adjoint is written in).
     constexpr bool FAST = !TF32;
     constexpr int PARTS = EPI_WARPS / 4;                 // warps per lane quadrant
     constexpr int UPTS = TF32 ? 8 : 16;                  // points per unit
@@ -593,13 +593,14 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
     const int row = quad * 32 + lane;
     auto unit_col = [&](int u) { return part * (UNITS * UPTS) + UPTS * u; };
 
-    uint32_t znext[4][ZW];                               // adjoint: Z rows of the next unit
+    constexpr int ZR = 4;                                // jet rows loaded per unit
+    uint32_t znext[ZR][ZW];                              // adjoint: A rows of the next unit
     auto load_z = [&](int t_, int u_) {
       int mb_, nb_, k0_, k1_;
       coords(t_, mb_, nb_, k0_, k1_);
       const int m_ = mb_ * BM + row;
       if (m_ < p.M) {
-        const T* zr = reinterpret_cast<const T*>(p.e.zin) + toff(m_, (int64_t)nb_ * BN, p.M) + unit_col(u_);
+        const T* zr = reinterpret_cast<const T*>(p.e.ain) + toff(m_, (int64_t)nb_ * BN, p.M) + unit_col(u_);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           if constexpr (UPTS == 8) ld8raw(zr + 64 * r, znext[r]);
@@ -631,10 +632,10 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
         }
       };
       auto process = [&](int u, float (&v)[4][UPTS]) {
-        uint32_t zw[4][ZW];
+        uint32_t zw[ZR][ZW];
         if constexpr (MODE == TC_ADJ) {
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
+          for (int r = 0; r < ZR; ++r)
 #pragma unroll
             for (int j = 0; j < ZW; ++j) zw[r][j] = znext[r][j];
           if (u + 1 < UNITS) load_z(t, u + 1);
@@ -647,9 +648,6 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
           const float bias = p.e.bias[m];
 #pragma unroll
           for (int i = 0; i < UPTS; ++i) v[0][i] += bias;
-          T* zo = reinterpret_cast<T*>(p.e.zout) + cbase;
-#pragma unroll
-          for (int r = 0; r < 4; ++r) st_row(zo + 64 * r, v[r]);
 #pragma unroll
           for (int i = 0; i < UPTS; ++i) {
             float z[4] = {v[0][i], v[1][i], v[2][i], v[3][i]}, a[4];
@@ -673,11 +671,11 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
         } else if constexpr (MODE == TC_ADJ) {
 #pragma unroll
           for (int i = 0; i < UPTS; ++i) {
-            float z[4];
+            float av[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) z[r] = raw_elem<T>(zw[r], i);
+            for (int r = 0; r < 4; ++r) av[r] = raw_elem<T>(zw[r], i);
             float ab[4] = {v[0][i], v[1][i], v[2][i], v[3][i]}, zb[4];
-            jet_adj<FAST>(z, ab, zb, p.e.jet_mode);
+            jet_adj_a(av, ab, zb, p.e.jet_mode);
 #pragma unroll
             for (int r = 0; r < 4; ++r) v[r][i] = zb[r];
           }
