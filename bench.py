@@ -195,12 +195,13 @@ def algorithmic_work(w, n_pts, precision):
     rows, so 4 * points columns).  Per column and hidden GEMM layer (fan_in fi,
     fan_out fo), FLOPs are 2 fi fo for each of forward, adjoint and weight
     gradient (no adjoint into the first GEMM after a frozen Fourier embedding; the
-    tiny raw-coordinate first layer and the output layer's dW are counted in the dW
-    phase only where they are GEMMs).  Bytes per column and layer, e = element size:
-      forward   read A (fi e) + write A, Z (2 fo e)   [+ BF16 value-row low halves,
-                                                       fi/2 + fo/2 bytes per column]
-      adjoint   read Zbar (fo e) + Z (fi e) + write Zbar (fi e)
-      weights   read Zbar (fo e) + A (fi e)
+    tiny raw-coordinate first layer is not a GEMM).  Bytes per column and layer,
+    e = element size (only the activations A are stored; the adjoint is written in
+    them):
+      forward   read A_in (fi e) + write A_out (fo e)   [+ BF16 value-row low halves,
+                                                         fi/2 + fo/2 bytes per column]
+      adjoint   read Zbar_in (fo e) + A_in (fi e) + write Zbar_out (fi e)
+      weights   read Zbar (fo e) + A_in (fi e)
     """
     spec = w.spec
     e = 2 if precision == "bf16" else 4
@@ -212,14 +213,12 @@ def algorithmic_work(w, n_pts, precision):
         if li == 0 and not spec.ff_m:
             continue
         fl["fwd_gemm"] += 2.0 * fi * fo * cols
-        by["fwd_gemm"] += cols * ((fi + 2 * fo) * e + lo * (fi + fo) / 2.0)
+        by["fwd_gemm"] += cols * ((fi + fo) * e + lo * (fi + fo) / 2.0)
         fl["dw_gemm"] += 2.0 * fi * fo * cols
         by["dw_gemm"] += cols * (fo + fi) * e
         if li >= 1:
             fl["adj_gemm"] += 2.0 * fi * fo * cols
             by["adj_gemm"] += cols * (fo + 2 * fi) * e
-    fl["dw_gemm"] += 2.0 * spec.d_out * spec.widths[-1] * cols
-    by["dw_gemm"] += cols * (spec.widths[-1] * e + spec.d_out * 4)
     return fl, by
 
 
@@ -456,6 +455,7 @@ def run_ours(args, ws_n, rank, local):
         "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
         "roofline": roof,
         "roofline_other": roof_alt,
+        "jet_gemms": jet_gemm_rate(flops, prof, args.steps, peaks, precision),
         "clocks": clk,
         "device_status": status,
     }
@@ -469,6 +469,26 @@ def run_ours(args, ws_n, rank, local):
     if not args.no_cpu and ws_n == 1:
         out["cpu_baseline"] = oracle_sample_rate(w, params, B, batch)
     return out
+
+
+def jet_gemm_rate(flops, prof, steps, peaks, precision):
+    """All jet GEMMs of the step together (forward, adjoint, weight gradient):
+    algorithmic FLOPs over their summed device time, against the peak of the
+    precision's engine (BF16: measured; TF32: measured BF16 x the nominal 1/2;
+    FP32: CUDA-core FMA peak from unit counts and the maximum clock)."""
+    ms = sum(prof[k][0] for k in ("fwd_gemm", "adj_gemm", "dw_gemm")) / steps
+    if ms <= 0:
+        return None
+    tf = sum(flops.values()) / (ms / 1e3) / 1e12
+    if precision == "fp32":
+        p_sus = p_burst = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        src = "fp32 FMA: 152 SMs x 128 lanes x 2 FLOP x max clock"
+    else:
+        r = 0.5 if precision == "tf32" else 1.0
+        p_sus, p_burst = r * peaks["bf16_tflops_sustained"], r * peaks["bf16_tflops"]
+        src = "measured bf16" + (" x 1/2 (nominal tf32 ratio)" if r < 1 else "")
+    return {"tflops": round(tf, 1), "ms_per_step": round(ms, 4), "frac_of_sustained": round(tf / p_sus, 4),
+            "frac_of_burst": round(tf / p_burst, 4), "peak_source": src}
 
 
 def _traffic(kernel, workload):
