@@ -50,8 +50,10 @@ def parse():
     ap.add_argument("--no-torch", action="store_true", help="skip the torch autograd baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--chunk-points", type=int, default=0, help="process the batch in chunks of this many points")
-    ap.add_argument("--value-split", action="store_true",
+    ap.add_argument("--value-split", dest="value_split", action="store_true", default=None,
                     help="BF16: split the weights into high/low halves on the value rows only")
+    ap.add_argument("--full-split", dest="value_split", action="store_false",
+                    help="BF16: split the weights on every jet row (overrides the workload's setting)")
     return ap.parse_args()
 
 
@@ -224,8 +226,10 @@ def algorithmic_work(w, n_pts, precision):
 
 # ------------------------------------------------------------------------------ arms
 
-def oracle_sample_rate(w, params, B, batch, target_s=10.0, n_res=8192):
-    """FP64 oracle throughput on a bounded sample of the workload (host cores)."""
+def oracle_sample_rate(w, params, B, batch, target_s=10.0, n_res=8192, net=None):
+    """FP64 oracle throughput on a bounded sample of the workload (host cores).  With
+    `net`, the same sample also runs through the library, and the line states the
+    library's relative error against the oracle there (loss total, gradient L2)."""
     import oracle
     frac = min(1.0, n_res / max(batch.n_res, 1))
     sub = batch.subset(min(n_res, batch.n_res), int(round(batch.n_ic * frac)), int(round(batch.n_bc * frac)))
@@ -240,9 +244,22 @@ def oracle_sample_rate(w, params, B, batch, target_s=10.0, n_res=8192):
         if time.perf_counter() - t0 >= target_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": pts * calls / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-            "sample": f"{sub.n_res} interior + {sub.n_ic} initial + {sub.n_bc} boundary points of {w.name}, "
-                      f"{calls} loss+grad call(s), FP64 numpy"}
+    out = {"value": pts * calls / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+           "sample": f"{sub.n_res} interior + {sub.n_ic} initial + {sub.n_bc} boundary points of {w.name}, "
+                     f"{calls} loss+grad call(s), FP64 numpy"}
+    if net is not None:
+        import torch
+        from paper_2604_15645_gb300 import api
+        terms, g = oracle.loss_and_grad(m, params, B, sub, w.problem.nu, lam)
+        prob = api.make_problem(w.problem.nu, *lam)
+        t_gpu, g_gpu = net.loss_grad(torch.tensor(params, device=net.device), api.DeviceBatch.from_host(sub, net.device),
+                                     prob)
+        t0_gpu = float(t_gpu[0])
+        g_gpu = g_gpu.cpu().numpy().astype(np.float64)
+        out["library_error_vs_oracle"] = {
+            "loss_rel": abs(t0_gpu - terms["total"]) / abs(terms["total"]),
+            "grad_rel_l2": float(np.linalg.norm(g_gpu - g) / np.linalg.norm(g)), "points": pts}
+    return out
 
 
 def torch_autograd_rate(w, params, B, batch, steps=5, warmup=2):
@@ -338,8 +355,9 @@ def run_ours(args, ws_n, rank, local):
     dev = torch.device("cuda", local)
     w, params, B, batch = workload_inputs(args.workload, args.n_res)
     precision = args.precision or w.precision
+    value_split = (w.value_split if args.value_split is None else args.value_split) and precision == "bf16"
     net = api.PinnNet.from_spec(w.spec, precision, device=dev, chunk_points=args.chunk_points,
-                                value_split=args.value_split)
+                                value_split=value_split)
     if B is not None:
         net.set_ff_matrix(B)
     db = api.DeviceBatch.from_host(batch, device=dev)
@@ -447,7 +465,7 @@ def run_ours(args, ws_n, rank, local):
                    "n_res": batch.n_res, "n_ic": batch.n_ic, "n_bc": batch.n_bc, "points_per_step": n_pts,
                    "jet_columns": ncols, "parallelism": f"replicas x{ws_n}",
                    "workspace_gb": round(ws_bytes / 1e9, 2), "chunk_points": args.chunk_points,
-                   "bf16_weight_split": ("value rows" if args.value_split else "all rows") if precision == "bf16" else None,
+                   "bf16_weight_split": ("value rows" if value_split else "all rows") if precision == "bf16" else None,
                    "l2": f"working set {ws_bytes / 1e9:.2f} GB per step > 129 MB L2 (no flush needed)"},
         "e2e": {"value": round(whole_job_rate(n_pts, ws_n, e2e_ms_max), 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms_max, 4)},
@@ -467,7 +485,7 @@ def run_ours(args, ws_n, rank, local):
         except Exception as e:   # reported, not hidden
             out["torch_autograd"] = {"error": repr(e)[:300]}
     if not args.no_cpu and ws_n == 1:
-        out["cpu_baseline"] = oracle_sample_rate(w, params, B, batch)
+        out["cpu_baseline"] = oracle_sample_rate(w, params, B, batch, net=net)
     return out
 
 

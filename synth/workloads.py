@@ -136,6 +136,7 @@ class Workload:
     precision: str
     note: str = ""
     members: list = field(default_factory=list)   # for the many-network family
+    value_split: bool = False   # BF16: split the weights on the value rows only (library option)
 
 
 def layer_dims(spec: NetSpec):
@@ -292,7 +293,7 @@ WORKLOADS = {
     "ns_cavity_6x256": Workload(
         "ns_cavity_6x256", 1, NetSpec(PDE_NS, 2, 3, [256] * 6, ff_m=128, ff_sigma=1.0, rwf=True),
         Problem(nu=1.0 / 100.0), 65536, 0, 4096, "bf16",
-        "steady cavity Re=100, 65,536 interior + 4x1024 wall points"),
+        "steady cavity Re=100, 65,536 interior + 4x1024 wall points", value_split=True),
     "maxwell_te_5x512": Workload(
         "maxwell_te_5x512", 2, NetSpec(PDE_MAXWELL, 3, 3, [512] * 5, rwf=True),
         Problem(nu=0.0), 262144, 16384, 16384, "bf16",
@@ -304,7 +305,7 @@ WORKLOADS = {
     "ns_cavity_8x512": Workload(
         "ns_cavity_8x512", 4, NetSpec(PDE_NS, 2, 3, [512] * 8, ff_m=256, ff_sigma=2.0, rwf=True),
         Problem(nu=1.0 / 100.0), 1048576, 0, 16384, "bf16",
-        "cavity at scale, 1,048,576 interior + 4x4096 wall points"),
+        "cavity at scale, 1,048,576 interior + 4x4096 wall points", value_split=True),
 }
 
 

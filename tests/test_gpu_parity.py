@@ -179,13 +179,13 @@ def test_nonfinite_loss_is_latched(cuda_lib):
 _FULL_ORACLE = {}
 
 
-@pytest.mark.parametrize("precision", ["bf16", "tf32"])
-def test_cavity_full_size_against_chunked_oracle(cuda_lib, precision):
+@pytest.mark.parametrize("precision,value_split", [("bf16", True), ("bf16", False), ("tf32", False)])
+def test_cavity_full_size_against_chunked_oracle(cuda_lib, precision, value_split):
     """The bench workload at full size (65,536 interior + 4,096 wall points) in the
-    launch configuration the bench times; the oracle sums chunks of points (computed
-    once for both precisions)."""
+    launch configuration the bench times (BF16 with the value-row weight split is the
+    workload's default); the oracle sums chunks of points (computed once)."""
     w, p, B, b = make_workload("ns_cavity_6x256")
-    gt, gg = run_gpu(w.spec, p, B, b, w.problem, precision)
+    gt, gg = run_gpu(w.spec, p, B, b, w.problem, precision, value_split=value_split)
     if "ref" not in _FULL_ORACLE:
         _FULL_ORACLE["ref"] = run_oracle(w.spec, p, B, b, w.problem, chunk=8192)
     rt, rg = _FULL_ORACLE["ref"]
