@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--chunk-points", type=int, default=0, help="process the batch in chunks of this many points")
     ap.add_argument("--value-split", dest="value_split", action="store_true", default=None,
                     help="BF16: split the weights into high/low halves on the value rows only")
+    ap.add_argument("--terms", action="store_true",
+                    help="also time the loss-balancing step: per-term gradients + weight update (Sec. 2.6.4)")
     ap.add_argument("--full-split", dest="value_split", action="store_false",
                     help="BF16: split the weights on every jet row (overrides the workload's setting)")
     return ap.parse_args()
@@ -419,6 +421,25 @@ def run_ours(args, ws_n, rank, local):
     e2e_s = (time.perf_counter() - t0) / args.steps
     barrier()
 
+    # the loss-balancing step (per-term gradients + weight update), if asked for
+    terms_ms = None
+    if args.terms:
+        grads = torch.empty(3, p.numel(), dtype=torch.float32, device=dev)
+        lam = torch.ones(3, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            net.loss_grad_terms(p, db, prob, grads=grads)
+            net.loss_balance(grads, lam)
+        torch.cuda.synchronize()
+        barrier()
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        for _ in range(args.steps):
+            net.loss_grad_terms(p, db, prob, grads=grads)
+            net.loss_balance(grads, lam)
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        terms_ms = t0e.elapsed_time(t1e) / args.steps
+
     # max over ranks
     ms_max, e2e_ms_max = max_over_ranks([ms, e2e_s * 1e3], ws_n, dev)
     if rank != 0:
@@ -474,6 +495,9 @@ def run_ours(args, ws_n, rank, local):
         "roofline": roof,
         "roofline_other": roof_alt,
         "jet_gemms": jet_gemm_rate(flops, prof, args.steps, peaks, precision),
+        "loss_balance_step": None if terms_ms is None else {
+            "ms_per_step": round(terms_ms, 4), "value": round(n_pts / (terms_ms / 1e3), 1), "unit": UNIT,
+            "what": "one forward + three reverse sweeps (unweighted PDE/IC/BC gradients) + device weight update"},
         "clocks": clk,
         "device_status": status,
     }

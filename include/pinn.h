@@ -168,6 +168,28 @@ PINN_API pinn_status pinn_loss_grad(pinn_handle* h, const pinn_problem* prob, co
                            const float* d_params, void* d_ws, size_t ws_bytes,
                            double* d_loss_terms, float* d_grad, void* stream);
 
+/* Per-term gradients for loss balancing (Sec. 2.6.4): the loss as pinn_loss_grad
+ * (d_loss_terms, weighted total with prob's lambdas), and in d_grad_terms FP32
+ * [3][P] the unweighted gradients dL_pde/dtheta, dL_ic/dtheta, dL_bc/dtheta
+ * (overwritten).  One forward sweep feeds three reverse sweeps, each seeded with
+ * weight 1 on its term and 0 on the others; so sum_i lambda_i d_grad_terms[i] equals
+ * pinn_loss_grad's gradient up to rounding.  Workspace and chunking as
+ * pinn_loss_grad. */
+PINN_API pinn_status pinn_loss_grad_terms(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch,
+                                          const float* d_params, void* d_ws, size_t ws_bytes,
+                                          double* d_loss_terms, float* d_grad_terms, void* stream);
+
+/* Loss-balancing weights (Sec. 2.6.4, Eqs. 18-19), on the device: the L2 norms
+ * n_i = |d_grad_terms[i]| (FP64, fixed reduction order) go to d_norms [3] (may be
+ * NULL); if `update`, lambda_hat_i = (n_pde + n_ic + n_bc) / (n_i + eps) and
+ * d_lambda[i] = alpha d_lambda[i] + (1 - alpha) lambda_hat_i, for i in (pde, ic, bc)
+ * with n_i > 0 (a term without points keeps its weight).  d_lambda: FP64 device [3],
+ * in/out.  The paper updates with alpha = 0.9 and eps = 1e-9 every 1000 steps: the
+ * caller picks the steps with `update`.  alpha outside [0, 1] or negative eps is
+ * PINN_ERR_INVALID_ARG. */
+PINN_API pinn_status pinn_loss_balance(pinn_handle* h, const float* d_grad_terms, double* d_lambda, double* d_norms,
+                                       double alpha, double eps, int update, void* stream);
+
 /* One Adam step in place over n entries (Sec. 2.6.5): m = b1 m + (1-b1) g,
  * v = b2 v + (1-b2) g^2, theta -= lr * (m/(1-b1^step)) / (sqrt(v/(1-b2^step)) + eps).
  * step is 1-based.  All four arrays FP32 device [n]. */

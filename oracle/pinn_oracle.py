@@ -441,3 +441,30 @@ def adam_step(theta, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     vhat = v / (1.0 - beta2 ** step)
     theta = theta - lr * mhat / (np.sqrt(vhat) + eps)
     return theta, m, v
+
+
+# --------------------------------------------------------------------------------------
+# Loss balancing (Sec. 2.6.4, Eqs. 17-19)
+# --------------------------------------------------------------------------------------
+
+def term_gradients(model, theta, B, batch, nu):
+    """Unweighted gradients of L_pde, L_ic and L_bc (Eq. 17's terms), stacked [3][P]:
+    the plain loss gradient with unit weight on one term and zero on the others."""
+    return np.stack([loss_and_grad(model, theta, B, batch, nu, lam)[1]
+                     for lam in ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0))])
+
+
+def loss_balance(grads, lambdas, alpha=0.9, eps=1e-9, update=True):
+    """Eq. 18: lambda_hat_i = (|g_pde| + |g_ic| + |g_bc|) / |g_i| (the eps guards the
+    division, as the paper's code does); Eq. 19: lambda = alpha lambda + (1 - alpha)
+    lambda_hat.  A term whose gradient is zero (no points) keeps its weight.
+    Returns (new lambdas, norms), float64, order (pde, ic, bc)."""
+    g = np.asarray(grads, dtype=np.float64)
+    norms = np.array([np.sqrt(np.sum(g[i] * g[i])) for i in range(3)])
+    total = norms.sum()
+    lam = np.array(lambdas, dtype=np.float64).copy()
+    if update:
+        for i in range(3):
+            if norms[i] > 0.0:
+                lam[i] = alpha * lam[i] + (1.0 - alpha) * total / (norms[i] + eps)
+    return lam, norms

@@ -25,7 +25,8 @@ EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_by
            "pinn_loss_grad_static", "pinn_tanh_selftest", "pinn_multi_create", "pinn_multi_destroy",
            "pinn_multi_param_offsets", "pinn_multi_workspace_bytes", "pinn_multi_set_ff_matrix",
            "pinn_multi_set_engine", "pinn_multi_get_engine", "pinn_multi_train_step", "pinn_multi_autotune",
-           "pinn_multi_status_poll", "pinn_multi_last_error", "pinn_set_chunk_points"]
+           "pinn_multi_status_poll", "pinn_multi_last_error", "pinn_set_chunk_points",
+           "pinn_loss_grad_terms", "pinn_loss_balance"]
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 8
 PHASE_NAMES = ["rwf", "embed", "fwd_gemm", "out_loss", "dw_gemm", "adj_gemm", "reduce", "other"]
@@ -106,6 +107,10 @@ def load(path: str = LIB_PATH):
     lib.pinn_tensor_core_layers.argtypes = [H, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int32)]
     lib.pinn_profile_read.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     lib.pinn_set_chunk_points.argtypes = [H, C.c_int64]
+    lib.pinn_loss_grad_terms.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
+                                         C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.pinn_loss_balance.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,
+                                      C.c_void_p]
     for name in EXPORTS:
         if name not in ("pinn_last_error", "pinn_status_string", "pinn_version", "pinn_multi_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -155,6 +160,15 @@ def pinn_workspace_bytes(h: int, n_res: int, n_ic: int, n_bc: int) -> int:
     b = C.c_size_t()
     check(load().pinn_workspace_bytes(h, n_res, n_ic, n_bc, C.byref(b)), h)
     return b.value
+
+
+def pinn_loss_grad_terms(h, prob, batch, d_params, d_ws, ws_bytes, d_loss, d_grad_terms, stream):
+    check(load().pinn_loss_grad_terms(h, C.byref(prob), C.byref(batch), d_params, d_ws, ws_bytes, d_loss,
+                                      d_grad_terms, stream), h)
+
+
+def pinn_loss_balance(h, d_grad_terms, d_lambda, d_norms, alpha, eps, update, stream):
+    check(load().pinn_loss_balance(h, d_grad_terms, d_lambda, d_norms, alpha, eps, int(update), stream), h)
 
 
 def pinn_set_chunk_points(h: int, points: int):

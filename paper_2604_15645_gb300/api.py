@@ -114,6 +114,25 @@ class PinnNet:
                             out.data_ptr(), grad.data_ptr(), _stream())
         return out, grad
 
+    def loss_grad_terms(self, params, batch: DeviceBatch, problem, grads=None, out=None):
+        """Loss and the unweighted gradients of the PDE, initial and boundary terms,
+        [3][P] (Sec. 2.6.4): one forward sweep, three reverse sweeps."""
+        assert params.dtype == torch.float32 and params.is_contiguous() and params.numel() == self.P
+        ws = self.workspace(batch)
+        out = self.loss_buf if out is None else out
+        grads = torch.empty(3, self.P, dtype=torch.float32, device=self.device) if grads is None else grads
+        _lib.pinn_loss_grad_terms(self.h, problem, batch.c_struct(), params.data_ptr(), ws.data_ptr(), ws.numel(),
+                                  out.data_ptr(), grads.data_ptr(), _stream())
+        return out, grads
+
+    def loss_balance(self, grads, lambdas, norms=None, alpha=0.9, eps=1e-9, update=True):
+        """Loss-balancing weights (Sec. 2.6.4, Eqs. 18-19) from loss_grad_terms' gradients;
+        `lambdas` is an FP64 device tensor [3] (pde, ic, bc), updated in place."""
+        assert lambdas.dtype == torch.float64 and lambdas.numel() == 3
+        _lib.pinn_loss_balance(self.h, grads.data_ptr(), lambdas.data_ptr(),
+                               norms.data_ptr() if norms is not None else None, alpha, eps, update, _stream())
+        return lambdas
+
     def tensor_core_layers(self, n_res, n_ic, n_bc):
         return _lib.pinn_tensor_core_layers(self.h, n_res, n_ic, n_bc)
 

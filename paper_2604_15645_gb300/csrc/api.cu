@@ -189,7 +189,7 @@ struct PassCtx {
 // One forward + reverse sweep over the points of `b` (the whole batch, or one chunk).
 pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
                      char* ws, size_t ws_bytes, double* d_loss, float* d_grad, cudaStream_t st, bool want_grad,
-                     const PassCtx& pc) {
+                     const PassCtx& pc, float* d_grad_terms = nullptr) {
   pinn_status s = PINN_OK;
   CallPlan cp;
   plan_call(h, b->n_res, b->n_ic, b->n_bc, &cp);
@@ -255,6 +255,16 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     }
   }
 
+  // 4-7 run once for the weighted loss, or once per loss term (weight 1 for that term,
+  // 0 for the others) when the per-term gradients are asked for (Sec. 2.6.4); the
+  // forward jets above are shared.
+  const int nterms = d_grad_terms ? 3 : 1;
+  for (int term = 0; term < nterms; ++term) {
+  const double lam_pde = d_grad_terms ? (term == 0 ? 1.0 : 0.0) : prob->lambda_pde;
+  const double lam_ic = d_grad_terms ? (term == 1 ? 1.0 : 0.0) : prob->lambda_ic;
+  const double lam_bc = d_grad_terms ? (term == 2 ? 1.0 : 0.0) : prob->lambda_bc;
+  float* grad_out = d_grad_terms ? d_grad_terms + (size_t)term * h->P : d_grad;
+
   // 4. Output layer, residual, loss partials, adjoint seed and Zbar_L.
   OutArgs oa{};
   oa.AL = ws + p.A[L]; oa.ALlo = (p.lo && prec == PINN_BF16) ? ws + p.Alo[L] : nullptr;
@@ -263,9 +273,9 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
   oa.n_res = p.n_res; oa.n_ic = p.n_ic; oa.n_bc = p.n_bc; oa.NP = p.NP; oa.NC = p.NC;
   oa.w = cp.lay[L].fin; oa.d_out = h->d_out; oa.pde = h->spec.pde; oa.jet_mode = mode;
   oa.nu = (float)prob->nu;
-  oa.k_pde = pc.N_res ? (float)(prob->lambda_pde / (double)pc.N_res) : 0.f;
-  oa.k_ic = pc.N_ic ? (float)(prob->lambda_ic / (double)pc.N_ic) : 0.f;
-  oa.k_bc = pc.N_bc ? (float)(prob->lambda_bc / (double)pc.N_bc) : 0.f;
+  oa.k_pde = pc.N_res ? (float)(lam_pde / (double)pc.N_res) : 0.f;
+  oa.k_ic = pc.N_ic ? (float)(lam_ic / (double)pc.N_ic) : 0.f;
+  oa.k_bc = pc.N_bc ? (float)(lam_bc / (double)pc.N_bc) : 0.f;
   oa.want_grad = want_grad;
   oa.dwpart = reinterpret_cast<float*>(ws + cp.lay[L].dwpart);
   oa.dbpart = reinterpret_cast<float*>(ws + cp.lay[L].dbpart);
@@ -277,7 +287,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     const cudaError_t e = launch_out_loss(oa, prec, p.nloss_blocks, st);
     if (e != cudaSuccess) return cuda_check(h, e, "output/loss launch");
   }
-  {
+  if (term == 0) {   // the loss terms are unweighted sums; the total uses the problem's weights
   PhaseScope ps_fl(h, st, PH_RED, 1);
   launch_finalize_loss(oa.losspart, p.nloss_blocks, pc.N_res, (b->ic_mask ? pc.N_ic : 0), (b->bc_mask ? pc.N_bc : 0),
                        prob->lambda_pde, prob->lambda_ic, prob->lambda_bc, d_loss, pc.loss_acc, pc.first, pc.last,
@@ -346,7 +356,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
 
   // 7. Ordered FP64 reduction + RWF chain rule into the packed gradient.
   FinalizeArgs fa{};
-  fa.params = d_params; fa.grad = d_grad; fa.ws = ws; fa.L1 = L1; fa.rwf = h->spec.rwf;
+  fa.params = d_params; fa.grad = grad_out; fa.ws = ws; fa.L1 = L1; fa.rwf = h->spec.rwf;
   fa.first_raw = !h->spec.ff_m; fa.nbpart = p.nbpart; fa.accumulate = pc.first ? 0 : 1;
   for (int li = 0; li < L1; ++li) {
     fa.fin[li] = cp.lay[li].fin; fa.fout[li] = cp.lay[li].fout;
@@ -361,6 +371,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     fa.dbstride[li] = (li == 0 && fa.first_raw) ? 1 + h->d_in : 1;
   }
   { PhaseScope ps(h, st, PH_RED, 1); launch_finalize_grad(fa, st); }
+  }   // terms
   return cuda_check(h, cudaGetLastError(), "loss_grad launch");
 }
 
@@ -423,9 +434,10 @@ cudaError_t copy_rows(float* dst, const float* src, int rows, int64_t ld, int64_
 }
 
 pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params, void* d_ws,
-                size_t ws_bytes, double* d_loss, float* d_grad, void* stream, bool want_grad) {
+                size_t ws_bytes, double* d_loss, float* d_grad, void* stream, bool want_grad,
+                float* d_grad_terms = nullptr) {
   if (!h) return PINN_ERR_INVALID_ARG;
-  if (!prob || !d_params || !d_ws || !d_loss || (want_grad && !d_grad)) {
+  if (!prob || !d_params || !d_ws || !d_loss || (want_grad && !d_grad && !d_grad_terms)) {
     set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG;
   }
   if (reinterpret_cast<uintptr_t>(d_ws) % 256) { set_err(h, "workspace must be 256-byte aligned"); return PINN_ERR_INVALID_ARG; }
@@ -437,7 +449,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   const int64_t N = b->n_res + b->n_ic + b->n_bc;
   PassCtx pc{b->n_res, b->n_ic, b->n_bc, true, true, nullptr};
   if (h->chunk_points <= 0 || N <= h->chunk_points)
-    return run_pass(h, prob, b, d_params, ws, ws_bytes, d_loss, d_grad, st, want_grad, pc);
+    return run_pass(h, prob, b, d_params, ws, ws_bytes, d_loss, d_grad, st, want_grad, pc, d_grad_terms);
 
   const int64_t C = h->chunk_points;
   const size_t need = chunked_bytes(h, b->n_res, b->n_ic, b->n_bc);
@@ -464,7 +476,8 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
     if (e != cudaSuccess) return cuda_check(h, e, "chunk staging copy");
     pc.first = (s0 == 0);
     pc.last = (s1 == N);
-    s = run_pass(h, prob, &cb, d_params, ws + cl.pass, ws_bytes - cl.pass, d_loss, d_grad, st, want_grad, pc);
+    s = run_pass(h, prob, &cb, d_params, ws + cl.pass, ws_bytes - cl.pass, d_loss, d_grad, st, want_grad, pc,
+                 d_grad_terms);
     if (s) return s;
   }
   return PINN_OK;
@@ -516,8 +529,10 @@ pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
   h->P = off;
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
-      cudaMalloc(&h->d_status, 256) != cudaSuccess || cudaMemset(h->d_status, 0, 256) != cudaSuccess) {
+      cudaMalloc(&h->d_status, 256) != cudaSuccess || cudaMemset(h->d_status, 0, 256) != cudaSuccess ||
+      cudaMalloc(&h->d_scratch, 4096) != cudaSuccess) {
     if (h->d_status) cudaFree(h->d_status);
+    if (h->d_scratch) cudaFree(h->d_scratch);
     delete h;
     return PINN_ERR_CUDA;
   }
@@ -535,6 +550,7 @@ pinn_status pinn_destroy(pinn_handle* h) {
     delete[] h->prof_launches;
   }
   if (h->d_status) cudaFree(h->d_status);
+  if (h->d_scratch) cudaFree(h->d_scratch);
   delete h;
   return PINN_OK;
 }
@@ -578,6 +594,21 @@ pinn_status pinn_set_ff_matrix(pinn_handle* h, const float* d_B) {
 pinn_status pinn_loss(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch, const float* d_params,
                       void* d_ws, size_t ws_bytes, double* d_loss_terms, void* stream) {
   return run(h, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, nullptr, stream, false);
+}
+
+pinn_status pinn_loss_grad_terms(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch,
+                                 const float* d_params, void* d_ws, size_t ws_bytes, double* d_loss_terms,
+                                 float* d_grad_terms, void* stream) {
+  if (!d_grad_terms) { if (h) set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG; }
+  return run(h, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, nullptr, stream, true, d_grad_terms);
+}
+
+pinn_status pinn_loss_balance(pinn_handle* h, const float* d_grad_terms, double* d_lambda, double* d_norms,
+                              double alpha, double eps, int update, void* stream) {
+  if (!h || !d_grad_terms || !d_lambda || !(alpha >= 0.0 && alpha <= 1.0) || !(eps >= 0.0))
+    return PINN_ERR_INVALID_ARG;
+  launch_loss_balance(d_grad_terms, h->P, d_lambda, d_norms, alpha, eps, update, h->d_scratch, (cudaStream_t)stream);
+  return cuda_check(h, cudaGetLastError(), "loss-balance launch");
 }
 
 pinn_status pinn_loss_grad(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch, const float* d_params,

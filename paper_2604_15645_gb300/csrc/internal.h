@@ -68,6 +68,7 @@ struct pinn_handle {
   pinn::LayerPlan layers[PINN_MAX_HIDDEN + 1];
   const float* ff_B = nullptr;
   int* d_status = nullptr;   // device status word (bit 0 nonfinite, bit 1 timeout)
+  double* d_scratch = nullptr;  // small device scratch (loss-balancing partial sums), allocated at create
   int device = 0;
   int sm_count = 0;
   int64_t chunk_points = 0;  // 0: one pass; else points per chunk (multiple of 64)
@@ -180,6 +181,12 @@ void launch_finalize_grad(const FinalizeArgs& a, cudaStream_t st);
 void launch_finalize_loss(const double* losspart, int nblocks, int64_t n_res, int64_t n_ic, int64_t n_bc,
                           double lam_pde, double lam_ic, double lam_bc, double* out, double* acc, int first, int last,
                           int* status, cudaStream_t st);
+// Loss balancing (Sec. 2.6.4): L2 norms of the three term gradients [3][P] (FP64,
+// fixed order), lambda_hat_i = sum_j |g_j| / (|g_i| + eps) over the terms whose gradient
+// is nonzero, and (update) lambda = alpha lambda + (1 - alpha) lambda_hat.
+// part: 3 x 64 doubles of scratch.
+void launch_loss_balance(const float* g, int64_t P, double* lambda, double* norms, double alpha, double eps,
+                         int update, double* part, cudaStream_t st);
 // Ordered compaction of S split partials [S][n] into S2 [S2][n] (out may not alias in).
 void launch_sum_splits(const float* in, float* out, int S, int S2, int64_t n, cudaStream_t st);
 constexpr int OUT_SUM_SLOTS = 16;   // output-layer dW partials after compaction

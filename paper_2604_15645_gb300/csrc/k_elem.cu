@@ -691,6 +691,44 @@ void launch_finalize_loss(const double* part, int nblocks, int64_t n_res, int64_
 }
 
 // ------------------------------------------------------------------------------------
+// Loss balancing (Sec. 2.6.4, Eqs. 18-19).  Stage 1: per (block, term) sums of squares;
+// stage 2 (one thread): the norms in a fixed order, then the weights.
+// ------------------------------------------------------------------------------------
+constexpr int LB_BLOCKS = 64;
+__global__ void k_sumsq(const float* __restrict__ g, int64_t P, double* part) {
+  const int term = blockIdx.y;
+  const float* x = g + (int64_t)term * P;
+  Acc2 acc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
+    acc.add(x[i] * x[i]);
+  __shared__ double sh[256 / 32];
+  const double s = block_sum_d(acc.value(), sh);
+  if (threadIdx.x == 0) part[term * LB_BLOCKS + blockIdx.x] = s;
+}
+__global__ void k_balance(const double* part, double* lambda, double* norms, double alpha, double eps, int update) {
+  if (threadIdx.x != 0) return;
+  double n[3], sum = 0.0;
+  for (int t = 0; t < 3; ++t) {
+    double s = 0.0;
+    for (int b = 0; b < LB_BLOCKS; ++b) s += part[t * LB_BLOCKS + b];
+    n[t] = sqrt(s);
+    sum += n[t];
+    if (norms) norms[t] = n[t];
+  }
+  if (!update) return;
+  for (int t = 0; t < 3; ++t) {
+    if (n[t] == 0.0) continue;   // a term without points keeps its weight
+    const double hat = sum / (n[t] + eps);
+    lambda[t] = alpha * lambda[t] + (1.0 - alpha) * hat;
+  }
+}
+void launch_loss_balance(const float* g, int64_t P, double* lambda, double* norms, double alpha, double eps,
+                         int update, double* part, cudaStream_t st) {
+  k_sumsq<<<dim3(LB_BLOCKS, 3), 256, 0, st>>>(g, P, part);
+  k_balance<<<1, 32, 0, st>>>(part, lambda, norms, alpha, eps, update);
+}
+
+// ------------------------------------------------------------------------------------
 // Ordered partial-sum compaction: in [S][n] -> out [S2][n], slot k summing splits
 // k*ceil(S/S2) .. in order (compensated), so the finalisation reads S2 splits.
 // ------------------------------------------------------------------------------------

@@ -329,3 +329,34 @@ def test_mutation_wrong_adjoint_sign_is_caught(monkeypatch):
     v = np.random.default_rng(3).standard_normal(p.shape)
     cs = oracle.loss_terms(m, p.astype(np.float64) + 1e-30j * v, B, b, w.problem.nu)["total"].imag / 1e-30
     assert abs(cs - g @ v) > 1e-6 * abs(cs)
+
+
+def test_loss_balance_closed_form():
+    """Eqs. 18-19 on gradients with norms 5, 1 and 10: lambda_hat = 16/5, 16, 16/10,
+    then one moving-average step with alpha = 0.9 from lambda = (1, 1, 1)."""
+    g = np.array([[3.0, 4.0, 0.0], [0.0, 1.0, 0.0], [6.0, 0.0, 8.0]])
+    lam, norms = oracle.loss_balance(g, [1.0, 1.0, 1.0], alpha=0.9, eps=0.0)
+    assert np.allclose(norms, [5.0, 1.0, 10.0], rtol=0, atol=1e-15)
+    assert np.allclose(lam, [0.9 + 0.1 * 3.2, 0.9 + 0.1 * 16.0, 0.9 + 0.1 * 1.6], rtol=1e-15)
+    same, _ = oracle.loss_balance(g, [2.0, 3.0, 4.0], update=False)
+    assert np.array_equal(same, [2.0, 3.0, 4.0])
+    # a term without points (zero gradient) keeps its weight
+    g[1] = 0.0
+    lam, _ = oracle.loss_balance(g, [1.0, 7.0, 1.0], alpha=0.5, eps=0.0)
+    assert lam[1] == 7.0 and np.isclose(lam[0], 0.5 + 0.5 * 15.0 / 5.0)
+
+
+@pytest.mark.parametrize("name", ["burgers1d_4x64", "maxwell_te_5x512"])
+def test_term_gradients_sum_to_the_weighted_gradient(name):
+    """Linearity: sum_i lambda_i dL_i/dtheta equals the gradient of the weighted loss,
+    and a term without points has a zero gradient."""
+    w, p, B, b = make_workload(name, n_res=40, n_ic=12, n_bc=16, random_bias=0.1)
+    m = oracle.Model.from_spec(w.spec)
+    G = oracle.term_gradients(m, p, B, b, w.problem.nu)
+    lam = (0.7, 1.9, 3.1)
+    _, g = oracle.loss_and_grad(m, p, B, b, w.problem.nu, lam)
+    assert np.allclose(lam[0] * G[0] + lam[1] * G[1] + lam[2] * G[2], g, rtol=1e-12, atol=1e-14 * np.abs(g).max())
+    assert all(np.abs(G[i]).max() > 0 for i in range(3))
+    b0 = b.subset(40, 0, 16)
+    G0 = oracle.term_gradients(m, p, B, b0, w.problem.nu)
+    assert np.abs(G0[1]).max() == 0.0
