@@ -97,9 +97,17 @@ def loss(model, batch_t, nu, lambdas=(1.0, 1.0, 1.0)):
             rs = [u * u_x + v * u_y + gp[:, 0] - nu * (u_xx + u_yy),
                   u * v_x + v * v_y + gp[:, 1] - nu * (v_xx + v_yy),
                   u_x + v_y]
-        else:
+        elif spec.pde == 2:
             ge, gx, gy = _d(U[:, 0], X), _d(U[:, 1], X), _d(U[:, 2], X)
             rs = [ge[:, 2] - (gy[:, 0] - gx[:, 1]), gx[:, 2] + ge[:, 1], gy[:, 2] - ge[:, 0]]
+        elif spec.pde == 3:      # advection u_t + c u_x, c = nu (Sec. 4.1)
+            gu = _d(U[:, 0], X)
+            rs = [gu[:, 1] + nu * gu[:, 0]]
+        else:                    # Allen-Cahn u_t - eps u_xx + 5u^3 - 5u, eps = nu (Sec. 4.2)
+            u = U[:, 0]
+            gu = _d(u, X)
+            u_xx = _d(gu[:, 0], X)[:, 0]
+            rs = [gu[:, 1] - nu * u_xx + 5.0 * u ** 3 - 5.0 * u]
         per_eq = [torch.mean(r * r) for r in rs]
         terms["pde_eq"] = per_eq
         terms["pde"] = sum(per_eq)

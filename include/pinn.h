@@ -70,7 +70,9 @@ typedef enum {
 typedef enum {
   PINN_BURGERS_1D = 0,     /* inputs (x,t),   output u;          r = u_t + u u_x - nu u_xx  */
   PINN_NS_STEADY_2D = 1,   /* inputs (x,y),   outputs (u,v,p);   momentum x, y + continuity */
-  PINN_MAXWELL_TE_2D = 2   /* inputs (x,y,t), outputs (Ez,Hx,Hy); TE curl equations       */
+  PINN_MAXWELL_TE_2D = 2,  /* inputs (x,y,t), outputs (Ez,Hx,Hy); TE curl equations       */
+  PINN_ADVECTION_1D = 3,   /* inputs (x,t),   output u;          r = u_t + c u_x, c = nu (Sec. 4.1)      */
+  PINN_ALLEN_CAHN_1D = 4   /* inputs (x,t),   output u;  r = u_t - nu u_xx + 5u^3 - 5u (Sec. 4.2)         */
 } pinn_pde;
 
 /* Network description (pinn_create).  d_in and d_out follow from `pde`
@@ -147,6 +149,22 @@ PINN_API pinn_status pinn_workspace_bytes(const pinn_handle* h, int64_t n_res, i
  * rounding and is deterministic.  Peak workspace then stays at one chunk's size for
  * any batch.  Negative `points` is PINN_ERR_INVALID_ARG. */
 PINN_API pinn_status pinn_set_chunk_points(pinn_handle* h, int64_t points);
+
+/* Temporal causality (Sec. 2.6.8, Eqs. 20-21) for time-dependent problems: the time
+ * domain [t0, t1] is cut into `segments` equal segments (1..32; 0 switches it off);
+ * an interior point at time t belongs to segment floor((t - t0)/(t1 - t0) * M),
+ * clamped.  The PDE term becomes L_pde = (1/M) sum_i omega_i L^i, with L^i the mean
+ * squared residual (summed over equations) of segment i's points, omega_1 = 1 and
+ * omega_i = exp(-eps sum_{k<i} L^k).  The weights are evaluated from the current
+ * parameters and held constant in the gradient (stop-gradient); each call computes
+ * them with an extra output-layer pass before the seeds.  Time is input 1 (x, t) or
+ * input 2 (Maxwell x, y, t); the steady Navier-Stokes problem is
+ * PINN_ERR_UNSUPPORTED.  Causality with point chunking is PINN_ERR_UNSUPPORTED
+ * (the weights need every segment first). */
+PINN_API pinn_status pinn_set_causal(pinn_handle* h, int segments, double eps, double t0, double t1);
+
+/* The weights omega_i of the last loss call with causality on, FP64 device [segments]. */
+PINN_API pinn_status pinn_causal_weights(pinn_handle* h, double* d_weights, void* stream);
 
 /* Register the frozen Fourier-feature matrix B, FP32 device [d_in][m] (Eq. 14).
  * Required before any loss call when ff_m > 0.  The pointer is kept, not copied. */

@@ -42,11 +42,11 @@ from __future__ import annotations
 
 import numpy as np
 
-PDE_BURGERS, PDE_NS, PDE_MAXWELL = 0, 1, 2
+PDE_BURGERS, PDE_NS, PDE_MAXWELL, PDE_ADVECTION, PDE_ALLEN_CAHN = 0, 1, 2, 3, 4
 
 # Which input-derivative order each residual needs (Burgers/NS: second, Maxwell: first).
-PDE_ORDER = {PDE_BURGERS: 2, PDE_NS: 2, PDE_MAXWELL: 1}
-PDE_N_EQ = {PDE_BURGERS: 1, PDE_NS: 3, PDE_MAXWELL: 3}
+PDE_ORDER = {PDE_BURGERS: 2, PDE_NS: 2, PDE_MAXWELL: 1, PDE_ADVECTION: 1, PDE_ALLEN_CAHN: 2}
+PDE_N_EQ = {PDE_BURGERS: 1, PDE_NS: 3, PDE_MAXWELL: 3, PDE_ADVECTION: 1, PDE_ALLEN_CAHN: 1}
 
 
 # --------------------------------------------------------------------------------------
@@ -232,6 +232,8 @@ def residuals(pde, u, u1, u2, nu):
     Maxwell TE (inputs x, y, t; Ez, Hx, Hy):     r1 = Ez_t - (Hy_x - Hx_y)
                                                 r2 = Hx_t + Ez_y
                                                 r3 = Hy_t - Ez_x
+    Advection (Sec. 4.1; inputs x, t; u):        r = u_t + c u_x, with c = nu
+    Allen-Cahn (Sec. 4.2; inputs x, t; u):       r = u_t - eps u_xx + 5 u^3 - 5 u, with eps = nu
     """
     if pde == PDE_BURGERS:
         U, Ux, Ut, Uxx = u[:, 0], u1[0, :, 0], u1[1, :, 0], u2[0, 0, :, 0]
@@ -250,6 +252,11 @@ def residuals(pde, u, u1, u2, nu):
         Hx_y, Hx_t = u1[1, :, 1], u1[2, :, 1]
         Hy_x, Hy_t = u1[0, :, 2], u1[2, :, 2]
         return np.stack([Ez_t - (Hy_x - Hx_y), Hx_t + Ez_y, Hy_t - Ez_x])
+    if pde == PDE_ADVECTION:
+        return np.stack([u1[1, :, 0] + nu * u1[0, :, 0]])
+    if pde == PDE_ALLEN_CAHN:
+        U = u[:, 0]
+        return np.stack([u1[1, :, 0] - nu * u2[0, 0, :, 0] + 5.0 * U ** 3 - 5.0 * U])
     raise ValueError(pde)
 
 
@@ -296,6 +303,16 @@ def residual_seeds(pde, u, u1, u2, nu, coef):
         u1b[1, :, 0] = g2              # Ez_y in r2
         u1b[2, :, 2] = g3              # Hy_t in r3
         u1b[0, :, 0] = -g3             # Ez_x in r3
+    elif pde == PDE_ADVECTION:
+        g = rb[0]
+        u1b[0, :, 0] = nu * g          # d r / d u_x = c
+        u1b[1, :, 0] = g               # d r / d u_t = 1
+    elif pde == PDE_ALLEN_CAHN:
+        U = u[:, 0]
+        g = rb[0]
+        ub[:, 0] = g * (15.0 * U ** 2 - 5.0)   # d r / d u = 15 u^2 - 5
+        u1b[1, :, 0] = g               # d r / d u_t = 1
+        u2b[0, 0, :, 0] = -nu * g      # d r / d u_xx = -eps
     return ub, u1b, u2b
 
 
@@ -327,8 +344,11 @@ def _coords(x):
     return np.asarray(x, dtype=np.float64).T      # SoA [d][N] -> [N, d]
 
 
-def loss_terms(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0)):
-    """Loss terms as a dict: total, pde, pde_eq (list), ic, bc.  Complex-safe."""
+def loss_terms(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=None, omega=None):
+    """Loss terms as a dict: total, pde, pde_eq (list), ic, bc.  Complex-safe.  With
+    `causal` (see loss_and_grad) the PDE term is causally weighted, with the weights
+    `omega` held fixed when given (for complex-step checks of the stop-gradient
+    gradient), else evaluated from the segment losses."""
     theta = np.asarray(theta)
     if not np.iscomplexobj(theta):
         theta = theta.astype(np.float64)
@@ -340,7 +360,18 @@ def loss_terms(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0)):
     if batch.n_res:
         (u, u1, u2), _ = forward(Ws, bs, _coords(batch.x_res), Bd, order)
         r = residuals(model.pde, u, u1, u2, nu)
-        per_eq = [np.mean(r[e] * r[e]) for e in range(r.shape[0])]
+        if causal is None:
+            per_eq = [np.mean(r[e] * r[e]) for e in range(r.shape[0])]
+        else:
+            M = causal["segments"]
+            seg = causal_segments(batch, causal)
+            seg_eq = []
+            for i in range(M):
+                sel = seg == i
+                seg_eq.append([np.mean(r[e][sel] ** 2) if np.any(sel) else 0.0 for e in range(r.shape[0])])
+            seg_eq = np.array(seg_eq)
+            w = causal_weights(seg_eq.real.sum(axis=1), causal["eps"]) if omega is None else np.asarray(omega)
+            per_eq = [np.sum(w * seg_eq[:, e]) / M for e in range(r.shape[0])]
         out["pde_eq"] = per_eq
         out["pde"] = sum(per_eq)
     for key, x, g, mask in (("ic", batch.x_ic, batch.g_ic, batch.ic_mask),
@@ -359,8 +390,33 @@ def loss_terms(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0)):
     return out
 
 
-def loss_and_grad(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0)):
-    """Loss terms and dL/dtheta (packed like theta), float64."""
+def causal_segments(batch, causal):
+    """Time segment of every interior point (Sec. 2.6.8): the time domain [t0, t1] is cut
+    into M equal segments; a point at time t falls in floor((t - t0) / (t1 - t0) * M),
+    clamped to 0..M-1."""
+    t = np.asarray(batch.x_res[causal["t_index"]], dtype=np.float64)
+    M = causal["segments"]
+    seg = np.floor((t - causal["t0"]) / (causal["t1"] - causal["t0"]) * M).astype(np.int64)
+    return np.clip(seg, 0, M - 1)
+
+
+def causal_weights(seg_losses, eps):
+    """Eq. 20: omega_1 = 1, omega_i = exp(-eps sum_{k<i} L^k)."""
+    w = np.ones(len(seg_losses))
+    for i in range(1, len(seg_losses)):
+        w[i] = np.exp(-eps * np.sum(seg_losses[:i]))
+    return w
+
+
+def loss_and_grad(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=None):
+    """Loss terms and dL/dtheta (packed like theta), float64.
+
+    With `causal` = dict(segments=M, eps=eps, t_index=j, t0=t0, t1=t1) the PDE term is
+    the causally weighted one of Sec. 2.6.8 (Eq. 21): L_pde = (1/M) sum_i omega_i L^i,
+    L^i the mean squared residual over segment i's points and omega_i from Eq. 20.  The
+    weights are evaluated at the current parameters and held constant in the gradient
+    (the paper does not say; this is the usual stop-gradient reading of causal
+    weighting).  terms["causal_weights"] holds the omega_i."""
     theta = np.asarray(theta, dtype=np.float64)
     Bd = None if B is None else np.asarray(B, dtype=np.float64)
     layers, Ws, bs = _weights(model, theta)
@@ -375,9 +431,24 @@ def loss_and_grad(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0)):
         N = batch.n_res
         (u, u1, u2), cache = forward(Ws, bs, _coords(batch.x_res), Bd, order)
         r = residuals(model.pde, u, u1, u2, nu)
-        per_eq = [float(np.mean(r[e] * r[e])) for e in range(r.shape[0])]
+        if causal is None:
+            per_eq = [float(np.mean(r[e] * r[e])) for e in range(r.shape[0])]
+            coef = lam_pde / N
+        else:
+            M = causal["segments"]
+            seg = causal_segments(batch, causal)
+            cnt = np.array([np.sum(seg == i) for i in range(M)], dtype=np.float64)
+            seg_eq = np.zeros((M, r.shape[0]))
+            for i in range(M):
+                if cnt[i]:
+                    seg_eq[i] = [np.mean(r[e][seg == i] ** 2) for e in range(r.shape[0])]
+            omega = causal_weights(seg_eq.sum(axis=1), causal["eps"])
+            per_eq = [float(np.sum(omega * seg_eq[:, e]) / M) for e in range(r.shape[0])]
+            terms["causal_weights"] = omega
+            safe = np.where(cnt > 0, cnt, 1.0)
+            coef = lam_pde * (omega / (M * safe))[seg]      # per-point seed scale
         terms["pde_eq"], terms["pde"] = per_eq, sum(per_eq)
-        ub, u1b, u2b = residual_seeds(model.pde, u, u1, u2, nu, lam_pde / N)
+        ub, u1b, u2b = residual_seeds(model.pde, u, u1, u2, nu, coef)
         gW, gb = backward(Ws, cache, ub, u1b, u2b, order)
         for l in range(L1):
             dW[l] += gW[l]

@@ -26,7 +26,7 @@ EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_by
            "pinn_multi_param_offsets", "pinn_multi_workspace_bytes", "pinn_multi_set_ff_matrix",
            "pinn_multi_set_engine", "pinn_multi_get_engine", "pinn_multi_train_step", "pinn_multi_autotune",
            "pinn_multi_status_poll", "pinn_multi_last_error", "pinn_set_chunk_points",
-           "pinn_loss_grad_terms", "pinn_loss_balance"]
+           "pinn_loss_grad_terms", "pinn_loss_balance", "pinn_set_causal", "pinn_causal_weights"]
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 8
 PHASE_NAMES = ["rwf", "embed", "fwd_gemm", "out_loss", "dw_gemm", "adj_gemm", "reduce", "other"]
@@ -107,6 +107,8 @@ def load(path: str = LIB_PATH):
     lib.pinn_tensor_core_layers.argtypes = [H, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int32)]
     lib.pinn_profile_read.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     lib.pinn_set_chunk_points.argtypes = [H, C.c_int64]
+    lib.pinn_set_causal.argtypes = [H, C.c_int, C.c_double, C.c_double, C.c_double]
+    lib.pinn_causal_weights.argtypes = [H, C.c_void_p, C.c_void_p]
     lib.pinn_loss_grad_terms.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
                                          C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.pinn_loss_balance.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,
@@ -169,6 +171,14 @@ def pinn_loss_grad_terms(h, prob, batch, d_params, d_ws, ws_bytes, d_loss, d_gra
 
 def pinn_loss_balance(h, d_grad_terms, d_lambda, d_norms, alpha, eps, update, stream):
     check(load().pinn_loss_balance(h, d_grad_terms, d_lambda, d_norms, alpha, eps, int(update), stream), h)
+
+
+def pinn_set_causal(h, segments, eps, t0, t1):
+    check(load().pinn_set_causal(h, segments, eps, t0, t1), h)
+
+
+def pinn_causal_weights(h, d_weights, stream):
+    check(load().pinn_causal_weights(h, d_weights, stream), h)
 
 
 def pinn_set_chunk_points(h: int, points: int):

@@ -133,6 +133,19 @@ class PinnNet:
                                norms.data_ptr() if norms is not None else None, alpha, eps, update, _stream())
         return lambdas
 
+    def set_causal(self, segments, eps, t0=0.0, t1=1.0):
+        """Temporal causality (Sec. 2.6.8): `segments` time segments over [t0, t1]
+        (0 switches it off), decay `eps`."""
+        _lib.pinn_set_causal(self.h, segments, eps, t0, t1)
+        self._ws_key = None
+        self.causal_segments = segments
+
+    def causal_weights(self):
+        """The segment weights omega_i of the last call, FP64 device tensor."""
+        w = torch.empty(self.causal_segments, dtype=torch.float64, device=self.device)
+        _lib.pinn_causal_weights(self.h, w.data_ptr(), _stream())
+        return w
+
     def tensor_core_layers(self, n_res, n_ic, n_bc):
         return _lib.pinn_tensor_core_layers(self.h, n_res, n_ic, n_bc)
 

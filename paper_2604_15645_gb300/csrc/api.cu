@@ -52,7 +52,7 @@ struct PhaseScope {
 };
 
 int pde_din(int pde) { return pde == PINN_MAXWELL_TE_2D ? 3 : 2; }
-int pde_dout(int pde) { return pde == PINN_BURGERS_1D ? 1 : 3; }
+int pde_dout(int pde) { return (pde == PINN_NS_STEADY_2D || pde == PINN_MAXWELL_TE_2D) ? 3 : 1; }
 
 }  // namespace
 
@@ -85,6 +85,7 @@ pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   q.Zbar[1] = take((size_t)h->w_max * q.NC * q.es);
   q.nloss_blocks = out_loss_blocks(q.NP);
   q.losspart = take((size_t)q.nloss_blocks * 8 * sizeof(double));
+  if (h->causal_M > 0) q.segpart = take((size_t)q.nloss_blocks * CAUSAL_MAX * 4 * sizeof(double));
   *p = q;
   p->total = off;
   return PINN_OK;
@@ -277,17 +278,41 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
   oa.k_ic = pc.N_ic ? (float)(lam_ic / (double)pc.N_ic) : 0.f;
   oa.k_bc = pc.N_bc ? (float)(lam_bc / (double)pc.N_bc) : 0.f;
   oa.want_grad = want_grad;
+  oa.x_res = b->x_res;
   oa.dwpart = reinterpret_cast<float*>(ws + cp.lay[L].dwpart);
   oa.dbpart = reinterpret_cast<float*>(ws + cp.lay[L].dbpart);
   oa.Zbar = ws + p.Zbar[L % 2];
   oa.losspart = reinterpret_cast<double*>(ws + p.losspart);
   oa.status = h->d_status;
-  {
+  const bool causal = h->causal_M > 0;
+  double* causal_omega = h->d_scratch + 256;                           // [CAUSAL_MAX] doubles
+  float* causal_scale = reinterpret_cast<float*>(h->d_scratch + 288);   // [CAUSAL_MAX] floats
+  if (causal) {
+    // Temporal causality (Sec. 2.6.8): a first pass gathers the segment losses, the
+    // weights follow, and the seeds of the second pass are scaled per segment.
+    oa.segments = h->causal_M;
+    oa.t_index = h->spec.pde == PINN_MAXWELL_TE_2D ? 2 : 1;
+    oa.t0 = (float)h->causal_t0;
+    oa.tinv = (float)(h->causal_M / (h->causal_t1 - h->causal_t0));
+    if (term == 0) {
+      OutArgs o1 = oa;
+      o1.want_grad = 0;
+      o1.segpart = reinterpret_cast<double*>(ws + p.segpart);
+      PhaseScope ps(h, st, PH_OUT, 1);
+      const cudaError_t e = launch_out_loss(o1, prec, p.nloss_blocks, st);
+      if (e != cudaSuccess) return cuda_check(h, e, "output/loss launch");
+      launch_finalize_causal(o1.segpart, o1.losspart, p.nloss_blocks, h->causal_M, h->causal_eps,
+                             b->ic_mask ? pc.N_ic : 0, b->bc_mask ? pc.N_bc : 0, prob->lambda_pde, prob->lambda_ic,
+                             prob->lambda_bc, lam_pde, d_loss, causal_omega, causal_scale, h->d_status, st);
+    }
+    oa.seg_scale = lam_pde != 0.0 ? causal_scale : nullptr;
+  }
+  if (!causal || want_grad) {
     PhaseScope ps(h, st, PH_OUT, 1);
     const cudaError_t e = launch_out_loss(oa, prec, p.nloss_blocks, st);
     if (e != cudaSuccess) return cuda_check(h, e, "output/loss launch");
   }
-  if (term == 0) {   // the loss terms are unweighted sums; the total uses the problem's weights
+  if (term == 0 && !causal) {   // the loss terms are unweighted sums; the total uses the problem's weights
   PhaseScope ps_fl(h, st, PH_RED, 1);
   launch_finalize_loss(oa.losspart, p.nloss_blocks, pc.N_res, (b->ic_mask ? pc.N_ic : 0), (b->bc_mask ? pc.N_bc : 0),
                        prob->lambda_pde, prob->lambda_ic, prob->lambda_bc, d_loss, pc.loss_acc, pc.first, pc.last,
@@ -448,6 +473,10 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   char* ws = (char*)d_ws;
   const int64_t N = b->n_res + b->n_ic + b->n_bc;
   PassCtx pc{b->n_res, b->n_ic, b->n_bc, true, true, nullptr};
+  if (h->causal_M > 0 && h->chunk_points > 0 && N > h->chunk_points) {
+    set_err(h, "temporal causality needs all points in one pass (the weights depend on every segment)");
+    return PINN_ERR_UNSUPPORTED;
+  }
   if (h->chunk_points <= 0 || N <= h->chunk_points)
     return run_pass(h, prob, b, d_params, ws, ws_bytes, d_loss, d_grad, st, want_grad, pc, d_grad_terms);
 
@@ -487,6 +516,26 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
 
 extern "C" {
 
+pinn_status pinn_set_causal(pinn_handle* h, int segments, double eps, double t0, double t1) {
+  if (!h || segments < 0 || segments > CAUSAL_MAX || !(eps >= 0.0) || !(t1 > t0)) return PINN_ERR_INVALID_ARG;
+  if (segments > 0 && h->spec.pde == PINN_NS_STEADY_2D) {
+    set_err(h, "the steady Navier-Stokes problem has no time input");
+    return PINN_ERR_UNSUPPORTED;
+  }
+  h->causal_M = segments;
+  h->causal_eps = eps;
+  h->causal_t0 = t0;
+  h->causal_t1 = t1;
+  return PINN_OK;
+}
+
+pinn_status pinn_causal_weights(pinn_handle* h, double* d_weights, void* stream) {
+  if (!h || !d_weights || h->causal_M <= 0) return PINN_ERR_INVALID_ARG;
+  return cuda_check(h, cudaMemcpyAsync(d_weights, h->d_scratch + 256, sizeof(double) * h->causal_M,
+                                       cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+                    "causal weights copy");
+}
+
 pinn_status pinn_set_chunk_points(pinn_handle* h, int64_t points) {
   if (!h || points < 0) return PINN_ERR_INVALID_ARG;
   h->chunk_points = (int64_t)align_up((size_t)points, PT_ALIGN);
@@ -496,7 +545,7 @@ pinn_status pinn_set_chunk_points(pinn_handle* h, int64_t points) {
 pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
   if (!spec || !out) return PINN_ERR_INVALID_ARG;
   *out = nullptr;
-  if (spec->pde < 0 || spec->pde > 2) return PINN_ERR_INVALID_ARG;
+  if (spec->pde < 0 || spec->pde > PINN_ALLEN_CAHN_1D) return PINN_ERR_INVALID_ARG;
   if (spec->n_hidden < 1 || spec->n_hidden > PINN_MAX_HIDDEN) return PINN_ERR_INVALID_ARG;
   for (int i = 0; i < spec->n_hidden; ++i)
     if (spec->widths[i] < 1 || spec->widths[i] > 2048) return PINN_ERR_INVALID_ARG;
@@ -511,7 +560,8 @@ pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
   h->L = spec->n_hidden;
   h->d_in = pde_din(spec->pde);
   h->d_out = pde_dout(spec->pde);
-  h->jet_mode = spec->pde == PINN_BURGERS_1D ? JET_BURGERS : spec->pde == PINN_NS_STEADY_2D ? JET_NS : JET_MAXWELL;
+  // scalar 1-D problems carry [u, u_x, u_t, u_xx]
+  h->jet_mode = spec->pde == PINN_NS_STEADY_2D ? JET_NS : spec->pde == PINN_MAXWELL_TE_2D ? JET_MAXWELL : JET_BURGERS;
   h->first_gemm = spec->ff_m ? 0 : 1;
   int64_t off = 0;
   int prev = spec->ff_m ? 2 * spec->ff_m : h->d_in;

@@ -51,6 +51,7 @@ struct Plan {
   size_t Alo[PINN_MAX_HIDDEN + 1] = {}; // low half of the value rows, tile-major [NP/64][w_l][64]
   size_t Zbar[2] = {};                  // ping-pong adjoints [w_max][NC] compute type
   size_t losspart = 0;                  // per-block loss partials, double [nloss_blocks][8]
+  size_t segpart = 0;                   // causality: per-block segment sums [nloss_blocks][CAUSAL_MAX][4]
   int nloss_blocks = 0;
   int nbpart = 0;                       // column chunks of the bias/first-layer reductions
   size_t total = 0;
@@ -68,7 +69,9 @@ struct pinn_handle {
   pinn::LayerPlan layers[PINN_MAX_HIDDEN + 1];
   const float* ff_B = nullptr;
   int* d_status = nullptr;   // device status word (bit 0 nonfinite, bit 1 timeout)
-  double* d_scratch = nullptr;  // small device scratch (loss-balancing partial sums), allocated at create
+  double* d_scratch = nullptr;  // small device scratch (loss balancing; causal weights), allocated at create
+  int causal_M = 0;          // temporal causality: segments (0 off), decay, time domain
+  double causal_eps = 0.0, causal_t0 = 0.0, causal_t1 = 1.0;
   int device = 0;
   int sm_count = 0;
   int64_t chunk_points = 0;  // 0: one pass; else points per chunk (multiple of 64)
@@ -145,6 +148,13 @@ struct OutArgs {
   float nu;
   float k_pde, k_ic, k_bc;  // 2 lambda / N per set (adjoint seed scale)
   int want_grad;
+  // temporal causality (Sec. 2.6.8): segment of an interior point from its time input
+  int segments;          // 0: off
+  const float* x_res;    // interior coordinates [d_in][n_res] (for the time input)
+  int t_index;           // which input is time
+  float t0, tinv;        // segment = floor((t - t0) * tinv), tinv = M / (t1 - t0)
+  double* segpart;       // phase 1: per-block segment sums [nblocks][CAUSAL_MAX][4] (3 equations + count)
+  const float* seg_scale;  // phase 2: per-segment seed scale lambda omega_i / (M N_i), replacing k_pde
   float* dwpart;         // output-layer dW partials [nblocks][d_out][w] (per block, fixed order)
   float* dbpart;         // output-layer bias partials [d_out][nblocks]
   void* Zbar;            // Zbar_L^T [w][NC] compute type
@@ -187,6 +197,14 @@ void launch_finalize_loss(const double* losspart, int nblocks, int64_t n_res, in
 // part: 3 x 64 doubles of scratch.
 void launch_loss_balance(const float* g, int64_t P, double* lambda, double* norms, double alpha, double eps,
                          int update, double* part, cudaStream_t st);
+// Temporal causality (Sec. 2.6.8, Eqs. 20-21): segment losses from the output/loss
+// kernel's segment partials (fixed order), the weights omega_i (written to omega), the
+// causally weighted loss terms (out[8], with the IC/BC terms from losspart) and the
+// per-segment seed scales lam_seed omega_i / (M N_i) (scale, for the second pass).
+constexpr int CAUSAL_MAX = 32;
+void launch_finalize_causal(const double* segpart, const double* losspart, int nblocks, int M, double eps,
+                            int64_t n_ic, int64_t n_bc, double lam_pde, double lam_ic, double lam_bc, double lam_seed,
+                            double* out, double* omega, float* scale, int* status, cudaStream_t st);
 // Ordered compaction of S split partials [S][n] into S2 [S2][n] (out may not alias in).
 void launch_sum_splits(const float* in, float* out, int S, int S2, int64_t n, cudaStream_t st);
 constexpr int OUT_SUM_SLOTS = 16;   // output-layer dW partials after compaction

@@ -209,21 +209,37 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
 }
 
 // Residual and seed for one point from its output jets U[c][r] (bias included).
+// k: the interior seed scale (k_pde, or the point's causal segment scale); rr: the
+// point's squared residual per equation (interior points).
 template <int D>
-__device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_t idx, float U[3][4], float Ub[3][4],
-                                               double lacc[5]) {
+__device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_t idx, float k, float U[3][4],
+                                               float Ub[3][4], double lacc[5], float rr[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
     for (int r = 0; r < 4; ++r) Ub[c][r] = 0.f;
+  rr[0] = rr[1] = rr[2] = 0.f;
   if (set == SET_RES) {
-    const float k = a.k_pde, nu = a.nu;
+    const float nu = a.nu;
     if (a.pde == PINN_BURGERS_1D) {
       // rows [u, u_x, u_t, u_xx]
       const float r = U[0][2] + U[0][0] * U[0][1] - nu * U[0][3];
-      lacc[0] += (double)r * r;
+      lacc[0] += (double)r * r; rr[0] = r * r;
       const float g2 = 2.f * k * r;
       Ub[0][0] = g2 * U[0][1]; Ub[0][1] = g2 * U[0][0]; Ub[0][2] = g2; Ub[0][3] = -nu * g2;
+    } else if (a.pde == PINN_ADVECTION_1D) {
+      // u_t + c u_x with c = nu (Sec. 4.1)
+      const float r = fmaf(nu, U[0][1], U[0][2]);
+      lacc[0] += (double)r * r; rr[0] = r * r;
+      const float g2 = 2.f * k * r;
+      Ub[0][1] = nu * g2; Ub[0][2] = g2;
+    } else if (a.pde == PINN_ALLEN_CAHN_1D) {
+      // u_t - eps u_xx + 5 u^3 - 5 u with eps = nu (Sec. 4.2)
+      const float u = U[0][0];
+      const float r = U[0][2] - nu * U[0][3] + 5.f * u * (u * u - 1.f);
+      lacc[0] += (double)r * r; rr[0] = r * r;
+      const float g2 = 2.f * k * r;
+      Ub[0][0] = g2 * (15.f * u * u - 5.f); Ub[0][2] = g2; Ub[0][3] = -nu * g2;
     } else if (a.pde == PINN_NS_STEADY_2D) {
       // outputs u, v, p; rows [value, d/dx, d/dy, Laplacian]
       const float u = U[0][0], v = U[1 % D][0];
@@ -231,6 +247,7 @@ __device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_
       const float r2 = u * U[1 % D][1] + v * U[1 % D][2] + U[2 % D][2] - nu * U[1 % D][3];
       const float r3 = U[0][1] + U[1 % D][2];
       lacc[0] += (double)r1 * r1; lacc[1] += (double)r2 * r2; lacc[2] += (double)r3 * r3;
+      rr[0] = r1 * r1; rr[1] = r2 * r2; rr[2] = r3 * r3;
       const float g1 = 2.f * k * r1, g2 = 2.f * k * r2, g3 = 2.f * k * r3;
       Ub[0][0] = g1 * U[0][1] + g2 * U[1 % D][1];
       Ub[1 % D][0] = g1 * U[0][2] + g2 * U[1 % D][2];
@@ -243,6 +260,7 @@ __device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_
       const float r2 = U[1 % D][3] + U[0][2];
       const float r3 = U[2 % D][3] - U[0][1];
       lacc[0] += (double)r1 * r1; lacc[1] += (double)r2 * r2; lacc[2] += (double)r3 * r3;
+      rr[0] = r1 * r1; rr[1] = r2 * r2; rr[2] = r3 * r3;
       const float g1 = 2.f * k * r1, g2 = 2.f * k * r2, g3 = 2.f * k * r3;
       Ub[0][3] = g1; Ub[2 % D][1] = -g1; Ub[1 % D][2] = g1;
       Ub[1 % D][3] = g2; Ub[0][2] = g2;
@@ -286,6 +304,13 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   const int64_t NC = a.NC, ntiles = a.NP / TILE_PTS;
   double acc[5] = {0, 0, 0, 0, 0};
   float dbo[3] = {0.f, 0.f, 0.f};                 // output bias gradient (value-row seeds)
+  // temporal causality, first pass: this block's segment sums (3 equations + count),
+  // accumulated by one thread over the tile's points in a fixed order
+  __shared__ double segacc[CAUSAL_MAX][4];
+  __shared__ int s_seg[TILE_PTS];
+  __shared__ float s_rr[TILE_PTS][3];
+  if (a.segpart)
+    for (int i = threadIdx.x; i < CAUSAL_MAX * 4; i += blockDim.x) segacc[i / 4][i % 4] = 0.0;
   for (int64_t T0 = blockIdx.x; T0 < ntiles; T0 += gridDim.x) {
     const int64_t cb = T0 * TILE_COLS + q0;        // column of row 0 of the first point
     const int64_t p0 = T0 * TILE_PTS + q0;
@@ -331,6 +356,8 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
         }
     float Ub[4][3][4];
     double lacc[5] = {0, 0, 0, 0, 0};
+    int segj[4];
+    float rrj[4][3];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int64_t idx;
@@ -339,10 +366,33 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
 #pragma unroll
         for (int c = 0; c < D; ++c) U[j][c][0] += a.b[c];
       }
-      point_residual<D>(a, set, idx, U[j], Ub[j], lacc);
+      float kp = a.k_pde;
+      segj[j] = -1;
+      if (a.segments && set == SET_RES) {
+        const float tt = a.x_res[(int64_t)a.t_index * a.n_res + idx];
+        segj[j] = min(a.segments - 1, max(0, (int)floorf((tt - a.t0) * a.tinv)));
+        if (a.seg_scale) kp = a.seg_scale[segj[j]];
+      }
+      point_residual<D>(a, set, idx, kp, U[j], Ub[j], lacc, rrj[j]);
     }
     if (sl == 0)
       for (int i = 0; i < 5; ++i) acc[i] += lacc[i];
+    if (a.segpart) {   // uniform over the block
+      if (sl == 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          s_seg[q0 + j] = segj[j];
+          s_rr[q0 + j][0] = rrj[j][0]; s_rr[q0 + j][1] = rrj[j][1]; s_rr[q0 + j][2] = rrj[j][2];
+        }
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int q = 0; q < TILE_PTS; ++q)
+          if (s_seg[q] >= 0) {
+            double* sa = segacc[s_seg[q]];
+            sa[0] += s_rr[q][0]; sa[1] += s_rr[q][1]; sa[2] += s_rr[q][2]; sa[3] += 1.0;
+          }
+      __syncthreads();
+    }
     if (!a.want_grad) continue;
     if (sl == 0) {
 #pragma unroll
@@ -402,6 +452,11 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   for (int i = 0; i < 5; ++i) {
     const double s = block_sum_d(acc[i], sh);
     if (threadIdx.x == 0) a.losspart[(int64_t)blockIdx.x * 8 + i] = s;
+  }
+  if (a.segpart) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < CAUSAL_MAX * 4; i += blockDim.x)
+      a.segpart[(int64_t)blockIdx.x * CAUSAL_MAX * 4 + i] = segacc[i / 4][i % 4];
   }
   if (!a.want_grad) return;
   // block partials of the output layer's dW (warps summed in a fixed order) and bias
@@ -688,6 +743,57 @@ void launch_finalize_loss(const double* part, int nblocks, int64_t n_res, int64_
                           cudaStream_t st) {
   k_finalize_loss<<<1, 256, 0, st>>>(part, nblocks, n_res, n_ic, n_bc, lam_pde, lam_ic, lam_bc, out, acc, first, last,
                                      status);
+}
+
+// ------------------------------------------------------------------------------------
+// Temporal causality (Sec. 2.6.8, Eqs. 20-21).  Thread (i, e) sums segment i's
+// equation-e partials over the blocks in order; thread 0 then forms the segment
+// losses L^i = sum_e S_ie / N_i, omega_1 = 1, omega_i = exp(-eps sum_{k<i} L^k), the
+// weighted PDE term (1/M) sum_i omega_i L^i (and per equation), and the seed scales.
+// ------------------------------------------------------------------------------------
+__global__ void k_finalize_causal(const double* segpart, const double* losspart, int nblocks, int M, double eps,
+                                  int64_t n_ic, int64_t n_bc, double lam_pde, double lam_ic, double lam_bc,
+                                  double lam_seed, double* out, double* omega, float* scale, int* status) {
+  __shared__ double S[CAUSAL_MAX][4];
+  __shared__ double ib[2];
+  const int t = threadIdx.x;
+  if (t < M * 4) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += segpart[(int64_t)b * CAUSAL_MAX * 4 + t];
+    S[t / 4][t % 4] = s;
+  } else if (t >= 128 && t < 130) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += losspart[(int64_t)b * 8 + 3 + (t - 128)];
+    ib[t - 128] = s;
+  }
+  __syncthreads();
+  if (t != 0) return;
+  double cum = 0.0, pe[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < M; ++i) {
+    const double n = S[i][3];
+    const double w = exp(-eps * cum);             // omega_i from the segments before i
+    double Li = 0.0;
+    for (int e = 0; e < 3; ++e) {
+      const double le = n > 0.0 ? S[i][e] / n : 0.0;
+      pe[e] += w * le / M;
+      Li += le;
+    }
+    cum += Li;
+    omega[i] = w;
+    scale[i] = n > 0.0 ? (float)(lam_seed * w / (M * n)) : 0.f;
+  }
+  const double lic = n_ic ? ib[0] / n_ic : 0.0, lbc = n_bc ? ib[1] / n_bc : 0.0;
+  const double lpde = pe[0] + pe[1] + pe[2];
+  const double tot = lam_pde * lpde + lam_ic * lic + lam_bc * lbc;
+  out[0] = tot; out[1] = lpde; out[2] = pe[0]; out[3] = pe[1]; out[4] = pe[2]; out[5] = lic; out[6] = lbc; out[7] = 0.0;
+  if (!isfinite(tot)) atomicOr(status, 1);
+}
+
+void launch_finalize_causal(const double* segpart, const double* losspart, int nblocks, int M, double eps,
+                            int64_t n_ic, int64_t n_bc, double lam_pde, double lam_ic, double lam_bc, double lam_seed,
+                            double* out, double* omega, float* scale, int* status, cudaStream_t st) {
+  k_finalize_causal<<<1, 256, 0, st>>>(segpart, losspart, nblocks, M, eps, n_ic, n_bc, lam_pde, lam_ic, lam_bc,
+                                       lam_seed, out, omega, scale, status);
 }
 
 // ------------------------------------------------------------------------------------

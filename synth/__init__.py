@@ -8,5 +8,5 @@ computation they are compared on.
 from .workloads import (  # noqa: F401
     SplitMix64, NetSpec, Problem, Batch, WORKLOADS, make_workload, layer_dims,
     param_count, init_params, ff_matrix, make_batch, family_specs, make_family,
-    PDE_BURGERS, PDE_NS, PDE_MAXWELL,
+    PDE_BURGERS, PDE_NS, PDE_MAXWELL, PDE_ADVECTION, PDE_ALLEN_CAHN,
 )

@@ -33,7 +33,10 @@ import numpy as np
 PDE_BURGERS = 0
 PDE_NS = 1
 PDE_MAXWELL = 2
-PDE_NAMES = {PDE_BURGERS: "burgers_1d", PDE_NS: "ns_steady_2d", PDE_MAXWELL: "maxwell_te_2d"}
+PDE_ADVECTION = 3
+PDE_ALLEN_CAHN = 4
+PDE_NAMES = {PDE_BURGERS: "burgers_1d", PDE_NS: "ns_steady_2d", PDE_MAXWELL: "maxwell_te_2d",
+             PDE_ADVECTION: "advection_1d", PDE_ALLEN_CAHN: "allen_cahn_1d"}
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -196,7 +199,7 @@ def _r_sequence(n: int, d: int, offset: np.ndarray) -> np.ndarray:
 
 
 def make_batch(pde: int, n_res: int, n_ic: int, n_bc: int, seed_res: int, seed_bd: int,
-               low_discrepancy: bool = False, maxwell_sigma: float = 0.05) -> Batch:
+               low_discrepancy: bool = False, maxwell_sigma: float = 0.05, wave_speed: float = 10.0) -> Batch:
     r = SplitMix64(seed_res)
     q = SplitMix64(seed_bd)
     f32 = np.float32
@@ -215,6 +218,31 @@ def make_batch(pde: int, n_res: int, n_ic: int, n_bc: int, seed_res: int, seed_b
         g_bc = np.zeros((1, n_bc))
         return Batch(x_res.astype(f32), x_ic.astype(f32), g_ic.astype(f32), 1,
                      x_bc.astype(f32), g_bc.astype(f32), 1)
+    if pde == PDE_ADVECTION:
+        # x in [0, 2 pi], t in [0, 1]; IC u(x,0) = sin x (Sec. 4.1).  The periodic walls
+        # are given as Dirichlet targets of the exact solution u = sin(x - c t), with the
+        # wave speed c passed as `wave_speed`.
+        x = 2.0 * np.pi * r.uniform(n_res)
+        t = r.uniform(n_res)
+        xi = 2.0 * np.pi * q.uniform(n_ic)
+        half = n_bc // 2
+        xb = np.concatenate([np.zeros(half), 2.0 * np.pi * np.ones(n_bc - half)])
+        tb = q.uniform(n_bc)
+        return Batch(np.stack([x, t]).astype(f32), np.stack([xi, np.zeros(n_ic)]).astype(f32),
+                     np.sin(xi)[None, :].astype(f32), 1, np.stack([xb, tb]).astype(f32),
+                     np.sin(xb - wave_speed * tb)[None, :].astype(f32), 1)
+    if pde == PDE_ALLEN_CAHN:
+        # x in [-1, 1], t in [0, 1]; IC u(x,0) = x^2 cos(pi x) (Sec. 4.2).  The periodic
+        # walls are given as the Dirichlet value the initial state has there, u = -1.
+        x = -1.0 + 2.0 * r.uniform(n_res)
+        t = r.uniform(n_res)
+        xi = -1.0 + 2.0 * q.uniform(n_ic)
+        half = n_bc // 2
+        xb = np.concatenate([-np.ones(half), np.ones(n_bc - half)])
+        tb = q.uniform(n_bc)
+        return Batch(np.stack([x, t]).astype(f32), np.stack([xi, np.zeros(n_ic)]).astype(f32),
+                     (xi ** 2 * np.cos(np.pi * xi))[None, :].astype(f32), 1, np.stack([xb, tb]).astype(f32),
+                     -np.ones((1, n_bc), dtype=f32), 1)
     if pde == PDE_NS:
         # (x,y) in [0,1]^2; walls bottom, top (lid u=1), left, right; u,v constrained.
         x_res = np.stack([r.uniform(n_res), r.uniform(n_res)])
@@ -302,6 +330,14 @@ WORKLOADS = {
         "burgers_family_64", 3, NetSpec(PDE_BURGERS, 2, 1, [64] * 3),
         Problem(nu=0.01), 0, 256, 256, "bf16",
         "64 independent Burgers nets, uneven width/depth/point count"),
+    "advection1d_4x128": Workload(
+        "advection1d_4x128", 5, NetSpec(PDE_ADVECTION, 2, 1, [128] * 4, ff_m=64, ff_sigma=1.0),
+        Problem(nu=10.0), 16384, 512, 512, "bf16",
+        "linear advection c=10 on [0, 2 pi] x [0, 1], Fourier features; 16,384 interior + 512 initial + 512 boundary"),
+    "allen_cahn1d_4x128": Workload(
+        "allen_cahn1d_4x128", 6, NetSpec(PDE_ALLEN_CAHN, 2, 1, [128] * 4),
+        Problem(nu=1e-4), 16384, 512, 512, "bf16",
+        "Allen-Cahn eps=1e-4 on [-1, 1] x [0, 1]; 16,384 interior + 512 initial + 512 boundary"),
     "ns_cavity_8x512": Workload(
         "ns_cavity_8x512", 4, NetSpec(PDE_NS, 2, 3, [512] * 8, ff_m=256, ff_sigma=2.0, rwf=True),
         Problem(nu=1.0 / 100.0), 1048576, 0, 16384, "bf16",
@@ -323,7 +359,7 @@ def make_workload(name: str, n_res: Optional[int] = None, n_ic: Optional[int] = 
     params = init_params(w.spec, 1000 + k, random_bias)
     B = ff_matrix(w.spec, 4000 + k)
     batch = make_batch(w.spec.pde, n_res, n_ic, n_bc, 2000 + k, 3000 + k,
-                       low_discrepancy=(w.spec.pde == PDE_MAXWELL))
+                       low_discrepancy=(w.spec.pde == PDE_MAXWELL), wave_speed=w.problem.nu)
     return w, params, B, batch
 
 

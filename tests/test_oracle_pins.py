@@ -22,7 +22,7 @@ import torch
 import oracle
 from oracle import pinn_oracle as po
 from synth import Batch, NetSpec, Problem, init_params, ff_matrix, make_batch, make_workload
-from synth.workloads import PDE_BURGERS, PDE_NS, PDE_MAXWELL
+from synth.workloads import PDE_BURGERS, PDE_NS, PDE_MAXWELL, PDE_ADVECTION, PDE_ALLEN_CAHN
 
 
 def _model(spec):
@@ -190,6 +190,32 @@ def test_te_standing_mode_zero_maxwell_residual():
     assert np.max(np.abs(oracle.residuals(PDE_MAXWELL, u, bad, None, 0.0))) > 1e-2
 
 
+def test_advection_exact_solution_zero_residual():
+    # u = sin(x - c t) solves u_t + c u_x = 0 (Sec. 4.1); jets written out by hand.
+    c = 10.0
+    X = np.random.default_rng(7).uniform([0, 0], [2 * math.pi, 1], (64, 2))
+    ph = X[:, 0] - c * X[:, 1]
+    N = X.shape[0]
+    u = np.sin(ph)[:, None]
+    u1 = np.zeros((2, N, 1)); u1[0, :, 0] = np.cos(ph); u1[1, :, 0] = -c * np.cos(ph)
+    assert np.max(np.abs(oracle.residuals(PDE_ADVECTION, u, u1, None, c))) < 1e-12
+    assert np.max(np.abs(oracle.residuals(PDE_ADVECTION, u, u1, None, 0.9 * c))) > 0.5
+
+
+def test_allen_cahn_stationary_kink_is_a_one_neuron_network():
+    # u = tanh(x / delta) with delta = sqrt(2 eps / 5) solves u_t - eps u_xx + 5u^3 - 5u = 0:
+    # eps u_xx = -2 eps/delta^2 u (1 - u^2) = 5 (u^3 - u).  It is one tanh neuron.
+    eps = 1e-2
+    k = 1.0 / math.sqrt(2 * eps / 5)
+    spec = NetSpec(PDE_ALLEN_CAHN, 2, 1, [1])
+    theta = np.array([k, 0.0, 0.0, 1.0, 0.0])
+    X = np.random.default_rng(8).uniform([-1, 0], [1, 1], (50, 2))
+    u, u1, u2 = oracle.output_jets(_model(spec), theta, None, X, 2)
+    np.testing.assert_allclose(u[:, 0], np.tanh(k * X[:, 0]), rtol=1e-14)
+    assert np.max(np.abs(oracle.residuals(PDE_ALLEN_CAHN, u, u1, u2, eps))) < 1e-11
+    assert np.max(np.abs(oracle.residuals(PDE_ALLEN_CAHN, u, u1, u2, 1.2 * eps))) > 1e-2
+
+
 # ------------------------------------------------------------------ loss definitions
 
 def _constant_net_theta(spec, const):
@@ -247,9 +273,10 @@ def test_gradient_complex_step_directions(name):
         assert tc["total"].imag / h == pytest.approx(g @ v, rel=1e-11)
 
 
-@pytest.mark.parametrize("pde,d_in,ff", [(PDE_BURGERS, 2, 0), (PDE_NS, 2, 2), (PDE_MAXWELL, 3, 0)])
+@pytest.mark.parametrize("pde,d_in,ff", [(PDE_BURGERS, 2, 0), (PDE_NS, 2, 2), (PDE_MAXWELL, 3, 0),
+                                         (PDE_ADVECTION, 2, 2), (PDE_ALLEN_CAHN, 2, 0)])
 def test_gradient_every_coordinate_complex_step(pde, d_in, ff):
-    spec = NetSpec(pde, d_in, 1 if pde == PDE_BURGERS else 3, [3, 4], ff_m=ff, ff_sigma=1.0, rwf=True)
+    spec = NetSpec(pde, d_in, 3 if pde in (PDE_NS, PDE_MAXWELL) else 1, [3, 4], ff_m=ff, ff_sigma=1.0, rwf=True)
     p = init_params(spec, 31, 0.2).astype(np.float64)
     B = ff_matrix(spec, 32)
     b = make_batch(pde, 8, 4, 8, 33, 34)
@@ -265,7 +292,8 @@ def test_gradient_every_coordinate_complex_step(pde, d_in, ff):
     np.testing.assert_allclose(g, cs, rtol=1e-10, atol=1e-14 * np.max(np.abs(cs)))
 
 
-@pytest.mark.parametrize("name", ["burgers1d_4x64", "ns_cavity_6x256", "maxwell_te_5x512"])
+@pytest.mark.parametrize("name", ["burgers1d_4x64", "ns_cavity_6x256", "maxwell_te_5x512", "advection1d_4x128",
+                                  "allen_cahn1d_4x128"])
 def test_agrees_with_torch_float64_double_backward(name):
     from baseline import torch_autograd
     w, p, B, b = make_workload(name, n_res=64, n_ic=32, n_bc=32, random_bias=0.1)
@@ -360,3 +388,48 @@ def test_term_gradients_sum_to_the_weighted_gradient(name):
     b0 = b.subset(40, 0, 16)
     G0 = oracle.term_gradients(m, p, B, b0, w.problem.nu)
     assert np.abs(G0[1]).max() == 0.0
+
+
+# ------------------------------------------------------------------ temporal causality
+
+def test_causal_weights_closed_form():
+    """Eq. 20: omega = (1, e^{-eps L1}, e^{-eps (L1 + L2)}, ...)."""
+    w = oracle.causal_weights(np.array([2.0, 3.0, 5.0]), 0.5)
+    assert np.allclose(w, [1.0, math.exp(-1.0), math.exp(-2.5)], rtol=1e-15)
+
+
+def test_causal_loss_reduces_to_segment_mean():
+    """eps = 0 gives omega = 1, so L_pde = (1/M) sum_i L^i; with one segment this is the
+    plain mean, and the gradient equals the plain gradient."""
+    w, p, B, b = make_workload("burgers1d_4x64", n_res=60, n_ic=10, n_bc=10, random_bias=0.1)
+    m = oracle.Model.from_spec(w.spec)
+    one = dict(segments=1, eps=3.0, t_index=1, t0=0.0, t1=1.0)
+    t1, g1 = oracle.loss_and_grad(m, p, B, b, w.problem.nu, causal=one)
+    t0, g0 = oracle.loss_and_grad(m, p, B, b, w.problem.nu)
+    assert t1["pde"] == pytest.approx(t0["pde"], rel=1e-14) and np.allclose(g1, g0, rtol=1e-13, atol=0)
+    four = dict(segments=4, eps=0.0, t_index=1, t0=0.0, t1=1.0)
+    t4, _ = oracle.loss_and_grad(m, p, B, b, w.problem.nu, causal=four)
+    seg = oracle.causal_segments(b, four)
+    (u, u1, u2) = oracle.output_jets(m, p, B, b.x_res.T.astype(np.float64), 2)
+    r = oracle.residuals(w.spec.pde, u, u1, u2, w.problem.nu)[0]
+    assert t4["pde"] == pytest.approx(np.mean([np.mean(r[seg == i] ** 2) for i in range(4)]), rel=1e-13)
+
+
+@pytest.mark.parametrize("name", ["burgers1d_4x64", "maxwell_te_5x512"])
+def test_causal_gradient_complex_step_with_frozen_weights(name):
+    """The gradient holds omega fixed: complex-step on the loss with omega frozen at
+    its current value gives the same directional derivatives."""
+    w, p, B, b = make_workload(name, n_res=48, n_ic=8, n_bc=8, random_bias=0.1)
+    m = oracle.Model.from_spec(w.spec)
+    ti = 2 if w.spec.pde == PDE_MAXWELL else 1
+    cz = dict(segments=3, eps=0.7, t_index=ti, t0=0.0, t1=1.0)
+    terms, g = oracle.loss_and_grad(m, p, B, b, w.problem.nu, (1.0, 0.5, 2.0), causal=cz)
+    assert terms["causal_weights"][0] == 1.0 and np.all(np.diff(terms["causal_weights"]) < 0)
+    rng = np.random.default_rng(12)
+    h = 1e-30
+    for _ in range(3):
+        v = rng.standard_normal(p.size)
+        tc = oracle.loss_terms(m, p.astype(np.float64) + 1j * h * v, B, b, w.problem.nu, (1.0, 0.5, 2.0), causal=cz,
+                               omega=terms["causal_weights"])
+        assert tc["total"].real == pytest.approx(terms["total"], rel=1e-13)
+        assert tc["total"].imag / h == pytest.approx(g @ v, rel=1e-11)
