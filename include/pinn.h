@@ -208,6 +208,33 @@ PINN_API pinn_status pinn_loss_grad_terms(pinn_handle* h, const pinn_problem* pr
 PINN_API pinn_status pinn_loss_balance(pinn_handle* h, const float* d_grad_terms, double* d_lambda, double* d_norms,
                                        double alpha, double eps, int update, void* stream);
 
+/* ---- L-BFGS refinement (Sec. 2.6.5, Eqs. 22-26) ----------------------------------
+ * A pinn_lbfgs keeps the last `history` pairs s_k = theta_{k+1} - theta_k,
+ * y_k = g_{k+1} - g_k on the device (2 history P floats plus five P-vectors, allocated
+ * by pinn_lbfgs_create).  The direction p = -H g is the two-loop recursion (initial
+ * matrix gamma I, gamma = s.y / y.y of the newest pair), with every scalar an FP64
+ * fixed-order reduction kept on the device. */
+typedef struct pinn_lbfgs pinn_lbfgs;
+PINN_API pinn_status pinn_lbfgs_create(pinn_handle* h, int history, pinn_lbfgs** out);   /* history 1..64 */
+PINN_API pinn_status pinn_lbfgs_destroy(pinn_lbfgs* lb);
+/* Forget the pairs and the cached gradient (e.g. after the parameters were changed
+ * outside pinn_lbfgs_step). */
+PINN_API pinn_status pinn_lbfgs_reset(pinn_lbfgs* lb);
+/* One step: the direction from the history, a backtracking line search (Eq. 26)
+ * taking the first lambda in 1, 1/2, 1/4, ... (at most 30 trials) with
+ * L(theta + lambda p) <= L(theta) + 1e-4 lambda g.p (the last trial is taken if none
+ * passes), the gradient at the new point, and the new pair when s.y > 0.  A
+ * non-descent direction restarts from -g with an empty history.  d_params is
+ * updated in place; *loss_out (host, may be NULL) receives the new loss and
+ * *backtracks_out (host, may be NULL) the number of halvings.  Synchronises
+ * `stream` once per line-search trial to read the loss. */
+PINN_API pinn_status pinn_lbfgs_step(pinn_lbfgs* lb, const pinn_problem* prob, const pinn_batch* batch,
+                                     float* d_params, void* d_ws, size_t ws_bytes, double* loss_out,
+                                     int* backtracks_out, void* stream);
+/* Test hooks: p = -H g from the current history (d_g, d_p device [P]); append a pair. */
+PINN_API pinn_status pinn_lbfgs_direction(pinn_lbfgs* lb, const float* d_g, float* d_p, void* stream);
+PINN_API pinn_status pinn_lbfgs_push_pair(pinn_lbfgs* lb, const float* d_s, const float* d_y, void* stream);
+
 /* One Adam step in place over n entries (Sec. 2.6.5): m = b1 m + (1-b1) g,
  * v = b2 v + (1-b2) g^2, theta -= lr * (m/(1-b1^step)) / (sqrt(v/(1-b2^step)) + eps).
  * step is 1-based.  All four arrays FP32 device [n]. */

@@ -539,3 +539,57 @@ def loss_balance(grads, lambdas, alpha=0.9, eps=1e-9, update=True):
             if norms[i] > 0.0:
                 lam[i] = alpha * lam[i] + (1.0 - alpha) * total / (norms[i] + eps)
     return lam, norms
+
+
+# --------------------------------------------------------------------------------------
+# L-BFGS (Sec. 2.6.5, Eqs. 22-26)
+# --------------------------------------------------------------------------------------
+
+def lbfgs_direction(g, S, Y):
+    """p = -H g with H the L-BFGS inverse-Hessian approximation built from the pairs
+    (s_i, y_i), oldest first (Eqs. 22-24; the two-loop recursion of Nocedal and
+    Wright, Algorithm 7.4).  The initial matrix is gamma I, gamma = s.y / y.y of the
+    newest pair (I without pairs)."""
+    q = np.array(g, dtype=np.float64)
+    m = len(S)
+    rho = [1.0 / float(np.dot(Y[i], S[i])) for i in range(m)]
+    alpha = [0.0] * m
+    for i in range(m - 1, -1, -1):
+        alpha[i] = rho[i] * float(np.dot(S[i], q))
+        q = q - alpha[i] * Y[i]
+    gamma = float(np.dot(S[-1], Y[-1]) / np.dot(Y[-1], Y[-1])) if m else 1.0
+    r = gamma * q
+    for i in range(m):
+        beta = rho[i] * float(np.dot(Y[i], r))
+        r = r + (alpha[i] - beta) * S[i]
+    return -r
+
+
+def lbfgs_minimize(f_and_g, x0, history=10, steps=20, c1=1e-4, max_backtracks=30):
+    """L-BFGS with a backtracking line search (Eq. 26) that accepts the first step
+    length lambda in 1, 1/2, 1/4, ... meeting the sufficient-decrease condition
+    f(x + lambda p) <= f(x) + c1 lambda g.p; pairs with s.y <= 0 are not stored.
+    Returns the iterates' losses and the final x."""
+    x = np.array(x0, dtype=np.float64)
+    fx, g = f_and_g(x)
+    S, Y, losses = [], [], [fx]
+    for _ in range(steps):
+        p = lbfgs_direction(g, S, Y)
+        gp = float(np.dot(g, p))
+        if gp >= 0.0:                       # not a descent direction: restart from -g
+            S, Y = [], []
+            p, gp = -g, -float(np.dot(g, g))
+        lam = 1.0
+        for _ in range(max_backtracks):
+            fn, gn = f_and_g(x + lam * p)
+            if fn <= fx + c1 * lam * gp:
+                break
+            lam *= 0.5
+        s, y = lam * p, gn - g
+        if float(np.dot(s, y)) > 0.0:
+            S.append(s); Y.append(y)
+            if len(S) > history:
+                S.pop(0); Y.pop(0)
+        x, fx, g = x + lam * p, fn, gn
+        losses.append(fx)
+    return losses, x

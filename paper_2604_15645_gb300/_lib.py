@@ -26,7 +26,9 @@ EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_by
            "pinn_multi_param_offsets", "pinn_multi_workspace_bytes", "pinn_multi_set_ff_matrix",
            "pinn_multi_set_engine", "pinn_multi_get_engine", "pinn_multi_train_step", "pinn_multi_autotune",
            "pinn_multi_status_poll", "pinn_multi_last_error", "pinn_set_chunk_points",
-           "pinn_loss_grad_terms", "pinn_loss_balance", "pinn_set_causal", "pinn_causal_weights"]
+           "pinn_loss_grad_terms", "pinn_loss_balance", "pinn_set_causal", "pinn_causal_weights",
+           "pinn_lbfgs_create", "pinn_lbfgs_destroy", "pinn_lbfgs_reset", "pinn_lbfgs_step", "pinn_lbfgs_direction",
+           "pinn_lbfgs_push_pair"]
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 8
 PHASE_NAMES = ["rwf", "embed", "fwd_gemm", "out_loss", "dw_gemm", "adj_gemm", "reduce", "other"]
@@ -109,6 +111,13 @@ def load(path: str = LIB_PATH):
     lib.pinn_set_chunk_points.argtypes = [H, C.c_int64]
     lib.pinn_set_causal.argtypes = [H, C.c_int, C.c_double, C.c_double, C.c_double]
     lib.pinn_causal_weights.argtypes = [H, C.c_void_p, C.c_void_p]
+    lib.pinn_lbfgs_create.argtypes = [H, C.c_int, C.POINTER(C.c_void_p)]
+    lib.pinn_lbfgs_destroy.argtypes = [C.c_void_p]
+    lib.pinn_lbfgs_reset.argtypes = [C.c_void_p]
+    lib.pinn_lbfgs_step.argtypes = [C.c_void_p, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p,
+                                    C.c_void_p, C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p]
+    lib.pinn_lbfgs_direction.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.pinn_lbfgs_push_pair.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.pinn_loss_grad_terms.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
                                          C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.pinn_loss_balance.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,

@@ -2,6 +2,8 @@
 all computation from the library's kernels."""
 from __future__ import annotations
 
+import ctypes as C
+
 import torch
 
 from . import _lib
@@ -238,3 +240,41 @@ class PinnMulti:
 
     def status_poll(self):
         return _lib.load().pinn_multi_status_poll(self.h, _stream())
+
+
+class Lbfgs:
+    """L-BFGS refinement (Sec. 2.6.5) over a PinnNet's loss and gradient: the history,
+    the two-loop direction and the backtracking line search run in the library."""
+
+    def __init__(self, net: PinnNet, history=10):
+        self.net = net
+        h = C.c_void_p()
+        _lib.check(_lib.load().pinn_lbfgs_create(net.h, history, C.byref(h)), net.h)
+        self.lb = h.value
+
+    def __del__(self):
+        lb = getattr(self, "lb", None)
+        if lb:
+            try:
+                _lib.load().pinn_lbfgs_destroy(lb)
+            except Exception:
+                pass
+            self.lb = None
+
+    def reset(self):
+        _lib.check(_lib.load().pinn_lbfgs_reset(self.lb))
+
+    def step(self, params, batch: DeviceBatch, problem):
+        """One L-BFGS step in place on params; returns (loss, line-search halvings)."""
+        ws = self.net.workspace(batch)
+        loss, bt = C.c_double(), C.c_int()
+        _lib.check(_lib.load().pinn_lbfgs_step(self.lb, C.byref(problem), C.byref(batch.c_struct()), params.data_ptr(),
+                                               ws.data_ptr(), ws.numel(), C.byref(loss), C.byref(bt), _stream()),
+                   self.net.h)
+        return loss.value, bt.value
+
+    def direction(self, g, p):
+        _lib.check(_lib.load().pinn_lbfgs_direction(self.lb, g.data_ptr(), p.data_ptr(), _stream()))
+
+    def push_pair(self, s, y):
+        _lib.check(_lib.load().pinn_lbfgs_push_pair(self.lb, s.data_ptr(), y.data_ptr(), _stream()))

@@ -433,3 +433,32 @@ def test_causal_gradient_complex_step_with_frozen_weights(name):
                                omega=terms["causal_weights"])
         assert tc["total"].real == pytest.approx(terms["total"], rel=1e-13)
         assert tc["total"].imag / h == pytest.approx(g @ v, rel=1e-11)
+
+
+# ------------------------------------------------------------------ L-BFGS
+
+def test_lbfgs_secant_condition():
+    """Eq. 24: with the newest pair, H y = s holds exactly for the two-loop matrix."""
+    rng = np.random.default_rng(21)
+    n = 12
+    S = [rng.standard_normal(n) for _ in range(4)]
+    A = rng.standard_normal((n, n)); A = A @ A.T + n * np.eye(n)
+    Y = [A @ s for s in S]
+    Hy = -oracle.lbfgs_direction(Y[-1], S, Y)
+    np.testing.assert_allclose(Hy, S[-1], rtol=1e-10, atol=1e-12)
+    # without history the direction is steepest descent
+    g = rng.standard_normal(n)
+    np.testing.assert_array_equal(oracle.lbfgs_direction(g, [], []), -g)
+
+
+def test_lbfgs_minimises_a_quadratic():
+    """On f = x.A x / 2 - b.x the iterates decrease monotonically and reach the
+    minimiser A^-1 b."""
+    rng = np.random.default_rng(22)
+    n = 8
+    A = rng.standard_normal((n, n)); A = A @ A.T + np.eye(n)
+    b = rng.standard_normal(n)
+    fg = lambda x: (0.5 * x @ A @ x - b @ x, A @ x - b)
+    losses, x = oracle.lbfgs_minimize(fg, np.zeros(n), history=10, steps=60)
+    assert all(l1 <= l0 + 1e-12 for l0, l1 in zip(losses, losses[1:]))
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-6, atol=1e-8)
