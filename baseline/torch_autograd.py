@@ -55,7 +55,10 @@ class TorchPINN:
             W = V if s is None else torch.exp(s)[:, None] * V
             h = h @ W.T + b
             if i < n - 1:
-                h = torch.tanh(h)
+                if getattr(self.spec, "activation", "tanh") == "sine":
+                    h = torch.sin(self.spec.omega0 * h)
+                else:
+                    h = torch.tanh(h)
         return h
 
     def flat_grad(self):

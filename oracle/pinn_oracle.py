@@ -24,7 +24,12 @@ What it computes, in the paper's order and notation:
     summed; L = lambda_pde L_pde + lambda_ic L_ic + lambda_bc L_bc.
   * Gradient: an explicit reverse sweep through the jets (adjoint of each step
     above), then the RWF chain rule dL/dV = exp(s) * dL/dW, dL/ds_i =
-    sum_j dL/dW_ij W_ij.  B gets no gradient.
+    sum_j dL/dW_ij W_ij.  B gets no gradient in training; ff_matrix_grad gives
+    dL/dB from the adjoint of the input jets for callers that want it.
+  * Strict periodic input map (Sec. 2.6.3, Eq. 16): w = [cos(2 pi x_k / P_k),
+    sin(2 pi x_k / P_k)] per input k, in that order; the gradient with respect to
+    the periods P_k (P_t is trainable in the paper) by the same input adjoint.
+  * Periodic activation (Sec. 2.6, Table 1): sin(omega0 z) in place of tanh.
   * Adam (Sec. 2.6.5): biased moments, bias correction, theta -= alpha m_hat /
     (sqrt(v_hat) + eps).
 
@@ -88,6 +93,20 @@ def effective_weight(V, s):
 # tanh and its derivatives (from sech^2, independently of the identity t'' = -2 t t')
 # --------------------------------------------------------------------------------------
 
+def sine_derivs(z, omega):
+    """The periodic activation sin(omega z) (appendix, periodic activation function) and
+    its first three derivatives."""
+    s, c = np.sin(omega * z), np.cos(omega * z)
+    return s, omega * c, -omega ** 2 * s, -omega ** 3 * c
+
+
+def act_derivs(z, act):
+    """(t, t', t'', t''') of the hidden activation: act None / "tanh" or ("sine", omega)."""
+    if act is None or act == "tanh":
+        return tanh_derivs(z)
+    return sine_derivs(z, act[1])
+
+
 def tanh_derivs(z):
     t = np.tanh(z)
     sech2 = 1.0 / np.cosh(z) ** 2
@@ -100,6 +119,28 @@ def tanh_derivs(z):
 # --------------------------------------------------------------------------------------
 # Input jets
 # --------------------------------------------------------------------------------------
+
+def periodic_input_jets(X, P, order):
+    """Jets of the strict periodic input map of Eq. 16 at points X [N, d], in the
+    paper's order [cos(2 pi x_1/P_1), sin(2 pi x_1/P_1), cos(2 pi x_2/P_2), ...].
+    With theta_k = 2 pi / P_k: d cos/dx_k = -sin theta_k, d sin/dx_k = cos theta_k,
+    d^2 cos/dx_k^2 = -cos theta_k^2, d^2 sin/dx_k^2 = -sin theta_k^2 (other
+    directions 0).  Complex-safe in X and P."""
+    N, d = X.shape
+    th = 2.0 * np.pi / np.asarray(P)
+    dt = np.result_type(X, th)
+    a = np.zeros((N, 2 * d), dtype=dt)
+    a1 = np.zeros((d, N, 2 * d), dtype=dt) if order >= 1 else None
+    a2 = np.zeros((d, d, N, 2 * d), dtype=dt) if order >= 2 else None
+    for k in range(d):
+        c, s = np.cos(th[k] * X[:, k]), np.sin(th[k] * X[:, k])
+        a[:, 2 * k], a[:, 2 * k + 1] = c, s
+        if order >= 1:
+            a1[k, :, 2 * k], a1[k, :, 2 * k + 1] = -s * th[k], c * th[k]
+        if order >= 2:
+            a2[k, k, :, 2 * k], a2[k, k, :, 2 * k + 1] = -c * th[k] ** 2, -s * th[k] ** 2
+    return a, a1, a2
+
 
 def input_jets(X, B, order):
     """Jets of the network input for points X [N, d].
@@ -139,15 +180,16 @@ def input_jets(X, B, order):
 # Forward jets through the MLP
 # --------------------------------------------------------------------------------------
 
-def forward(Ws, bs, X, B, order):
+def forward(Ws, bs, X, B, order, act=None, periods=None):
     """Propagate jets through hidden tanh layers and the final linear layer.
 
     Linear layer (Eq. 4): z = a W^T + b on the value; derivatives are linear:
     z1_k = a1_k W^T, z2_kl = a2_kl W^T.  Activation (Eq. 5) by the chain rule:
     a = t(z), a1_k = t'(z) z1_k, a2_kl = t''(z) z1_k z1_l + t'(z) z2_kl.
     Returns output jets (u, u1, u2) and the per-layer cache for the reverse sweep.
+    With `periods` the input is the periodic map of Eq. 16 instead.
     """
-    a, a1, a2 = input_jets(X, B, order)
+    a, a1, a2 = input_jets(X, B, order) if periods is None else periodic_input_jets(X, periods, order)
     cache = []
     L = len(Ws) - 1
     for l in range(L):
@@ -156,7 +198,7 @@ def forward(Ws, bs, X, B, order):
         z1 = a1 @ W.T if order >= 1 else None
         z2 = a2 @ W.T if order >= 2 else None
         cache.append((a, a1, a2, z, z1, z2))
-        t, t1, t2, _ = tanh_derivs(z)
+        t, t1, t2, _ = act_derivs(z, act)
         na = t
         na1 = t1[None] * z1 if order >= 1 else None
         na2 = None
@@ -171,8 +213,10 @@ def forward(Ws, bs, X, B, order):
     return (u, u1, u2), cache
 
 
-def backward(Ws, cache, ubar, u1bar, u2bar, order):
-    """Reverse sweep through the jets of forward().  Returns (dW list, db list).
+def backward(Ws, cache, ubar, u1bar, u2bar, order, act=None, input_adjoint=False):
+    """Reverse sweep through the jets of forward().  Returns (dW list, db list), and
+    with `input_adjoint` also the adjoint of the input jets (abar, a1bar, a2bar) =
+    (gbar W_1, g1bar W_1, g2bar W_1) of the first layer.
 
     Output layer: abar = ubar W, a1bar_k = u1bar_k W, a2bar_kl = u2bar_kl W;
     dW = ubar^T a + sum_k u1bar_k^T a1_k + sum_kl u2bar_kl^T a2_kl; db = sum ubar.
@@ -194,13 +238,16 @@ def backward(Ws, cache, ubar, u1bar, u2bar, order):
         dWs[l] = dW
         dbs[l] = gbar.sum(axis=0)
         if l == 0:
+            if input_adjoint:
+                W = Ws[0]
+                return dWs, dbs, (gbar @ W, g1bar @ W if order >= 1 else None, g2bar @ W if order >= 2 else None)
             break
         W = Ws[l]
         abar = gbar @ W
         a1bar = g1bar @ W if order >= 1 else None
         a2bar = g2bar @ W if order >= 2 else None
         _, _, _, z, z1, z2 = cache[l - 1]
-        t, t1, t2, t3 = tanh_derivs(z)
+        t, t1, t2, t3 = act_derivs(z, act)
         zbar = abar * t1
         if order >= 1:
             zbar = zbar + np.sum(a1bar * t2[None] * z1, axis=0)
@@ -323,14 +370,17 @@ def residual_seeds(pde, u, u1, u2, nu, coef):
 class Model:
     """Architecture description for the oracle (plain data)."""
 
-    def __init__(self, pde, d_in, d_out, widths, ff_m=0, rwf=False):
+    def __init__(self, pde, d_in, d_out, widths, ff_m=0, rwf=False, act=None, periods=None):
         self.pde, self.d_in, self.d_out = pde, d_in, d_out
         self.widths, self.ff_m, self.rwf = list(widths), ff_m, rwf
-        self.dims = layer_dims(d_in, d_out, widths, ff_m)
+        self.act = act       # None (tanh) or ("sine", omega0)
+        self.periods = periods   # None, or [P_1..P_d]: the periodic input map of Eq. 16
+        self.dims = layer_dims(d_in, d_out, widths, d_in if periods is not None else ff_m)
 
     @classmethod
     def from_spec(cls, spec):
-        return cls(spec.pde, spec.d_in, spec.d_out, spec.widths, spec.ff_m, spec.rwf)
+        act = ("sine", spec.omega0) if getattr(spec, "activation", "tanh") == "sine" else None
+        return cls(spec.pde, spec.d_in, spec.d_out, spec.widths, spec.ff_m, spec.rwf, act)
 
 
 def _weights(model, theta):
@@ -352,13 +402,13 @@ def loss_terms(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=None,
     theta = np.asarray(theta)
     if not np.iscomplexobj(theta):
         theta = theta.astype(np.float64)
-    Bd = None if B is None else np.asarray(B, dtype=np.float64)
+    Bd = None if B is None else (np.asarray(B) if np.iscomplexobj(B) else np.asarray(B, dtype=np.float64))
     _, Ws, bs = _weights(model, theta)
     lam_pde, lam_ic, lam_bc = lambdas
     order = PDE_ORDER[model.pde]
     out = {"pde_eq": [0.0] * PDE_N_EQ[model.pde], "pde": 0.0, "ic": 0.0, "bc": 0.0}
     if batch.n_res:
-        (u, u1, u2), _ = forward(Ws, bs, _coords(batch.x_res), Bd, order)
+        (u, u1, u2), _ = forward(Ws, bs, _coords(batch.x_res), Bd, order, model.act, model.periods)
         r = residuals(model.pde, u, u1, u2, nu)
         if causal is None:
             per_eq = [np.mean(r[e] * r[e]) for e in range(r.shape[0])]
@@ -379,7 +429,7 @@ def loss_terms(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=None,
         n = x.shape[1]
         if n == 0 or mask == 0:
             continue
-        (u, _, _), _ = forward(Ws, bs, _coords(x), Bd, 0)
+        (u, _, _), _ = forward(Ws, bs, _coords(x), Bd, 0, model.act, model.periods)
         term = 0.0
         for c in range(model.d_out):
             if mask >> c & 1:
@@ -408,7 +458,73 @@ def causal_weights(seg_losses, eps):
     return w
 
 
-def loss_and_grad(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=None):
+def ff_matrix_grad_terms(X, B, abar, a1bar, a2bar):
+    """dL/dB [d, m] of the Fourier embedding (Eq. 14) from the adjoint of its jets.
+    With phi_j = sum_e x_e B_ej, c = cos phi_j, s = sin phi_j, the jets are
+      value [c, s];  d/dx_k [-s B_kj, c B_kj];  d2/dx_k dx_l [-c B_kj B_lj, -s B_kj B_lj],
+    and their derivatives with respect to B_ej (dphi/dB_ej = x_e):
+      value        [-s x_e, c x_e]
+      d/dx_k       [-c x_e B_kj - s [k=e],  -s x_e B_kj + c [k=e]]
+      d2/dx_k dx_l [s x_e B_kj B_lj - c ([k=e] B_lj + [l=e] B_kj),
+                    -c x_e B_kj B_lj - s ([k=e] B_lj + [l=e] B_kj)]."""
+    N, d = X.shape
+    m = B.shape[1]
+    phi = X @ B
+    c, s = np.cos(phi), np.sin(phi)
+    g = np.zeros((d, m))
+    for e in range(d):
+        xe = X[:, e:e + 1]
+        g[e] += np.sum(abar[:, :m] * (-s * xe) + abar[:, m:] * (c * xe), axis=0)
+        if a1bar is not None:
+            for k in range(d):
+                Bk = B[k][None, :]
+                dc = -c * xe * Bk - (s if k == e else 0.0)
+                ds = -s * xe * Bk + (c if k == e else 0.0)
+                g[e] += np.sum(a1bar[k][:, :m] * dc + a1bar[k][:, m:] * ds, axis=0)
+        if a2bar is not None:
+            for k in range(d):
+                for l in range(d):
+                    Bk, Bl = B[k][None, :], B[l][None, :]
+                    cross = (Bl if k == e else 0.0) + (Bk if l == e else 0.0)
+                    dc = s * xe * Bk * Bl - c * cross
+                    ds = -c * xe * Bk * Bl - s * cross
+                    g[e] += np.sum(a2bar[k, l][:, :m] * dc + a2bar[k, l][:, m:] * ds, axis=0)
+    return g
+
+
+def period_grad_terms(X, P, abar, a1bar, a2bar):
+    """dL/dP [d] of the periodic map (Eq. 16) from the adjoint of its jets.  With
+    theta_k = 2 pi / P_k (dtheta_k/dP_k = -theta_k / P_k), c = cos(theta_k x_k),
+    s = sin(theta_k x_k), the derivatives with respect to theta_k are
+      value [-s x_k, c x_k];  d/dx_k [-c x_k theta_k - s, -s x_k theta_k + c];
+      d2/dx_k^2 [s x_k theta_k^2 - 2 c theta_k, -c x_k theta_k^2 - 2 s theta_k]."""
+    N, d = X.shape
+    g = np.zeros(d)
+    for k in range(d):
+        th = 2.0 * np.pi / P[k]
+        x = X[:, k]
+        c, s = np.cos(th * x), np.sin(th * x)
+        gt = np.sum(abar[:, 2 * k] * (-s * x) + abar[:, 2 * k + 1] * (c * x))
+        if a1bar is not None:
+            gt += np.sum(a1bar[k][:, 2 * k] * (-c * x * th - s) + a1bar[k][:, 2 * k + 1] * (-s * x * th + c))
+        if a2bar is not None:
+            gt += np.sum(a2bar[k, k][:, 2 * k] * (s * x * th ** 2 - 2 * c * th)
+                         + a2bar[k, k][:, 2 * k + 1] * (-c * x * th ** 2 - 2 * s * th))
+        g[k] = gt * (-th / P[k])
+    return g
+
+
+def _input_grad(model, Bd, X, adj, terms):
+    """Adds one point set's dL/dB (Fourier features) or dL/dP (periodic map) to terms."""
+    if model.periods is not None:
+        g = period_grad_terms(X, np.asarray(model.periods, dtype=np.float64), *adj)
+        terms["grad_periods"] = terms.get("grad_periods", 0.0) + g
+    elif Bd is not None:
+        g = ff_matrix_grad_terms(X, Bd, *adj)
+        terms["grad_B"] = terms.get("grad_B", 0.0) + g
+
+
+def loss_and_grad(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=None, input_grad=False):
     """Loss terms and dL/dtheta (packed like theta), float64.
 
     With `causal` = dict(segments=M, eps=eps, t_index=j, t0=t0, t1=t1) the PDE term is
@@ -416,7 +532,11 @@ def loss_and_grad(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=No
     L^i the mean squared residual over segment i's points and omega_i from Eq. 20.  The
     weights are evaluated at the current parameters and held constant in the gradient
     (the paper does not say; this is the usual stop-gradient reading of causal
-    weighting).  terms["causal_weights"] holds the omega_i."""
+    weighting).  terms["causal_weights"] holds the omega_i.
+
+    With `input_grad`, terms["grad_B"] ([d, m], Fourier features) or
+    terms["grad_periods"] ([d], periodic map) holds the gradient with respect to the
+    input map's matrix or periods."""
     theta = np.asarray(theta, dtype=np.float64)
     Bd = None if B is None else np.asarray(B, dtype=np.float64)
     layers, Ws, bs = _weights(model, theta)
@@ -429,7 +549,7 @@ def loss_and_grad(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=No
 
     if batch.n_res:
         N = batch.n_res
-        (u, u1, u2), cache = forward(Ws, bs, _coords(batch.x_res), Bd, order)
+        (u, u1, u2), cache = forward(Ws, bs, _coords(batch.x_res), Bd, order, model.act, model.periods)
         r = residuals(model.pde, u, u1, u2, nu)
         if causal is None:
             per_eq = [float(np.mean(r[e] * r[e])) for e in range(r.shape[0])]
@@ -449,7 +569,11 @@ def loss_and_grad(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=No
             coef = lam_pde * (omega / (M * safe))[seg]      # per-point seed scale
         terms["pde_eq"], terms["pde"] = per_eq, sum(per_eq)
         ub, u1b, u2b = residual_seeds(model.pde, u, u1, u2, nu, coef)
-        gW, gb = backward(Ws, cache, ub, u1b, u2b, order)
+        if input_grad:
+            gW, gb, adj = backward(Ws, cache, ub, u1b, u2b, order, model.act, input_adjoint=True)
+            _input_grad(model, Bd, _coords(batch.x_res), adj, terms)
+        else:
+            gW, gb = backward(Ws, cache, ub, u1b, u2b, order, model.act)
         for l in range(L1):
             dW[l] += gW[l]
             db[l] += gb[l]
@@ -459,7 +583,7 @@ def loss_and_grad(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=No
         n = x.shape[1]
         if n == 0 or mask == 0:
             continue
-        (u, _, _), cache = forward(Ws, bs, _coords(x), Bd, 0)
+        (u, _, _), cache = forward(Ws, bs, _coords(x), Bd, 0, model.act, model.periods)
         ub = np.zeros_like(u)
         term = 0.0
         for c in range(model.d_out):
@@ -468,7 +592,11 @@ def loss_and_grad(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=No
                 term += float(np.mean(e * e))
                 ub[:, c] = 2.0 * lam * e / n
         terms[key] = term
-        gW, gb = backward(Ws, cache, ub, None, None, 0)
+        if input_grad:
+            gW, gb, adj = backward(Ws, cache, ub, None, None, 0, model.act, input_adjoint=True)
+            _input_grad(model, Bd, _coords(x), adj, terms)
+        else:
+            gW, gb = backward(Ws, cache, ub, None, None, 0, model.act)
         for l in range(L1):
             dW[l] += gW[l]
             db[l] += gb[l]
@@ -494,7 +622,7 @@ def output_jets(model, theta, B, X, order):
         theta = theta.astype(np.float64)
     Bd = None if B is None else np.asarray(B, dtype=np.float64)
     _, Ws, bs = _weights(model, theta)
-    (u, u1, u2), _ = forward(Ws, bs, X, Bd, order)
+    (u, u1, u2), _ = forward(Ws, bs, X, Bd, order, model.act, model.periods)
     return u, u1, u2
 
 

@@ -87,6 +87,8 @@ class NetSpec:
     rwf: bool = False
     rwf_mu: float = 1.0
     rwf_sigma: float = 0.1
+    activation: str = "tanh"    # or "sine": sin(omega0 z) in every hidden layer
+    omega0: float = 1.0
 
 
 @dataclass

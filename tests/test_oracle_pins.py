@@ -462,3 +462,195 @@ def test_lbfgs_minimises_a_quadratic():
     losses, x = oracle.lbfgs_minimize(fg, np.zeros(n), history=10, steps=60)
     assert all(l1 <= l0 + 1e-12 for l0, l1 in zip(losses, losses[1:]))
     np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-6, atol=1e-8)
+
+
+# ------------------------------------------------------------------ sine activation
+
+def _sine_spec(pde, d_in, d_out, widths, ff=0, rwf=True, omega0=2.0):
+    return NetSpec(pde, d_in, d_out, widths, ff_m=ff, ff_sigma=1.0, rwf=rwf, activation="sine", omega0=omega0)
+
+
+def test_sine_derivatives_against_differences():
+    z = np.linspace(-3, 3, 37)
+    w = 2.5
+    t, t1, t2, t3 = po.sine_derivs(z, w)
+    np.testing.assert_allclose(t, np.sin(w * z), rtol=1e-15)
+    def rich(f, h=1e-3):
+        d = lambda hh: (f(z + hh) - f(z - hh)) / (2 * hh)
+        return (4 * d(h / 2) - d(h)) / 3
+    np.testing.assert_allclose(rich(lambda x: po.sine_derivs(x, w)[0]), t1, atol=1e-9)
+    np.testing.assert_allclose(rich(lambda x: po.sine_derivs(x, w)[1]), t2, atol=1e-8)
+    np.testing.assert_allclose(rich(lambda x: po.sine_derivs(x, w)[2]), t3, atol=1e-7)
+    # sin'' = -w^2 sin: the second derivative is the function itself, scaled
+    np.testing.assert_allclose(t2, -w * w * t, atol=1e-13)
+
+
+@pytest.mark.parametrize("rwf", [False, True])
+def test_sine_one_hidden_layer_closed_form(rwf):
+    w0 = 1.7
+    spec = _sine_spec(PDE_BURGERS, 2, 1, [5], rwf=rwf, omega0=w0)
+    theta = init_params(spec, 13, random_bias=0.3).astype(np.float64)
+    m = _model(spec)
+    assert m.act == ("sine", w0)
+    layers = po.unpack(theta, m.dims, rwf)
+    W1 = po.effective_weight(layers[0][0], layers[0][1]); b1 = layers[0][2]
+    c = po.effective_weight(layers[1][0], layers[1][1])[0]; d = layers[1][2][0]
+    X = np.random.default_rng(6).uniform(-1, 1, (7, 2))
+    u, u1, u2 = oracle.output_jets(m, theta, None, X, 2)
+    z = X @ W1.T + b1
+    np.testing.assert_allclose(u[:, 0], np.sin(w0 * z) @ c + d, rtol=1e-14)
+    for k in range(2):
+        np.testing.assert_allclose(u1[k, :, 0], (w0 * np.cos(w0 * z) * W1[:, k]) @ c, rtol=1e-13, atol=1e-15)
+        for l in range(2):
+            closed = (-w0 ** 2 * np.sin(w0 * z) * W1[:, k] * W1[:, l]) @ c
+            np.testing.assert_allclose(u2[k, l, :, 0], closed, rtol=1e-12, atol=1e-14)
+
+
+def test_sine_neuron_is_an_exact_advection_solution():
+    # u = sin(k (x - c t)) solves u_t + c u_x = 0: one sine neuron, omega0 folded into W
+    k, c, w0 = 1.0, 10.0, 3.0
+    spec = _sine_spec(PDE_ADVECTION, 2, 1, [1], rwf=False, omega0=w0)
+    theta = np.array([k / w0, -k * c / w0, 0.0, 1.0, 0.0])
+    X = np.random.default_rng(7).uniform([0, 0], [2 * np.pi, 1], (40, 2))
+    u, u1, u2 = oracle.output_jets(_model(spec), theta, None, X, 2)
+    np.testing.assert_allclose(u[:, 0], np.sin(k * (X[:, 0] - c * X[:, 1])), rtol=1e-12, atol=1e-14)
+    r = oracle.residuals(PDE_ADVECTION, u, u1, u2, c)
+    assert np.max(np.abs(r)) < 1e-12
+    assert np.max(np.abs(oracle.residuals(PDE_ADVECTION, u, u1, u2, 1.1 * c))) > 1e-2
+
+
+@pytest.mark.parametrize("pde,d_in,ff", [(PDE_BURGERS, 2, 0), (PDE_NS, 2, 2), (PDE_MAXWELL, 3, 0),
+                                         (PDE_ALLEN_CAHN, 2, 2)])
+def test_sine_gradient_every_coordinate_complex_step(pde, d_in, ff):
+    spec = _sine_spec(pde, d_in, 3 if pde in (PDE_NS, PDE_MAXWELL) else 1, [3, 4], ff=ff)
+    p = init_params(spec, 35, 0.2).astype(np.float64)
+    B = ff_matrix(spec, 36)
+    b = make_batch(pde, 8, 4, 8, 37, 38)
+    if pde == PDE_NS:
+        b = Batch(b.x_res, b.x_ic, b.g_ic, 0, b.x_bc, b.g_bc, 0b111)
+    m = _model(spec)
+    _, g = oracle.loss_and_grad(m, p, B, b, 0.02)
+    h = 1e-30
+    cs = np.empty_like(p)
+    for i in range(p.size):
+        pc = p.astype(complex); pc[i] += 1j * h
+        cs[i] = oracle.loss_terms(m, pc, B, b, 0.02)["total"].imag / h
+    np.testing.assert_allclose(g, cs, rtol=1e-10, atol=1e-14 * np.max(np.abs(cs)))
+
+
+@pytest.mark.parametrize("name", ["burgers1d_4x64", "ns_cavity_6x256", "maxwell_te_5x512"])
+def test_sine_agrees_with_torch_float64_double_backward(name):
+    from baseline import torch_autograd
+    w, p, B, b = make_workload(name, n_res=48, n_ic=16, n_bc=16, random_bias=0.1)
+    w.spec.widths = [24] * 3
+    w.spec.activation, w.spec.omega0 = "sine", 1.5
+    p = init_params(w.spec, 79, 0.1)
+    m = _model(w.spec)
+    terms, g = oracle.loss_and_grad(m, p, B, b, w.problem.nu)
+    tl, tg, _ = torch_autograd.loss_and_grad(w.spec, p, B, b, w.problem.nu)
+    assert float(tl) == pytest.approx(terms["total"], rel=1e-12)
+    np.testing.assert_allclose(tg.numpy(), g, rtol=1e-9, atol=1e-12 * np.max(np.abs(g)))
+
+
+def test_mutation_sine_third_derivative_sign_is_caught(monkeypatch):
+    """Plant a sign error in sin''' (used only by the reverse sweep); the complex-step
+    gradient pin must see it."""
+    good = po.sine_derivs
+    monkeypatch.setattr(po, "sine_derivs", lambda z, w: (lambda t: (t[0], t[1], t[2], -t[3]))(good(z, w)))
+    with pytest.raises(AssertionError):
+        test_sine_gradient_every_coordinate_complex_step(PDE_BURGERS, 2, 0)
+
+
+# ------------------------------------------------------------------ input-map gradients, periodic map
+
+def _small_case(pde, d_in, d_out, ff, seed):
+    spec = NetSpec(pde, d_in, d_out, [5, 4], ff_m=ff, ff_sigma=1.0, rwf=True)
+    p = init_params(spec, seed, 0.2).astype(np.float64)
+    b = make_batch(pde, 9, 4, 6, seed + 1, seed + 2)
+    if pde == PDE_NS:
+        b = Batch(b.x_res, b.x_ic, b.g_ic, 0, b.x_bc, b.g_bc, 0b111)
+    return spec, p, b
+
+
+@pytest.mark.parametrize("pde,d_in,d_out", [(PDE_BURGERS, 2, 1), (PDE_NS, 2, 3), (PDE_MAXWELL, 3, 3)])
+def test_fourier_matrix_gradient_complex_step(pde, d_in, d_out):
+    spec, p, b = _small_case(pde, d_in, d_out, 3, 41)
+    B = ff_matrix(spec, 44).astype(np.float64)
+    m = _model(spec)
+    t, _ = oracle.loss_and_grad(m, p, B, b, 0.02, input_grad=True)
+    cs = np.zeros_like(B)
+    for e in range(B.shape[0]):
+        for j in range(B.shape[1]):
+            Bc = B.astype(complex); Bc[e, j] += 1e-30j
+            cs[e, j] = oracle.loss_terms(m, p, Bc, b, 0.02)["total"].imag / 1e-30
+    np.testing.assert_allclose(t["grad_B"], cs, rtol=1e-10, atol=1e-13 * np.max(np.abs(cs)))
+
+
+def _periodic_model(pde, d_in, d_out, P):
+    return oracle.Model(pde, d_in, d_out, [5, 4], 0, True, None, np.asarray(P, dtype=np.float64))
+
+
+@pytest.mark.parametrize("pde,d_in,d_out", [(PDE_ADVECTION, 2, 1), (PDE_NS, 2, 3), (PDE_MAXWELL, 3, 3)])
+def test_period_gradient_complex_step(pde, d_in, d_out):
+    spec, p, b = _small_case(pde, d_in, d_out, d_in, 51)     # fan-in 2 d_in, like the map
+    P = np.array([2 * np.pi, 1.3, 0.9])[:d_in]
+    m = _periodic_model(pde, d_in, d_out, P)
+    t, g = oracle.loss_and_grad(m, p, None, b, 0.02, input_grad=True)
+    cs = np.zeros(d_in)
+    for k in range(d_in):
+        Pc = P.astype(complex); Pc[k] += 1e-30j
+        m.periods = Pc
+        cs[k] = oracle.loss_terms(m, p, None, b, 0.02)["total"].imag / 1e-30
+    np.testing.assert_allclose(t["grad_periods"], cs, rtol=1e-10, atol=1e-14 * np.max(np.abs(cs)))
+
+
+def test_periodic_map_is_periodic_with_its_derivatives():
+    # the paper's point of Eq. 16: values and derivatives agree one period apart
+    P = np.array([2.0, 1.5])
+    spec, p, _ = _small_case(PDE_BURGERS, 2, 1, 2, 61)
+    m = _periodic_model(PDE_BURGERS, 2, 1, P)
+    X = np.random.default_rng(9).uniform(0, 1, (10, 2))
+    for k in range(2):
+        Xs = X.copy(); Xs[:, k] += P[k]
+        a = oracle.output_jets(m, p, None, X, 2)
+        c = oracle.output_jets(m, p, None, Xs, 2)
+        for u, v in zip(a, c):
+            np.testing.assert_allclose(u, v, rtol=1e-11, atol=1e-12)
+    # a different period breaks it
+    m.periods = P * 1.1
+    a = oracle.output_jets(m, p, None, X, 0)[0]
+    c = oracle.output_jets(m, p, None, X + np.array([P[0], 0.0]), 0)[0]
+    assert np.max(np.abs(a - c)) > 1e-3
+
+
+def ff_column_order(d):
+    """Fourier-feature column q of the diagonal map holds periodic-map column perm[q]."""
+    return [2 * q for q in range(d)] + [2 * q + 1 for q in range(d)]
+
+
+def periodic_to_ff_params(theta, dims, d):
+    """Permute the first layer's input columns from the paper's order
+    [cos x1, sin x1, cos x2, ...] to the Fourier-feature order [cos x1, cos x2, ..., sin x1, ...]."""
+    fin, fout = dims[0]
+    V = theta[:fin * fout].reshape(fout, fin)
+    out = theta.copy()
+    out[:fin * fout] = V[:, ff_column_order(d)].ravel()
+    return out
+
+
+@pytest.mark.parametrize("pde,d_in,d_out", [(PDE_ALLEN_CAHN, 2, 1), (PDE_MAXWELL, 3, 3)])
+def test_periodic_map_equals_diagonal_fourier_features(pde, d_in, d_out):
+    """Eq. 16 is Eq. 14 with B = diag(2 pi / P) up to the first layer's column order,
+    and dL/dP_k = -(2 pi / P_k^2) dL/dB_kk: the form the GPU path computes it in."""
+    spec, p, b = _small_case(pde, d_in, d_out, d_in, 71)
+    P = np.array([2.0, 1.0, 1.5])[:d_in]
+    mp = _periodic_model(pde, d_in, d_out, P)
+    tp, gp = oracle.loss_and_grad(mp, p, None, b, 0.02, input_grad=True)
+    mf = _model(spec)
+    pf = periodic_to_ff_params(p, mf.dims, d_in)
+    B = np.diag(2 * np.pi / P)
+    tf, gf = oracle.loss_and_grad(mf, pf, B, b, 0.02, input_grad=True)
+    assert tf["total"] == pytest.approx(tp["total"], rel=1e-13)
+    np.testing.assert_allclose(gf, periodic_to_ff_params(gp, mf.dims, d_in), rtol=1e-11, atol=1e-14)
+    dP = -2 * np.pi / P ** 2 * np.diag(tf["grad_B"])
+    np.testing.assert_allclose(dP, tp["grad_periods"], rtol=1e-11)
