@@ -150,6 +150,17 @@ PINN_API pinn_status pinn_workspace_bytes(const pinn_handle* h, int64_t n_res, i
  * any batch.  Negative `points` is PINN_ERR_INVALID_ARG. */
 PINN_API pinn_status pinn_set_chunk_points(pinn_handle* h, int64_t points);
 
+/* Hidden-layer activation: PINN_ACT_TANH (the default, Eq. 5) or PINN_ACT_SINE, the
+ * periodic activation sin(omega0 z) of Sec. 2.6 (Table 1), in every hidden layer.
+ * A sine network keeps each hidden layer's pre-activation jets for the adjoint (one
+ * more FP32 [w_l][4 N] array per layer, counted by pinn_workspace_bytes), because
+ * the sign of cos(omega0 z) cannot be recovered from the stored sin; its jet GEMMs
+ * run on CUDA cores (TF32 then computes in FP32; BF16 keeps BF16 activations).
+ * Unknown `act`, or omega0 not finite and > 0: PINN_ERR_INVALID_ARG. */
+#define PINN_ACT_TANH 0
+#define PINN_ACT_SINE 1
+PINN_API pinn_status pinn_set_activation(pinn_handle* h, int act, double omega0);
+
 /* Temporal causality (Sec. 2.6.8, Eqs. 20-21) for time-dependent problems: the time
  * domain [t0, t1] is cut into `segments` equal segments (1..32; 0 switches it off);
  * an interior point at time t belongs to segment floor((t - t0)/(t1 - t0) * M),
@@ -169,6 +180,28 @@ PINN_API pinn_status pinn_causal_weights(pinn_handle* h, double* d_weights, void
 /* Register the frozen Fourier-feature matrix B, FP32 device [d_in][m] (Eq. 14).
  * Required before any loss call when ff_m > 0.  The pointer is kept, not copied. */
 PINN_API pinn_status pinn_set_ff_matrix(pinn_handle* h, const float* d_B);
+
+/* Strict periodic input map (Sec. 2.6.3, Eq. 16) for a network with ff_m = d_in:
+ * the input is mapped to [cos(2 pi x_k / P_k) for k..., sin(2 pi x_k / P_k) for k...],
+ * i.e. the Fourier embedding with B = diag(2 pi / P) held by the handle (a device
+ * copy is made here; no pinn_set_ff_matrix needed).  This is the paper's map up to
+ * the order of the first layer's input columns (the paper interleaves cos and sin per
+ * input).  `periods` is a host array [d_in] of finite values > 0; anything else, or
+ * ff_m != d_in, is PINN_ERR_INVALID_ARG.  pinn_set_ff_matrix switches back to a
+ * caller-owned B. */
+PINN_API pinn_status pinn_set_periodic(pinn_handle* h, const double* periods);
+
+/* pinn_loss_grad plus the gradient with respect to the input map: with a Fourier
+ * matrix, d_grad_ff receives dL/dB, FP32 device [d_in][m] (Eq. 14 treated as
+ * trainable); with the periodic map it receives dL/dP, FP32 device [d_in], the
+ * gradient with respect to the periods (the paper trains P_t).  It is computed from
+ * the adjoint of the input jets, W_1^T Zbar_1, by CUDA-core kernels after the first
+ * layer's weight gradient; FP64 block partials are summed in a fixed order.  With
+ * point chunking it accumulates over chunks like the parameter gradient.  A network
+ * without Fourier features, or d_grad_ff NULL, is PINN_ERR_INVALID_ARG. */
+PINN_API pinn_status pinn_loss_grad_ff(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch,
+                                       const float* d_params, void* d_ws, size_t ws_bytes, double* d_loss_terms,
+                                       float* d_grad, float* d_grad_ff, void* stream);
 
 /* Loss only.  d_loss_terms receives PINN_LOSS_TERMS doubles:
  *   [0] total = lambda_pde*L_pde + lambda_ic*L_ic + lambda_bc*L_bc

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(PKG, "libpinn.so")
 PINN_MAX_HIDDEN = 16
 PINN_LOSS_TERMS = 8
 PINN_FP32, PINN_TF32, PINN_BF16 = 0, 1, 2
+PINN_BURGERS_1D, PINN_NS_STEADY_2D, PINN_MAXWELL_TE_2D, PINN_ADVECTION_1D, PINN_ALLEN_CAHN_1D = 0, 1, 2, 3, 4
 PINN_FLAG_CUDA_CORES, PINN_FLAG_BF16_VALUE_SPLIT = 1, 4
 PRECISIONS = {"fp32": PINN_FP32, "tf32": PINN_TF32, "bf16": PINN_BF16}
 STATUS = {0: "PINN_OK", 1: "PINN_ERR_INVALID_ARG", 2: "PINN_ERR_UNSUPPORTED", 3: "PINN_ERR_CUDA",
@@ -28,7 +29,8 @@ EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_by
            "pinn_multi_status_poll", "pinn_multi_last_error", "pinn_set_chunk_points",
            "pinn_loss_grad_terms", "pinn_loss_balance", "pinn_set_causal", "pinn_causal_weights",
            "pinn_lbfgs_create", "pinn_lbfgs_destroy", "pinn_lbfgs_reset", "pinn_lbfgs_step", "pinn_lbfgs_direction",
-           "pinn_lbfgs_push_pair"]
+           "pinn_lbfgs_push_pair", "pinn_set_activation", "pinn_set_periodic", "pinn_loss_grad_ff"]
+PINN_ACT_TANH, PINN_ACT_SINE = 0, 1
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 8
 PHASE_NAMES = ["rwf", "embed", "fwd_gemm", "out_loss", "dw_gemm", "adj_gemm", "reduce", "other"]
@@ -109,6 +111,10 @@ def load(path: str = LIB_PATH):
     lib.pinn_tensor_core_layers.argtypes = [H, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int32)]
     lib.pinn_profile_read.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     lib.pinn_set_chunk_points.argtypes = [H, C.c_int64]
+    lib.pinn_set_activation.argtypes = [H, C.c_int, C.c_double]
+    lib.pinn_set_periodic.argtypes = [H, C.POINTER(C.c_double)]
+    lib.pinn_loss_grad_ff.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
+                                      C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.pinn_set_causal.argtypes = [H, C.c_int, C.c_double, C.c_double, C.c_double]
     lib.pinn_causal_weights.argtypes = [H, C.c_void_p, C.c_void_p]
     lib.pinn_lbfgs_create.argtypes = [H, C.c_int, C.POINTER(C.c_void_p)]
@@ -194,6 +200,10 @@ def pinn_set_chunk_points(h: int, points: int):
     check(load().pinn_set_chunk_points(h, points), h)
 
 
+def pinn_set_activation(h: int, act: int, omega0: float):
+    check(load().pinn_set_activation(h, act, omega0), h)
+
+
 def pinn_set_ff_matrix(h: int, d_B: int):
     check(load().pinn_set_ff_matrix(h, d_B), h)
 
@@ -205,6 +215,16 @@ def pinn_loss(h, prob, batch, d_params, d_ws, ws_bytes, d_loss, stream):
 def pinn_loss_grad(h, prob, batch, d_params, d_ws, ws_bytes, d_loss, d_grad, stream):
     check(load().pinn_loss_grad(h, C.byref(prob), C.byref(batch), d_params, d_ws, ws_bytes, d_loss, d_grad,
                                 stream), h)
+
+
+def pinn_loss_grad_ff(h, prob, batch, d_params, d_ws, ws_bytes, d_loss, d_grad, d_grad_ff, stream):
+    check(load().pinn_loss_grad_ff(h, C.byref(prob), C.byref(batch), d_params, d_ws, ws_bytes, d_loss, d_grad,
+                                   d_grad_ff, stream), h)
+
+
+def pinn_set_periodic(h, periods):
+    arr = (C.c_double * len(periods))(*[float(x) for x in periods])
+    check(load().pinn_set_periodic(h, arr), h)
 
 
 def pinn_adam_step(d_params, d_grad, d_m, d_v, n, step, lr, beta1, beta2, eps, stream):

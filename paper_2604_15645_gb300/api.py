@@ -52,7 +52,7 @@ class PinnNet:
     """One network handle (pinn_create) plus a cached workspace."""
 
     def __init__(self, pde, widths, ff_m=0, rwf=False, precision="fp32", device="cuda", chunk_points=0,
-                 value_split=False):
+                 value_split=False, activation="tanh", omega0=1.0):
         self.device = torch.device(device)
         self.precision = precision
         flags = _lib.PINN_FLAG_BF16_VALUE_SPLIT if value_split else 0
@@ -62,14 +62,24 @@ class PinnNet:
         self.P = _lib.pinn_param_count(self.h)
         if chunk_points:
             _lib.pinn_set_chunk_points(self.h, chunk_points)
+        if activation != "tanh":
+            self.set_activation(activation, omega0)
         self._B = None
+        self._periodic = False
         self._ws = None
         self._ws_key = None
         self.loss_buf = torch.zeros(_lib.PINN_LOSS_TERMS, dtype=torch.float64, device=self.device)
 
     @classmethod
     def from_spec(cls, spec, precision="fp32", device="cuda", chunk_points=0, value_split=False):
-        return cls(spec.pde, spec.widths, spec.ff_m, spec.rwf, precision, device, chunk_points, value_split)
+        return cls(spec.pde, spec.widths, spec.ff_m, spec.rwf, precision, device, chunk_points, value_split,
+                   getattr(spec, "activation", "tanh"), getattr(spec, "omega0", 1.0))
+
+    def set_activation(self, activation, omega0=1.0):
+        """Hidden activation: "tanh" or "sine" (sin(omega0 z), CUDA-core jet GEMMs)."""
+        act = {"tanh": _lib.PINN_ACT_TANH, "sine": _lib.PINN_ACT_SINE}[activation]
+        _lib.pinn_set_activation(self.h, act, omega0)
+        self._ws_key = None
 
     def set_chunk_points(self, points):
         """Process batches in chunks of at most `points` points (0: one pass)."""
@@ -88,6 +98,7 @@ class PinnNet:
     def set_ff_matrix(self, B):
         self._B = torch.as_tensor(B, dtype=torch.float32, device=self.device).contiguous()
         _lib.pinn_set_ff_matrix(self.h, self._B.data_ptr())
+        self._periodic = False
 
     def workspace_bytes(self, n_res, n_ic, n_bc):
         return _lib.pinn_workspace_bytes(self.h, n_res, n_ic, n_bc)
@@ -115,6 +126,27 @@ class PinnNet:
         _lib.pinn_loss_grad(self.h, problem, batch.c_struct(), params.data_ptr(), ws.data_ptr(), ws.numel(),
                             out.data_ptr(), grad.data_ptr(), _stream())
         return out, grad
+
+    def set_periodic(self, periods):
+        """Strict periodic input map (Eq. 16) with these periods [d_in]; needs ff_m = d_in."""
+        _lib.pinn_set_periodic(self.h, list(periods))
+        self._B = None
+        self._periodic = True
+
+    def loss_grad_ff(self, params, batch: DeviceBatch, problem, grad=None, grad_ff=None, out=None):
+        """Loss, dL/dparams and the input-map gradient: dL/dB [d_in][m] with a Fourier
+        matrix, dL/dP [d_in] with the periodic map."""
+        assert params.dtype == torch.float32 and params.is_contiguous() and params.numel() == self.P
+        ws = self.workspace(batch)
+        out = self.loss_buf if out is None else out
+        grad = torch.empty_like(params) if grad is None else grad
+        if grad_ff is None:
+            d_in = 3 if self.spec.pde == _lib.PINN_MAXWELL_TE_2D else 2
+            n = d_in if self._periodic else d_in * self.spec.ff_m
+            grad_ff = torch.empty(n, dtype=torch.float32, device=self.device)
+        _lib.pinn_loss_grad_ff(self.h, problem, batch.c_struct(), params.data_ptr(), ws.data_ptr(), ws.numel(),
+                               out.data_ptr(), grad.data_ptr(), grad_ff.data_ptr(), _stream())
+        return out, grad, grad_ff
 
     def loss_grad_terms(self, params, batch: DeviceBatch, problem, grads=None, out=None):
         """Loss and the unweighted gradients of the PDE, initial and boundary terms,

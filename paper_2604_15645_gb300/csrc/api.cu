@@ -80,12 +80,17 @@ pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   for (int l = 1; l <= L; ++l) {
     q.A[l] = take((size_t)h->spec.widths[l - 1] * q.NC * q.es);
     if (q.lo) q.Alo[l] = take((size_t)h->spec.widths[l - 1] * q.NP * q.lo_es);
+    // the sine activation's adjoint needs z itself (cos(w z) is not a function of sin(w z))
+    if (h->act == PINN_ACT_SINE) q.Z[l] = take((size_t)h->spec.widths[l - 1] * q.NC * 4);
   }
-  q.Zbar[0] = take((size_t)h->w_max * q.NC * q.es);
-  q.Zbar[1] = take((size_t)h->w_max * q.NC * q.es);
+  // the ping-pong adjoints also hold the input-jet adjoint (2m rows) of pinn_loss_grad_ff
+  const size_t zrows = (size_t)std::max(h->w_max, 2 * h->spec.ff_m);
+  q.Zbar[0] = take(zrows * q.NC * q.es);
+  q.Zbar[1] = take(zrows * q.NC * q.es);
   q.nloss_blocks = out_loss_blocks(q.NP);
   q.losspart = take((size_t)q.nloss_blocks * 8 * sizeof(double));
   if (h->causal_M > 0) q.segpart = take((size_t)q.nloss_blocks * CAUSAL_MAX * 4 * sizeof(double));
+  if (h->spec.ff_m) q.ffpart = take((size_t)h->spec.ff_m * FFG_BLOCKS * h->d_in * sizeof(double));
   *p = q;
   p->total = off;
   return PINN_OK;
@@ -190,7 +195,7 @@ struct PassCtx {
 // One forward + reverse sweep over the points of `b` (the whole batch, or one chunk).
 pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
                      char* ws, size_t ws_bytes, double* d_loss, float* d_grad, cudaStream_t st, bool want_grad,
-                     const PassCtx& pc, float* d_grad_terms = nullptr) {
+                     const PassCtx& pc, float* d_grad_terms = nullptr, float* d_grad_ff = nullptr) {
   pinn_status s = PINN_OK;
   CallPlan cp;
   plan_call(h, b->n_res, b->n_ic, b->n_bc, &cp);
@@ -200,6 +205,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
   const Plan& p = cp.p;
   const int L = h->L, L1 = L + 1, prec = h->spec.precision;
   const int mode = h->jet_mode;
+  const bool sine = h->act == PINN_ACT_SINE;
 
   // 1. RWF weights (Eq. 15) for every layer.
   RwfArgs ra{};
@@ -223,7 +229,8 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
                     ws + p.A[0], p.lo ? ws + p.Alo[0] : nullptr, p.NP, prec, st);
   } else {
     launch_first_layer(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, W32(0), bias(0),
-                       cp.lay[0].fout, mode, ws + p.A[1], p.lo ? ws + p.Alo[1] : nullptr, p.NP, prec, st);
+                       cp.lay[0].fout, mode, ws + p.A[1], p.lo ? ws + p.Alo[1] : nullptr, p.NP, prec, h->omega0,
+                       sine ? reinterpret_cast<float*>(ws + p.Z[1]) : nullptr, st);
   }
   if (cp.pm) {
     const int f0 = h->first_gemm;
@@ -240,6 +247,8 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     // exact FP32 and only the tensor-core forward (which truncates) uses the low half.
     e.alo_in = (p.lo && prec == PINN_BF16) ? ws + p.Alo[li] : nullptr;
     e.jet_mode = mode;
+    e.act = h->act; e.omega0 = h->omega0;
+    e.zout = sine ? reinterpret_cast<float*>(ws + p.Z[li + 1]) : nullptr;
     PhaseScope ps(h, st, PH_FWD, 1);
     if (cp.tc[li] && cp.pm) {
       // TF32: point-major input; the epilogue also writes the next layer's point-major input
@@ -282,6 +291,8 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
   oa.dwpart = reinterpret_cast<float*>(ws + cp.lay[L].dwpart);
   oa.dbpart = reinterpret_cast<float*>(ws + cp.lay[L].dbpart);
   oa.Zbar = ws + p.Zbar[L % 2];
+  oa.ZL = sine ? reinterpret_cast<const float*>(ws + p.Z[L]) : nullptr;
+  oa.omega0 = h->omega0;
   oa.losspart = reinterpret_cast<double*>(ws + p.losspart);
   oa.status = h->d_status;
   const bool causal = h->causal_M > 0;
@@ -354,11 +365,24 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
       launch_row_reduce(zb, false, lp.fout, p.NP, p.n_res, p.n_ic, p.n_bc, p.nbpart, b->x_res, b->x_ic, b->x_bc,
                         raw ? h->d_in : 0, mode, reinterpret_cast<float*>(ws + lp.dbpart), prec, st);
     }
+    if (li == 0 && d_grad_ff) {
+      // Input-map gradient: Abar_0 = W_1^T Zbar_1 (into the free adjoint buffer), then
+      // its contraction with the embedding's derivatives by B (or the periods).
+      PhaseScope ps(h, st, PH_OTHER, 3);
+      double* ffpart = reinterpret_cast<double*>(ws + p.ffpart);
+      launch_simt_gemm_lin(reinterpret_cast<const float*>(ws + lp.wt32), zb, lp.fin, lp.fout, p.NP, ws + p.Zbar[0],
+                           prec, st);
+      launch_ff_grad(ws + p.Zbar[0], b->x_res, b->x_ic, b->x_bc, p.n_res, p.n_ic, p.n_bc, h->d_in, h->ff_B,
+                     h->spec.ff_m, mode, p.NP, ffpart, prec, st);
+      launch_ff_grad_final(ffpart, h->d_in, h->spec.ff_m, h->periodic, h->periods, pc.first ? 0 : 1, d_grad_ff, st);
+    }
     if (li >= 1) {
       EpiArgs e{};
       e.out = ws + p.Zbar[li % 2]; e.ain = ws + p.A[li];
       e.ain_lo = p.lo ? ws + p.Alo[li] : nullptr;
       e.jet_mode = mode;
+      e.act = h->act; e.omega0 = h->omega0;
+      e.zin = sine ? reinterpret_cast<const float*>(ws + p.Z[li]) : nullptr;
       if (cp.fused_db[li - 1]) {
         e.dbpart = reinterpret_cast<float*>(ws + cp.lay[li - 1].dbpart);
         e.dterms = (li - 1 == 0 && !h->spec.ff_m) ? h->d_in : 0;
@@ -460,7 +484,7 @@ cudaError_t copy_rows(float* dst, const float* src, int rows, int64_t ld, int64_
 
 pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params, void* d_ws,
                 size_t ws_bytes, double* d_loss, float* d_grad, void* stream, bool want_grad,
-                float* d_grad_terms = nullptr) {
+                float* d_grad_terms = nullptr, float* d_grad_ff = nullptr) {
   if (!h) return PINN_ERR_INVALID_ARG;
   if (!prob || !d_params || !d_ws || !d_loss || (want_grad && !d_grad && !d_grad_terms)) {
     set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG;
@@ -478,7 +502,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
     return PINN_ERR_UNSUPPORTED;
   }
   if (h->chunk_points <= 0 || N <= h->chunk_points)
-    return run_pass(h, prob, b, d_params, ws, ws_bytes, d_loss, d_grad, st, want_grad, pc, d_grad_terms);
+    return run_pass(h, prob, b, d_params, ws, ws_bytes, d_loss, d_grad, st, want_grad, pc, d_grad_terms, d_grad_ff);
 
   const int64_t C = h->chunk_points;
   const size_t need = chunked_bytes(h, b->n_res, b->n_ic, b->n_bc);
@@ -506,7 +530,7 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
     pc.first = (s0 == 0);
     pc.last = (s1 == N);
     s = run_pass(h, prob, &cb, d_params, ws + cl.pass, ws_bytes - cl.pass, d_loss, d_grad, st, want_grad, pc,
-                 d_grad_terms);
+                 d_grad_terms, d_grad_ff);
     if (s) return s;
   }
   return PINN_OK;
@@ -539,6 +563,17 @@ pinn_status pinn_causal_weights(pinn_handle* h, double* d_weights, void* stream)
 pinn_status pinn_set_chunk_points(pinn_handle* h, int64_t points) {
   if (!h || points < 0) return PINN_ERR_INVALID_ARG;
   h->chunk_points = (int64_t)align_up((size_t)points, PT_ALIGN);
+  return PINN_OK;
+}
+
+pinn_status pinn_set_activation(pinn_handle* h, int act, double omega0) {
+  if (!h) return PINN_ERR_INVALID_ARG;
+  if (act != PINN_ACT_TANH && act != PINN_ACT_SINE) { set_err(h, "unknown activation %d", act); return PINN_ERR_INVALID_ARG; }
+  if (!(omega0 > 0.0) || !std::isfinite(omega0) || omega0 > 1e4) {
+    set_err(h, "omega0 must be finite and in (0, 1e4]"); return PINN_ERR_INVALID_ARG;
+  }
+  h->act = act;
+  h->omega0 = (float)omega0;
   return PINN_OK;
 }
 
@@ -601,6 +636,7 @@ pinn_status pinn_destroy(pinn_handle* h) {
   }
   if (h->d_status) cudaFree(h->d_status);
   if (h->d_scratch) cudaFree(h->d_scratch);
+  if (h->d_periodic_B) cudaFree(h->d_periodic_B);
   delete h;
   return PINN_OK;
 }
@@ -638,7 +674,41 @@ pinn_status pinn_set_ff_matrix(pinn_handle* h, const float* d_B) {
   if (!h || !d_B) return PINN_ERR_INVALID_ARG;
   if (!h->spec.ff_m) { set_err(h, "network has no Fourier features"); return PINN_ERR_INVALID_ARG; }
   h->ff_B = d_B;
+  h->periodic = false;
   return PINN_OK;
+}
+
+pinn_status pinn_set_periodic(pinn_handle* h, const double* periods) {
+  if (!h || !periods) return PINN_ERR_INVALID_ARG;
+  if (h->spec.ff_m != h->d_in) {
+    set_err(h, "the periodic input map needs ff_m = d_in (%d), got %d", h->d_in, h->spec.ff_m);
+    return PINN_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < h->d_in; ++k)
+    if (!(periods[k] > 0.0) || !std::isfinite(periods[k])) { set_err(h, "periods must be finite and > 0"); return PINN_ERR_INVALID_ARG; }
+  const int d = h->d_in;
+  if (!h->d_periodic_B) {
+    pinn_status s = cuda_check(h, cudaMalloc(&h->d_periodic_B, (size_t)d * d * sizeof(float)), "periodic map alloc");
+    if (s) return s;
+  }
+  float Bh[9] = {0.f};
+  for (int k = 0; k < d; ++k) Bh[k * d + k] = (float)(2.0 * 3.14159265358979323846 / periods[k]);
+  pinn_status s = cuda_check(h, cudaMemcpy(h->d_periodic_B, Bh, (size_t)d * d * sizeof(float), cudaMemcpyHostToDevice),
+                             "periodic map upload");
+  if (s) return s;
+  for (int k = 0; k < d; ++k) h->periods[k] = periods[k];
+  h->ff_B = h->d_periodic_B;
+  h->periodic = true;
+  return PINN_OK;
+}
+
+pinn_status pinn_loss_grad_ff(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch, const float* d_params,
+                              void* d_ws, size_t ws_bytes, double* d_loss_terms, float* d_grad, float* d_grad_ff,
+                              void* stream) {
+  if (!h) return PINN_ERR_INVALID_ARG;
+  if (!h->spec.ff_m) { set_err(h, "network has no input map (Fourier features or periodic)"); return PINN_ERR_INVALID_ARG; }
+  if (!d_grad_ff) { set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG; }
+  return run(h, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, d_grad, stream, true, nullptr, d_grad_ff);
 }
 
 pinn_status pinn_loss(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch, const float* d_params,

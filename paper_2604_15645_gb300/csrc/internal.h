@@ -49,9 +49,11 @@ struct Plan {
   int lo_es = 2;       // bytes per low-half element (BF16 2, TF32 4)
   size_t A[PINN_MAX_HIDDEN + 1] = {};   // A_l^T [w_l][NC] compute type, l = 0..L (A_0 only with FF)
   size_t Alo[PINN_MAX_HIDDEN + 1] = {}; // low half of the value rows, tile-major [NP/64][w_l][64]
+  size_t Z[PINN_MAX_HIDDEN + 1] = {};   // sine activation only: pre-activations Z_l^T [w_l][NC] FP32
   size_t Zbar[2] = {};                  // ping-pong adjoints [w_max][NC] compute type
   size_t losspart = 0;                  // per-block loss partials, double [nloss_blocks][8]
   size_t segpart = 0;                   // causality: per-block segment sums [nloss_blocks][CAUSAL_MAX][4]
+  size_t ffpart = 0;                    // Fourier features: dL/dB block partials, double [m][FFG_BLOCKS][d_in]
   int nloss_blocks = 0;
   int nbpart = 0;                       // column chunks of the bias/first-layer reductions
   size_t total = 0;
@@ -75,6 +77,11 @@ struct pinn_handle {
   int device = 0;
   int sm_count = 0;
   int64_t chunk_points = 0;  // 0: one pass; else points per chunk (multiple of 64)
+  float* d_periodic_B = nullptr;   // periodic input map: owned diag(2 pi / P) [d_in][d_in]
+  bool periodic = false;     // ff_B is d_periodic_B; the input-map gradient is dL/dP
+  double periods[3] = {0, 0, 0};
+  int act = PINN_ACT_TANH;   // hidden activation; sine keeps Z and runs on CUDA cores
+  float omega0 = 1.f;
   char err[512] = {0};
   // phase profiler (pinn_set_profiling)
   bool prof = false;
@@ -105,7 +112,7 @@ void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, i
 
 void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                         int64_t n_bc, int d_in, const float* W, const float* b, int fout, int jet_mode, void* A1,
-                        void* A1lo, int64_t NP, int prec, cudaStream_t st);
+                        void* A1lo, int64_t NP, int prec, float omega0, float* Z1, cudaStream_t st);
 
 struct EpiArgs {
   const float* bias;      // fwd: bias of this layer [M]
@@ -116,6 +123,12 @@ struct EpiArgs {
   const void* ain_lo;     // adj, BF16: low half of its value rows [NP/64][M][64] (t = hi + lo)
   void* out_pm;           // TF32 tensor-core path: point-major copy of `out`, [NC][M] FP32 (nullptr = none)
   int jet_mode;
+  // sine activation (CUDA-core path): fwd writes the pre-activation jets to zout,
+  // adj reads them from zin ([M][NC] FP32, tile-major); act 0 = tanh.
+  int act;
+  float omega0;
+  float* zout;
+  const float* zin;
   // adjoint only: bias-gradient partials of the layer whose pre-activation adjoint
   // this epilogue writes ([part][M][1 + dterms]; nullptr = not fused), and for a
   // first layer on raw coordinates the coordinate terms of its dW (dterms = d_in).
@@ -130,6 +143,9 @@ struct EpiArgs {
 void launch_simt_gemm_fwd(const float* Aop, const void* Bop, int M, int K, int64_t NP, const EpiArgs& e, int prec,
                           cudaStream_t st);
 void launch_simt_gemm_adj(const float* Aop, const void* Bop, int M, int K, int64_t NP, const EpiArgs& e, int prec,
+                          cudaStream_t st);
+// out[M][4 NP] = Aop[M][K] Bop[K][4 NP] with no epilogue (the input-jet adjoint W_1^T Zbar_1).
+void launch_simt_gemm_lin(const float* Aop, const void* Bop, int M, int K, int64_t NP, void* out, int prec,
                           cudaStream_t st);
 // part[s][M][N] = sum_{k in split s} Aop[m][k] Bop[n][k]; Aop/Bop row-major with ld = NC.
 // a_fp32 / b_fp32 select float storage, else the compute type.
@@ -158,11 +174,23 @@ struct OutArgs {
   float* dwpart;         // output-layer dW partials [nblocks][d_out][w] (per block, fixed order)
   float* dbpart;         // output-layer bias partials [d_out][nblocks]
   void* Zbar;            // Zbar_L^T [w][NC] compute type
+  const float* ZL;       // sine activation: Z_L^T [w][NC] FP32 for the adjoint (else nullptr)
+  float omega0;
   double* losspart;      // [nblocks][8]
   int* status;
 };
 // Output layer, residuals, loss partials and (want_grad) the adjoint seeds, Zbar_L
 // and the output layer's dW and bias partials, one block per 64-point tile stride.
+// dL/dB of the Fourier embedding (Eq. 14) from the input-jet adjoint Abar_0 [2m][NC]
+// (compute type): per-block FP64 partials, then an ordered sum into out [d_in][m]
+// (accumulating when `accumulate`), or, for the periodic map (Eq. 16, B = diag(2 pi/P)),
+// out[k] = dL/dP_k = -(2 pi / P_k^2) dL/dB_kk.
+constexpr int FFG_BLOCKS = 32;
+void launch_ff_grad(const void* Abar0, const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res,
+                    int64_t n_ic, int64_t n_bc, int d_in, const float* B, int m, int jet_mode, int64_t NP,
+                    double* part, int prec, cudaStream_t st);
+void launch_ff_grad_final(const double* part, int d_in, int m, bool periodic, const double* periods, int accumulate,
+                          float* out, cudaStream_t st);
 cudaError_t launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st);
 int out_loss_blocks(int64_t n_points);
 

@@ -86,6 +86,53 @@ __device__ __forceinline__ void jet_adj_a(const float a[4], const float ab[4], f
   }
 }
 
+// ---- periodic activation sin(omega z) ----------------------------------------------
+// The sine activation (periodic activation function, Sec. 2.6) uses the same jet rule
+// with t = sin(w z), t' = w cos(w z), t'' = -w^2 sin(w z), t''' = -w^3 cos(w z).  Its
+// adjoint cannot be written in A alone (the sign of cos is lost in sin), so sine
+// layers keep their pre-activation jets Z and evaluate the adjoint from z:
+//   zbar_L = abar_L t'
+//   zbar_k = abar_k t' + [k in S] 2 abar_L t'' z_k
+//   zbar   = abar t' + t'' sum_k abar_k z_k + abar_L (t''' sum_{k in S} z_k^2 + t'' z_L),
+// and for Maxwell's first-order fourth row zbar = abar t' + t'' sum_k abar_k z_k.
+__device__ __forceinline__ void jet_fwd_sine(const float z[4], float a[4], int mode, float w) {
+  float s, c;
+  sincosf(w * z[0], &s, &c);
+  const float tp = w * c;
+  a[0] = s;
+  a[1] = tp * z[1];
+  a[2] = tp * z[2];
+  if (mode == JET_MAXWELL) {
+    a[3] = tp * z[3];
+  } else {
+    const float tpp = -w * w * s;
+    const float q = z[1] * z[1] + (mode == JET_NS ? z[2] * z[2] : 0.f);
+    a[3] = fmaf(tpp, q, tp * z[3]);
+  }
+}
+
+__device__ __forceinline__ void jet_adj_sine(const float z[4], const float ab[4], float zb[4], int mode, float w) {
+  float s, c;
+  sincosf(w * z[0], &s, &c);
+  const float tp = w * c, tpp = -w * w * s, tppp = -w * w * tp;
+  if (mode == JET_MAXWELL) {
+    zb[1] = ab[1] * tp;
+    zb[2] = ab[2] * tp;
+    zb[3] = ab[3] * tp;
+    zb[0] = fmaf(ab[0], tp, tpp * (ab[1] * z[1] + ab[2] * z[2] + ab[3] * z[3]));
+  } else {
+    const bool ns = (mode == JET_NS);
+    const float q = z[1] * z[1] + (ns ? z[2] * z[2] : 0.f);
+    const float t2 = 2.f * ab[3] * tpp;
+    zb[3] = ab[3] * tp;
+    zb[1] = fmaf(ab[1], tp, t2 * z[1]);
+    zb[2] = ns ? fmaf(ab[2], tp, t2 * z[2]) : ab[2] * tp;
+    // sum_k abar_k z_k over the two first-order rows, plus abar_L's second-order terms
+    const float g1 = ab[1] * z[1] + ab[2] * z[2];
+    zb[0] = fmaf(ab[0], tp, fmaf(tpp, g1, ab[3] * fmaf(tppp, q, tpp * z[3])));
+  }
+}
+
 // ---- geometry of the jet matrices ------------------------------------------------------
 // Every point (interior, initial, boundary, padding) owns four columns.  Points are
 // grouped in tiles of 64; inside a 256-column tile the columns are blocked by jet

@@ -133,13 +133,13 @@ void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, i
 // ------------------------------------------------------------------------------------
 // First hidden layer on raw coordinates (no Fourier features): z = W x + b on the
 // value row, z_k = W[:, d_k] on the first-derivative rows of interior points, 0 on
-// the second-order row (the input has no curvature); then the tanh jet rule.
-// Writes A_1 (and its value-row low half).
+// the second-order row (the input has no curvature); then the activation's jet rule.
+// Writes A_1 (and its value-row low half), and for the sine activation Z_1 (FP32).
 // ------------------------------------------------------------------------------------
 template <typename T, int LO>
 __global__ void k_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                               int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, T* A1,
-                              void* A1lo, int64_t NP) {
+                              void* A1lo, int64_t NP, float omega0, float* Z1) {
   const int f = blockIdx.y;
   const int64_t NC = 4 * NP;
   float Wf[3] = {0.f, 0.f, 0.f};
@@ -148,7 +148,7 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
 
   for (int64_t p0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); p0 < NP;
        p0 += 4 * (int64_t)gridDim.x * blockDim.x) {
-    float aa[4][4];   // [row][point]
+    float aa[4][4], zs[4][4];   // [row][point]
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int64_t p = p0 + k;
@@ -163,14 +163,16 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
           z[r] = d >= 0 ? Wf[d] : 0.f;
         }
       }
-      jet_fwd<(LO == 1)>(z, a, mode);
+      if (Z1) jet_fwd_sine(z, a, mode, omega0);
+      else jet_fwd<(LO == 1)>(z, a, mode);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) aa[r][k] = a[r];
+      for (int r = 0; r < 4; ++r) { aa[r][k] = a[r]; zs[r][k] = z[r]; }
     }
     const int64_t c0 = jcol(p0, 0);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       store4<T>(A1 + toff(f, c0 + 64 * r, fout), aa[r]);
+      if (Z1) store4<float>(Z1 + toff(f, c0 + 64 * r, fout), zs[r]);
     }
     if (LO) store_lo4<LO>(A1lo, loff(f, p0, fout), aa[0]);
   }
@@ -178,14 +180,14 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
 
 void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                         int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, void* A1,
-                        void* A1lo, int64_t NP, int prec, cudaStream_t st) {
+                        void* A1lo, int64_t NP, int prec, float omega0, float* Z1, cudaStream_t st) {
   dim3 grid((unsigned)std::min<int64_t>((NP / 4 + 255) / 256, 4096), fout);
   if (prec == PINN_BF16)
     k_first_layer<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout,
-                                                          mode, (__nv_bfloat16*)A1, A1lo, NP);
+                                                          mode, (__nv_bfloat16*)A1, A1lo, NP, omega0, Z1);
   else
     k_first_layer<float, 0><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
-                                                  (float*)A1, nullptr, NP);
+                                                  (float*)A1, nullptr, NP, omega0, Z1);
 }
 
 // ------------------------------------------------------------------------------------
@@ -402,9 +404,13 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
     }
     // A_L read again (from L2) for the output layer's dW[c][f] = sum over the tile's
     // columns of Ubar[c] A_L[f], and for abar_L = Ubar W_out (rank <= 3) followed by
-    // the tanh-jet adjoint written in A_L.
+    // the tanh-jet adjoint written in A_L.  Every lane runs every pass (the dW sum
+    // shuffles across the warp); a slice past the width reads feature w-1 and
+    // discards what it computed.
 #pragma unroll 2
-    for (int f = sl; f < w; f += 8) {
+    for (int f0 = 0; f0 < w; f0 += 8) {
+      const bool live = f0 + sl < w;
+      const int f = live ? f0 + sl : w - 1;
       float av[4][4], zb[4][4];                    // [row][point]
       {
         const T* arow = AL + toff(f, cb, w);
@@ -425,9 +431,10 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
             for (int r = 0; r < 4; ++r) g = fmaf(Ub[j][c][r], av[r][j], g);
           g += __shfl_xor_sync(0xffffffffu, g, 8);    // the warp's four point groups
           g += __shfl_xor_sync(0xffffffffu, g, 16);
-          if (pg == 0) sdw[(warp * D + c) * w + f] += g;
+          if (pg == 0 && live) sdw[(warp * D + c) * w + f] += g;
         }
       }
+      if (!live) continue;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         float ab[4] = {0.f, 0.f, 0.f, 0.f}, zz[4], o[4];
@@ -437,9 +444,15 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
 #pragma unroll
           for (int r = 0; r < 4; ++r) ab[r] = fmaf(wc, Ub[j][c][r], ab[r]);
         }
+        if (a.ZL) {   // sine: the adjoint is evaluated from the pre-activation jets
 #pragma unroll
-        for (int r = 0; r < 4; ++r) zz[r] = av[r][j];
-        jet_adj_a(zz, ab, o, a.jet_mode);
+          for (int r = 0; r < 4; ++r) zz[r] = a.ZL[toff(f, cb + 64 * r + j, w)];
+          jet_adj_sine(zz, ab, o, a.jet_mode, a.omega0);
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) zz[r] = av[r][j];
+          jet_adj_a(zz, ab, o, a.jet_mode);
+        }
 #pragma unroll
         for (int r = 0; r < 4; ++r) zb[r][j] = o[r];
       }
@@ -794,6 +807,103 @@ void launch_finalize_causal(const double* segpart, const double* losspart, int n
                             double* out, double* omega, float* scale, int* status, cudaStream_t st) {
   k_finalize_causal<<<1, 256, 0, st>>>(segpart, losspart, nblocks, M, eps, n_ic, n_bc, lam_pde, lam_ic, lam_bc,
                                        lam_seed, out, omega, scale, status);
+}
+
+// ------------------------------------------------------------------------------------
+// Gradient of the input map.  The Fourier embedding (Eq. 14) has, per feature j with
+// phi = sum_e x_e B_ej, c = cos phi, s = sin phi, the jets  value [c, s];  row of
+// direction d [-s B_dj, c B_dj];  second-order row [-c q, -s q], q = sum_{k in S} B_kj^2.
+// Their derivatives with respect to B_ej (dphi/dB_ej = x_e):
+//   value            [-s x_e, c x_e]
+//   direction d      [-c x_e B_dj - s [d=e],  -s x_e B_dj + c [d=e]]
+//   second order     [s x_e q - 2 c B_ej [e in S],  -c x_e q - 2 s B_ej [e in S]]
+// dL/dB_ej = sum over points and rows of Abar_0 (the adjoint of these jets) times them.
+// Grid (FFG_BLOCKS, m): block (b, j) reduces its points' terms for feature j in FP64.
+// ------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_ff_grad(const T* __restrict__ Abar, const float* x_res, const float* x_ic, const float* x_bc,
+                          int64_t n_res, int64_t n_ic, int64_t n_bc, int d_in, const float* B, int m, int mode,
+                          int64_t NP, double* part) {
+  const int j = blockIdx.y;
+  float Bj[3] = {0.f, 0.f, 0.f};
+  for (int i = 0; i < d_in; ++i) Bj[i] = B[(int64_t)i * m + j];
+  const float q = (mode == JET_MAXWELL) ? 0.f : (Bj[0] * Bj[0] + (mode == JET_NS ? Bj[1] * Bj[1] : 0.f));
+  const int64_t wA = 2 * (int64_t)m;
+  double g[3] = {0.0, 0.0, 0.0};
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < NP; p += (int64_t)gridDim.x * blockDim.x) {
+    int64_t idx;
+    const int set = point_set(p, n_res, n_ic, n_bc, idx);
+    if (set == SET_PAD) continue;
+    float x[3] = {0.f, 0.f, 0.f};
+    float phi = 0.f;
+    for (int i = 0; i < d_in; ++i) {
+      x[i] = point_coord(x_res, x_ic, x_bc, n_res, n_ic, n_bc, p, i);
+      phi = fmaf(x[i], Bj[i], phi);
+    }
+    float sn, cs;
+    sincosf(phi, &sn, &cs);
+    const int nr = (set == SET_RES) ? 4 : 1;   // initial/boundary points carry the value row only
+    float ac[4], as[4];
+    for (int r = 0; r < nr; ++r) {
+      ac[r] = to_f<T>(Abar[toff(j, jcol(p, r), wA)]);
+      as[r] = to_f<T>(Abar[toff(m + j, jcol(p, r), wA)]);
+    }
+    for (int e = 0; e < d_in; ++e) {
+      float ge = (cs * as[0] - sn * ac[0]) * x[e];
+      for (int r = 1; r < nr; ++r) {
+        const int d = row_dir(mode, r);
+        if (d >= 0) {
+          ge += ac[r] * (-cs * x[e] * Bj[d] - (d == e ? sn : 0.f)) + as[r] * (-sn * x[e] * Bj[d] + (d == e ? cs : 0.f));
+        } else {
+          const bool in_s = (e == 0) || (mode == JET_NS && e == 1);
+          ge += ac[r] * (sn * x[e] * q - (in_s ? 2.f * cs * Bj[e] : 0.f)) +
+                as[r] * (-cs * x[e] * q - (in_s ? 2.f * sn * Bj[e] : 0.f));
+        }
+      }
+      g[e] += (double)ge;
+    }
+  }
+  __shared__ double sh[8];
+  for (int e = 0; e < d_in; ++e) {
+    const double v = block_sum_d(g[e], sh);
+    if (threadIdx.x == 0) part[((int64_t)j * gridDim.x + blockIdx.x) * d_in + e] = v;
+  }
+}
+
+void launch_ff_grad(const void* Abar0, const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res,
+                    int64_t n_ic, int64_t n_bc, int d_in, const float* B, int m, int jet_mode, int64_t NP,
+                    double* part, int prec, cudaStream_t st) {
+  dim3 grid(FFG_BLOCKS, m);
+  if (prec == PINN_BF16)
+    k_ff_grad<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16*)Abar0, x_res, x_ic, x_bc, n_res, n_ic, n_bc,
+                                                   d_in, B, m, jet_mode, NP, part);
+  else
+    k_ff_grad<float><<<grid, 256, 0, st>>>((const float*)Abar0, x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, B, m,
+                                           jet_mode, NP, part);
+}
+
+struct PeriodFactors { double f[3]; };
+
+// Ordered FP64 sum of the block partials; one thread per output entry.
+__global__ void k_ff_grad_final(const double* part, int d_in, int m, int periodic, PeriodFactors pf, int accumulate,
+                                float* out) {
+  const int n = periodic ? d_in : d_in * m;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int e = periodic ? t : t / m, j = periodic ? t : t % m;
+    double s = 0.0;
+    for (int b = 0; b < FFG_BLOCKS; ++b) s += part[((int64_t)j * FFG_BLOCKS + b) * d_in + e];
+    if (periodic) s *= pf.f[e];
+    out[t] = accumulate ? (float)((double)out[t] + s) : (float)s;
+  }
+}
+
+void launch_ff_grad_final(const double* part, int d_in, int m, bool periodic, const double* periods, int accumulate,
+                          float* out, cudaStream_t st) {
+  PeriodFactors pf{{0.0, 0.0, 0.0}};
+  if (periodic)   // B_kk = 2 pi / P_k, so dB_kk/dP_k = -2 pi / P_k^2
+    for (int k = 0; k < d_in; ++k) pf.f[k] = -2.0 * 3.14159265358979323846 / (periods[k] * periods[k]);
+  const int n = periodic ? d_in : d_in * m;
+  k_ff_grad_final<<<(n + 255) / 256, 256, 0, st>>>(part, d_in, m, periodic ? 1 : 0, pf, accumulate, out);
 }
 
 // ------------------------------------------------------------------------------------

@@ -32,8 +32,10 @@ __device__ __forceinline__ void load_vec8<__nv_bfloat16>(const __nv_bfloat16* p,
 // One block per (64 features, one 256-column tile = 64 points).  Thread (ty, tx)
 // owns features 4ty..4ty+3 and points 4tx..4tx+3 of the tile, i.e. the columns
 // 64 r + 4 tx + j of all four jet rows r, so the jet rule is thread-local.
-// EPI 0: forward (bias on value rows, tanh jet, writes A, Z and the BF16 low half)
-// EPI 1: adjoint (reads Z_{l-1}, tanh-jet adjoint, writes Zbar_{l-1})
+// EPI 0: forward (bias on value rows, activation jet, writes A and the BF16 low half;
+//        with the sine activation also the pre-activation jets Z)
+// EPI 1: adjoint (reads A_{l-1}, or Z_{l-1} for sine, the jet adjoint, writes Zbar_{l-1})
+// EPI 2: linear adjoint (writes W^T Zbar itself: the adjoint of the input jets)
 template <typename T, int EPI>
 __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__ Aop, const T* __restrict__ Bop,
                                                        const __nv_bfloat16* __restrict__ Blo, int M, int K,
@@ -102,7 +104,10 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
     const int f = m0 + ty * 4 + i;
     if (f >= M) continue;
     float o[4][4], zz[4][4];   // [row][point]
-    if (EPI == 1) {   // the output jet of the layer below (value row: hi + lo for BF16)
+    if (EPI == 1 && e.act) {   // sine: the pre-activation jets of the layer below
+      const float* zr = e.zin + toff(f, n0 + 4 * tx, M);
+      for (int r = 0; r < 4; ++r) load4<float>(zr + 64 * r, zz[r]);
+    } else if (EPI == 1) {   // tanh: the output jet of the layer below (value row: hi + lo for BF16)
       const T* ar = reinterpret_cast<const T*>(e.ain) + toff(f, n0 + 4 * tx, M);
       for (int r = 0; r < 4; ++r) load4<T>(ar + 64 * r, zz[r]);
       if (sizeof(T) == 2 && e.ain_lo) {
@@ -118,13 +123,25 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
         if (EPI == 0) z[r] = acc[i][4 * r + j] + (r == 0 ? bias : 0.f);
         else { z[r] = zz[r][j]; ab[r] = acc[i][4 * r + j]; }
       }
-      if (EPI == 0) {
-        jet_fwd<FAST>(z, a, e.jet_mode);
+      if (EPI == 2) {
+        for (int r = 0; r < 4; ++r) o[r][j] = acc[i][4 * r + j];
+      } else if (EPI == 0) {
+        if (e.act) {
+          jet_fwd_sine(z, a, e.jet_mode, e.omega0);
+          for (int r = 0; r < 4; ++r) zz[r][j] = z[r];
+        } else {
+          jet_fwd<FAST>(z, a, e.jet_mode);
+        }
         for (int r = 0; r < 4; ++r) o[r][j] = a[r];
       } else {
-        jet_adj_a(z, ab, a, e.jet_mode);
+        if (e.act) jet_adj_sine(z, ab, a, e.jet_mode, e.omega0);
+        else jet_adj_a(z, ab, a, e.jet_mode);
         for (int r = 0; r < 4; ++r) o[r][j] = a[r];
       }
+    }
+    if (EPI == 0 && e.act) {
+      float* zrow = e.zout + toff(f, n0 + 4 * tx, M);
+      for (int r = 0; r < 4; ++r) store4<float>(zrow + 64 * r, zz[r]);
     }
     T* orow = out + toff(f, n0 + 4 * tx, M);
     for (int r = 0; r < 4; ++r) store4<T>(orow + 64 * r, o[r]);
@@ -212,6 +229,17 @@ void launch_simt_gemm_adj(const float* Aop, const void* Bop, int M, int K, int64
     k_simt_gemm<__nv_bfloat16, 1><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, nullptr, M, K, NP, e);
   else
     k_simt_gemm<float, 1><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
+}
+
+void launch_simt_gemm_lin(const float* Aop, const void* Bop, int M, int K, int64_t NP, void* out, int prec,
+                          cudaStream_t st) {
+  dim3 grid((unsigned)(NP / TILE_PTS), (M + BM - 1) / BM);
+  EpiArgs e{};
+  e.out = out;
+  if (prec == PINN_BF16)
+    k_simt_gemm<__nv_bfloat16, 2><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, nullptr, M, K, NP, e);
+  else
+    k_simt_gemm<float, 2><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
 }
 
 void launch_simt_gemm_dw(const void* Aop, bool a_fp32, const void* Bop, bool b_fp32, int M, int N, int64_t NC,

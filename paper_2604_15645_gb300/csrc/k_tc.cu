@@ -856,6 +856,7 @@ void tc_init(pinn_handle* h) {
 
 bool tc_layer_supported(const pinn_handle* h, int li, int64_t NC) {
   if (!g_encode || h->spec.precision == PINN_FP32 || (h->spec.flags & PINN_FLAG_CUDA_CORES)) return false;
+  if (h->act != PINN_ACT_TANH) return false;   // the tensor-core epilogues carry the tanh jet only
   if (NC % BN) return false;
   const int fin = h->layers[li].fin, fout = h->layers[li].fout;
   // TMA row strides must be multiples of 16 bytes: fin and fout multiples of 8 elements.

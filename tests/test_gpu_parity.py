@@ -58,6 +58,18 @@ def test_ragged_widths_and_weights(cuda_lib, precision):
     _check(spec, p, B, b, Problem(0.02, 0.3, 2.0, 5.0), precision, "ragged")
 
 
+@pytest.mark.parametrize("pde,d_in,d_out,widths,ff", [(PDE_BURGERS, 2, 1, [13, 7], 0), (PDE_NS, 2, 3, [5, 11, 3], 6),
+                                                       (PDE_MAXWELL, 3, 3, [9, 1], 0)])
+def test_widths_not_multiples_of_eight(cuda_lib, pde, d_in, d_out, widths, ff):
+    # the output layer's feature slices run uneven passes; every lane still joins the shuffles
+    spec = NetSpec(pde, d_in, d_out, widths, ff_m=ff, ff_sigma=1.0, rwf=True)
+    p = init_params(spec, 57, 0.2)
+    B = ff_matrix(spec, 58) if ff else None
+    b = make_batch(pde, 300, 40 if pde != PDE_NS else 0, 50, 59, 60)
+    for precision in ("fp32", "bf16"):
+        _check(spec, p, B, b, Problem(0.02, 0.3, 2.0, 5.0), precision, f"odd widths {widths} {precision}")
+
+
 @pytest.mark.parametrize("precision,expect_tc", [("fp32", False), ("tf32", True), ("bf16", True)])
 def test_tensor_core_engine_selection(cuda_lib, precision, expect_tc):
     # FP32 runs the exact CUDA-core GEMMs; TF32 and BF16 run every hidden layer on tcgen05
