@@ -56,6 +56,8 @@ def parse():
                     help="also time the loss-balancing step: per-term gradients + weight update (Sec. 2.6.4)")
     ap.add_argument("--full-split", dest="value_split", action="store_false",
                     help="BF16: split the weights on every jet row (overrides the workload's setting)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false", default=True,
+                    help="launch every step eagerly instead of replaying one captured CUDA graph")
     return ap.parse_args()
 
 
@@ -374,14 +376,18 @@ def run_ours(args, ws_n, rank, local):
         if ws_n > 1:
             torch.distributed.barrier()
 
+    # warm-up: eager steps, then (graph mode) the capture and one replay
     for _ in range(args.warmup):
         net.loss_grad(p, db, prob, grad=grad)
+    if args.graph:
+        net.set_graph(True)
+        for _ in range(2):
+            net.loss_grad(p, db, prob, grad=grad)
     torch.cuda.synchronize()
     assert net.status_poll() == 0, "device status after warm-up"
 
     clocks = ClockSampler(local)
     clocks.start()
-    _lib.pinn_set_profiling(net.h, True)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -393,10 +399,18 @@ def run_ours(args, ws_n, rank, local):
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    prof = _lib.pinn_profile_read(net.h)
-    _lib.pinn_set_profiling(net.h, False)
     clk = clocks.stop()
     status = net.status_poll()
+
+    # per-phase kernel times: the same K steps again, launched eagerly with a CUDA
+    # event pair around each launch group on the launching stream (graph replays
+    # cannot carry them); the kernels are the ones the timed region replays
+    _lib.pinn_set_profiling(net.h, True)
+    for _ in range(args.steps):
+        net.loss_grad(p, db, prob, grad=grad)
+    torch.cuda.synchronize()
+    prof = _lib.pinn_profile_read(net.h)
+    _lib.pinn_set_profiling(net.h, False)
 
     # end to end through the public API with host buffers: per step, H2D of the
     # collocation sets from pinned memory, the step, D2H of the loss terms.
@@ -486,6 +500,8 @@ def run_ours(args, ws_n, rank, local):
                    "n_res": batch.n_res, "n_ic": batch.n_ic, "n_bc": batch.n_bc, "points_per_step": n_pts,
                    "jet_columns": ncols, "parallelism": f"replicas x{ws_n}",
                    "workspace_gb": round(ws_bytes / 1e9, 2), "chunk_points": args.chunk_points,
+                   "launch": "one CUDA graph per step" if args.graph else "eager launches",
+                   "phase_timing": "CUDA events per launch group in an eager pass of the same K steps",
                    "bf16_weight_split": ("value rows" if value_split else "all rows") if precision == "bf16" else None,
                    "l2": f"working set {ws_bytes / 1e9:.2f} GB per step > 129 MB L2 (no flush needed)"},
         "e2e": {"value": round(whole_job_rate(n_pts, ws_n, e2e_ms_max), 1), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -75,6 +75,10 @@ class PinnNet:
         return cls(spec.pde, spec.widths, spec.ff_m, spec.rwf, precision, device, chunk_points, value_split,
                    getattr(spec, "activation", "tanh"), getattr(spec, "omega0", 1.0))
 
+    def set_graph(self, on=True):
+        """Replay each call from a captured CUDA graph while its arguments stay the same."""
+        _lib.pinn_set_graph(self.h, on)
+
     def set_activation(self, activation, omega0=1.0):
         """Hidden activation: "tanh" or "sine" (sin(omega0 z), CUDA-core jet GEMMs)."""
         act = {"tanh": _lib.PINN_ACT_TANH, "sine": _lib.PINN_ACT_SINE}[activation]

@@ -536,6 +536,66 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   return PINN_OK;
 }
 
+// One call by kind: 0 loss, 1 loss+grad, 2 loss+grad+input-map gradient, 3 per-term grads.
+pinn_status run_kind(pinn_handle* h, int kind, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
+                     void* d_ws, size_t ws_bytes, double* d_loss, float* d_grad, float* out2, void* stream) {
+  switch (kind) {
+    case 0: return run(h, prob, b, d_params, d_ws, ws_bytes, d_loss, nullptr, stream, false);
+    case 1: return run(h, prob, b, d_params, d_ws, ws_bytes, d_loss, d_grad, stream, true);
+    case 2: return run(h, prob, b, d_params, d_ws, ws_bytes, d_loss, d_grad, stream, true, nullptr, out2);
+    default: return run(h, prob, b, d_params, d_ws, ws_bytes, d_loss, nullptr, stream, true, out2);
+  }
+}
+
+void drop_graph(pinn_handle* h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  h->graph_exec = nullptr;
+  memset(&h->graph_key, 0, sizeof(h->graph_key));
+}
+
+// run_kind, replayed from a captured CUDA graph when the handle asks for it.
+pinn_status run_graphed(pinn_handle* h, int kind, const pinn_problem* prob, const pinn_batch* b,
+                        const float* d_params, void* d_ws, size_t ws_bytes, double* d_loss, float* d_grad,
+                        float* out2, void* stream) {
+  if (!h || !h->graph_on || h->prof || !prob || !b)
+    return run_kind(h, kind, prob, b, d_params, d_ws, ws_bytes, d_loss, d_grad, out2, stream);
+  pinn_graph_key k;
+  memset(&k, 0, sizeof(k));
+  k.kind = kind; k.prob = *prob; k.batch = *b;
+  k.params = d_params; k.ws = d_ws; k.ws_bytes = ws_bytes; k.loss = d_loss; k.grad = d_grad; k.out2 = out2;
+  k.chunk_points = h->chunk_points;
+  k.causal_M = h->causal_M; k.causal_eps = h->causal_eps; k.causal_t0 = h->causal_t0; k.causal_t1 = h->causal_t1;
+  k.act = h->act; k.omega0 = h->omega0;
+  k.ff_B = h->ff_B; k.periodic = h->periodic ? 1 : 0;
+  for (int i = 0; i < 3; ++i) k.periods[i] = h->periods[i];
+  k.stream = stream;
+  if (!h->graph_exec || memcmp(&k, &h->graph_key, sizeof(k)) != 0) {
+    drop_graph(h);
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      set_err(h, "cannot begin stream capture");
+      return PINN_ERR_CUDA;
+    }
+    const pinn_status s = run_kind(h, kind, prob, b, d_params, d_ws, ws_bytes, d_loss, d_grad, out2, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (s || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (!s) set_err(h, "graph capture failed: %s", cudaGetErrorString(e));
+      return s ? s : PINN_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->graph_exec = nullptr;
+      return cuda_check(h, ei, "graph instantiation");
+    }
+    h->graph_key = k;
+  }
+  return cuda_check(h, cudaGraphLaunch(h->graph_exec, (cudaStream_t)stream), "graph launch");
+}
+
 }  // namespace
 
 extern "C" {
@@ -563,6 +623,17 @@ pinn_status pinn_causal_weights(pinn_handle* h, double* d_weights, void* stream)
 pinn_status pinn_set_chunk_points(pinn_handle* h, int64_t points) {
   if (!h || points < 0) return PINN_ERR_INVALID_ARG;
   h->chunk_points = (int64_t)align_up((size_t)points, PT_ALIGN);
+  return PINN_OK;
+}
+
+pinn_status pinn_set_graph(pinn_handle* h, int on) {
+  if (!h || (on != 0 && on != 1)) return PINN_ERR_INVALID_ARG;
+  if (on && !h->cap_stream) {
+    pinn_status s = cuda_check(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+    if (s) return s;
+  }
+  if (!on) drop_graph(h);
+  h->graph_on = on != 0;
   return PINN_OK;
 }
 
@@ -637,6 +708,8 @@ pinn_status pinn_destroy(pinn_handle* h) {
   if (h->d_status) cudaFree(h->d_status);
   if (h->d_scratch) cudaFree(h->d_scratch);
   if (h->d_periodic_B) cudaFree(h->d_periodic_B);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return PINN_OK;
 }
@@ -708,19 +781,19 @@ pinn_status pinn_loss_grad_ff(pinn_handle* h, const pinn_problem* prob, const pi
   if (!h) return PINN_ERR_INVALID_ARG;
   if (!h->spec.ff_m) { set_err(h, "network has no input map (Fourier features or periodic)"); return PINN_ERR_INVALID_ARG; }
   if (!d_grad_ff) { set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG; }
-  return run(h, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, d_grad, stream, true, nullptr, d_grad_ff);
+  return run_graphed(h, 2, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, d_grad, d_grad_ff, stream);
 }
 
 pinn_status pinn_loss(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch, const float* d_params,
                       void* d_ws, size_t ws_bytes, double* d_loss_terms, void* stream) {
-  return run(h, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, nullptr, stream, false);
+  return run_graphed(h, 0, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, nullptr, nullptr, stream);
 }
 
 pinn_status pinn_loss_grad_terms(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch,
                                  const float* d_params, void* d_ws, size_t ws_bytes, double* d_loss_terms,
                                  float* d_grad_terms, void* stream) {
   if (!d_grad_terms) { if (h) set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG; }
-  return run(h, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, nullptr, stream, true, d_grad_terms);
+  return run_graphed(h, 3, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, nullptr, d_grad_terms, stream);
 }
 
 pinn_status pinn_loss_balance(pinn_handle* h, const float* d_grad_terms, double* d_lambda, double* d_norms,
@@ -733,7 +806,7 @@ pinn_status pinn_loss_balance(pinn_handle* h, const float* d_grad_terms, double*
 
 pinn_status pinn_loss_grad(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch, const float* d_params,
                            void* d_ws, size_t ws_bytes, double* d_loss_terms, float* d_grad, void* stream) {
-  return run(h, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, d_grad, stream, true);
+  return run_graphed(h, 1, prob, batch, d_params, d_ws, ws_bytes, d_loss_terms, d_grad, nullptr, stream);
 }
 
 pinn_status pinn_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t n, int64_t step,

@@ -61,6 +61,20 @@ struct Plan {
 
 }  // namespace pinn
 
+// Everything a captured step depends on: the call's arguments and the handle's
+// settings.  Zero-filled before use so that memcmp also covers the padding.
+struct pinn_graph_key {
+  int kind;                  // 0 loss, 1 loss+grad, 2 loss+grad+input map, 3 per-term grads
+  pinn_problem prob;
+  pinn_batch batch;
+  const void* params; void* ws; size_t ws_bytes; void* loss; void* grad; void* out2;
+  int64_t chunk_points;
+  int causal_M; double causal_eps, causal_t0, causal_t1;
+  int act; float omega0;
+  const float* ff_B; int periodic; double periods[3];
+  void* stream;
+};
+
 struct pinn_handle {
   pinn_spec spec{};
   int d_in = 0, d_out = 0, L = 0;
@@ -80,6 +94,11 @@ struct pinn_handle {
   float* d_periodic_B = nullptr;   // periodic input map: owned diag(2 pi / P) [d_in][d_in]
   bool periodic = false;     // ff_B is d_periodic_B; the input-map gradient is dL/dP
   double periods[3] = {0, 0, 0};
+  // CUDA-graph replay of whole calls (pinn_set_graph): the last captured call and its key
+  bool graph_on = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  pinn_graph_key graph_key{};
   int act = PINN_ACT_TANH;   // hidden activation; sine keeps Z and runs on CUDA cores
   float omega0 = 1.f;
   char err[512] = {0};

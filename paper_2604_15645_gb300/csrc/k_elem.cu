@@ -136,7 +136,7 @@ void launch_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, i
 // the second-order row (the input has no curvature); then the activation's jet rule.
 // Writes A_1 (and its value-row low half), and for the sine activation Z_1 (FP32).
 // ------------------------------------------------------------------------------------
-template <typename T, int LO>
+template <typename T, int LO, bool SINE>
 __global__ void k_first_layer(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                               int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, T* A1,
                               void* A1lo, int64_t NP, float omega0, float* Z1) {
@@ -163,7 +163,7 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
           z[r] = d >= 0 ? Wf[d] : 0.f;
         }
       }
-      if (Z1) jet_fwd_sine(z, a, mode, omega0);
+      if constexpr (SINE) jet_fwd_sine(z, a, mode, omega0);
       else jet_fwd<(LO == 1)>(z, a, mode);
 #pragma unroll
       for (int r = 0; r < 4; ++r) { aa[r][k] = a[r]; zs[r][k] = z[r]; }
@@ -172,7 +172,7 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       store4<T>(A1 + toff(f, c0 + 64 * r, fout), aa[r]);
-      if (Z1) store4<float>(Z1 + toff(f, c0 + 64 * r, fout), zs[r]);
+      if constexpr (SINE) store4<float>(Z1 + toff(f, c0 + 64 * r, fout), zs[r]);
     }
     if (LO) store_lo4<LO>(A1lo, loff(f, p0, fout), aa[0]);
   }
@@ -182,12 +182,22 @@ void launch_first_layer(const float* x_res, const float* x_ic, const float* x_bc
                         int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, void* A1,
                         void* A1lo, int64_t NP, int prec, float omega0, float* Z1, cudaStream_t st) {
   dim3 grid((unsigned)std::min<int64_t>((NP / 4 + 255) / 256, 4096), fout);
-  if (prec == PINN_BF16)
-    k_first_layer<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout,
-                                                          mode, (__nv_bfloat16*)A1, A1lo, NP, omega0, Z1);
-  else
-    k_first_layer<float, 0><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout, mode,
-                                                  (float*)A1, nullptr, NP, omega0, Z1);
+  if (prec == PINN_BF16) {
+    if (Z1)
+      k_first_layer<__nv_bfloat16, 1, true><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b,
+                                                                  fout, mode, (__nv_bfloat16*)A1, A1lo, NP, omega0, Z1);
+    else
+      k_first_layer<__nv_bfloat16, 1, false><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b,
+                                                                   fout, mode, (__nv_bfloat16*)A1, A1lo, NP, omega0,
+                                                                   nullptr);
+  } else {
+    if (Z1)
+      k_first_layer<float, 0, true><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout,
+                                                          mode, (float*)A1, nullptr, NP, omega0, Z1);
+    else
+      k_first_layer<float, 0, false><<<grid, 256, 0, st>>>(x_res, x_ic, x_bc, n_res, n_ic, n_bc, d_in, W, b, fout,
+                                                           mode, (float*)A1, nullptr, NP, omega0, nullptr);
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -289,7 +299,7 @@ __device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_
 // lane = 8 * pg + sl: point group pg (4 consecutive points) and feature slice sl
 // (features sl, sl+8, ...).  The 8 slices of a point group combine their partial
 // outputs with three xor-shuffles; every slice then holds the group's outputs.
-template <typename T, int D, bool FAST>
+template <typename T, int D, bool FAST, bool SINE>
 __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   extern __shared__ float sW[];   // [d_out][w] weights, then [warps][d_out][w] dW accumulators
   const int w = a.w;
@@ -434,7 +444,6 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
           if (pg == 0 && live) sdw[(warp * D + c) * w + f] += g;
         }
       }
-      if (!live) continue;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         float ab[4] = {0.f, 0.f, 0.f, 0.f}, zz[4], o[4];
@@ -444,7 +453,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
 #pragma unroll
           for (int r = 0; r < 4; ++r) ab[r] = fmaf(wc, Ub[j][c][r], ab[r]);
         }
-        if (a.ZL) {   // sine: the adjoint is evaluated from the pre-activation jets
+        if constexpr (SINE) {   // the adjoint is evaluated from the pre-activation jets
 #pragma unroll
           for (int r = 0; r < 4; ++r) zz[r] = a.ZL[toff(f, cb + 64 * r + j, w)];
           jet_adj_sine(zz, ab, o, a.jet_mode, a.omega0);
@@ -457,8 +466,9 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
         for (int r = 0; r < 4; ++r) zb[r][j] = o[r];
       }
       T* zbrow = Zb + toff(f, cb, w);
+      if (live)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) store4<T>(zbrow + 64 * r, zb[r]);
+        for (int r = 0; r < 4; ++r) store4<T>(zbrow + 64 * r, zb[r]);
     }
   }
   __shared__ double sh[OUT_THREADS / 32];
@@ -500,9 +510,9 @@ int out_loss_blocks(int64_t NP) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(NP / TILE_PTS, 4096));
 }
 
-template <typename T, int D, bool FAST>
+template <typename T, int D, bool FAST, bool SINE>
 cudaError_t out_loss_launch(const OutArgs& a, int nblocks, size_t smem, cudaStream_t st) {
-  auto kern = k_out_loss<T, D, FAST>;
+  auto kern = k_out_loss<T, D, FAST, SINE>;
   // weights + per-warp dW accumulators: up to 120 KB for 2048-wide, 3-output networks
   static size_t reserved = 48 * 1024;
   if (smem > reserved) {
@@ -516,11 +526,20 @@ cudaError_t out_loss_launch(const OutArgs& a, int nblocks, size_t smem, cudaStre
 
 cudaError_t launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st) {
   const size_t smem = sizeof(float) * a.d_out * a.w * (1 + OUT_THREADS / 32);
+  // the sine adjoint (from stored pre-activations) is a separate instantiation, so the
+  // tanh kernels carry none of its registers
+  if (a.ZL) {
+    if (prec == PINN_BF16)
+      return a.d_out == 1 ? out_loss_launch<__nv_bfloat16, 1, true, true>(a, nblocks, smem, st)
+                          : out_loss_launch<__nv_bfloat16, 3, true, true>(a, nblocks, smem, st);
+    return a.d_out == 1 ? out_loss_launch<float, 1, false, true>(a, nblocks, smem, st)
+                        : out_loss_launch<float, 3, false, true>(a, nblocks, smem, st);
+  }
   if (prec == PINN_BF16)
-    return a.d_out == 1 ? out_loss_launch<__nv_bfloat16, 1, true>(a, nblocks, smem, st)
-                        : out_loss_launch<__nv_bfloat16, 3, true>(a, nblocks, smem, st);
-  return a.d_out == 1 ? out_loss_launch<float, 1, false>(a, nblocks, smem, st)
-                      : out_loss_launch<float, 3, false>(a, nblocks, smem, st);
+    return a.d_out == 1 ? out_loss_launch<__nv_bfloat16, 1, true, false>(a, nblocks, smem, st)
+                        : out_loss_launch<__nv_bfloat16, 3, true, false>(a, nblocks, smem, st);
+  return a.d_out == 1 ? out_loss_launch<float, 1, false, false>(a, nblocks, smem, st)
+                      : out_loss_launch<float, 3, false, false>(a, nblocks, smem, st);
 }
 
 

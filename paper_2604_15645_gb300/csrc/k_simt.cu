@@ -36,7 +36,7 @@ __device__ __forceinline__ void load_vec8<__nv_bfloat16>(const __nv_bfloat16* p,
 //        with the sine activation also the pre-activation jets Z)
 // EPI 1: adjoint (reads A_{l-1}, or Z_{l-1} for sine, the jet adjoint, writes Zbar_{l-1})
 // EPI 2: linear adjoint (writes W^T Zbar itself: the adjoint of the input jets)
-template <typename T, int EPI>
+template <typename T, int EPI, bool SINE>
 __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__ Aop, const T* __restrict__ Bop,
                                                        const __nv_bfloat16* __restrict__ Blo, int M, int K,
                                                        int64_t NP, EpiArgs e) {
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
     const int f = m0 + ty * 4 + i;
     if (f >= M) continue;
     float o[4][4], zz[4][4];   // [row][point]
-    if (EPI == 1 && e.act) {   // sine: the pre-activation jets of the layer below
+    if (EPI == 1 && SINE) {   // sine: the pre-activation jets of the layer below
       const float* zr = e.zin + toff(f, n0 + 4 * tx, M);
       for (int r = 0; r < 4; ++r) load4<float>(zr + 64 * r, zz[r]);
     } else if (EPI == 1) {   // tanh: the output jet of the layer below (value row: hi + lo for BF16)
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
       if (EPI == 2) {
         for (int r = 0; r < 4; ++r) o[r][j] = acc[i][4 * r + j];
       } else if (EPI == 0) {
-        if (e.act) {
+        if constexpr (SINE) {
           jet_fwd_sine(z, a, e.jet_mode, e.omega0);
           for (int r = 0; r < 4; ++r) zz[r][j] = z[r];
         } else {
@@ -134,12 +134,12 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
         }
         for (int r = 0; r < 4; ++r) o[r][j] = a[r];
       } else {
-        if (e.act) jet_adj_sine(z, ab, a, e.jet_mode, e.omega0);
+        if constexpr (SINE) jet_adj_sine(z, ab, a, e.jet_mode, e.omega0);
         else jet_adj_a(z, ab, a, e.jet_mode);
         for (int r = 0; r < 4; ++r) o[r][j] = a[r];
       }
     }
-    if (EPI == 0 && e.act) {
+    if (EPI == 0 && SINE) {
       float* zrow = e.zout + toff(f, n0 + 4 * tx, M);
       for (int r = 0; r < 4; ++r) store4<float>(zrow + 64 * r, zz[r]);
     }
@@ -215,20 +215,37 @@ __global__ void __launch_bounds__(THREADS) k_simt_dw(const TA* __restrict__ Aop,
 void launch_simt_gemm_fwd(const float* Aop, const void* Bop, int M, int K, int64_t NP, const EpiArgs& e, int prec,
                           cudaStream_t st) {
   dim3 grid((unsigned)(NP / TILE_PTS), (M + BM - 1) / BM);
-  if (prec == PINN_BF16)
-    k_simt_gemm<__nv_bfloat16, 0><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop,
-                                                            (const __nv_bfloat16*)e.alo_in, M, K, NP, e);
-  else
-    k_simt_gemm<float, 0><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
+  if (prec == PINN_BF16) {
+    if (e.act)
+      k_simt_gemm<__nv_bfloat16, 0, true><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop,
+                                                                    (const __nv_bfloat16*)e.alo_in, M, K, NP, e);
+    else
+      k_simt_gemm<__nv_bfloat16, 0, false><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop,
+                                                                     (const __nv_bfloat16*)e.alo_in, M, K, NP, e);
+  } else {
+    if (e.act)
+      k_simt_gemm<float, 0, true><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
+    else
+      k_simt_gemm<float, 0, false><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
+  }
 }
 
 void launch_simt_gemm_adj(const float* Aop, const void* Bop, int M, int K, int64_t NP, const EpiArgs& e, int prec,
                           cudaStream_t st) {
   dim3 grid((unsigned)(NP / TILE_PTS), (M + BM - 1) / BM);
-  if (prec == PINN_BF16)
-    k_simt_gemm<__nv_bfloat16, 1><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, nullptr, M, K, NP, e);
-  else
-    k_simt_gemm<float, 1><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
+  if (prec == PINN_BF16) {
+    if (e.act)
+      k_simt_gemm<__nv_bfloat16, 1, true><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, nullptr, M, K,
+                                                                    NP, e);
+    else
+      k_simt_gemm<__nv_bfloat16, 1, false><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, nullptr, M, K,
+                                                                     NP, e);
+  } else {
+    if (e.act)
+      k_simt_gemm<float, 1, true><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
+    else
+      k_simt_gemm<float, 1, false><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
+  }
 }
 
 void launch_simt_gemm_lin(const float* Aop, const void* Bop, int M, int K, int64_t NP, void* out, int prec,
@@ -237,9 +254,10 @@ void launch_simt_gemm_lin(const float* Aop, const void* Bop, int M, int K, int64
   EpiArgs e{};
   e.out = out;
   if (prec == PINN_BF16)
-    k_simt_gemm<__nv_bfloat16, 2><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, nullptr, M, K, NP, e);
+    k_simt_gemm<__nv_bfloat16, 2, false><<<grid, THREADS, 0, st>>>(Aop, (const __nv_bfloat16*)Bop, nullptr, M, K,
+                                                                   NP, e);
   else
-    k_simt_gemm<float, 2><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
+    k_simt_gemm<float, 2, false><<<grid, THREADS, 0, st>>>(Aop, (const float*)Bop, nullptr, M, K, NP, e);
 }
 
 void launch_simt_gemm_dw(const void* Aop, bool a_fp32, const void* Bop, bool b_fp32, int M, int N, int64_t NC,

@@ -72,5 +72,7 @@ def test_invalid_width_and_null_args(lib):
     assert lib.pinn_destroy(None) == 0
     assert lib.pinn_set_chunk_points(None, 64) == 1
     assert lib.pinn_set_activation(None, 1, 2.0) == 1
+    assert lib.pinn_set_graph(None, 1) == 1
+    assert lib.pinn_set_periodic(None, None) == 1
     # Adam argument checks happen before any device work
     assert lib.pinn_adam_step(None, None, None, None, 10, 1, 1e-3, 0.9, 0.999, 1e-8, None) == 1
