@@ -295,6 +295,32 @@ __device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_
   }
 }
 
+// Cache hints for the two passes over A_L: the second read is its last use, and the
+// adjoint Zbar_L is written once and read by the next kernel, so neither should push
+// the first pass's A_L lines out of L2 before the second pass re-reads them.
+template <typename T> __device__ __forceinline__ void load4_last(const T* p, float v[4]);
+template <> __device__ __forceinline__ void load4_last<float>(const float* p, float v[4]) {
+  const float4 q = __ldlu(reinterpret_cast<const float4*>(p));
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <> __device__ __forceinline__ void load4_last<__nv_bfloat16>(const __nv_bfloat16* p, float v[4]) {
+  const uint2 u = __ldlu(reinterpret_cast<const uint2*>(p));
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <typename T> __device__ __forceinline__ void store4_stream(T* p, const float v[4]);
+template <> __device__ __forceinline__ void store4_stream<float>(float* p, const float v[4]) {
+  __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+template <> __device__ __forceinline__ void store4_stream<__nv_bfloat16>(__nv_bfloat16* p, const float v[4]) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 u;
+  u.x = *reinterpret_cast<const uint32_t*>(&lo);
+  u.y = *reinterpret_cast<const uint32_t*>(&hi);
+  __stcs(reinterpret_cast<uint2*>(p), u);
+}
+
 // One block per 64-point tile (grid-stride).  Warp w takes points 16w..16w+15;
 // lane = 8 * pg + sl: point group pg (4 consecutive points) and feature slice sl
 // (features sl, sl+8, ...).  The 8 slices of a point group combine their partial
@@ -425,7 +451,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
       {
         const T* arow = AL + toff(f, cb, w);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) load4<T>(arow + 64 * r, av[r]);
+        for (int r = 0; r < 4; ++r) load4_last<T>(arow + 64 * r, av[r]);
         if (ALlo) {
           float lo[4];
           load4<__nv_bfloat16>(ALlo + loff(f, p0, w), lo);
@@ -468,7 +494,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
       T* zbrow = Zb + toff(f, cb, w);
       if (live)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) store4<T>(zbrow + 64 * r, zb[r]);
+        for (int r = 0; r < 4; ++r) store4_stream<T>(zbrow + 64 * r, zb[r]);
     }
   }
   __shared__ double sh[OUT_THREADS / 32];
@@ -638,7 +664,9 @@ __device__ __forceinline__ void put_grad(const FinalizeArgs& a, int64_t idx, flo
   a.grad[idx] = a.accumulate ? a.grad[idx] + v : v;
 }
 
-__global__ void k_finalize_grad(FinalizeArgs a) {
+constexpr int FIN_THREADS = 128;
+
+__global__ void __launch_bounds__(FIN_THREADS) k_finalize_grad(FinalizeArgs a) {
   const int l = blockIdx.y, i = blockIdx.x;
   const int fin = a.fin[l], fout = a.fout[l];
   if (i >= fout) return;
@@ -669,7 +697,7 @@ __global__ void k_finalize_grad(FinalizeArgs a) {
     if ((fin & 3) == 0 && fin / 4 <= (int)blockDim.x) {
       // G thread groups each sum every G-th split of the same float4 column; the
       // groups are then combined in a fixed order (deterministic).
-      __shared__ double shd[128][4];
+      __shared__ double shd[FIN_THREADS][4];
       const int ncol4 = fin / 4;
       const int G = blockDim.x / ncol4;
       const int q = threadIdx.x % ncol4, g = threadIdx.x / ncol4;
@@ -736,7 +764,7 @@ void launch_finalize_grad(const FinalizeArgs& a, cudaStream_t st) {
   int maxout = 1;
   for (int l = 0; l < a.L1; ++l) maxout = std::max(maxout, a.fout[l]);
   dim3 grid(maxout, a.L1);
-  k_finalize_grad<<<grid, 128, 0, st>>>(a);
+  k_finalize_grad<<<grid, FIN_THREADS, 0, st>>>(a);
 }
 
 __global__ void k_finalize_loss(const double* part, int nblocks, int64_t n_res, int64_t n_ic, int64_t n_bc,
