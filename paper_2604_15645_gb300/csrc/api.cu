@@ -106,6 +106,7 @@ struct CallPlan {
   LayerPlan lay[PINN_MAX_HIDDEN + 1];
   bool tc[PINN_MAX_HIDDEN + 1];      // layer li runs its jet GEMMs on tensor cores
   bool fused_db[PINN_MAX_HIDDEN + 1];  // layer li's bias partials come from a fused adjoint epilogue
+  bool out_db = false;                 // the last hidden layer's bias partials come from the output/loss kernel
   int nbpart[PINN_MAX_HIDDEN + 1];     // bias partial count of layer li
   bool pm = false;                     // TF32 on tensor cores: point-major operand copies
   size_t apm[2] = {0, 0};              // point-major A_l, buffer l % 2 ([NC][fin] FP32)
@@ -154,7 +155,11 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
     // Bias partials of hidden layer li come from the tensor-core adjoint epilogue of
     // layer li+1 when that one runs on tensor cores, else from a row reduction.
     c->fused_db[li] = (li + 1 < h->L) && c->tc[li + 1];
-    c->nbpart[li] = li == h->L ? c->p.nloss_blocks
+    // the last hidden layer's bias partials come from the output/loss kernel (it
+    // writes that layer's adjoint), unless it is a first layer on raw coordinates
+    const bool out_db = (li == h->L - 1) && !raw;
+    if (li == h->L - 1) c->out_db = out_db;
+    c->nbpart[li] = (li == h->L || out_db) ? c->p.nloss_blocks
                     : c->fused_db[li] ? (int)(c->p.NC / TC_BN) * TC_DB_PARTS : c->p.nbpart;
     const int dbs = raw ? 1 + h->d_in : 1;
     lp.dbpart = take((size_t)c->nbpart[li] * lp.fout * dbs * 4);
@@ -290,6 +295,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
   oa.x_res = b->x_res;
   oa.dwpart = reinterpret_cast<float*>(ws + cp.lay[L].dwpart);
   oa.dbpart = reinterpret_cast<float*>(ws + cp.lay[L].dbpart);
+  oa.dbhid = cp.out_db ? reinterpret_cast<float*>(ws + cp.lay[L - 1].dbpart) : nullptr;
   oa.Zbar = ws + p.Zbar[L % 2];
   oa.ZL = sine ? reinterpret_cast<const float*>(ws + p.Z[L]) : nullptr;
   oa.omega0 = h->omega0;
@@ -360,7 +366,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
                             reinterpret_cast<float*>(ws + lp.dwpart), prec, st);
       }
     }
-    if (!cp.fused_db[li]) {
+    if (!cp.fused_db[li] && !(li == L - 1 && cp.out_db)) {
       PhaseScope ps(h, st, PH_RED, 1);
       launch_row_reduce(zb, false, lp.fout, p.NP, p.n_res, p.n_ic, p.n_bc, p.nbpart, b->x_res, b->x_ic, b->x_bc,
                         raw ? h->d_in : 0, mode, reinterpret_cast<float*>(ws + lp.dbpart), prec, st);

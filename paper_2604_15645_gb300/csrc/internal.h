@@ -192,6 +192,7 @@ struct OutArgs {
   const float* seg_scale;  // phase 2: per-segment seed scale lambda omega_i / (M N_i), replacing k_pde
   float* dwpart;         // output-layer dW partials [nblocks][d_out][w] (per block, fixed order)
   float* dbpart;         // output-layer bias partials [d_out][nblocks]
+  float* dbhid;          // last hidden layer's bias partials [w][nblocks] (value rows of Zbar_L), or nullptr
   void* Zbar;            // Zbar_L^T [w][NC] compute type
   const float* ZL;       // sine activation: Z_L^T [w][NC] FP32 for the adjoint (else nullptr)
   float omega0;

@@ -327,11 +327,14 @@ template <> __device__ __forceinline__ void store4_stream<__nv_bfloat16>(__nv_bf
 // outputs with three xor-shuffles; every slice then holds the group's outputs.
 template <typename T, int D, bool FAST, bool SINE>
 __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
-  extern __shared__ float sW[];   // [d_out][w] weights, then [warps][d_out][w] dW accumulators
+  // [d_out][w] weights, then [warps][d_out][w] dW accumulators, then [warps][w] bias
+  // accumulators of the last hidden layer
+  extern __shared__ float sW[];
   const int w = a.w;
   float* sdw = sW + D * w;
+  float* sdb = sdw + (OUT_THREADS / 32) * D * w;
   for (int i = threadIdx.x; i < D * w; i += blockDim.x) sW[i] = a.W[i];
-  for (int i = threadIdx.x; i < (OUT_THREADS / 32) * D * w; i += blockDim.x) sdw[i] = 0.f;
+  for (int i = threadIdx.x; i < (OUT_THREADS / 32) * (D + 1) * w; i += blockDim.x) sdw[i] = 0.f;
   __syncthreads();
   const T* AL = reinterpret_cast<const T*>(a.AL);
   const __nv_bfloat16* ALlo = reinterpret_cast<const __nv_bfloat16*>(a.ALlo);
@@ -495,6 +498,12 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
       if (live)
 #pragma unroll
         for (int r = 0; r < 4; ++r) store4_stream<T>(zbrow + 64 * r, zb[r]);
+      if (a.dbhid) {   // the last hidden layer's bias gradient: value rows of Zbar_L
+        float s = (zb[0][0] + zb[0][1]) + (zb[0][2] + zb[0][3]);
+        s += __shfl_xor_sync(0xffffffffu, s, 8);
+        s += __shfl_xor_sync(0xffffffffu, s, 16);
+        if (pg == 0 && live) sdb[warp * w + f] += s;
+      }
     }
   }
   __shared__ double sh[OUT_THREADS / 32];
@@ -516,6 +525,13 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
     for (int k = 0; k < OUT_THREADS / 32; ++k) s += sdw[k * D * w + i];
     a.dwpart[(int64_t)blockIdx.x * D * w + i] = s;
   }
+  if (a.dbhid)
+    for (int i = threadIdx.x; i < w; i += blockDim.x) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < OUT_THREADS / 32; ++k) s += sdb[k * w + i];
+      a.dbhid[(int64_t)i * gridDim.x + blockIdx.x] = s;
+    }
   for (int c = 0; c < D; ++c) {
     float v = dbo[c];
     v += __shfl_xor_sync(0xffffffffu, v, 8);
@@ -551,7 +567,7 @@ cudaError_t out_loss_launch(const OutArgs& a, int nblocks, size_t smem, cudaStre
 }
 
 cudaError_t launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st) {
-  const size_t smem = sizeof(float) * a.d_out * a.w * (1 + OUT_THREADS / 32);
+  const size_t smem = sizeof(float) * a.w * (a.d_out * (1 + OUT_THREADS / 32) + OUT_THREADS / 32);
   // the sine adjoint (from stored pre-activations) is a separate instantiation, so the
   // tanh kernels carry none of its registers
   if (a.ZL) {

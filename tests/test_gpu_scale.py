@@ -85,3 +85,46 @@ def test_cavity_at_scale_gradient_against_finite_differences(cuda_lib):
     # the BF16 paths under test (full weight split, and value-row split), at the stated tolerance
     for _, g16 in bf16.values():
         assert rel(g16[idx], fd) <= TOL["bf16"]
+
+
+def test_maxwell_full_size_gradient_against_finite_differences(cuda_lib):
+    """The Maxwell workload at full size (262,144 interior points, 5x512, RWF) in the
+    BF16 configuration the bench times: the gradient on 24 seeded coordinates against
+    central differences of the FP32 loss, and the loss against the FP32 loss."""
+    from paper_2604_15645_gb300 import api
+    _free()
+    w, p, B, b = make_workload("maxwell_te_5x512")
+    prob = api.make_problem(w.problem.nu, w.problem.lambda_pde, w.problem.lambda_ic, w.problem.lambda_bc)
+    db = api.DeviceBatch.from_host(b)
+    params = torch.tensor(p, device="cuda")
+    net16 = api.PinnNet.from_spec(w.spec, "bf16")
+    if B is not None:
+        net16.set_ff_matrix(B)
+    t16, g16 = net16.loss_grad(params, db, prob)
+    loss16, g16 = float(t16[0]), g16.cpu().numpy().astype(np.float64)
+    assert net16.status_poll() == 0
+    del net16
+    _free()
+
+    net = api.PinnNet.from_spec(w.spec, "fp32")
+    if B is not None:
+        net.set_ff_matrix(B)
+    t32, g32 = net.loss_grad(params, db, prob)
+    loss32, g32 = float(t32[0]), g32.cpu().numpy().astype(np.float64)
+    assert abs(loss16 - loss32) <= TOL["bf16"] * abs(loss32)
+    rng = np.random.default_rng(2025)
+    idx = np.sort(rng.choice(params.numel(), size=24, replace=False))
+    fd = np.empty(idx.size)
+    out = torch.empty(8, dtype=torch.float64, device="cuda")
+    for n, i in enumerate(idx):
+        th = float(p[i])
+        h = 1e-3 * max(1.0, abs(th))
+        vals = []
+        for s in (+1, -1):
+            params[i] = th + s * h
+            vals.append(float(net.loss(params, db, prob, out=out)[0]))
+        params[i] = th
+        fd[n] = (vals[0] - vals[1]) / (2 * h)
+    assert net.status_poll() == 0
+    assert rel(g32[idx], fd) < 1e-3
+    assert rel(g16[idx], fd) <= TOL["bf16"]
