@@ -73,7 +73,6 @@ template <typename T, int LO>
 __global__ void k_embed_ff(const float* x_res, const float* x_ic, const float* x_bc, int64_t n_res, int64_t n_ic,
                            int64_t n_bc, int d_in, const float* B, int m, int mode, T* A0, void* A0lo, int64_t NP) {
   const int j = blockIdx.y;
-  const int64_t NC = 4 * NP;
   float Bj[3] = {0.f, 0.f, 0.f};
   for (int i = 0; i < d_in; ++i) Bj[i] = B[(int64_t)i * m + j];
   const float q = (mode == JET_MAXWELL) ? 0.f : (Bj[0] * Bj[0] + (mode == JET_NS ? Bj[1] * Bj[1] : 0.f));
@@ -141,7 +140,6 @@ __global__ void k_first_layer(const float* x_res, const float* x_ic, const float
                               int64_t n_bc, int d_in, const float* W, const float* b, int fout, int mode, T* A1,
                               void* A1lo, int64_t NP, float omega0, float* Z1) {
   const int f = blockIdx.y;
-  const int64_t NC = 4 * NP;
   float Wf[3] = {0.f, 0.f, 0.f};
   for (int i = 0; i < d_in; ++i) Wf[i] = W[(int64_t)f * d_in + i];
   const float bf = b[f];
@@ -342,7 +340,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pg = lane >> 3, sl = lane & 7;
   const int q0 = 16 * warp + 4 * pg;               // first of this thread's 4 points in the tile
-  const int64_t NC = a.NC, ntiles = a.NP / TILE_PTS;
+  const int64_t ntiles = a.NP / TILE_PTS;
   double acc[5] = {0, 0, 0, 0, 0};
   float dbo[3] = {0.f, 0.f, 0.f};                 // output bias gradient (value-row seeds)
   // temporal causality, first pass: this block's segment sums (3 equations + count),
@@ -607,7 +605,6 @@ __global__ void k_row_reduce(const T* Zb, int M, int64_t NP, int64_t n_res, int6
   const int row = blockIdx.x * (blockDim.x >> 5) + warp;
   if (row >= M) return;
   const int chunk = blockIdx.y;
-  const int64_t NC = 4 * NP;
   const int64_t per = (NP + nbpart - 1) / nbpart;
   const int64_t p0 = chunk * per, p1 = min(NP, p0 + per);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};

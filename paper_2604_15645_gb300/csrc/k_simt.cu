@@ -47,7 +47,6 @@ __global__ void __launch_bounds__(THREADS) k_simt_gemm(const float* __restrict__
   const int ty = t >> 4, tx = t & 15;
   const int m0 = blockIdx.y * BM;
   const int64_t tile = blockIdx.x;
-  const int64_t NC = 4 * NP;
   const int64_t n0 = tile * BN;
   float acc[4][16];
 #pragma unroll

@@ -126,18 +126,6 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
   }
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, float v[16]) {
   uint32_t* r = reinterpret_cast<uint32_t*>(v);
   asm volatile(
@@ -174,24 +162,6 @@ __device__ __forceinline__ void st16(__nv_bfloat16* p, const float v[16]) {
   }
   st_global_256(p, w);
 }
-__device__ __forceinline__ void st16(float* p, const float v[16]) {
-  st_global_256(p, reinterpret_cast<const uint32_t*>(v));
-  st_global_256(p + 8, reinterpret_cast<const uint32_t*>(v + 8));
-}
-__device__ __forceinline__ void ld16(const __nv_bfloat16* p, float v[16]) {
-  uint32_t w[8];
-  ld_global_256(p, w);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
-    v[2 * i] = f.x;
-    v[2 * i + 1] = f.y;
-  }
-}
-__device__ __forceinline__ void ld16(const float* p, float v[16]) {
-  ld_global_256(p, reinterpret_cast<uint32_t*>(v));
-  ld_global_256(p + 8, reinterpret_cast<uint32_t*>(v + 8));
-}
 
 // One unit row of a jet matrix: 16 BF16 or 8 FP32 values, one full 32-byte sector.
 __device__ __forceinline__ void st_row(__nv_bfloat16* p, const float v[16]) { st16(p, v); }
@@ -203,23 +173,6 @@ template <int N>
 __device__ __forceinline__ void st_f32(float* p, const float* v) {
 #pragma unroll
   for (int i = 0; i < N; i += 8) st_global_256(p + i, reinterpret_cast<const uint32_t*>(v + i));
-}
-// 8 consecutive elements of a row: BF16 as one 16-byte access, FP32 as one 32-byte access.
-__device__ __forceinline__ void st8(__nv_bfloat16* p, const float v[8]) {
-  uint32_t w[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    w[i] = *reinterpret_cast<uint32_t*>(&h);
-  }
-  asm volatile("st.global.v4.b32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
-               : "memory");
-}
-__device__ __forceinline__ void st8(float* p, const float v[8]) {
-  st_global_256(p, reinterpret_cast<const uint32_t*>(v));
-}
-__device__ __forceinline__ void ld8raw(const __nv_bfloat16* p, uint32_t w[4]) {
-  asm volatile("ld.global.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
 }
 __device__ __forceinline__ void ld8raw(const float* p, uint32_t w[8]) { ld_global_256(p, w); }
 // Element i of 8 raw row words (BF16 pairs or FP32).
@@ -286,80 +239,6 @@ struct Cfg {
   static constexpr int BOX_BYTES = BKE * 128;     // one MN-major box: BKE rows of 128 bytes
   static constexpr size_t SMEM = (size_t)STAGES * STAGE + BLOC_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 };
-
-template <typename T>
-__device__ __forceinline__ void store16(T* p, const float v[16]);
-template <>
-__device__ __forceinline__ void store16<float>(float* p, const float v[16]) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    reinterpret_cast<float4*>(p)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-}
-template <>
-__device__ __forceinline__ void store16<__nv_bfloat16>(__nv_bfloat16* p, const float v[16]) {
-  uint32_t u[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    u[i] = *reinterpret_cast<uint32_t*>(&h);
-  }
-  reinterpret_cast<uint4*>(p)[0] = make_uint4(u[0], u[1], u[2], u[3]);
-  reinterpret_cast<uint4*>(p)[1] = make_uint4(u[4], u[5], u[6], u[7]);
-}
-// 16 elements as raw 128-bit words (8 registers for BF16), converted on use.
-template <typename T>
-struct Raw16 {
-  uint4 w[sizeof(T) * 16 / 16];
-};
-template <typename T>
-__device__ __forceinline__ void load_raw16(const T* p, Raw16<T>& r) {
-#pragma unroll
-  for (int i = 0; i < (int)(sizeof(r.w) / sizeof(uint4)); ++i) r.w[i] = reinterpret_cast<const uint4*>(p)[i];
-}
-__device__ __forceinline__ void unpack16(const Raw16<__nv_bfloat16>& r, float v[16]) {
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const uint32_t w[4] = {r.w[i].x, r.w[i].y, r.w[i].z, r.w[i].w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[j]));
-      v[8 * i + 2 * j] = f.x;
-      v[8 * i + 2 * j + 1] = f.y;
-    }
-  }
-}
-__device__ __forceinline__ void unpack16(const Raw16<float>& r, float v[16]) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    v[4 * i] = __uint_as_float(r.w[i].x); v[4 * i + 1] = __uint_as_float(r.w[i].y);
-    v[4 * i + 2] = __uint_as_float(r.w[i].z); v[4 * i + 3] = __uint_as_float(r.w[i].w);
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void load16(const T* p, float v[16]);
-template <>
-__device__ __forceinline__ void load16<float>(const float* p, float v[16]) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float4 q = reinterpret_cast<const float4*>(p)[i];
-    v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
-  }
-}
-template <>
-__device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, float v[16]) {
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const uint4 q = reinterpret_cast<const uint4*>(p)[i];
-    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[j]));
-      v[8 * i + 2 * j] = f.x;
-      v[8 * i + 2 * j + 1] = f.y;
-    }
-  }
-}
 
 // Point-major copy [NC][M] of one thread's 8 points x 4 rows of feature m: column
 // c0 + 64 r + i.  Lanes hold consecutive features, so each store instruction writes
