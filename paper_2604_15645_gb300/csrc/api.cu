@@ -254,6 +254,9 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     e.jet_mode = mode;
     e.act = h->act; e.omega0 = h->omega0;
     e.zout = sine ? reinterpret_cast<float*>(ws + p.Z[li + 1]) : nullptr;
+    // alternate the tile order from layer to layer: each forward starts on the tiles
+    // the previous kernel wrote last (the embedding goes first to last)
+    e.reverse = ((li - h->first_gemm) % 2 == 0) ? 1 : 0;
     PhaseScope ps(h, st, PH_FWD, 1);
     if (cp.tc[li] && cp.pm) {
       // TF32: point-major input; the epilogue also writes the next layer's point-major input
@@ -298,6 +301,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
   oa.dbhid = cp.out_db ? reinterpret_cast<float*>(ws + cp.lay[L - 1].dbpart) : nullptr;
   oa.Zbar = ws + p.Zbar[L % 2];
   oa.ZL = sine ? reinterpret_cast<const float*>(ws + p.Z[L]) : nullptr;
+  oa.reverse = ((L - 1 - h->first_gemm) % 2 == 0) ? 0 : 1;   // against the last forward's order
   oa.omega0 = h->omega0;
   oa.losspart = reinterpret_cast<double*>(ws + p.losspart);
   oa.status = h->d_status;
@@ -389,6 +393,8 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
       e.jet_mode = mode;
       e.act = h->act; e.omega0 = h->omega0;
       e.zin = sine ? reinterpret_cast<const float*>(ws + p.Z[li]) : nullptr;
+      // against the order in which the adjoint it reads was written
+      e.reverse = (((L - 1 - li) % 2 == 0) == (oa.reverse != 0)) ? 0 : 1;
       if (cp.fused_db[li - 1]) {
         e.dbpart = reinterpret_cast<float*>(ws + cp.lay[li - 1].dbpart);
         e.dterms = (li - 1 == 0 && !h->spec.ff_m) ? h->d_in : 0;

@@ -148,6 +148,9 @@ struct EpiArgs {
   float omega0;
   float* zout;
   const float* zin;
+  // tensor-core forward / adjoint: visit the column tiles last to first, so a kernel
+  // starts on the tiles its predecessor touched last (still in L2)
+  int reverse;
   // adjoint only: bias-gradient partials of the layer whose pre-activation adjoint
   // this epilogue writes ([part][M][1 + dterms]; nullptr = not fused), and for a
   // first layer on raw coordinates the coordinate terms of its dW (dterms = d_in).
@@ -195,6 +198,7 @@ struct OutArgs {
   float* dbhid;          // last hidden layer's bias partials [w][nblocks] (value rows of Zbar_L), or nullptr
   void* Zbar;            // Zbar_L^T [w][NC] compute type
   const float* ZL;       // sine activation: Z_L^T [w][NC] FP32 for the adjoint (else nullptr)
+  int reverse;           // visit the point tiles last to first
   float omega0;
   double* losspart;      // [nblocks][8]
   int* status;

@@ -363,7 +363,8 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   __shared__ float s_rr[TILE_PTS][3];
   if (a.segpart)
     for (int i = threadIdx.x; i < CAUSAL_MAX * 4; i += blockDim.x) segacc[i / 4][i % 4] = 0.0;
-  for (int64_t T0 = blockIdx.x; T0 < ntiles; T0 += gridDim.x) {
+  for (int64_t T0i = blockIdx.x; T0i < ntiles; T0i += gridDim.x) {
+    const int64_t T0 = a.reverse ? ntiles - 1 - T0i : T0i;
     const int64_t cb = T0 * TILE_COLS + q0;        // column of row 0 of the first point
     const int64_t p0 = T0 * TILE_PTS + q0;
     float U[4][3][4];                              // [point][output][row]

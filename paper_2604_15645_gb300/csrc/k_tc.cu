@@ -299,6 +299,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
 
   const int total = p.m_tiles * p.n_tiles * (MODE == TC_DW ? p.nsplit : 1);
   auto coords = [&](int t, int& mb, int& nb, int& k0, int& k1) {
+    if (MODE != TC_DW && p.e.reverse) t = total - 1 - t;   // same tiles, last column tile first
     mb = t % p.m_tiles;
     int r = t / p.m_tiles;
     nb = r % p.n_tiles;
