@@ -266,7 +266,7 @@ def oracle_sample_rate(w, params, B, batch, target_s=10.0, n_res=8192, net=None)
     return out
 
 
-TORCH_MAX_POINTS = 262144   # above this the double-backward graph of the larger networks outgrows HBM
+TORCH_MAX_POINTS = 320000   # above this the double-backward graph of the larger networks outgrows HBM
 
 
 def torch_autograd_rate(w, params, B, batch, steps=5, warmup=2):

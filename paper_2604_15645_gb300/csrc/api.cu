@@ -70,7 +70,7 @@ pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   const int L = h->L;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-  q.nbpart = (int)std::min<int64_t>(256, std::max<int64_t>(1, q.NC / 8192));
+  q.nbpart = (int)std::min<int64_t>(256, std::max<int64_t>(1, q.NC / 1024));   // row-reduction chunks of >= 256 points
   if (h->spec.ff_m) {
     q.A[0] = take((size_t)2 * h->spec.ff_m * q.NC * q.es);
     if (q.lo) q.Alo[0] = take((size_t)2 * h->spec.ff_m * q.NP * q.lo_es);
@@ -146,7 +146,7 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
     } else {
       const int tiles = ((lp.fout + 63) / 64) * ((lp.fin + 63) / 64);
       int ns = (4 * std::max(h->sm_count, 1) + tiles - 1) / tiles;
-      ns = (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->p.NC / 512));
+      ns = (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->p.NC / 128));   // >= 128 jet columns per split
       lp.nsplit = ns;
     }
     // the output layer keeps room for its compacted partials after the per-block ones
