@@ -68,3 +68,26 @@ def test_graph_with_chunking_and_loss_only(cuda_lib):
         g1 = net.loss_grad(p, db, prob)[1].clone()
         torch.cuda.synchronize()
         assert torch.equal(t1, t0) and torch.equal(g1, g0)
+
+
+def test_graph_replay_at_full_bench_size(cuda_lib):
+    """The bench's configuration: the full cavity workload (65,536 + 4,096 points, BF16
+    with the value-row weight split) replayed from a graph equals the eager call bit for
+    bit; the eager call is the one the full-size parity test checks against the oracle."""
+    from paper_2604_15645_gb300 import api
+    w, pp, B, b = make_workload("ns_cavity_6x256")      # the full-size parity test's inputs
+    assert w.value_split
+    net = api.PinnNet.from_spec(w.spec, "bf16", value_split=True)
+    net.set_ff_matrix(B)
+    db = api.DeviceBatch.from_host(b)
+    prob = api.make_problem(w.problem.nu, w.problem.lambda_pde, w.problem.lambda_ic, w.problem.lambda_bc)
+    p = torch.tensor(pp, device="cuda")
+    g0 = torch.empty_like(p)
+    t0 = net.loss_grad(p, db, prob, grad=g0)[0].clone()
+    net.set_graph(True)
+    g1 = torch.empty_like(p)
+    for _ in range(3):
+        t1 = net.loss_grad(p, db, prob, grad=g1)[0].clone()
+    torch.cuda.synchronize()
+    assert torch.equal(t1, t0) and torch.equal(g1, g0)
+    assert net.status_poll() == 0

@@ -70,6 +70,17 @@ def test_widths_not_multiples_of_eight(cuda_lib, pde, d_in, d_out, widths, ff):
         _check(spec, p, B, b, Problem(0.02, 0.3, 2.0, 5.0), precision, f"odd widths {widths} {precision}")
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_maximum_width(cuda_lib, precision):
+    # the widest layer the library takes (2048): the output kernel's shared-memory
+    # accumulators (weights, dW and bias slots) are at their largest
+    spec = NetSpec(PDE_NS, 2, 3, [64, 2048], ff_m=16, ff_sigma=1.0, rwf=True)
+    p = init_params(spec, 63, 0.05)
+    B = ff_matrix(spec, 64)
+    b = make_batch(PDE_NS, 200, 0, 56, 65, 66)
+    _check(spec, p, B, b, Problem(0.01, 1.0, 1.0, 1.0), precision, f"width 2048 {precision}")
+
+
 @pytest.mark.parametrize("precision,expect_tc", [("fp32", False), ("tf32", True), ("bf16", True)])
 def test_tensor_core_engine_selection(cuda_lib, precision, expect_tc):
     # FP32 runs the exact CUDA-core GEMMs; TF32 and BF16 run every hidden layer on tcgen05
