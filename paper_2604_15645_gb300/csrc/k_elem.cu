@@ -708,7 +708,6 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize_grad(FinalizeArgs a) {
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   {
     Acc2 ab[4];
-#pragma unroll 8
     for (int p = threadIdx.x; p < nbp; p += blockDim.x) {
       const float* q = dbp + ((int64_t)i * nbp + p) * dbs;
       ab[0].add(q[0]);
@@ -733,7 +732,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize_grad(FinalizeArgs a) {
       if (g < G) {
         const float* base = part + (int64_t)i * fin + 4 * q;
         Acc2 a0, a1, a2, a3;
-#pragma unroll 8
+#pragma unroll 4
         for (int s = g; s < ns; s += G) {
           const float4 x = *reinterpret_cast<const float4*>(base + s * sstride);
           a0.add(x.x); a1.add(x.y); a2.add(x.z); a3.add(x.w);
