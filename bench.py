@@ -266,10 +266,56 @@ def oracle_sample_rate(w, params, B, batch, target_s=10.0, n_res=8192, net=None)
     return out
 
 
+def host_description():
+    """Architecture, CPU model and logical core count of the host."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and model is None:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return {"arch": platform.machine(), "model": model, "nproc": os.cpu_count()}
+
+
+def oracle_one_core_rate(workload, n_res=2048, target_s=5.0):
+    """The oracle on one host core: a child process with every BLAS pool at one thread,
+    on a smaller sample of the same workload."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    code = (
+        "import sys, time, json\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import oracle\n"
+        "from synth import make_workload\n"
+        f"w, p, B, b = make_workload({workload!r})\n"
+        f"f = min(1.0, {n_res} / max(b.n_res, 1))\n"
+        f"s = b.subset(min({n_res}, b.n_res), int(round(b.n_ic * f)), int(round(b.n_bc * f)))\n"
+        "m = oracle.Model.from_spec(w.spec)\n"
+        "lam = (w.problem.lambda_pde, w.problem.lambda_ic, w.problem.lambda_bc)\n"
+        "t0 = time.perf_counter(); n = 0\n"
+        "while True:\n"
+        "    oracle.loss_and_grad(m, p, B, s, w.problem.nu, lam); n += 1\n"
+        f"    if time.perf_counter() - t0 >= {target_s}: break\n"
+        "dt = time.perf_counter() - t0\n"
+        "pts = s.n_res + s.n_ic + s.n_bc\n"
+        "print(json.dumps({'value': pts * n / dt, 'unit': 'points/s', 'cores': 1, "
+        "'sample': f'{s.n_res} interior + {s.n_ic} initial + {s.n_bc} boundary points, {n} call(s)'}))\n")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:   # reported, not hidden
+        return {"error": repr(e)[:300]}
+
+
 TORCH_MAX_POINTS = 320000   # above this the double-backward graph of the larger networks outgrows HBM
 
 
-def torch_autograd_rate(w, params, B, batch, steps=5, warmup=2):
+def torch_autograd_rate(w, params, B, batch, steps=5, warmup=2, tf32=False):
     """The paper's recipe (torch.autograd.grad create_graph + loss.backward), FP32,
     TF32 off, same parameters and points, CUDA events.  Batches above TORCH_MAX_POINTS
     run on a leading sample of every point set, scaled alike (points/s is a per-point
@@ -284,8 +330,8 @@ def torch_autograd_rate(w, params, B, batch, steps=5, warmup=2):
         batch = batch.subset(nr, ni, nb)
         sample = f"{nr} interior + {ni} initial + {nb} boundary points (the leading {f:.3f} of each set)"
 
-    torch.backends.cuda.matmul.allow_tf32 = False
-    torch.backends.cudnn.allow_tf32 = False
+    torch.backends.cuda.matmul.allow_tf32 = tf32
+    torch.backends.cudnn.allow_tf32 = tf32
     model = ta.TorchPINN(w.spec, params, B, "cuda", torch.float32)
     bt = ta.batch_to_torch(batch, "cuda", torch.float32)
     lam = (w.problem.lambda_pde, w.problem.lambda_ic, w.problem.lambda_bc)
@@ -418,6 +464,15 @@ def run_ours(args, ws_n, rank, local):
     clk = clocks.stop()
     status = net.status_poll()
 
+    # the spread of single steps: the same K calls again, an event pair around each
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        a.record(stream)
+        net.loss_grad(p, db, prob, grad=grad)
+        b.record(stream)
+    torch.cuda.synchronize()
+    per_step = np.array([a.elapsed_time(b) for a, b in ev])
+
     # per-phase kernel times: the same K steps again, launched eagerly with a CUDA
     # event pair around each launch group on the launching stream (graph replays
     # cannot carry them); the kernels are the ones the timed region replays
@@ -511,6 +566,11 @@ def run_ours(args, ws_n, rank, local):
         "metric": METRIC, "value": round(whole_job_rate(n_pts, ws_n, ms_max), 1), "unit": UNIT, "n_gpus": ws_n,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
+        "interior_points_per_s": round(whole_job_rate(batch.n_res, ws_n, ms_max), 1),
+        "ms_per_step_single": {"p10": round(float(np.percentile(per_step, 10)), 4),
+                               "p50": round(float(np.percentile(per_step, 50)), 4),
+                               "p90": round(float(np.percentile(per_step, 90)), 4),
+                               "how": "one event pair around each of K further steps (this rank)"},
         "config": {"workload": w.name, "pde": "ns_steady_2d" if w.spec.pde == 1 else w.spec.pde,
                    "network": f"{'FF' + str(2 * w.spec.ff_m) + ' -> ' if w.spec.ff_m else ''}"
                               f"{len(w.spec.widths)}x{w.spec.widths[0]} tanh -> {w.spec.d_out}"
@@ -542,8 +602,17 @@ def run_ours(args, ws_n, rank, local):
             out["torch_autograd"] = tr
         except Exception as e:   # reported, not hidden
             out["torch_autograd"] = {"error": repr(e)[:300]}
+        try:
+            tr = torch_autograd_rate(w, params, B, batch, tf32=True)
+            tr["dtype"] = "f32 storage, tf32 matmuls"
+            tr["speedup"] = round(out["value"] / tr["value"], 2)
+            out["torch_autograd_tf32"] = tr
+        except Exception as e:
+            out["torch_autograd_tf32"] = {"error": repr(e)[:300]}
     if not args.no_cpu and ws_n == 1:
         out["cpu_baseline"] = oracle_sample_rate(w, params, B, batch, net=net)
+        out["cpu_baseline"]["one_core"] = oracle_one_core_rate(w.name)
+        out["cpu_baseline"]["host"] = host_description()
     return out
 
 
