@@ -278,7 +278,8 @@ def host_description():
                     model = line.split(":", 1)[1].strip()
     except OSError:
         pass
-    return {"arch": platform.machine(), "model": model, "nproc": os.cpu_count()}
+    names = {"0xd4f": "Arm Neoverse V2 (0xd4f)", "0xd40": "Arm Neoverse V1 (0xd40)"}
+    return {"arch": platform.machine(), "model": names.get(model, model), "nproc": os.cpu_count()}
 
 
 def oracle_one_core_rate(workload, n_res=2048, target_s=5.0):
