@@ -150,6 +150,16 @@ PINN_API pinn_status pinn_workspace_bytes(const pinn_handle* h, int64_t n_res, i
  * any batch.  Negative `points` is PINN_ERR_INVALID_ARG. */
 PINN_API pinn_status pinn_set_chunk_points(pinn_handle* h, int64_t points);
 
+/* Shard of a larger batch (data parallelism without a collective in the library):
+ * normalise every mean by these global point counts instead of the batch's own, so a
+ * call on one slice of the points returns that slice's share of each loss term and of
+ * the gradient.  Summing the shares over the slices (for instance an all-reduce the
+ * caller performs across ranks) gives the whole batch's loss and gradient, up to
+ * rounding.  All zero switches it off.  Negative counts are PINN_ERR_INVALID_ARG; a
+ * later call on a batch larger than the counts is PINN_ERR_INVALID_ARG, and with
+ * temporal causality on it is PINN_ERR_UNSUPPORTED (the weights need every segment). */
+PINN_API pinn_status pinn_set_global_counts(pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc);
+
 /* CUDA-graph replay (on = 1; 0 = off, the default).  With it on, pinn_loss,
  * pinn_loss_grad, pinn_loss_grad_ff and pinn_loss_grad_terms capture their whole launch
  * sequence into a CUDA graph on the first call (on a stream the handle owns) and

@@ -30,7 +30,7 @@ EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_by
            "pinn_loss_grad_terms", "pinn_loss_balance", "pinn_set_causal", "pinn_causal_weights",
            "pinn_lbfgs_create", "pinn_lbfgs_destroy", "pinn_lbfgs_reset", "pinn_lbfgs_step", "pinn_lbfgs_direction",
            "pinn_lbfgs_push_pair", "pinn_set_activation", "pinn_set_periodic", "pinn_loss_grad_ff",
-           "pinn_set_graph"]
+           "pinn_set_graph", "pinn_set_global_counts"]
 PINN_ACT_TANH, PINN_ACT_SINE = 0, 1
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 8
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
     lib.pinn_set_chunk_points.argtypes = [H, C.c_int64]
     lib.pinn_set_activation.argtypes = [H, C.c_int, C.c_double]
     lib.pinn_set_graph.argtypes = [H, C.c_int]
+    lib.pinn_set_global_counts.argtypes = [H, C.c_int64, C.c_int64, C.c_int64]
     lib.pinn_set_periodic.argtypes = [H, C.POINTER(C.c_double)]
     lib.pinn_loss_grad_ff.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
                                       C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -200,6 +201,10 @@ def pinn_causal_weights(h, d_weights, stream):
 
 def pinn_set_chunk_points(h: int, points: int):
     check(load().pinn_set_chunk_points(h, points), h)
+
+
+def pinn_set_global_counts(h: int, n_res: int, n_ic: int, n_bc: int):
+    check(load().pinn_set_global_counts(h, n_res, n_ic, n_bc), h)
 
 
 def pinn_set_graph(h: int, on: bool):

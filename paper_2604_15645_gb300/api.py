@@ -75,6 +75,10 @@ class PinnNet:
         return cls(spec.pde, spec.widths, spec.ff_m, spec.rwf, precision, device, chunk_points, value_split,
                    getattr(spec, "activation", "tanh"), getattr(spec, "omega0", 1.0))
 
+    def set_global_counts(self, n_res=0, n_ic=0, n_bc=0):
+        """Normalise the means by the whole batch's counts (this net sees one shard of it)."""
+        _lib.pinn_set_global_counts(self.h, n_res, n_ic, n_bc)
+
     def set_graph(self, on=True):
         """Replay each call from a captured CUDA graph while its arguments stay the same."""
         _lib.pinn_set_graph(self.h, on)

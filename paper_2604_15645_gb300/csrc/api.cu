@@ -509,6 +509,18 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   char* ws = (char*)d_ws;
   const int64_t N = b->n_res + b->n_ic + b->n_bc;
   PassCtx pc{b->n_res, b->n_ic, b->n_bc, true, true, nullptr};
+  if (h->global_counts) {
+    // a shard of a larger batch: every mean is over the whole batch's points
+    if (b->n_res > h->g_res || b->n_ic > h->g_ic || b->n_bc > h->g_bc) {
+      set_err(h, "batch has more points than the global counts set by pinn_set_global_counts");
+      return PINN_ERR_INVALID_ARG;
+    }
+    if (h->causal_M > 0) {
+      set_err(h, "temporal causality needs every segment's loss, not one shard's");
+      return PINN_ERR_UNSUPPORTED;
+    }
+    pc.N_res = h->g_res; pc.N_ic = h->g_ic; pc.N_bc = h->g_bc;
+  }
   if (h->causal_M > 0 && h->chunk_points > 0 && N > h->chunk_points) {
     set_err(h, "temporal causality needs all points in one pass (the weights depend on every segment)");
     return PINN_ERR_UNSUPPORTED;
@@ -576,6 +588,7 @@ pinn_status run_graphed(pinn_handle* h, int kind, const pinn_problem* prob, cons
   k.kind = kind; k.prob = *prob; k.batch = *b;
   k.params = d_params; k.ws = d_ws; k.ws_bytes = ws_bytes; k.loss = d_loss; k.grad = d_grad; k.out2 = out2;
   k.chunk_points = h->chunk_points;
+  k.global_counts = h->global_counts ? 1 : 0; k.g_res = h->g_res; k.g_ic = h->g_ic; k.g_bc = h->g_bc;
   k.causal_M = h->causal_M; k.causal_eps = h->causal_eps; k.causal_t0 = h->causal_t0; k.causal_t1 = h->causal_t1;
   k.act = h->act; k.omega0 = h->omega0;
   k.ff_B = h->ff_B; k.periodic = h->periodic ? 1 : 0;
@@ -635,6 +648,13 @@ pinn_status pinn_causal_weights(pinn_handle* h, double* d_weights, void* stream)
 pinn_status pinn_set_chunk_points(pinn_handle* h, int64_t points) {
   if (!h || points < 0) return PINN_ERR_INVALID_ARG;
   h->chunk_points = (int64_t)align_up((size_t)points, PT_ALIGN);
+  return PINN_OK;
+}
+
+pinn_status pinn_set_global_counts(pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc) {
+  if (!h || n_res < 0 || n_ic < 0 || n_bc < 0) return PINN_ERR_INVALID_ARG;
+  h->global_counts = (n_res + n_ic + n_bc) > 0;
+  h->g_res = n_res; h->g_ic = n_ic; h->g_bc = n_bc;
   return PINN_OK;
 }
 

@@ -69,6 +69,7 @@ struct pinn_graph_key {
   pinn_batch batch;
   const void* params; void* ws; size_t ws_bytes; void* loss; void* grad; void* out2;
   int64_t chunk_points;
+  int global_counts; int64_t g_res, g_ic, g_bc;
   int causal_M; double causal_eps, causal_t0, causal_t1;
   int act; float omega0;
   const float* ff_B; int periodic; double periods[3];
@@ -91,6 +92,8 @@ struct pinn_handle {
   int device = 0;
   int sm_count = 0;
   int64_t chunk_points = 0;  // 0: one pass; else points per chunk (multiple of 64)
+  bool global_counts = false; // normalise the means by these counts (a shard of a larger batch)
+  int64_t g_res = 0, g_ic = 0, g_bc = 0;
   float* d_periodic_B = nullptr;   // periodic input map: owned diag(2 pi / P) [d_in][d_in]
   bool periodic = false;     // ff_B is d_periodic_B; the input-map gradient is dL/dP
   double periods[3] = {0, 0, 0};
