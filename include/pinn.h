@@ -27,8 +27,10 @@
  *     without queuing work.  Numerical faults found on the device (a non-finite
  *     loss, or a kernel wait that ran past its bound) are latched in a device
  *     status word and reported by pinn_status_poll().
- *   - After pinn_create() no entry point allocates device memory: the caller
- *     provides the workspace (size from pinn_workspace_bytes()).
+ *   - After pinn_create() no call allocates device memory except the option
+ *     setters that say so (pinn_set_periodic keeps its matrix; with pinn_set_graph
+ *     the first call of each argument set captures and instantiates a CUDA graph):
+ *     the caller provides the workspace (size from pinn_workspace_bytes()).
  *   - A handle is not thread-safe; one handle per host thread.
  */
 #ifndef PINN_H
