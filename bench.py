@@ -194,32 +194,34 @@ def layer_dims_of(spec):
     return dims
 
 
-def algorithmic_work(w, n_pts, precision):
+def algorithmic_work(w, n_cols, n_pts, precision):
     """Algorithmic FLOPs and HBM bytes of one step, per GEMM phase.
 
-    Units: a jet column (4 per point; initial/boundary points carry zero derivative
-    rows, so 4 * points columns).  Per column and hidden GEMM layer (fan_in fi,
+    Units: a jet row of the method, 4 per interior point and 1 per initial or
+    boundary point (n_cols = 4 N_res + N_ic + N_bc); the kernels also carry three zero
+    rows for every initial/boundary point, which is layout, not algorithmic work.  The
+    BF16 value-row low halves count once per point (n_pts).  Per row and hidden GEMM layer (fan_in fi,
     fan_out fo), FLOPs are 2 fi fo for each of forward, adjoint and weight
     gradient (no adjoint into the first GEMM after a frozen Fourier embedding; the
-    tiny raw-coordinate first layer is not a GEMM).  Bytes per column and layer,
+    tiny raw-coordinate first layer is not a GEMM).  Bytes per row and layer,
     e = element size (only the activations A are stored; the adjoint is written in
     them):
       forward   read A_in (fi e) + write A_out (fo e)   [+ BF16 value-row low halves,
-                                                         fi/2 + fo/2 bytes per column]
+                                                         2 (fi + fo) bytes per point]
       adjoint   read Zbar_in (fo e) + A_in (fi e) + write Zbar_out (fi e)
       weights   read Zbar (fo e) + A_in (fi e)
     """
     spec = w.spec
     e = 2 if precision == "bf16" else 4
-    lo = 1.0 if precision == "bf16" else 0.0   # (fi + fo) * 2 bytes per point = (fi + fo) / 2 per column
-    cols = 4.0 * n_pts
+    lo = 2.0 if precision == "bf16" else 0.0   # (fi + fo) * 2 bytes per point
+    cols = float(n_cols)
     fl = {"fwd_gemm": 0.0, "dw_gemm": 0.0, "adj_gemm": 0.0}
     by = {"fwd_gemm": 0.0, "dw_gemm": 0.0, "adj_gemm": 0.0}
     for li, (fi, fo) in enumerate(layer_dims_of(spec)):
         if li == 0 and not spec.ff_m:
             continue
         fl["fwd_gemm"] += 2.0 * fi * fo * cols
-        by["fwd_gemm"] += cols * ((fi + fo) * e + lo * (fi + fo) / 2.0)
+        by["fwd_gemm"] += cols * (fi + fo) * e + n_pts * lo * (fi + fo)
         fl["dw_gemm"] += 2.0 * fi * fo * cols
         by["dw_gemm"] += cols * (fo + fi) * e
         if li >= 1:
@@ -532,7 +534,7 @@ def run_ours(args, ws_n, rank, local):
         return None
 
     peaks, peak_src = load_peaks()
-    flops, nbytes = algorithmic_work(w, n_pts, precision)
+    flops, nbytes = algorithmic_work(w, ncols, n_pts, precision)
     phases = {k: prof[k] for k in ("fwd_gemm", "dw_gemm", "adj_gemm", "out_loss", "embed", "reduce", "rwf")}
     # the dominant kernel among those with an algorithmic work model (the GEMM phases)
     modelled = [k for k in phases if k in flops and phases[k][1] > 0] or list(phases)
