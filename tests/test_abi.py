@@ -76,3 +76,18 @@ def test_invalid_width_and_null_args(lib):
     assert lib.pinn_set_periodic(None, None) == 1
     # Adam argument checks happen before any device work
     assert lib.pinn_adam_step(None, None, None, None, 10, 1, 1e-3, 0.9, 0.999, 1e-8, None) == 1
+
+
+def test_no_gpu_fails_loudly(lib):
+    """Without a usable GPU the library refuses (PINN_ERR_CUDA, no handle) and the
+    Python layer raises: there is no CPU fallback."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    spec = _lib.make_spec(0, [64, 64], 0, False)
+    h = C.c_void_p()
+    assert lib.pinn_create(C.byref(spec), C.byref(h)) == 3
+    assert not h.value
+    from paper_2604_15645_gb300 import api
+    with pytest.raises(Exception):
+        api.PinnNet(0, [64, 64], device="cpu")
