@@ -38,7 +38,7 @@ def _causal_case(name, precision, M, eps, **sizes):
 
 
 @pytest.mark.parametrize("name,precision", [("burgers1d_4x64", "fp32"), ("maxwell_te_5x512", "fp32"),
-                                            ("maxwell_te_5x512", "bf16")])
+                                            ("maxwell_te_5x512", "bf16"), ("advection1d_4x128", "tf32")])
 def test_causal_loss_and_gradient_match_oracle(cuda_lib, name, precision):
     api, w, p, B, b, cz, net, db, prob, lam = _causal_case(name, precision, 4, 0.5, n_res=900, n_ic=100, n_bc=100)
     t, g = net.loss_grad(torch.tensor(p, device="cuda"), db, prob)
@@ -83,3 +83,42 @@ def test_causal_refusals(cuda_lib):
         net.loss_grad(torch.tensor(p, device="cuda"), api.DeviceBatch.from_host(b), api.make_problem(w.problem.nu))
     with pytest.raises(_lib.PinnError):
         net.set_causal(33, 1.0)
+
+
+def test_periodic_map_with_causality_maxwell(cuda_lib):
+    """The paper's Maxwell configuration combines the strict periodic input map (Eq. 16)
+    with temporal causality (Eqs. 20-21): both on the GPU against the oracle, which
+    implements the map in the paper's column order."""
+    from paper_2604_15645_gb300 import api
+    from synth import NetSpec, Problem, init_params, make_batch
+    from synth.workloads import PDE_MAXWELL
+    P = np.array([2.0, 2.0, 1.5])
+    widths = [64, 64]
+    spec = NetSpec(PDE_MAXWELL, 3, 3, widths, ff_m=3, rwf=True)
+    p_paper = init_params(spec, 91, 0.1)
+    b = make_batch(PDE_MAXWELL, 1200, 150, 0, 92, 93)
+    cz = dict(segments=4, eps=0.002, t_index=2, t0=0.0, t1=1.0)   # weights well inside (0, 1)
+    lam = (1.0, 0.5, 1.0)
+    m = oracle.Model(PDE_MAXWELL, 3, 3, widths, 0, True, None, P)
+    rt, rg = oracle.loss_and_grad(m, p_paper, None, b, 0.0, lam, causal=cz)
+    # the library's first layer takes the map's columns in Fourier-feature order
+    order = [0, 2, 4, 1, 3, 5]
+    fin, fout = 6, widths[0]
+    p_lib = np.array(p_paper, dtype=np.float64).copy()
+    p_lib[:fin * fout] = p_lib[:fin * fout].reshape(fout, fin)[:, order].ravel()
+    net = api.PinnNet.from_spec(spec, "bf16")
+    net.set_periodic(P)
+    net.set_causal(4, 0.002, 0.0, 1.0)
+    t, g = net.loss_grad(torch.tensor(p_lib, device="cuda", dtype=torch.float32), api.DeviceBatch.from_host(b),
+                         api.make_problem(0.0, *lam))
+    torch.cuda.synchronize()
+    assert net.status_poll() == 0
+    t = t.cpu().numpy()
+    g = g.cpu().numpy().astype(np.float64)
+    g_paper = g.copy()
+    g_paper[:fin * fout] = g[:fin * fout].reshape(fout, fin)[:, np.argsort(order)].ravel()
+    assert abs(t[0] - rt["total"]) <= TOL["bf16"] * abs(rt["total"])
+    assert abs(t[1] - rt["pde"]) <= TOL["bf16"] * abs(rt["pde"])
+    assert rel(g_paper, rg) <= TOL["bf16"]
+    assert 0.01 < rt["causal_weights"][-1] < 0.99
+    assert np.allclose(net.causal_weights().cpu().numpy(), rt["causal_weights"], rtol=TOL["bf16"])
