@@ -654,3 +654,37 @@ def test_periodic_map_equals_diagonal_fourier_features(pde, d_in, d_out):
     np.testing.assert_allclose(gf, periodic_to_ff_params(gp, mf.dims, d_in), rtol=1e-11, atol=1e-14)
     dP = -2 * np.pi / P ** 2 * np.diag(tf["grad_B"])
     np.testing.assert_allclose(dP, tp["grad_periods"], rtol=1e-11)
+
+
+def test_mutation_dropped_direction_term_in_fourier_gradient_is_caught(monkeypatch):
+    """Plant a mistake in dL/dB (drop the -sin [k=e] term of the derivative rows); the
+    complex-step pin on B must see it."""
+    good = po.ff_matrix_grad_terms
+
+    def bad(X, B, abar, a1bar, a2bar):
+        # the same contraction without the [k=e] terms of the first-derivative rows
+        g = good(X, B, abar, a1bar, a2bar)
+        if a1bar is None:
+            return g
+        m = B.shape[1]
+        phi = X @ B
+        c, s = np.cos(phi), np.sin(phi)
+        for e in range(X.shape[1]):
+            g[e] -= np.sum(a1bar[e][:, :m] * (-s) + a1bar[e][:, m:] * c, axis=0)
+        return g
+    monkeypatch.setattr(po, "ff_matrix_grad_terms", bad)
+    with pytest.raises(AssertionError):
+        test_fourier_matrix_gradient_complex_step(PDE_MAXWELL, 3, 3)
+
+
+def test_mutation_period_chain_factor_is_caught(monkeypatch):
+    """Plant a mistake in dL/dP (return dL/dtheta, forgetting dtheta/dP = -theta/P);
+    the complex-step pin on P must see it."""
+    good = po.period_grad_terms
+
+    def bad(X, P, abar, a1bar, a2bar):
+        th = 2.0 * np.pi / np.asarray(P)
+        return good(X, P, abar, a1bar, a2bar) / (-th / np.asarray(P))
+    monkeypatch.setattr(po, "period_grad_terms", bad)
+    with pytest.raises(AssertionError):
+        test_period_gradient_complex_step(PDE_ADVECTION, 2, 1)
