@@ -42,6 +42,11 @@ Readings where the paper is silent or garbled (also listed in the design notes):
   * Every layer (including RWF layers) has a bias b^(l) as in Eq. 4.
   * Multi-equation / multi-component terms are sums of per-equation means.
   * tanh'(z) is evaluated as 1/cosh(z)^2 here (the GPU path uses (1-t)(1+t)).
+  * The periodic map keeps the paper's column order, cos then sin per input; a network
+    whose first layer takes [cos x1, cos x2, ..., sin x1, ...] is the same function with
+    its first-layer columns permuted.
+  * The sine activation takes omega0 as given, with no special initialisation (the
+    paper names the hyper-parameter only).
 """
 from __future__ import annotations
 
