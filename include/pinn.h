@@ -31,6 +31,9 @@
  *     setters that say so (pinn_set_periodic keeps its matrix; with pinn_set_graph
  *     the first call of each argument set captures and instantiates a CUDA graph):
  *     the caller provides the workspace (size from pinn_workspace_bytes()).
+ *     Calls that do allocate return PINN_ERR_OOM when an allocation fails.
+ *   - Every call that launches work must be made with the device the handle was
+ *     created on current; otherwise it returns PINN_ERR_INVALID_ARG.
  *   - A handle is not thread-safe; one handle per host thread.
  */
 #ifndef PINN_H
@@ -59,7 +62,8 @@ typedef enum {
   PINN_ERR_CUDA = 3,          /* a CUDA runtime/driver call failed                  */
   PINN_ERR_WORKSPACE = 4,     /* workspace smaller than pinn_workspace_bytes()      */
   PINN_ERR_NONFINITE = 5,     /* device saw a NaN/Inf loss (latched)                */
-  PINN_ERR_TIMEOUT = 6        /* a bounded device-side wait expired (latched)       */
+  PINN_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired (latched)       */
+  PINN_ERR_OOM = 7            /* a host or device allocation the call makes failed  */
 } pinn_status;
 
 typedef enum {
@@ -172,6 +176,10 @@ PINN_API pinn_status pinn_set_global_counts(pinn_handle* h, int64_t n_res, int64
  * without the graph.  Capture or instantiation failures return PINN_ERR_CUDA. */
 PINN_API pinn_status pinn_set_graph(pinn_handle* h, int on);
 
+/* *held = 1 if the handle currently holds an instantiated CUDA graph (pinn_set_graph),
+ * else 0.  An inspection hook with no counterpart in the paper. */
+PINN_API pinn_status pinn_graph_held(const pinn_handle* h, int32_t* held);
+
 /* Hidden-layer activation: PINN_ACT_TANH (the default, Eq. 5) or PINN_ACT_SINE, the
  * periodic activation sin(omega0 z) of Sec. 2.6 (Table 1), in every hidden layer.
  * A sine network keeps each hidden layer's pre-activation jets for the adjoint (one
@@ -225,18 +233,33 @@ PINN_API pinn_status pinn_loss_grad_ff(pinn_handle* h, const pinn_problem* prob,
                                        const float* d_params, void* d_ws, size_t ws_bytes, double* d_loss_terms,
                                        float* d_grad, float* d_grad_ff, void* stream);
 
-/* Loss only.  d_loss_terms receives PINN_LOSS_TERMS doubles:
+/* Loss only: the composite MSE loss of Sec. 2.3 (Eqs. 10-13) with the weights of
+ * Sec. 2.6.4 (Eq. 17), over the network of Sec. 2.2 (Eqs. 4-6) with the optional
+ * Fourier embedding (Eq. 14) and weight factorisation (Eq. 15); each residual is the
+ * PDE of `spec.pde` (Sec. 4.1-4.4, 4.8) evaluated from the input derivatives that
+ * the paper takes by autograd (Sec. 2.3).  d_loss_terms receives PINN_LOSS_TERMS
+ * doubles:
  *   [0] total = lambda_pde*L_pde + lambda_ic*L_ic + lambda_bc*L_bc
  *   [1] L_pde (sum over equations)  [2..4] L_pde per equation (unused = 0)
  *   [5] L_ic   [6] L_bc   [7] 0
- * d_params: FP32 [P].  d_ws: at least pinn_workspace_bytes(), 256-byte aligned. */
+ * d_params: FP32 [P] in the packed layout of pinn_create.  d_ws: at least
+ * pinn_workspace_bytes(), 256-byte aligned, caller-owned; its contents on entry do
+ * not matter.  d_loss_terms: FP64 device [8], overwritten.  Errors: NULL pointers,
+ * a misaligned workspace, an empty batch, masks naming missing outputs or a missing
+ * Fourier matrix are PINN_ERR_INVALID_ARG; a workspace smaller than needed is
+ * PINN_ERR_WORKSPACE; a launch failure is PINN_ERR_CUDA.  Nothing is queued on error. */
 PINN_API pinn_status pinn_loss(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch,
                       const float* d_params, void* d_ws, size_t ws_bytes,
                       double* d_loss_terms, void* stream);
 
-/* Loss and its gradient dL/dtheta, FP32 [P] in the packed layout (overwritten).
- * Reductions over points are ordered and done in FP64, so repeated calls on the
- * same inputs give bitwise identical results. */
+/* Loss (as pinn_loss) and its gradient dL/dtheta with respect to every packed
+ * parameter: the paper obtains it by differentiating the autograd input derivatives
+ * once more (Sec. 2.3, double backward); here it comes from the hand-written adjoint
+ * of the jets, then the factorisation's chain rule dV = exp(s) dW,
+ * ds_i = sum_j dW_ij W_ij (Eq. 15).  d_grad: FP32 device [P], packed like d_params,
+ * overwritten.  Reductions over points are ordered and done in FP64, so repeated
+ * calls on the same inputs give bitwise identical results.  Workspace, ownership and
+ * errors as pinn_loss; a NULL d_grad is PINN_ERR_INVALID_ARG. */
 PINN_API pinn_status pinn_loss_grad(pinn_handle* h, const pinn_problem* prob, const pinn_batch* batch,
                            const float* d_params, void* d_ws, size_t ws_bytes,
                            double* d_loss_terms, float* d_grad, void* stream);
@@ -340,6 +363,18 @@ PINN_API pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res
 PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, const void* d_A, const void* d_A2,
                                       const void* d_B, float* d_D, void* stream);
 
+/* Test hook for failure detection, with no counterpart in the paper: the kind-0 BF16
+ * self-test GEMM (d_A [M][K] row-major, d_B [K][N] tile-major, d_D [M][N] FP32;
+ * N % 256 == 0, M and K multiples of 8) launched with its MMA-issuing thread first
+ * waiting on an mbarrier that no thread ever arrives on, with every wait bounded by
+ * wait_us microseconds (1..2,000,000).  The wait expires, the kernel latches
+ * PINN_ERR_TIMEOUT in h's status word, stops its other roles, waits (bounded) for its
+ * own copies in flight, frees its tensor memory and returns; d_D is left partly or
+ * wholly unwritten.  Asynchronous on `stream`; pinn_status_poll(h) then reports
+ * PINN_ERR_TIMEOUT and clears it, and the context stays usable. */
+PINN_API pinn_status pinn_debug_wait_expiry(pinn_handle* h, int M, int N, int K, const void* d_A, const void* d_B,
+                                            float* d_D, int64_t wait_us, void* stream);
+
 /* ---- many independent networks in one training step --------------------------------
  * A pinn_multi holds one network handle per spec (uneven widths, depths and point
  * counts allowed).  pinn_multi_train_step runs, for every network, the loss and
@@ -397,8 +432,15 @@ PINN_API pinn_status pinn_tanh_selftest(int64_t n, const float* d_z, float* d_t,
  *   - A batch whose pinn_workspace_bytes() exceeds that size is rejected with
  *     PINN_ERR_WORKSPACE (message in pinn_last_error) and nothing is queued.
  *   - The call allocates nothing (no cudaMalloc/cudaFree or allocating library call).
- *     Its first call on a device, with that device current, looks up the array's
- *     address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     It always launches eagerly: a handle with pinn_set_graph on captures no graph
+ *     here (capturing and instantiating one would allocate), and the graph it may
+ *     hold for its other calls is left as it is.
+ *   - The handle's device must be current (else PINN_ERR_INVALID_ARG).  Every call
+ *     looks up the array's device address on it (cudaGetSymbolAddress, no
+ *     allocation), so a device whose context was reset gets the new address.  The
+ *     first call on a device, and the first after such a reset, makes the CUDA
+ *     runtime load the library's device code there, which reserves the array: make
+ *     that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents; every value
  *     a call reads is written earlier in the same call.  Calls whose GPU work
  *     overlaps (e.g. on two streams) race on the array. */

@@ -447,11 +447,18 @@ def loss_terms(model, theta, B, batch, nu, lambdas=(1.0, 1.0, 1.0), causal=None,
 
 def causal_segments(batch, causal):
     """Time segment of every interior point (Sec. 2.6.8): the time domain [t0, t1] is cut
-    into M equal segments; a point at time t falls in floor((t - t0) / (t1 - t0) * M),
-    clamped to 0..M-1."""
-    t = np.asarray(batch.x_res[causal["t_index"]], dtype=np.float64)
+    into M equal segments [t0 + i D, t0 + (i + 1) D), D = (t1 - t0) / M, the last one
+    closed at t1; a point at time t falls in floor((t - t0) * M / (t1 - t0)), clamped to
+    0..M-1 (points outside [t0, t1] join the end segments).
+
+    The index is an integer decided by floating point, so it is decided in the
+    precision the GPU path uses for it: the FP32 time, FP32 t0, the FP32-rounded factor
+    M / (t1 - t0), and FP32 rounding after the subtraction and after the product."""
+    t = np.asarray(batch.x_res[causal["t_index"]], dtype=np.float32)
     M = causal["segments"]
-    seg = np.floor((t - causal["t0"]) / (causal["t1"] - causal["t0"]) * M).astype(np.int64)
+    t0 = np.float32(causal["t0"])
+    tinv = np.float32(M / (float(causal["t1"]) - float(causal["t0"])))
+    seg = np.floor((t - t0) * tinv).astype(np.int64)
     return np.clip(seg, 0, M - 1)
 
 

@@ -17,7 +17,7 @@ PINN_BURGERS_1D, PINN_NS_STEADY_2D, PINN_MAXWELL_TE_2D, PINN_ADVECTION_1D, PINN_
 PINN_FLAG_CUDA_CORES, PINN_FLAG_BF16_VALUE_SPLIT = 1, 4
 PRECISIONS = {"fp32": PINN_FP32, "tf32": PINN_TF32, "bf16": PINN_BF16}
 STATUS = {0: "PINN_OK", 1: "PINN_ERR_INVALID_ARG", 2: "PINN_ERR_UNSUPPORTED", 3: "PINN_ERR_CUDA",
-          4: "PINN_ERR_WORKSPACE", 5: "PINN_ERR_NONFINITE", 6: "PINN_ERR_TIMEOUT"}
+          4: "PINN_ERR_WORKSPACE", 5: "PINN_ERR_NONFINITE", 6: "PINN_ERR_TIMEOUT", 7: "PINN_ERR_OOM"}
 
 # Every symbol declared in include/pinn.h (checked by the CPU tests).
 EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_bytes", "pinn_set_ff_matrix",
@@ -30,7 +30,7 @@ EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_by
            "pinn_loss_grad_terms", "pinn_loss_balance", "pinn_set_causal", "pinn_causal_weights",
            "pinn_lbfgs_create", "pinn_lbfgs_destroy", "pinn_lbfgs_reset", "pinn_lbfgs_step", "pinn_lbfgs_direction",
            "pinn_lbfgs_push_pair", "pinn_set_activation", "pinn_set_periodic", "pinn_loss_grad_ff",
-           "pinn_set_graph", "pinn_set_global_counts"]
+           "pinn_set_graph", "pinn_set_global_counts", "pinn_graph_held", "pinn_debug_wait_expiry"]
 PINN_ACT_TANH, PINN_ACT_SINE = 0, 1
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 8
@@ -114,6 +114,9 @@ def load(path: str = LIB_PATH):
     lib.pinn_set_chunk_points.argtypes = [H, C.c_int64]
     lib.pinn_set_activation.argtypes = [H, C.c_int, C.c_double]
     lib.pinn_set_graph.argtypes = [H, C.c_int]
+    lib.pinn_graph_held.argtypes = [H, C.POINTER(C.c_int32)]
+    lib.pinn_debug_wait_expiry.argtypes = [H, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_int64, C.c_void_p]
     lib.pinn_set_global_counts.argtypes = [H, C.c_int64, C.c_int64, C.c_int64]
     lib.pinn_set_periodic.argtypes = [H, C.POINTER(C.c_double)]
     lib.pinn_loss_grad_ff.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
@@ -209,6 +212,16 @@ def pinn_set_global_counts(h: int, n_res: int, n_ic: int, n_bc: int):
 
 def pinn_set_graph(h: int, on: bool):
     check(load().pinn_set_graph(h, 1 if on else 0), h)
+
+
+def pinn_graph_held(h: int) -> bool:
+    held = C.c_int32()
+    check(load().pinn_graph_held(h, C.byref(held)), h)
+    return bool(held.value)
+
+
+def pinn_debug_wait_expiry(h, M, N, K, d_A, d_B, d_D, wait_us, stream):
+    check(load().pinn_debug_wait_expiry(h, M, N, K, d_A, d_B, d_D, wait_us, stream), h)
 
 
 def pinn_set_activation(h: int, act: int, omega0: float):

@@ -502,6 +502,16 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
     set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG;
   }
   if (reinterpret_cast<uintptr_t>(d_ws) % 256) { set_err(h, "workspace must be 256-byte aligned"); return PINN_ERR_INVALID_ARG; }
+  {
+    // every buffer the handle owns (status word, scratch) lives on the device it was
+    // created on; kernels launched with another device current could not reach them
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device) {
+      cudaGetLastError();
+      set_err(h, "the current device (%d) is not the device the handle was created on (%d)", dev, h->device);
+      return PINN_ERR_INVALID_ARG;
+    }
+  }
   pinn_status s = validate_batch(h, b);
   if (s) return s;
   if (h->spec.ff_m && !h->ff_B) { set_err(h, "Fourier-feature matrix not set (pinn_set_ff_matrix)"); return PINN_ERR_INVALID_ARG; }
@@ -623,6 +633,15 @@ pinn_status run_graphed(pinn_handle* h, int kind, const pinn_problem* prob, cons
 
 }  // namespace
 
+namespace pinn {
+
+pinn_status loss_grad_eager(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
+                            void* d_ws, size_t ws_bytes, double* d_loss, float* d_grad, void* stream) {
+  return run_kind(h, 1, prob, b, d_params, d_ws, ws_bytes, d_loss, d_grad, nullptr, stream);
+}
+
+}  // namespace pinn
+
 extern "C" {
 
 pinn_status pinn_set_causal(pinn_handle* h, int segments, double eps, double t0, double t1) {
@@ -669,6 +688,12 @@ pinn_status pinn_set_graph(pinn_handle* h, int on) {
   return PINN_OK;
 }
 
+pinn_status pinn_graph_held(const pinn_handle* h, int32_t* held) {
+  if (!h || !held) return PINN_ERR_INVALID_ARG;
+  *held = h->graph_exec ? 1 : 0;
+  return PINN_OK;
+}
+
 pinn_status pinn_set_activation(pinn_handle* h, int act, double omega0) {
   if (!h) return PINN_ERR_INVALID_ARG;
   if (act != PINN_ACT_TANH && act != PINN_ACT_SINE) { set_err(h, "unknown activation %d", act); return PINN_ERR_INVALID_ARG; }
@@ -693,7 +718,7 @@ pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
   if (spec->flags & ~(PINN_FLAG_CUDA_CORES | PINN_FLAG_BF16_VALUE_SPLIT))
     return PINN_ERR_INVALID_ARG;
   pinn_handle* h = new (std::nothrow) pinn_handle();
-  if (!h) return PINN_ERR_INVALID_ARG;
+  if (!h) return PINN_ERR_OOM;
   h->spec = *spec;
   h->L = spec->n_hidden;
   h->d_in = pde_din(spec->pde);
@@ -715,14 +740,17 @@ pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
     prev = fout;
   }
   h->P = off;
-  if (cudaGetDevice(&h->device) != cudaSuccess ||
-      cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
-      cudaMalloc(&h->d_status, 256) != cudaSuccess || cudaMemset(h->d_status, 0, 256) != cudaSuccess ||
-      cudaMalloc(&h->d_scratch, 4096) != cudaSuccess) {
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_status, 256);
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, 256);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, 4096);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
     if (h->d_status) cudaFree(h->d_status);
     if (h->d_scratch) cudaFree(h->d_scratch);
     delete h;
-    return PINN_ERR_CUDA;
+    return e == cudaErrorMemoryAllocation ? PINN_ERR_OOM : PINN_ERR_CUDA;
   }
   tc_init(h);
   *out = h;
@@ -793,7 +821,9 @@ pinn_status pinn_set_periodic(pinn_handle* h, const double* periods) {
     if (!(periods[k] > 0.0) || !std::isfinite(periods[k])) { set_err(h, "periods must be finite and > 0"); return PINN_ERR_INVALID_ARG; }
   const int d = h->d_in;
   if (!h->d_periodic_B) {
-    pinn_status s = cuda_check(h, cudaMalloc(&h->d_periodic_B, (size_t)d * d * sizeof(float)), "periodic map alloc");
+    const cudaError_t e = cudaMalloc(&h->d_periodic_B, (size_t)d * d * sizeof(float));
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); set_err(h, "periodic map alloc: out of memory"); return PINN_ERR_OOM; }
+    pinn_status s = cuda_check(h, e, "periodic map alloc");
     if (s) return s;
   }
   float Bh[9] = {0.f};
@@ -914,6 +944,7 @@ const char* pinn_status_string(pinn_status s) {
     case PINN_ERR_WORKSPACE: return "PINN_ERR_WORKSPACE";
     case PINN_ERR_NONFINITE: return "PINN_ERR_NONFINITE";
     case PINN_ERR_TIMEOUT: return "PINN_ERR_TIMEOUT";
+    case PINN_ERR_OOM: return "PINN_ERR_OOM";
   }
   return "PINN_ERR_UNKNOWN";
 }

@@ -269,4 +269,9 @@ void launch_to_point_major(const void* src, void* dst, int w, int64_t NC, cudaSt
 void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
                  float bc1, float bc2, cudaStream_t st);
 
+// pinn_loss_grad without CUDA-graph capture or replay, whatever pinn_set_graph says
+// (the launch sequence only; it allocates nothing).
+pinn_status loss_grad_eager(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
+                            void* d_ws, size_t ws_bytes, double* d_loss, float* d_grad, void* stream);
+
 }  // namespace pinn

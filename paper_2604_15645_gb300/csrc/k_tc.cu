@@ -45,7 +45,7 @@ namespace {
 constexpr int BM = 128;          // accumulator rows (TMEM lanes)
 constexpr int BN = 256;          // accumulator columns per buffer
 constexpr int EPI_WARPS = 8;     // two warps per TMEM lane quadrant, each on 32 of a tile's 64 points
-constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
+constexpr uint64_t WAIT_NS = 2000000000ull;   // default bound on any single wait: 2 s
 
 enum TcMode { TC_FWD = 0, TC_ADJ = 1, TC_DW = 2, TC_STORE = 3 };
 
@@ -77,16 +77,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false when another role aborted or the bound expired (then the
-// abort flag and the device status word are set).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+// Bounded wait: false when another role aborted or the bound (limit_ns) expired
+// (then the abort flag and the device status word are set).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                          uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   for (uint32_t spin = 1;; ++spin) {
     if (mbar_try(bar, parity)) return true;
     if ((spin & 63) == 0) {
       if (*abort_flag) return false;
-      if (gtimer() - t0 > WAIT_NS) {
+      if (gtimer() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicOr(status, 2);
         return false;
@@ -212,6 +213,8 @@ struct TcParams {
   float* out32;        // dW partials / selftest output
   int* status;
   int wlo_values_only; // forward: W_lo . B on the 64 value columns only (PINN_FLAG_BF16_VALUE_SPLIT)
+  uint64_t wait_ns;    // bound on every mbarrier wait (WAIT_NS)
+  int stall;           // test hook: the MMA issuer first waits on a barrier nothing arrives on
 };
 
 template <bool TF32, int MODE, bool SPLIT>
@@ -267,7 +270,8 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* lo_full = acc_empty + 2;                  // converter -> MMA: B_lo ready
   uint64_t* lo_empty = lo_full + 1;                   // MMA -> converter: B_lo consumed
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(lo_empty + 1);
+  uint64_t* never = lo_empty + 1;                     // test hook (p.stall): no thread arrives on it
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(never + 1);
   volatile int* inflight = abort_flag + 1;             // [STAGES]: parity+1 of an armed, unconsumed stage
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int*>(inflight + C::STAGES));
 
@@ -284,6 +288,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
     }
     mbar_init(lo_full, 1);
     mbar_init(lo_empty, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
         int mb, nb, k0, k1;
         coords(t, mb, nb, k0, k1);
         for (int kb = k0; kb < k1; ++kb) {
-          if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, p.status)) break;
+          if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, p.status, p.wait_ns)) break;
           uint8_t* sa = smem + stage * C::STAGE;
           uint8_t* sa2 = sa + C::A_BYTES;
           uint8_t* sb = sa + C::A_BYTES * (SPLIT ? 2 : 1);
@@ -364,16 +369,19 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
       int stage = 0;
       uint32_t phase = 0, lo_phase = 0;
       int local = 0;
-      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++local) {
+      // test hook: a dependency that is never satisfied, so the bounded wait expires and
+      // the whole CTA takes the abort path (status bit 1, teardown below)
+      const bool stalled = p.stall && !mbar_wait(never, 0, abort_flag, p.status, p.wait_ns);
+      for (int t = blockIdx.x; t < total && !*abort_flag && !stalled; t += gridDim.x, ++local) {
         int mb, nb, k0, k1;
         coords(t, mb, nb, k0, k1);
         const int buf = local & 1;
-        if (!mbar_wait(&acc_empty[buf], ((local >> 1) & 1) ^ 1, abort_flag, p.status)) break;
+        if (!mbar_wait(&acc_empty[buf], ((local >> 1) & 1) ^ 1, abort_flag, p.status, p.wait_ns)) break;
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
         bool ok = true;
         for (int kb = k0; kb < k1; ++kb) {
-          if (!mbar_wait(&full[stage], phase, abort_flag, p.status)) { ok = false; break; }
+          if (!mbar_wait(&full[stage], phase, abort_flag, p.status, p.wait_ns)) { ok = false; break; }
           inflight[stage] = 0;
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + stage * C::STAGE);
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
           }
           if (C::KPM) {
             // TF32: D += W_hi . B_lo once the converters have written B_lo
-            if (!mbar_wait(lo_full, lo_phase, abort_flag, p.status)) { ok = false; break; }
+            if (!mbar_wait(lo_full, lo_phase, abort_flag, p.status, p.wait_ns)) { ok = false; break; }
             tc_fence_after();
             const uint32_t sbl = smem_u32(blo);
 #pragma unroll
@@ -426,8 +434,8 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
       coords(t, mb, nb, k0, k1);
       bool ok = true;
       for (int kb = k0; kb < k1; ++kb) {
-        if (!mbar_wait(&full[stage], phase, abort_flag, p.status) ||
-            !mbar_wait(lo_empty, lo_phase ^ 1, abort_flag, p.status)) { ok = false; break; }
+        if (!mbar_wait(&full[stage], phase, abort_flag, p.status, p.wait_ns) ||
+            !mbar_wait(lo_empty, lo_phase ^ 1, abort_flag, p.status, p.wait_ns)) { ok = false; break; }
         const float4* src = reinterpret_cast<const float4*>(smem + stage * C::STAGE + C::A_BYTES * (SPLIT ? 2 : 1));
         float4* dst = reinterpret_cast<float4*>(blo);
         // latency-bound: keep 16 shared-memory loads in flight per thread
@@ -497,7 +505,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
       int mb, nb, k0, k1;
       coords(t, mb, nb, k0, k1);
       const int buf = local & 1;
-      if (!mbar_wait(&acc_full[buf], (local >> 1) & 1, abort_flag, p.status)) break;
+      if (!mbar_wait(&acc_full[buf], (local >> 1) & 1, abort_flag, p.status, p.wait_ns)) break;
       tc_fence_after();
       const int m = mb * BM + row;
       const bool mvalid = m < p.M;
@@ -763,6 +771,8 @@ TcParams base_params(int M, int N, int K, int64_t NC, int kblock, int* status) {
   p.k_iters = (K + kblock - 1) / kblock;
   p.nsplit = 1; p.kps = p.k_iters;
   p.status = status;
+  p.wait_ns = WAIT_NS;
+  p.stall = 0;
   return p;
 }
 
@@ -866,7 +876,8 @@ pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout
 namespace {
 template <bool TF32>
 pinn_status selftest_impl(pinn_handle* h, int layout, int M, int N, int K, const void* d_A, const void* d_A2,
-                          const void* d_B, float* d_D, int* status, cudaStream_t st) {
+                          const void* d_B, float* d_D, int* status, cudaStream_t st, uint64_t wait_ns = 0,
+                          int stall = 0) {
   using namespace pinn;
   CUtensorMap ma, ma2, mb;
   if (layout == 0) {
@@ -877,6 +888,8 @@ pinn_status selftest_impl(pinn_handle* h, int layout, int M, int N, int K, const
       return PINN_ERR_CUDA;
     TcParams p = base_params(M, N, K, N, C::BKE, status);
     p.out32 = d_D;
+    if (wait_ns) p.wait_ns = wait_ns;
+    p.stall = stall;
     const int grid = grid_for(h, p.m_tiles * p.n_tiles);
     if (d_A2) return launch<TF32, TC_STORE, true>(h, ma, ma2, mb, mb, p, grid, st);
     return launch<TF32, TC_STORE, false>(h, ma, ma, mb, mb, p, grid, st);
@@ -923,4 +936,18 @@ extern "C" PINN_API pinn_status pinn_tc_selftest(int kind, int M, int N, int K, 
   }
   cudaFree(status);
   return r;
+}
+
+extern "C" PINN_API pinn_status pinn_debug_wait_expiry(pinn_handle* h, int M, int N, int K, const void* d_A,
+                                                       const void* d_B, float* d_D, int64_t wait_us, void* stream) {
+  using namespace pinn;
+  if (!h || !d_A || !d_B || !d_D || M < 1 || N < 1 || K < 1 || wait_us < 1 || wait_us > 2000000)
+    return PINN_ERR_INVALID_ARG;
+  if (K % 8 || M % 8 || N % TILE_COLS) return PINN_ERR_INVALID_ARG;
+  if (!g_encode) return PINN_ERR_UNSUPPORTED;
+  // the kind-0 BF16 GEMM with its MMA issuer waiting first on a barrier that nothing
+  // arrives on: the wait expires after wait_us, and the kernel latches the timeout in
+  // the handle's status word and returns through its abort path
+  return selftest_impl<false>(h, 0, M, N, K, d_A, nullptr, d_B, d_D, h->d_status, (cudaStream_t)stream,
+                              (uint64_t)wait_us * 1000ull, 1);
 }

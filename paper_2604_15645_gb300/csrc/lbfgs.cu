@@ -168,7 +168,7 @@ pinn_status pinn_lbfgs_create(pinn_handle* h, int history, pinn_lbfgs** out) {
   if (!h || !out || history < 1 || history > 64) return PINN_ERR_INVALID_ARG;
   *out = nullptr;
   pinn_lbfgs* lb = new (std::nothrow) pinn_lbfgs();
-  if (!lb) return PINN_ERR_INVALID_ARG;
+  if (!lb) return PINN_ERR_OOM;
   lb->h = h;
   lb->m = history;
   lb->P = h->P;
@@ -182,8 +182,9 @@ pinn_status pinn_lbfgs_create(pinn_handle* h, int history, pinn_lbfgs** out) {
             cudaMalloc(&lb->sc, sizeof(double) * 16) == cudaSuccess &&
             cudaMalloc(&lb->part, sizeof(double) * DOT_BLOCKS) == cudaSuccess;
   if (!ok) {
+    const bool oom = cudaGetLastError() == cudaErrorMemoryAllocation;
     pinn_lbfgs_destroy(lb);
-    return PINN_ERR_CUDA;
+    return oom ? PINN_ERR_OOM : PINN_ERR_CUDA;
   }
   *out = lb;
   return PINN_OK;

@@ -147,7 +147,7 @@ PINN_API pinn_status pinn_multi_create(const pinn_spec* specs, int32_t n_nets, p
   if (!specs || !out || n_nets < 1 || n_nets > 4096) return PINN_ERR_INVALID_ARG;
   *out = nullptr;
   pinn_multi* m = new (std::nothrow) pinn_multi();
-  if (!m) return PINN_ERR_INVALID_ARG;
+  if (!m) return PINN_ERR_OOM;
   m->n = n_nets;
   m->poff.assign(n_nets + 1, 0);
   for (int i = 0; i < n_nets; ++i) {

@@ -19,34 +19,24 @@
 //     Every value the computation reads is written earlier in the same call, so
 //     nothing needs clearing between calls.  Calls whose GPU work overlaps (for
 //     example on two streams) race on the array and give undefined results.
-//   - The first call on each device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current); make that first call before
-//     any stream capture.
+//   - The launch sequence always runs eagerly, even on a handle with
+//     pinn_set_graph on: capturing and instantiating a graph would allocate.
+//   - In host code g_static_ws names a host-side stand-in, not device memory, so
+//     every call asks the runtime for the array's device address with the handle's
+//     device current (cudaGetSymbolAddress).  The lookup allocates nothing; asking
+//     on every call keeps the address right after the device's context has been
+//     reset and the library's device code loaded again.  The first call on a device
+//     (and the first after such a reset) makes the runtime load that code, which
+//     reserves the array: make it before any stream capture.
 #include <cstdio>
-#include <mutex>
 
 #include "internal.h"
 
 namespace {
 
 constexpr size_t kStaticWsBytes = PINN_STATIC_WS_BYTES;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_ws[kStaticWsBytes];
-
-void* g_ws_addr[kMaxDevices] = {};
-std::mutex g_ws_mutex;
-
-pinn_status static_ws_address(int device, void** out) {
-  std::lock_guard<std::mutex> lock(g_ws_mutex);
-  if (!g_ws_addr[device]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_ws) != cudaSuccess || !p) return PINN_ERR_CUDA;
-    g_ws_addr[device] = p;
-  }
-  *out = g_ws_addr[device];
-  return PINN_OK;
-}
 
 }  // namespace
 
@@ -63,15 +53,21 @@ extern "C" pinn_status pinn_loss_grad_static(pinn_handle* h, const pinn_problem*
              need, kStaticWsBytes);
     return PINN_ERR_WORKSPACE;
   }
-  int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) {
-    snprintf(h->err, sizeof(h->err), "pinn_loss_grad_static: no usable current device");
-    return PINN_ERR_CUDA;
+  int device = -1;
+  if (cudaGetDevice(&device) != cudaSuccess || device != h->device) {
+    cudaGetLastError();
+    snprintf(h->err, sizeof(h->err),
+             "pinn_loss_grad_static: the current device (%d) is not the device the handle was created on (%d)",
+             device, h->device);
+    return PINN_ERR_INVALID_ARG;
   }
   void* ws = nullptr;
-  if (static_ws_address(device, &ws) != PINN_OK) {
-    snprintf(h->err, sizeof(h->err), "pinn_loss_grad_static: cudaGetSymbolAddress of the static workspace failed");
+  const cudaError_t e = cudaGetSymbolAddress(&ws, g_static_ws);
+  if (e != cudaSuccess || !ws) {
+    cudaGetLastError();
+    snprintf(h->err, sizeof(h->err), "pinn_loss_grad_static: cudaGetSymbolAddress of the static workspace: %s",
+             cudaGetErrorString(e));
     return PINN_ERR_CUDA;
   }
-  return pinn_loss_grad(h, prob, batch, d_params, ws, kStaticWsBytes, d_loss_terms, d_grad, stream);
+  return pinn::loss_grad_eager(h, prob, batch, d_params, ws, kStaticWsBytes, d_loss_terms, d_grad, stream);
 }

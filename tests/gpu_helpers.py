@@ -6,6 +6,8 @@ import torch
 import oracle
 from paper_2604_15645_gb300 import api
 
+from parity_blocks import check_blocks, report
+
 TOL = {"fp32": 1e-5, "tf32": 1e-3, "bf16": 2e-2}
 
 
@@ -77,7 +79,10 @@ def _pack(t):
     return out
 
 
-def assert_parity(gpu_terms, gpu_grad, ref_terms, ref_grad, tol, what=""):
+def assert_parity(gpu_terms, gpu_grad, ref_terms, ref_grad, tol, what="", spec=None):
+    """Loss terms element by element; the gradient as a whole (relative L2) and, given
+    the network's spec, block by block (every layer's V, s and b; see parity_blocks).
+    The per-block errors and norms are printed (shown with pytest -s)."""
     for i in (0, 1, 2, 3, 4, 5, 6):
         if abs(ref_terms[i]) > 0:
             e = abs(gpu_terms[i] - ref_terms[i]) / abs(ref_terms[i])
@@ -87,3 +92,6 @@ def assert_parity(gpu_terms, gpu_grad, ref_terms, ref_grad, tol, what=""):
     if gpu_grad is not None:
         e = rel(gpu_grad, ref_grad)
         assert e <= tol, f"{what} gradient rel L2 err {e:.3e} > {tol}"
+        if spec is not None:
+            rows = check_blocks(gpu_grad, ref_grad, spec, tol, what)
+            print(f"{what}: gradient rel L2 {e:.3e}; per block:\n{report(rows)}")

@@ -37,7 +37,7 @@ def test_chunked_cavity_matches_oracle_and_one_pass(cuda_lib, precision):
     (t1, g1), _ = _run(w, p, B, b, precision)
     (tc, gc), _ = _run(w, p, B, b, precision, chunk=256)
     rt, rg = run_oracle(w.spec, p, B, b, w.problem)
-    assert_parity(tc, gc, rt, rg, TOL[precision], f"chunked cavity {precision}")
+    assert_parity(tc, gc, rt, rg, TOL[precision], f"chunked cavity {precision}", spec=w.spec)
     assert rel(tc[:7], t1[:7]) < 1e-6 and rel(gc, g1) < 1e-6
 
 
@@ -47,7 +47,7 @@ def test_chunked_maxwell_sets_straddle_chunks(cuda_lib):
     w, p, B, b = make_workload("maxwell_te_5x512", n_res=600, n_ic=100, n_bc=150, random_bias=0.1)
     (tc, gc), _ = _run(w, p, B, b, "fp32", chunk=192)
     rt, rg = run_oracle(w.spec, p, B, b, w.problem)
-    assert_parity(tc, gc, rt, rg, TOL["fp32"], "chunked maxwell")
+    assert_parity(tc, gc, rt, rg, TOL["fp32"], "chunked maxwell", spec=w.spec)
 
 
 def test_chunked_loss_only(cuda_lib):

@@ -42,7 +42,7 @@ def test_fourier_matrix_gradient(cuda_lib, name, precision):
     m = oracle.Model.from_spec(w.spec)
     lam = (w.problem.lambda_pde, w.problem.lambda_ic, w.problem.lambda_bc)
     rt, rg = oracle.loss_and_grad(m, p, B, b, w.problem.nu, lam, input_grad=True)
-    assert_parity(gt, gg, _pack(rt), rg, TOL[precision], f"{name} {precision}")
+    assert_parity(gt, gg, _pack(rt), rg, TOL[precision], f"{name} {precision}", spec=w.spec)
     e = rel(gB.reshape(B.shape), rt["grad_B"])
     assert e <= TOL[precision], f"dL/dB rel err {e:.3e}"
 
@@ -77,7 +77,7 @@ def test_periodic_map_and_period_gradient(cuda_lib, pde, widths, P, nu, precisio
     gt, gg, gP = _gpu(spec, p_lib, b, problem, precision, periods=P)
     inv = np.argsort(order)
     assert_parity(gt, _permute_first_layer(gg, fin, fout, inv), _pack(rt), rg, TOL[precision],
-                  f"periodic pde {pde} {precision}")
+                  f"periodic pde {pde} {precision}", spec=spec)
     e = rel(gP, rt["grad_periods"])
     assert e <= TOL[precision], f"dL/dP rel err {e:.3e}: {gP} vs {rt['grad_periods']}"
 

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 def _check(spec, params, B, batch, problem, precision, what, chunk=None):
     gt, gg = run_gpu(spec, params, B, batch, problem, precision)
     rt, rg = run_oracle(spec, params, B, batch, problem, chunk=chunk)
-    assert_parity(gt, gg, rt, rg, TOL[precision], what)
+    assert_parity(gt, gg, rt, rg, TOL[precision], what, spec=spec)
     return gt, gg, rt, rg
 
 
@@ -32,7 +32,7 @@ def test_cavity_value_split_ragged_subset(cuda_lib):
     w, p, B, b = make_workload("ns_cavity_6x256", n_res=1000, n_bc=300, random_bias=0.1)
     gt, gg = run_gpu(w.spec, p, B, b, w.problem, "bf16", value_split=True)
     rt, rg = run_oracle(w.spec, p, B, b, w.problem)
-    assert_parity(gt, gg, rt, rg, TOL["bf16"], "cavity bf16 value split")
+    assert_parity(gt, gg, rt, rg, TOL["bf16"], "cavity bf16 value split", spec=w.spec)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
@@ -212,4 +212,4 @@ def test_cavity_full_size_against_chunked_oracle(cuda_lib, precision, value_spli
     if "ref" not in _FULL_ORACLE:
         _FULL_ORACLE["ref"] = run_oracle(w.spec, p, B, b, w.problem, chunk=8192)
     rt, rg = _FULL_ORACLE["ref"]
-    assert_parity(gt, gg, rt, rg, TOL[precision], f"cavity full {precision}")
+    assert_parity(gt, gg, rt, rg, TOL[precision], f"cavity full {precision}", spec=w.spec)

@@ -19,7 +19,7 @@ def test_new_residuals_match_oracle(cuda_lib, name, precision):
     w, p, B, b = make_workload(name, n_res=1000, n_ic=120, n_bc=90, random_bias=0.1)
     gt, gg = run_gpu(w.spec, p, B, b, w.problem, precision)
     rt, rg = run_oracle(w.spec, p, B, b, w.problem)
-    assert_parity(gt, gg, rt, rg, TOL[precision], f"{name} {precision}")
+    assert_parity(gt, gg, rt, rg, TOL[precision], f"{name} {precision}", spec=w.spec)
 
 
 def _causal_case(name, precision, M, eps, **sizes):

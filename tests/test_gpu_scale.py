@@ -19,7 +19,7 @@ def test_maxwell_low_discrepancy_subset_bf16(cuda_lib):
     w, p, B, b = make_workload("maxwell_te_5x512", n_res=16384, n_ic=1024, n_bc=1024)
     gt, gg = run_gpu(w.spec, p, B, b, w.problem, "bf16")
     rt, rg = run_oracle(w.spec, p, B, b, w.problem, chunk=4096)
-    assert_parity(gt, gg, rt, rg, TOL["bf16"], "maxwell 16k bf16")
+    assert_parity(gt, gg, rt, rg, TOL["bf16"], "maxwell 16k bf16", spec=w.spec)
 
 
 @pytest.mark.parametrize("value_split", [False, True])
@@ -27,7 +27,8 @@ def test_cavity_at_scale_architecture_subset_bf16(cuda_lib, value_split):
     w, p, B, b = make_workload("ns_cavity_8x512", n_res=4096, n_bc=256)
     gt, gg = run_gpu(w.spec, p, B, b, w.problem, "bf16", value_split=value_split)
     rt, rg = run_oracle(w.spec, p, B, b, w.problem, chunk=2048)
-    assert_parity(gt, gg, rt, rg, TOL["bf16"], f"cavity 8x512 subset bf16 value_split={value_split}")
+    assert_parity(gt, gg, rt, rg, TOL["bf16"], f"cavity 8x512 subset bf16 value_split={value_split}",
+                  spec=w.spec)
 
 
 def _free():

@@ -27,7 +27,8 @@ def test_sine_burgers_raw_inputs(cuda_lib, precision):
     gt, gg = run_gpu(w.spec, p, B, b, w.problem, precision)
     rt, rg = run_oracle(w.spec, p, B, b, w.problem)
     # TF32 with sine computes in FP32 on CUDA cores
-    assert_parity(gt, gg, rt, rg, TOL["fp32" if precision == "tf32" else precision], f"sine burgers {precision}")
+    assert_parity(gt, gg, rt, rg, TOL["fp32" if precision == "tf32" else precision], f"sine burgers {precision}",
+                  spec=w.spec)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
@@ -38,7 +39,7 @@ def test_sine_cavity_fourier_rwf_ragged(cuda_lib, precision):
     p = init_params(w.spec, 6, 0.1)
     gt, gg = run_gpu(w.spec, p, B, b, w.problem, precision)
     rt, rg = run_oracle(w.spec, p, B, b, w.problem)
-    assert_parity(gt, gg, rt, rg, TOL[precision], f"sine cavity {precision}")
+    assert_parity(gt, gg, rt, rg, TOL[precision], f"sine cavity {precision}", spec=w.spec)
 
 
 @pytest.mark.parametrize("omega0", [1.5, 3.0])
@@ -51,7 +52,8 @@ def test_sine_maxwell_first_order_rows(cuda_lib, omega0):
     p = init_params(w.spec, 7, 0.1)
     gt, gg = run_gpu(w.spec, p, B, b, w.problem, "fp32")
     rt, rg = run_oracle(w.spec, p, B, b, w.problem)
-    assert_parity(gt, gg, rt, rg, TOL["fp32"] * max(1.0, omega0 / 2.0), f"sine maxwell omega0={omega0}")
+    assert_parity(gt, gg, rt, rg, TOL["fp32"] * max(1.0, omega0 / 2.0), f"sine maxwell omega0={omega0}",
+                  spec=w.spec)
 
 
 def test_sine_advection_single_neuron_solution(cuda_lib):

@@ -42,7 +42,7 @@ def test_multi_step_matches_oracle_per_network(cuda_lib, precision):
     off = multi.offsets
     for i, (spec, p, b, pr) in enumerate(fam):
         rt, rg = run_oracle(spec, p, None, b, pr)
-        assert_parity(L[i], g[off[i]:off[i + 1]], rt, rg, TOL[precision], f"net {i} {spec.widths}")
+        assert_parity(L[i], g[off[i]:off[i + 1]], rt, rg, TOL[precision], f"net {i} {spec.widths}", spec=spec)
     b1, b2, lr, eps = (float(np.float32(x)) for x in (0.9, 0.999, 1e-3, 1e-8))
     th, _, _ = oracle.adam_step(p0.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, lr, b1, b2, eps)
     assert rel(params.cpu().numpy(), th) < 1e-6
@@ -91,4 +91,5 @@ def test_multi_autotune_cache(cuda_lib, tmp_path):
     torch.cuda.synchronize()
     spec, p, b, pr = fam[0]
     rt, rg = run_oracle(spec, p, None, b, pr)
-    assert_parity(loss[0].cpu().numpy(), grad[:multi.offsets[1]].cpu().numpy(), rt, rg, TOL["bf16"], "tuned net 0")
+    assert_parity(loss[0].cpu().numpy(), grad[:multi.offsets[1]].cpu().numpy(), rt, rg, TOL["bf16"], "tuned net 0",
+                  spec=spec)

@@ -415,6 +415,30 @@ def test_causal_loss_reduces_to_segment_mean():
     assert t4["pde"] == pytest.approx(np.mean([np.mean(r[seg == i] ** 2) for i in range(4)]), rel=1e-13)
 
 
+@pytest.mark.parametrize("t0,t1,M,cases", [
+    # (t, segment) pairs written out by hand from the definition: segment i is
+    # [t0 + i D, t0 + (i + 1) D) with D = (t1 - t0) / M, the last one closed at t1, and
+    # times outside [t0, t1] join the first or last segment
+    (0.0, 1.0, 4, [(0.0, 0), (0.125, 0), (0.2490234375, 0), (0.25, 1), (0.5, 2), (0.625, 2), (0.75, 3),
+                   (0.9990234375, 3), (1.0, 3), (-0.5, 0), (-1e-7, 0), (1.5, 3), (1.0000001, 3)]),
+    (-1.0, 1.0, 8, [(-1.0, 0), (-0.75, 1), (-0.5, 2), (-0.25, 3), (0.0, 4), (0.25, 5), (0.5, 6), (0.75, 7),
+                    (1.0, 7), (-0.7509765625, 0), (0.7490234375, 6), (-3.0, 0), (2.0, 7)]),
+    (0.0, 1.5, 3, [(0.0, 0), (0.4990234375, 0), (0.5, 1), (1.0, 2), (0.9990234375, 1), (1.5, 2), (1.75, 2)]),
+    (0.5, 1.0, 1, [(0.5, 0), (0.75, 0), (1.0, 0), (0.0, 0), (2.0, 0)]),
+])
+def test_causal_segments_hand_placed_times(t0, t1, M, cases):
+    """Sec. 2.6.8 cuts the time domain into M equal segments.  Times on t0, on t1, exactly
+    on every segment edge (which belongs to the segment above it), just below an edge,
+    and outside [t0, t1]: every index is written out by hand, none from the oracle."""
+    from synth import Batch
+    t = np.array([c[0] for c in cases], dtype=np.float32)
+    x_res = np.stack([np.zeros_like(t), t])                  # (x, t): time is input 1
+    empty = np.zeros((2, 0), np.float32)
+    b = Batch(x_res, empty, np.zeros((1, 0), np.float32), 0, empty, np.zeros((1, 0), np.float32), 0)
+    seg = oracle.causal_segments(b, dict(segments=M, eps=1.0, t_index=1, t0=t0, t1=t1))
+    assert seg.tolist() == [c[1] for c in cases]
+
+
 @pytest.mark.parametrize("name", ["burgers1d_4x64", "maxwell_te_5x512"])
 def test_causal_gradient_complex_step_with_frozen_weights(name):
     """The gradient holds omega fixed: complex-step on the loss with omega frozen at

@@ -5,8 +5,17 @@ workspace it uses a 64 MiB scratch array compiled into the library.  Its results
 must match pinn_loss_grad (caller-provided workspace) within the parity tolerance,
 on two calls in a row, and it must refuse batches that do not fit the array.
 
+It always launches eagerly: on a handle with CUDA-graph replay switched on it
+captures no graph (capturing and instantiating one would allocate).  And it must
+find its array again after the device's context has been reset (tests/c_static_reset.c,
+a plain-C caller, since a reset would also pull device memory out from under torch).
+
 This file is collected last on purpose, so a stop-at-first-failure run has already
 run every other test if it fails."""
+import os
+import shutil
+import subprocess
+
 import numpy as np
 import pytest
 import torch
@@ -66,3 +75,38 @@ def test_static_entry_rejects_batches_beyond_its_array(cuda_lib):
     assert e.value.status == 4 and "static array" in str(e.value)
     torch.cuda.synchronize()
     assert float(grad.abs().sum()) == 0.0      # nothing was queued
+
+
+def test_static_entry_captures_no_graph(cuda_lib):
+    from paper_2604_15645_gb300 import _lib, api
+    w, p, B, b = make_workload("ns_cavity_6x256", n_res=300, n_bc=64, random_bias=0.1)
+    net = api.PinnNet.from_spec(w.spec, "bf16")
+    net.set_ff_matrix(B)
+    net.set_graph(True)
+    db = api.DeviceBatch.from_host(b)
+    prob = api.make_problem(w.problem.nu)
+    params = torch.tensor(p, device="cuda")
+    loss_s = torch.zeros(8, dtype=torch.float64, device="cuda")
+    grad_s = torch.zeros_like(params)
+    _static_call(net, prob, db, params, loss_s, grad_s)
+    torch.cuda.synchronize()
+    assert not _lib.pinn_graph_held(net.h)          # graph mode on, yet nothing captured
+    loss_w, grad_w = net.loss_grad(params, db, prob, out=torch.empty_like(loss_s))
+    torch.cuda.synchronize()
+    assert _lib.pinn_graph_held(net.h)              # the workspace entry point did capture
+    _static_call(net, prob, db, params, loss_s, grad_s)
+    torch.cuda.synchronize()
+    assert _lib.pinn_graph_held(net.h) and net.status_poll() == 0
+    assert rel(grad_s.cpu().numpy(), grad_w.cpu().numpy()) <= 1e-6
+    assert rel(loss_s.cpu().numpy()[:7], loss_w.cpu().numpy()[:7]) <= 1e-12
+
+
+def test_static_entry_survives_a_device_reset(cuda_lib, tmp_path):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    pkg = os.path.join(root, "paper_2604_15645_gb300")
+    exe = str(tmp_path / "c_static_reset")
+    subprocess.run([nvcc, "-O2", os.path.join(root, "tests", "c_static_reset.c"), "-I", os.path.join(root, "include"),
+                    "-L", pkg, "-lpinn", "-Xlinker", "-rpath", "-Xlinker", pkg, "-o", exe], check=True, timeout=300)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
