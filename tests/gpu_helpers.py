@@ -79,10 +79,11 @@ def _pack(t):
     return out
 
 
-def assert_parity(gpu_terms, gpu_grad, ref_terms, ref_grad, tol, what="", spec=None):
+def assert_parity(gpu_terms, gpu_grad, ref_terms, ref_grad, tol, what="", spec=None, block_tol=None):
     """Loss terms element by element; the gradient as a whole (relative L2) and, given
-    the network's spec, block by block (every layer's V, s and b; see parity_blocks).
-    The per-block errors and norms are printed (shown with pytest -s)."""
+    the network's spec, block by block (every layer's V, s and b; see parity_blocks) at
+    `block_tol` (default: tol).  The per-block errors and norms are printed (shown with
+    pytest -s or -rP)."""
     for i in (0, 1, 2, 3, 4, 5, 6):
         if abs(ref_terms[i]) > 0:
             e = abs(gpu_terms[i] - ref_terms[i]) / abs(ref_terms[i])
@@ -93,5 +94,5 @@ def assert_parity(gpu_terms, gpu_grad, ref_terms, ref_grad, tol, what="", spec=N
         e = rel(gpu_grad, ref_grad)
         assert e <= tol, f"{what} gradient rel L2 err {e:.3e} > {tol}"
         if spec is not None:
-            rows = check_blocks(gpu_grad, ref_grad, spec, tol, what)
+            rows = check_blocks(gpu_grad, ref_grad, spec, tol if block_tol is None else block_tol, what)
             print(f"{what}: gradient rel L2 {e:.3e}; per block:\n{report(rows)}")

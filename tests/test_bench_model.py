@@ -17,7 +17,19 @@ def test_jet_gemm_flops_per_step(name, expected):
     from synth import make_workload
     w, _, _, b = make_workload(name)
     rows = 4 * b.n_res + b.n_ic + b.n_bc
-    fl, by = bench.algorithmic_work(w, rows, b.n_res + b.n_ic + b.n_bc, "bf16")
+    fl, by, sch = bench.algorithmic_work(w, rows, b.n_res + b.n_ic + b.n_bc, "bf16")
     assert sum(fl.values()) == pytest.approx(expected, rel=5e-3)
     # bytes: every phase moves at least its activations once
     assert all(v > 0 for v in by.values())
+    # the BF16 scheme's value-row low halves are reported apart from the method's bytes
+    assert sch["fwd_gemm"] > 0 and sch["adj_gemm"] == 0 and sch["dw_gemm"] == 0
+
+
+def test_block_layout_matches_parameter_count():
+    import bench
+    from synth import make_workload, param_count
+    for name in ("burgers1d_4x64", "ns_cavity_6x256", "maxwell_te_5x512"):
+        w = make_workload(name, n_res=8)[0]
+        blocks = bench._blocks(w.spec)
+        assert blocks[0][1] == 0 and blocks[-1][2] == param_count(w.spec)
+        assert all(a[2] == b[1] for a, b in zip(blocks, blocks[1:]))

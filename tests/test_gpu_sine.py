@@ -45,15 +45,18 @@ def test_sine_cavity_fourier_rwf_ragged(cuda_lib, precision):
 @pytest.mark.parametrize("omega0", [1.5, 3.0])
 def test_sine_maxwell_first_order_rows(cuda_lib, omega0):
     # Rounding of each pre-activation enters sin(omega0 z) multiplied by omega0, so the
-    # FP32 bound grows with it: 1e-5 up to omega0 = 2, then in proportion.
+    # FP32 bound grows with it: 1e-5 up to omega0 = 2, then in proportion.  Per block,
+    # the layers nearest the input take that factor once more: their gradient is the
+    # adjoint carried back through the sine layers, whose rounding is amplified alike.
     w, p, B, b = make_workload("maxwell_te_5x512", n_res=600, n_ic=100, n_bc=150, random_bias=0.1)
     w.spec.widths = [96, 80, 96]
     _sine(w.spec, omega0)
     p = init_params(w.spec, 7, 0.1)
     gt, gg = run_gpu(w.spec, p, B, b, w.problem, "fp32")
     rt, rg = run_oracle(w.spec, p, B, b, w.problem)
-    assert_parity(gt, gg, rt, rg, TOL["fp32"] * max(1.0, omega0 / 2.0), f"sine maxwell omega0={omega0}",
-                  spec=w.spec)
+    amp = max(1.0, omega0 / 2.0)
+    assert_parity(gt, gg, rt, rg, TOL["fp32"] * amp, f"sine maxwell omega0={omega0}", spec=w.spec,
+                  block_tol=TOL["fp32"] * amp * amp)
 
 
 def test_sine_advection_single_neuron_solution(cuda_lib):
