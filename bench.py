@@ -197,7 +197,7 @@ def layer_dims_of(spec):
     return dims
 
 
-def algorithmic_work(w, n_cols, n_pts, precision):
+def algorithmic_work(w, n_cols, n_pts, precision, engines=None):
     """Algorithmic FLOPs and HBM bytes of one step, per GEMM phase.
 
     Units: a jet row of the method, 4 per interior point and 1 per initial or
@@ -211,6 +211,9 @@ def algorithmic_work(w, n_cols, n_pts, precision):
       forward   read A_in (fi e) + write A_out (fo e)
       adjoint   read Zbar_in (fo e) + A_in (fi e) + write Zbar_out (fi e)
       weights   read Zbar (fo e) + A_in (fi e)
+    A layer whose adjoint and weight gradient run as one fused kernel (engines[li] == 2)
+    books both GEMMs' FLOPs under "adjdw_gemm", with the adjoint's bytes (the weight
+    gradient reads the same two arrays in the same pass).
     Returns (flops, bytes, scheme_bytes): scheme_bytes are the extra bytes of this
     library's BF16 precision scheme (the low halves of the value rows, 2 (fi + fo)
     bytes per point in the forward), which are not the method's work.
@@ -219,15 +222,18 @@ def algorithmic_work(w, n_cols, n_pts, precision):
     e = 2 if precision == "bf16" else 4
     lo = 2.0 if precision == "bf16" else 0.0
     cols = float(n_cols)
-    fl = {"fwd_gemm": 0.0, "dw_gemm": 0.0, "adj_gemm": 0.0}
-    by = {"fwd_gemm": 0.0, "dw_gemm": 0.0, "adj_gemm": 0.0}
-    sch = {"fwd_gemm": 0.0, "dw_gemm": 0.0, "adj_gemm": 0.0}
+    keys = ("fwd_gemm", "dw_gemm", "adj_gemm", "adjdw_gemm")
+    fl, by, sch = ({k: 0.0 for k in keys} for _ in range(3))
     for li, (fi, fo) in enumerate(layer_dims_of(spec)):
         if li == 0 and not spec.ff_m:
             continue
         fl["fwd_gemm"] += 2.0 * fi * fo * cols
         by["fwd_gemm"] += cols * (fi + fo) * e
         sch["fwd_gemm"] += n_pts * lo * (fi + fo)
+        if li >= 1 and engines is not None and engines[li] == 2:
+            fl["adjdw_gemm"] += 4.0 * fi * fo * cols
+            by["adjdw_gemm"] += cols * (fo + 2 * fi) * e
+            continue
         fl["dw_gemm"] += 2.0 * fi * fo * cols
         by["dw_gemm"] += cols * (fo + fi) * e
         if li >= 1:
@@ -658,8 +664,10 @@ def measure(name, precision, value_split, steps, warmup, ws_n, rank, local, grap
         return None, ctx
 
     peaks, peak_src = load_peaks()
-    flops, nbytes, scheme = algorithmic_work(w, ncols, n_pts, precision)
-    phases = {k: prof[k] for k in ("fwd_gemm", "dw_gemm", "adj_gemm", "out_loss", "embed", "reduce", "rwf")}
+    engines = net.layer_engines(*db.sizes)
+    flops, nbytes, scheme = algorithmic_work(w, ncols, n_pts, precision, engines)
+    phases = {k: prof[k] for k in ("fwd_gemm", "dw_gemm", "adj_gemm", "adjdw_gemm", "out_loss", "embed", "reduce",
+                                   "rwf")}
     # the dominant kernel among those with an algorithmic work model (the GEMM phases)
     modelled = [k for k in phases if k in flops and phases[k][1] > 0] or list(phases)
     dom = max(modelled, key=lambda k: phases[k][0])
@@ -679,6 +687,8 @@ def measure(name, precision, value_split, steps, warmup, ws_n, rank, local, grap
                    "launch": "one CUDA graph per step" if graph else "eager launches",
                    "phase_timing": "CUDA events per launch group in an eager pass of the same K steps",
                    "bf16_weight_split": ("value rows" if value_split else "all rows") if precision == "bf16" else None,
+                   "layer_engines": "".join("ctf"[x] for x in engines) + " (c CUDA cores, t tensor cores, "
+                                    "f tensor cores with fused adjoint + weight gradient)",
                    "l2": f"working set {ws_bytes / 1e9:.2f} GB per step > 129 MB L2 (no flush needed)"},
         "gpu_launches": int(sum(v[1] for v in prof.values() if v[1] > 0)),
         "phases_ms_per_step": {k: round(v[0] / steps, 4) for k, v in prof.items()},
@@ -789,7 +799,7 @@ def jet_gemm_rate(flops, prof, steps, peaks, precision):
     """All jet GEMMs of the step together (forward, adjoint, weight gradient):
     algorithmic FLOPs over their summed device time, against the burst and the
     sustained peak of the precision's engine."""
-    ms = sum(prof[k][0] for k in ("fwd_gemm", "adj_gemm", "dw_gemm")) / steps
+    ms = sum(prof[k][0] for k in ("fwd_gemm", "adj_gemm", "dw_gemm", "adjdw_gemm")) / steps
     if ms <= 0:
         return None
     tf = sum(flops.values()) / (ms / 1e3) / 1e12

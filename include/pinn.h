@@ -333,9 +333,10 @@ PINN_API const char* pinn_status_string(pinn_status s);
  * with CUDA events on the caller's stream (no synchronisation inside the call).
  * Phases: 0 RWF weights, 1 input embedding / first layer, 2 forward jet GEMMs,
  * 3 output layer + residual + loss, 4 weight-gradient GEMMs, 5 adjoint GEMMs,
- * 6 reductions and finalisation, 7 other.  At most 16384 event pairs are kept
- * between reads; later ones are dropped (and counted in launches as -1). */
-#define PINN_PROF_PHASES 8
+ * 6 reductions and finalisation, 7 other, 8 fused adjoint + weight-gradient GEMMs
+ * (pinn_layer_engines, engine 2).  At most 16384 event pairs are kept between reads;
+ * later ones are dropped (and counted in launches of the last phase as -1). */
+#define PINN_PROF_PHASES 9
 PINN_API pinn_status pinn_set_profiling(pinn_handle* h, int enable);
 
 /* Synchronise on the recorded events, then return per phase the summed GPU time
@@ -347,6 +348,13 @@ PINN_API pinn_status pinn_profile_read(pinn_handle* h, double* ms, int64_t* laun
  * of these sizes (the rest run on CUDA cores), written to *n. */
 PINN_API pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc,
                                              int32_t* n);
+
+/* The engine of every hidden layer's jet GEMMs for a batch of these sizes, written to
+ * engines[0..L-1]: 0 CUDA cores; 1 tensor cores (separate forward, adjoint and
+ * weight-gradient kernels); 2 tensor cores with the layer's adjoint and weight
+ * gradient fused into one kernel (BF16, fan-out <= 256, every layer but the first). */
+PINN_API pinn_status pinn_layer_engines(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc,
+                                        int32_t* engines);
 
 /* Self-test of the tensor-core GEMM core (no PINN arithmetic): FP32 output, all
  * device pointers.  "Tile-major" is the library's jet-matrix layout: a logical

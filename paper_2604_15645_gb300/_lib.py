@@ -30,11 +30,12 @@ EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_by
            "pinn_loss_grad_terms", "pinn_loss_balance", "pinn_set_causal", "pinn_causal_weights",
            "pinn_lbfgs_create", "pinn_lbfgs_destroy", "pinn_lbfgs_reset", "pinn_lbfgs_step", "pinn_lbfgs_direction",
            "pinn_lbfgs_push_pair", "pinn_set_activation", "pinn_set_periodic", "pinn_loss_grad_ff",
-           "pinn_set_graph", "pinn_set_global_counts", "pinn_graph_held", "pinn_debug_wait_expiry"]
+           "pinn_set_graph", "pinn_set_global_counts", "pinn_graph_held", "pinn_debug_wait_expiry",
+           "pinn_layer_engines"]
 PINN_ACT_TANH, PINN_ACT_SINE = 0, 1
 PINN_STATIC_WS_BYTES = 64 << 20
-PINN_PROF_PHASES = 8
-PHASE_NAMES = ["rwf", "embed", "fwd_gemm", "out_loss", "dw_gemm", "adj_gemm", "reduce", "other"]
+PINN_PROF_PHASES = 9
+PHASE_NAMES = ["rwf", "embed", "fwd_gemm", "out_loss", "dw_gemm", "adj_gemm", "reduce", "other", "adjdw_gemm"]
 
 
 class pinn_spec(C.Structure):
@@ -110,6 +111,7 @@ def load(path: str = LIB_PATH):
     lib.pinn_tc_selftest.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p]
     lib.pinn_tensor_core_layers.argtypes = [H, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int32)]
+    lib.pinn_layer_engines.argtypes = [H, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int32)]
     lib.pinn_profile_read.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     lib.pinn_set_chunk_points.argtypes = [H, C.c_int64]
     lib.pinn_set_activation.argtypes = [H, C.c_int, C.c_double]
@@ -279,6 +281,14 @@ def pinn_tensor_core_layers(h, n_res, n_ic, n_bc) -> int:
     n = C.c_int32()
     check(load().pinn_tensor_core_layers(h, n_res, n_ic, n_bc, C.byref(n)), h)
     return n.value
+
+
+def pinn_layer_engines(h, n_hidden, n_res, n_ic, n_bc):
+    """Per hidden layer: 0 CUDA cores, 1 tensor cores, 2 tensor cores with the fused
+    adjoint + weight-gradient kernel."""
+    out = (C.c_int32 * n_hidden)()
+    check(load().pinn_layer_engines(h, n_res, n_ic, n_bc, out), h)
+    return list(out)
 
 
 def pinn_tc_selftest(kind, M, N, K, d_A, d_A2, d_B, d_D, stream):

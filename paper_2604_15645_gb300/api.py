@@ -188,6 +188,11 @@ class PinnNet:
         _lib.pinn_causal_weights(self.h, w.data_ptr(), _stream())
         return w
 
+    def layer_engines(self, n_res, n_ic, n_bc):
+        """Per hidden layer: 0 CUDA cores, 1 tensor cores, 2 tensor cores with the fused
+        adjoint + weight-gradient kernel."""
+        return _lib.pinn_layer_engines(self.h, self.spec.n_hidden, n_res, n_ic, n_bc)
+
     def tensor_core_layers(self, n_res, n_ic, n_bc):
         return _lib.pinn_tensor_core_layers(self.h, n_res, n_ic, n_bc)
 

@@ -31,7 +31,8 @@ pinn_status cuda_check(pinn_handle* h, cudaError_t e, const char* what) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 constexpr int PROF_MAX = 16384;
-enum Phase { PH_RWF = 0, PH_EMBED = 1, PH_FWD = 2, PH_OUT = 3, PH_DW = 4, PH_ADJ = 5, PH_RED = 6, PH_OTHER = 7 };
+enum Phase { PH_RWF = 0, PH_EMBED = 1, PH_FWD = 2, PH_OUT = 3, PH_DW = 4, PH_ADJ = 5, PH_RED = 6, PH_OTHER = 7,
+             PH_ADJDW = 8 };
 
 // Brackets one launch group with a pair of CUDA events when profiling is on.
 struct PhaseScope {
@@ -105,6 +106,7 @@ struct CallPlan {
   Plan p;
   LayerPlan lay[PINN_MAX_HIDDEN + 1];
   bool tc[PINN_MAX_HIDDEN + 1];      // layer li runs its jet GEMMs on tensor cores
+  bool fused[PINN_MAX_HIDDEN + 1];   // layer li's adjoint and weight gradient run as one fused kernel
   bool fused_db[PINN_MAX_HIDDEN + 1];  // layer li's bias partials come from a fused adjoint epilogue
   bool out_db = false;                 // the last hidden layer's bias partials come from the output/loss kernel
   int nbpart[PINN_MAX_HIDDEN + 1];     // bias partial count of layer li
@@ -129,6 +131,7 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
     for (int li = 0; li < L1; ++li) c->tc[li] = c->tc[li] && all;
     c->pm = all && h->first_gemm < h->L;
   }
+  for (int li = 0; li < L1; ++li) c->fused[li] = c->tc[li] && tc_adjdw_supported(h, li, c->p.NC);
   for (int li = 0; li < L1; ++li) {
     LayerPlan lp = h->layers[li];
     const bool raw = (li == 0 && !h->spec.ff_m);
@@ -141,6 +144,8 @@ pinn_status plan_call(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
       lp.nsplit = 0;
     } else if (li == h->L) {
       lp.nsplit = c->p.nloss_blocks;   // output layer: one dW partial per output/loss block
+    } else if (c->fused[li]) {
+      lp.nsplit = tc_adjdw_splits(h, lp.fin, c->p.NC);   // one partial per fused-kernel CTA and m-tile
     } else if (c->tc[li]) {
       lp.nsplit = tc_dw_splits(h, lp.fout, lp.fin, c->p.NC);
     } else {
@@ -360,7 +365,7 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     const LayerPlan& lp = cp.lay[li];
     void* zb = ws + p.Zbar[(li + 1) % 2];
     const bool raw = (li == 0 && !h->spec.ff_m);
-    if (!raw) {
+    if (!raw && !cp.fused[li]) {   // (a fused layer's weight gradient comes with its adjoint below)
       PhaseScope ps(h, st, PH_DW, 1);
       if (cp.tc[li]) {
         s = tc_gemm_dw(h, zb, ws + p.A[li], lp.fout, lp.fin, p.NC, lp.nsplit, reinterpret_cast<float*>(ws + lp.dwpart), st);
@@ -401,8 +406,12 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
         e.x_res = b->x_res; e.x_ic = b->x_ic; e.x_bc = b->x_bc;
         e.n_res = p.n_res; e.n_ic = p.n_ic; e.n_bc = p.n_bc;
       }
-      PhaseScope ps(h, st, PH_ADJ, 1);
-      if (cp.tc[li] && cp.pm) {
+      PhaseScope ps(h, st, cp.fused[li] ? PH_ADJDW : PH_ADJ, 1);
+      if (cp.fused[li]) {
+        s = tc_gemm_adjdw(h, ws + lp.wtc, zb, ws + p.A[li], lp.fin, lp.fout, p.NC, e,
+                          reinterpret_cast<float*>(ws + lp.dwpart), lp.nsplit, st);
+        if (s) return s;
+      } else if (cp.tc[li] && cp.pm) {
         e.out_pm = (li - 1 >= 1) ? ws + cp.zbpm[li % 2] : nullptr;
         s = tc_gemm_adj(h, ws + lp.wtc, ws + lp.wtlo, ws + cp.zbpm[(li + 1) % 2], lp.fin, lp.fout, p.NC, e, st);
         if (s) return s;
@@ -800,6 +809,14 @@ pinn_status pinn_tensor_core_layers(const pinn_handle* h, int64_t n_res, int64_t
   int32_t c = 0;
   for (int li = 0; li < h->L; ++li) c += cp.tc[li] ? 1 : 0;
   *n = c;
+  return PINN_OK;
+}
+
+pinn_status pinn_layer_engines(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t n_bc, int32_t* engines) {
+  if (!h || !engines || n_res < 0 || n_ic < 0 || n_bc < 0) return PINN_ERR_INVALID_ARG;
+  CallPlan cp;
+  plan_call(h, n_res, n_ic, n_bc, &cp);
+  for (int li = 0; li < h->L; ++li) engines[li] = cp.fused[li] ? 2 : cp.tc[li] ? 1 : 0;
   return PINN_OK;
 }
 

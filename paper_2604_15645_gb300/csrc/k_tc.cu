@@ -869,6 +869,379 @@ pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout
   return dw_impl<false>(h, Zbar, A, fout, fin, NC, nsplit, part, st);
 }
 
+// ==== fused adjoint + weight gradient (BF16, fan-out <= 256) ==========================
+//
+// For a hidden layer whose adjoint and weight gradient both run on tensor cores, the
+// two GEMMs read the same two arrays for the same column tile: Zbar_l^T [fout][NC]
+// and A_{l-1}^T [fin][NC].  One persistent kernel does both per work unit (fin
+// m-tile mb, column tile nb):
+//   adjoint  Abar^T[mb rows][256 cols] = W^T[mb rows][fout] . Zbar^T[fout][256 cols]
+//            (MN-major B), then the activation-form tanh-jet adjoint in the epilogue
+//   weights  dW^T[mb rows][fout] += A_{l-1}^T[mb rows][256 cols] . Zbar^T[fout][256 cols]^T
+//            (both K-major over the columns), accumulated in tensor memory across all
+//            of the CTA's column tiles and written once as its split partial.
+// Every CTA keeps one m-tile (the grid is a multiple of the m-tile count), so its dW
+// slab stays in tensor memory: 256 columns for the adjoint accumulator (single
+// buffer; the epilogue copies it to registers and releases it at once) plus up to
+// 256 for dW^T.  The A_{l-1} tile is staged by TMA in shared memory (two buffers)
+// and serves both the dW MMAs and the epilogue, which reads it from there instead of
+// global memory.  Zbar is read once from HBM per column tile (the m-tile CTAs of a
+// column tile run side by side, the second read hits L2), A once, Zbar_{l-1} written
+// once: the separate weight-gradient pass and its re-reads are gone.
+//
+// Warp roles (352 threads): 0 stage producer (W^T chunk + Zbar chunk), 1 TMEM
+// allocator + MMA issuer, 2-9 epilogue, 10 A-tile producer.
+namespace {
+
+constexpr int FZ_EPI = EPI_WARPS;
+constexpr int FZ_NT = 64 + 32 * FZ_EPI + 32;
+constexpr int FZ_WB = BM * 128;                  // W^T chunk [128 fin][64 fout]       16 KB
+constexpr int FZ_BOX = 64 * 128;                 // Zbar box [64 fout][64 cols]         8 KB
+constexpr int FZ_ZB = 4 * FZ_BOX;                // Zbar chunk [64 fout][256 cols]     32 KB
+constexpr int FZ_STAGE = FZ_WB + FZ_ZB;          // 48 KB
+constexpr int FZ_STAGES = 2;
+constexpr int FZ_ABOX = BM * 128;                // A box [128 fin][64 cols]           16 KB
+constexpr int FZ_AT = 4 * FZ_ABOX;               // A_{l-1} tile [128 fin][256 cols]   64 KB
+constexpr int FZ_ABUF = 2;
+constexpr size_t FZ_SMEM = (size_t)FZ_STAGES * FZ_STAGE + (size_t)FZ_ABUF * FZ_AT + 1024 + 256;
+static_assert(FZ_SMEM <= 227 * 1024, "fused adjoint: shared memory budget");
+constexpr int FZ_DW_COL = BN;                    // dW^T accumulator: TMEM columns 256..511
+
+__global__ void __launch_bounds__(FZ_NT, 1)
+    k_tc_adjdw(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapZ,
+               const __grid_constant__ CUtensorMap mapA, const TcParams p) {
+  using T = __nv_bfloat16;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* abase = smem + FZ_STAGES * FZ_STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(abase + FZ_ABUF * FZ_AT);
+  uint64_t* empty = full + FZ_STAGES;
+  uint64_t* acc_full = empty + FZ_STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* a_full = acc_empty + 1;
+  uint64_t* a_empty = a_full + FZ_ABUF;
+  uint64_t* dw_full = a_empty + FZ_ABUF;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(dw_full + 1);
+  volatile int* inflight = abort_flag + 1;              // [FZ_STAGES]
+  volatile int* a_inflight = inflight + FZ_STAGES;      // [FZ_ABUF]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int*>(a_inflight + FZ_ABUF));
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < FZ_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      inflight[s] = 0;
+    }
+    for (int b = 0; b < FZ_ABUF; ++b) {
+      mbar_init(&a_full[b], 1);
+      mbar_init(&a_empty[b], 1 + 32 * FZ_EPI);   // the dW MMAs' commit + every epilogue thread
+      a_inflight[b] = 0;
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 32 * FZ_EPI);
+    mbar_init(dw_full, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int total = p.m_tiles * p.n_tiles;
+  auto coords = [&](int t, int& mb, int& nb) {
+    if (p.e.reverse) t = total - 1 - t;
+    mb = t % p.m_tiles;
+    nb = t / p.m_tiles;
+  };
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- stage producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+        int mb, nb;
+        coords(t, mb, nb);
+        for (int kb = 0; kb < p.k_iters; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, p.status, p.wait_ns)) break;
+          uint8_t* sw = smem + stage * FZ_STAGE;
+          uint8_t* sz = sw + FZ_WB;
+          mbar_expect_tx(&full[stage], FZ_STAGE);
+          inflight[stage] = (int)phase + 1;
+          tma_load_2d(sw, &mapW, &full[stage], kb * 64, mb * BM);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) tma_load_3d(sz + j * FZ_BOX, &mapZ, &full[stage], j * 64, kb * 64, nb);
+          if (++stage == FZ_STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+    }
+  } else if (warp == 2 + FZ_EPI) {
+    // ---------------------------------------------------------------- A-tile producer
+    if (lane == 0) {
+      int local = 0;
+      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++local) {
+        int mb, nb;
+        coords(t, mb, nb);
+        const int ab = local & 1;
+        const uint32_t aph = (uint32_t)(local >> 1) & 1;
+        if (!mbar_wait(&a_empty[ab], aph ^ 1, abort_flag, p.status, p.wait_ns)) break;
+        mbar_expect_tx(&a_full[ab], FZ_AT);
+        a_inflight[ab] = (int)aph + 1;
+        uint8_t* at = abase + ab * FZ_AT;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tma_load_3d(at + j * FZ_ABOX, &mapA, &a_full[ab], j * 64, mb * BM, nb);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc_adj = make_idesc(1u, 1u, BN);   // W^T . Zbar, B MN-major, N = 256
+      constexpr uint32_t idesc_dw = make_idesc(1u, 0u, 64);    // A_{l-1} . Zbar chunk^T, both K-major, N = 64
+      const uint32_t d_adj = tmem_base;
+      const uint32_t d_dw = tmem_base + FZ_DW_COL;
+      int stage = 0;
+      uint32_t phase = 0;
+      int local = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && !*abort_flag && ok; t += gridDim.x, ++local) {
+        const int ab = local & 1;
+        if (!mbar_wait(&a_full[ab], (uint32_t)(local >> 1) & 1, abort_flag, p.status, p.wait_ns)) { ok = false; break; }
+        a_inflight[ab] = 0;
+        tc_fence_after();
+        const uint32_t sa_t = smem_u32(abase + ab * FZ_AT);
+        for (int kb = 0; kb < p.k_iters; ++kb) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, p.status, p.wait_ns)) { ok = false; break; }
+          inflight[stage] = 0;
+          tc_fence_after();
+          const uint32_t sw = smem_u32(smem + stage * FZ_STAGE);
+          const uint32_t sz = sw + FZ_WB;
+          // weight gradient of this 64-row fout chunk: dW^T[:, 64 kb ..] += A_tile . Zbar_chunk^T
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              tc_mma<false>(d_dw + 64 * kb, make_desc(sa_t + j * FZ_ABOX + kk * 32, 16, 1024),
+                            make_desc(sz + j * FZ_BOX + kk * 32, 16, 1024), idesc_dw,
+                            (local > 0 || j > 0 || kk > 0) ? 1u : 0u);
+          if (kb == 0) {
+            // the single adjoint accumulator: wait until the epilogue has copied out the last tile
+            if (!mbar_wait(acc_empty, ((uint32_t)local & 1) ^ 1, abort_flag, p.status, p.wait_ns)) { ok = false; break; }
+            tc_fence_after();
+          }
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            tc_mma<false>(d_adj, make_desc(sw + kk * 32, 16, 1024), make_desc(sz + kk * 16 * 128, FZ_BOX, 1024),
+                          idesc_adj, (kb > 0 || kk > 0) ? 1u : 0u);
+          tc_commit(&empty[stage]);
+          if (++stage == FZ_STAGES) { stage = 0; phase ^= 1; }
+        }
+        if (!ok) break;
+        tc_commit(&a_empty[ab]);
+        tc_commit(acc_full);
+      }
+      if (ok && !*abort_flag) tc_commit(dw_full);
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    constexpr int PARTS = FZ_EPI / 4;
+    constexpr int UPTS = 16;
+    constexpr int UNITS = TILE_PTS / (UPTS * PARTS);   // 2
+    const int quad = warp & 3;
+    const int part = (warp - 2) >> 2;
+    const int rr = quad * 32 + lane;                    // accumulator row = feature within the m-tile
+    auto unit_col = [&](int u) { return part * (UNITS * UPTS) + UPTS * u; };
+    const uint32_t tq = tmem_base + ((uint32_t)(quad * 32) << 16);
+    int local = 0;
+    int mb_cta = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+      int mb, nb;
+      coords(t, mb, nb);
+      mb_cta = mb;
+      if (!mbar_wait(acc_full, (uint32_t)local & 1, abort_flag, p.status, p.wait_ns)) break;
+      tc_fence_after();
+      float v[UNITS][4][UPTS];
+#pragma unroll
+      for (int u = 0; u < UNITS; ++u)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) tmem_ld16_issue(tq + unit_col(u) + 64 * r, v[u][r]);
+      tmem_wait_ld();
+      tc_fence_before();
+      mbar_arrive(acc_empty);            // the next tile's adjoint MMAs may overwrite it now
+      const int ab = local & 1;
+      if (!mbar_wait(&a_full[ab], (uint32_t)(local >> 1) & 1, abort_flag, p.status, p.wait_ns)) break;
+      const uint8_t* at = abase + ab * FZ_AT;
+      const int m = mb * BM + rr;
+      const bool mvalid = m < p.M;
+      float db[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < UNITS; ++u) {
+        const int pc = unit_col(u);
+#pragma unroll
+        for (int h8 = 0; h8 < UPTS / 8; ++h8) {
+          // A_{l-1} of 8 points x 4 jet rows from the swizzled tile: row rr of box r,
+          // 16-byte chunk (pc + 8 h8) / 8 XOR (rr mod 8)
+          uint32_t aw[4][4];
+          const int chunk = ((pc + 8 * h8) >> 3) ^ (rr & 7);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const uint32_t addr = smem_u32(at + r * FZ_ABOX + rr * 128 + chunk * 16);
+            asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(aw[r][0]), "=r"(aw[r][1]), "=r"(aw[r][2]), "=r"(aw[r][3])
+                         : "r"(addr));
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            float av[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) av[r] = raw_elem<T>(aw[r], i);
+            float abr[4] = {v[u][0][8 * h8 + i], v[u][1][8 * h8 + i], v[u][2][8 * h8 + i], v[u][3][8 * h8 + i]};
+            float zb[4];
+            jet_adj_a(av, abr, zb, p.e.jet_mode);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) v[u][r][8 * h8 + i] = zb[r];
+          }
+        }
+        if (mvalid) {
+          const int64_t cbase = toff(m, (int64_t)nb * BN, p.M) + pc;
+          T* zbo = reinterpret_cast<T*>(p.e.out) + cbase;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) st_row(zbo + 64 * r, v[u][r]);
+          if (p.e.dbpart) {
+#pragma unroll
+            for (int i = 0; i < UPTS; ++i) db[0] += v[u][0][i];
+            if (p.e.dterms) {
+              const int64_t p0 = (int64_t)nb * TILE_PTS + pc;
+              const int nd = (p.e.jet_mode == JET_MAXWELL) ? 3 : 2;
+#pragma unroll
+              for (int i = 0; i < UPTS; ++i) {
+                const int64_t pp = p0 + i;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                  if (j >= p.e.dterms) break;
+                  float x = point_coord(p.e.x_res, p.e.x_ic, p.e.x_bc, p.e.n_res, p.e.n_ic, p.e.n_bc, pp, j);
+                  db[1 + j] = fmaf(v[u][0][i], x, db[1 + j]);
+                  if (j < nd) db[1 + j] += v[u][1 + j][i];
+                }
+              }
+            }
+          }
+        }
+      }
+      mbar_arrive(&a_empty[ab]);          // done with this A tile in shared memory
+      if (mvalid && p.e.dbpart) {
+        float* dst = p.e.dbpart + ((int64_t)m * (p.n_tiles * PARTS) + nb * PARTS + part) * (1 + p.e.dterms);
+        dst[0] = db[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          if (j < p.e.dterms) dst[1 + j] = db[1 + j];
+      }
+    }
+    // this CTA's dW^T slab (its m-tile rows x all fout) as split partial blockIdx / m_tiles
+    if (local > 0 && !*abort_flag && mbar_wait(dw_full, 0, abort_flag, p.status, p.wait_ns)) {
+      tc_fence_after();
+      const int m = mb_cta * BM + rr;
+      const int split = blockIdx.x / p.m_tiles;
+      const int f0 = part * 128;
+      for (int c = 0; c < 128; c += 16) {
+        if (f0 + c >= p.K) break;
+        float d[16];
+        tmem_ld16_issue(tq + FZ_DW_COL + f0 + c, d);
+        tmem_wait_ld();
+        if (m < p.M) {
+          float* dst = p.out32 + ((int64_t)split * p.K + f0 + c) * p.M + m;
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (f0 + c + i < p.K) dst[(int64_t)i * p.M] = d[i];
+        }
+      }
+    }
+  }
+
+  // ---- teardown: wait (bounded) for copies still in flight, free TMEM ----------------
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    for (int s = 0; s < FZ_STAGES; ++s) {
+      const int f = inflight[s];
+      if (f) {
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(&full[s], (uint32_t)(f - 1)) && gtimer() - t0 < WAIT_NS) {}
+      }
+    }
+    for (int b = 0; b < FZ_ABUF; ++b) {
+      const int f = a_inflight[b];
+      if (f) {
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(&a_full[b], (uint32_t)(f - 1)) && gtimer() - t0 < WAIT_NS) {}
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * BN));
+  }
+}
+
+int adjdw_grid(const pinn_handle* h, int fin, int64_t NC) {
+  const int mt = (fin + BM - 1) / BM;
+  const int tiles = mt * (int)(NC / TILE_COLS);
+  const int per = std::max(1, std::max(h->sm_count, 1) / mt) * mt;   // a multiple of the m-tile count
+  return std::max(mt, std::min(tiles, per));
+}
+
+}  // namespace
+
+bool tc_adjdw_supported(const pinn_handle* h, int li, int64_t NC) {
+  if (h->spec.precision != PINN_BF16 || li < 1 || !tc_layer_supported(h, li, NC)) return false;
+  return h->layers[li].fout <= BN;   // the dW^T slab fits beside the adjoint accumulator
+}
+
+int tc_adjdw_splits(const pinn_handle* h, int fin, int64_t NC) {
+  return adjdw_grid(h, fin, NC) / ((fin + BM - 1) / BM);
+}
+
+pinn_status tc_gemm_adjdw(pinn_handle* h, const void* WT, const void* Zbar, const void* Ain, int fin, int fout,
+                          int64_t NC, const EpiArgs& e, float* dwpart, int nsplit, cudaStream_t st) {
+  CUtensorMap mw, mz, ma;
+  const uint64_t nt = (uint64_t)(NC / TILE_COLS);
+  if (!make_map(&mw, WT, false, fout, fin, 64, BM)) return map_err(h, "fused adjoint weights");
+  if (!make_map3(&mz, Zbar, false, TILE_COLS, fout, nt, 64, 64)) return map_err(h, "fused adjoint input");
+  if (!make_map3(&ma, Ain, false, TILE_COLS, fin, nt, 64, BM)) return map_err(h, "fused adjoint activations");
+  TcParams p = base_params(fin, (int)NC, fout, NC, 64, h->d_status);
+  p.e = e;
+  p.out32 = dwpart;
+  const int grid = adjdw_grid(h, fin, NC);
+  if (grid / p.m_tiles != nsplit || grid > p.m_tiles * p.n_tiles) {
+    snprintf(h->err, sizeof(h->err), "fused adjoint: split plan mismatch");
+    return PINN_ERR_INVALID_ARG;
+  }
+  p.nsplit = nsplit;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_tc_adjdw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM) != cudaSuccess) {
+      cudaGetLastError();
+      snprintf(h->err, sizeof(h->err), "fused adjoint kernel: cannot reserve %zu bytes of shared memory", FZ_SMEM);
+      return PINN_ERR_CUDA;
+    }
+    attr_set = true;
+  }
+  k_tc_adjdw<<<grid, FZ_NT, FZ_SMEM, st>>>(mw, mz, ma, p);
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    snprintf(h->err, sizeof(h->err), "fused adjoint launch: %s", cudaGetErrorString(err));
+    return PINN_ERR_CUDA;
+  }
+  return PINN_OK;
+}
+
 }  // namespace pinn
 
 // Raw tensor-core GEMM of the library's two operand layouts, FP32 output, for

@@ -33,4 +33,13 @@ pinn_status tc_gemm_adj(pinn_handle* h, const void* WT, const void* WTlo, const 
 pinn_status tc_gemm_dw(pinn_handle* h, const void* Zbar, const void* A, int fout, int fin, int64_t NC, int nsplit,
                        float* part, cudaStream_t st);
 
+// Fused adjoint + weight gradient (BF16, hidden layer li >= 1 on tensor cores with
+// fan-out <= 256): one kernel computes Abar = W^T Zbar with the tanh-jet adjoint
+// epilogue (as tc_gemm_adj) and dW^T = A_{l-1} Zbar^T, written as tc_adjdw_splits()
+// partials [nsplit][fout][fin] (as tc_gemm_dw).  Ain is A_{l-1}^T [fin][NC] tile-major.
+bool tc_adjdw_supported(const pinn_handle* h, int li, int64_t NC);
+int tc_adjdw_splits(const pinn_handle* h, int fin, int64_t NC);
+pinn_status tc_gemm_adjdw(pinn_handle* h, const void* WT, const void* Zbar, const void* Ain, int fin, int fout,
+                          int64_t NC, const EpiArgs& e, float* dwpart, int nsplit, cudaStream_t st);
+
 }  // namespace pinn

@@ -20,7 +20,7 @@ def test_jet_gemm_flops_per_step(name, expected):
     fl, by, sch = bench.algorithmic_work(w, rows, b.n_res + b.n_ic + b.n_bc, "bf16")
     assert sum(fl.values()) == pytest.approx(expected, rel=5e-3)
     # bytes: every phase moves at least its activations once
-    assert all(v > 0 for v in by.values())
+    assert all(by[k] > 0 for k in ("fwd_gemm", "dw_gemm", "adj_gemm")) and by["adjdw_gemm"] == 0
     # the BF16 scheme's value-row low halves are reported apart from the method's bytes
     assert sch["fwd_gemm"] > 0 and sch["adj_gemm"] == 0 and sch["dw_gemm"] == 0
 
@@ -33,3 +33,20 @@ def test_block_layout_matches_parameter_count():
         blocks = bench._blocks(w.spec)
         assert blocks[0][1] == 0 and blocks[-1][2] == param_count(w.spec)
         assert all(a[2] == b[1] for a, b in zip(blocks, blocks[1:]))
+
+
+def test_fused_layers_book_both_gemms_once():
+    """With the adjoint and weight gradient of every layer after the first fused, the
+    FLOPs move to the fused phase and the total is unchanged; the fused phase moves the
+    adjoint's bytes only (the weight gradient reads the same arrays in the same pass)."""
+    import bench
+    from synth import make_workload
+    w, _, _, b = make_workload("ns_cavity_6x256")
+    rows = 4 * b.n_res + b.n_ic + b.n_bc
+    n = b.n_res + b.n_ic + b.n_bc
+    fl0, by0, _ = bench.algorithmic_work(w, rows, n, "bf16")
+    engines = [1] + [2] * (len(w.spec.widths) - 1)
+    fl1, by1, _ = bench.algorithmic_work(w, rows, n, "bf16", engines)
+    assert sum(fl1.values()) == pytest.approx(sum(fl0.values()), rel=1e-12)
+    assert fl1["adj_gemm"] == 0 and fl1["adjdw_gemm"] > 0
+    assert by1["adjdw_gemm"] == pytest.approx(by0["adj_gemm"], rel=1e-12)
