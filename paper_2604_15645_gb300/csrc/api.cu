@@ -88,7 +88,9 @@ pinn_status make_plan(const pinn_handle* h, int64_t n_res, int64_t n_ic, int64_t
   const size_t zrows = (size_t)std::max(h->w_max, 2 * h->spec.ff_m);
   q.Zbar[0] = take(zrows * q.NC * q.es);
   q.Zbar[1] = take(zrows * q.NC * q.es);
-  q.nloss_blocks = out_loss_blocks(q.NP);
+  q.nloss_blocks = out_loss_tma_ok(h->spec.precision, h->act, h->spec.widths[L - 1])
+                      ? out_loss_tma_blocks(q.NP, h->sm_count)
+                      : out_loss_blocks(q.NP);
   q.losspart = take((size_t)q.nloss_blocks * 8 * sizeof(double));
   if (h->causal_M > 0) q.segpart = take((size_t)q.nloss_blocks * CAUSAL_MAX * 4 * sizeof(double));
   if (h->spec.ff_m) q.ffpart = take((size_t)h->spec.ff_m * FFG_BLOCKS * h->d_in * sizeof(double));

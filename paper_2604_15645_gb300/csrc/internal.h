@@ -220,6 +220,11 @@ void launch_ff_grad_final(const double* part, int d_in, int m, bool periodic, co
                           float* out, cudaStream_t st);
 cudaError_t launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st);
 int out_loss_blocks(int64_t n_points);
+// The output/loss kernel with A_L staged by TMA (BF16 tanh networks, last hidden width
+// <= 512) runs two blocks per SM; its block count (the number of loss, dW and bias
+// partials) is out_loss_tma_blocks.
+bool out_loss_tma_ok(int prec, int act, int w);
+int out_loss_tma_blocks(int64_t n_points, int sm_count);
 
 // Bias gradient partials of a layer from its pre-activation adjoint (value rows
 // only), plus, for a first layer applied to raw coordinates, the coordinate terms

@@ -3,8 +3,12 @@
 // per-row reductions, the ordered FP64 finalisation, and Adam.
 #include <cmath>
 
+#include <cuda.h>
+
 #include "internal.h"
 #include "jet.cuh"
+#include "ptx.cuh"
+#include "tc.h"
 
 namespace pinn {
 
@@ -564,6 +568,365 @@ int out_loss_blocks(int64_t NP) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(NP / TILE_PTS, 4096));
 }
 
+// ------------------------------------------------------------------------------------
+// The same output layer, residual, loss and adjoint seed for BF16 tanh networks
+// (hidden width <= 512), with A_L staged through shared memory by TMA instead of
+// register-limited global loads.  A producer warp streams each 64-point tile's A_L
+// in chunks of 32 features (four 128-byte swizzled boxes, one per jet row, plus the
+// value-row low half) through a three-stage ring: once for the output jets and the
+// residual, and once more (an L2 hit) for the output layer's dW, the adjoint
+// abar_L = Ubar W_out and its tanh-jet adjoint.  Four consumer warps use the same
+// lane mapping as k_out_loss (point group pg = lane / 8, feature slice sl = lane % 8);
+// the swizzle spreads a warp's eight features over all banks.  Results (loss and
+// segment partials, dW, bias partials, Zbar_L) and their summation order per block
+// are those of k_out_loss.
+// ------------------------------------------------------------------------------------
+constexpr int OT_CONS = 128;                     // consumer threads (4 warps)
+constexpr int OT_THREADS = OT_CONS + 32;         // + the producer warp
+constexpr int OT_FC = 32;                        // features per chunk
+constexpr int OT_ROWB = OT_FC * 128;             // one jet-row box: 32 features x 64 points x 2 B = 4 KB
+constexpr int OT_STAGE = 5 * OT_ROWB;            // four jet rows + the value-row low half: 20 KB
+constexpr int OT_STAGES = 3;
+constexpr uint64_t OT_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(OT_CONS) : "memory"); }
+
+// Four BF16 values of (feature fi, points q0..q0+3) of a 128-byte swizzled box row.
+__device__ __forceinline__ void ot_load4(const uint8_t* box, int fi, int q0, float v[4]) {
+  const int chunk = (q0 >> 3) ^ (fi & 7);
+  const uint2 u = *reinterpret_cast<const uint2*>(box + fi * 128 + chunk * 16 + (q0 & 7) * 2);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+__device__ __forceinline__ double cons_sum_d(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  cons_sync();
+  if (l == 0) sh[w] = v;
+  cons_sync();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < OT_CONS / 32; ++i) s += sh[i];
+  return s;
+}
+
+template <int D>
+__global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_constant__ CUtensorMap mapA,
+                                                            const __grid_constant__ CUtensorMap mapLo, OutArgs a) {
+  extern __shared__ uint8_t ot_raw[];
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ot_raw) + 1023) & ~uintptr_t(1023));
+  const int w = a.w;
+  float* sW = reinterpret_cast<float*>(ring + OT_STAGES * OT_STAGE);   // [D][w] output weights
+  float* sdw = sW + D * w;                                            // [4 warps][D][w] dW accumulators
+  float* sdb = sdw + (OT_CONS / 32) * D * w;                          // [4 warps][w] hidden bias accumulators
+  uint64_t* full = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(sdb + (OT_CONS / 32) * w) + 7) & ~uintptr_t(7));
+  uint64_t* empty = full + OT_STAGES;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + OT_STAGES);
+  __shared__ double segacc[CAUSAL_MAX][4];
+  __shared__ int s_seg[TILE_PTS];
+  __shared__ float s_rr[TILE_PTS][3];
+  __shared__ double sh[OT_CONS / 32];
+  __shared__ float shb[OT_CONS / 32];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OT_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], OT_CONS);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < D * w; i += blockDim.x) sW[i] = a.W[i];
+  for (int i = threadIdx.x; i < (OT_CONS / 32) * (D + 1) * w; i += blockDim.x) sdw[i] = 0.f;
+  if (a.segpart)
+    for (int i = threadIdx.x; i < CAUSAL_MAX * 4; i += blockDim.x) segacc[i / 4][i % 4] = 0.0;
+  __syncthreads();
+
+  const int64_t ntiles = a.NP / TILE_PTS;
+  const int nchunks = (w + OT_FC - 1) / OT_FC;
+  const int passes = a.want_grad ? 2 : 1;
+  const bool lo = a.ALlo != nullptr;
+
+  if (warp == OT_CONS / 32) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int armed[OT_STAGES] = {0, 0, 0};
+      for (int64_t T0i = blockIdx.x; T0i < ntiles && !*abort_flag; T0i += gridDim.x) {
+        const int T0 = (int)(a.reverse ? ntiles - 1 - T0i : T0i);
+        for (int pass = 0; pass < passes && !*abort_flag; ++pass)
+          for (int k = 0; k < nchunks; ++k) {
+            if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.status, OT_WAIT_NS)) break;
+            uint8_t* sb = ring + stage * OT_STAGE;
+            mbar_expect_tx(&full[stage], (lo ? 5 : 4) * OT_ROWB);
+            armed[stage] = (int)phase + 1;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) tma_load_3d(sb + r * OT_ROWB, &mapA, &full[stage], 64 * r, OT_FC * k, T0);
+            if (lo) tma_load_3d(sb + 4 * OT_ROWB, &mapLo, &full[stage], 0, OT_FC * k, T0);
+            if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
+          }
+      }
+      // every load this thread issued lands before the block may exit (bounded)
+      for (int s = 0; s < OT_STAGES; ++s)
+        if (armed[s]) {
+          const uint64_t t0 = gtimer();
+          while (!mbar_try(&full[s], (uint32_t)(armed[s] - 1)) && gtimer() - t0 < OT_WAIT_NS) {}
+        }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------------ consumers
+  const __nv_bfloat16* ALlo = reinterpret_cast<const __nv_bfloat16*>(a.ALlo);
+  (void)ALlo;
+  __nv_bfloat16* Zb = reinterpret_cast<__nv_bfloat16*>(a.Zbar);
+  const int pg = lane >> 3, sl = lane & 7;
+  const int q0 = 16 * warp + 4 * pg;
+  double acc[5] = {0, 0, 0, 0, 0};
+  float dbo[3] = {0.f, 0.f, 0.f};
+  int stage = 0;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t T0i = blockIdx.x; T0i < ntiles && ok; T0i += gridDim.x) {
+    const int64_t T0 = a.reverse ? ntiles - 1 - T0i : T0i;
+    const int64_t cb = T0 * TILE_COLS + q0;
+    const int64_t p0 = T0 * TILE_PTS + q0;
+    float U[4][3][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) U[j][c][r] = 0.f;
+    for (int k = 0; k < nchunks; ++k) {
+      if (!mbar_wait(&full[stage], phase, abort_flag, a.status, OT_WAIT_NS)) { ok = false; break; }
+      const uint8_t* sb = ring + stage * OT_STAGE;
+#pragma unroll
+      for (int e = 0; e < OT_FC / 8; ++e) {
+        const int fi = sl + 8 * e, f = OT_FC * k + fi;
+        if (f < w) {
+          float v[4][4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) ot_load4(sb + r * OT_ROWB, fi, q0 & 63, v[r]);
+          if (lo) {
+            float l4[4];
+            ot_load4(sb + 4 * OT_ROWB, fi, q0 & 63, l4);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[0][j] += l4[j];
+          }
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const float wc = sW[c * w + f];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+              for (int r = 0; r < 4; ++r) U[j][c][r] = fmaf(wc, v[r][j], U[j][c][r]);
+          }
+        }
+      }
+      mbar_arrive(&empty[stage]);
+      if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
+    }
+    if (!ok) break;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float x = U[j][c][r];
+          x += __shfl_xor_sync(0xffffffffu, x, 1);
+          x += __shfl_xor_sync(0xffffffffu, x, 2);
+          x += __shfl_xor_sync(0xffffffffu, x, 4);
+          U[j][c][r] = x;
+        }
+    float Ub[4][3][4];
+    double lacc[5] = {0, 0, 0, 0, 0};
+    int segj[4];
+    float rrj[4][3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t idx;
+      const int set = point_set(p0 + j, a.n_res, a.n_ic, a.n_bc, idx);
+      if (set != SET_PAD) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) U[j][c][0] += a.b[c];
+      }
+      float kp = a.k_pde;
+      segj[j] = -1;
+      if (a.segments && set == SET_RES) {
+        const float tt = a.x_res[(int64_t)a.t_index * a.n_res + idx];
+        segj[j] = min(a.segments - 1, max(0, (int)floorf((tt - a.t0) * a.tinv)));
+        if (a.seg_scale) kp = a.seg_scale[segj[j]];
+      }
+      point_residual<D>(a, set, idx, kp, U[j], Ub[j], lacc, rrj[j]);
+    }
+    if (sl == 0)
+      for (int i = 0; i < 5; ++i) acc[i] += lacc[i];
+    if (a.segpart) {
+      if (sl == 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          s_seg[q0 + j] = segj[j];
+          s_rr[q0 + j][0] = rrj[j][0]; s_rr[q0 + j][1] = rrj[j][1]; s_rr[q0 + j][2] = rrj[j][2];
+        }
+      cons_sync();
+      if (threadIdx.x == 0)
+        for (int q = 0; q < TILE_PTS; ++q)
+          if (s_seg[q] >= 0) {
+            double* sa = segacc[s_seg[q]];
+            sa[0] += s_rr[q][0]; sa[1] += s_rr[q][1]; sa[2] += s_rr[q][2]; sa[3] += 1.0;
+          }
+      cons_sync();
+    }
+    if (!a.want_grad) continue;
+    if (sl == 0) {
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dbo[c] += Ub[j][c][0];
+    }
+    for (int k = 0; k < nchunks; ++k) {
+      if (!mbar_wait(&full[stage], phase, abort_flag, a.status, OT_WAIT_NS)) { ok = false; break; }
+      const uint8_t* sb = ring + stage * OT_STAGE;
+#pragma unroll
+      for (int e = 0; e < OT_FC / 8; ++e) {
+        const int fi0 = sl + 8 * e;
+        const bool live = OT_FC * k + fi0 < w;
+        const int fi = live ? fi0 : (w - 1 - OT_FC * k);   // a slice past the width re-reads the last feature
+        const int f = OT_FC * k + fi;
+        float av[4][4], zb[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) ot_load4(sb + r * OT_ROWB, fi, q0 & 63, av[r]);
+        if (lo) {
+          float l4[4];
+          ot_load4(sb + 4 * OT_ROWB, fi, q0 & 63, l4);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) av[0][j] += l4[j];
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          float g = 0.f;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) g = fmaf(Ub[j][c][r], av[r][j], g);
+          g += __shfl_xor_sync(0xffffffffu, g, 8);
+          g += __shfl_xor_sync(0xffffffffu, g, 16);
+          if (pg == 0 && live) sdw[(warp * D + c) * w + f] += g;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float ab[4] = {0.f, 0.f, 0.f, 0.f}, zz[4], o[4];
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const float wc = sW[c * w + f];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) ab[r] = fmaf(wc, Ub[j][c][r], ab[r]);
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r) zz[r] = av[r][j];
+          jet_adj_a(zz, ab, o, a.jet_mode);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) zb[r][j] = o[r];
+        }
+        __nv_bfloat16* zbrow = Zb + toff(f, cb, w);
+        if (live)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) store4_stream<__nv_bfloat16>(zbrow + 64 * r, zb[r]);
+        if (a.dbhid) {
+          float s = (zb[0][0] + zb[0][1]) + (zb[0][2] + zb[0][3]);
+          s += __shfl_xor_sync(0xffffffffu, s, 8);
+          s += __shfl_xor_sync(0xffffffffu, s, 16);
+          if (pg == 0 && live) sdb[warp * w + f] += s;
+        }
+      }
+      mbar_arrive(&empty[stage]);
+      if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
+    }
+  }
+  for (int i = 0; i < 5; ++i) {
+    const double s = cons_sum_d(acc[i], sh);
+    if (threadIdx.x == 0) a.losspart[(int64_t)blockIdx.x * 8 + i] = s;
+  }
+  if (a.segpart) {
+    cons_sync();
+    for (int i = threadIdx.x; i < CAUSAL_MAX * 4; i += OT_CONS)
+      a.segpart[(int64_t)blockIdx.x * CAUSAL_MAX * 4 + i] = segacc[i / 4][i % 4];
+  }
+  if (!a.want_grad) return;
+  cons_sync();
+  for (int i = threadIdx.x; i < D * w; i += OT_CONS) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < OT_CONS / 32; ++k) s += sdw[k * D * w + i];
+    a.dwpart[(int64_t)blockIdx.x * D * w + i] = s;
+  }
+  if (a.dbhid)
+    for (int i = threadIdx.x; i < w; i += OT_CONS) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < OT_CONS / 32; ++k) s += sdb[k * w + i];
+      a.dbhid[(int64_t)i * gridDim.x + blockIdx.x] = s;
+    }
+  for (int c = 0; c < D; ++c) {
+    float v = dbo[c];
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    cons_sync();
+    if (lane == 0) shb[warp] = v;
+    cons_sync();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int k = 0; k < OT_CONS / 32; ++k) t += shb[k];
+      a.dbpart[(int64_t)c * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+// Whether the TMA-staged output kernel applies: BF16 tanh networks whose last hidden
+// layer is at most 512 wide.
+bool out_loss_tma_ok(int prec, int act, int w) { return prec == PINN_BF16 && act == PINN_ACT_TANH && w <= 512; }
+
+int out_loss_tma_blocks(int64_t NP, int sm_count) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(NP / TILE_PTS, 2 * (int64_t)std::max(sm_count, 1)));
+}
+
+static size_t ot_smem(int w, int d_out) {
+  return (size_t)OT_STAGES * OT_STAGE + 1024 +
+         sizeof(float) * (size_t)w * (d_out * (1 + OT_CONS / 32) + OT_CONS / 32) + 8 + 8 * 2 * OT_STAGES + 16;
+}
+
+template <int D>
+cudaError_t out_loss_tma_launch(const CUtensorMap& ma, const CUtensorMap& ml, const OutArgs& a, int nblocks,
+                                cudaStream_t st) {
+  auto kern = k_out_loss_tma<D>;
+  const size_t smem = ot_smem(a.w, D);
+  static size_t reserved = 0;
+  if (smem > reserved) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    reserved = smem;
+  }
+  kern<<<nblocks, OT_THREADS, smem, st>>>(ma, ml, a);
+  return cudaGetLastError();
+}
+
+// Returns cudaErrorNotSupported (nothing launched) when the tensor maps cannot be built.
+cudaError_t launch_out_loss_tma(const OutArgs& a, int nblocks, cudaStream_t st) {
+  CUtensorMap ma, ml;
+  const uint64_t nt = (uint64_t)(a.NP / TILE_PTS);
+  if (!tc_map3(&ma, a.AL, false, TILE_COLS, (uint64_t)a.w, nt, 64, OT_FC)) return cudaErrorNotSupported;
+  ml = ma;
+  if (a.ALlo && !tc_map3(&ml, a.ALlo, false, TILE_PTS, (uint64_t)a.w, nt, 64, OT_FC)) return cudaErrorNotSupported;
+  return a.d_out == 1 ? out_loss_tma_launch<1>(ma, ml, a, nblocks, st) : out_loss_tma_launch<3>(ma, ml, a, nblocks, st);
+}
+
 template <typename T, int D, bool FAST, bool SINE>
 cudaError_t out_loss_launch(const OutArgs& a, int nblocks, size_t smem, cudaStream_t st) {
   auto kern = k_out_loss<T, D, FAST, SINE>;
@@ -579,6 +942,10 @@ cudaError_t out_loss_launch(const OutArgs& a, int nblocks, size_t smem, cudaStre
 }
 
 cudaError_t launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st) {
+  if (!a.ZL && out_loss_tma_ok(prec, PINN_ACT_TANH, a.w)) {
+    const cudaError_t e = launch_out_loss_tma(a, nblocks, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   const size_t smem = sizeof(float) * a.w * (a.d_out * (1 + OUT_THREADS / 32) + OUT_THREADS / 32);
   // the sine adjoint (from stored pre-activations) is a separate instantiation, so the
   // tanh kernels carry none of its registers

@@ -1,6 +1,8 @@
 // Tensor-core (tcgen05 / TMA) jet GEMMs for sm_103a.
 #pragma once
 
+#include <cuda.h>
+
 #include "internal.h"
 
 namespace pinn {
@@ -8,6 +10,11 @@ namespace pinn {
 // Called once from pinn_create: resolves the driver entry point used to build
 // TMA tensor maps.
 void tc_init(pinn_handle* h);
+// 3-D TMA tensor map over a tile-major jet matrix [ntiles][rows][tcols] (BF16, or FP32
+// when fp32), box [1][box_rows][box_cols], 128-byte swizzle, zero fill out of bounds.
+// False if the driver entry point is missing or the encoding fails.
+bool tc_map3(CUtensorMap* m, const void* base, bool fp32, uint64_t tcols, uint64_t rows, uint64_t ntiles,
+             uint32_t box_cols, uint32_t box_rows);
 // True when hidden layer li (0-based weight layer) runs on tensor cores.
 bool tc_layer_supported(const pinn_handle* h, int li, int64_t NC);
 // Bias partials per column tile written by the fused adjoint epilogue.

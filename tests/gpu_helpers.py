@@ -96,3 +96,52 @@ def assert_parity(gpu_terms, gpu_grad, ref_terms, ref_grad, tol, what="", spec=N
         if spec is not None:
             rows = check_blocks(gpu_grad, ref_grad, spec, tol if block_tol is None else block_tol, what)
             print(f"{what}: gradient rel L2 {e:.3e}; per block:\n{report(rows)}")
+
+
+def torch_loss_grad(spec, params, B, batch, problem, dtype, chunk=65536, want_grad=True):
+    """The paper's own method at any size: torch double-backward autograd (Sec. 2.3),
+    in `dtype`, over chunks of the interior points.  Every loss term is a sum over its
+    points divided by its count, so chunk losses weighted by their share of the interior
+    points (initial and boundary sets in the first chunk) add up to the whole loss, and
+    so do their gradients.  Returns (loss total, gradient as float64 numpy or None)."""
+    from baseline import torch_autograd as ta
+    from synth import Batch
+    model = ta.TorchPINN(spec, params, B, "cuda", dtype)
+    lam = (problem.lambda_pde, problem.lambda_ic, problem.lambda_bc)
+    n = batch.n_res
+    total = 0.0
+    for s in range(0, max(n, 1), chunk):
+        e = min(n, s + chunk)
+        first = s == 0
+        sub = Batch(batch.x_res[:, s:e], batch.x_ic if first else batch.x_ic[:, :0],
+                    batch.g_ic if first else batch.g_ic[:, :0], batch.ic_mask,
+                    batch.x_bc if first else batch.x_bc[:, :0], batch.g_bc if first else batch.g_bc[:, :0],
+                    batch.bc_mask)
+        frac = (e - s) / n if n else 1.0
+        t, _ = ta.loss(model, ta.batch_to_torch(sub, "cuda", dtype), problem.nu, (lam[0] * frac, lam[1], lam[2]))
+        if want_grad:
+            t.backward()
+        total += float(t.detach())
+        del t
+    g = model.flat_grad().detach().double().cpu().numpy() if want_grad else None
+    del model
+    torch.cuda.empty_cache()
+    return total, g
+
+
+def layer_coordinates(spec, per_layer_v, seed, layers=None):
+    """Seeded parameter indices: per weight layer `per_layer_v` entries of V, one of s
+    (with RWF) and one of b (Eqs. 4 and 15 blocks), for the layers listed (default all)."""
+    from parity_blocks import param_blocks
+    rng = np.random.default_rng(seed)
+    blocks = {n: (a, b) for n, a, b in param_blocks(spec)}
+    n_layers = len(spec.widths) + 1
+    out = []
+    for l in (layers or range(1, n_layers + 1)):
+        a, b = blocks[f"V{l}"]
+        out.extend(rng.choice(np.arange(a, b), size=per_layer_v, replace=False).tolist())
+        for name in (f"s{l}", f"b{l}"):
+            if name in blocks:
+                a, b = blocks[name]
+                out.append(int(rng.integers(a, b)))
+    return np.array(sorted(out))
