@@ -107,6 +107,17 @@ typedef struct {
 #define PINN_FLAG_BF16_VALUE_SPLIT 4
 /* (flag value 2 is reserved) */
 
+/* pinn_spec.flags, kernel variants (same results up to rounding; the many-network
+ * autotuner picks among them per network shape):
+ *   PINN_FLAG_UNFUSED_ADJOINT  run every layer's adjoint and weight gradient as two
+ *                              kernels even where the fused kernel applies (BF16,
+ *                              fan-out <= 256);
+ *   PINN_FLAG_DW_ROWS_128      weight-gradient tiles of 128 output rows (default: 256
+ *                              rows, two accumulators sharing each staged operand, for
+ *                              layers with more than 128 outputs). */
+#define PINN_FLAG_UNFUSED_ADJOINT 8
+#define PINN_FLAG_DW_ROWS_128 16
+
 /* Loss weights and the PDE coefficient (nu for Burgers; 1/Re for Navier-Stokes;
  * ignored for Maxwell). */
 typedef struct {
@@ -404,7 +415,16 @@ PINN_API pinn_status pinn_multi_destroy(pinn_multi* m);
 PINN_API pinn_status pinn_multi_param_offsets(const pinn_multi* m, int64_t* offsets);
 PINN_API pinn_status pinn_multi_workspace_bytes(pinn_multi* m, const pinn_batch* batches, size_t* bytes);
 PINN_API pinn_status pinn_multi_set_ff_matrix(pinn_multi* m, int32_t net, const float* d_B);
-/* cuda_cores = 1 forces the CUDA-core GEMMs for network `net`, 0 allows tcgen05. */
+/* Kernel configuration of network `net` (same results up to rounding):
+ *   0 tcgen05, fused adjoint + weight gradient where it applies (the default);
+ *   1 CUDA-core GEMMs;
+ *   2 tcgen05 with separate adjoint and weight-gradient kernels (PINN_FLAG_UNFUSED_ADJOINT);
+ *   3 as 2 with 128-row weight-gradient tiles (PINN_FLAG_DW_ROWS_128).
+ * Anything else is PINN_ERR_INVALID_ARG. */
+PINN_API pinn_status pinn_multi_set_config(pinn_multi* m, int32_t net, int32_t config);
+PINN_API pinn_status pinn_multi_get_config(const pinn_multi* m, int32_t net, int32_t* config);
+/* cuda_cores = 1 forces the CUDA-core GEMMs for network `net` (configuration 1), 0 the
+ * default tcgen05 configuration 0. */
 PINN_API pinn_status pinn_multi_set_engine(pinn_multi* m, int32_t net, int32_t cuda_cores);
 PINN_API pinn_status pinn_multi_get_engine(const pinn_multi* m, int32_t net, int32_t* cuda_cores);
 /* One training step (1-based `step`); asynchronous on `stream` except for graph
@@ -413,9 +433,11 @@ PINN_API pinn_status pinn_multi_train_step(pinn_multi* m, const pinn_problem* pr
                                            float* d_params, float* d_grad, float* d_m, float* d_v, int64_t step,
                                            float lr, float beta1, float beta2, float eps, void* d_ws,
                                            size_t ws_bytes, double* d_loss, void* stream);
-/* Times both GEMM engines per network (keyed by width, depth, power-of-two point
- * bucket and precision), selects the faster, and reads / writes the choices as a
- * JSON object in `cache_path` (NULL: no file).  Runs eagerly and synchronises. */
+/* Times every kernel configuration that applies to a network (keyed by width, depth,
+ * power-of-two point bucket and precision), selects the fastest, and reads / writes
+ * the choices as a JSON object in `cache_path` (NULL: no file).  Runs eagerly and
+ * synchronises.  The training step spreads the networks over up to 32 worker
+ * streams, longest first by estimated jet-GEMM work. */
 PINN_API pinn_status pinn_multi_autotune(pinn_multi* m, const pinn_problem* probs, const pinn_batch* batches,
                                          const float* d_params, void* d_ws, size_t ws_bytes, double* d_loss,
                                          float* d_grad, const char* cache_path, void* stream);

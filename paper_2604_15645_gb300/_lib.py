@@ -15,6 +15,7 @@ PINN_LOSS_TERMS = 8
 PINN_FP32, PINN_TF32, PINN_BF16 = 0, 1, 2
 PINN_BURGERS_1D, PINN_NS_STEADY_2D, PINN_MAXWELL_TE_2D, PINN_ADVECTION_1D, PINN_ALLEN_CAHN_1D = 0, 1, 2, 3, 4
 PINN_FLAG_CUDA_CORES, PINN_FLAG_BF16_VALUE_SPLIT = 1, 4
+PINN_FLAG_UNFUSED_ADJOINT, PINN_FLAG_DW_ROWS_128 = 8, 16
 PRECISIONS = {"fp32": PINN_FP32, "tf32": PINN_TF32, "bf16": PINN_BF16}
 STATUS = {0: "PINN_OK", 1: "PINN_ERR_INVALID_ARG", 2: "PINN_ERR_UNSUPPORTED", 3: "PINN_ERR_CUDA",
           4: "PINN_ERR_WORKSPACE", 5: "PINN_ERR_NONFINITE", 6: "PINN_ERR_TIMEOUT", 7: "PINN_ERR_OOM"}
@@ -31,7 +32,7 @@ EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_by
            "pinn_lbfgs_create", "pinn_lbfgs_destroy", "pinn_lbfgs_reset", "pinn_lbfgs_step", "pinn_lbfgs_direction",
            "pinn_lbfgs_push_pair", "pinn_set_activation", "pinn_set_periodic", "pinn_loss_grad_ff",
            "pinn_set_graph", "pinn_set_global_counts", "pinn_graph_held", "pinn_debug_wait_expiry",
-           "pinn_layer_engines"]
+           "pinn_layer_engines", "pinn_multi_set_config", "pinn_multi_get_config"]
 PINN_ACT_TANH, PINN_ACT_SINE = 0, 1
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 9
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH):
     lib.pinn_multi_set_ff_matrix.argtypes = [H, C.c_int32, C.c_void_p]
     lib.pinn_multi_set_engine.argtypes = [H, C.c_int32, C.c_int32]
     lib.pinn_multi_get_engine.argtypes = [H, C.c_int32, C.POINTER(C.c_int32)]
+    lib.pinn_multi_set_config.argtypes = [H, C.c_int32, C.c_int32]
+    lib.pinn_multi_get_config.argtypes = [H, C.c_int32, C.POINTER(C.c_int32)]
     lib.pinn_multi_train_step.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_float,
                                           C.c_float, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]

@@ -268,6 +268,20 @@ class PinnMulti:
             out.append("cuda_cores" if v.value else "tc")
         return out
 
+    CONFIGS = ("tc", "cuda_cores", "tc_unfused", "tc_unfused_dw128")
+
+    def configs(self):
+        """Kernel configuration of every network (one of CONFIGS)."""
+        out = []
+        for i in range(self.n):
+            v = _lib.C.c_int32()
+            _lib.check_multi(_lib.load().pinn_multi_get_config(self.h, i, _lib.C.byref(v)), self.h)
+            out.append(self.CONFIGS[v.value])
+        return out
+
+    def set_config(self, i, config):
+        _lib.check_multi(_lib.load().pinn_multi_set_config(self.h, i, self.CONFIGS.index(config)), self.h)
+
     def set_engine(self, i, cuda_cores):
         _lib.check_multi(_lib.load().pinn_multi_set_engine(self.h, i, int(bool(cuda_cores))), self.h)
 

@@ -726,7 +726,8 @@ pinn_status pinn_create(const pinn_spec* spec, pinn_handle** out) {
   if (spec->ff_m < 0 || spec->ff_m > 2048) return PINN_ERR_INVALID_ARG;
   if (spec->rwf != 0 && spec->rwf != 1) return PINN_ERR_INVALID_ARG;
   if (spec->precision < PINN_FP32 || spec->precision > PINN_BF16) return PINN_ERR_INVALID_ARG;
-  if (spec->flags & ~(PINN_FLAG_CUDA_CORES | PINN_FLAG_BF16_VALUE_SPLIT))
+  if (spec->flags & ~(PINN_FLAG_CUDA_CORES | PINN_FLAG_BF16_VALUE_SPLIT | PINN_FLAG_UNFUSED_ADJOINT |
+                      PINN_FLAG_DW_ROWS_128))
     return PINN_ERR_INVALID_ARG;
   pinn_handle* h = new (std::nothrow) pinn_handle();
   if (!h) return PINN_ERR_OOM;

@@ -167,9 +167,13 @@ __global__ void __launch_bounds__(THREADS) k_simt_dw(const TA* __restrict__ Aop,
   const int m0 = blockIdx.y * DBM, nn0 = blockIdx.x * DBN;
   const int s = blockIdx.z;
   const int64_t kb = (int64_t)s * kchunk, ke = min(NC, kb + kchunk);
-  float acc[4][4];
+  // A split sums up to NC / nsplit jet columns (hundreds of thousands at a million
+  // points): each DBK-column block is summed on its own, and the block sums are added
+  // to the running total with Kahan compensation, so the rounding error stays near
+  // that of a DBK-term sum instead of growing with the split's length.
+  float acc[4][4], comp[4][4];
   for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[i][j] = comp[i][j] = 0.f;
   for (int64_t k0 = kb; k0 < ke; k0 += DBK) {
     const int i = t >> 2, kk = (t & 3) * 8;   // 64 rows x 32 k, 8 per thread
     {
@@ -187,6 +191,11 @@ __global__ void __launch_bounds__(THREADS) k_simt_dw(const TA* __restrict__ Aop,
       for (int q = 0; q < 8; ++q) Bs[kk + q][i] = v[q];
     }
     __syncthreads();
+    float blk[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) blk[p][q] = 0.f;
 #pragma unroll
     for (int k = 0; k < DBK; ++k) {
       const float4 a4 = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
@@ -195,8 +204,17 @@ __global__ void __launch_bounds__(THREADS) k_simt_dw(const TA* __restrict__ Aop,
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+        for (int q = 0; q < 4; ++q) blk[p][q] = fmaf(a[p], b[q], blk[p][q]);
     }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {   // Kahan: acc + blk with the lost low part kept in comp
+        const float y = blk[p][q] - comp[p][q];
+        const float t = acc[p][q] + y;
+        comp[p][q] = (t - acc[p][q]) - y;
+        acc[p][q] = t;
+      }
     __syncthreads();
   }
   for (int p = 0; p < 4; ++p) {

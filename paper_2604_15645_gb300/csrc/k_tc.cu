@@ -125,6 +125,11 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
               const TcParams p) {
   using C = Cfg<TF32, MODE, SPLIT>;
   using T = typename std::conditional<TF32, float, __nv_bfloat16>::type;
+  // weight gradient with 256-row tiles: two 128-row accumulators (TMEM columns 0..255 and
+  // 256..511) share each staged B operand, so the B rows are read once for 256 output
+  // rows; one work item fills both accumulators (no double buffering across items)
+  constexpr bool DW2 = (MODE == TC_DW) && SPLIT;
+  constexpr int MROWS = DW2 ? 2 * BM : BM;                // output rows per work item
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* blo = smem + C::STAGES * C::STAGE;          // TF32 B_lo buffer (BLOC_BYTES)
@@ -219,7 +224,8 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
             // weight gradient: K runs over jet columns, 256 / BKE K-blocks per tile
             constexpr int KPT = TILE_COLS / C::BKE;
             const int tz = kb / KPT, tx = (kb % KPT) * C::BKE;
-            tma_load_3d(sa, &mapA, &full[stage], tx, mb * BM, tz);
+            tma_load_3d(sa, &mapA, &full[stage], tx, mb * MROWS, tz);
+            if (DW2) tma_load_3d(sa2, &mapA, &full[stage], tx, mb * MROWS + BM, tz);
             tma_load_3d(sb, &mapB, &full[stage], tx, nb * BN, tz);
           }
           if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
@@ -239,8 +245,9 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
       for (int t = blockIdx.x; t < total && !*abort_flag && !stalled; t += gridDim.x, ++local) {
         int mb, nb, k0, k1;
         coords(t, mb, nb, k0, k1);
-        const int buf = local & 1;
-        if (!mbar_wait(&acc_empty[buf], ((local >> 1) & 1) ^ 1, abort_flag, p.status, p.wait_ns)) break;
+        const int buf = DW2 ? 0 : local & 1;
+        const uint32_t par = DW2 ? ((uint32_t)local & 1) : ((uint32_t)(local >> 1) & 1);
+        if (!mbar_wait(&acc_empty[buf], par ^ 1, abort_flag, p.status, p.wait_ns)) break;
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
         bool ok = true;
@@ -257,8 +264,11 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
             const uint64_t bd = C::B_MN ? make_desc(sb + kk * C::UK * 128, C::BOX_BYTES, 1024)
                                         : make_desc(sb + kk * 32, 16, 1024);
             tc_mma<TF32>(d, ad, bd, idesc, (kb > k0 || kk > 0) ? 1u : 0u);
-            // low half of the weights: D += W_lo . A on every column, or on the value columns
-            if (SPLIT) {
+            if constexpr (DW2) {
+              // the second 128 output rows, same B operand, into TMEM columns 256..511
+              tc_mma<TF32>(d + BN, make_desc(sa2 + kk * 32, 16, 1024), bd, idesc, (kb > k0 || kk > 0) ? 1u : 0u);
+            } else if (SPLIT) {
+              // low half of the weights: D += W_lo . A on every column, or on the value columns
               constexpr uint32_t idesc_v = make_idesc(TF32 ? 2u : 1u, C::B_MN ? 1u : 0u, TILE_PTS);
               tc_mma<TF32>(d, make_desc(sa2 + kk * 32, 16, 1024), bd, p.wlo_values_only ? idesc_v : idesc, 1u);
             }
@@ -368,12 +378,14 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
       int mb, nb, k0, k1;
       coords(t, mb, nb, k0, k1);
-      const int buf = local & 1;
-      if (!mbar_wait(&acc_full[buf], (local >> 1) & 1, abort_flag, p.status, p.wait_ns)) break;
+      const int buf = DW2 ? 0 : local & 1;
+      if (!mbar_wait(&acc_full[buf], DW2 ? ((uint32_t)local & 1) : ((uint32_t)(local >> 1) & 1), abort_flag,
+                     p.status, p.wait_ns)) break;
       tc_fence_after();
-      const int m = mb * BM + row;
+      for (int half = 0; half < (DW2 ? 2 : 1); ++half) {
+      const int m = mb * MROWS + half * BM + row;
       const bool mvalid = m < p.M;
-      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BN;
+      const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (DW2 ? half : buf) * BN;
       float db[4] = {0.f, 0.f, 0.f, 0.f};
 
       auto issue = [&](int u, float (&v)[4][UPTS]) {
@@ -506,6 +518,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
         for (int j = 0; j < 3; ++j)
           if (j < p.e.dterms) dst[1 + j] = db[1 + j];
       }
+      }   // half
       tc_fence_before();
       mbar_arrive(&acc_empty[buf]);
     }
@@ -624,8 +637,14 @@ bool tc_layer_supported(const pinn_handle* h, int li, int64_t NC) {
   return (fin % 8 == 0) && (fout % 8 == 0) && fin >= 16 && fout >= 16;
 }
 
+// Weight-gradient tiles have 256 output rows (two accumulators sharing B) when the
+// layer has more than 128 outputs, else (or with PINN_FLAG_DW_ROWS_128) 128.
+static int dw_rows(const pinn_handle* h, int fout) {
+  return (fout > BM && !(h->spec.flags & PINN_FLAG_DW_ROWS_128)) ? 2 * BM : BM;
+}
+
 int tc_dw_splits(const pinn_handle* h, int fout, int fin, int64_t NC) {
-  const int tiles = ((fout + BM - 1) / BM) * ((fin + BN - 1) / BN);
+  const int tiles = ((fout + dw_rows(h, fout) - 1) / dw_rows(h, fout)) * ((fin + BN - 1) / BN);
   const int kblock = (h->spec.precision == PINN_TF32) ? 32 : 64;
   const int k_iters = (int)((NC + kblock - 1) / kblock);
   int ns = std::max(1, (std::max(h->sm_count, 1) + tiles - 1) / tiles);
@@ -706,12 +725,14 @@ pinn_status adj_impl(pinn_handle* h, const void* WT, const void* WTlo, const voi
 template <bool TF32>
 pinn_status dw_impl(pinn_handle* h, const void* Zbar, const void* A, int fout, int fin, int64_t NC, int nsplit,
                     float* part, cudaStream_t st) {
-  using C = Cfg<TF32, TC_DW, false>;
+  using C = Cfg<TF32, TC_DW, false>;   // (the 256-row variant stages the same boxes, twice for A)
+  const bool two = dw_rows(h, fout) > BM;
   CUtensorMap ma, mb;
   const uint64_t nt = (uint64_t)(NC / TILE_COLS);
   if (!make_map3(&ma, Zbar, TF32, TILE_COLS, fout, nt, C::BKE, BM)) return map_err(h, "weight-gradient adjoint");
   if (!make_map3(&mb, A, TF32, TILE_COLS, fin, nt, C::BKE, BN)) return map_err(h, "weight-gradient activations");
   TcParams p = base_params(fout, fin, (int)NC, NC, C::BKE, h->d_status);
+  if (two) p.m_tiles = (fout + 2 * BM - 1) / (2 * BM);
   p.nsplit = nsplit;
   p.kps = (p.k_iters + nsplit - 1) / nsplit;
   if ((p.k_iters + p.kps - 1) / p.kps != nsplit) {
@@ -719,7 +740,9 @@ pinn_status dw_impl(pinn_handle* h, const void* Zbar, const void* A, int fout, i
     return PINN_ERR_INVALID_ARG;
   }
   p.out32 = part;
-  return launch<TF32, TC_DW, false>(h, ma, ma, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles * nsplit), st);
+  const int grid = grid_for(h, p.m_tiles * p.n_tiles * nsplit);
+  if (two) return launch<TF32, TC_DW, true>(h, ma, ma, mb, mb, p, grid, st);
+  return launch<TF32, TC_DW, false>(h, ma, ma, mb, mb, p, grid, st);
 }
 
 }  // namespace
@@ -1074,6 +1097,7 @@ int adjdw_grid(const pinn_handle* h, int fin, int64_t NC) {
 
 bool tc_adjdw_supported(const pinn_handle* h, int li, int64_t NC) {
   if (h->spec.precision != PINN_BF16 || li < 1 || !tc_layer_supported(h, li, NC)) return false;
+  if (h->spec.flags & PINN_FLAG_UNFUSED_ADJOINT) return false;
   return h->layers[li].fout <= BN;   // the dW^T slab fits beside the adjoint accumulator
 }
 

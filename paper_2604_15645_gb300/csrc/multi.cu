@@ -11,10 +11,14 @@
 // step-dependent bias corrections) are written into the captured Adam node's
 // arguments before each replay, so a replay needs no re-capture.
 //
-// pinn_multi_autotune picks, per network, the faster of the two GEMM engines
-// (tcgen05 tiles of 128 features x 256 columns, or CUDA-core tiles of 64 x 256) by
-// timing both, and caches the choice per (width, depth, point-count bucket,
-// precision) in a JSON file.
+// pinn_multi_autotune picks, per network, the fastest kernel configuration by timing
+// each: tcgen05 with the fused adjoint + weight-gradient kernel, tcgen05 with separate
+// adjoint and weight-gradient kernels (weight-gradient tiles of 256 or of 128 output
+// rows), or the CUDA-core GEMMs (tiles of 64 x 256), and caches the choice per (width,
+// depth, point-count bucket, precision) in a JSON file.  Networks are spread over the
+// worker streams longest first (each to the stream with the least estimated work so far,
+// the estimate being the jet-GEMM FLOPs), so the big networks start at once and the
+// small ones fill in around them.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -47,7 +51,34 @@ struct pinn_multi {
 
 namespace {
 
-constexpr int kMaxStreams = 16;
+constexpr int kMaxStreams = 32;
+
+// Kernel configurations the autotuner chooses among (pinn_multi_set_config).
+enum NetConfig { CFG_TC = 0, CFG_CUDA_CORES = 1, CFG_TC_UNFUSED = 2, CFG_TC_UNFUSED_DW128 = 3, CFG_COUNT = 4 };
+const char* const kConfigNames[CFG_COUNT] = {"tc", "cuda_cores", "tc_unfused", "tc_unfused_dw128"};
+constexpr int32_t kConfigFlags = PINN_FLAG_CUDA_CORES | PINN_FLAG_UNFUSED_ADJOINT | PINN_FLAG_DW_ROWS_128;
+
+int32_t config_flags(int c) {
+  switch (c) {
+    case CFG_CUDA_CORES: return PINN_FLAG_CUDA_CORES;
+    case CFG_TC_UNFUSED: return PINN_FLAG_UNFUSED_ADJOINT;
+    case CFG_TC_UNFUSED_DW128: return PINN_FLAG_UNFUSED_ADJOINT | PINN_FLAG_DW_ROWS_128;
+    default: return 0;
+  }
+}
+int config_of(int32_t flags) {
+  if (flags & PINN_FLAG_CUDA_CORES) return CFG_CUDA_CORES;
+  if (flags & PINN_FLAG_UNFUSED_ADJOINT) return (flags & PINN_FLAG_DW_ROWS_128) ? CFG_TC_UNFUSED_DW128 : CFG_TC_UNFUSED;
+  return CFG_TC;
+}
+
+// Jet-GEMM work of network i on its batch (2 MAC per jet column and weight entry).
+double net_cost(const pinn_handle* h, const pinn_batch& b) {
+  const double cols = 4.0 * (double)(b.n_res + b.n_ic + b.n_bc);
+  double c = 0.0;
+  for (int l = h->first_gemm; l < h->L; ++l) c += 6.0 * h->layers[l].fin * h->layers[l].fout * cols;
+  return c;
+}
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -60,13 +91,16 @@ pinn_status set_err(pinn_multi* m, const char* msg) {
 // engines never invalidates the caller's buffer.
 pinn_status net_ws(pinn_handle* h, const pinn_batch& b, size_t* bytes) {
   const int32_t saved = h->spec.flags;
-  size_t a = 0, c = 0;
-  h->spec.flags = saved & ~PINN_FLAG_CUDA_CORES;
-  pinn_status s = pinn_workspace_bytes(h, b.n_res, b.n_ic, b.n_bc, &a);
-  h->spec.flags = saved | PINN_FLAG_CUDA_CORES;
-  if (!s) s = pinn_workspace_bytes(h, b.n_res, b.n_ic, b.n_bc, &c);
+  size_t most = 0;
+  pinn_status s = PINN_OK;
+  for (int c = 0; c < CFG_COUNT && !s; ++c) {
+    size_t x = 0;
+    h->spec.flags = (saved & ~kConfigFlags) | config_flags(c);
+    s = pinn_workspace_bytes(h, b.n_res, b.n_ic, b.n_bc, &x);
+    most = std::max(most, x);
+  }
   h->spec.flags = saved;
-  *bytes = align256(std::max(a, c));
+  *bytes = align256(most);
   return s;
 }
 
@@ -108,9 +142,16 @@ pinn_status enqueue_step(pinn_multi* m, const pinn_problem* probs, const pinn_ba
   const int ns = (int)m->streams.size();
   for (int k = 0; k < ns; ++k)
     if (cudaStreamWaitEvent(m->streams[k], m->fork, 0) != cudaSuccess) return PINN_ERR_CUDA;
-  for (int i = 0; i < m->n; ++i) {
+  // longest-processing-time-first: biggest networks first, each to the least loaded stream
+  std::vector<int> order(m->n);
+  std::vector<double> cost(m->n), load(ns, 0.0);
+  for (int i = 0; i < m->n; ++i) { order[i] = i; cost[i] = net_cost(m->nets[i], batches[i]); }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[k] += cost[i];
     pinn_status s = pinn_loss_grad(m->nets[i], &probs[i], &batches[i], d_p + m->poff[i], ws + ws_off[i], ws_sz[i],
-                                   d_loss + (int64_t)i * PINN_LOSS_TERMS, d_g + m->poff[i], m->streams[i % ns]);
+                                   d_loss + (int64_t)i * PINN_LOSS_TERMS, d_g + m->poff[i], m->streams[k]);
     if (s) {
       snprintf(m->err, sizeof(m->err), "network %d: %s", i, pinn_last_error(m->nets[i]));
       return s;
@@ -217,7 +258,20 @@ PINN_API pinn_status pinn_multi_set_ff_matrix(pinn_multi* m, int32_t net, const 
 PINN_API pinn_status pinn_multi_set_engine(pinn_multi* m, int32_t net, int32_t cuda_cores) {
   if (!m || net < 0 || net >= m->n) return PINN_ERR_INVALID_ARG;
   int32_t& f = m->nets[net]->spec.flags;
-  f = cuda_cores ? (f | PINN_FLAG_CUDA_CORES) : (f & ~PINN_FLAG_CUDA_CORES);
+  f = (f & ~kConfigFlags) | (cuda_cores ? PINN_FLAG_CUDA_CORES : 0);
+  return PINN_OK;
+}
+
+PINN_API pinn_status pinn_multi_set_config(pinn_multi* m, int32_t net, int32_t config) {
+  if (!m || net < 0 || net >= m->n || config < 0 || config >= CFG_COUNT) return PINN_ERR_INVALID_ARG;
+  int32_t& f = m->nets[net]->spec.flags;
+  f = (f & ~kConfigFlags) | config_flags(config);
+  return PINN_OK;
+}
+
+PINN_API pinn_status pinn_multi_get_config(const pinn_multi* m, int32_t net, int32_t* config) {
+  if (!m || !config || net < 0 || net >= m->n) return PINN_ERR_INVALID_ARG;
+  *config = config_of(m->nets[net]->spec.flags);
   return PINN_OK;
 }
 
@@ -323,8 +377,9 @@ PINN_API pinn_status pinn_multi_status_poll(pinn_multi* m, void* stream) {
 
 PINN_API const char* pinn_multi_last_error(const pinn_multi* m) { return m ? m->err : "NULL handle"; }
 
-// Autotuner: time both engines per (width, depth, point bucket, precision) and keep
-// the faster.  The cache file holds one JSON object of "key": "tc" | "cuda_cores".
+// Autotuner: time every applicable kernel configuration per (width, depth, point
+// bucket, precision) and keep the fastest.  The cache file holds one JSON object of
+// "key": "tc" | "cuda_cores" | "tc_unfused" | "tc_unfused_dw128".
 PINN_API pinn_status pinn_multi_autotune(pinn_multi* m, const pinn_problem* probs, const pinn_batch* batches,
                                          const float* d_params, void* d_ws, size_t ws_bytes, double* d_loss,
                                          float* d_grad, const char* cache_path, void* stream) {
@@ -334,12 +389,14 @@ PINN_API pinn_status pinn_multi_autotune(pinn_multi* m, const pinn_problem* prob
   pinn_status s = plan_ws(m, batches, off, sz, &total);
   if (s) return s;
   if (ws_bytes < total) return PINN_ERR_WORKSPACE;
-  std::map<std::string, int> cache;   // key -> 1 = CUDA cores, 0 = tensor cores
+  std::map<std::string, int> cache;   // key -> configuration
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "r")) {
       char line[256], k[128], v[32];
       while (fgets(line, sizeof(line), f))
-        if (sscanf(line, " \"%127[^\"]\" : \"%31[^\"]\"", k, v) == 2) cache[k] = strcmp(v, "cuda_cores") == 0 ? 1 : 0;
+        if (sscanf(line, " \"%127[^\"]\" : \"%31[^\"]\"", k, v) == 2)
+          for (int c = 0; c < CFG_COUNT; ++c)
+            if (strcmp(v, kConfigNames[c]) == 0) cache[k] = c;
       fclose(f);
     }
   }
@@ -362,15 +419,29 @@ PINN_API pinn_status pinn_multi_autotune(pinn_multi* m, const pinn_problem* prob
              h->spec.precision == PINN_BF16 ? "bf16" : h->spec.precision == PINN_TF32 ? "tf32" : "fp32");
     auto it = cache.find(key);
     if (it != cache.end()) {
-      pinn_multi_set_engine(m, i, it->second);
+      pinn_multi_set_config(m, i, it->second);
       continue;
     }
-    float best_ms[2] = {1e30f, 1e30f};
-    for (int eng = 0; eng < 2 && !s; ++eng) {
-      pinn_multi_set_engine(m, i, eng);
-      int32_t tc_layers = 0;
-      pinn_tensor_core_layers(h, b.n_res, b.n_ic, b.n_bc, &tc_layers);
-      if (eng == 0 && tc_layers == 0) continue;   // tensor cores do not apply to this network
+    // which configurations differ for this network: engines per layer under each
+    int32_t eng[CFG_COUNT][PINN_MAX_HIDDEN];
+    bool wide_dw = false;
+    for (int c = 0; c < CFG_COUNT; ++c) {
+      pinn_multi_set_config(m, i, c);
+      pinn_layer_engines(h, b.n_res, b.n_ic, b.n_bc, eng[c]);
+    }
+    for (int l = 0; l < h->L; ++l) wide_dw = wide_dw || (eng[CFG_TC_UNFUSED][l] == 1 && h->layers[l].fout > 128);
+    float best_ms[CFG_COUNT];
+    for (int c = 0; c < CFG_COUNT; ++c) best_ms[c] = 1e30f;
+    for (int c = 0; c < CFG_COUNT && !s; ++c) {
+      bool any_tc = false, same_as_tc = true;
+      for (int l = 0; l < h->L; ++l) {
+        any_tc = any_tc || eng[c][l] != 0;
+        same_as_tc = same_as_tc && eng[c][l] == eng[CFG_TC][l];
+      }
+      if (c != CFG_CUDA_CORES && !any_tc) continue;                  // tensor cores do not apply
+      if (c == CFG_TC_UNFUSED && same_as_tc) continue;              // nothing fused to undo
+      if (c == CFG_TC_UNFUSED_DW128 && (!wide_dw)) continue;         // every dW tile is 128 rows already
+      pinn_multi_set_config(m, i, c);
       for (int rep = 0; rep < 4 && !s; ++rep) {
         cudaEventRecord(e0, st);
         s = pinn_loss_grad(h, &probs[i], &b, d_params + m->poff[i], static_cast<char*>(d_ws) + off[i], sz[i],
@@ -379,11 +450,14 @@ PINN_API pinn_status pinn_multi_autotune(pinn_multi* m, const pinn_problem* prob
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0) best_ms[eng] = std::min(best_ms[eng], ms);
+        if (rep > 0) best_ms[c] = std::min(best_ms[c], ms);
       }
     }
-    const int choice = best_ms[1] < best_ms[0] ? 1 : 0;
-    pinn_multi_set_engine(m, i, choice);
+    int choice = 0;
+    for (int c = 1; c < CFG_COUNT; ++c)
+      if (best_ms[c] < best_ms[choice]) choice = c;
+    if (best_ms[choice] >= 1e30f) choice = CFG_CUDA_CORES;
+    pinn_multi_set_config(m, i, choice);
     cache[key] = choice;
   }
   cudaEventDestroy(e0);
@@ -397,7 +471,7 @@ PINN_API pinn_status pinn_multi_autotune(pinn_multi* m, const pinn_problem* prob
       fputs("{\n", f);
       size_t k = 0;
       for (const auto& kv : cache)
-        fprintf(f, "  \"%s\": \"%s\"%s\n", kv.first.c_str(), kv.second ? "cuda_cores" : "tc",
+        fprintf(f, "  \"%s\": \"%s\"%s\n", kv.first.c_str(), kConfigNames[kv.second],
                 ++k < cache.size() ? "," : "");
       fputs("}\n", f);
       fclose(f);

@@ -52,7 +52,7 @@ def test_struct_layout_matches_header():
 
 
 @pytest.mark.parametrize("field,value", [("pde", 7), ("n_hidden", 0), ("n_hidden", 17), ("ff_m", -1),
-                                         ("rwf", 2), ("precision", 5), ("flags", 8)])
+                                         ("rwf", 2), ("precision", 5), ("flags", 2), ("flags", 32)])
 def test_invalid_spec_rejected_on_host(lib, field, value):
     spec = _lib.make_spec(1, [64, 64], 8, True, _lib.PINN_BF16)
     setattr(spec, field, value)

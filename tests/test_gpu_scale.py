@@ -113,6 +113,7 @@ def test_cavity_at_scale_gradient_against_torch_float64(cuda_lib):
     print(f"cavity 8x512 full size vs torch-f64 on {idx.size} coordinates: torch fp32 {rel(gt32[idx], g64[idx]):.2e}, "
           f"library fp32 {rel(g32[idx], g64[idx]):.2e}, " +
           ", ".join(f"library bf16 value_split={vs} {rel(g[idx], g64[idx]):.2e}" for (_, vs), (_, g) in lib.items()))
+    print(report(check_blocks(g32, g64, w.spec, 1.0, "cavity 8x512 fp32 (report)")))
     assert abs(l32 - l64) <= TOL["fp32"] * abs(l64) and rel(g32, g64) <= TOL["fp32"]
     assert rel(gt32[idx], g64[idx]) <= 1e-3           # the paper's FP32 recipe, for context
     for (_, vs), (l16, g16) in lib.items():

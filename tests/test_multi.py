@@ -79,12 +79,12 @@ def test_multi_autotune_cache(cuda_lib, tmp_path):
     multi.autotune(params, grad, path)
     with open(path) as f:
         cache = json.load(f)
-    assert cache and all(v in ("tc", "cuda_cores") for v in cache.values())
-    first = multi.engines()
+    assert cache and all(v in api.PinnMulti.CONFIGS for v in cache.values())
+    first = multi.configs()
     for i in range(multi.n):
         multi.set_engine(i, i % 2)
     multi.autotune(params, grad, path)          # reads the cache, no re-timing
-    assert multi.engines() == first
+    assert multi.configs() == first
     # a step after tuning still matches the oracle
     m, v = torch.zeros_like(params), torch.zeros_like(params)
     loss = multi.train_step(params, grad, m, v, step=1)
@@ -93,3 +93,27 @@ def test_multi_autotune_cache(cuda_lib, tmp_path):
     rt, rg = run_oracle(spec, p, None, b, pr)
     assert_parity(loss[0].cpu().numpy(), grad[:multi.offsets[1]].cpu().numpy(), rt, rg, TOL["bf16"], "tuned net 0",
                   spec=spec)
+
+
+@pytest.mark.parametrize("config", ["tc", "cuda_cores", "tc_unfused", "tc_unfused_dw128"])
+def test_every_kernel_configuration_matches_oracle(cuda_lib, config):
+    """The configurations the autotuner chooses among (fused or separate adjoint and
+    weight gradient, 256- or 128-row weight-gradient tiles, CUDA cores) all give the
+    oracle's loss and gradient, on networks of the family with 256-wide layers."""
+    api, fam, multi, p0 = _setup(12, 1536, "bf16")
+    wide = [i for i, (s, _, _, _) in enumerate(fam) if s.widths[0] >= 128][:3]
+    assert wide
+    for i in range(multi.n):
+        multi.set_config(i, config)
+    assert multi.configs() == [config] * multi.n
+    params = torch.tensor(p0, device="cuda")
+    grad, m, v = (torch.zeros_like(params) for _ in range(3))
+    loss = multi.train_step(params, grad, m, v, step=1)
+    torch.cuda.synchronize()
+    assert multi.status_poll() == 0
+    g = grad.cpu().numpy().astype(np.float64)
+    for i in wide:
+        spec, p, b, pr = fam[i]
+        rt, rg = run_oracle(spec, p, None, b, pr)
+        assert_parity(loss[i].cpu().numpy(), g[multi.offsets[i]:multi.offsets[i + 1]], rt, rg, TOL["bf16"],
+                      f"{config} net {i} {spec.widths}", spec=spec)
