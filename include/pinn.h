@@ -195,8 +195,9 @@ PINN_API pinn_status pinn_graph_held(const pinn_handle* h, int32_t* held);
  * periodic activation sin(omega0 z) of Sec. 2.6 (Table 1), in every hidden layer.
  * A sine network keeps each hidden layer's pre-activation jets for the adjoint (one
  * more FP32 [w_l][4 N] array per layer, counted by pinn_workspace_bytes), because
- * the sign of cos(omega0 z) cannot be recovered from the stored sin; its jet GEMMs
- * run on CUDA cores (TF32 then computes in FP32; BF16 keeps BF16 activations).
+ * the sign of cos(omega0 z) cannot be recovered from the stored sin.  BF16 sine
+ * networks run their hidden jet GEMMs on tcgen05 tensor cores (separate adjoint and
+ * weight-gradient kernels); TF32 sine networks compute in FP32 on CUDA cores.
  * Unknown `act`, or omega0 not finite and > 0: PINN_ERR_INVALID_ARG. */
 #define PINN_ACT_TANH 0
 #define PINN_ACT_SINE 1

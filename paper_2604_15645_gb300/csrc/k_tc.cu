@@ -118,7 +118,11 @@ __device__ __forceinline__ void store_pm8(float* pm, int64_t c0, int M, int m, c
 }
 
 // ---- the kernel -----------------------------------------------------------------------
-template <bool TF32, int MODE, bool SPLIT>
+// SINE (BF16 forward / adjoint): the periodic activation sin(w0 z) instead of tanh.  Its
+// adjoint cannot be written in the activations (the sign of cos is lost), so the
+// forward epilogue also stores the pre-activation jets Z (FP32) and the adjoint
+// epilogue evaluates the rule from them.
+template <bool TF32, int MODE, bool SPLIT, bool SINE = false>
 __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
               const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
         }
       }
     };
-    if constexpr (MODE == TC_ADJ) {
+    if constexpr (MODE == TC_ADJ && !SINE) {
       if ((int)blockIdx.x < total) load_z(blockIdx.x, 0);
     }
 
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
       };
       auto process = [&](int u, float (&v)[4][UPTS]) {
         uint32_t zw[ZR][ZW];
-        if constexpr (MODE == TC_ADJ) {
+        if constexpr (MODE == TC_ADJ && !SINE) {
 #pragma unroll
           for (int r = 0; r < ZR; ++r)
 #pragma unroll
@@ -412,10 +416,17 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
           const float bias = p.e.bias[m];
 #pragma unroll
           for (int i = 0; i < UPTS; ++i) v[0][i] += bias;
+          if constexpr (SINE) {
+            // the pre-activation jets for the adjoint, FP32 [M][NC] tile-major
+            float* zo = p.e.zout + cbase;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) st_f32<UPTS>(zo + 64 * r, v[r]);
+          }
 #pragma unroll
           for (int i = 0; i < UPTS; ++i) {
             float z[4] = {v[0][i], v[1][i], v[2][i], v[3][i]}, a[4];
-            jet_fwd<FAST>(z, a, p.e.jet_mode);
+            if constexpr (SINE) jet_fwd_sine(z, a, p.e.jet_mode, p.e.omega0);
+            else jet_fwd<FAST>(z, a, p.e.jet_mode);
 #pragma unroll
             for (int r = 0; r < 4; ++r) v[r][i] = a[r];
           }
@@ -433,15 +444,36 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
             st_row(reinterpret_cast<T*>(p.e.alo_out) + loff(m, (int64_t)nb * TILE_PTS, p.M) + pc, lo);
           }
         } else if constexpr (MODE == TC_ADJ) {
+          if constexpr (SINE) {
+            // the rule from the stored pre-activation jets z of the layer below
+            const float* zr = p.e.zin + cbase;
 #pragma unroll
-          for (int i = 0; i < UPTS; ++i) {
-            float av[4];
+            for (int h8 = 0; h8 < UPTS / 8; ++h8) {
+              uint32_t zz[4][8];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) av[r] = raw_elem<T>(zw[r], i);
-            float ab[4] = {v[0][i], v[1][i], v[2][i], v[3][i]}, zb[4];
-            jet_adj_a(av, ab, zb, p.e.jet_mode);
+              for (int r = 0; r < 4; ++r) ld_global_256(zr + 64 * r + 8 * h8, zz[r]);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) v[r][i] = zb[r];
+              for (int i = 0; i < 8; ++i) {
+                float z[4] = {__uint_as_float(zz[0][i]), __uint_as_float(zz[1][i]), __uint_as_float(zz[2][i]),
+                              __uint_as_float(zz[3][i])};
+                const int k = 8 * h8 + i;
+                float ab[4] = {v[0][k], v[1][k], v[2][k], v[3][k]}, zb[4];
+                jet_adj_sine(z, ab, zb, p.e.jet_mode, p.e.omega0);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) v[r][k] = zb[r];
+              }
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < UPTS; ++i) {
+              float av[4];
+#pragma unroll
+              for (int r = 0; r < 4; ++r) av[r] = raw_elem<T>(zw[r], i);
+              float ab[4] = {v[0][i], v[1][i], v[2][i], v[3][i]}, zb[4];
+              jet_adj_a(av, ab, zb, p.e.jet_mode);
+#pragma unroll
+              for (int r = 0; r < 4; ++r) v[r][i] = zb[r];
+            }
           }
           T* zbo = reinterpret_cast<T*>(p.e.out) + cbase;
 #pragma unroll
@@ -590,11 +622,11 @@ bool tc_map3(CUtensorMap* m, const void* base, bool fp32, uint64_t tcols, uint64
 
 namespace {
 
-template <bool TF32, int MODE, bool SPLIT>
+template <bool TF32, int MODE, bool SPLIT, bool SINE = false>
 pinn_status launch(pinn_handle* h, const CUtensorMap& a, const CUtensorMap& a2, const CUtensorMap& b,
                    const CUtensorMap& blo, const TcParams& p, int grid, cudaStream_t st) {
   using C = Cfg<TF32, MODE, SPLIT>;
-  auto kern = k_tc_gemm<TF32, MODE, SPLIT>;
+  auto kern = k_tc_gemm<TF32, MODE, SPLIT, SINE>;
   static bool attr_set = false;   // per instantiation
   if (!attr_set) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) != cudaSuccess) {
@@ -630,7 +662,8 @@ void tc_init(pinn_handle* h) {
 
 bool tc_layer_supported(const pinn_handle* h, int li, int64_t NC) {
   if (!g_encode || h->spec.precision == PINN_FP32 || (h->spec.flags & PINN_FLAG_CUDA_CORES)) return false;
-  if (h->act != PINN_ACT_TANH) return false;   // the tensor-core epilogues carry the tanh jet only
+  // the tensor-core epilogues carry the tanh jet, and (BF16) the sine jet
+  if (h->act != PINN_ACT_TANH && !(h->act == PINN_ACT_SINE && h->spec.precision == PINN_BF16)) return false;
   if (NC % BN) return false;
   const int fin = h->layers[li].fin, fout = h->layers[li].fout;
   // TMA row strides must be multiples of 16 bytes: fin and fout multiples of 8 elements.
@@ -697,7 +730,10 @@ pinn_status fwd_impl(pinn_handle* h, const void* W, const void* Wlo, const void*
   TcParams p = base_params(fout, (int)NC, fin, NC, C::BKE, h->d_status);
   p.e = e;
   p.wlo_values_only = (!TF32 && (h->spec.flags & PINN_FLAG_BF16_VALUE_SPLIT)) ? 1 : 0;
-  return launch<TF32, TC_FWD, true>(h, ma, ma2, mb, mlo, p, grid_for(h, p.m_tiles * p.n_tiles), st);
+  const int grid = grid_for(h, p.m_tiles * p.n_tiles);
+  if constexpr (!TF32)
+    if (h->act == PINN_ACT_SINE) return launch<TF32, TC_FWD, true, true>(h, ma, ma2, mb, mlo, p, grid, st);
+  return launch<TF32, TC_FWD, true>(h, ma, ma2, mb, mlo, p, grid, st);
 }
 
 template <bool TF32>
@@ -719,7 +755,10 @@ pinn_status adj_impl(pinn_handle* h, const void* WT, const void* WTlo, const voi
   }
   TcParams p = base_params(fin, (int)NC, fout, NC, C::BKE, h->d_status);
   p.e = e;
-  return launch<TF32, TC_ADJ, SPLIT>(h, ma, ma2, mb, mb, p, grid_for(h, p.m_tiles * p.n_tiles), st);
+  const int grid = grid_for(h, p.m_tiles * p.n_tiles);
+  if constexpr (!TF32)
+    if (h->act == PINN_ACT_SINE) return launch<TF32, TC_ADJ, SPLIT, true>(h, ma, ma2, mb, mb, p, grid, st);
+  return launch<TF32, TC_ADJ, SPLIT>(h, ma, ma2, mb, mb, p, grid, st);
 }
 
 template <bool TF32>
@@ -1098,6 +1137,7 @@ int adjdw_grid(const pinn_handle* h, int fin, int64_t NC) {
 bool tc_adjdw_supported(const pinn_handle* h, int li, int64_t NC) {
   if (h->spec.precision != PINN_BF16 || li < 1 || !tc_layer_supported(h, li, NC)) return false;
   if (h->spec.flags & PINN_FLAG_UNFUSED_ADJOINT) return false;
+  if (h->act != PINN_ACT_TANH) return false;   // the fused epilogue carries the tanh jet only
   return h->layers[li].fout <= BN;   // the dW^T slab fits beside the adjoint accumulator
 }
 

@@ -75,7 +75,10 @@ def test_sine_workspace_and_engine(cuda_lib):
     tanh_net = api.PinnNet.from_spec(w.spec, "bf16")
     sine_net = api.PinnNet.from_spec(_sine(w.spec, 1.0), "bf16")
     assert tanh_net.tensor_core_layers(b.n_res, 0, b.n_bc) == len(w.spec.widths)
-    assert sine_net.tensor_core_layers(b.n_res, 0, b.n_bc) == 0
+    # BF16 sine networks run on tcgen05 too, with separate adjoint and weight-gradient
+    # kernels (the fused one carries the tanh rule only)
+    assert sine_net.tensor_core_layers(b.n_res, 0, b.n_bc) == len(w.spec.widths)
+    assert 2 not in sine_net.layer_engines(b.n_res, 0, b.n_bc) and 2 in tanh_net.layer_engines(b.n_res, 0, b.n_bc)
     # on the same (CUDA-core, FP32) engine, one FP32 pre-activation jet array per hidden
     # layer on top of the tanh workspace
     w.spec.activation = "tanh"
@@ -106,3 +109,22 @@ def test_sine_chunked_matches_one_pass(cuda_lib):
     torch.cuda.synchronize()
     assert abs(float(t1[0]) - float(t2[0])) <= 1e-5 * abs(float(t1[0]))
     assert float((g1 - g2).norm() / g1.norm()) < 1e-5
+
+
+@pytest.mark.parametrize("name,widths", [("ns_cavity_6x256", [128] * 4), ("burgers1d_4x64", [64] * 4)])
+def test_sine_bf16_runs_on_tensor_cores(cuda_lib, name, widths):
+    """BF16 sine networks run their hidden jet GEMMs on tcgen05 (the forward epilogue
+    applies the sine jet rule and stores the pre-activations, the adjoint evaluates the
+    rule from them); FP32 sine networks stay on CUDA cores."""
+    from paper_2604_15645_gb300 import api
+    w, p, B, b = make_workload(name, n_res=1000, n_ic=120, n_bc=90, random_bias=0.1)
+    w.spec.widths = widths
+    _sine(w.spec, 2.0)
+    first_gemm = 0 if w.spec.ff_m else 1
+    for precision, expect in (("bf16", len(widths) - first_gemm), ("fp32", 0)):
+        net = api.PinnNet.from_spec(w.spec, precision)
+        assert net.tensor_core_layers(b.n_res, b.n_ic, b.n_bc) == expect, precision
+    p = init_params(w.spec, 8, 0.1)
+    gt, gg = run_gpu(w.spec, p, B, b, w.problem, "bf16")
+    rt, rg = run_oracle(w.spec, p, B, b, w.problem)
+    assert_parity(gt, gg, rt, rg, TOL["bf16"], f"sine {name} bf16 tensor cores", spec=w.spec)

@@ -117,3 +117,44 @@ def test_every_kernel_configuration_matches_oracle(cuda_lib, config):
         rt, rg = run_oracle(spec, p, None, b, pr)
         assert_parity(loss[i].cpu().numpy(), g[multi.offsets[i]:multi.offsets[i + 1]], rt, rg, TOL["bf16"],
                       f"{config} net {i} {spec.widths}", spec=spec)
+
+
+def test_full_family_every_network_against_torch_float64(cuda_lib):
+    """The benchmark's 64-network family at its full sizes (widths 32-256, depths 3-6,
+    1,024-65,536 interior points each) after autotuning: one training step's loss and
+    gradient of every network against the paper's method run in float64 on the GPU
+    (torch double-backward autograd), and against the oracle on each network's first
+    256 interior points plus its initial and boundary sets (a separate call)."""
+    from paper_2604_15645_gb300 import api
+    from gpu_helpers import torch_loss_grad
+    fam = make_family(64)
+    multi = api.PinnMulti([s for s, _, _, _ in fam], "bf16")
+    multi.set_inputs([api.DeviceBatch.from_host(b) for _, _, b, _ in fam],
+                     [api.make_problem(pr.nu) for _, _, _, pr in fam])
+    p0 = np.concatenate([p for _, p, _, _ in fam]).astype(np.float32)
+    params = torch.tensor(p0, device="cuda")
+    grad, m, v = (torch.zeros_like(params) for _ in range(3))
+    multi.autotune(params, grad)
+    loss = multi.train_step(params, grad, m, v, step=1)
+    torch.cuda.synchronize()
+    assert multi.status_poll() == 0
+    L = loss.cpu().numpy()
+    g = grad.cpu().numpy().astype(np.float64)
+    off = multi.offsets
+    worst = 0.0
+    for i, (spec, p, b, pr) in enumerate(fam):
+        l64, g64 = torch_loss_grad(spec, p, None, b, pr, torch.float64)
+        assert abs(L[i][0] - l64) <= TOL["bf16"] * abs(l64), (i, L[i][0], l64)
+        e = rel(g[off[i]:off[i + 1]], g64)
+        worst = max(worst, e)
+        assert e <= TOL["bf16"], (i, spec.widths, b.n_res, e)
+    print(f"64 networks, full sizes: worst gradient error against torch float64 {worst:.2e}")
+    # the oracle on subsets: one network call per member on its leading 256 interior points
+    for i in range(0, 64, 8):
+        spec, p, b, pr = fam[i]
+        sub = b.subset(256)
+        net = api.PinnNet.from_spec(spec, "bf16")
+        t, gg = net.loss_grad(torch.tensor(p, device="cuda"), api.DeviceBatch.from_host(sub), api.make_problem(pr.nu))
+        rt, rg = run_oracle(spec, p, None, sub, pr)
+        assert_parity(t.cpu().numpy(), gg.cpu().numpy().astype(np.float64), rt, rg, TOL["bf16"], f"family net {i}",
+                      spec=spec)
