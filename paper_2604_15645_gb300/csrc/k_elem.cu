@@ -235,12 +235,27 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
   return s;
 }
 
+// Compensated FP32 accumulation (Knuth's TwoSum): s + c tracks the exact sum of
+// the added values to about 2^-48 relative, using the FP32 pipe; it is turned into
+// FP64 once per thread, so the FP64 work of the final reductions stays small.
+struct Acc2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // Residual and seed for one point from its output jets U[c][r] (bias included).
 // k: the interior seed scale (k_pde, or the point's causal segment scale); rr: the
-// point's squared residual per equation (interior points).
-template <int D>
+// point's squared residual per equation (interior points); lacc (FP64, or FP32 for a
+// few points at a time) gathers the squared errors per loss term.
+template <int D, typename LT>
 __device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_t idx, float k, float U[3][4],
-                                               float Ub[3][4], double lacc[5], float rr[3]) {
+                                               float Ub[3][4], LT lacc[5], float rr[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -251,20 +266,20 @@ __device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_
     if (a.pde == PINN_BURGERS_1D) {
       // rows [u, u_x, u_t, u_xx]
       const float r = U[0][2] + U[0][0] * U[0][1] - nu * U[0][3];
-      lacc[0] += (double)r * r; rr[0] = r * r;
+      lacc[0] += (LT)r * r; rr[0] = r * r;
       const float g2 = 2.f * k * r;
       Ub[0][0] = g2 * U[0][1]; Ub[0][1] = g2 * U[0][0]; Ub[0][2] = g2; Ub[0][3] = -nu * g2;
     } else if (a.pde == PINN_ADVECTION_1D) {
       // u_t + c u_x with c = nu (Sec. 4.1)
       const float r = fmaf(nu, U[0][1], U[0][2]);
-      lacc[0] += (double)r * r; rr[0] = r * r;
+      lacc[0] += (LT)r * r; rr[0] = r * r;
       const float g2 = 2.f * k * r;
       Ub[0][1] = nu * g2; Ub[0][2] = g2;
     } else if (a.pde == PINN_ALLEN_CAHN_1D) {
       // u_t - eps u_xx + 5 u^3 - 5 u with eps = nu (Sec. 4.2)
       const float u = U[0][0];
       const float r = U[0][2] - nu * U[0][3] + 5.f * u * (u * u - 1.f);
-      lacc[0] += (double)r * r; rr[0] = r * r;
+      lacc[0] += (LT)r * r; rr[0] = r * r;
       const float g2 = 2.f * k * r;
       Ub[0][0] = g2 * (15.f * u * u - 5.f); Ub[0][2] = g2; Ub[0][3] = -nu * g2;
     } else if (a.pde == PINN_NS_STEADY_2D) {
@@ -273,7 +288,7 @@ __device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_
       const float r1 = u * U[0][1] + v * U[0][2] + U[2 % D][1] - nu * U[0][3];
       const float r2 = u * U[1 % D][1] + v * U[1 % D][2] + U[2 % D][2] - nu * U[1 % D][3];
       const float r3 = U[0][1] + U[1 % D][2];
-      lacc[0] += (double)r1 * r1; lacc[1] += (double)r2 * r2; lacc[2] += (double)r3 * r3;
+      lacc[0] += (LT)r1 * r1; lacc[1] += (LT)r2 * r2; lacc[2] += (LT)r3 * r3;
       rr[0] = r1 * r1; rr[1] = r2 * r2; rr[2] = r3 * r3;
       const float g1 = 2.f * k * r1, g2 = 2.f * k * r2, g3 = 2.f * k * r3;
       Ub[0][0] = g1 * U[0][1] + g2 * U[1 % D][1];
@@ -286,7 +301,7 @@ __device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_
       const float r1 = U[0][3] - (U[2 % D][1] - U[1 % D][2]);
       const float r2 = U[1 % D][3] + U[0][2];
       const float r3 = U[2 % D][3] - U[0][1];
-      lacc[0] += (double)r1 * r1; lacc[1] += (double)r2 * r2; lacc[2] += (double)r3 * r3;
+      lacc[0] += (LT)r1 * r1; lacc[1] += (LT)r2 * r2; lacc[2] += (LT)r3 * r3;
       rr[0] = r1 * r1; rr[1] = r2 * r2; rr[2] = r3 * r3;
       const float g1 = 2.f * k * r1, g2 = 2.f * k * r2, g3 = 2.f * k * r3;
       Ub[0][3] = g1; Ub[2 % D][1] = -g1; Ub[1 % D][2] = g1;
@@ -303,7 +318,7 @@ __device__ __forceinline__ void point_residual(const OutArgs& a, int set, int64_
     for (int c = 0; c < D; ++c) {
       if (mask >> c & 1u) {
         const float err = U[c][0] - gt[(int64_t)c * n + idx];
-        lacc[ic ? 3 : 4] += (double)err * err;
+        lacc[ic ? 3 : 4] += (LT)err * err;
         Ub[c][0] = 2.f * k * err;
       }
     }
@@ -358,7 +373,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   const int pg = lane >> 3, sl = lane & 7;
   const int q0 = 16 * warp + 4 * pg;               // first of this thread's 4 points in the tile
   const int64_t ntiles = a.NP / TILE_PTS;
-  double acc[5] = {0, 0, 0, 0, 0};
+  Acc2 acc[5];   // compensated FP32 running sums (FP64 is a slow pipe on this part)
   float dbo[3] = {0.f, 0.f, 0.f};                 // output bias gradient (value-row seeds)
   // temporal causality, first pass: this block's segment sums (3 equations + count),
   // accumulated by one thread over the tile's points in a fixed order
@@ -412,7 +427,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
           U[j][c][r] = x;
         }
     float Ub[4][3][4];
-    double lacc[5] = {0, 0, 0, 0, 0};
+    float lacc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     int segj[4];
     float rrj[4][3];
 #pragma unroll
@@ -433,7 +448,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
       point_residual<D>(a, set, idx, kp, U[j], Ub[j], lacc, rrj[j]);
     }
     if (sl == 0)
-      for (int i = 0; i < 5; ++i) acc[i] += lacc[i];
+      for (int i = 0; i < 5; ++i) acc[i].add(lacc[i]);
     if (a.segpart) {   // uniform over the block
       if (sl == 0)
 #pragma unroll
@@ -524,7 +539,7 @@ __global__ void __launch_bounds__(OUT_THREADS) k_out_loss(OutArgs a) {
   }
   __shared__ double sh[OUT_THREADS / 32];
   for (int i = 0; i < 5; ++i) {
-    const double s = block_sum_d(acc[i], sh);
+    const double s = block_sum_d(acc[i].value(), sh);
     if (threadIdx.x == 0) a.losspart[(int64_t)blockIdx.x * 8 + i] = s;
   }
   if (a.segpart) {
@@ -612,7 +627,10 @@ __device__ __forceinline__ double cons_sum_d(double v, double* sh) {
   return s;
 }
 
-template <int D>
+// D outputs, jet rule MODE and the presence of the value-row low half (LO) are
+// compile-time, and the width is a multiple of the 32-feature chunk: the unrolled
+// per-feature loops carry no branches, so their loads and arithmetic interleave.
+template <int D, int MODE, bool LO>
 __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_constant__ CUtensorMap mapA,
                                                             const __grid_constant__ CUtensorMap mapLo, OutArgs a) {
   extern __shared__ uint8_t ot_raw[];
@@ -647,9 +665,8 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
   __syncthreads();
 
   const int64_t ntiles = a.NP / TILE_PTS;
-  const int nchunks = (w + OT_FC - 1) / OT_FC;
+  const int nchunks = w / OT_FC;
   const int passes = a.want_grad ? 2 : 1;
-  const bool lo = a.ALlo != nullptr;
 
   if (warp == OT_CONS / 32) {
     // ---------------------------------------------------------------- producer
@@ -663,11 +680,11 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
           for (int k = 0; k < nchunks; ++k) {
             if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.status, OT_WAIT_NS)) break;
             uint8_t* sb = ring + stage * OT_STAGE;
-            mbar_expect_tx(&full[stage], (lo ? 5 : 4) * OT_ROWB);
+            mbar_expect_tx(&full[stage], (LO ? 5 : 4) * OT_ROWB);
             armed[stage] = (int)phase + 1;
 #pragma unroll
             for (int r = 0; r < 4; ++r) tma_load_3d(sb + r * OT_ROWB, &mapA, &full[stage], 64 * r, OT_FC * k, T0);
-            if (lo) tma_load_3d(sb + 4 * OT_ROWB, &mapLo, &full[stage], 0, OT_FC * k, T0);
+            if constexpr (LO) tma_load_3d(sb + 4 * OT_ROWB, &mapLo, &full[stage], 0, OT_FC * k, T0);
             if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
           }
       }
@@ -687,7 +704,9 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
   __nv_bfloat16* Zb = reinterpret_cast<__nv_bfloat16*>(a.Zbar);
   const int pg = lane >> 3, sl = lane & 7;
   const int q0 = 16 * warp + 4 * pg;
-  double acc[5] = {0, 0, 0, 0, 0};
+  // squared errors: FP32 per tile (four points), compensated FP32 across tiles, FP64
+  // only in the block's final sum (FP64 is a slow pipe on this part)
+  Acc2 acc[5];
   float dbo[3] = {0.f, 0.f, 0.f};
   int stage = 0;
   uint32_t phase = 0;
@@ -709,24 +728,22 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
 #pragma unroll
       for (int e = 0; e < OT_FC / 8; ++e) {
         const int fi = sl + 8 * e, f = OT_FC * k + fi;
-        if (f < w) {
-          float v[4][4];
+        float v[4][4];
 #pragma unroll
-          for (int r = 0; r < 4; ++r) ot_load4(sb + r * OT_ROWB, fi, q0 & 63, v[r]);
-          if (lo) {
-            float l4[4];
-            ot_load4(sb + 4 * OT_ROWB, fi, q0 & 63, l4);
+        for (int r = 0; r < 4; ++r) ot_load4(sb + r * OT_ROWB, fi, q0 & 63, v[r]);
+        if constexpr (LO) {
+          float l4[4];
+          ot_load4(sb + 4 * OT_ROWB, fi, q0 & 63, l4);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[0][j] += l4[j];
-          }
+          for (int j = 0; j < 4; ++j) v[0][j] += l4[j];
+        }
 #pragma unroll
-          for (int c = 0; c < D; ++c) {
-            const float wc = sW[c * w + f];
+        for (int c = 0; c < D; ++c) {
+          const float wc = sW[c * w + f];
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+          for (int j = 0; j < 4; ++j)
 #pragma unroll
-              for (int r = 0; r < 4; ++r) U[j][c][r] = fmaf(wc, v[r][j], U[j][c][r]);
-          }
+            for (int r = 0; r < 4; ++r) U[j][c][r] = fmaf(wc, v[r][j], U[j][c][r]);
         }
       }
       mbar_arrive(&empty[stage]);
@@ -746,7 +763,7 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
           U[j][c][r] = x;
         }
     float Ub[4][3][4];
-    double lacc[5] = {0, 0, 0, 0, 0};
+    float lacc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     int segj[4];
     float rrj[4][3];
 #pragma unroll
@@ -767,7 +784,7 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
       point_residual<D>(a, set, idx, kp, U[j], Ub[j], lacc, rrj[j]);
     }
     if (sl == 0)
-      for (int i = 0; i < 5; ++i) acc[i] += lacc[i];
+      for (int i = 0; i < 5; ++i) acc[i].add(lacc[i]);
     if (a.segpart) {
       if (sl == 0)
 #pragma unroll
@@ -796,14 +813,12 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
       const uint8_t* sb = ring + stage * OT_STAGE;
 #pragma unroll
       for (int e = 0; e < OT_FC / 8; ++e) {
-        const int fi0 = sl + 8 * e;
-        const bool live = OT_FC * k + fi0 < w;
-        const int fi = live ? fi0 : (w - 1 - OT_FC * k);   // a slice past the width re-reads the last feature
+        const int fi = sl + 8 * e;
         const int f = OT_FC * k + fi;
         float av[4][4], zb[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) ot_load4(sb + r * OT_ROWB, fi, q0 & 63, av[r]);
-        if (lo) {
+        if constexpr (LO) {
           float l4[4];
           ot_load4(sb + 4 * OT_ROWB, fi, q0 & 63, l4);
 #pragma unroll
@@ -818,7 +833,7 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
             for (int r = 0; r < 4; ++r) g = fmaf(Ub[j][c][r], av[r][j], g);
           g += __shfl_xor_sync(0xffffffffu, g, 8);
           g += __shfl_xor_sync(0xffffffffu, g, 16);
-          if (pg == 0 && live) sdw[(warp * D + c) * w + f] += g;
+          if (pg == 0) sdw[(warp * D + c) * w + f] += g;
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -831,19 +846,18 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
           }
 #pragma unroll
           for (int r = 0; r < 4; ++r) zz[r] = av[r][j];
-          jet_adj_a(zz, ab, o, a.jet_mode);
+          jet_adj_a(zz, ab, o, MODE);
 #pragma unroll
           for (int r = 0; r < 4; ++r) zb[r][j] = o[r];
         }
         __nv_bfloat16* zbrow = Zb + toff(f, cb, w);
-        if (live)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) store4_stream<__nv_bfloat16>(zbrow + 64 * r, zb[r]);
+        for (int r = 0; r < 4; ++r) store4_stream<__nv_bfloat16>(zbrow + 64 * r, zb[r]);
         if (a.dbhid) {
           float s = (zb[0][0] + zb[0][1]) + (zb[0][2] + zb[0][3]);
           s += __shfl_xor_sync(0xffffffffu, s, 8);
           s += __shfl_xor_sync(0xffffffffu, s, 16);
-          if (pg == 0 && live) sdb[warp * w + f] += s;
+          if (pg == 0) sdb[warp * w + f] += s;
         }
       }
       mbar_arrive(&empty[stage]);
@@ -851,7 +865,7 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
     }
   }
   for (int i = 0; i < 5; ++i) {
-    const double s = cons_sum_d(acc[i], sh);
+    const double s = cons_sum_d(acc[i].value(), sh);
     if (threadIdx.x == 0) a.losspart[(int64_t)blockIdx.x * 8 + i] = s;
   }
   if (a.segpart) {
@@ -890,8 +904,10 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
 }
 
 // Whether the TMA-staged output kernel applies: BF16 tanh networks whose last hidden
-// layer is at most 512 wide.
-bool out_loss_tma_ok(int prec, int act, int w) { return prec == PINN_BF16 && act == PINN_ACT_TANH && w <= 512; }
+// layer is at most 512 wide and a multiple of 32 features.
+bool out_loss_tma_ok(int prec, int act, int w) {
+  return prec == PINN_BF16 && act == PINN_ACT_TANH && w <= 512 && w % OT_FC == 0;
+}
 
 int out_loss_tma_blocks(int64_t NP, int sm_count) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(NP / TILE_PTS, 2 * (int64_t)std::max(sm_count, 1)));
@@ -902,10 +918,10 @@ static size_t ot_smem(int w, int d_out) {
          sizeof(float) * (size_t)w * (d_out * (1 + OT_CONS / 32) + OT_CONS / 32) + 8 + 8 * 2 * OT_STAGES + 16;
 }
 
-template <int D>
+template <int D, int MODE, bool LO>
 cudaError_t out_loss_tma_launch(const CUtensorMap& ma, const CUtensorMap& ml, const OutArgs& a, int nblocks,
                                 cudaStream_t st) {
-  auto kern = k_out_loss_tma<D>;
+  auto kern = k_out_loss_tma<D, MODE, LO>;
   const size_t smem = ot_smem(a.w, D);
   static size_t reserved = 0;
   if (smem > reserved) {
@@ -924,7 +940,17 @@ cudaError_t launch_out_loss_tma(const OutArgs& a, int nblocks, cudaStream_t st) 
   if (!tc_map3(&ma, a.AL, false, TILE_COLS, (uint64_t)a.w, nt, 64, OT_FC)) return cudaErrorNotSupported;
   ml = ma;
   if (a.ALlo && !tc_map3(&ml, a.ALlo, false, TILE_PTS, (uint64_t)a.w, nt, 64, OT_FC)) return cudaErrorNotSupported;
-  return a.d_out == 1 ? out_loss_tma_launch<1>(ma, ml, a, nblocks, st) : out_loss_tma_launch<3>(ma, ml, a, nblocks, st);
+  const bool lo = a.ALlo != nullptr;
+  if (a.d_out == 1 && a.jet_mode == JET_BURGERS)
+    return lo ? out_loss_tma_launch<1, JET_BURGERS, true>(ma, ml, a, nblocks, st)
+              : out_loss_tma_launch<1, JET_BURGERS, false>(ma, ml, a, nblocks, st);
+  if (a.d_out == 3 && a.jet_mode == JET_NS)
+    return lo ? out_loss_tma_launch<3, JET_NS, true>(ma, ml, a, nblocks, st)
+              : out_loss_tma_launch<3, JET_NS, false>(ma, ml, a, nblocks, st);
+  if (a.d_out == 3 && a.jet_mode == JET_MAXWELL)
+    return lo ? out_loss_tma_launch<3, JET_MAXWELL, true>(ma, ml, a, nblocks, st)
+              : out_loss_tma_launch<3, JET_MAXWELL, false>(ma, ml, a, nblocks, st);
+  return cudaErrorNotSupported;
 }
 
 template <typename T, int D, bool FAST, bool SINE>
@@ -1026,20 +1052,6 @@ void launch_row_reduce(const void* Zbar, bool fp32_in, int M, int64_t NP, int64_
 // (Eq. 15): dV = exp(s) dW, ds_i = sum_j dW_ij W_ij, plus db.  One block per
 // (output row, layer).
 // ------------------------------------------------------------------------------------
-// Compensated FP32 accumulation (Knuth's TwoSum): s + c tracks the exact sum of
-// the added values to about 2^-48 relative, using the FP32 pipe; it is turned into
-// FP64 once per thread, so the FP64 work of the final reductions stays small.
-struct Acc2 {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = s + x;
-    const float bp = t - s;
-    c += (s - (t - bp)) + (x - bp);
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-
 // Deterministic block sum of N doubles per thread (fixed assignment and order).
 template <int N>
 __device__ __forceinline__ void block_sum_n(double v[N], double (*sh)[N]) {
@@ -1058,9 +1070,14 @@ __device__ __forceinline__ void put_grad(const FinalizeArgs& a, int64_t idx, flo
   a.grad[idx] = a.accumulate ? a.grad[idx] + v : v;
 }
 
+// Each block is bound by memory latency, not bandwidth: its threads keep 8 partial
+// loads in flight (the splits of a row then take a few memory latencies instead of
+// one per split), the bias partials are read as float4, and 128-thread blocks at
+// most 40 registers keep the whole grid resident in one wave.
 constexpr int FIN_THREADS = 128;
+constexpr int FIN_UNROLL = 8;
 
-__global__ void __launch_bounds__(FIN_THREADS) k_finalize_grad(FinalizeArgs a) {
+__global__ void __launch_bounds__(FIN_THREADS, 12) k_finalize_grad(FinalizeArgs a) {
   const int l = blockIdx.y, i = blockIdx.x;
   const int fin = a.fin[l], fout = a.fout[l];
   if (i >= fout) return;
@@ -1075,11 +1092,30 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize_grad(FinalizeArgs a) {
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   {
     Acc2 ab[4];
-    for (int p = threadIdx.x; p < nbp; p += blockDim.x) {
-      const float* q = dbp + ((int64_t)i * nbp + p) * dbs;
-      ab[0].add(q[0]);
-      if (raw)
-        for (int j = 0; j < fin && j < 3; ++j) ab[1 + j].add(q[1 + j]);
+    if (!raw && (nbp & 3) == 0) {
+      // one row's bias partials are contiguous: float4 p4 = t, t + T, ..., each
+      // summed in element order
+      const float4* q4 = reinterpret_cast<const float4*>(dbp + (int64_t)i * nbp);
+      const int n4 = nbp >> 2, T = blockDim.x;
+      int p4 = threadIdx.x;
+      for (; p4 + 3 * T < n4; p4 += 4 * T) {
+        float4 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = __ldcs(q4 + p4 + u * T);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { ab[0].add(x[u].x); ab[0].add(x[u].y); ab[0].add(x[u].z); ab[0].add(x[u].w); }
+      }
+      for (; p4 < n4; p4 += T) {
+        const float4 x = __ldcs(q4 + p4);
+        ab[0].add(x.x); ab[0].add(x.y); ab[0].add(x.z); ab[0].add(x.w);
+      }
+    } else {
+      for (int p = threadIdx.x; p < nbp; p += blockDim.x) {
+        const float* q = dbp + ((int64_t)i * nbp + p) * dbs;
+        ab[0].add(q[0]);
+        if (raw)
+          for (int j = 0; j < fin && j < 3; ++j) ab[1 + j].add(q[1 + j]);
+      }
     }
     v[1] = ab[0].value();
     for (int j = 0; j < 3; ++j) v[2 + j] = ab[1 + j].value();
@@ -1099,9 +1135,19 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize_grad(FinalizeArgs a) {
       if (g < G) {
         const float* base = part + (int64_t)i * fin + 4 * q;
         Acc2 a0, a1, a2, a3;
-#pragma unroll 4
-        for (int s = g; s < ns; s += G) {
-          const float4 x = *reinterpret_cast<const float4*>(base + s * sstride);
+        // splits g, g + G, g + 2G, ... in that order; the loads of FIN_UNROLL splits
+        // are issued before any of them is added (the partials are read once: streaming)
+        int s = g;
+        for (; s + (FIN_UNROLL - 1) * G < ns; s += FIN_UNROLL * G) {
+          float4 x[FIN_UNROLL];
+#pragma unroll
+          for (int u = 0; u < FIN_UNROLL; ++u)
+            x[u] = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)(s + u * G) * sstride));
+#pragma unroll
+          for (int u = 0; u < FIN_UNROLL; ++u) { a0.add(x[u].x); a1.add(x[u].y); a2.add(x[u].z); a3.add(x[u].w); }
+        }
+        for (; s < ns; s += G) {
+          const float4 x = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)s * sstride));
           a0.add(x.x); a1.add(x.y); a2.add(x.z); a3.add(x.w);
         }
         d[0] = a0.value(); d[1] = a1.value(); d[2] = a2.value(); d[3] = a3.value();
