@@ -634,13 +634,15 @@ template <int D, int MODE, bool LO>
 __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_constant__ CUtensorMap mapA,
                                                             const __grid_constant__ CUtensorMap mapLo, OutArgs a) {
   extern __shared__ uint8_t ot_raw[];
-  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ot_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned by offsetting the shared array itself (not through an integer
+  // round trip), so the compiler keeps every access below in the shared window
+  uint8_t* ring = ot_raw + ((1024u - (smem_u32(ot_raw) & 1023u)) & 1023u);
   const int w = a.w;
   float* sW = reinterpret_cast<float*>(ring + OT_STAGES * OT_STAGE);   // [D][w] output weights
   float* sdw = sW + D * w;                                            // [4 warps][D][w] dW accumulators
   float* sdb = sdw + (OT_CONS / 32) * D * w;                          // [4 warps][w] hidden bias accumulators
-  uint64_t* full = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(sdb + (OT_CONS / 32) * w) + 7) & ~uintptr_t(7));
+  const int bar_off = (OT_STAGES * OT_STAGE + (int)sizeof(float) * (D * w + (OT_CONS / 32) * (D + 1) * w) + 7) & ~7;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + bar_off);
   uint64_t* empty = full + OT_STAGES;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + OT_STAGES);
   __shared__ double segacc[CAUSAL_MAX][4];

@@ -135,7 +135,9 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
   constexpr bool DW2 = (MODE == TC_DW) && SPLIT;
   constexpr int MROWS = DW2 ? 2 * BM : BM;                // output rows per work item
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned by offsetting the shared array itself (an integer round trip would
+  // hide the address space and turn every shared access below into a generic one)
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* blo = smem + C::STAGES * C::STAGE;          // TF32 B_lo buffer (BLOC_BYTES)
   uint64_t* full = reinterpret_cast<uint64_t*>(blo + C::BLOC_BYTES);
   uint64_t* empty = full + C::STAGES;
@@ -847,7 +849,9 @@ __global__ void __launch_bounds__(FZ_NT, 1)
                const __grid_constant__ CUtensorMap mapA, const TcParams p) {
   using T = __nv_bfloat16;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned by offsetting the shared array itself (an integer round trip would
+  // hide the address space and turn every shared access below into a generic one)
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* abase = smem + FZ_STAGES * FZ_STAGE;
   uint64_t* full = reinterpret_cast<uint64_t*>(abase + FZ_ABUF * FZ_AT);
   uint64_t* empty = full + FZ_STAGES;
