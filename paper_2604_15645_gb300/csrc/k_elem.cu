@@ -955,6 +955,558 @@ cudaError_t launch_out_loss_tma(const OutArgs& a, int nblocks, cudaStream_t st) 
   return cudaErrorNotSupported;
 }
 
+// ------------------------------------------------------------------------------------
+// The output layer, residual, loss and adjoint seed for BF16 tanh networks whose last
+// hidden layer is at most 256 wide, with the three contractions of width d_out on
+// warp-level tensor-core MMAs (m16n8k16, BF16 operands, FP32 accumulation):
+//   U     = W_out A_L           (rows: W_hi in MMA rows c, W_lo in rows 8 + c)
+//   dW    = Ubar A_L^T          (rows: Ubar_hi in c, Ubar_lo in 8 + c)
+//   Abar  = W_out^T Ubar        (k-slots: W_hi.Ubar_hi, W_lo.Ubar_hi, W_hi.Ubar_lo)
+// The hi/lo splits make the products accurate to about 2^-16 relative, like the FP32
+// weights and seeds of k_out_loss_tma.  tcgen05's smallest M is 64 and would leave 61
+// of 64 accumulator lanes idle for d_out = 3; these MMAs keep the fragments in
+// registers beside the residual and jet arithmetic.  The A_L chunks arrive through
+// the same TMA ring; the ldmatrix fragments the weight gradient reads from them are
+// exactly the activations the tanh-jet adjoint needs for the same (feature, point)
+// pairs.  The four warps stmatrix their adjoints into one staging chunk laid out like
+// the load boxes, which leaves as four bulk tensor stores (per-lane 32-byte stores
+// touch 32 lines per instruction and cost a fifth of the kernel).  Warp w (of four)
+// owns points 16 w .. 16 w + 15 of every 64-point tile.  A failed bounded wait in any
+// warp is ANDed over the warps at the next barrier, so they all leave together.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void ldsm4(uint32_t addr, uint32_t r[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void ldsm4_t(uint32_t addr, uint32_t r[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void stsm4(uint32_t addr, const uint32_t r[4]) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(r[0]), "r"(r[1]),
+               "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+constexpr int OM_MAXW = 256;
+constexpr int OM_SCRATCH = 3584;                  // per warp: U gather and seed fragments
+constexpr int OM_STAGE_OUT = 4 * OT_ROWB;         // one chunk of Zbar_L (4 jet-row boxes), 16 KB
+static_assert(4 * OM_SCRATCH <= OM_STAGE_OUT, "the seed scratch fits in the output staging");
+
+// dynamic shared memory after the ring (byte offsets from the ring's start)
+struct OmLayout {
+  int stg, wa, wf, dw, db, bar, total;
+  __host__ __device__ OmLayout(int w, int d) {
+    stg = OT_STAGES * OT_STAGE;                   // Zbar_L chunk for the bulk store (1024-aligned, swizzled like
+                                                  // the load boxes); between the passes, the per-warp seed scratch
+    wa = stg + OM_STAGE_OUT;                      // W_hi / W_lo rows: bf16 [16][w + 8]
+    wf = wa + 32 * (w + 8);                       // W^T fragments: u32 [w / 16][32 lanes][4]
+    dw = wf + 32 * w;                             // dW accumulators: float [4 warps][d][w + 8]
+    db = dw + 16 * d * (w + 8);                   // hidden-bias accumulators: float [4 warps][w]
+    bar = db + 16 * w;                            // 2 OT_STAGES mbarriers + the abort flag
+    total = bar + 16 * OT_STAGES + 16;
+  }
+};
+
+// Named barrier over the four consumer warps that also ANDs a predicate over them, so
+// that a failed (bounded) wait in any warp makes every warp leave the loop together.
+__device__ __forceinline__ bool cons_sync_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(OT_CONS)
+      : "memory");
+  return r != 0;
+}
+
+template <int D, int MODE, bool LO>
+__global__ void __launch_bounds__(OT_THREADS) k_out_loss_mma(const __grid_constant__ CUtensorMap mapA,
+                                                            const __grid_constant__ CUtensorMap mapLo,
+                                                            const __grid_constant__ CUtensorMap mapZ, OutArgs a) {
+  constexpr int NB = LO ? 5 : 4;                  // staged boxes per chunk: four jet rows (+ the low half)
+  extern __shared__ uint8_t om_raw[];
+  uint8_t* ring = om_raw + ((1024u - (smem_u32(om_raw) & 1023u)) & 1023u);
+  const int w = a.w;
+  const int was = w + 8;                          // sWA row stride (elements): conflict-free A fragments
+  const OmLayout lay(w, D);
+  __nv_bfloat16* sWA = reinterpret_cast<__nv_bfloat16*>(ring + lay.wa);
+  uint32_t* sWf = reinterpret_cast<uint32_t*>(ring + lay.wf);
+  float* sdw = reinterpret_cast<float*>(ring + lay.dw);
+  float* sdb = reinterpret_cast<float*>(ring + lay.db);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + lay.bar);
+  uint64_t* empty = full + OT_STAGES;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + OT_STAGES);
+  __shared__ double segacc[CAUSAL_MAX][4];
+  __shared__ int s_seg[TILE_PTS];
+  __shared__ float s_rr[TILE_PTS][3];
+  __shared__ double sh[OT_CONS / 32];
+  __shared__ float shb[OT_CONS / 32];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OT_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], OT_CONS);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  // weights as MMA operands: W_hi rows c, W_lo rows 8 + c (zero elsewhere), and the
+  // W^T fragments of every 16-feature m-tile with k-slots (W_hi, W_lo, W_hi)
+  for (int i = threadIdx.x; i < 16 * was; i += blockDim.x) {
+    const int row = i / was, f = i - row * was;
+    float v = 0.f;
+    if (f < w && (row & 7) < D) {
+      const float x = a.W[(row & 7) * w + f];
+      const float hi = __bfloat162float(__float2bfloat16_rn(x));
+      v = row < 8 ? hi : x - hi;
+    }
+    sWA[i] = __float2bfloat16_rn(v);
+  }
+  for (int i = threadIdx.x; i < (w / 16) * 32; i += blockDim.x) {
+    const int mt = i >> 5, l = i & 31, g = l >> 2, t = l & 3;
+    auto wk = [&](int f, int k) -> float {     // W^T with k-slots
+      const int c = k % D, part = k / D;
+      if (part > 2) return 0.f;
+      const float x = a.W[c * w + f];
+      const float hi = __bfloat162float(__float2bfloat16_rn(x));
+      return part == 1 ? x - hi : hi;
+    };
+    const int f0 = 16 * mt + g;
+    uint32_t q[4];
+    q[0] = pack_bf16(wk(f0, 2 * t), wk(f0, 2 * t + 1));
+    q[1] = pack_bf16(wk(f0 + 8, 2 * t), wk(f0 + 8, 2 * t + 1));
+    q[2] = pack_bf16(wk(f0, 2 * t + 8), wk(f0, 2 * t + 9));
+    q[3] = pack_bf16(wk(f0 + 8, 2 * t + 8), wk(f0 + 8, 2 * t + 9));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sWf[4 * i + j] = q[j];
+  }
+  for (int i = threadIdx.x; i < 4 * D * (w + 8) + 4 * w; i += blockDim.x) sdw[i] = 0.f;   // sdw and sdb
+  if (a.segpart)
+    for (int i = threadIdx.x; i < CAUSAL_MAX * 4; i += blockDim.x) segacc[i / 4][i % 4] = 0.0;
+  __syncthreads();
+
+  const int64_t ntiles = a.NP / TILE_PTS;
+  const int nchunks = w / OT_FC;
+  const int passes = a.want_grad ? 2 : 1;
+
+  if (warp == OT_CONS / 32) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int armed[OT_STAGES] = {};
+      for (int64_t T0i = blockIdx.x; T0i < ntiles && !*abort_flag; T0i += gridDim.x) {
+        const int T0 = (int)(a.reverse ? ntiles - 1 - T0i : T0i);
+        for (int pass = 0; pass < passes && !*abort_flag; ++pass) {
+          for (int k = 0; k < nchunks; ++k) {
+            if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.status, OT_WAIT_NS)) break;
+            uint8_t* sb = ring + stage * OT_STAGE;
+            mbar_expect_tx(&full[stage], NB * OT_ROWB);
+            armed[stage] = (int)phase + 1;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) tma_load_3d(sb + r * OT_ROWB, &mapA, &full[stage], 64 * r, OT_FC * k, T0);
+            if constexpr (LO) tma_load_3d(sb + 4 * OT_ROWB, &mapLo, &full[stage], 0, OT_FC * k, T0);
+            if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
+          }
+        }
+      }
+      for (int s = 0; s < OT_STAGES; ++s)
+        if (armed[s]) {
+          const uint64_t t0 = gtimer();
+          while (!mbar_try(&full[s], (uint32_t)(armed[s] - 1)) && gtimer() - t0 < OT_WAIT_NS) {}
+        }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------------ consumers
+  const int g = lane >> 2, t = lane & 3;
+  const int p0 = 16 * warp;                        // this warp's first point in a tile
+  const int ck = p0 >> 3;                          // its first 16-byte chunk in a box row
+  uint8_t* scr = ring + lay.stg + warp * OM_SCRATCH;
+  float* sU = reinterpret_cast<float*>(scr);                                  // [16 points][D][4]
+  __nv_bfloat16* sUd = reinterpret_cast<__nv_bfloat16*>(scr + 768);          // [hi/lo][4 rows][D][16 points]
+  uint8_t* sUb = scr + 1536;                                                   // [4 rows][16 points][16 k] bf16
+  const uint32_t stg = smem_u32(ring + lay.stg);                              // Zbar_L chunk staging
+  const uint32_t sWA_u = smem_u32(sWA);
+  const uint32_t sUd_u = smem_u32(sUd);
+  const uint32_t sUb_u = smem_u32(sUb);
+  float* sdw_w = sdw + warp * D * (w + 8);
+  float* sdb_w = sdb + warp * w;
+  Acc2 acc[5];
+  float dbo[3] = {0.f, 0.f, 0.f};
+  int stage = 0;
+  uint32_t phase = 0;
+  bool ok = true;
+  // ldmatrix row address inside a box for (feature fi in the chunk, 16-byte point chunk c)
+  auto box_row = [&](uint32_t box, int fi, int c) { return box + fi * 128 + ((c ^ (fi & 7)) << 4); };
+  const int lm = lane >> 3, li = lane & 7;
+
+  for (int64_t T0i = blockIdx.x; T0i < ntiles; T0i += gridDim.x) {
+    const int64_t T0 = a.reverse ? ntiles - 1 - T0i : T0i;
+    // ---------------- pass 1: U = W_out A_L for this warp's 16 points
+    float acc1[NB][2][4];
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc1[b][j][e] = 0.f;
+    for (int k = 0; k < nchunks; ++k) {
+      if (!mbar_wait(&full[stage], phase, abort_flag, a.status, OT_WAIT_NS)) { ok = false; break; }
+      const uint32_t sb = smem_u32(ring + stage * OT_STAGE);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int f0 = OT_FC * k + 16 * s;
+        uint32_t af[4];
+        const uint32_t wa = sWA_u + 2 * (f0 + 2 * t);
+        af[0] = lds32(wa + 2 * g * was);
+        af[1] = lds32(wa + 2 * (g + 8) * was);
+        af[2] = lds32(wa + 2 * g * was + 16);
+        af[3] = lds32(wa + 2 * (g + 8) * was + 16);
+        // B fragments (k = features, n = points) through the transposing load:
+        // matrices (features +0/+8, points +0/+8) in the order n-tile 0 (k lo, k hi), n-tile 1
+        const int fi = 16 * s + 8 * (lm & 1) + li, c = ck + (lm >> 1);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          uint32_t r[4];
+          ldsm4_t(box_row(sb + b * OT_ROWB, fi, c), r);
+          mma_bf16_16816(acc1[b][0], af, r[0], r[1]);
+          mma_bf16_16816(acc1[b][1], af, r[2], r[3]);
+        }
+      }
+      mbar_arrive(&empty[stage]);
+      if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
+    }
+    // every warp is through its first pass, and the last bulk store has read the staging
+    // (the seed scratch below shares it)
+    if (threadIdx.x == 0) bulk_wait_read0();
+    ok = cons_sync_and(ok);
+    if (!ok) break;
+
+    // ---------------- U to the point lanes, residual, seeds
+    if (g < D) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            float u = acc1[b][j][e] + acc1[b][j][2 + e];
+            if constexpr (LO) {
+              if (b == 0) u += acc1[NB - 1][j][e] + acc1[NB - 1][j][2 + e];
+            }
+            const int q = 8 * j + 2 * t + e;
+            sU[(q * D + g) * 4 + b] = u;
+          }
+    }
+    __syncwarp();
+    float rr[3] = {0.f, 0.f, 0.f};
+    int seg = -1;
+    if (lane < 16) {
+      const int q = lane;
+      float U[3][4], Ub[3][4];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) U[c][r] = c < D ? sU[(q * D + c) * 4 + r] : 0.f;
+      int64_t idx;
+      const int set = point_set(T0 * TILE_PTS + p0 + q, a.n_res, a.n_ic, a.n_bc, idx);
+      if (set != SET_PAD) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) U[c][0] += a.b[c];
+      }
+      float kp = a.k_pde;
+      if (a.segments && set == SET_RES) {
+        const float tt = a.x_res[(int64_t)a.t_index * a.n_res + idx];
+        seg = min(a.segments - 1, max(0, (int)floorf((tt - a.t0) * a.tinv)));
+        if (a.seg_scale) kp = a.seg_scale[seg];
+      }
+      float lacc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      point_residual<D>(a, set, idx, kp, U, Ub, lacc, rr);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) acc[i].add(lacc[i]);
+      if (a.want_grad) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) dbo[c] += Ub[c][0];
+        // seed fragments: Ubar_hi / Ubar_lo per (row, output) over the warp's points,
+        // and per (row, point) the 16 k-slots (Ubar_hi, Ubar_hi, Ubar_lo, zeros)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float kv[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) kv[i] = 0.f;
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const __nv_bfloat16 hb = __float2bfloat16_rn(Ub[c][r]);
+            const float hi = __bfloat162float(hb);
+            const float lo = Ub[c][r] - hi;
+            sUd[((0 * 4 + r) * D + c) * 16 + q] = hb;
+            sUd[((1 * 4 + r) * D + c) * 16 + q] = __float2bfloat16_rn(lo);
+            kv[c] = hi;
+            kv[D + c] = hi;
+            kv[2 * D + c] = lo;
+          }
+          uint32_t pk[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(kv[2 * i], kv[2 * i + 1]);
+          uint4* dst = reinterpret_cast<uint4*>(sUb + (r * 16 + q) * 32);
+          dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+      }
+    }
+    if (a.segpart) {   // uniform over the block
+      if (lane < 16) {
+        s_seg[p0 + lane] = seg;
+        s_rr[p0 + lane][0] = rr[0]; s_rr[p0 + lane][1] = rr[1]; s_rr[p0 + lane][2] = rr[2];
+      }
+      cons_sync();
+      if (threadIdx.x == 0)
+        for (int q = 0; q < TILE_PTS; ++q)
+          if (s_seg[q] >= 0) {
+            double* sa = segacc[s_seg[q]];
+            sa[0] += s_rr[q][0]; sa[1] += s_rr[q][1]; sa[2] += s_rr[q][2]; sa[3] += 1.0;
+          }
+      cons_sync();
+    }
+    if (!a.want_grad) continue;
+    __syncwarp();
+    // weight-gradient A fragments (rows: Ubar_hi c, Ubar_lo 8 + c; k = the row's 16 points)
+    uint32_t ua[4][4], ub[4][2][2];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const bool live = g < D;
+      const uint32_t hrow = sUd_u + 2 * (((0 * 4 + r) * D + (live ? g : 0)) * 16 + 2 * t);
+      const uint32_t lrow = sUd_u + 2 * (((1 * 4 + r) * D + (live ? g : 0)) * 16 + 2 * t);
+      ua[r][0] = live ? lds32(hrow) : 0u;
+      ua[r][1] = live ? lds32(lrow) : 0u;
+      ua[r][2] = live ? lds32(hrow + 16) : 0u;
+      ua[r][3] = live ? lds32(lrow + 16) : 0u;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint32_t kc = sUb_u + (r * 16 + 8 * j + g) * 32 + 4 * t;   // point 8 j + g, k-slots 2t, 2t+1 (+8)
+        ub[r][j][0] = lds32(kc);
+        ub[r][j][1] = lds32(kc + 16);
+      }
+    }
+    __syncwarp();   // the scratch is the store staging from here on
+
+    // ---------------- pass 2: dW, the adjoint Abar = W^T Ubar, its tanh-jet adjoint, Zbar_L
+    for (int k = 0; k < nchunks; ++k) {
+      ok = mbar_wait(&full[stage], phase, abort_flag, a.status, OT_WAIT_NS);
+      // the staging is free once the previous chunk's bulk store has read it
+      if (threadIdx.x == 0) bulk_wait_read0();
+      ok = cons_sync_and(ok);
+      if (!ok) break;
+      const uint32_t sb = smem_u32(ring + stage * OT_STAGE);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int f0 = OT_FC * k + 16 * s;
+        // A_L of features f0 .. f0 + 15 at the warp's points: matrices (features +0, points
+        // +0), (+0, +8), (+8, +0), (+8, +8), each thread (feature g, points 2t, 2t + 1)
+        uint32_t L[NB][4];
+        const int fi = 16 * s + 8 * (lm >> 1) + li, c = ck + (lm & 1);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) ldsm4(box_row(sb + b * OT_ROWB, fi, c), L[b]);
+        // weight gradient of these 16 features (two n-tiles), K = the warp's points
+        float dacc[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) dacc[nt][e] = 0.f;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) mma_bf16_16816(dacc[nt], ua[b < 4 ? b : 0], L[b][2 * nt], L[b][2 * nt + 1]);
+        }
+        if (g < D) {
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) {
+            float* d = sdw_w + g * (w + 8) + f0 + 8 * nt + 2 * t;
+            d[0] += dacc[nt][0] + dacc[nt][2];
+            d[1] += dacc[nt][1] + dacc[nt][3];
+          }
+        }
+        // the adjoint of the 16 features at the warp's 16 points x 4 rows
+        uint32_t wfr[4];
+        {
+          const uint4 q = *reinterpret_cast<const uint4*>(sWf + 4 * ((f0 / 16) * 32 + lane));
+          wfr[0] = q.x; wfr[1] = q.y; wfr[2] = q.z; wfr[3] = q.w;
+        }
+        float adj[4][2][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) adj[r][j][e] = 0.f;
+            mma_bf16_16816(adj[r][j], wfr, ub[r][j][0], ub[r][j][1]);
+          }
+        // tanh-jet adjoint per (feature f0 + 8 fh + g, point p0 + 8 j + 2 t + e)
+        uint32_t zp[2][4][2];
+        float dbs[2] = {0.f, 0.f};
+#pragma unroll
+        for (int fh = 0; fh < 2; ++fh)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            float zo[2][4];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              float av[4], ab[4];
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                const uint32_t u = L[r][2 * fh + j];
+                av[r] = e ? bf16_hi(u) : bf16_lo(u);
+                ab[r] = adj[r][j][2 * fh + e];
+              }
+              if constexpr (LO) {
+                const uint32_t u = L[NB - 1][2 * fh + j];
+                av[0] += e ? bf16_hi(u) : bf16_lo(u);
+              }
+              jet_adj_a(av, ab, zo[e], MODE);
+              dbs[fh] += zo[e][0];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) zp[fh][r][j] = pack_bf16(zo[0][r], zo[1][r]);
+          }
+        // into the chunk's staging boxes (the load boxes' swizzled layout), at the rows
+        // and 16-byte chunks this warp's ldmatrix read
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const uint32_t v[4] = {zp[0][r][0], zp[0][r][1], zp[1][r][0], zp[1][r][1]};
+          stsm4(box_row(stg + r * OT_ROWB, fi, c), v);
+        }
+        if (a.dbhid) {
+#pragma unroll
+          for (int fh = 0; fh < 2; ++fh) {
+            float x = dbs[fh];
+            x += __shfl_xor_sync(0xffffffffu, x, 1);
+            x += __shfl_xor_sync(0xffffffffu, x, 2);
+            if (t == 0) sdb_w[f0 + 8 * fh + g] += x;
+          }
+        }
+      }
+      // the chunk's Zbar_L (32 features x 4 rows x 64 points) as four bulk tensor stores
+      fence_proxy_async_smem();
+      cons_sync();
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) tma_store_3d(&mapZ, ring + lay.stg + r * OT_ROWB, 64 * r, OT_FC * k, (int)T0);
+        bulk_commit();
+      }
+      mbar_arrive(&empty[stage]);
+      if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
+    }
+    if (!ok) break;
+  }
+  if (threadIdx.x == 0) bulk_wait0();   // every bulk store has completed
+  for (int i = 0; i < 5; ++i) {
+    const double s = cons_sum_d(acc[i].value(), sh);
+    if (threadIdx.x == 0) a.losspart[(int64_t)blockIdx.x * 8 + i] = s;
+  }
+  if (a.segpart) {
+    cons_sync();
+    for (int i = threadIdx.x; i < CAUSAL_MAX * 4; i += OT_CONS)
+      a.segpart[(int64_t)blockIdx.x * CAUSAL_MAX * 4 + i] = segacc[i / 4][i % 4];
+  }
+  if (!a.want_grad) return;
+  cons_sync();
+  for (int i = threadIdx.x; i < D * w; i += OT_CONS) {
+    const int c = i / w, f = i - c * w;
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < OT_CONS / 32; ++k) s += sdw[(k * D + c) * (w + 8) + f];
+    a.dwpart[(int64_t)blockIdx.x * D * w + i] = s;
+  }
+  if (a.dbhid)
+    for (int i = threadIdx.x; i < w; i += OT_CONS) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < OT_CONS / 32; ++k) s += sdb[k * w + i];
+      a.dbhid[(int64_t)i * gridDim.x + blockIdx.x] = s;
+    }
+  for (int c = 0; c < D; ++c) {
+    float v = dbo[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    cons_sync();
+    if (lane == 0) shb[warp] = v;
+    cons_sync();
+    if (threadIdx.x == 0) {
+      float tsum = 0.f;
+      for (int k = 0; k < OT_CONS / 32; ++k) tsum += shb[k];
+      a.dbpart[(int64_t)c * gridDim.x + blockIdx.x] = tsum;
+    }
+  }
+}
+
+// Whether the MMA output kernel applies: BF16 tanh networks whose last hidden layer is
+// at most 256 wide and a multiple of 32 features.
+bool out_loss_mma_ok(int prec, int act, int w) {
+  return prec == PINN_BF16 && act == PINN_ACT_TANH && w <= OM_MAXW && w % OT_FC == 0;
+}
+
+template <int D, int MODE, bool LO>
+cudaError_t out_loss_mma_launch(const CUtensorMap& ma, const CUtensorMap& ml, const CUtensorMap& mz, const OutArgs& a,
+                                int nblocks, cudaStream_t st) {
+  auto kern = k_out_loss_mma<D, MODE, LO>;
+  const size_t smem = (size_t)OmLayout(a.w, D).total + 1024;
+  static size_t reserved = 0;
+  if (smem > reserved) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    reserved = smem;
+  }
+  kern<<<nblocks, OT_THREADS, smem, st>>>(ma, ml, mz, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_out_loss_mma(const OutArgs& a, int nblocks, cudaStream_t st) {
+  CUtensorMap ma, ml, mz;
+  const uint64_t nt = (uint64_t)(a.NP / TILE_PTS);
+  if (!tc_map3(&ma, a.AL, false, TILE_COLS, (uint64_t)a.w, nt, 64, OT_FC)) return cudaErrorNotSupported;
+  // Zbar_L has A_L's layout: the same boxes serve the bulk stores (loss-only calls store nothing)
+  mz = ma;
+  if (a.want_grad && !tc_map3(&mz, a.Zbar, false, TILE_COLS, (uint64_t)a.w, nt, 64, OT_FC)) return cudaErrorNotSupported;
+  ml = ma;
+  if (a.ALlo && !tc_map3(&ml, a.ALlo, false, TILE_PTS, (uint64_t)a.w, nt, 64, OT_FC)) return cudaErrorNotSupported;
+  const bool lo = a.ALlo != nullptr;
+  if (a.d_out == 1 && a.jet_mode == JET_BURGERS)
+    return lo ? out_loss_mma_launch<1, JET_BURGERS, true>(ma, ml, mz, a, nblocks, st)
+              : out_loss_mma_launch<1, JET_BURGERS, false>(ma, ml, mz, a, nblocks, st);
+  if (a.d_out == 3 && a.jet_mode == JET_NS)
+    return lo ? out_loss_mma_launch<3, JET_NS, true>(ma, ml, mz, a, nblocks, st)
+              : out_loss_mma_launch<3, JET_NS, false>(ma, ml, mz, a, nblocks, st);
+  if (a.d_out == 3 && a.jet_mode == JET_MAXWELL)
+    return lo ? out_loss_mma_launch<3, JET_MAXWELL, true>(ma, ml, mz, a, nblocks, st)
+              : out_loss_mma_launch<3, JET_MAXWELL, false>(ma, ml, mz, a, nblocks, st);
+  return cudaErrorNotSupported;
+}
+
+
 template <typename T, int D, bool FAST, bool SINE>
 cudaError_t out_loss_launch(const OutArgs& a, int nblocks, size_t smem, cudaStream_t st) {
   auto kern = k_out_loss<T, D, FAST, SINE>;
@@ -970,6 +1522,10 @@ cudaError_t out_loss_launch(const OutArgs& a, int nblocks, size_t smem, cudaStre
 }
 
 cudaError_t launch_out_loss(const OutArgs& a, int prec, int nblocks, cudaStream_t st) {
+  if (!a.ZL && out_loss_mma_ok(prec, PINN_ACT_TANH, a.w)) {
+    const cudaError_t e = launch_out_loss_mma(a, nblocks, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (!a.ZL && out_loss_tma_ok(prec, PINN_ACT_TANH, a.w)) {
     const cudaError_t e = launch_out_loss_tma(a, nblocks, st);
     if (e != cudaErrorNotSupported) return e;

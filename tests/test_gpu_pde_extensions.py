@@ -38,7 +38,8 @@ def _causal_case(name, precision, M, eps, **sizes):
 
 
 @pytest.mark.parametrize("name,precision", [("burgers1d_4x64", "fp32"), ("maxwell_te_5x512", "fp32"),
-                                            ("maxwell_te_5x512", "bf16"), ("advection1d_4x128", "tf32")])
+                                            ("maxwell_te_5x512", "bf16"), ("advection1d_4x128", "tf32"),
+                                            ("advection1d_4x128", "bf16")])
 def test_causal_loss_and_gradient_match_oracle(cuda_lib, name, precision):
     api, w, p, B, b, cz, net, db, prob, lam = _causal_case(name, precision, 4, 0.5, n_res=900, n_ic=100, n_bc=100)
     t, g = net.loss_grad(torch.tensor(p, device="cuda"), db, prob)
