@@ -268,7 +268,7 @@ def rooflines(dom, flops, nbytes, scheme, prof, steps, peaks, peak_src, precisio
     tflops = f_l / (per_launch_ms / 1e3) / 1e12
     gbs = b_l / (per_launch_ms / 1e3) / 1e9
     burst, _, bound, src = tensor_peaks(peaks, precision)
-    traffic = _traffic(dom, workload)
+    traffic = _traffic(dom, workload if precision == "bf16" else f"{workload}/{precision}")
     compute = {"bound": bound, "achieved": round(tflops, 2), "peak": round(burst, 1), "unit": "TFLOP/s",
                "frac": round(tflops / burst, 4), "traffic": traffic, "kernel": dom, "flop_per_launch": f_l,
                "launch_ms": round(per_launch_ms, 4),
