@@ -1043,7 +1043,7 @@ __device__ __forceinline__ bool cons_sync_and(bool v) {
 }
 
 template <int D, int MODE, bool LO>
-__global__ void __launch_bounds__(OT_THREADS) k_out_loss_mma(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(OT_THREADS, 2) k_out_loss_mma(const __grid_constant__ CUtensorMap mapA,
                                                             const __grid_constant__ CUtensorMap mapLo,
                                                             const __grid_constant__ CUtensorMap mapZ, OutArgs a) {
   constexpr int NB = LO ? 5 : 4;                  // staged boxes per chunk: four jet rows (+ the low half)
@@ -1119,20 +1119,31 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_mma(const __grid_consta
       int stage = 0;
       uint32_t phase = 0;
       int armed[OT_STAGES] = {};
-      for (int64_t T0i = blockIdx.x; T0i < ntiles && !*abort_flag; T0i += gridDim.x) {
-        const int T0 = (int)(a.reverse ? ntiles - 1 - T0i : T0i);
-        for (int pass = 0; pass < passes && !*abort_flag; ++pass) {
-          for (int k = 0; k < nchunks; ++k) {
-            if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.status, OT_WAIT_NS)) break;
-            uint8_t* sb = ring + stage * OT_STAGE;
-            mbar_expect_tx(&full[stage], NB * OT_ROWB);
-            armed[stage] = (int)phase + 1;
+      // the consumers' order: chunk k of the previous tile's second pass, then chunk k of
+      // this tile's first pass, so every first-pass (DRAM) load leads its use by a
+      // second-pass chunk
+      bool live = true;
+      auto load_chunk = [&](int k, int T) {
+        if (!live || !mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.status, OT_WAIT_NS)) { live = false; return; }
+        uint8_t* sb = ring + stage * OT_STAGE;
+        mbar_expect_tx(&full[stage], NB * OT_ROWB);
+        armed[stage] = (int)phase + 1;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) tma_load_3d(sb + r * OT_ROWB, &mapA, &full[stage], 64 * r, OT_FC * k, T0);
-            if constexpr (LO) tma_load_3d(sb + 4 * OT_ROWB, &mapLo, &full[stage], 0, OT_FC * k, T0);
-            if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
-          }
+        for (int r = 0; r < 4; ++r) tma_load_3d(sb + r * OT_ROWB, &mapA, &full[stage], 64 * r, OT_FC * k, T);
+        if constexpr (LO) tma_load_3d(sb + 4 * OT_ROWB, &mapLo, &full[stage], 0, OT_FC * k, T);
+        if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
+      };
+      int prevT = -1;
+      for (int64_t T0i = blockIdx.x; live; T0i += gridDim.x) {
+        const bool cur = T0i < ntiles;
+        const bool prev = prevT >= 0;
+        if (!cur && !prev) break;
+        const int Tc = cur ? (int)(a.reverse ? ntiles - 1 - T0i : T0i) : 0;
+        for (int k = 0; k < nchunks; ++k) {
+          if (prev) load_chunk(k, prevT);
+          if (cur) load_chunk(k, Tc);
         }
+        prevT = (cur && passes == 2) ? Tc : -1;
       }
       for (int s = 0; s < OT_STAGES; ++s)
         if (armed[s]) {
@@ -1166,9 +1177,16 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_mma(const __grid_consta
   auto box_row = [&](uint32_t box, int fi, int c) { return box + fi * 128 + ((c ^ (fi & 7)) << 4); };
   const int lm = lane >> 3, li = lane & 7;
 
-  for (int64_t T0i = blockIdx.x; T0i < ntiles; T0i += gridDim.x) {
-    const int64_t T0 = a.reverse ? ntiles - 1 - T0i : T0i;
-    // ---------------- pass 1: U = W_out A_L for this warp's 16 points
+  // Software pipeline over this block's tiles: in each round, chunk k of the previous
+  // tile's second pass is followed by chunk k of the current tile's first pass.  A failed
+  // bounded wait skips the work but still reaches the next ANDed barrier.
+  int64_t prevT = -1;                              // the tile whose second pass is pending
+  uint32_t ua[4][4], ub[4][2][2];                  // its seed fragments
+  for (int64_t T0i = blockIdx.x;; T0i += gridDim.x) {
+    const bool cur = T0i < ntiles;
+    const bool prev = prevT >= 0;
+    if (!cur && !prev) break;
+    const int64_t Tc = cur ? (a.reverse ? ntiles - 1 - T0i : T0i) : 0;
     float acc1[NB][2][4];
 #pragma unroll
     for (int b = 0; b < NB; ++b)
@@ -1177,152 +1195,14 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_mma(const __grid_consta
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc1[b][j][e] = 0.f;
     for (int k = 0; k < nchunks; ++k) {
-      if (!mbar_wait(&full[stage], phase, abort_flag, a.status, OT_WAIT_NS)) { ok = false; break; }
-      const uint32_t sb = smem_u32(ring + stage * OT_STAGE);
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int f0 = OT_FC * k + 16 * s;
-        uint32_t af[4];
-        const uint32_t wa = sWA_u + 2 * (f0 + 2 * t);
-        af[0] = lds32(wa + 2 * g * was);
-        af[1] = lds32(wa + 2 * (g + 8) * was);
-        af[2] = lds32(wa + 2 * g * was + 16);
-        af[3] = lds32(wa + 2 * (g + 8) * was + 16);
-        // B fragments (k = features, n = points) through the transposing load:
-        // matrices (features +0/+8, points +0/+8) in the order n-tile 0 (k lo, k hi), n-tile 1
-        const int fi = 16 * s + 8 * (lm & 1) + li, c = ck + (lm >> 1);
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          uint32_t r[4];
-          ldsm4_t(box_row(sb + b * OT_ROWB, fi, c), r);
-          mma_bf16_16816(acc1[b][0], af, r[0], r[1]);
-          mma_bf16_16816(acc1[b][1], af, r[2], r[3]);
-        }
-      }
-      mbar_arrive(&empty[stage]);
-      if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
-    }
-    // every warp is through its first pass, and the last bulk store has read the staging
-    // (the seed scratch below shares it)
-    if (threadIdx.x == 0) bulk_wait_read0();
-    ok = cons_sync_and(ok);
-    if (!ok) break;
-
-    // ---------------- U to the point lanes, residual, seeds
-    if (g < D) {
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            float u = acc1[b][j][e] + acc1[b][j][2 + e];
-            if constexpr (LO) {
-              if (b == 0) u += acc1[NB - 1][j][e] + acc1[NB - 1][j][2 + e];
-            }
-            const int q = 8 * j + 2 * t + e;
-            sU[(q * D + g) * 4 + b] = u;
-          }
-    }
-    __syncwarp();
-    float rr[3] = {0.f, 0.f, 0.f};
-    int seg = -1;
-    if (lane < 16) {
-      const int q = lane;
-      float U[3][4], Ub[3][4];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) U[c][r] = c < D ? sU[(q * D + c) * 4 + r] : 0.f;
-      int64_t idx;
-      const int set = point_set(T0 * TILE_PTS + p0 + q, a.n_res, a.n_ic, a.n_bc, idx);
-      if (set != SET_PAD) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) U[c][0] += a.b[c];
-      }
-      float kp = a.k_pde;
-      if (a.segments && set == SET_RES) {
-        const float tt = a.x_res[(int64_t)a.t_index * a.n_res + idx];
-        seg = min(a.segments - 1, max(0, (int)floorf((tt - a.t0) * a.tinv)));
-        if (a.seg_scale) kp = a.seg_scale[seg];
-      }
-      float lacc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-      point_residual<D>(a, set, idx, kp, U, Ub, lacc, rr);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) acc[i].add(lacc[i]);
-      if (a.want_grad) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) dbo[c] += Ub[c][0];
-        // seed fragments: Ubar_hi / Ubar_lo per (row, output) over the warp's points,
-        // and per (row, point) the 16 k-slots (Ubar_hi, Ubar_hi, Ubar_lo, zeros)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          float kv[16];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) kv[i] = 0.f;
-#pragma unroll
-          for (int c = 0; c < D; ++c) {
-            const __nv_bfloat16 hb = __float2bfloat16_rn(Ub[c][r]);
-            const float hi = __bfloat162float(hb);
-            const float lo = Ub[c][r] - hi;
-            sUd[((0 * 4 + r) * D + c) * 16 + q] = hb;
-            sUd[((1 * 4 + r) * D + c) * 16 + q] = __float2bfloat16_rn(lo);
-            kv[c] = hi;
-            kv[D + c] = hi;
-            kv[2 * D + c] = lo;
-          }
-          uint32_t pk[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(kv[2 * i], kv[2 * i + 1]);
-          uint4* dst = reinterpret_cast<uint4*>(sUb + (r * 16 + q) * 32);
-          dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-          dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-        }
-      }
-    }
-    if (a.segpart) {   // uniform over the block
-      if (lane < 16) {
-        s_seg[p0 + lane] = seg;
-        s_rr[p0 + lane][0] = rr[0]; s_rr[p0 + lane][1] = rr[1]; s_rr[p0 + lane][2] = rr[2];
-      }
-      cons_sync();
-      if (threadIdx.x == 0)
-        for (int q = 0; q < TILE_PTS; ++q)
-          if (s_seg[q] >= 0) {
-            double* sa = segacc[s_seg[q]];
-            sa[0] += s_rr[q][0]; sa[1] += s_rr[q][1]; sa[2] += s_rr[q][2]; sa[3] += 1.0;
-          }
-      cons_sync();
-    }
-    if (!a.want_grad) continue;
-    __syncwarp();
-    // weight-gradient A fragments (rows: Ubar_hi c, Ubar_lo 8 + c; k = the row's 16 points)
-    uint32_t ua[4][4], ub[4][2][2];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const bool live = g < D;
-      const uint32_t hrow = sUd_u + 2 * (((0 * 4 + r) * D + (live ? g : 0)) * 16 + 2 * t);
-      const uint32_t lrow = sUd_u + 2 * (((1 * 4 + r) * D + (live ? g : 0)) * 16 + 2 * t);
-      ua[r][0] = live ? lds32(hrow) : 0u;
-      ua[r][1] = live ? lds32(lrow) : 0u;
-      ua[r][2] = live ? lds32(hrow + 16) : 0u;
-      ua[r][3] = live ? lds32(lrow + 16) : 0u;
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const uint32_t kc = sUb_u + (r * 16 + 8 * j + g) * 32 + 4 * t;   // point 8 j + g, k-slots 2t, 2t+1 (+8)
-        ub[r][j][0] = lds32(kc);
-        ub[r][j][1] = lds32(kc + 16);
-      }
-    }
-    __syncwarp();   // the scratch is the store staging from here on
-
-    // ---------------- pass 2: dW, the adjoint Abar = W^T Ubar, its tanh-jet adjoint, Zbar_L
-    for (int k = 0; k < nchunks; ++k) {
-      ok = mbar_wait(&full[stage], phase, abort_flag, a.status, OT_WAIT_NS);
+      if (prev) {
+      // ---------------- pass 2, chunk k of the previous tile: dW, Abar = W^T Ubar, its tanh-jet
+      // adjoint, Zbar_L
+      if (ok) ok = mbar_wait(&full[stage], phase, abort_flag, a.status, OT_WAIT_NS);
       // the staging is free once the previous chunk's bulk store has read it
       if (threadIdx.x == 0) bulk_wait_read0();
       ok = cons_sync_and(ok);
-      if (!ok) break;
+      if (!ok) break;   // (uniform: every consumer thread leaves the tile loop)
       const uint32_t sb = smem_u32(ring + stage * OT_STAGE);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
@@ -1414,13 +1294,159 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_mma(const __grid_consta
       cons_sync();
       if (threadIdx.x == 0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) tma_store_3d(&mapZ, ring + lay.stg + r * OT_ROWB, 64 * r, OT_FC * k, (int)T0);
+        for (int r = 0; r < 4; ++r) tma_store_3d(&mapZ, ring + lay.stg + r * OT_ROWB, 64 * r, OT_FC * k, (int)prevT);
         bulk_commit();
       }
       mbar_arrive(&empty[stage]);
       if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
+          }
+      if (cur) {
+      // ---------------- pass 1, chunk k of this tile: U = W_out A_L for this warp's 16 points
+      if (ok) ok = mbar_wait(&full[stage], phase, abort_flag, a.status, OT_WAIT_NS);
+      if (ok) {
+      const uint32_t sb = smem_u32(ring + stage * OT_STAGE);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int f0 = OT_FC * k + 16 * s;
+        uint32_t af[4];
+        const uint32_t wa = sWA_u + 2 * (f0 + 2 * t);
+        af[0] = lds32(wa + 2 * g * was);
+        af[1] = lds32(wa + 2 * (g + 8) * was);
+        af[2] = lds32(wa + 2 * g * was + 16);
+        af[3] = lds32(wa + 2 * (g + 8) * was + 16);
+        // B fragments (k = features, n = points) through the transposing load:
+        // matrices (features +0/+8, points +0/+8) in the order n-tile 0 (k lo, k hi), n-tile 1
+        const int fi = 16 * s + 8 * (lm & 1) + li, c = ck + (lm >> 1);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          uint32_t r[4];
+          ldsm4_t(box_row(sb + b * OT_ROWB, fi, c), r);
+          mma_bf16_16816(acc1[b][0], af, r[0], r[1]);
+          mma_bf16_16816(acc1[b][1], af, r[2], r[3]);
+        }
+      }
+      mbar_arrive(&empty[stage]);
+      if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
+      }
+      }
     }
+    // (a failed first-pass wait is not uniform: it reaches the ANDed barrier below)
+    if (!cur) break;
+    // every warp is through its first pass, and the last bulk store has read the staging
+    // (the seed scratch below shares it)
+    if (threadIdx.x == 0) bulk_wait_read0();
+    ok = cons_sync_and(ok);
     if (!ok) break;
+
+    // ---------------- U to the point lanes, residual, seeds
+    if (g < D) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            float u = acc1[b][j][e] + acc1[b][j][2 + e];
+            if constexpr (LO) {
+              if (b == 0) u += acc1[NB - 1][j][e] + acc1[NB - 1][j][2 + e];
+            }
+            const int q = 8 * j + 2 * t + e;
+            sU[(q * D + g) * 4 + b] = u;
+          }
+    }
+    __syncwarp();
+    float rr[3] = {0.f, 0.f, 0.f};
+    int seg = -1;
+    if (lane < 16) {
+      const int q = lane;
+      float U[3][4], Ub[3][4];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) U[c][r] = c < D ? sU[(q * D + c) * 4 + r] : 0.f;
+      int64_t idx;
+      const int set = point_set(Tc * TILE_PTS + p0 + q, a.n_res, a.n_ic, a.n_bc, idx);
+      if (set != SET_PAD) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) U[c][0] += a.b[c];
+      }
+      float kp = a.k_pde;
+      if (a.segments && set == SET_RES) {
+        const float tt = a.x_res[(int64_t)a.t_index * a.n_res + idx];
+        seg = min(a.segments - 1, max(0, (int)floorf((tt - a.t0) * a.tinv)));
+        if (a.seg_scale) kp = a.seg_scale[seg];
+      }
+      float lacc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      point_residual<D>(a, set, idx, kp, U, Ub, lacc, rr);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) acc[i].add(lacc[i]);
+      if (a.want_grad) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) dbo[c] += Ub[c][0];
+        // seed fragments: Ubar_hi / Ubar_lo per (row, output) over the warp's points,
+        // and per (row, point) the 16 k-slots (Ubar_hi, Ubar_hi, Ubar_lo, zeros)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float kv[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) kv[i] = 0.f;
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const __nv_bfloat16 hb = __float2bfloat16_rn(Ub[c][r]);
+            const float hi = __bfloat162float(hb);
+            const float lo = Ub[c][r] - hi;
+            sUd[((0 * 4 + r) * D + c) * 16 + q] = hb;
+            sUd[((1 * 4 + r) * D + c) * 16 + q] = __float2bfloat16_rn(lo);
+            kv[c] = hi;
+            kv[D + c] = hi;
+            kv[2 * D + c] = lo;
+          }
+          uint32_t pk[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(kv[2 * i], kv[2 * i + 1]);
+          uint4* dst = reinterpret_cast<uint4*>(sUb + (r * 16 + q) * 32);
+          dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+      }
+    }
+    if (a.segpart) {   // uniform over the block
+      if (lane < 16) {
+        s_seg[p0 + lane] = seg;
+        s_rr[p0 + lane][0] = rr[0]; s_rr[p0 + lane][1] = rr[1]; s_rr[p0 + lane][2] = rr[2];
+      }
+      cons_sync();
+      if (threadIdx.x == 0)
+        for (int q = 0; q < TILE_PTS; ++q)
+          if (s_seg[q] >= 0) {
+            double* sa = segacc[s_seg[q]];
+            sa[0] += s_rr[q][0]; sa[1] += s_rr[q][1]; sa[2] += s_rr[q][2]; sa[3] += 1.0;
+          }
+      cons_sync();
+    }
+    if (a.want_grad) {
+    __syncwarp();
+    // weight-gradient A fragments (rows: Ubar_hi c, Ubar_lo 8 + c; k = the row's 16 points)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const bool live = g < D;
+      const uint32_t hrow = sUd_u + 2 * (((0 * 4 + r) * D + (live ? g : 0)) * 16 + 2 * t);
+      const uint32_t lrow = sUd_u + 2 * (((1 * 4 + r) * D + (live ? g : 0)) * 16 + 2 * t);
+      ua[r][0] = live ? lds32(hrow) : 0u;
+      ua[r][1] = live ? lds32(lrow) : 0u;
+      ua[r][2] = live ? lds32(hrow + 16) : 0u;
+      ua[r][3] = live ? lds32(lrow + 16) : 0u;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint32_t kc = sUb_u + (r * 16 + 8 * j + g) * 32 + 4 * t;   // point 8 j + g, k-slots 2t, 2t+1 (+8)
+        ub[r][j][0] = lds32(kc);
+        ub[r][j][1] = lds32(kc + 16);
+      }
+    }
+    __syncwarp();   // the scratch is the store staging from here on
+    }
+
+    prevT = a.want_grad ? Tc : -1;
   }
   if (threadIdx.x == 0) bulk_wait0();   // every bulk store has completed
   for (int i = 0; i < 5; ++i) {
