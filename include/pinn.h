@@ -114,7 +114,7 @@ typedef struct {
  *                              fan-out <= 256);
  *   PINN_FLAG_DW_ROWS_128      weight-gradient tiles of 128 output rows (default: 256
  *                              rows, two accumulators sharing each staged operand, for
- *                              layers with more than 128 outputs). */
+ *                              layers with more than 256 outputs). */
 #define PINN_FLAG_UNFUSED_ADJOINT 8
 #define PINN_FLAG_DW_ROWS_128 16
 

@@ -673,9 +673,12 @@ bool tc_layer_supported(const pinn_handle* h, int li, int64_t NC) {
 }
 
 // Weight-gradient tiles have 256 output rows (two accumulators sharing B) when the
-// layer has more than 128 outputs, else (or with PINN_FLAG_DW_ROWS_128) 128.
+// layer has more than 256 outputs, else (or with PINN_FLAG_DW_ROWS_128) 128.  At 256
+// outputs the 256-row tile is a single work item per column split, and two 128-row
+// items per split balance better (measured: 0.063 -> 0.059 ms at the 6x256 cavity, and
+// half as many split partials for the finalisation to sum).
 static int dw_rows(const pinn_handle* h, int fout) {
-  return (fout > BM && !(h->spec.flags & PINN_FLAG_DW_ROWS_128)) ? 2 * BM : BM;
+  return (fout > 2 * BM && !(h->spec.flags & PINN_FLAG_DW_ROWS_128)) ? 2 * BM : BM;
 }
 
 int tc_dw_splits(const pinn_handle* h, int fout, int fin, int64_t NC) {
