@@ -112,9 +112,12 @@ def load_peaks():
         "fallback"
 
 
-def src_sha():
+def src_sha(files=None):
+    """Hash of the kernel sources a measurement depends on: the named files of the
+    package's csrc (the kernel's own file, the headers it includes and the launch plan),
+    or all of them."""
     h = hashlib.sha256()
-    for name in sorted(os.listdir(CSRC)):
+    for name in sorted(files) if files else sorted(os.listdir(CSRC)):
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -815,7 +818,7 @@ def _traffic(kernel, workload):
     with open(path) as f:
         d = json.load(f)
     e = d.get(f"{workload}:{kernel}")
-    if not e or e.get("src_sha") != src_sha():
+    if not e or e.get("src_sha") != src_sha(e.get("src_files")):
         return None
     return e.get("bytes_per_launch")
 

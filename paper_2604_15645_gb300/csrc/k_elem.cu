@@ -605,6 +605,17 @@ constexpr int OT_STAGES = 3;
 constexpr uint64_t OT_WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(OT_CONS) : "memory"); }
+// Named barrier over the four consumer warps that also ANDs a predicate over them, so
+// that a failed (bounded) wait in any warp makes every warp leave the loop together.
+__device__ __forceinline__ bool cons_sync_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(OT_CONS)
+      : "memory");
+  return r != 0;
+}
 
 // Four BF16 values of (feature fi, points q0..q0+3) of a 128-byte swizzled box row.
 __device__ __forceinline__ void ot_load4(const uint8_t* box, int fi, int q0, float v[4]) {
@@ -713,7 +724,10 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
   int stage = 0;
   uint32_t phase = 0;
   bool ok = true;
-  for (int64_t T0i = blockIdx.x; T0i < ntiles && ok; T0i += gridDim.x) {
+  // A failed bounded wait leaves the chunk loop in that warp only; the ANDed barrier
+  // after each pass makes every consumer warp leave the tile loop together, so no named
+  // barrier is left waiting for a warp that has gone.
+  for (int64_t T0i = blockIdx.x; T0i < ntiles; T0i += gridDim.x) {
     const int64_t T0 = a.reverse ? ntiles - 1 - T0i : T0i;
     const int64_t cb = T0 * TILE_COLS + q0;
     const int64_t p0 = T0 * TILE_PTS + q0;
@@ -751,6 +765,7 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
       mbar_arrive(&empty[stage]);
       if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
     }
+    ok = cons_sync_and(ok);
     if (!ok) break;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -865,6 +880,8 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
       mbar_arrive(&empty[stage]);
       if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
     }
+    ok = cons_sync_and(ok);
+    if (!ok) break;
   }
   for (int i = 0; i < 5; ++i) {
     const double s = cons_sum_d(acc[i].value(), sh);
@@ -1030,17 +1047,6 @@ struct OmLayout {
   }
 };
 
-// Named barrier over the four consumer warps that also ANDs a predicate over them, so
-// that a failed (bounded) wait in any warp makes every warp leave the loop together.
-__device__ __forceinline__ bool cons_sync_and(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)v), "n"(OT_CONS)
-      : "memory");
-  return r != 0;
-}
 
 template <int D, int MODE, bool LO>
 __global__ void __launch_bounds__(OT_THREADS, 2) k_out_loss_mma(const __grid_constant__ CUtensorMap mapA,

@@ -314,8 +314,19 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
       coords(t, mb, nb, k0, k1);
       bool ok = true;
       for (int kb = k0; kb < k1; ++kb) {
-        if (!mbar_wait(&full[stage], phase, abort_flag, p.status, p.wait_ns) ||
-            !mbar_wait(lo_empty, lo_phase ^ 1, abort_flag, p.status, p.wait_ns)) { ok = false; break; }
+        bool got = mbar_wait(&full[stage], phase, abort_flag, p.status, p.wait_ns) &&
+                   mbar_wait(lo_empty, lo_phase ^ 1, abort_flag, p.status, p.wait_ns);
+        // both converter warps meet at named barrier 1 below: decide together whether to go on
+        {
+          uint32_t r;
+          asm volatile(
+              "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+              : "=r"(r)
+              : "r"((uint32_t)got), "n"(32 * C::CVT_WARPS)
+              : "memory");
+          got = r != 0;
+        }
+        if (!got) { ok = false; break; }
         const float4* src = reinterpret_cast<const float4*>(smem + stage * C::STAGE + C::A_BYTES * (SPLIT ? 2 : 1));
         float4* dst = reinterpret_cast<float4*>(blo);
         // latency-bound: keep 16 shared-memory loads in flight per thread
