@@ -528,7 +528,21 @@ def run_family(steps, warmup, ws_n, rank, local, precision="bf16", error_nets=4)
     ms = e0.elapsed_time(e1) / steps
     clk = clocks.stop()
     status = multi.status_poll()
-    ms_max, = max_over_ranks([ms], ws_n, dev)
+    # beside it, the same steps with one grouped tcgen05 launch per layer level
+    multi.grouped = True
+    for _ in range(warmup):
+        step += 1
+        multi.train_step(params, grad, m, v, step)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        step += 1
+        multi.train_step(params, grad, m, v, step)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_grouped = e0.elapsed_time(e1) / steps
+    multi.grouped = False
+    ms_max, ms_grouped_max = max_over_ranks([ms, ms_grouped], ws_n, dev)
     if rank != 0:
         return None
     engines = multi.engines()
@@ -537,7 +551,10 @@ def run_family(steps, warmup, ws_n, rank, local, precision="bf16", error_nets=4)
         "steps": steps, "warmup": warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
         "config": {"workload": "burgers_family_64", "networks": 64, "points_per_step": n_pts,
-                   "params": int(params.numel()), "step": "loss + adjoint + fused Adam, one CUDA graph",
+                   "params": int(params.numel()),
+                   "step": "loss + adjoint + fused Adam, one CUDA graph, each network's launches on one of "
+                           "32 worker streams",
+                   "grouped_level_launches_ms_per_step": round(ms_grouped_max, 4),
                    "engines": {"tc": engines.count("tc"), "cuda_cores": engines.count("cuda_cores")},
                    "autotune_s": round(t_tune, 2), "parallelism": f"replicas x{ws_n}"},
         "library_error_vs_oracle": err, "clocks": clk, "device_status": status,

@@ -400,9 +400,14 @@ PINN_API pinn_status pinn_debug_wait_expiry(pinn_handle* h, int M, int N, int K,
  * counts allowed).  pinn_multi_train_step runs, for every network, the loss and
  * gradient of its own batch and problem (as pinn_loss_grad), then one Adam step
  * (Sec. 2.6.5) over the concatenation of all parameter vectors.  The first call with
- * a given set of buffers captures the whole step in a CUDA graph (networks on
- * parallel worker streams, then the Adam launch); later calls replay it, updating
- * only the Adam scalars.  Parameters, gradients and Adam moments are single FP32
+ * a given set of buffers captures the whole step in a CUDA graph; later calls replay
+ * it, updating only the Adam scalars.  By default each network's launch sequence runs
+ * on one of up to 32 parallel worker streams.  With pinn_multi_set_grouped(m, 1) the
+ * step runs all networks level by level instead: at each layer level one grouped
+ * tcgen05 launch per kernel variant covers that level's tensor-core GEMMs of every
+ * network (each GEMM with the CTAs and work split of its own launch, so the results
+ * are bitwise those of separate launches), and the other launches of the level run on
+ * the worker streams.  Parameters, gradients and Adam moments are single FP32
  * device vectors laid out by pinn_multi_param_offsets (network i owns
  * [offsets[i], offsets[i+1])).  d_loss receives PINN_LOSS_TERMS doubles per network.
  * The workspace (pinn_multi_workspace_bytes) serves both GEMM engines, so
@@ -428,8 +433,21 @@ PINN_API pinn_status pinn_multi_get_config(const pinn_multi* m, int32_t net, int
  * default tcgen05 configuration 0. */
 PINN_API pinn_status pinn_multi_set_engine(pinn_multi* m, int32_t net, int32_t cuda_cores);
 PINN_API pinn_status pinn_multi_get_engine(const pinn_multi* m, int32_t net, int32_t* cuda_cores);
+/* on = 1: grouped launches per layer level, as above; on = 0 (the default): each
+ * network's launch sequence (pinn_loss_grad's launches) on its worker stream, the
+ * networks side by side.  Both give bitwise the same step.  The grouped step keeps a
+ * level's data of all networks in flight at once, where the per-network sequences
+ * read each layer's input while the layer below has just left it in L2, and it waits
+ * for the slowest network at every level: on the 64-network Burgers family it is the
+ * slower of the two on one GB300 (measured).  A change takes effect
+ * with the next pinn_multi_train_step, which captures a new graph.  A bounded wait
+ * that expires inside a grouped launch is reported (PINN_ERR_TIMEOUT, through
+ * pinn_multi_status_poll) on the network whose GEMM the waiting CTA was running. */
+PINN_API pinn_status pinn_multi_set_grouped(pinn_multi* m, int32_t on);
+PINN_API pinn_status pinn_multi_get_grouped(const pinn_multi* m, int32_t* on);
 /* One training step (1-based `step`); asynchronous on `stream` except for graph
- * (re)capture on the first call with new buffers. */
+ * (re)capture on the first call with new buffers, which also synchronises `stream`
+ * and may allocate (the grouped launches' device table). */
 PINN_API pinn_status pinn_multi_train_step(pinn_multi* m, const pinn_problem* probs, const pinn_batch* batches,
                                            float* d_params, float* d_grad, float* d_m, float* d_v, int64_t step,
                                            float lr, float beta1, float beta2, float eps, void* d_ws,

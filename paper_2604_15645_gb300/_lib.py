@@ -32,7 +32,8 @@ EXPORTS = ["pinn_create", "pinn_destroy", "pinn_param_count", "pinn_workspace_by
            "pinn_lbfgs_create", "pinn_lbfgs_destroy", "pinn_lbfgs_reset", "pinn_lbfgs_step", "pinn_lbfgs_direction",
            "pinn_lbfgs_push_pair", "pinn_set_activation", "pinn_set_periodic", "pinn_loss_grad_ff",
            "pinn_set_graph", "pinn_set_global_counts", "pinn_graph_held", "pinn_debug_wait_expiry",
-           "pinn_layer_engines", "pinn_multi_set_config", "pinn_multi_get_config"]
+           "pinn_layer_engines", "pinn_multi_set_config", "pinn_multi_get_config", "pinn_multi_set_grouped",
+           "pinn_multi_get_grouped"]
 PINN_ACT_TANH, PINN_ACT_SINE = 0, 1
 PINN_STATIC_WS_BYTES = 64 << 20
 PINN_PROF_PHASES = 9
@@ -100,6 +101,8 @@ def load(path: str = LIB_PATH):
     lib.pinn_multi_get_engine.argtypes = [H, C.c_int32, C.POINTER(C.c_int32)]
     lib.pinn_multi_set_config.argtypes = [H, C.c_int32, C.c_int32]
     lib.pinn_multi_get_config.argtypes = [H, C.c_int32, C.POINTER(C.c_int32)]
+    lib.pinn_multi_set_grouped.argtypes = [H, C.c_int32]
+    lib.pinn_multi_get_grouped.argtypes = [H, C.POINTER(C.c_int32)]
     lib.pinn_multi_train_step.argtypes = [H, C.POINTER(pinn_problem), C.POINTER(pinn_batch), C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_float,
                                           C.c_float, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]

@@ -282,6 +282,18 @@ class PinnMulti:
     def set_config(self, i, config):
         _lib.check_multi(_lib.load().pinn_multi_set_config(self.h, i, self.CONFIGS.index(config)), self.h)
 
+    @property
+    def grouped(self):
+        """True: one grouped tcgen05 launch per layer level over all networks; False
+        (the default): each network's launches on its own worker stream."""
+        v = _lib.C.c_int32()
+        _lib.check_multi(_lib.load().pinn_multi_get_grouped(self.h, _lib.C.byref(v)), self.h)
+        return bool(v.value)
+
+    @grouped.setter
+    def grouped(self, on):
+        _lib.check_multi(_lib.load().pinn_multi_set_grouped(self.h, int(bool(on))), self.h)
+
     def set_engine(self, i, cuda_cores):
         _lib.check_multi(_lib.load().pinn_multi_set_engine(self.h, i, int(bool(cuda_cores))), self.h)
 

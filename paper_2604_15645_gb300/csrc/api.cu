@@ -204,61 +204,88 @@ struct PassCtx {
   double* loss_acc;            // 5 FP64 running loss sums (chunked calls only)
 };
 
-// One forward + reverse sweep over the points of `b` (the whole batch, or one chunk).
-pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
-                     char* ws, size_t ws_bytes, double* d_loss, float* d_grad, cudaStream_t st, bool want_grad,
-                     const PassCtx& pc, float* d_grad_terms = nullptr, float* d_grad_ff = nullptr) {
-  pinn_status s = PINN_OK;
+// One forward + reverse sweep over the points of `b` (the whole batch, or one chunk),
+// in stages: the prologue (RWF weights, input jets), one forward stage per GEMM layer,
+// then per loss term the output stage, one backward stage per hidden layer (top down)
+// and the gradient finalisation.  run_pass runs the stages in this order; the
+// many-network step runs the stages of all its networks level by level, so that their
+// tensor-core GEMMs of one level share grouped launches.
+struct Pass {
+  pinn_handle* h = nullptr;
+  const pinn_problem* prob = nullptr;
+  const pinn_batch* b = nullptr;
+  const float* d_params = nullptr;
+  char* ws = nullptr;
+  double* d_loss = nullptr;
+  float* d_grad = nullptr;
+  bool want_grad = false;
+  PassCtx pc{};
+  float* d_grad_terms = nullptr;   // per-term gradients [3][P] (Sec. 2.6.4), or null
+  float* d_grad_ff = nullptr;      // input-map gradient, or null
   CallPlan cp;
-  plan_call(h, b->n_res, b->n_ic, b->n_bc, &cp);
-  if (ws_bytes < cp.p.total) {
-    set_err(h, "workspace too small: %zu < %zu bytes", ws_bytes, cp.p.total); return PINN_ERR_WORKSPACE;
-  }
-  const Plan& p = cp.p;
-  const int L = h->L, L1 = L + 1, prec = h->spec.precision;
-  const int mode = h->jet_mode;
-  const bool sine = h->act == PINN_ACT_SINE;
+  // the loss term of the output, backward and finalisation stages
+  int term = 0;
+  double lam_pde = 0, lam_ic = 0, lam_bc = 0;
+  float* grad_out = nullptr;
+  OutArgs oa{};
 
-  // 1. RWF weights (Eq. 15) for every layer.
-  RwfArgs ra{};
-  ra.params = d_params; ra.ws = ws; ra.L1 = L1; ra.rwf = h->spec.rwf; ra.prec = prec;
-  for (int li = 0; li < L1; ++li) {
-    ra.fin[li] = cp.lay[li].fin; ra.fout[li] = cp.lay[li].fout;
-    ra.offV[li] = cp.lay[li].off_V; ra.offs[li] = cp.lay[li].off_s;
-    ra.w32[li] = cp.lay[li].w32; ra.wc[li] = cp.lay[li].wc; ra.wtc[li] = cp.lay[li].wtc;
-    ra.wt32[li] = cp.lay[li].wt32; ra.wlo[li] = cp.lay[li].wlo; ra.wtlo[li] = cp.lay[li].wtlo;
-  }
-  { PhaseScope ps(h, st, PH_RWF, 1); launch_rwf_prep(ra, st); }
+  int nterms() const { return d_grad_terms ? 3 : 1; }
+  const float* W32(int li) const { return reinterpret_cast<const float*>(ws + cp.lay[li].w32); }
+  const float* bias(int li) const { return d_params + cp.lay[li].off_b; }
 
-  auto W32 = [&](int li) { return reinterpret_cast<const float*>(ws + cp.lay[li].w32); };
-  auto bias = [&](int li) { return d_params + cp.lay[li].off_b; };
-
-  // 2. Input embedding jets (Eq. 14) or the first layer on raw coordinates.
-  {
-  PhaseScope ps(h, st, PH_EMBED, 1);
-  if (h->spec.ff_m) {
-    launch_embed_ff(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, h->ff_B, h->spec.ff_m, mode,
-                    ws + p.A[0], p.lo ? ws + p.Alo[0] : nullptr, p.NP, prec, st);
-  } else {
-    launch_first_layer(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, W32(0), bias(0),
-                       cp.lay[0].fout, mode, ws + p.A[1], p.lo ? ws + p.Alo[1] : nullptr, p.NP, prec, h->omega0,
-                       sine ? reinterpret_cast<float*>(ws + p.Z[1]) : nullptr, st);
-  }
-  if (cp.pm) {
-    const int f0 = h->first_gemm;
-    launch_to_point_major(ws + p.A[f0], ws + cp.apm[f0 % 2], cp.lay[f0].fin, p.NC, st);
-  }
+  pinn_status init(size_t ws_bytes) {
+    plan_call(h, b->n_res, b->n_ic, b->n_bc, &cp);
+    if (ws_bytes < cp.p.total) {
+      set_err(h, "workspace too small: %zu < %zu bytes", ws_bytes, cp.p.total); return PINN_ERR_WORKSPACE;
+    }
+    return PINN_OK;
   }
 
-  // 3. Hidden jet GEMMs with the tanh-jet epilogue.
-  for (int li = h->first_gemm; li < L; ++li) {
+  // 1-2: RWF weights and the input jets.
+  pinn_status prologue(cudaStream_t st) {
+    const Plan& p = cp.p;
+    const int L1 = h->L + 1, prec = h->spec.precision, mode = h->jet_mode;
+    const bool sine = h->act == PINN_ACT_SINE;
+    // 1. RWF weights (Eq. 15) for every layer.
+    RwfArgs ra{};
+    ra.params = d_params; ra.ws = ws; ra.L1 = L1; ra.rwf = h->spec.rwf; ra.prec = prec;
+    for (int li = 0; li < L1; ++li) {
+      ra.fin[li] = cp.lay[li].fin; ra.fout[li] = cp.lay[li].fout;
+      ra.offV[li] = cp.lay[li].off_V; ra.offs[li] = cp.lay[li].off_s;
+      ra.w32[li] = cp.lay[li].w32; ra.wc[li] = cp.lay[li].wc; ra.wtc[li] = cp.lay[li].wtc;
+      ra.wt32[li] = cp.lay[li].wt32; ra.wlo[li] = cp.lay[li].wlo; ra.wtlo[li] = cp.lay[li].wtlo;
+    }
+    { PhaseScope ps(h, st, PH_RWF, 1); launch_rwf_prep(ra, st); }
+
+    // 2. Input embedding jets (Eq. 14) or the first layer on raw coordinates.
+    PhaseScope ps(h, st, PH_EMBED, 1);
+    if (h->spec.ff_m) {
+      launch_embed_ff(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, h->ff_B, h->spec.ff_m, mode,
+                      ws + p.A[0], p.lo ? ws + p.Alo[0] : nullptr, p.NP, prec, st);
+    } else {
+      launch_first_layer(b->x_res, b->x_ic, b->x_bc, b->n_res, b->n_ic, b->n_bc, h->d_in, W32(0), bias(0),
+                         cp.lay[0].fout, mode, ws + p.A[1], p.lo ? ws + p.Alo[1] : nullptr, p.NP, prec, h->omega0,
+                         sine ? reinterpret_cast<float*>(ws + p.Z[1]) : nullptr, st);
+    }
+    if (cp.pm) {
+      const int f0 = h->first_gemm;
+      launch_to_point_major(ws + p.A[f0], ws + cp.apm[f0 % 2], cp.lay[f0].fin, p.NC, st);
+    }
+    return PINN_OK;
+  }
+
+  // 3. Hidden jet GEMM li (first_gemm <= li < L) with the tanh-jet epilogue.
+  pinn_status forward(int li, cudaStream_t st) {
+    const Plan& p = cp.p;
+    const int L = h->L, prec = h->spec.precision;
+    const bool sine = h->act == PINN_ACT_SINE;
     EpiArgs e{};
     e.bias = bias(li); e.out = ws + p.A[li + 1];
     e.alo_out = p.lo ? ws + p.Alo[li + 1] : nullptr;
     // BF16 storage is rounded, so consumers add the low half back; TF32 storage is
     // exact FP32 and only the tensor-core forward (which truncates) uses the low half.
     e.alo_in = (p.lo && prec == PINN_BF16) ? ws + p.Alo[li] : nullptr;
-    e.jet_mode = mode;
+    e.jet_mode = h->jet_mode;
     e.act = h->act; e.omega0 = h->omega0;
     e.zout = sine ? reinterpret_cast<float*>(ws + p.Z[li + 1]) : nullptr;
     // alternate the tile order from layer to layer: each forward starts on the tiles
@@ -268,109 +295,116 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
     if (cp.tc[li] && cp.pm) {
       // TF32: point-major input; the epilogue also writes the next layer's point-major input
       e.out_pm = (li + 1 < L) ? ws + cp.apm[(li + 1) % 2] : nullptr;
-      s = tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + cp.lay[li].wlo, ws + cp.apm[li % 2], nullptr, cp.lay[li].fout,
-                      cp.lay[li].fin, p.NC, e, st);
-      if (s) return s;
-    } else if (cp.tc[li]) {
-      s = tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + cp.lay[li].wlo, ws + p.A[li], ws + p.Alo[li], cp.lay[li].fout,
-                      cp.lay[li].fin, p.NC, e, st);
-      if (s) return s;
-    } else {
-      launch_simt_gemm_fwd(W32(li), ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NP, e, prec, st);
+      return tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + cp.lay[li].wlo, ws + cp.apm[li % 2], nullptr, cp.lay[li].fout,
+                         cp.lay[li].fin, p.NC, e, st);
     }
+    if (cp.tc[li])
+      return tc_gemm_fwd(h, ws + cp.lay[li].wc, ws + cp.lay[li].wlo, ws + p.A[li], ws + p.Alo[li], cp.lay[li].fout,
+                         cp.lay[li].fin, p.NC, e, st);
+    launch_simt_gemm_fwd(W32(li), ws + p.A[li], cp.lay[li].fout, cp.lay[li].fin, p.NP, e, prec, st);
+    return PINN_OK;
   }
 
-  // 4-7 run once for the weighted loss, or once per loss term (weight 1 for that term,
-  // 0 for the others) when the per-term gradients are asked for (Sec. 2.6.4); the
-  // forward jets above are shared.
-  const int nterms = d_grad_terms ? 3 : 1;
-  for (int term = 0; term < nterms; ++term) {
-  const double lam_pde = d_grad_terms ? (term == 0 ? 1.0 : 0.0) : prob->lambda_pde;
-  const double lam_ic = d_grad_terms ? (term == 1 ? 1.0 : 0.0) : prob->lambda_ic;
-  const double lam_bc = d_grad_terms ? (term == 2 ? 1.0 : 0.0) : prob->lambda_bc;
-  float* grad_out = d_grad_terms ? d_grad_terms + (size_t)term * h->P : d_grad;
+  // 4-5 for loss term t (one weighted term, or term t of the per-term gradients):
+  // output layer, residual, loss partials, adjoint seed and Zbar_L; then the output
+  // layer's dW partials compacted.  Without a gradient the pass ends here.
+  pinn_status output(int t, cudaStream_t st) {
+    const Plan& p = cp.p;
+    const int L = h->L, prec = h->spec.precision, mode = h->jet_mode;
+    const bool sine = h->act == PINN_ACT_SINE;
+    term = t;
+    lam_pde = d_grad_terms ? (term == 0 ? 1.0 : 0.0) : prob->lambda_pde;
+    lam_ic = d_grad_terms ? (term == 1 ? 1.0 : 0.0) : prob->lambda_ic;
+    lam_bc = d_grad_terms ? (term == 2 ? 1.0 : 0.0) : prob->lambda_bc;
+    grad_out = d_grad_terms ? d_grad_terms + (size_t)term * h->P : d_grad;
 
-  // 4. Output layer, residual, loss partials, adjoint seed and Zbar_L.
-  OutArgs oa{};
-  oa.AL = ws + p.A[L]; oa.ALlo = (p.lo && prec == PINN_BF16) ? ws + p.Alo[L] : nullptr;
-  oa.W = W32(L); oa.b = bias(L);
-  oa.g_ic = b->g_ic; oa.g_bc = b->g_bc; oa.ic_mask = b->ic_mask; oa.bc_mask = b->bc_mask;
-  oa.n_res = p.n_res; oa.n_ic = p.n_ic; oa.n_bc = p.n_bc; oa.NP = p.NP; oa.NC = p.NC;
-  oa.w = cp.lay[L].fin; oa.d_out = h->d_out; oa.pde = h->spec.pde; oa.jet_mode = mode;
-  oa.nu = (float)prob->nu;
-  oa.k_pde = pc.N_res ? (float)(lam_pde / (double)pc.N_res) : 0.f;
-  oa.k_ic = pc.N_ic ? (float)(lam_ic / (double)pc.N_ic) : 0.f;
-  oa.k_bc = pc.N_bc ? (float)(lam_bc / (double)pc.N_bc) : 0.f;
-  oa.want_grad = want_grad;
-  oa.x_res = b->x_res;
-  oa.dwpart = reinterpret_cast<float*>(ws + cp.lay[L].dwpart);
-  oa.dbpart = reinterpret_cast<float*>(ws + cp.lay[L].dbpart);
-  oa.dbhid = cp.out_db ? reinterpret_cast<float*>(ws + cp.lay[L - 1].dbpart) : nullptr;
-  oa.Zbar = ws + p.Zbar[L % 2];
-  oa.ZL = sine ? reinterpret_cast<const float*>(ws + p.Z[L]) : nullptr;
-  oa.reverse = ((L - 1 - h->first_gemm) % 2 == 0) ? 0 : 1;   // against the last forward's order
-  oa.omega0 = h->omega0;
-  oa.losspart = reinterpret_cast<double*>(ws + p.losspart);
-  oa.status = h->d_status;
-  const bool causal = h->causal_M > 0;
-  double* causal_omega = h->d_scratch + 256;                           // [CAUSAL_MAX] doubles
-  float* causal_scale = reinterpret_cast<float*>(h->d_scratch + 288);   // [CAUSAL_MAX] floats
-  if (causal) {
-    // Temporal causality (Sec. 2.6.8): a first pass gathers the segment losses, the
-    // weights follow, and the seeds of the second pass are scaled per segment.
-    oa.segments = h->causal_M;
-    oa.t_index = h->spec.pde == PINN_MAXWELL_TE_2D ? 2 : 1;
-    oa.t0 = (float)h->causal_t0;
-    oa.tinv = (float)(h->causal_M / (h->causal_t1 - h->causal_t0));
-    if (term == 0) {
-      OutArgs o1 = oa;
-      o1.want_grad = 0;
-      o1.segpart = reinterpret_cast<double*>(ws + p.segpart);
+    // 4. Output layer, residual, loss partials, adjoint seed and Zbar_L.
+    oa = OutArgs{};
+    oa.AL = ws + p.A[L]; oa.ALlo = (p.lo && prec == PINN_BF16) ? ws + p.Alo[L] : nullptr;
+    oa.W = W32(L); oa.b = bias(L);
+    oa.g_ic = b->g_ic; oa.g_bc = b->g_bc; oa.ic_mask = b->ic_mask; oa.bc_mask = b->bc_mask;
+    oa.n_res = p.n_res; oa.n_ic = p.n_ic; oa.n_bc = p.n_bc; oa.NP = p.NP; oa.NC = p.NC;
+    oa.w = cp.lay[L].fin; oa.d_out = h->d_out; oa.pde = h->spec.pde; oa.jet_mode = mode;
+    oa.nu = (float)prob->nu;
+    oa.k_pde = pc.N_res ? (float)(lam_pde / (double)pc.N_res) : 0.f;
+    oa.k_ic = pc.N_ic ? (float)(lam_ic / (double)pc.N_ic) : 0.f;
+    oa.k_bc = pc.N_bc ? (float)(lam_bc / (double)pc.N_bc) : 0.f;
+    oa.want_grad = want_grad;
+    oa.x_res = b->x_res;
+    oa.dwpart = reinterpret_cast<float*>(ws + cp.lay[L].dwpart);
+    oa.dbpart = reinterpret_cast<float*>(ws + cp.lay[L].dbpart);
+    oa.dbhid = cp.out_db ? reinterpret_cast<float*>(ws + cp.lay[L - 1].dbpart) : nullptr;
+    oa.Zbar = ws + p.Zbar[L % 2];
+    oa.ZL = sine ? reinterpret_cast<const float*>(ws + p.Z[L]) : nullptr;
+    oa.reverse = ((L - 1 - h->first_gemm) % 2 == 0) ? 0 : 1;   // against the last forward's order
+    oa.omega0 = h->omega0;
+    oa.losspart = reinterpret_cast<double*>(ws + p.losspart);
+    oa.status = h->d_status;
+    const bool causal = h->causal_M > 0;
+    double* causal_omega = h->d_scratch + 256;                           // [CAUSAL_MAX] doubles
+    float* causal_scale = reinterpret_cast<float*>(h->d_scratch + 288);   // [CAUSAL_MAX] floats
+    if (causal) {
+      // Temporal causality (Sec. 2.6.8): a first pass gathers the segment losses, the
+      // weights follow, and the seeds of the second pass are scaled per segment.
+      oa.segments = h->causal_M;
+      oa.t_index = h->spec.pde == PINN_MAXWELL_TE_2D ? 2 : 1;
+      oa.t0 = (float)h->causal_t0;
+      oa.tinv = (float)(h->causal_M / (h->causal_t1 - h->causal_t0));
+      if (term == 0) {
+        OutArgs o1 = oa;
+        o1.want_grad = 0;
+        o1.segpart = reinterpret_cast<double*>(ws + p.segpart);
+        PhaseScope ps(h, st, PH_OUT, 1);
+        const cudaError_t e = launch_out_loss(o1, prec, p.nloss_blocks, st);
+        if (e != cudaSuccess) return cuda_check(h, e, "output/loss launch");
+        launch_finalize_causal(o1.segpart, o1.losspart, p.nloss_blocks, h->causal_M, h->causal_eps,
+                               b->ic_mask ? pc.N_ic : 0, b->bc_mask ? pc.N_bc : 0, prob->lambda_pde,
+                               prob->lambda_ic, prob->lambda_bc, lam_pde, d_loss, causal_omega, causal_scale,
+                               h->d_status, st);
+      }
+      oa.seg_scale = lam_pde != 0.0 ? causal_scale : nullptr;
+    }
+    if (!causal || want_grad) {
       PhaseScope ps(h, st, PH_OUT, 1);
-      const cudaError_t e = launch_out_loss(o1, prec, p.nloss_blocks, st);
+      const cudaError_t e = launch_out_loss(oa, prec, p.nloss_blocks, st);
       if (e != cudaSuccess) return cuda_check(h, e, "output/loss launch");
-      launch_finalize_causal(o1.segpart, o1.losspart, p.nloss_blocks, h->causal_M, h->causal_eps,
-                             b->ic_mask ? pc.N_ic : 0, b->bc_mask ? pc.N_bc : 0, prob->lambda_pde, prob->lambda_ic,
-                             prob->lambda_bc, lam_pde, d_loss, causal_omega, causal_scale, h->d_status, st);
     }
-    oa.seg_scale = lam_pde != 0.0 ? causal_scale : nullptr;
-  }
-  if (!causal || want_grad) {
-    PhaseScope ps(h, st, PH_OUT, 1);
-    const cudaError_t e = launch_out_loss(oa, prec, p.nloss_blocks, st);
-    if (e != cudaSuccess) return cuda_check(h, e, "output/loss launch");
-  }
-  if (term == 0 && !causal) {   // the loss terms are unweighted sums; the total uses the problem's weights
-  PhaseScope ps_fl(h, st, PH_RED, 1);
-  launch_finalize_loss(oa.losspart, p.nloss_blocks, pc.N_res, (b->ic_mask ? pc.N_ic : 0), (b->bc_mask ? pc.N_bc : 0),
-                       prob->lambda_pde, prob->lambda_ic, prob->lambda_bc, d_loss, pc.loss_acc, pc.first, pc.last,
-                       h->d_status, st);
-  }
-  if (!want_grad) return cuda_check(h, cudaGetLastError(), "loss launch");
-  if (cp.pm) {
-    PhaseScope ps(h, st, PH_OTHER, 1);
-    launch_to_point_major(ws + p.Zbar[L % 2], ws + cp.zbpm[L % 2], cp.lay[L].fin, p.NC, st);
-  }
+    if (term == 0 && !causal) {   // the loss terms are unweighted sums; the total uses the problem's weights
+      PhaseScope ps_fl(h, st, PH_RED, 1);
+      launch_finalize_loss(oa.losspart, p.nloss_blocks, pc.N_res, (b->ic_mask ? pc.N_ic : 0),
+                           (b->bc_mask ? pc.N_bc : 0), prob->lambda_pde, prob->lambda_ic, prob->lambda_bc, d_loss,
+                           pc.loss_acc, pc.first, pc.last, h->d_status, st);
+    }
+    if (!want_grad) return PINN_OK;
+    if (cp.pm) {
+      PhaseScope ps(h, st, PH_OTHER, 1);
+      launch_to_point_major(ws + p.Zbar[L % 2], ws + cp.zbpm[L % 2], cp.lay[L].fin, p.NC, st);
+    }
 
-  // 5. The output layer's dW and bias partials came from the output/loss kernel; its
-  //    per-block dW partials are compacted (in order) so the finalisation reads a few.
-  {
+    // 5. The output layer's dW and bias partials came from the output/loss kernel; its
+    //    per-block dW partials are compacted (in order) so the finalisation reads a few.
     PhaseScope ps(h, st, PH_RED, 1);
     const LayerPlan& lo = cp.lay[L];
     float* part = reinterpret_cast<float*>(ws + lo.dwpart);
     launch_sum_splits(part, part + (size_t)lo.nsplit * lo.fout * lo.fin, lo.nsplit, OUT_SUM_SLOTS,
                       (int64_t)lo.fout * lo.fin, st);
+    return PINN_OK;
   }
 
-  // 6. Hidden layers in reverse: dW, db, then the adjoint GEMM into the layer below.
-  for (int li = L - 1; li >= 0; --li) {
+  // 6. Hidden layer li (L-1 down to 0): dW, db, then the adjoint GEMM into the layer below.
+  pinn_status backward(int li, cudaStream_t st) {
+    const Plan& p = cp.p;
+    const int L = h->L, prec = h->spec.precision, mode = h->jet_mode;
+    const bool sine = h->act == PINN_ACT_SINE;
+    pinn_status s = PINN_OK;
     const LayerPlan& lp = cp.lay[li];
     void* zb = ws + p.Zbar[(li + 1) % 2];
     const bool raw = (li == 0 && !h->spec.ff_m);
     if (!raw && !cp.fused[li]) {   // (a fused layer's weight gradient comes with its adjoint below)
       PhaseScope ps(h, st, PH_DW, 1);
       if (cp.tc[li]) {
-        s = tc_gemm_dw(h, zb, ws + p.A[li], lp.fout, lp.fin, p.NC, lp.nsplit, reinterpret_cast<float*>(ws + lp.dwpart), st);
+        s = tc_gemm_dw(h, zb, ws + p.A[li], lp.fout, lp.fin, p.NC, lp.nsplit, reinterpret_cast<float*>(ws + lp.dwpart),
+                       st);
         if (s) return s;
       } else {
         launch_simt_gemm_dw(zb, false, ws + p.A[li], false, lp.fout, lp.fin, p.NC, lp.nsplit,
@@ -393,57 +427,81 @@ pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch*
                      h->spec.ff_m, mode, p.NP, ffpart, prec, st);
       launch_ff_grad_final(ffpart, h->d_in, h->spec.ff_m, h->periodic, h->periods, pc.first ? 0 : 1, d_grad_ff, st);
     }
-    if (li >= 1) {
-      EpiArgs e{};
-      e.out = ws + p.Zbar[li % 2]; e.ain = ws + p.A[li];
-      e.ain_lo = p.lo ? ws + p.Alo[li] : nullptr;
-      e.jet_mode = mode;
-      e.act = h->act; e.omega0 = h->omega0;
-      e.zin = sine ? reinterpret_cast<const float*>(ws + p.Z[li]) : nullptr;
-      // against the order in which the adjoint it reads was written
-      e.reverse = (((L - 1 - li) % 2 == 0) == (oa.reverse != 0)) ? 0 : 1;
-      if (cp.fused_db[li - 1]) {
-        e.dbpart = reinterpret_cast<float*>(ws + cp.lay[li - 1].dbpart);
-        e.dterms = (li - 1 == 0 && !h->spec.ff_m) ? h->d_in : 0;
-        e.x_res = b->x_res; e.x_ic = b->x_ic; e.x_bc = b->x_bc;
-        e.n_res = p.n_res; e.n_ic = p.n_ic; e.n_bc = p.n_bc;
-      }
-      PhaseScope ps(h, st, cp.fused[li] ? PH_ADJDW : PH_ADJ, 1);
-      if (cp.fused[li]) {
-        s = tc_gemm_adjdw(h, ws + lp.wtc, zb, ws + p.A[li], lp.fin, lp.fout, p.NC, e,
-                          reinterpret_cast<float*>(ws + lp.dwpart), lp.nsplit, st);
-        if (s) return s;
-      } else if (cp.tc[li] && cp.pm) {
-        e.out_pm = (li - 1 >= 1) ? ws + cp.zbpm[li % 2] : nullptr;
-        s = tc_gemm_adj(h, ws + lp.wtc, ws + lp.wtlo, ws + cp.zbpm[(li + 1) % 2], lp.fin, lp.fout, p.NC, e, st);
-        if (s) return s;
-      } else if (cp.tc[li]) {
-        s = tc_gemm_adj(h, ws + lp.wtc, nullptr, zb, lp.fin, lp.fout, p.NC, e, st);
-        if (s) return s;
-      } else {
-        launch_simt_gemm_adj(reinterpret_cast<const float*>(ws + lp.wt32), zb, lp.fin, lp.fout, p.NP, e, prec, st);
-      }
+    if (li < 1) return PINN_OK;
+    EpiArgs e{};
+    e.out = ws + p.Zbar[li % 2]; e.ain = ws + p.A[li];
+    e.ain_lo = p.lo ? ws + p.Alo[li] : nullptr;
+    e.jet_mode = mode;
+    e.act = h->act; e.omega0 = h->omega0;
+    e.zin = sine ? reinterpret_cast<const float*>(ws + p.Z[li]) : nullptr;
+    // against the order in which the adjoint it reads was written
+    e.reverse = (((L - 1 - li) % 2 == 0) == (oa.reverse != 0)) ? 0 : 1;
+    if (cp.fused_db[li - 1]) {
+      e.dbpart = reinterpret_cast<float*>(ws + cp.lay[li - 1].dbpart);
+      e.dterms = (li - 1 == 0 && !h->spec.ff_m) ? h->d_in : 0;
+      e.x_res = b->x_res; e.x_ic = b->x_ic; e.x_bc = b->x_bc;
+      e.n_res = p.n_res; e.n_ic = p.n_ic; e.n_bc = p.n_bc;
     }
+    PhaseScope ps(h, st, cp.fused[li] ? PH_ADJDW : PH_ADJ, 1);
+    if (cp.fused[li])
+      return tc_gemm_adjdw(h, ws + lp.wtc, zb, ws + p.A[li], lp.fin, lp.fout, p.NC, e,
+                           reinterpret_cast<float*>(ws + lp.dwpart), lp.nsplit, st);
+    if (cp.tc[li] && cp.pm) {
+      e.out_pm = (li - 1 >= 1) ? ws + cp.zbpm[li % 2] : nullptr;
+      return tc_gemm_adj(h, ws + lp.wtc, ws + lp.wtlo, ws + cp.zbpm[(li + 1) % 2], lp.fin, lp.fout, p.NC, e, st);
+    }
+    if (cp.tc[li]) return tc_gemm_adj(h, ws + lp.wtc, nullptr, zb, lp.fin, lp.fout, p.NC, e, st);
+    launch_simt_gemm_adj(reinterpret_cast<const float*>(ws + lp.wt32), zb, lp.fin, lp.fout, p.NP, e, prec, st);
+    return PINN_OK;
   }
 
   // 7. Ordered FP64 reduction + RWF chain rule into the packed gradient.
-  FinalizeArgs fa{};
-  fa.params = d_params; fa.grad = grad_out; fa.ws = ws; fa.L1 = L1; fa.rwf = h->spec.rwf;
-  fa.first_raw = !h->spec.ff_m; fa.nbpart = p.nbpart; fa.accumulate = pc.first ? 0 : 1;
-  for (int li = 0; li < L1; ++li) {
-    fa.fin[li] = cp.lay[li].fin; fa.fout[li] = cp.lay[li].fout;
-    fa.offV[li] = cp.lay[li].off_V; fa.offs[li] = cp.lay[li].off_s; fa.offb[li] = cp.lay[li].off_b;
-    fa.w32[li] = cp.lay[li].w32; fa.dwpart[li] = cp.lay[li].dwpart; fa.dbpart[li] = cp.lay[li].dbpart;
-    fa.nsplit[li] = cp.lay[li].nsplit;
-    if (li == L) {   // the compacted output-layer partials
-      fa.dwpart[li] += (size_t)cp.lay[li].nsplit * cp.lay[li].fout * cp.lay[li].fin * 4;
-      fa.nsplit[li] = OUT_SUM_SLOTS;
+  pinn_status finalize(cudaStream_t st) {
+    const Plan& p = cp.p;
+    const int L = h->L, L1 = L + 1;
+    FinalizeArgs fa{};
+    fa.params = d_params; fa.grad = grad_out; fa.ws = ws; fa.L1 = L1; fa.rwf = h->spec.rwf;
+    fa.first_raw = !h->spec.ff_m; fa.nbpart = p.nbpart; fa.accumulate = pc.first ? 0 : 1;
+    for (int li = 0; li < L1; ++li) {
+      fa.fin[li] = cp.lay[li].fin; fa.fout[li] = cp.lay[li].fout;
+      fa.offV[li] = cp.lay[li].off_V; fa.offs[li] = cp.lay[li].off_s; fa.offb[li] = cp.lay[li].off_b;
+      fa.w32[li] = cp.lay[li].w32; fa.dwpart[li] = cp.lay[li].dwpart; fa.dbpart[li] = cp.lay[li].dbpart;
+      fa.nsplit[li] = cp.lay[li].nsplit;
+      if (li == L) {   // the compacted output-layer partials
+        fa.dwpart[li] += (size_t)cp.lay[li].nsplit * cp.lay[li].fout * cp.lay[li].fin * 4;
+        fa.nsplit[li] = OUT_SUM_SLOTS;
+      }
+      fa.nbpart_l[li] = cp.nbpart[li];
+      fa.dbstride[li] = (li == 0 && fa.first_raw) ? 1 + h->d_in : 1;
     }
-    fa.nbpart_l[li] = cp.nbpart[li];
-    fa.dbstride[li] = (li == 0 && fa.first_raw) ? 1 + h->d_in : 1;
+    PhaseScope ps(h, st, PH_RED, 1);
+    launch_finalize_grad(fa, st);
+    return PINN_OK;
   }
-  { PhaseScope ps(h, st, PH_RED, 1); launch_finalize_grad(fa, st); }
-  }   // terms
+};
+
+pinn_status run_pass(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
+                     char* ws, size_t ws_bytes, double* d_loss, float* d_grad, cudaStream_t st, bool want_grad,
+                     const PassCtx& pc, float* d_grad_terms = nullptr, float* d_grad_ff = nullptr) {
+  Pass ps;
+  ps.h = h; ps.prob = prob; ps.b = b; ps.d_params = d_params; ps.ws = ws; ps.d_loss = d_loss; ps.d_grad = d_grad;
+  ps.want_grad = want_grad; ps.pc = pc; ps.d_grad_terms = d_grad_terms; ps.d_grad_ff = d_grad_ff;
+  pinn_status s = ps.init(ws_bytes);
+  if (s) return s;
+  s = ps.prologue(st);
+  for (int li = h->first_gemm; li < h->L && !s; ++li) s = ps.forward(li, st);
+  if (s) return s;
+  // 4-7 run once for the weighted loss, or once per loss term (weight 1 for that term,
+  // 0 for the others) when the per-term gradients are asked for (Sec. 2.6.4); the
+  // forward jets above are shared.
+  for (int term = 0; term < ps.nterms(); ++term) {
+    s = ps.output(term, st);
+    if (s) return s;
+    if (!want_grad) return cuda_check(h, cudaGetLastError(), "loss launch");
+    for (int li = h->L - 1; li >= 0 && !s; --li) s = ps.backward(li, st);
+    if (!s) s = ps.finalize(st);
+    if (s) return s;
+  }
   return cuda_check(h, cudaGetLastError(), "loss_grad launch");
 }
 
@@ -505,9 +563,9 @@ cudaError_t copy_rows(float* dst, const float* src, int rows, int64_t ld, int64_
                            cudaMemcpyDeviceToDevice, st);
 }
 
-pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params, void* d_ws,
-                size_t ws_bytes, double* d_loss, float* d_grad, void* stream, bool want_grad,
-                float* d_grad_terms = nullptr, float* d_grad_ff = nullptr) {
+// Argument and state checks of one call; the mean normalisation of its pass(es).
+pinn_status check_call(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
+                       void* d_ws, double* d_loss, float* d_grad, bool want_grad, float* d_grad_terms, PassCtx* pc) {
   if (!h) return PINN_ERR_INVALID_ARG;
   if (!prob || !d_params || !d_ws || !d_loss || (want_grad && !d_grad && !d_grad_terms)) {
     set_err(h, "NULL argument"); return PINN_ERR_INVALID_ARG;
@@ -526,10 +584,8 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
   pinn_status s = validate_batch(h, b);
   if (s) return s;
   if (h->spec.ff_m && !h->ff_B) { set_err(h, "Fourier-feature matrix not set (pinn_set_ff_matrix)"); return PINN_ERR_INVALID_ARG; }
-  cudaStream_t st = (cudaStream_t)stream;
-  char* ws = (char*)d_ws;
   const int64_t N = b->n_res + b->n_ic + b->n_bc;
-  PassCtx pc{b->n_res, b->n_ic, b->n_bc, true, true, nullptr};
+  *pc = PassCtx{b->n_res, b->n_ic, b->n_bc, true, true, nullptr};
   if (h->global_counts) {
     // a shard of a larger batch: every mean is over the whole batch's points
     if (b->n_res > h->g_res || b->n_ic > h->g_ic || b->n_bc > h->g_bc) {
@@ -540,12 +596,24 @@ pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, c
       set_err(h, "temporal causality needs every segment's loss, not one shard's");
       return PINN_ERR_UNSUPPORTED;
     }
-    pc.N_res = h->g_res; pc.N_ic = h->g_ic; pc.N_bc = h->g_bc;
+    pc->N_res = h->g_res; pc->N_ic = h->g_ic; pc->N_bc = h->g_bc;
   }
   if (h->causal_M > 0 && h->chunk_points > 0 && N > h->chunk_points) {
     set_err(h, "temporal causality needs all points in one pass (the weights depend on every segment)");
     return PINN_ERR_UNSUPPORTED;
   }
+  return PINN_OK;
+}
+
+pinn_status run(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params, void* d_ws,
+                size_t ws_bytes, double* d_loss, float* d_grad, void* stream, bool want_grad,
+                float* d_grad_terms = nullptr, float* d_grad_ff = nullptr) {
+  PassCtx pc;
+  pinn_status s = check_call(h, prob, b, d_params, d_ws, d_loss, d_grad, want_grad, d_grad_terms, &pc);
+  if (s) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  const int64_t N = b->n_res + b->n_ic + b->n_bc;
   if (h->chunk_points <= 0 || N <= h->chunk_points)
     return run_pass(h, prob, b, d_params, ws, ws_bytes, d_loss, d_grad, st, want_grad, pc, d_grad_terms, d_grad_ff);
 
@@ -649,6 +717,52 @@ namespace pinn {
 pinn_status loss_grad_eager(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
                             void* d_ws, size_t ws_bytes, double* d_loss, float* d_grad, void* stream) {
   return run_kind(h, 1, prob, b, d_params, d_ws, ws_bytes, d_loss, d_grad, nullptr, stream);
+}
+
+struct StagedPass {
+  Pass pass;
+};
+
+pinn_status staged_create(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
+                          void* d_ws, size_t ws_bytes, double* d_loss, float* d_grad, StagedPass** out) {
+  *out = nullptr;
+  PassCtx pc;
+  pinn_status s = check_call(h, prob, b, d_params, d_ws, d_loss, d_grad, true, nullptr, &pc);
+  if (s) return s;
+  if (h->chunk_points > 0 && b->n_res + b->n_ic + b->n_bc > h->chunk_points) {
+    set_err(h, "a staged pass covers the whole batch in one pass (no point chunking)");
+    return PINN_ERR_UNSUPPORTED;
+  }
+  StagedPass* sp = new (std::nothrow) StagedPass();
+  if (!sp) return PINN_ERR_OOM;
+  Pass& p = sp->pass;
+  p.h = h; p.prob = prob; p.b = b; p.d_params = d_params; p.ws = (char*)d_ws; p.d_loss = d_loss; p.d_grad = d_grad;
+  p.want_grad = true; p.pc = pc;
+  s = p.init(ws_bytes);
+  if (s) { delete sp; return s; }
+  *out = sp;
+  return PINN_OK;
+}
+
+void staged_destroy(StagedPass* sp) { delete sp; }
+
+int staged_forward_levels(const StagedPass* sp) { return sp->pass.h->L - sp->pass.h->first_gemm; }
+
+pinn_status staged_prologue(StagedPass* sp, cudaStream_t st) { return sp->pass.prologue(st); }
+
+pinn_status staged_forward(StagedPass* sp, int level, cudaStream_t st) {
+  return sp->pass.forward(sp->pass.h->first_gemm + level, st);
+}
+
+pinn_status staged_output(StagedPass* sp, cudaStream_t st) { return sp->pass.output(0, st); }
+
+pinn_status staged_backward(StagedPass* sp, int level, cudaStream_t st) {
+  return sp->pass.backward(sp->pass.h->L - 1 - level, st);
+}
+
+pinn_status staged_finalize(StagedPass* sp, cudaStream_t st) {
+  const pinn_status s = sp->pass.finalize(st);
+  return s ? s : cuda_check(sp->pass.h, cudaGetLastError(), "loss_grad launch");
 }
 
 }  // namespace pinn

@@ -10,6 +10,8 @@
 
 namespace pinn {
 
+struct TcBatch;   // grouped tensor-core launches (tc.h)
+
 // Jet rows per point: r=0 value, r=1,2 first derivatives, r=3 either a
 // second-order row (Burgers d2/dx2, Navier-Stokes Laplacian) or a third first
 // derivative (Maxwell d/dt).  The column layout (tiles of 64 points, blocked by
@@ -103,6 +105,7 @@ struct pinn_handle {
   cudaGraphExec_t graph_exec = nullptr;
   pinn_graph_key graph_key{};
   int act = PINN_ACT_TANH;   // hidden activation; sine keeps Z and runs on CUDA cores
+  pinn::TcBatch* tc_batch = nullptr;   // set: tensor-core GEMMs are collected for a grouped launch
   float omega0 = 1.f;
   char err[512] = {0};
   // phase profiler (pinn_set_profiling)
@@ -278,5 +281,23 @@ void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float 
 // (the launch sequence only; it allocates nothing).
 pinn_status loss_grad_eager(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
                             void* d_ws, size_t ws_bytes, double* d_loss, float* d_grad, void* stream);
+
+// The stages of one whole-batch loss + gradient pass (the launch sequence of
+// pinn_loss_grad split where the many-network step interleaves networks): the
+// prologue (RWF weights, input jets), forward levels 0 .. staged_forward_levels()-1
+// (one hidden GEMM each), the output/loss stage, backward levels 0 .. L-1 (hidden
+// layer L-1 first), and the gradient finalisation.  Run in that order on one stream
+// they enqueue exactly pinn_loss_grad's launches.  staged_create validates like
+// pinn_loss_grad and refuses point chunking (PINN_ERR_UNSUPPORTED).
+struct StagedPass;
+pinn_status staged_create(pinn_handle* h, const pinn_problem* prob, const pinn_batch* b, const float* d_params,
+                          void* d_ws, size_t ws_bytes, double* d_loss, float* d_grad, StagedPass** out);
+void staged_destroy(StagedPass* sp);
+int staged_forward_levels(const StagedPass* sp);
+pinn_status staged_prologue(StagedPass* sp, cudaStream_t st);
+pinn_status staged_forward(StagedPass* sp, int level, cudaStream_t st);
+pinn_status staged_output(StagedPass* sp, cudaStream_t st);
+pinn_status staged_backward(StagedPass* sp, int level, cudaStream_t st);
+pinn_status staged_finalize(StagedPass* sp, cudaStream_t st);
 
 }  // namespace pinn

@@ -19,11 +19,26 @@ namespace pinn {
 // the compute type (the low half of the two-term BF16 weight used by the forward
 // GEMM).  blockIdx.y selects the layer.
 // ------------------------------------------------------------------------------------
+// One 32 x 32 tile of layer blockIdx.y per block iteration: the row-major outputs are
+// stored straight from the loads, the transposed ones through a shared-memory tile, so
+// every store of a warp is one contiguous row segment (a store per element at stride
+// fout would scatter each warp's writes over 32 rows).
+constexpr int RWF_T = 32;
+
 template <typename T>
-__global__ void k_rwf_prep(RwfArgs a) {
+__device__ __forceinline__ void rwf_split(float w, int prec, T& wh, T& wl) {
+  // high / low halves of the weight in the compute type (BF16 rounding; TF32 truncation)
+  const float whf = (prec == PINN_TF32) ? tf32_trunc(w) : to_f<T>(from_f<T>(w));
+  wh = from_f<T>(whf);
+  wl = from_f<T>(w - whf);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rwf_prep(RwfArgs a) {
+  __shared__ float tw[RWF_T][RWF_T + 1];
   const int l = blockIdx.y;
   const int fin = a.fin[l], fout = a.fout[l];
-  const int64_t n = (int64_t)fin * fout;
+  const int tj_n = (fin + RWF_T - 1) / RWF_T, ntiles = tj_n * ((fout + RWF_T - 1) / RWF_T);
   const float* V = a.params + a.offV[l];
   const float* s = a.rwf ? a.params + a.offs[l] : nullptr;
   float* W32 = reinterpret_cast<float*>(a.ws + a.w32[l]);
@@ -32,25 +47,46 @@ __global__ void k_rwf_prep(RwfArgs a) {
   float* WT32 = reinterpret_cast<float*>(a.ws + a.wt32[l]);
   T* Wlo = reinterpret_cast<T*>(a.ws + a.wlo[l]);
   T* WTlo = reinterpret_cast<T*>(a.ws + a.wtlo[l]);
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / fin), j = (int)(idx % fin);
-    float w = V[idx];
-    if (s) w *= expf(s[i]);
-    W32[idx] = w;
-    // high / low halves of the weight in the compute type (BF16 rounding; TF32 truncation)
-    const float whf = (a.prec == PINN_TF32) ? tf32_trunc(w) : to_f<T>(from_f<T>(w));
-    const T wh = from_f<T>(whf);
-    Wc[idx] = wh;
-    const T wl = from_f<T>(w - whf);
-    Wlo[idx] = wl;
-    WTlo[(int64_t)j * fout + i] = wl;
-    WTc[(int64_t)j * fout + i] = wh;
-    WT32[(int64_t)j * fout + i] = w;
+  const int tx = threadIdx.x % RWF_T, ty = threadIdx.x / RWF_T;   // 32 x 8 threads
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int i0 = (t / tj_n) * RWF_T, j0 = (t % tj_n) * RWF_T;
+    for (int r = ty; r < RWF_T; r += 256 / RWF_T) {
+      const int i = i0 + r, j = j0 + tx;
+      float w = 0.f;
+      if (i < fout && j < fin) {
+        const int64_t idx = (int64_t)i * fin + j;
+        w = V[idx];
+        if (s) w *= expf(s[i]);
+        T wh, wl;
+        rwf_split<T>(w, a.prec, wh, wl);
+        W32[idx] = w;
+        Wc[idx] = wh;
+        Wlo[idx] = wl;
+      }
+      tw[r][tx] = w;
+    }
+    __syncthreads();
+    for (int r = ty; r < RWF_T; r += 256 / RWF_T) {
+      const int j = j0 + r, i = i0 + tx;
+      if (i < fout && j < fin) {
+        const float w = tw[tx][r];
+        T wh, wl;
+        rwf_split<T>(w, a.prec, wh, wl);
+        const int64_t tidx = (int64_t)j * fout + i;
+        WT32[tidx] = w;
+        WTc[tidx] = wh;
+        WTlo[tidx] = wl;
+      }
+    }
+    __syncthreads();
   }
 }
 
 void launch_rwf_prep(const RwfArgs& a, cudaStream_t st) {
-  dim3 grid(128, a.L1);
+  int tiles = 1;
+  for (int l = 0; l < a.L1; ++l)
+    tiles = std::max(tiles, ((a.fin[l] + RWF_T - 1) / RWF_T) * ((a.fout[l] + RWF_T - 1) / RWF_T));
+  dim3 grid(std::min(tiles, 1024), a.L1);
   if (a.prec == PINN_BF16) k_rwf_prep<__nv_bfloat16><<<grid, 256, 0, st>>>(a);
   else k_rwf_prep<float><<<grid, 256, 0, st>>>(a);
 }

@@ -34,6 +34,8 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <new>
+#include <vector>
 
 #include "jet.cuh"
 #include "ptx.cuh"
@@ -81,6 +83,46 @@ struct TcParams {
   int stall;           // test hook: the MMA issuer first waits on a barrier nothing arrives on
 };
 
+// One GEMM of a grouped launch: its tensor maps (the GEMM kernel's four, or the fused
+// adjoint's three), its parameters, and the blocks of the grouped grid it owns.  Each
+// GEMM keeps the CTA count and work split it has when launched alone.
+struct TcGroupEntry {   // 128-byte aligned (CUtensorMap)
+  CUtensorMap map[4];
+  TcParams p;
+  int block0;   // first block of the grouped grid that runs this GEMM
+  int grid;     // its block count
+};
+
+// Orders this thread's later TMA reads of the entry's tensor maps after the writes that
+// put them in global memory (the table is rewritten by the host between captures).
+__device__ __forceinline__ void acquire_maps(const TcGroupEntry& g, int nmaps) {
+  for (int i = 0; i < nmaps; ++i)
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&g.map[i]) : "memory");
+}
+
+// The entry that owns block b: the last one whose first block is <= b (block0 ascends).
+__device__ __forceinline__ int group_of_block(const TcGroupEntry* __restrict__ tab, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].block0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Where a CTA sits in the launch: the hardware indices of a single launch (read where
+// used, as a plain kernel would), or its share of a grouped launch.
+struct SingleGrid {
+  __device__ __forceinline__ int bx() const { return (int)blockIdx.x; }
+  __device__ __forceinline__ int gdim() const { return (int)gridDim.x; }
+};
+struct GroupShare {
+  int b, g;
+  __device__ __forceinline__ int bx() const { return b; }
+  __device__ __forceinline__ int gdim() const { return g; }
+};
+
 template <bool TF32, int MODE, bool SPLIT>
 struct Cfg {
   static constexpr int ES = TF32 ? 4 : 2;
@@ -122,11 +164,12 @@ __device__ __forceinline__ void store_pm8(float* pm, int64_t c0, int M, int m, c
 // adjoint cannot be written in the activations (the sign of cos is lost), so the
 // forward epilogue also stores the pre-activation jets Z (FP32) and the adjoint
 // epilogue evaluates the rule from them.
-template <bool TF32, int MODE, bool SPLIT, bool SINE = false>
-__global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
-              const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
-              const TcParams p) {
+// The body runs as CTA grid.bx() of grid.gdim() CTAs over the GEMM that p and the maps
+// describe: the whole grid of a single launch, or one GEMM's share of a grouped launch.
+template <bool TF32, int MODE, bool SPLIT, bool SINE, typename Grid>
+__device__ __forceinline__ void tc_gemm_body(const CUtensorMap* mapA, const CUtensorMap* mapA2,
+                                             const CUtensorMap* mapB, const CUtensorMap* mapBlo, const TcParams& p,
+                                             const Grid grid) {
   using C = Cfg<TF32, MODE, SPLIT>;
   using T = typename std::conditional<TF32, float, __nv_bfloat16>::type;
   // weight gradient with 256-row tiles: two 128-row accumulators (TMEM columns 0..255 and
@@ -198,7 +241,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+      for (int t = grid.bx(); t < total && !*abort_flag; t += grid.gdim()) {
         int mb, nb, k0, k1;
         coords(t, mb, nb, k0, k1);
         for (int kb = k0; kb < k1; ++kb) {
@@ -211,28 +254,28 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
           const int kx = kb * C::BKE;
           if (C::KPM) {
             // A: weights [M][K]; B: point-major jets [NC][K], columns nb*BN.. (both 2-D, K-major)
-            tma_load_2d(sa, &mapA, &full[stage], kx, mb * BM);
-            if (SPLIT) tma_load_2d(sa2, &mapA2, &full[stage], kx, mb * BM);
-            tma_load_2d(sb, &mapB, &full[stage], kx, nb * BN);
+            tma_load_2d(sa, mapA, &full[stage], kx, mb * BM);
+            if (SPLIT) tma_load_2d(sa2, mapA2, &full[stage], kx, mb * BM);
+            tma_load_2d(sb, mapB, &full[stage], kx, nb * BN);
           } else if (C::B_MN) {
             // A: weights [M][K] (2-D); B: jet tile nb, rows kx..kx+BKE (3-D, tile-major)
-            tma_load_2d(sa, &mapA, &full[stage], kx, mb * BM);
-            if (SPLIT) tma_load_2d(sa2, &mapA2, &full[stage], kx, mb * BM);
+            tma_load_2d(sa, mapA, &full[stage], kx, mb * BM);
+            if (SPLIT) tma_load_2d(sa2, mapA2, &full[stage], kx, mb * BM);
 #pragma unroll
             for (int j = 0; j < C::NBOX; ++j)
-              tma_load_3d(sb + j * C::BOX_BYTES, &mapB, &full[stage], j * C::BOXN, kx, nb);
+              tma_load_3d(sb + j * C::BOX_BYTES, mapB, &full[stage], j * C::BOXN, kx, nb);
             if (C::VLO) {
 #pragma unroll
               for (int j = 0; j < TILE_PTS / C::BOXN; ++j)
-                tma_load_3d(sb + C::B_BYTES + j * C::BOX_BYTES, &mapBlo, &full[stage], j * C::BOXN, kx, nb);
+                tma_load_3d(sb + C::B_BYTES + j * C::BOX_BYTES, mapBlo, &full[stage], j * C::BOXN, kx, nb);
             }
           } else {
             // weight gradient: K runs over jet columns, 256 / BKE K-blocks per tile
             constexpr int KPT = TILE_COLS / C::BKE;
             const int tz = kb / KPT, tx = (kb % KPT) * C::BKE;
-            tma_load_3d(sa, &mapA, &full[stage], tx, mb * MROWS, tz);
-            if (DW2) tma_load_3d(sa2, &mapA, &full[stage], tx, mb * MROWS + BM, tz);
-            tma_load_3d(sb, &mapB, &full[stage], tx, nb * BN, tz);
+            tma_load_3d(sa, mapA, &full[stage], tx, mb * MROWS, tz);
+            if (DW2) tma_load_3d(sa2, mapA, &full[stage], tx, mb * MROWS + BM, tz);
+            tma_load_3d(sb, mapB, &full[stage], tx, nb * BN, tz);
           }
           if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
         }
@@ -248,7 +291,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
       // test hook: a dependency that is never satisfied, so the bounded wait expires and
       // the whole CTA takes the abort path (status bit 1, teardown below)
       const bool stalled = p.stall && !mbar_wait(never, 0, abort_flag, p.status, p.wait_ns);
-      for (int t = blockIdx.x; t < total && !*abort_flag && !stalled; t += gridDim.x, ++local) {
+      for (int t = grid.bx(); t < total && !*abort_flag && !stalled; t += grid.gdim(), ++local) {
         int mb, nb, k0, k1;
         coords(t, mb, nb, k0, k1);
         const int buf = DW2 ? 0 : local & 1;
@@ -309,7 +352,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
     const int ct = threadIdx.x - 32 * (2 + EPI_WARPS);
     int stage = 0;
     uint32_t phase = 0, lo_phase = 0;
-    for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+    for (int t = grid.bx(); t < total && !*abort_flag; t += grid.gdim()) {
       int mb, nb, k0, k1;
       coords(t, mb, nb, k0, k1);
       bool ok = true;
@@ -388,11 +431,11 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
       }
     };
     if constexpr (MODE == TC_ADJ && !SINE) {
-      if ((int)blockIdx.x < total) load_z(blockIdx.x, 0);
+      if (grid.bx() < total) load_z(grid.bx(), 0);
     }
 
     int local = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+    for (int t = grid.bx(); t < total; t += grid.gdim(), ++local) {
       int mb, nb, k0, k1;
       coords(t, mb, nb, k0, k1);
       const int buf = DW2 ? 0 : local & 1;
@@ -420,7 +463,7 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
 #pragma unroll
             for (int j = 0; j < ZW; ++j) zw[r][j] = znext[r][j];
           if (u + 1 < UNITS) load_z(t, u + 1);
-          else if (t + (int)gridDim.x < total) load_z(t + gridDim.x, 0);
+          else if (t + grid.gdim() < total) load_z(t + grid.gdim(), 0);
         }
         if (!mvalid) return;
         const int pc = unit_col(u);                                   // first point of the unit in its tile
@@ -588,6 +631,25 @@ __global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
   }
 }
 
+template <bool TF32, int MODE, bool SPLIT, bool SINE = false>
+__global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
+              const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
+              const __grid_constant__ TcParams p) {
+  tc_gemm_body<TF32, MODE, SPLIT, SINE>(&mapA, &mapA2, &mapB, &mapBlo, p, SingleGrid{});
+}
+
+// Grouped launch: the GEMMs of several networks (or layers) side by side, each entry of
+// the device table holding one GEMM's tensor maps and parameters and its block range.
+template <bool TF32, int MODE, bool SPLIT, bool SINE = false>
+__global__ void __launch_bounds__(Cfg<TF32, MODE, SPLIT>::NTHREADS, 1)
+    k_tc_gemm_group(const TcGroupEntry* __restrict__ tab, const int n) {
+  const TcGroupEntry& g = tab[group_of_block(tab, n, (int)blockIdx.x)];
+  acquire_maps(g, 4);
+  tc_gemm_body<TF32, MODE, SPLIT, SINE>(&g.map[0], &g.map[1], &g.map[2], &g.map[3], g.p,
+                                        GroupShare{(int)blockIdx.x - g.block0, g.grid});
+}
+
 // ---- host side ------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -635,27 +697,86 @@ bool tc_map3(CUtensorMap* m, const void* base, bool fp32, uint64_t tcols, uint64
 
 namespace {
 
+// Reserves the dynamic shared memory of kernel `kern` once per kernel.
+template <typename K>
+pinn_status reserve_smem(pinn_handle* h, K kern, size_t bytes, bool& done, const char* what) {
+  if (done) return PINN_OK;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+    cudaGetLastError();   // do not leave the failure for the next launch to report
+    snprintf(h->err, sizeof(h->err), "%s: cannot reserve %zu bytes of shared memory", what, bytes);
+    return PINN_ERR_CUDA;
+  }
+  done = true;
+  return PINN_OK;
+}
+
+pinn_status launch_check(pinn_handle* h, const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return PINN_OK;
+  snprintf(h->err, sizeof(h->err), "%s launch: %s", what, cudaGetErrorString(e));
+  return PINN_ERR_CUDA;
+}
+
+// Grouped launch of n table entries (blocks in all) of one GEMM kernel variant.
+template <bool TF32, int MODE, bool SPLIT, bool SINE>
+pinn_status launch_group(pinn_handle* h, const TcGroupEntry* d_tab, int n, int blocks, cudaStream_t st) {
+  using C = Cfg<TF32, MODE, SPLIT>;
+  auto kern = k_tc_gemm_group<TF32, MODE, SPLIT, SINE>;
+  static bool attr_set = false;   // per instantiation
+  pinn_status s = reserve_smem(h, kern, C::SMEM, attr_set, "grouped tcgen05 kernel");
+  if (s) return s;
+  kern<<<blocks, C::NTHREADS, C::SMEM, st>>>(d_tab, n);
+  return launch_check(h, "grouped tcgen05 kernel");
+}
+
+pinn_status launch_adjdw_group(pinn_handle* h, const TcGroupEntry* d_tab, int n, int blocks, cudaStream_t st);
+
+}  // namespace
+
+// Tensor-core GEMMs collected from several handles (tc_batch_attach) and issued as
+// grouped launches: one per kernel variant, the GEMMs with the most work first.
+struct TcBatch {
+  using GroupFn = pinn_status (*)(pinn_handle*, const TcGroupEntry*, int, int, cudaStream_t);
+  struct Item {
+    GroupFn fn;
+    TcGroupEntry e;
+    double work;   // tiles x K iterations: the order of the grouped grid
+  };
+  std::vector<Item> pending;
+  std::vector<TcGroupEntry> table;   // every issued entry, in device-table order
+  TcGroupEntry* d_table = nullptr;
+  size_t capacity = 0;               // entries d_table holds
+  int launches = 0;
+};
+
+namespace {
+
+pinn_status batch_add(TcBatch* b, TcBatch::GroupFn fn, const CUtensorMap* maps, int nmaps, const TcParams& p,
+                      int grid) {
+  TcBatch::Item it{};
+  it.fn = fn;
+  for (int i = 0; i < nmaps; ++i) it.e.map[i] = maps[i];
+  it.e.p = p;
+  it.e.grid = grid;
+  it.work = (double)p.m_tiles * p.n_tiles * std::max(p.k_iters, 1);
+  b->pending.push_back(it);
+  return PINN_OK;
+}
+
 template <bool TF32, int MODE, bool SPLIT, bool SINE = false>
 pinn_status launch(pinn_handle* h, const CUtensorMap& a, const CUtensorMap& a2, const CUtensorMap& b,
                    const CUtensorMap& blo, const TcParams& p, int grid, cudaStream_t st) {
+  if (h->tc_batch) {
+    const CUtensorMap maps[4] = {a, a2, b, blo};
+    return batch_add(h->tc_batch, &launch_group<TF32, MODE, SPLIT, SINE>, maps, 4, p, grid);
+  }
   using C = Cfg<TF32, MODE, SPLIT>;
   auto kern = k_tc_gemm<TF32, MODE, SPLIT, SINE>;
   static bool attr_set = false;   // per instantiation
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) != cudaSuccess) {
-      cudaGetLastError();   // do not leave the failure for the next launch to report
-      snprintf(h->err, sizeof(h->err), "tcgen05 kernel: cannot reserve %zu bytes of shared memory", C::SMEM);
-      return PINN_ERR_CUDA;
-    }
-    attr_set = true;
-  }
+  pinn_status s = reserve_smem(h, kern, C::SMEM, attr_set, "tcgen05 kernel");
+  if (s) return s;
   kern<<<grid, C::NTHREADS, C::SMEM, st>>>(a, a2, b, blo, p);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    snprintf(h->err, sizeof(h->err), "tcgen05 kernel launch: %s", cudaGetErrorString(e));
-    return PINN_ERR_CUDA;
-  }
-  return PINN_OK;
+  return launch_check(h, "tcgen05 kernel");
 }
 
 int grid_for(const pinn_handle* h, int tiles) { return std::max(1, std::min(tiles, std::max(h->sm_count, 1))); }
@@ -858,9 +979,9 @@ constexpr size_t FZ_SMEM = (size_t)FZ_STAGES * FZ_STAGE + (size_t)FZ_ABUF * FZ_A
 static_assert(FZ_SMEM <= 227 * 1024, "fused adjoint: shared memory budget");
 constexpr int FZ_DW_COL = BN;                    // dW^T accumulator: TMEM columns 256..511
 
-__global__ void __launch_bounds__(FZ_NT, 1)
-    k_tc_adjdw(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapZ,
-               const __grid_constant__ CUtensorMap mapA, const TcParams p) {
+template <typename Grid>
+__device__ __forceinline__ void tc_adjdw_body(const CUtensorMap* mapW, const CUtensorMap* mapZ,
+                                              const CUtensorMap* mapA, const TcParams& p, const Grid grid) {
   using T = __nv_bfloat16;
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned by offsetting the shared array itself (an integer round trip would
@@ -919,7 +1040,7 @@ __global__ void __launch_bounds__(FZ_NT, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+      for (int t = grid.bx(); t < total && !*abort_flag; t += grid.gdim()) {
         int mb, nb;
         coords(t, mb, nb);
         for (int kb = 0; kb < p.k_iters; ++kb) {
@@ -928,9 +1049,9 @@ __global__ void __launch_bounds__(FZ_NT, 1)
           uint8_t* sz = sw + FZ_WB;
           mbar_expect_tx(&full[stage], FZ_STAGE);
           inflight[stage] = (int)phase + 1;
-          tma_load_2d(sw, &mapW, &full[stage], kb * 64, mb * BM);
+          tma_load_2d(sw, mapW, &full[stage], kb * 64, mb * BM);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) tma_load_3d(sz + j * FZ_BOX, &mapZ, &full[stage], j * 64, kb * 64, nb);
+          for (int j = 0; j < 4; ++j) tma_load_3d(sz + j * FZ_BOX, mapZ, &full[stage], j * 64, kb * 64, nb);
           if (++stage == FZ_STAGES) { stage = 0; phase ^= 1; }
         }
       }
@@ -939,7 +1060,7 @@ __global__ void __launch_bounds__(FZ_NT, 1)
     // ---------------------------------------------------------------- A-tile producer
     if (lane == 0) {
       int local = 0;
-      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++local) {
+      for (int t = grid.bx(); t < total && !*abort_flag; t += grid.gdim(), ++local) {
         int mb, nb;
         coords(t, mb, nb);
         const int ab = local & 1;
@@ -949,7 +1070,7 @@ __global__ void __launch_bounds__(FZ_NT, 1)
         a_inflight[ab] = (int)aph + 1;
         uint8_t* at = abase + ab * FZ_AT;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) tma_load_3d(at + j * FZ_ABOX, &mapA, &a_full[ab], j * 64, mb * BM, nb);
+        for (int j = 0; j < 4; ++j) tma_load_3d(at + j * FZ_ABOX, mapA, &a_full[ab], j * 64, mb * BM, nb);
       }
     }
   } else if (warp == 1) {
@@ -963,7 +1084,7 @@ __global__ void __launch_bounds__(FZ_NT, 1)
       uint32_t phase = 0;
       int local = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < total && !*abort_flag && ok; t += gridDim.x, ++local) {
+      for (int t = grid.bx(); t < total && !*abort_flag && ok; t += grid.gdim(), ++local) {
         const int ab = local & 1;
         if (!mbar_wait(&a_full[ab], (uint32_t)(local >> 1) & 1, abort_flag, p.status, p.wait_ns)) { ok = false; break; }
         a_inflight[ab] = 0;
@@ -1013,7 +1134,7 @@ __global__ void __launch_bounds__(FZ_NT, 1)
     const uint32_t tq = tmem_base + ((uint32_t)(quad * 32) << 16);
     int local = 0;
     int mb_cta = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+    for (int t = grid.bx(); t < total; t += grid.gdim(), ++local) {
       int mb, nb;
       coords(t, mb, nb);
       mb_cta = mb;
@@ -1096,11 +1217,11 @@ __global__ void __launch_bounds__(FZ_NT, 1)
           if (j < p.e.dterms) dst[1 + j] = db[1 + j];
       }
     }
-    // this CTA's dW^T slab (its m-tile rows x all fout) as split partial blockIdx / m_tiles
+    // this CTA's dW^T slab (its m-tile rows x all fout) as split partial (CTA index) / m_tiles
     if (local > 0 && !*abort_flag && mbar_wait(dw_full, 0, abort_flag, p.status, p.wait_ns)) {
       tc_fence_after();
       const int m = mb_cta * BM + rr;
-      const int split = blockIdx.x / p.m_tiles;
+      const int split = grid.bx() / p.m_tiles;
       const int f0 = part * 128;
       for (int c = 0; c < 128; c += 16) {
         if (f0 + c >= p.K) break;
@@ -1143,6 +1264,18 @@ __global__ void __launch_bounds__(FZ_NT, 1)
   }
 }
 
+__global__ void __launch_bounds__(FZ_NT, 1)
+    k_tc_adjdw(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapZ,
+               const __grid_constant__ CUtensorMap mapA, const __grid_constant__ TcParams p) {
+  tc_adjdw_body(&mapW, &mapZ, &mapA, p, SingleGrid{});
+}
+
+__global__ void __launch_bounds__(FZ_NT, 1) k_tc_adjdw_group(const TcGroupEntry* __restrict__ tab, const int n) {
+  const TcGroupEntry& g = tab[group_of_block(tab, n, (int)blockIdx.x)];
+  acquire_maps(g, 3);
+  tc_adjdw_body(&g.map[0], &g.map[1], &g.map[2], g.p, GroupShare{(int)blockIdx.x - g.block0, g.grid});
+}
+
 int adjdw_grid(const pinn_handle* h, int fin, int64_t NC) {
   const int mt = (fin + BM - 1) / BM;
   const int tiles = mt * (int)(NC / TILE_COLS);
@@ -1179,23 +1312,103 @@ pinn_status tc_gemm_adjdw(pinn_handle* h, const void* WT, const void* Zbar, cons
     return PINN_ERR_INVALID_ARG;
   }
   p.nsplit = nsplit;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(k_tc_adjdw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM) != cudaSuccess) {
-      cudaGetLastError();
-      snprintf(h->err, sizeof(h->err), "fused adjoint kernel: cannot reserve %zu bytes of shared memory", FZ_SMEM);
-      return PINN_ERR_CUDA;
-    }
-    attr_set = true;
+  if (h->tc_batch) {
+    const CUtensorMap maps[3] = {mw, mz, ma};
+    return batch_add(h->tc_batch, &launch_adjdw_group, maps, 3, p, grid);
   }
+  static bool attr_set = false;
+  pinn_status s = reserve_smem(h, k_tc_adjdw, FZ_SMEM, attr_set, "fused adjoint kernel");
+  if (s) return s;
   k_tc_adjdw<<<grid, FZ_NT, FZ_SMEM, st>>>(mw, mz, ma, p);
-  const cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) {
-    snprintf(h->err, sizeof(h->err), "fused adjoint launch: %s", cudaGetErrorString(err));
+  return launch_check(h, "fused adjoint");
+}
+
+namespace {
+
+pinn_status launch_adjdw_group(pinn_handle* h, const TcGroupEntry* d_tab, int n, int blocks, cudaStream_t st) {
+  static bool attr_set = false;
+  pinn_status s = reserve_smem(h, k_tc_adjdw_group, FZ_SMEM, attr_set, "grouped fused adjoint kernel");
+  if (s) return s;
+  k_tc_adjdw_group<<<blocks, FZ_NT, FZ_SMEM, st>>>(d_tab, n);
+  return launch_check(h, "grouped fused adjoint");
+}
+
+}  // namespace
+
+TcBatch* tc_batch_create() { return new (std::nothrow) TcBatch(); }
+
+void tc_batch_destroy(TcBatch* b) {
+  if (!b) return;
+  if (b->d_table) cudaFree(b->d_table);
+  delete b;
+}
+
+void tc_batch_attach(pinn_handle* h, TcBatch* b) { h->tc_batch = b; }
+
+void tc_batch_reset(TcBatch* b) {
+  b->pending.clear();
+  b->table.clear();
+  b->launches = 0;
+}
+
+pinn_status tc_batch_reserve(TcBatch* b, size_t entries) {
+  if (entries <= b->capacity) return PINN_OK;
+  if (b->d_table) cudaFree(b->d_table);
+  b->d_table = nullptr;
+  b->capacity = 0;
+  if (cudaMalloc(&b->d_table, entries * sizeof(TcGroupEntry)) != cudaSuccess) {
+    cudaGetLastError();
+    return PINN_ERR_CUDA;
+  }
+  b->capacity = entries;
+  return PINN_OK;
+}
+
+pinn_status tc_batch_flush(TcBatch* b, pinn_handle* h, cudaStream_t st) {
+  // one grouped launch per kernel variant, in the order the variants first appeared
+  std::vector<TcBatch::GroupFn> fns;
+  for (const TcBatch::Item& it : b->pending)
+    if (std::find(fns.begin(), fns.end(), it.fn) == fns.end()) fns.push_back(it.fn);
+  pinn_status s = PINN_OK;
+  for (TcBatch::GroupFn fn : fns) {
+    std::vector<const TcBatch::Item*> items;
+    for (const TcBatch::Item& it : b->pending)
+      if (it.fn == fn) items.push_back(&it);
+    // the GEMMs with the most work first, so that the small ones fill the tail
+    std::stable_sort(items.begin(), items.end(),
+                     [](const TcBatch::Item* x, const TcBatch::Item* y) { return x->work > y->work; });
+    const size_t off = b->table.size();
+    if (off + items.size() > b->capacity) {
+      snprintf(h->err, sizeof(h->err), "grouped launch table full (%zu entries)", b->capacity);
+      s = PINN_ERR_INVALID_ARG;
+      break;
+    }
+    int blocks = 0;
+    for (const TcBatch::Item* it : items) {
+      TcGroupEntry e = it->e;
+      e.block0 = blocks;
+      blocks += e.grid;
+      b->table.push_back(e);
+    }
+    s = fn(h, b->d_table + off, (int)items.size(), blocks, st);
+    if (s) break;
+    ++b->launches;
+  }
+  b->pending.clear();
+  return s;
+}
+
+pinn_status tc_batch_upload(TcBatch* b) {
+  if (b->table.empty()) return PINN_OK;
+  if (cudaMemcpy(b->d_table, b->table.data(), b->table.size() * sizeof(TcGroupEntry), cudaMemcpyHostToDevice) !=
+      cudaSuccess) {
+    cudaGetLastError();
     return PINN_ERR_CUDA;
   }
   return PINN_OK;
 }
+
+int tc_batch_launches(const TcBatch* b) { return b->launches; }
 
 }  // namespace pinn
 

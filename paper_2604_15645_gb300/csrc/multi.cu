@@ -19,6 +19,11 @@
 // worker streams longest first (each to the stream with the least estimated work so far,
 // the estimate being the jet-GEMM FLOPs), so the big networks start at once and the
 // small ones fill in around them.
+//
+// pinn_multi_set_grouped(m, 1) captures the step level by level instead: every
+// network's pass runs in stages, and at each layer level the tensor-core GEMMs of all
+// networks are issued as one grouped launch per kernel variant (tc.h), with the other
+// launches of the level on the worker streams between a fork and a join.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -29,6 +34,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tc.h"
 
 namespace pinn {
 const void* adam_kernel();
@@ -46,6 +52,8 @@ struct pinn_multi {
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t adam_node = nullptr;
   std::string key;                      // buffers / sizes / engines the graph was captured with
+  bool grouped = false;                 // tensor-core GEMMs of one level share grouped launches
+  pinn::TcBatch* batch = nullptr;       // the grouped launches' collector and device table
   char err[512] = {0};
 };
 
@@ -108,8 +116,8 @@ std::string make_key(pinn_multi* m, const pinn_batch* batches, const float* p, c
                      const float* v, void* ws, const double* loss, void* stream) {
   std::string k;
   char buf[160];
-  snprintf(buf, sizeof(buf), "%p %p %p %p %p %p %p|", (const void*)p, (const void*)g, (const void*)mm, (const void*)v,
-           ws, (const void*)loss, stream);
+  snprintf(buf, sizeof(buf), "%p %p %p %p %p %p %p %d|", (const void*)p, (const void*)g, (const void*)mm,
+           (const void*)v, ws, (const void*)loss, stream, m->grouped ? 1 : 0);
   k += buf;
   for (int i = 0; i < m->n; ++i) {
     const pinn_batch& b = batches[i];
@@ -130,6 +138,22 @@ void drop_graph(pinn_multi* m) {
   m->key.clear();
 }
 
+// Worker stream of each network: longest processing time first, the biggest networks
+// first, each to the stream with the least estimated work so far.
+std::vector<int> assign_streams(const pinn_multi* m, const pinn_batch* batches) {
+  const int ns = (int)m->streams.size();
+  std::vector<int> order(m->n), stream_of(m->n, 0);
+  std::vector<double> cost(m->n), load(ns, 0.0);
+  for (int i = 0; i < m->n; ++i) { order[i] = i; cost[i] = net_cost(m->nets[i], batches[i]); }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[k] += cost[i];
+    stream_of[i] = k;
+  }
+  return stream_of;
+}
+
 struct AdamArgs {
   float lr, b1, b2, eps, bc1, bc2;
 };
@@ -143,15 +167,15 @@ pinn_status enqueue_step(pinn_multi* m, const pinn_problem* probs, const pinn_ba
   for (int k = 0; k < ns; ++k)
     if (cudaStreamWaitEvent(m->streams[k], m->fork, 0) != cudaSuccess) return PINN_ERR_CUDA;
   // longest-processing-time-first: biggest networks first, each to the least loaded stream
+  const std::vector<int> stream_of = assign_streams(m, batches);
   std::vector<int> order(m->n);
-  std::vector<double> cost(m->n), load(ns, 0.0);
+  std::vector<double> cost(m->n);
   for (int i = 0; i < m->n; ++i) { order[i] = i; cost[i] = net_cost(m->nets[i], batches[i]); }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   for (int i : order) {
-    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    load[k] += cost[i];
     pinn_status s = pinn_loss_grad(m->nets[i], &probs[i], &batches[i], d_p + m->poff[i], ws + ws_off[i], ws_sz[i],
-                                   d_loss + (int64_t)i * PINN_LOSS_TERMS, d_g + m->poff[i], m->streams[k]);
+                                   d_loss + (int64_t)i * PINN_LOSS_TERMS, d_g + m->poff[i],
+                                   m->streams[stream_of[i]]);
     if (s) {
       snprintf(m->err, sizeof(m->err), "network %d: %s", i, pinn_last_error(m->nets[i]));
       return s;
@@ -161,6 +185,91 @@ pinn_status enqueue_step(pinn_multi* m, const pinn_problem* probs, const pinn_ba
     if (cudaEventRecord(m->joins[k], m->streams[k]) != cudaSuccess || cudaStreamWaitEvent(st, m->joins[k], 0) != cudaSuccess)
       return PINN_ERR_CUDA;
   }
+  pinn::launch_adam(d_p, d_g, d_m, d_v, m->poff[m->n], ad.lr, ad.b1, ad.b2, ad.eps, ad.bc1, ad.bc2, st);
+  return cudaGetLastError() == cudaSuccess ? PINN_OK : PINN_ERR_CUDA;
+}
+
+// Table entries the grouped step can issue: one per forward GEMM, two per hidden layer
+// (adjoint and weight gradient) and one to spare.
+size_t grouped_entries(const pinn_multi* m) {
+  size_t n = 0;
+  for (const pinn_handle* h : m->nets) n += (size_t)(h->L - h->first_gemm) + 2 * (size_t)h->L + 1;
+  return n;
+}
+
+// One training step with grouped tensor-core launches (under stream capture on `st`).
+// Every network's pass runs in stages (internal.h), level by level over all networks:
+// the per-network launches of a level (RWF weights and input jets, CUDA-core GEMMs,
+// output/loss, reductions, finalisation) go to the worker streams, and the tensor-core
+// GEMMs of the level are collected and issued on `st` as one grouped launch per kernel
+// variant; the workers fork from `st` before a level and join it after.  The per-network
+// order of the launches is that of pinn_loss_grad, and the stages of one level of one
+// network touch disjoint outputs, so the results are those of the per-network step.
+pinn_status enqueue_grouped(pinn_multi* m, const pinn_problem* probs, const pinn_batch* batches, float* d_p,
+                            float* d_g, float* d_m, float* d_v, char* ws, const std::vector<size_t>& ws_off,
+                            const std::vector<size_t>& ws_sz, const AdamArgs& ad, double* d_loss, cudaStream_t st) {
+  const int n = m->n, ns = (int)m->streams.size();
+  std::vector<pinn::StagedPass*> sp(n, nullptr);
+  struct Cleanup {
+    pinn_multi* m;
+    std::vector<pinn::StagedPass*>& sp;
+    ~Cleanup() {
+      for (pinn::StagedPass* x : sp) pinn::staged_destroy(x);
+      for (pinn_handle* h : m->nets) pinn::tc_batch_attach(h, nullptr);
+    }
+  } cleanup{m, sp};
+  auto net_err = [&](int i, pinn_status s) {
+    snprintf(m->err, sizeof(m->err), "network %d: %s", i, pinn_last_error(m->nets[i]));
+    return s;
+  };
+  for (int i = 0; i < n; ++i) {
+    pinn_status s = pinn::staged_create(m->nets[i], &probs[i], &batches[i], d_p + m->poff[i], ws + ws_off[i],
+                                        ws_sz[i], d_loss + (int64_t)i * PINN_LOSS_TERMS, d_g + m->poff[i], &sp[i]);
+    if (s) return net_err(i, s);
+  }
+  const std::vector<int> stream_of = assign_streams(m, batches);
+  pinn::tc_batch_reset(m->batch);
+  for (pinn_handle* h : m->nets) pinn::tc_batch_attach(h, m->batch);
+  auto fork = [&]() {
+    if (cudaEventRecord(m->fork, st) != cudaSuccess) return false;
+    for (int k = 0; k < ns; ++k)
+      if (cudaStreamWaitEvent(m->streams[k], m->fork, 0) != cudaSuccess) return false;
+    return true;
+  };
+  auto join = [&]() {
+    for (int k = 0; k < ns; ++k)
+      if (cudaEventRecord(m->joins[k], m->streams[k]) != cudaSuccess || cudaStreamWaitEvent(st, m->joins[k], 0) != cudaSuccess)
+        return false;
+    return true;
+  };
+  // runs `stage` for every network that has it, then the level's grouped launches
+  auto level = [&](auto&& stage) -> pinn_status {
+    if (!fork()) return PINN_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {
+      const pinn_status s = stage(i, m->streams[stream_of[i]]);
+      if (s) return net_err(i, s);
+    }
+    const pinn_status s = pinn::tc_batch_flush(m->batch, m->nets[0], st);
+    if (s) return net_err(0, s);
+    return join() ? PINN_OK : PINN_ERR_CUDA;
+  };
+  int fwd_levels = 0, bwd_levels = 0;
+  for (int i = 0; i < n; ++i) {
+    fwd_levels = std::max(fwd_levels, pinn::staged_forward_levels(sp[i]));
+    bwd_levels = std::max(bwd_levels, m->nets[i]->L);
+  }
+  pinn_status s = level([&](int i, cudaStream_t ws_) { return pinn::staged_prologue(sp[i], ws_); });
+  for (int l = 0; l < fwd_levels && !s; ++l)
+    s = level([&](int i, cudaStream_t ws_) {
+      return l < pinn::staged_forward_levels(sp[i]) ? pinn::staged_forward(sp[i], l, ws_) : PINN_OK;
+    });
+  if (!s) s = level([&](int i, cudaStream_t ws_) { return pinn::staged_output(sp[i], ws_); });
+  for (int l = 0; l < bwd_levels && !s; ++l)
+    s = level([&](int i, cudaStream_t ws_) {
+      return l < m->nets[i]->L ? pinn::staged_backward(sp[i], l, ws_) : PINN_OK;
+    });
+  if (!s) s = level([&](int i, cudaStream_t ws_) { return pinn::staged_finalize(sp[i], ws_); });
+  if (s) return s;
   pinn::launch_adam(d_p, d_g, d_m, d_v, m->poff[m->n], ad.lr, ad.b1, ad.b2, ad.eps, ad.bc1, ad.bc2, st);
   return cudaGetLastError() == cudaSuccess ? PINN_OK : PINN_ERR_CUDA;
 }
@@ -205,7 +314,8 @@ PINN_API pinn_status pinn_multi_create(const pinn_spec* specs, int32_t n_nets, p
     m->poff[i + 1] = m->poff[i] + P;
   }
   const int ns = std::min(n_nets, kMaxStreams);
-  bool ok = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) == cudaSuccess &&
+  m->batch = pinn::tc_batch_create();
+  bool ok = m->batch && cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) == cudaSuccess &&
             cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; ok && k < ns; ++k) {
     cudaStream_t s;
@@ -232,6 +342,7 @@ PINN_API pinn_status pinn_multi_destroy(pinn_multi* m) {
   for (cudaEvent_t e : m->joins) cudaEventDestroy(e);
   if (m->fork) cudaEventDestroy(m->fork);
   if (m->cap) cudaStreamDestroy(m->cap);
+  pinn::tc_batch_destroy(m->batch);
   for (pinn_handle* h : m->nets) pinn_destroy(h);
   delete m;
   return PINN_OK;
@@ -275,6 +386,18 @@ PINN_API pinn_status pinn_multi_get_config(const pinn_multi* m, int32_t net, int
   return PINN_OK;
 }
 
+PINN_API pinn_status pinn_multi_set_grouped(pinn_multi* m, int32_t on) {
+  if (!m) return PINN_ERR_INVALID_ARG;
+  m->grouped = on != 0;
+  return PINN_OK;
+}
+
+PINN_API pinn_status pinn_multi_get_grouped(const pinn_multi* m, int32_t* on) {
+  if (!m || !on) return PINN_ERR_INVALID_ARG;
+  *on = m->grouped ? 1 : 0;
+  return PINN_OK;
+}
+
 PINN_API pinn_status pinn_multi_get_engine(const pinn_multi* m, int32_t net, int32_t* cuda_cores) {
   if (!m || !cuda_cores || net < 0 || net >= m->n) return PINN_ERR_INVALID_ARG;
   *cuda_cores = (m->nets[net]->spec.flags & PINN_FLAG_CUDA_CORES) ? 1 : 0;
@@ -307,13 +430,22 @@ PINN_API pinn_status pinn_multi_train_step(pinn_multi* m, const pinn_problem* pr
   const std::string key = make_key(m, batches, d_params, d_grad, d_m, d_v, d_ws, d_loss, stream);
   if (key != m->key) {
     drop_graph(m);
+    if (m->grouped) {
+      // the table is rewritten below: no replay still reading it may be in flight
+      if (cudaStreamSynchronize(st) != cudaSuccess || pinn::tc_batch_reserve(m->batch, grouped_entries(m)) != PINN_OK) {
+        cudaGetLastError();
+        snprintf(m->err, sizeof(m->err), "cannot allocate the grouped launch table");
+        return PINN_ERR_OOM;
+      }
+    }
     // capture on the handle's own stream; the graph is launched on the caller's
     if (cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
       cudaGetLastError();
       snprintf(m->err, sizeof(m->err), "cannot begin stream capture");
       return PINN_ERR_CUDA;
     }
-    s = enqueue_step(m, probs, batches, d_params, d_grad, d_m, d_v, ws, off, sz, ad, d_loss, m->cap);
+    s = m->grouped ? enqueue_grouped(m, probs, batches, d_params, d_grad, d_m, d_v, ws, off, sz, ad, d_loss, m->cap)
+                   : enqueue_step(m, probs, batches, d_params, d_grad, d_m, d_v, ws, off, sz, ad, d_loss, m->cap);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(m->cap, &g);
     if (s || e != cudaSuccess || !g) {
@@ -321,6 +453,12 @@ PINN_API pinn_status pinn_multi_train_step(pinn_multi* m, const pinn_problem* pr
       cudaGetLastError();
       if (!s) snprintf(m->err, sizeof(m->err), "graph capture failed: %s", cudaGetErrorString(e));
       return s ? s : PINN_ERR_CUDA;
+    }
+    // the grouped launches' table, read by the graph's kernels from the first replay on
+    if (m->grouped && pinn::tc_batch_upload(m->batch) != PINN_OK) {
+      cudaGraphDestroy(g);
+      snprintf(m->err, sizeof(m->err), "grouped launch table upload failed");
+      return PINN_ERR_CUDA;
     }
     // find the Adam node, whose scalar arguments change from step to step
     size_t nn = 0;

@@ -49,4 +49,28 @@ int tc_adjdw_splits(const pinn_handle* h, int fin, int64_t NC);
 pinn_status tc_gemm_adjdw(pinn_handle* h, const void* WT, const void* Zbar, const void* Ain, int fin, int fout,
                           int64_t NC, const EpiArgs& e, float* dwpart, int nsplit, cudaStream_t st);
 
+// ---- grouped launches ---------------------------------------------------------------
+// A batch collects the tensor-core GEMMs that attached handles would launch and issues
+// them as grouped launches, one per kernel variant: each GEMM keeps the CTA count and
+// work split of its own launch (so its results are bitwise those of that launch), and
+// the CTAs of all GEMMs share one grid, the GEMMs with the most work first.  Each
+// grouped launch reads its GEMMs' tensor maps and parameters from a device table.
+struct TcBatch;
+TcBatch* tc_batch_create();
+void tc_batch_destroy(TcBatch* b);
+// Routes the tensor-core launches of h into b (nullptr: launch them directly again).
+void tc_batch_attach(pinn_handle* h, TcBatch* b);
+// Forgets the collected GEMMs and the table built so far.
+void tc_batch_reset(TcBatch* b);
+// Makes room for `entries` table entries on the device (cudaMalloc: not under capture).
+pinn_status tc_batch_reserve(TcBatch* b, size_t entries);
+// Issues the GEMMs collected since the last flush on st (errors are reported on h).
+// The launches read table entries that tc_batch_upload writes: upload before the
+// launches run (for a captured graph: after the capture, before the first replay).
+pinn_status tc_batch_flush(TcBatch* b, pinn_handle* h, cudaStream_t st);
+// Copies the table to the device (synchronous).
+pinn_status tc_batch_upload(TcBatch* b);
+// Grouped launches issued since the last reset.
+int tc_batch_launches(const TcBatch* b);
+
 }  // namespace pinn

@@ -1,7 +1,8 @@
 """Many independent networks in one graph-captured training step (pinn_multi_*):
 per-network loss and gradient against the FP64 oracle, the fused Adam update,
-bitwise equality of graph replays with eager single-network steps, and the engine
-autotuner's JSON cache."""
+bitwise equality of graph replays with eager single-network steps and of the grouped
+per-level launches with the per-network launch sequences (the default), and the
+engine autotuner's JSON cache."""
 import json
 
 import numpy as np
@@ -158,3 +159,51 @@ def test_full_family_every_network_against_torch_float64(cuda_lib):
         rt, rg = run_oracle(spec, p, None, sub, pr)
         assert_parity(t.cpu().numpy(), gg.cpu().numpy().astype(np.float64), rt, rg, TOL["bf16"], f"family net {i}",
                       spec=spec)
+
+
+def _two_steps(api, fam, multi, p0, grouped):
+    multi.grouped = grouped
+    assert multi.grouped == grouped
+    params = torch.tensor(p0, device="cuda")
+    grad, m, v = (torch.zeros_like(params) for _ in range(3))
+    losses = []
+    for step in (1, 2):
+        losses.append(multi.train_step(params, grad, m, v, step=step, lr=1e-3).clone())
+    torch.cuda.synchronize()
+    assert multi.status_poll() == 0
+    return params, grad, m, v, losses
+
+
+@pytest.mark.parametrize("precision,config", [("bf16", "tc"), ("bf16", "tc_unfused"), ("bf16", "tc_unfused_dw128"),
+                                              ("bf16", "mixed"), ("tf32", "tc"), ("fp32", "cuda_cores")])
+def test_grouped_step_equals_per_network_step(cuda_lib, precision, config):
+    """One grouped tcgen05 launch per layer level over all networks gives bitwise the
+    step of the per-network launch sequences (each GEMM keeps its CTAs and work split),
+    for every kernel configuration and a mix of them; both graphs are replayed twice."""
+    api, fam, multi, p0 = _setup(12, 1536, precision)
+    cfgs = api.PinnMulti.CONFIGS
+    for i in range(multi.n):
+        multi.set_config(i, cfgs[i % len(cfgs)] if config == "mixed" else config)
+    a = _two_steps(api, fam, multi, p0, True)
+    b = _two_steps(api, fam, multi, p0, False)
+    for x, y in zip(a[:4], b[:4]):
+        assert torch.equal(x, y)
+    for x, y in zip(a[4], b[4]):
+        assert torch.equal(x, y)
+
+
+def test_full_family_grouped_equals_per_network_step(cuda_lib):
+    """The benchmark's 64-network family at full size after autotuning: the grouped
+    step and the per-network step agree bitwise over two replays."""
+    from paper_2604_15645_gb300 import api
+    fam = make_family(64)
+    multi = api.PinnMulti([s for s, _, _, _ in fam], "bf16")
+    multi.set_inputs([api.DeviceBatch.from_host(b) for _, _, b, _ in fam],
+                     [api.make_problem(pr.nu) for _, _, _, pr in fam])
+    p0 = np.concatenate([p for _, p, _, _ in fam]).astype(np.float32)
+    params = torch.tensor(p0, device="cuda")
+    multi.autotune(params, torch.zeros_like(params))
+    a = _two_steps(api, fam, multi, p0, True)
+    b = _two_steps(api, fam, multi, p0, False)
+    for x, y in zip(a[:4], b[:4]):
+        assert torch.equal(x, y)
