@@ -630,7 +630,13 @@ int out_loss_blocks(int64_t NP) {
 // lane mapping as k_out_loss (point group pg = lane / 8, feature slice sl = lane % 8);
 // the swizzle spreads a warp's eight features over all banks.  Results (loss and
 // segment partials, dW, bias partials, Zbar_L) and their summation order per block
-// are those of k_out_loss.
+// are those of k_out_loss.  The consumers read the ring with ordinary shared loads
+// (generic proxy) and the producer refills it with bulk copies (async proxy): the
+// mbarrier's release/acquire orders only the generic proxy, so every consumer fences
+// the proxies (fence.proxy.async) after its last read of a slot and before releasing
+// it; without the fence a refill could overwrite a slot under reads still in flight
+// (measured: loss changes of 1e-5 to 1e-4 relative at width 512 that depended on
+// what else was in L2).
 // ------------------------------------------------------------------------------------
 constexpr int OT_CONS = 128;                     // consumer threads (4 warps)
 constexpr int OT_THREADS = OT_CONS + 32;         // + the producer warp
@@ -798,6 +804,7 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
             for (int r = 0; r < 4; ++r) U[j][c][r] = fmaf(wc, v[r][j], U[j][c][r]);
         }
       }
+      fence_proxy_async_smem();   // these reads before the producer's next bulk copy into the slot
       mbar_arrive(&empty[stage]);
       if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
     }
@@ -913,6 +920,7 @@ __global__ void __launch_bounds__(OT_THREADS) k_out_loss_tma(const __grid_consta
           if (pg == 0) sdb[warp * w + f] += s;
         }
       }
+      fence_proxy_async_smem();   // these reads before the producer's next bulk copy into the slot
       mbar_arrive(&empty[stage]);
       if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
     }
@@ -1019,7 +1027,7 @@ cudaError_t launch_out_loss_tma(const OutArgs& a, int nblocks, cudaStream_t st) 
 // weights and seeds of k_out_loss_tma.  tcgen05's smallest M is 64 and would leave 61
 // of 64 accumulator lanes idle for d_out = 3; these MMAs keep the fragments in
 // registers beside the residual and jet arithmetic.  The A_L chunks arrive through
-// the same TMA ring; the ldmatrix fragments the weight gradient reads from them are
+// the same TMA ring (each slot released after a proxy fence, as there); the ldmatrix fragments the weight gradient reads from them are
 // exactly the activations the tanh-jet adjoint needs for the same (feature, point)
 // pairs.  The four warps stmatrix their adjoints into one staging chunk laid out like
 // the load boxes, which leaves as four bulk tensor stores (per-lane 32-byte stores
@@ -1367,6 +1375,7 @@ __global__ void __launch_bounds__(OT_THREADS, 2) k_out_loss_mma(const __grid_con
           mma_bf16_16816(acc1[b][1], af, r[2], r[3]);
         }
       }
+      fence_proxy_async_smem();   // these reads before the producer's next bulk copy into the slot
       mbar_arrive(&empty[stage]);
       if (++stage == OT_STAGES) { stage = 0; phase ^= 1; }
       }
@@ -1723,17 +1732,14 @@ __global__ void __launch_bounds__(FIN_THREADS, 12) k_finalize_grad(FinalizeArgs 
       // summed in element order
       const float4* q4 = reinterpret_cast<const float4*>(dbp + (int64_t)i * nbp);
       const int n4 = nbp >> 2, T = blockDim.x;
-      int p4 = threadIdx.x;
-      for (; p4 + 3 * T < n4; p4 += 4 * T) {
+      // batches of four loads in flight, the last one predicated (same order of adds)
+      for (int p4 = threadIdx.x; p4 < n4; p4 += 4 * T) {
         float4 x[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = __ldcs(q4 + p4 + u * T);
+        for (int u = 0; u < 4; ++u) x[u] = (p4 + u * T < n4) ? __ldcs(q4 + p4 + u * T) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) { ab[0].add(x[u].x); ab[0].add(x[u].y); ab[0].add(x[u].z); ab[0].add(x[u].w); }
-      }
-      for (; p4 < n4; p4 += T) {
-        const float4 x = __ldcs(q4 + p4);
-        ab[0].add(x.x); ab[0].add(x.y); ab[0].add(x.z); ab[0].add(x.w);
+        for (int u = 0; u < 4; ++u)
+          if (p4 + u * T < n4) { ab[0].add(x[u].x); ab[0].add(x[u].y); ab[0].add(x[u].z); ab[0].add(x[u].w); }
       }
     } else {
       for (int p = threadIdx.x; p < nbp; p += blockDim.x) {
@@ -1762,7 +1768,9 @@ __global__ void __launch_bounds__(FIN_THREADS, 12) k_finalize_grad(FinalizeArgs 
         const float* base = part + (int64_t)i * fin + 4 * q;
         Acc2 a0, a1, a2, a3;
         // splits g, g + G, g + 2G, ... in that order; the loads of FIN_UNROLL splits
-        // are issued before any of them is added (the partials are read once: streaming)
+        // are issued before any of them is added (the partials are read once: streaming),
+        // and the remaining splits form one more batch, predicated, instead of a chain
+        // of single loads each waiting for the one before
         int s = g;
         for (; s + (FIN_UNROLL - 1) * G < ns; s += FIN_UNROLL * G) {
           float4 x[FIN_UNROLL];
@@ -1772,9 +1780,14 @@ __global__ void __launch_bounds__(FIN_THREADS, 12) k_finalize_grad(FinalizeArgs 
 #pragma unroll
           for (int u = 0; u < FIN_UNROLL; ++u) { a0.add(x[u].x); a1.add(x[u].y); a2.add(x[u].z); a3.add(x[u].w); }
         }
-        for (; s < ns; s += G) {
-          const float4 x = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)s * sstride));
-          a0.add(x.x); a1.add(x.y); a2.add(x.z); a3.add(x.w);
+        if (s < ns) {
+          float4 x[FIN_UNROLL - 1];
+#pragma unroll
+          for (int u = 0; u < FIN_UNROLL - 1; ++u)
+            if (s + u * G < ns) x[u] = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)(s + u * G) * sstride));
+#pragma unroll
+          for (int u = 0; u < FIN_UNROLL - 1; ++u)
+            if (s + u * G < ns) { a0.add(x[u].x); a1.add(x[u].y); a2.add(x[u].z); a3.add(x[u].w); }
         }
         d[0] = a0.value(); d[1] = a1.value(); d[2] = a2.value(); d[3] = a3.value();
       }

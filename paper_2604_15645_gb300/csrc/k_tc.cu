@@ -1208,7 +1208,10 @@ __device__ __forceinline__ void tc_adjdw_body(const CUtensorMap* mapW, const CUt
           }
         }
       }
-      mbar_arrive(&a_empty[ab]);          // done with this A tile in shared memory
+      // done with this A tile: its ordinary shared loads ordered before the next bulk copy
+      // into the buffer (the mbarrier orders the generic proxy only)
+      fence_proxy_async_smem();
+      mbar_arrive(&a_empty[ab]);
       if (mvalid && p.e.dbpart) {
         float* dst = p.e.dbpart + ((int64_t)m * (p.n_tiles * PARTS) + nb * PARTS + part) * (1 + p.e.dterms);
         dst[0] = db[0];
